@@ -1,0 +1,263 @@
+"""FP64 CPU oracle of the Galerkin-FFT homogenization method (arXiv 2110.00733).
+
+TEST INFRASTRUCTURE.  This package is the slow, obviously correct reference
+that the GPU library is checked against.  Only the tests, the smoke check and
+the CPU-baseline leg of the benchmark may import it; the GPU library never
+does, and this package never imports the GPU library.
+
+The numerical work is in ``hom_oracle.c`` (plain C, FP64, its own
+mixed-radix FFT); this module compiles it with gcc on first use and wraps it
+with ctypes.  Fields are 6 x V arrays of Mandel components (section 2.1 stores
+the strain at each voxel centre); the wrappers below take and return tensor
+components where marked.
+
+Parity pins (tests/test_oracle_*.py): FFT against numpy.fft, the rotated
+frequency against its tan form and against the real-space stencil symbol, the
+projector's idempotence / Hermitian symmetry / rank, homogeneous and laminate
+closed forms, the void laminate, MINRES against SciPy, and a dense real-space
+direct solve on odd grids.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hom_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SQ2 = np.sqrt(2.0)
+
+
+def build(force: bool = False) -> str:
+    """Compile hom_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_fft3d.argtypes = [ip, dp, ctypes.c_int]
+        lib.orc_fft1d.argtypes = [ctypes.c_int, dp, ctypes.c_int]
+        lib.orc_frequency.argtypes = [ip, ip, ctypes.c_int, dp]
+        lib.orc_gamma_apply.argtypes = [dp, dp, dp]
+        lib.orc_stiffness_mandel.argtypes = [ctypes.c_double, ctypes.c_double, dp]
+        lib.orc_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, dp, dp]
+        lib.orc_rhs.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int, dp, dp]
+        lib.orc_project.argtypes = [ip, ctypes.c_int, dp, dp]
+        lib.MATVEC = ctypes.CFUNCTYPE(None, ctypes.c_void_p, dp, dp)
+        lib.orc_minres.argtypes = [ctypes.c_long, lib.MATVEC, ctypes.c_void_p,
+                                   dp, dp, ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.orc_minres.restype = ctypes.c_int
+        lib.orc_solve.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
+                                  dp, dp, dp, dp]
+        lib.orc_solve.restype = ctypes.c_int
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(seq):
+    arr = (ctypes.c_int * len(seq))(*[int(s) for s in seq])
+    return arr
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# --------------------------------------------------------------------------
+# Mandel <-> tensor components (e11, e22, e33, e23, e13, e12)
+# --------------------------------------------------------------------------
+
+def tensor_to_mandel(t):
+    """(..., 6) or (6, ...) tensor components -> Mandel; axis 0 is the component."""
+    m = np.array(t, dtype=np.float64, copy=True)
+    m[3:] *= SQ2
+    return m
+
+
+def mandel_to_tensor(m):
+    t = np.array(m, dtype=np.float64, copy=True)
+    t[3:] /= SQ2
+    return t
+
+
+# --------------------------------------------------------------------------
+# Wrapped steps
+# --------------------------------------------------------------------------
+
+def fft3d(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Unnormalised 3-D DFT of a complex array (3-D), sign -1 forward."""
+    lib = _load()
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    assert a.ndim == 3
+    out = a.copy()
+    lib.orc_fft3d(_ip(a.shape), out.view(np.float64).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double)), int(sign))
+    return out
+
+
+def fft1d(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    lib = _load()
+    out = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    lib.orc_fft1d(int(out.size), out.view(np.float64).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double)), int(sign))
+    return out
+
+
+def frequency(shape, k, deriv: int) -> np.ndarray:
+    """Frequency vector (3 complex) at FFT index k; deriv 0 continuous, 1 rotated."""
+    lib = _load()
+    out = np.zeros(6)
+    lib.orc_frequency(_ip(shape), _ip(k), int(deriv), _dp(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def gamma_apply(xi, tau_mandel) -> np.ndarray:
+    """Projector of eq. (galop) at one frequency on a complex Mandel 6-vector."""
+    lib = _load()
+    xi = np.asarray(xi, dtype=np.complex128)
+    t = np.asarray(tau_mandel, dtype=np.complex128)
+    xr = np.ascontiguousarray(np.stack([xi.real, xi.imag], -1).reshape(-1))
+    tr = np.ascontiguousarray(np.stack([t.real, t.imag], -1).reshape(-1))
+    out = np.zeros(12)
+    lib.orc_gamma_apply(_dp(xr), _dp(tr), _dp(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def stiffness_mandel(E: float, nu: float) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(36)
+    lib.orc_stiffness_mandel(float(E), float(nu), _dp(out))
+    return out.reshape(6, 6)
+
+
+def _phi(phi):
+    p = np.ascontiguousarray(phi, dtype=np.float64)
+    assert p.ndim == 3
+    return p
+
+
+def apply(phi, E, nu, deriv, eps_mandel) -> np.ndarray:
+    """A(eps) of eq. (linearOp); eps, result: (6, N1, N2, N3) Mandel."""
+    lib = _load()
+    p = _phi(phi)
+    e = np.ascontiguousarray(eps_mandel, dtype=np.float64).reshape((6,) + p.shape)
+    out = np.empty_like(e)
+    lib.orc_apply(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), _dp(e), _dp(out))
+    return out
+
+
+def rhs(phi, E, nu, deriv, Ebar_tensor) -> np.ndarray:
+    """b of eq. (gallin) for a macro strain in tensor components (strain control)."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    out = np.empty((6,) + p.shape)
+    lib.orc_rhs(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), _dp(Eb), _dp(out))
+    return out
+
+
+def project(shape, deriv, field_mandel) -> np.ndarray:
+    """F^-1 G F applied to a real 6 x V field (no material)."""
+    lib = _load()
+    f = np.ascontiguousarray(field_mandel, dtype=np.float64).reshape((6,) + tuple(shape))
+    out = np.empty_like(f)
+    lib.orc_project(_ip(shape), int(deriv), _dp(f), _dp(out))
+    return out
+
+
+def minres(matvec, b, tol=1e-12, max_it=1000):
+    """Oracle MINRES on a Python matvec (used to pin it against SciPy)."""
+    lib = _load()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = b.size
+    x = np.zeros(n)
+    hist = np.zeros(max_it + 1)
+    rel = ctypes.c_double(0.0)
+
+    def cb(_ctx, xp, yp):
+        xv = np.ctypeslib.as_array(xp, shape=(n,))
+        yv = np.ctypeslib.as_array(yp, shape=(n,))
+        yv[:] = matvec(xv.copy())
+
+    cfun = lib.MATVEC(cb)
+    it = lib.orc_minres(n, cfun, None, _dp(b), _dp(x), float(tol), int(max_it),
+                        ctypes.byref(rel), _dp(hist))
+    return x, int(it), float(rel.value), hist[: it + 1]
+
+
+def solve(phi, E, nu, deriv, Ebar_tensor, tol=1e-10, max_it=5000, history=False):
+    """Full Galerkin-MINRES solve for one macro strain (tensor components).
+
+    Returns dict with eps_tilde (6,N1,N2,N3 Mandel), sigma_mean (tensor comps),
+    iterations, est_residual, true_residual (eq. galres)."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    eps = np.zeros((6,) + p.shape)
+    sig = np.zeros(6)
+    info = np.zeros(3)
+    hist = np.zeros(max_it + 1)
+    lib.orc_solve(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), _dp(Eb),
+                  float(tol), int(max_it), _dp(eps), _dp(sig), _dp(info), _dp(hist))
+    it = int(info[0])
+    out = {
+        "eps_tilde": eps,
+        "sigma_mean": mandel_to_tensor(sig),
+        "iterations": it,
+        "est_residual": float(info[1]),
+        "true_residual": float(info[2]),
+    }
+    if history:
+        out["history"] = hist[: it + 1].copy()
+    return out
+
+
+UNIT_CASES = np.eye(6)  # tensor components; shear cases have e_ab = e_ba = 1
+
+
+def effective_stiffness(phi, E, nu, deriv, tol=1e-10, max_it=5000):
+    """6x6 Voigt effective stiffness from the six unit macro strains.
+
+    Voigt convention sigma = C . (e11, e22, e33, 2e23, 2e13, 2e12); a unit
+    shear tensor strain e_ab = 1 is an engineering strain of 2, so those
+    columns are the mean stress divided by 2."""
+    C = np.zeros((6, 6))
+    sols = []
+    for J in range(6):
+        s = solve(phi, E, nu, deriv, UNIT_CASES[J], tol=tol, max_it=max_it)
+        gamma = 1.0 if J < 3 else 2.0
+        C[:, J] = s["sigma_mean"] / gamma
+        sols.append(s)
+    return C, sols

@@ -1,0 +1,532 @@
+/*
+ * hom_oracle.c -- plain FP64 CPU oracle of the Galerkin-FFT homogenization
+ * method of Lucarini, Cobian, Vilchez-Morales, Segurado, "Adaptation and
+ * validation of FFT methods for homogenization of lattice based materials"
+ * (arXiv 2110.00733).
+ *
+ * TEST INFRASTRUCTURE.  This file is the slow, obviously correct reference
+ * that the GPU library is checked against.  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it.  It shares no code,
+ * header, table or constant with the GPU library.
+ *
+ * Conventions (each a reading of the paper, listed in the design notes):
+ *   - grid n[0] x n[1] x n[2], C order (index n3 fastest), cell edges L_p = 1
+ *     (the projector is invariant under a rescaling of each xi_p by the same
+ *     factor, and all cells in the paper are cubic);
+ *   - strain/stress fields are stored as 6 Mandel components per voxel,
+ *     component-major: field[c*V + voxel], Mandel order
+ *     (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12), so that the Euclidean inner
+ *     product of two fields is the Frobenius product summed over voxels;
+ *   - forward DFT uses exp(-2 pi i k n / N), no normalisation; inverse uses
+ *     exp(+...) and the oracle divides by V itself.
+ *
+ * Nothing here is blocked, fused or reordered beyond the definitions: every
+ * step is the paper's formula written out with plain loops.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------------------ */
+/* 1-D DFT: recursive mixed-radix Cooley-Tukey, direct DFT for prime lengths. */
+/* Section 2.1: the transforms of eq. (gal) are discrete Fourier transforms   */
+/* evaluated with an FFT; this is a textbook decimation-in-time FFT.          */
+/* ------------------------------------------------------------------------ */
+
+static int smallest_factor(int n) {
+    for (int p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+/* out[k] = sum_j in[j*stride] * w[(j*k*(N/n)) mod N]   for k < n,
+ * where w[t] = exp(sign * 2 pi i t / N) is a table of the N-th roots of unity
+ * and n divides N.  scratch must hold n values. */
+static void dft_rec(const cplx *in, int stride, cplx *out, int n,
+                    const cplx *w, int N, cplx *scratch) {
+    if (n == 1) { out[0] = in[0]; return; }
+    int p = smallest_factor(n);
+    int step = N / n;                  /* w[step*t] = exp(sign 2 pi i t / n) */
+    if (p == n) {                      /* prime length: plain DFT */
+        for (int k = 0; k < n; ++k) {
+            cplx s = 0;
+            for (int j = 0; j < n; ++j)
+                s += in[(long)j * stride] * w[(long)step * ((long)j * k % n)];
+            out[k] = s;
+        }
+        return;
+    }
+    int m = n / p;
+    /* p sub-transforms of length m over the decimated sequences in[r + p j] */
+    for (int r = 0; r < p; ++r)
+        dft_rec(in + (long)r * stride, stride * p, out + r * m, m, w, N, scratch);
+    /* combine: X[k + q m] = sum_r exp(sign 2 pi i r (k + q m)/n) Y_r[k] */
+    for (int k = 0; k < m; ++k) {
+        for (int q = 0; q < p; ++q) {
+            cplx s = 0;
+            int kk = k + q * m;
+            for (int r = 0; r < p; ++r)
+                s += out[r * m + k] * w[(long)step * ((long)r * kk % n)];
+            scratch[kk] = s;
+        }
+    }
+    memcpy(out, scratch, sizeof(cplx) * n);
+}
+
+static cplx *roots_of_unity(int n, int sign) {
+    cplx *w = (cplx *)malloc(sizeof(cplx) * n);
+    for (int t = 0; t < n; ++t) {
+        double a = sign * 2.0 * PI * (double)t / (double)n;
+        w[t] = cos(a) + I * sin(a);
+    }
+    return w;
+}
+
+/* In-place unnormalised 3-D DFT of a complex array of shape n[0] x n[1] x n[2]
+ * (C order), sign = -1 forward, +1 inverse.  Applied axis by axis. */
+void orc_fft3d(const int n[3], double *data_ri, int sign) {
+    cplx *data = (cplx *)data_ri;
+    long V = (long)n[0] * n[1] * n[2];
+    long strides[3] = {(long)n[1] * n[2], n[2], 1};
+    for (int ax = 0; ax < 3; ++ax) {
+        int N = n[ax];
+        if (N == 1) continue;
+        cplx *w = roots_of_unity(N, sign);
+        long nlines = V / N;
+        long st = strides[ax];
+#pragma omp parallel
+        {
+            cplx *line = (cplx *)malloc(sizeof(cplx) * N);
+            cplx *res = (cplx *)malloc(sizeof(cplx) * N);
+            cplx *scr = (cplx *)malloc(sizeof(cplx) * N);
+#pragma omp for schedule(static)
+            for (long l = 0; l < nlines; ++l) {
+                /* line l: all indices except axis ax; base offset */
+                long outer = l / st, inner = l % st;
+                long base = outer * st * N + inner;
+                for (int j = 0; j < N; ++j) line[j] = data[base + j * st];
+                dft_rec(line, 1, res, N, w, N, scr);
+                for (int j = 0; j < N; ++j) data[base + j * st] = res[j];
+            }
+            free(line); free(res); free(scr);
+        }
+        free(w);
+    }
+}
+
+/* 1-D transform exposed for the FFT pins. */
+void orc_fft1d(int N, double *data_ri, int sign) {
+    int n[3] = {1, 1, N};
+    orc_fft3d(n, data_ri, sign);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Frequencies, eq. (freq) and the rotated scheme, eq. (freqrot).             */
+/* ------------------------------------------------------------------------ */
+
+/* Signed frequency index of FFT index k on an axis of N points:
+ * m = k for k < N/2, k - N otherwise (for even N, k = N/2 gives -N/2, the
+ * paper's n - N/2 = -N/2 end of [-pi, pi]). */
+static int signed_index(int k, int N) { return (2 * k < N) ? k : k - N; }
+
+static int is_nyquist(int k, int N) { return (N % 2 == 0) && (2 * k == N); }
+
+/* Frequency vector at FFT index (k1,k2,k3).
+ * deriv = 0: continuous, xi_p = i q_p N_p / L_p                (eq. freq)
+ * deriv = 1: rotated forward difference (Willot), eq. (freqrot):
+ *     xi'_p = i 2 (N_p/L_p) tan(q_p/2) prod_r 1/2 (1 + e^{i q_r}),
+ *   evaluated in the equivalent form
+ *     xi'_p = N_p (e^{i q_p} - 1) prod_{r != p} 1/2 (1 + e^{i q_r}),
+ *   since tan(q/2) (1 + e^{iq}) = -i (e^{iq} - 1); this form is finite at
+ *   q = +-pi where the tan form is infinity times zero. */
+void orc_frequency(const int n[3], const int k[3], int deriv, double xi_ri[6]) {
+    cplx xi[3];
+    double q[3];
+    for (int p = 0; p < 3; ++p) q[p] = 2.0 * PI * signed_index(k[p], n[p]) / n[p];
+    for (int p = 0; p < 3; ++p) {
+        if (deriv == 0) {
+            xi[p] = I * q[p] * n[p];
+        } else {
+            cplx v = n[p] * (cexp(I * q[p]) - 1.0);
+            for (int r = 0; r < 3; ++r)
+                if (r != p) v *= 0.5 * (1.0 + cexp(I * q[r]));
+            xi[p] = v;
+        }
+    }
+    for (int p = 0; p < 3; ++p) { xi_ri[2 * p] = creal(xi[p]); xi_ri[2 * p + 1] = cimag(xi[p]); }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mandel <-> tensor                                                          */
+/* ------------------------------------------------------------------------ */
+
+static const int MI[6] = {0, 1, 2, 1, 0, 0};  /* row of Mandel component c */
+static const int MJ[6] = {0, 1, 2, 2, 2, 1};  /* column                    */
+
+static void mandel_to_tensor(const cplx m[6], cplx t[3][3]) {
+    const double r2 = sqrt(2.0);
+    for (int c = 0; c < 6; ++c) {
+        cplx v = (c < 3) ? m[c] : m[c] / r2;
+        t[MI[c]][MJ[c]] = v;
+        t[MJ[c]][MI[c]] = v;
+    }
+}
+
+static void tensor_to_mandel(cplx t[3][3], cplx m[6]) {
+    const double r2 = sqrt(2.0);
+    for (int c = 0; c < 6; ++c) {
+        /* symmetric part of the (i,j) entry */
+        cplx v = 0.5 * (t[MI[c]][MJ[c]] + t[MJ[c]][MI[c]]);
+        m[c] = (c < 3) ? v : v * r2;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Galerkin projector, eq. (galop).                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Solve the 3x3 complex system K u = v by Gaussian elimination with partial
+ * pivoting.  Returns 0 if K is singular. */
+static int solve3(cplx K[3][3], cplx v[3], cplx u[3]) {
+    cplx A[3][4];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) A[i][j] = K[i][j];
+        A[i][3] = v[i];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (cabs(A[r][c]) > cabs(A[piv][c])) piv = r;
+        if (cabs(A[piv][c]) == 0.0) return 0;
+        if (piv != c)
+            for (int j = 0; j < 4; ++j) { cplx t = A[c][j]; A[c][j] = A[piv][j]; A[piv][j] = t; }
+        for (int r = c + 1; r < 3; ++r) {
+            cplx f = A[r][c] / A[c][c];
+            for (int j = c; j < 4; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    for (int i = 2; i >= 0; --i) {
+        cplx s = A[i][3];
+        for (int j = i + 1; j < 3; ++j) s -= A[i][j] * u[j];
+        u[i] = s / A[i][i];
+    }
+    return 1;
+}
+
+/* Projection of one frequency's 3x3 symmetric tensor onto the compatible
+ * strains {sym(u (x) xi)} at that frequency, orthogonal in the Hermitian
+ * Frobenius product -- the reading of the fourth branch of eq. (galop),
+ * [I^s_ijkl xi_j xi_l]^-1 xi_j xi_l, with the conjugate placed where a
+ * complex (rotated) xi needs it:
+ *   K_ik = I^s_ijkl conj(xi_j) xi_l = 1/2 (|xi|^2 delta_ik + xi_i conj(xi_k)),
+ *   v_i  = tau_ij conj(xi_j),   K u = v,   (G tau)_ij = 1/2 (u_i xi_j + u_j xi_i).
+ * Mandel components in and out (6 complex as re,im pairs).  xi = 0 gives 0,
+ * the strain-controlled branch of eq. (galop). */
+void orc_gamma_apply(const double xi_ri[6], const double tau_ri[12], double out_ri[12]) {
+    cplx xi[3], tm[6], t[3][3], K[3][3], v[3], u[3], o[3][3], om[6];
+    for (int p = 0; p < 3; ++p) xi[p] = xi_ri[2 * p] + I * xi_ri[2 * p + 1];
+    for (int c = 0; c < 6; ++c) tm[c] = tau_ri[2 * c] + I * tau_ri[2 * c + 1];
+    double n2 = 0;
+    for (int p = 0; p < 3; ++p) n2 += creal(xi[p] * conj(xi[p]));
+    if (n2 == 0.0) {
+        for (int c = 0; c < 12; ++c) out_ri[c] = 0.0;
+        return;
+    }
+    mandel_to_tensor(tm, t);
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            K[i][k] = 0.5 * ((i == k ? n2 : 0.0) + xi[i] * conj(xi[k]));
+    for (int i = 0; i < 3; ++i) {
+        v[i] = 0;
+        for (int j = 0; j < 3; ++j) v[i] += t[i][j] * conj(xi[j]);
+    }
+    if (!solve3(K, v, u)) {
+        for (int c = 0; c < 12; ++c) out_ri[c] = 0.0;
+        return;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) o[i][j] = 0.5 * (u[i] * xi[j] + u[j] * xi[i]);
+    tensor_to_mandel(o, om);
+    for (int c = 0; c < 6; ++c) { out_ri[2 * c] = creal(om[c]); out_ri[2 * c + 1] = cimag(om[c]); }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Material, operator A and right-hand side b (eqs. gallin, linearOp).        */
+/* ------------------------------------------------------------------------ */
+
+/* Isotropic stiffness C_m as a 6x6 Mandel matrix (lambda in the upper-left
+ * 3x3 block, 2 mu on the diagonal).  The local stiffness is C(x) = phi(x) C_m
+ * (Voigt rule, section 3.3). */
+void orc_stiffness_mandel(double E, double nu, double Cm[36]) {
+    double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double mu = E / (2.0 * (1.0 + nu));
+    for (int i = 0; i < 36; ++i) Cm[i] = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Cm[i * 6 + j] = lam;
+    for (int i = 0; i < 6; ++i) Cm[i * 6 + i] += 2.0 * mu;
+}
+
+typedef struct {
+    int n[3];
+    const double *phi;     /* V values in [0,1] */
+    double Cm[36];         /* Mandel stiffness of the lattice material */
+    int deriv;             /* 0 continuous, 1 rotated */
+} orc_problem;
+
+/* tau = C(x) : eps at every voxel (eps, tau: 6 x V Mandel). If eps_is_macro,
+ * eps points to a single 6-vector used at every voxel. */
+static void constitutive(const orc_problem *P, const double *eps, int eps_is_macro, cplx *tau) {
+    long V = (long)P->n[0] * P->n[1] * P->n[2];
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; ++x) {
+        double e[6];
+        for (int c = 0; c < 6; ++c) e[c] = eps_is_macro ? eps[c] : eps[(long)c * V + x];
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += P->Cm[i * 6 + j] * e[j];
+            tau[(long)i * V + x] = P->phi[x] * s;
+        }
+    }
+}
+
+/* out = F^-1 { G(xi) : F{ tau } }  (real part), tau: 6 x V complex, overwritten. */
+static void project_field(const orc_problem *P, cplx *tau, double *out) {
+    long V = (long)P->n[0] * P->n[1] * P->n[2];
+    for (int c = 0; c < 6; ++c) orc_fft3d(P->n, (double *)(tau + (long)c * V), -1);
+    int n1 = P->n[0], n2 = P->n[1], n3 = P->n[2];
+#pragma omp parallel for schedule(static)
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n2 * n3)), (int)((f / n3) % n2), (int)(f % n3)};
+        double o[12], t[12], xi[6];
+        int nyq = is_nyquist(k[0], n1) || is_nyquist(k[1], n2) || is_nyquist(k[2], n3);
+        if (nyq || (k[0] == 0 && k[1] == 0 && k[2] == 0)) {
+            /* eq. (galop): 0 at the Nyquist frequencies and, for strain-
+             * controlled components, at xi = 0 */
+            for (int c = 0; c < 6; ++c) tau[(long)c * V + f] = 0;
+            continue;
+        }
+        orc_frequency(P->n, k, P->deriv, xi);
+        for (int c = 0; c < 6; ++c) {
+            t[2 * c] = creal(tau[(long)c * V + f]);
+            t[2 * c + 1] = cimag(tau[(long)c * V + f]);
+        }
+        orc_gamma_apply(xi, t, o);
+        for (int c = 0; c < 6; ++c) tau[(long)c * V + f] = o[2 * c] + I * o[2 * c + 1];
+    }
+    for (int c = 0; c < 6; ++c) orc_fft3d(P->n, (double *)(tau + (long)c * V), +1);
+    for (long i = 0; i < 6 * V; ++i) out[i] = creal(tau[i]) / (double)V;
+}
+
+/* A(eps) = F^-1{ G : F{ C : eps } },  eq. (linearOp). */
+void orc_apply(const int n[3], const double *phi, double E, double nu, int deriv,
+               const double *eps, double *out) {
+    orc_problem P;
+    memcpy(P.n, n, sizeof P.n);
+    P.phi = phi; P.deriv = deriv;
+    orc_stiffness_mandel(E, nu, P.Cm);
+    long V = (long)n[0] * n[1] * n[2];
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
+    constitutive(&P, eps, 0, tau);
+    project_field(&P, tau, out);
+    free(tau);
+}
+
+/* b = -F^-1{ G : F{ C : Ebar } }  (strain control, sigma_bar = 0), eq. (gallin). */
+void orc_rhs(const int n[3], const double *phi, double E, double nu, int deriv,
+             const double Ebar[6], double *out) {
+    orc_problem P;
+    memcpy(P.n, n, sizeof P.n);
+    P.phi = phi; P.deriv = deriv;
+    orc_stiffness_mandel(E, nu, P.Cm);
+    long V = (long)n[0] * n[1] * n[2];
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
+    constitutive(&P, Ebar, 1, tau);
+    project_field(&P, tau, out);
+    for (long i = 0; i < 6 * V; ++i) out[i] = -out[i];
+    free(tau);
+}
+
+/* Projection alone, F^-1 G F applied to a real 6 x V field (no material). */
+void orc_project(const int n[3], int deriv, const double *in, double *out) {
+    orc_problem P;
+    memcpy(P.n, n, sizeof P.n);
+    P.phi = NULL; P.deriv = deriv;
+    long V = (long)n[0] * n[1] * n[2];
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
+    for (long i = 0; i < 6 * V; ++i) tau[i] = in[i];
+    project_field(&P, tau, out);
+    free(tau);
+}
+
+/* ------------------------------------------------------------------------ */
+/* MINRES (Paige & Saunders 1975), the Krylov solver the paper uses for the   */
+/* singular Galerkin system (section 2.1).  Written in the recurrence form of */
+/* Choi, Paige & Saunders (2011); x0 = 0; stops when the estimated relative   */
+/* residual phibar_k / beta_1 <= tol (eq. galres uses the true residual; the  */
+/* caller confirms it).                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef void (*orc_matvec_fn)(void *ctx, const double *x, double *y);
+
+static double dot(long n, const double *a, const double *b) {
+    double s = 0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Returns the number of iterations; *rel_res receives phibar_k / beta_1.
+ * hist (optional, max_it+1 entries) receives the estimated relative residual
+ * after each iteration (hist[0] = 1). */
+int orc_minres(long n, orc_matvec_fn A, void *ctx, const double *b, double *x,
+               double tol, int max_it, double *rel_res, double *hist) {
+    double *v_prev = (double *)calloc(n, sizeof(double));
+    double *v = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *w1 = (double *)calloc(n, sizeof(double));  /* w_{k-1} */
+    double *w2 = (double *)calloc(n, sizeof(double));  /* w_{k-2} */
+    for (long i = 0; i < n; ++i) x[i] = 0.0;
+    double beta1 = sqrt(dot(n, b, b));
+    if (hist) hist[0] = 1.0;
+    if (beta1 == 0.0) {
+        *rel_res = 0.0;
+        free(v_prev); free(v); free(p); free(w1); free(w2);
+        return 0;
+    }
+    for (long i = 0; i < n; ++i) v[i] = b[i] / beta1;
+    double beta = beta1;          /* beta_k (beta_1 for the first step) */
+    double phibar = beta1, c = -1.0, s = 0.0, dbar = 0.0, eps = 0.0;
+    int k = 0;
+    *rel_res = 1.0;
+    while (k < max_it) {
+        ++k;
+        A(ctx, v, p);                                         /* p = A v_k */
+        double alpha = dot(n, v, p);
+        double bk = (k == 1) ? 0.0 : beta;                    /* beta_k v_{k-1} term */
+        for (long i = 0; i < n; ++i) p[i] -= alpha * v[i] + bk * v_prev[i];
+        double beta_next = sqrt(dot(n, p, p));
+        /* apply the previous rotation, then make the new one */
+        double delta = c * dbar + s * alpha;
+        double gbar = s * dbar - c * alpha;
+        double eps_next = s * beta_next;
+        double dbar_next = -c * beta_next;
+        double gamma = hypot(gbar, beta_next);
+        if (gamma == 0.0) gamma = 1e-300;
+        c = gbar / gamma;
+        s = beta_next / gamma;
+        double tau = c * phibar;
+        phibar = s * phibar;
+        for (long i = 0; i < n; ++i) {
+            double wn = (v[i] - delta * w1[i] - eps * w2[i]) / gamma;
+            w2[i] = w1[i];
+            w1[i] = wn;
+            x[i] += tau * wn;
+        }
+        eps = eps_next;
+        dbar = dbar_next;
+        *rel_res = phibar / beta1;
+        if (hist) hist[k] = *rel_res;
+        if (*rel_res <= tol || beta_next == 0.0) break;
+        for (long i = 0; i < n; ++i) {
+            double vn = p[i] / beta_next;
+            v_prev[i] = v[i];
+            v[i] = vn;
+        }
+        beta = beta_next;
+    }
+    free(v_prev); free(v); free(p); free(w1); free(w2);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full solve: b, MINRES, true residual (eq. galres), mean stress.           */
+/* ------------------------------------------------------------------------ */
+
+/* Relative size of ||b|| / ||C : Ebar|| below which the right-hand side is
+ * FFT round-off and is taken as zero (the paper is silent on this case). */
+#define ORC_RHS_ZERO 1e-12
+
+typedef struct {
+    const int *n;
+    const double *phi;
+    double E, nu;
+    int deriv;
+} apply_ctx;
+
+static void apply_cb(void *ctx, const double *x, double *y) {
+    apply_ctx *a = (apply_ctx *)ctx;
+    orc_apply(a->n, a->phi, a->E, a->nu, a->deriv, x, y);
+}
+
+/* Solves A(eps_tilde) = b for one macro strain Ebar (Mandel), writes the
+ * fluctuation eps_tilde (6 x V Mandel), the volume-averaged stress
+ * <C : (Ebar + eps_tilde)> (Mandel, sig_mean[6]) and, in info[0..2], the
+ * iteration count, the estimated and the true relative residual. */
+int orc_solve(const int n[3], const double *phi, double E, double nu, int deriv,
+              const double Ebar[6], double tol, int max_it,
+              double *eps_tilde, double sig_mean[6], double info[3], double *hist) {
+    long V = (long)n[0] * n[1] * n[2];
+    long N6 = 6 * V;
+    double *b = (double *)malloc(sizeof(double) * N6);
+    double *r = (double *)malloc(sizeof(double) * N6);
+    orc_rhs(n, phi, E, nu, deriv, Ebar, b);
+    apply_ctx ctx = {n, phi, E, nu, deriv};
+    double Cm[36];
+    orc_stiffness_mandel(E, nu, Cm);
+    /* ||C : Ebar|| over the grid, the scale of the right-hand side */
+    double ce2 = 0.0, phi2 = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        double s = 0;
+        for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * Ebar[j];
+        ce2 += s * s;
+    }
+    for (long x = 0; x < V; ++x) phi2 += phi[x] * phi[x];
+    double ntau = sqrt(ce2 * phi2);
+    double est;
+    int it;
+    if (sqrt(dot(N6, b, b)) <= ORC_RHS_ZERO * ntau) {
+        /* b vanishes up to FFT round-off (e.g. a homogeneous cell, or a load
+         * the layout carries without any fluctuation): eps_tilde = 0. */
+        for (long i = 0; i < N6; ++i) { eps_tilde[i] = 0.0; b[i] = 0.0; }
+        if (hist) hist[0] = 0.0;
+        est = 0.0;
+        it = 0;
+    } else {
+        it = orc_minres(N6, apply_cb, &ctx, b, eps_tilde, tol, max_it, &est, hist);
+    }
+    /* true residual ||A eps - b|| / ||b|| */
+    orc_apply(n, phi, E, nu, deriv, eps_tilde, r);
+    double nb = sqrt(dot(N6, b, b)), nr = 0;
+    for (long i = 0; i < N6; ++i) { double d = r[i] - b[i]; nr += d * d; }
+    nr = sqrt(nr);
+    info[0] = it;
+    info[1] = est;
+    info[2] = (nb > 0) ? nr / nb : 0.0;
+    /* mean stress */
+    for (int i = 0; i < 6; ++i) sig_mean[i] = 0.0;
+    for (long x = 0; x < V; ++x) {
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * (Ebar[j] + eps_tilde[(long)j * V + x]);
+            sig_mean[i] += phi[x] * s;
+        }
+    }
+    for (int i = 0; i < 6; ++i) sig_mean[i] /= (double)V;
+    free(b); free(r);
+    return it;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,131 @@
+"""Seeded synthetic inputs for the homogenization solver.
+
+This module generates phase maps (per-voxel solid fraction phi) and macro
+strains.  It holds geometry and random-number generation only -- none of the
+homogenization arithmetic -- and it is the one module that both the CPU
+oracle's tests and the GPU library's tests and benchmark draw inputs from.
+
+* ``octet(n, rho, ...)``: octet-truss cell (FCC nearest-neighbour struts,
+  periodic capsules), phi from s^3 sub-voxel sampling (Voigt fine grid,
+  section 3.3), strut radius solved so that mean(phi) = rho (section 4.3).
+* ``laminate(n, ...)``: layered phase map normal to x1 (closed-form pins).
+* ``random_phi(n, ...)``: i.i.d. phases for operator parity tests.
+* ``unit_sphere_strain(rng)``: macro strain uniform on the Mandel unit sphere.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "voxelize.c")
+_LIB = os.path.join(_HERE, "_build", "libvoxelize.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                    _SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            fp = ctypes.POINTER(ctypes.c_float)
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.octet_phi.argtypes = [fp, ip, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int, fp]
+            lib.octet_phi.restype = ctypes.c_double
+            lib.octet_center_distance.argtypes = [fp, ip, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _grid(n):
+    if np.isscalar(n):
+        return (int(n),) * 3
+    g = tuple(int(v) for v in n)
+    assert len(g) == 3
+    return g
+
+
+def octet(n, rho: float, sub: int = 4, cells: int = 1, dist_perturb=None):
+    """Octet-truss phase map on an n^3 (or n1 x n2 x n3) grid.
+
+    Returns (phi float32 array of shape (n1,n2,n3), strut radius in
+    unit-cell lengths)."""
+    lib = _load()
+    g = _grid(n)
+    phi = np.zeros(g, dtype=np.float32)
+    pert = None
+    if dist_perturb is not None:
+        pert = np.ascontiguousarray(dist_perturb, dtype=np.float32).reshape(g)
+    r = lib.octet_phi(phi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                      (ctypes.c_int * 3)(*g), int(cells), float(rho), int(sub),
+                      None if pert is None else pert.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if r < 0:
+        raise RuntimeError("octet voxelizer could not bracket the strut radius")
+    return phi, float(r)
+
+
+def octet_center_distance(n, cells: int = 1):
+    lib = _load()
+    g = _grid(n)
+    out = np.zeros(g, dtype=np.float32)
+    lib.octet_center_distance(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              (ctypes.c_int * 3)(*g), int(cells))
+    return out
+
+
+def laminate(n, thickness, values, axis: int = 0):
+    """Layered phase map: consecutive layers of the given thicknesses (voxels)
+    along `axis`, taking the given phi values, repeated to fill the grid."""
+    g = _grid(n)
+    pattern = np.concatenate([np.full(t, v, dtype=np.float64)
+                              for t, v in zip(thickness, values)])
+    assert g[axis] % pattern.size == 0, "layers must tile the axis"
+    line = np.tile(pattern, g[axis] // pattern.size)
+    shape = [1, 1, 1]
+    shape[axis] = g[axis]
+    return np.broadcast_to(line.reshape(shape), g).astype(np.float64).copy()
+
+
+def random_phi(n, seed: int, void_fraction: float = 0.3, fractional: bool = True):
+    """i.i.d. phase map: a `void_fraction` of voxels empty (phi = 0), the rest
+    uniform in (0.05, 1] (or exactly 1 when fractional is False)."""
+    g = _grid(n)
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.05, 1.0, size=g) if fractional else np.ones(g)
+    phi[rng.random(g) < void_fraction] = 0.0
+    return phi
+
+
+def random_field(n, seed: int, ncomp: int = 6):
+    """Seeded standard-normal field of shape (ncomp, n1, n2, n3)."""
+    g = _grid(n)
+    return np.random.default_rng(seed).standard_normal((ncomp,) + g)
+
+
+def unit_sphere_strain(rng) -> np.ndarray:
+    """Macro strain, tensor components (e11,e22,e33,e23,e13,e12), drawn
+    uniformly on the unit sphere of the Mandel norm."""
+    m = rng.standard_normal(6)
+    m /= np.linalg.norm(m)
+    t = m.copy()
+    t[3:] /= np.sqrt(2.0)
+    return t
