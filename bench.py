@@ -1,0 +1,359 @@
+"""Benchmark: Galerkin-FFT + MINRES homogenization of an octet-truss cell.
+
+Workload (one step = one full solve through the C ABI): octet-truss unit cell
+on a 256^3 periodic grid, relative density 10 %, Voigt volume fractions from
+4^3 sub-voxel sampling, E = 110 GPa, nu = 0.3, rotated finite-difference
+frequencies, macro strain E11 = 1e-3, FP32 fields with FP64 Krylov scalars,
+tolerance 1e-6 on the FP64 true relative residual.  A step computes b, runs
+MINRES to the tolerance, checks the FP64 true residual and forms the mean
+stress.  Metric: MINRES voxel-iterations per second (V x iterations / time);
+ms_per_step is the time to the 1e-6 residual.
+
+Every field (403 MB per 6-component FP32 field) is larger than the 129 MB
+L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--n 256] [--rho 0.10]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+repository) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+E_M, NU_M = 110e9, 0.3
+MACRO = np.array([1e-3, 0, 0, 0, 0, 0], dtype=np.float64)
+TOL = 1e-6
+MAX_IT = 20000
+
+# Algorithmic bytes per voxel moved by each kernel of one MINRES iteration,
+# FP32 fields (the half spectrum holds 6 * (n3/2+1)/n3 complex64 per voxel).
+def kernel_bytes_per_voxel(n3: int) -> dict:
+    spec = 6 * 8 * (n3 // 2 + 1) / n3
+    f = 24.0                      # one 6-component FP32 field
+    return {
+        "x3_fwd": f + 4 + spec,   # read v, phi; write spectrum
+        "x2_fwd": 2 * spec,
+        "x1_gamma": 2 * spec,
+        "x2_inv": 2 * spec,
+        "x3_inv_dot": spec + 2 * f,   # read spectrum, v; write p
+        "lanczos": 3 * f + f,         # read p, v_k, v_{k-1}; write p
+        "update": 5 * f + 3 * f,      # read v, w1, w2, x, p; write w, x, v
+    }
+
+
+ITER_BYTES_PER_VOXEL = 196.0   # algorithmic minimum of one MINRES iteration (FP32 fields)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--rho", type=float, default=0.10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    return ap.parse_args()
+
+
+def config(n, rho):
+    return {"workload": f"octet_truss_{n}^3_rho{rho:.2f}_E11_tol1e-6",
+            "grid": [n, n, n], "relative_density": rho, "voigt_subsamples": 64,
+            "E_pa": E_M, "nu": NU_M, "derivative": "rotated", "macro_strain": "E11=1e-3",
+            "fields": "fp32", "krylov_scalars": "fp64", "tol": TOL,
+            "l2": "inputs larger than L2 (403 MB fields), no flush"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        mhz, maxm, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxm.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxm),
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(name, n):
+    """DRAM bytes per launch of `name` from the committed ncu summary, scaled
+    to an n^3 grid, or None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    k = d.get("kernels", {}).get(name)
+    if not k:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return k["dram_bytes_per_voxel"] * n ** 3
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_2110_00733_gb300", "csrc")
+    for fn in sorted(os.listdir(cdir)):
+        with open(os.path.join(cdir, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(phi64, iters):
+    """Oracle Galerkin-MINRES on the same cell, capped at `iters` iterations
+    (plus its right-hand side and true-residual operator applications)."""
+    import oracle
+    t0 = time.perf_counter()
+    s = oracle.solve(phi64, E_M, NU_M, 1, MACRO, tol=1e-30, max_it=iters)
+    dt = time.perf_counter() - t0
+    return s["iterations"], dt, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import rve_inputs as ri
+    n = args.n
+    phi, _ = ri.octet(n, args.rho)
+    phi64 = phi.astype(np.float64)
+    V = n ** 3
+    for _ in range(args.warmup):
+        cpu_oracle_sample(phi64, 1)
+    tot_it, tot_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        it, dt, cores = cpu_oracle_sample(phi64, args.cpu_iters)
+        tot_it += it
+        tot_t += dt
+    val = V * tot_it / tot_t
+    sample = (f"{n}^3 octet rho={args.rho}: {args.cpu_iters} MINRES iterations per step plus the "
+              f"right-hand side and true-residual operator applications, FP64 oracle")
+    line = {"impl": "reference", "metric": "minres_voxel_iters_per_s", "value": val,
+            "unit": "voxel-iter/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(n, args.rho),
+            "cpu_baseline": {"value": val, "unit": "voxel-iter/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+
+    n = args.n
+    V = n ** 3
+    phi, radius = ri.octet(n, args.rho)
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    stream = torch.cuda.Stream()
+    phi_dev = torch.from_numpy(phi).cuda()
+    ctx = hom.hom_create(phi.shape, phi_dev, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+                         derivative=hom.HOM_DERIV_ROTATED, precision=hom.HOM_PREC_FP32_FIELDS,
+                         device_ptrs=True, stream=stream.cuda_stream, device=local)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        rc, info = hom.hom_solve(ctx, MACRO, tol=TOL, max_it=MAX_IT)
+        return rc, info[0]
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = hom.hom_kernel_launches(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    iters, infos = 0, []
+    for _ in range(args.steps):
+        rc, inf = step()
+        iters += inf["iterations"]
+        infos.append(inf)
+    ev1.record(stream)
+    barrier()
+    launches = hom.hom_kernel_launches(ctx) - l0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t_local = ms / 1e3
+    if dist:
+        t = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = ws * V * iters / t_max
+
+    # per-kernel times (CUDA events on the library's stream) for the roofline
+    ktimes = hom.hom_time_kernels(ctx, reps=20)
+    kb = kernel_bytes_per_voxel(n)
+    dom = max((k for k in kb), key=lambda k: ktimes.get(k, 0.0))
+    peak, peak_kind = measured_peaks()
+    achieved = kb[dom] * V / (ktimes[dom] * 1e-3) / 1e9
+    iter_ms = sum(ktimes.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(dom, n),
+                "bytes_per_voxel": kb[dom],
+                "kernel_ms": ktimes,
+                "iteration": {"algorithmic_bytes_per_voxel": ITER_BYTES_PER_VOXEL,
+                              "achieved_gbs": ITER_BYTES_PER_VOXEL * V * iters / t_local / 1e9,
+                              "frac": ITER_BYTES_PER_VOXEL * V * iters / t_local / 1e9 / peak}}
+
+    # end-to-end through the C ABI with host buffers: create (phi H2D), solve,
+    # read the mean stress back, destroy
+    e2e_vals = []
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        c2 = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+                            derivative=hom.HOM_DERIV_ROTATED, device=local)
+        rc, info = hom.hom_solve(c2, MACRO, tol=TOL, max_it=MAX_IT)
+        _ = info[0]["sigma_mean"]
+        c2.close()
+        t1 = time.perf_counter()
+        e2e_vals.append(V * info[0]["iterations"] / (t1 - t0))
+    e2e = {"value": ws * statistics.median(e2e_vals), "unit": "voxel-iter/s",
+           "h2d_bytes_per_step": int(phi.nbytes), "d2h_bytes_per_step": 6 * 8 + 64}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        it, dt, cores = cpu_oracle_sample(phi.astype(np.float64), args.cpu_iters)
+        cpu = {"value": V * it / dt, "unit": "voxel-iter/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n}^3 octet, {it} FP64 MINRES iterations plus rhs and true-residual "
+                         f"applications ({dt:.1f} s)"}
+
+    last = infos[-1]
+    if rank == 0:
+        line = {"metric": "minres_voxel_iters_per_s", "value": value, "unit": "voxel-iter/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic octet-truss cell (seeded generator)",
+                "config": dict(config(n, args.rho), parallelism=f"replicas{ws}"),
+                "iterations_per_step": iters / args.steps,
+                "time_to_tol_ms": 1e3 * t_max / args.steps,
+                "true_residual": last["true_residual"], "sweeps": last["sweeps"],
+                "sigma11_pa": float(last["sigma_mean"][0]),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

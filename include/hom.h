@@ -1,0 +1,182 @@
+/*
+ * hom.h -- C ABI of the GB300 Galerkin-FFT homogenization library (libhom.so).
+ *
+ * The library solves the periodic cell problem of section 2.1 of Lucarini et
+ * al., "Adaptation and validation of FFT methods for homogenization of
+ * lattice based materials" (arXiv 2110.00733):
+ *
+ *   find the strain fluctuation e~ with  A(e~) = b,                eq. (gallin)
+ *   A(e) = F^-1{ G(xi) : F{ C(x) : e } },                          eq. (linearOp)
+ *   b    = -F^-1{ G(xi) : F{ C(x) : E_bar } }   (strain control),
+ *
+ * with C(x) = phi(x) C_m (isotropic E, nu scaled by the per-voxel solid
+ * fraction phi, Voigt rule of section 3.3; phi = 0 is empty space), G the
+ * compatible-strain projector of eq. (galop) built from the continuous
+ * frequencies of eq. (freq) or the rotated finite-difference frequencies of
+ * eq. (freqrot), solved by MINRES (section 2.1) to the relative residual of
+ * eq. (galres).  The effective stiffness is the volume average of the stress
+ * over the six unit macro strains (section 4.3).
+ *
+ * Conventions shared by every entry point
+ *   - grid n1 x n2 x n3, C order (index n3 fastest), unit cell edges;
+ *     each n_p in [2, 512] and of the form 2^a 3^b 5^c.
+ *   - V = n1*n2*n3.  A "field" is 6 x V values, component-major
+ *     (field[c*V + voxel]).  Entry points marked MANDEL use Mandel components
+ *     (e11, e22, e33, sqrt2 e23, sqrt2 e13, sqrt2 e12); the others use tensor
+ *     components (e11, e22, e33, e23, e13, e12).
+ *   - A "spectrum" is the half spectrum of 6 real components:
+ *     6 x n1 x n2 x (n3/2+1) complex values (re, im interleaved), component-
+ *     major, unnormalised forward DFT with kernel exp(-2 pi i k n / N).
+ *   - Field and spectrum buffers are float (HOM_PREC_FP32_FIELDS) or double
+ *     (HOM_PREC_FP64) as chosen at create time.  They are host pointers unless
+ *     hom_options.device_ptrs is set, in which case they are device pointers
+ *     on the context's device, used on the context's stream.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps.  The context owns its device workspace (allocated by hom_create,
+ *     freed by hom_destroy).
+ *   - Return value: HOM_OK (0), a positive warning (result valid), or a
+ *     negative error, in which case no output buffer has been written;
+ *     hom_last_error() then describes the failure.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef HOM_H
+#define HOM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HOM_OK = 0,
+    HOM_NOT_CONVERGED = 1,          /* max_it reached; best iterate returned */
+    HOM_EINVAL = -1,                /* bad argument */
+    HOM_EUNSUPPORTED_GRID = -2,     /* a grid size outside [2,512] or not 2^a3^b5^c */
+    HOM_ENOMEM = -3,                /* device allocation failed */
+    HOM_ECUDA = -4,                 /* CUDA runtime error */
+    HOM_ENAN = -5,                  /* NaN/Inf met in the input or a Krylov scalar */
+    HOM_ETIMEOUT = -6               /* reserved: a bounded device wait gave up */
+};
+
+enum { HOM_INPUT_PHASE_U8 = 0,      /* uint8 phase id: 0 empty, nonzero solid */
+       HOM_INPUT_FRACTION_F32 = 1,  /* float solid fraction phi in [0,1] */
+       HOM_INPUT_FRACTION_F64 = 2 };/* double solid fraction phi in [0,1] */
+enum { HOM_SMOOTH_NONE = 0 };       /* phi used as given (plain or Voigt-smoothed) */
+enum { HOM_DERIV_CONTINUOUS = 0,    /* xi_p = i q_p N_p, eq. (freq) */
+       HOM_DERIV_ROTATED = 1 };     /* rotated forward difference, eq. (freqrot) */
+enum { HOM_SOLVER_GALERKIN_MINRES = 0 };
+enum { HOM_PREC_FP32_FIELDS = 0,    /* FP32 fields and FFTs, FP64 Krylov scalars */
+       HOM_PREC_FP64 = 1 };         /* FP64 everywhere */
+
+typedef struct hom_ctx hom_ctx;     /* opaque, owned by the library */
+
+typedef struct {
+    int solver;         /* HOM_SOLVER_GALERKIN_MINRES */
+    int precision;      /* HOM_PREC_FP32_FIELDS (default) or HOM_PREC_FP64 */
+    int device_ptrs;    /* nonzero: buffer arguments are device pointers */
+    void *stream;       /* cudaStream_t to run on; NULL: a stream the context creates */
+    int device;         /* CUDA device ordinal; -1: the current device */
+    int refine;         /* FP32 fields: max FP64 iterative-refinement sweeps (default 3) */
+} hom_options;
+
+typedef struct {
+    int iterations;        /* MINRES iterations (summed over refinement sweeps) */
+    int status;            /* HOM_OK, HOM_NOT_CONVERGED or a negative error */
+    int sweeps;            /* refinement sweeps taken (1 = none) */
+    int reserved;
+    double est_residual;   /* MINRES estimate phibar_k / beta_1 at exit */
+    double true_residual;  /* ||A(e~) - b|| / ||b|| evaluated in FP64, eq. (galres) */
+    double sigma_mean[6];  /* volume-averaged stress, tensor components, units of E */
+    double time_ms;        /* device time of this case */
+} hom_solve_info;
+
+/* Fill *opt with the defaults. */
+void hom_default_options(hom_options *opt);
+
+/* Create a context for one cell.
+ *   grid[3]     n1, n2, n3 (see conventions).
+ *   phase       V values of the kind given by input_kind, C order; host
+ *               pointer, or device pointer if opt->device_ptrs.  Copied.
+ *   E, nu       isotropic lattice material (section 4.1), E > 0, -1 < nu < 0.5.
+ *   smoothing   HOM_SMOOTH_NONE.
+ *   derivative  HOM_DERIV_CONTINUOUS or HOM_DERIV_ROTATED.
+ *   opt         NULL for defaults.
+ * Errors: HOM_EINVAL (bad pointer, E, nu, enum, phi outside [0,1] or NaN),
+ * HOM_EUNSUPPORTED_GRID, HOM_ENOMEM, HOM_ECUDA. */
+int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_kind,
+               double E, double nu, int smoothing, int derivative,
+               const hom_options *opt);
+
+/* Solve eq. (gallin) for ncase macro strains (strain control).
+ *   macro_strain  ncase x 6 tensor components, host memory.
+ *   tol           relative residual of eq. (galres), e.g. 1e-6.
+ *   max_it        MINRES iteration cap per case (per refinement sweep).
+ *   warm_start    NULL (zero start) or ncase x 6 x V fluctuation fields, tensor
+ *                 components, host or device per device_ptrs; it is projected
+ *                 onto compatible fields before use.
+ *   info          NULL or ncase records.
+ * Returns HOM_OK if every case met tol, HOM_NOT_CONVERGED if one hit max_it,
+ * or a negative error.  The solutions stay in the context for
+ * hom_fields / hom_effective_stiffness until the next hom_solve.
+ * A right-hand side that vanishes up to round-off (e.g. a homogeneous cell)
+ * gives the zero fluctuation with 0 iterations. */
+int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol,
+              int max_it, const void *warm_start, hom_solve_info *info);
+
+/* 6x6 Voigt effective stiffness, row-major, sigma = C (e11,e22,e33,2e23,2e13,2e12),
+ * units of E, from the mean stresses of the last hom_solve.  That solve must
+ * have had ncase >= 6 cases whose macro strains span all six directions;
+ * otherwise HOM_EINVAL.  Section 4.3 extracts E and nu from such averages. */
+int hom_effective_stiffness(hom_ctx *ctx, double C[36]);
+
+/* Total strain E_bar + e~ and stress C(x):(E_bar + e~) of case icase of the
+ * last solve, each 6 x V tensor components (float or double per precision).
+ * Either pointer may be NULL. */
+int hom_fields(hom_ctx *ctx, int icase, void *strain, void *stress);
+
+/* Step entry points (one pass of the hot path each; used by parity tests). */
+
+/* out = A(eps), eq. (linearOp); eps and out are MANDEL fields. */
+int hom_apply(hom_ctx *ctx, const void *eps, void *out);
+
+/* out = b for one macro strain (6 tensor components, host), MANDEL field. */
+int hom_rhs(hom_ctx *ctx, const double macro_strain[6], void *out);
+
+/* Forward 3-D real-to-complex DFT of the 6 components of a field (no material,
+ * no projection): field 6 x V  ->  spectrum (see conventions). */
+int hom_fft_forward(hom_ctx *ctx, const void *field, void *spectrum);
+
+/* Inverse of hom_fft_forward including the 1/V factor (complex-to-real; the
+ * imaginary parts of the self-conjugate k3 = 0 and k3 = n3/2 planes are
+ * dropped as a real transform does). */
+int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field);
+
+/* out = F^-1{ G : F{ in } }: the projection of eq. (galop) alone (no
+ * material), MANDEL fields. */
+int hom_project(hom_ctx *ctx, const void *in, void *out);
+
+/* Average device time in milliseconds of each kernel of one MINRES iteration
+ * of this context, each launched `reps` times back to back on the context's
+ * stream between two CUDA events, on the workspace's current contents (an
+ * instrument for roofline measurements; it changes no solver state that a
+ * later hom_solve reads).  ms[0..8]: x3 forward (material + R2C), x2 forward,
+ * x1 (transform + projector + inverse), x2 inverse, x3 inverse (C2R + dot),
+ * alpha reduction, Lanczos axpy + norm, Givens step, w/x/v update.  Returns
+ * the number of entries written (<= nmax). */
+int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
+
+/* Grid, precision and workspace size of a context. */
+int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes);
+
+/* Number of kernels the library has launched on this context so far. */
+long long hom_kernel_launches(const hom_ctx *ctx);
+
+void hom_destroy(hom_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed hom_create when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char *hom_last_error(const hom_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOM_H */

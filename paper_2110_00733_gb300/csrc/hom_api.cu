@@ -1,0 +1,848 @@
+// hom_api.cu -- the C ABI of include/hom.h: contexts, FFT plans, the
+// operator of eq. (linearOp), MINRES (section 2.1) as a captured CUDA graph,
+// FP64 true residual of eq. (galres) with iterative refinement for FP32 fields,
+// and the volume-averaged stress of section 4.3.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/hom.h"
+#include "hom_internal.h"
+
+using namespace hom;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Status {
+    int code = HOM_OK;
+    std::string msg;
+};
+
+// Per-precision engine: tables, phase map and spectrum workspace of one cell.
+template <typename R> struct Engine {
+    Geometry g{};
+    R *phi = nullptr;
+    cpx<R> *spec = nullptr;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    void *D[3] = {nullptr, nullptr, nullptr};
+    void *M[3] = {nullptr, nullptr, nullptr};
+};
+
+}  // namespace
+
+struct hom_ctx {
+    int n[3];
+    long long V = 0, S = 0;
+    int prec = HOM_PREC_FP32_FIELDS;
+    int deriv = HOM_DERIV_ROTATED;
+    double E = 1.0, nu = 0.3, lam = 0.0, mu = 0.0;   // lam, mu in units of E
+    double phi2_sum = 0.0;                            // sum phi^2 (zero-rhs test)
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device_ptrs = 0;
+    int refine = 3;
+    Engine<float> e32;
+    Engine<double> e64;
+    // MINRES workspace in the solve precision (float or double)
+    void *vbuf[3] = {nullptr, nullptr, nullptr};
+    void *wbuf[2] = {nullptr, nullptr};
+    void *xs = nullptr;     // MINRES iterate of the current sweep
+    void *rhs = nullptr;    // MINRES right-hand side of the current sweep
+    double *b64 = nullptr, *r64 = nullptr, *stage64 = nullptr;
+    std::vector<double *> x64;      // per-case solutions (Mandel, FP64 master copy)
+    std::vector<double> macros;     // per-case macro strains (Mandel, as solved)
+    std::vector<double> sig_mean;   // per-case mean stress (tensor comps, units of E)
+    int ncase = 0;
+    double *partials = nullptr;
+    int npartials = 0;
+    MinresState *d_state = nullptr;
+    MinresState *h_state = nullptr;  // pinned
+    double *d_scalar = nullptr;
+    double *h_scalar = nullptr;      // pinned
+    int *d_flag = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 6;
+    long long graph_kernels = 0;
+    long long launches = 0;
+    long long workspace = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int fail(hom_ctx *c, int code, const std::string &m) {
+    if (c) c->err = m;
+    else g_create_error = m;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HOM_ENOMEM : HOM_ECUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+        }                                                                               \
+    } while (0)
+
+static bool factor_radices(int n, AxisPlan &p) {
+    int a = 0, m = n;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    int b = 0;
+    while (m % 3 == 0) { m /= 3; ++b; }
+    int c = 0;
+    while (m % 5 == 0) { m /= 5; ++c; }
+    if (m != 1) return false;
+    int ns = 0;
+    if (a > 0) {
+        int st2 = (a + 3) / 4;
+        int base = a / st2, extra = a % st2;
+        for (int i = 0; i < st2; ++i) p.radix[ns++] = 1 << (base + (i < extra ? 1 : 0));
+    }
+    for (int i = 0; i < b; ++i) p.radix[ns++] = 3;
+    for (int i = 0; i < c; ++i) p.radix[ns++] = 5;
+    if (ns > kMaxStages) return false;
+    p.nstages = ns;
+    p.n = n;
+    return true;
+}
+
+template <typename R> static size_t cpx_size() { return sizeof(R) * 2; }
+
+template <typename R>
+static int engine_init(hom_ctx *ctx, Engine<R> &E) {
+    Geometry &g = E.g;
+    g.n1 = ctx->n[0];
+    g.n2 = ctx->n[1];
+    g.n3 = ctx->n[2];
+    g.h = g.n3 / 2 + 1;
+    g.V = ctx->V;
+    g.S = ctx->S;
+    const size_t cs = cpx_size<R>();
+    // launch shapes: x3 passes hold 3*rows lines of n3, x2 tile2 lines of n2,
+    // x1 6*tile1 lines of n1, each twice (Stockham ping-pong)
+    int rows = 16;
+    while (rows > 1 && 2ull * g.n3 * 3 * rows * cs > 96 * 1024) rows >>= 1;
+    g.rows3 = rows;
+    int t2 = 32;
+    while (t2 > 1 && 2ull * g.n2 * t2 * cs > 96 * 1024) t2 >>= 1;
+    g.tile2 = t2;
+    int t1 = 16;
+    while (t1 > 1 && 2ull * g.n1 * 6 * t1 * cs > 200 * 1024) t1 >>= 1;
+    g.tile1 = t1;
+    g.smem3 = 2ull * g.n3 * 3 * g.rows3 * cs;
+    g.smem2 = 2ull * g.n2 * g.tile2 * cs;
+    g.smem1 = 2ull * g.n1 * 6 * g.tile1 * cs;
+    const double PI = 3.14159265358979323846;
+    for (int p = 0; p < 3; ++p) {
+        const int N = ctx->n[p];
+        if (!factor_radices(N, g.ax[p])) return fail(ctx, HOM_EUNSUPPORTED_GRID, "grid size not 2^a3^b5^c");
+        std::vector<R> tw(2 * N), D(2 * N), M(2 * N);
+        for (int t = 0; t < N; ++t) {
+            const double ang = 2.0 * PI * (double)t / (double)N;
+            tw[2 * t] = (R)std::cos(ang);
+            tw[2 * t + 1] = (R)-std::sin(ang);
+            const int m = (2 * t < N) ? t : t - N;        // signed frequency index
+            const double q = 2.0 * PI * (double)m / (double)N;
+            if (ctx->deriv == HOM_DERIV_CONTINUOUS) {      // xi_p = i q_p N_p, eq. (freq)
+                D[2 * t] = 0;
+                D[2 * t + 1] = (R)(q * N);
+                M[2 * t] = 1;
+                M[2 * t + 1] = 0;
+            } else {   // rotated scheme, eq. (freqrot): N (e^{iq}-1) and (1+e^{iq})/2
+                D[2 * t] = (R)(N * (std::cos(q) - 1.0));
+                D[2 * t + 1] = (R)(N * std::sin(q));
+                M[2 * t] = (R)(0.5 * (1.0 + std::cos(q)));
+                M[2 * t + 1] = (R)(0.5 * std::sin(q));
+            }
+        }
+        CU(cudaMalloc(&E.tw[p], cs * N));
+        CU(cudaMalloc(&E.D[p], cs * N));
+        CU(cudaMalloc(&E.M[p], cs * N));
+        CU(cudaMemcpy(E.tw[p], tw.data(), cs * N, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(E.D[p], D.data(), cs * N, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(E.M[p], M.data(), cs * N, cudaMemcpyHostToDevice));
+        g.ax[p].tw = E.tw[p];
+        g.D[p] = E.D[p];
+        g.M[p] = E.M[p];
+        ctx->workspace += 3 * (long long)cs * N;
+    }
+    CU(cudaMalloc(&E.phi, sizeof(R) * ctx->V));
+    CU(cudaMalloc(&E.spec, cs * 6 * ctx->S));
+    ctx->workspace += sizeof(R) * ctx->V + cs * 6 * ctx->S;
+    Launch<R>::table_init(g);
+    CU(cudaGetLastError());
+    return HOM_OK;
+}
+
+template <typename R>
+static void engine_free(Engine<R> &E) {
+    for (int p = 0; p < 3; ++p) {
+        cudaFree(E.tw[p]);
+        cudaFree(E.D[p]);
+        cudaFree(E.M[p]);
+    }
+    cudaFree(E.phi);
+    cudaFree(E.spec);
+}
+
+// One application of the operator chain: x3_fwd, x2, x1, x2^-1, x3_inv.
+template <typename R>
+static void op_chain(hom_ctx *ctx, Engine<R> &E, int fmode, const R *in, const double *macro, int x1flags,
+                     int imode, R *out, double scl, const R *dotv, double *partials, const MinresState *st) {
+    cudaStream_t s = ctx->stream;
+    Launch<R>::x3_fwd(E.g, s, fmode, in, E.phi, ctx->lam, ctx->mu, macro, E.spec, st);
+    Launch<R>::x2(E.g, s, 0, E.spec, st);
+    Launch<R>::x1(E.g, s, x1flags, E.spec, st);
+    Launch<R>::x2(E.g, s, 1, E.spec, st);
+    Launch<R>::x3_inv(E.g, s, imode, E.spec, out, scl, dotv, partials, st);
+    ctx->launches += 5;
+}
+
+static int x3_grid(const Geometry &g) { return (int)(((long long)g.n1 * g.n2 + g.rows3 - 1) / g.rows3); }
+static int ew_blocks(long long n) {
+    long long b = (n + kEwThreads - 1) / kEwThreads;
+    return (int)(b < kEwBlocks ? (b > 0 ? b : 1) : kEwBlocks);
+}
+
+// ||v||^2 of a device vector via the partials buffer; synchronous.
+template <typename R>
+static int dev_norm2(hom_ctx *ctx, const R *v, long long n, double *out) {
+    Launch<R>::norm2(n, ctx->stream, v, ctx->partials);
+    reduce_to(ctx->stream, ctx->partials, ew_blocks(n), ctx->d_scalar);
+    ctx->launches += 2;
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *out = *ctx->h_scalar;
+    return HOM_OK;
+}
+
+// Capture graph_iters MINRES iterations (pointer rotation period 6) once.
+template <typename R>
+static int build_graph(hom_ctx *ctx, Engine<R> &E) {
+    if (ctx->graph) return HOM_OK;
+    const long long n = 6 * ctx->V;
+    R *v[3] = {(R *)ctx->vbuf[0], (R *)ctx->vbuf[1], (R *)ctx->vbuf[2]};   // v_{k-1}, v_k, p
+    R *w[2] = {(R *)ctx->wbuf[0], (R *)ctx->wbuf[1]};                     // w_{k-1}, w_{k-2}
+    R *x = (R *)ctx->xs;
+    const int np3 = x3_grid(E.g), npe = ew_blocks(n);
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    long long before = ctx->launches;
+    for (int it = 0; it < ctx->graph_iters; ++it) {
+        R *vprev = v[0], *vk = v[1], *p = v[2];
+        R *w1 = w[0], *w2 = w[1];
+        // p = A v_k, partial <v_k, p>
+        op_chain<R>(ctx, E, X3F_MATERIAL, vk, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE_DOT, p,
+                    1.0 / (double)ctx->V, vk, ctx->partials, ctx->d_state);
+        scalar_alpha(ctx->stream, ctx->d_state, ctx->partials, np3);
+        // p -= alpha v_k + beta_k v_{k-1}; partial ||p||^2
+        Launch<R>::lanczos(n, ctx->stream, p, vk, vprev, ctx->d_state, ctx->partials);
+        scalar_givens(ctx->stream, ctx->d_state, ctx->partials, npe);
+        // w_k (into w_{k-2}'s buffer), x_k, v_{k+1} = p / beta_{k+1} (in place)
+        Launch<R>::update(n, ctx->stream, p, vk, w1, w2, x, ctx->d_state);
+        ctx->launches += 4;
+        v[0] = vk; v[1] = p; v[2] = vprev;
+        w[0] = w2; w[1] = w1;
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ctx->graph_kernels = ctx->launches - before;
+    ctx->launches = before;   // counted per replay instead
+    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HOM_OK;
+}
+
+// MINRES on A x = rhs (rhs in ctx->rhs, solution in ctx->xs, precision R),
+// zero start.  Returns iterations / estimate / status through the pointers.
+template <typename R>
+static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters, double *est, int *status) {
+    const long long n = 6 * ctx->V;
+    cudaStream_t s = ctx->stream;
+    int rc = build_graph<R>(ctx, E);
+    if (rc) return rc;
+    // beta_1 = ||rhs||, Givens start
+    Launch<R>::norm2(n, s, (const R *)ctx->rhs, ctx->partials);
+    scalar_start(s, ctx->d_state, ctx->partials, ew_blocks(n), tol, max_it);
+    ctx->launches += 2;
+    CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const double beta1 = ctx->h_state->beta1;
+    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * n, s));
+    if (!(beta1 > 0.0) || !std::isfinite(beta1)) {
+        *iters = 0;
+        *est = 0.0;
+        *status = std::isfinite(beta1) ? 0 : HOM_ENAN;
+        CU(cudaStreamSynchronize(s));
+        return HOM_OK;
+    }
+    // v_0 = 0, v_1 = rhs / beta_1, w = 0
+    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * n, s));
+    Launch<R>::axpby(n, s, 1.0 / beta1, (const R *)ctx->rhs, 0.0, (R *)ctx->vbuf[1]);
+    ctx->launches += 1;
+    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * n, s));
+    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * n, s));
+    // replay the captured iterations until the state says done
+    const int per_check = 4;
+    int replays = 0;
+    const int max_replays = (max_it + ctx->graph_iters - 1) / ctx->graph_iters + 1;
+    while (true) {
+        for (int r = 0; r < per_check && replays < max_replays; ++r, ++replays) {
+            CU(cudaGraphLaunch(ctx->graph, s));
+            ctx->launches += ctx->graph_kernels;
+        }
+        CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (ctx->h_state->done || replays >= max_replays) break;
+    }
+    *iters = ctx->h_state->k;
+    *est = ctx->h_state->est;
+    *status = ctx->h_state->status == -5 ? HOM_ENAN : (ctx->h_state->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
+    return HOM_OK;
+}
+
+static void macro_to_mandel(const double *t, double *m) {
+    const double r2 = std::sqrt(2.0);
+    for (int c = 0; c < 6; ++c) m[c] = (c < 3) ? t[c] : t[c] * r2;
+}
+
+// host <-> device staging for user buffers
+static int stage_in(hom_ctx *ctx, const void *user, size_t bytes, void *dev) {
+    if (ctx->device_ptrs) CU(cudaMemcpyAsync(dev, user, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    else CU(cudaMemcpyAsync(dev, user, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return HOM_OK;
+}
+static int stage_out(hom_ctx *ctx, void *user, size_t bytes, const void *dev) {
+    if (ctx->device_ptrs) CU(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    else CU(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HOM_OK;
+}
+
+static int finish(hom_ctx *ctx) {
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HOM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI (C linkage comes from the declarations in hom.h)
+// ---------------------------------------------------------------------------
+
+void hom_default_options(hom_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->solver = HOM_SOLVER_GALERKIN_MINRES;
+    opt->precision = HOM_PREC_FP32_FIELDS;
+    opt->device_ptrs = 0;
+    opt->stream = nullptr;
+    opt->device = -1;
+    opt->refine = 3;
+}
+
+const char *hom_last_error(const hom_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void hom_destroy(hom_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    engine_free(ctx->e32);
+    engine_free(ctx->e64);
+    for (int i = 0; i < 3; ++i) cudaFree(ctx->vbuf[i]);
+    for (int i = 0; i < 2; ++i) cudaFree(ctx->wbuf[i]);
+    cudaFree(ctx->xs);
+    cudaFree(ctx->rhs);
+    cudaFree(ctx->b64);
+    cudaFree(ctx->r64);
+    cudaFree(ctx->stage64);
+    for (double *p : ctx->x64) cudaFree(p);
+    cudaFree(ctx->partials);
+    cudaFree(ctx->d_state);
+    cudaFree(ctx->d_scalar);
+    cudaFree(ctx->d_flag);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
+    if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int input_kind) {
+    for (int p = 0; p < 3; ++p) {
+        AxisPlan tmp{};
+        if (grid[p] < 2 || grid[p] > 512 || !factor_radices(grid[p], tmp))
+            return fail(ctx, HOM_EUNSUPPORTED_GRID, "each grid size must be in [2,512] and of the form 2^a3^b5^c");
+        ctx->n[p] = grid[p];
+    }
+    ctx->V = (long long)grid[0] * grid[1] * grid[2];
+    ctx->S = (long long)grid[0] * grid[1] * (grid[2] / 2 + 1);
+    CU(cudaSetDevice(ctx->device));
+    if (!ctx->stream) {
+        CU(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    CU(cudaEventCreate(&ctx->ev0));
+    CU(cudaEventCreate(&ctx->ev1));
+    int rc = engine_init<double>(ctx, ctx->e64);
+    if (rc) return rc;
+    if (ctx->prec == HOM_PREC_FP32_FIELDS) {
+        rc = engine_init<float>(ctx, ctx->e32);
+        if (rc) return rc;
+    }
+    const long long n = 6 * ctx->V;
+    const size_t rs = (ctx->prec == HOM_PREC_FP64) ? sizeof(double) : sizeof(float);
+    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * n));
+    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->wbuf[i], rs * n));
+    CU(cudaMalloc(&ctx->xs, rs * n));
+    CU(cudaMalloc(&ctx->rhs, rs * n));
+    CU(cudaMalloc(&ctx->b64, sizeof(double) * n));
+    CU(cudaMalloc(&ctx->r64, sizeof(double) * n));
+    ctx->workspace += 7 * (long long)rs * n + 2 * (long long)sizeof(double) * n;
+    ctx->npartials = 8 * kEwBlocks;
+    const long long np3 = std::max((long long)x3_grid(ctx->e64.g),
+                                   ctx->prec == HOM_PREC_FP32_FIELDS ? (long long)x3_grid(ctx->e32.g) : 0LL);
+    if (np3 > ctx->npartials) ctx->npartials = (int)np3;
+    CU(cudaMalloc(&ctx->partials, sizeof(double) * ctx->npartials));
+    CU(cudaMalloc(&ctx->d_state, sizeof(MinresState)));
+    CU(cudaMalloc(&ctx->d_scalar, sizeof(double) * 8));
+    CU(cudaMalloc(&ctx->d_flag, sizeof(int)));
+    CU(cudaMallocHost(&ctx->h_state, sizeof(MinresState)));
+    CU(cudaMallocHost(&ctx->h_scalar, sizeof(double) * 8));
+    // phase map -> phi (FP64 copy always; FP32 copy for FP32 fields)
+    const size_t in_bytes = (input_kind == HOM_INPUT_PHASE_U8 ? 1 : input_kind == HOM_INPUT_FRACTION_F32 ? 4 : 8);
+    void *dev_in = nullptr;
+    CU(cudaMalloc(&dev_in, in_bytes * ctx->V));
+    rc = stage_in(ctx, phase, in_bytes * ctx->V, dev_in);
+    if (rc) { cudaFree(dev_in); return rc; }
+    CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    phi_convert<double>(ctx->V, ctx->stream, dev_in, input_kind, ctx->e64.phi, ctx->d_flag);
+    if (ctx->prec == HOM_PREC_FP32_FIELDS)
+        phi_convert<float>(ctx->V, ctx->stream, dev_in, input_kind, ctx->e32.phi, ctx->d_flag);
+    ctx->launches += 2;
+    int bad = 0;
+    CU(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(dev_in);
+    if (bad) return fail(ctx, HOM_EINVAL, "phase values must be finite and in [0,1]");
+    // sum phi^2 for the zero right-hand-side test
+    double s2 = 0.0;
+    rc = dev_norm2<double>(ctx, ctx->e64.phi, ctx->V, &s2);
+    if (rc) return rc;
+    ctx->phi2_sum = s2;
+    return finish(ctx);
+}
+
+int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_kind, double E, double nu,
+               int smoothing, int derivative, const hom_options *opt) {
+    if (!out || !grid || !phase) return fail(nullptr, HOM_EINVAL, "null argument");
+    *out = nullptr;
+    if (!(E > 0.0) || !std::isfinite(E) || !(nu > -1.0 && nu < 0.5))
+        return fail(nullptr, HOM_EINVAL, "need E > 0 and -1 < nu < 0.5");
+    if (input_kind < 0 || input_kind > 2) return fail(nullptr, HOM_EINVAL, "bad input_kind");
+    if (smoothing != HOM_SMOOTH_NONE) return fail(nullptr, HOM_EINVAL, "bad smoothing");
+    if (derivative != HOM_DERIV_CONTINUOUS && derivative != HOM_DERIV_ROTATED)
+        return fail(nullptr, HOM_EINVAL, "bad derivative");
+    hom_options o;
+    hom_default_options(&o);
+    if (opt) o = *opt;
+    if (o.solver != HOM_SOLVER_GALERKIN_MINRES) return fail(nullptr, HOM_EINVAL, "bad solver");
+    if (o.precision != HOM_PREC_FP32_FIELDS && o.precision != HOM_PREC_FP64)
+        return fail(nullptr, HOM_EINVAL, "bad precision");
+    hom_ctx *ctx = new hom_ctx();
+    ctx->prec = o.precision;
+    ctx->deriv = derivative;
+    ctx->E = E;
+    ctx->nu = nu;
+    ctx->lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));   // lambda / E
+    ctx->mu = 1.0 / (2.0 * (1.0 + nu));                // mu / E
+    ctx->device_ptrs = o.device_ptrs;
+    ctx->refine = o.refine < 0 ? 0 : o.refine;
+    ctx->stream = (cudaStream_t)o.stream;
+    if (o.device >= 0) ctx->device = o.device;
+    else if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, HOM_ECUDA, "no CUDA device");
+    }
+    int rc = create_impl(ctx, grid, phase, input_kind);
+    if (rc) {
+        g_create_error = ctx->err;
+        hom_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return HOM_OK;
+}
+
+template <typename R>
+static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
+    const long long n = 6 * ctx->V;
+    cudaStream_t s = ctx->stream;
+    R *v0 = (R *)ctx->vbuf[0], *v1 = (R *)ctx->vbuf[1], *p = (R *)ctx->vbuf[2];
+    R *w1 = (R *)ctx->wbuf[0], *w2 = (R *)ctx->wbuf[1], *x = (R *)ctx->xs;
+    // a private state that never stops: done = 0, unit coefficients
+    MinresState h{};
+    h.beta1 = 1.0; h.beta = 0.5; h.alpha = 0.25; h.c = -1.0; h.s = 0.0; h.phibar = 1.0; h.tol = 0.0;
+    h.u_delta = 0.1; h.u_eps = 0.1; h.u_inv_gamma = 1.0; h.u_tau = 0.0; h.u_inv_beta = 1.0;
+    h.max_it = 1 << 30;
+    MinresState *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(MinresState)));
+    CU(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    // finite field contents
+    Launch<R>::axpby(n, s, 0.0, v0, 0.0, v0);
+    Launch<R>::axpby(n, s, 0.0, v1, 0.0, v1);
+    Launch<R>::axpby(n, s, 0.0, p, 0.0, p);
+    Launch<R>::axpby(n, s, 0.0, w1, 0.0, w1);
+    Launch<R>::axpby(n, s, 0.0, w2, 0.0, w2);
+    Launch<R>::axpby(n, s, 0.0, x, 0.0, x);
+    const int np3 = x3_grid(E.g), npe = ew_blocks(n);
+    const int nk = 9;
+    for (int k = 0; k < nk && k < nmax; ++k) {
+        for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
+            const int r = pass ? reps : 1;
+            CU(cudaEventRecord(ctx->ev0, s));
+            for (int i = 0; i < r; ++i) {
+                switch (k) {
+                    case 0: Launch<R>::x3_fwd(E.g, s, X3F_MATERIAL, v1, E.phi, ctx->lam, ctx->mu, nullptr, E.spec, d); break;
+                    case 1: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
+                    case 2: Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA | X1_INV, E.spec, d); break;
+                    case 3: Launch<R>::x2(E.g, s, 1, E.spec, d); break;
+                    case 4: Launch<R>::x3_inv(E.g, s, X3I_STORE_DOT, E.spec, p, 1.0 / (double)ctx->V, v1, ctx->partials, d); break;
+                    case 5: scalar_alpha(s, d, ctx->partials, np3); break;
+                    case 6: Launch<R>::lanczos(n, s, p, v1, v0, d, ctx->partials); break;
+                    case 7: scalar_givens(s, d, ctx->partials, npe);
+                            CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
+                    default: Launch<R>::update(n, s, p, v1, w1, w2, x, d); break;
+                }
+            }
+            CU(cudaEventRecord(ctx->ev1, s));
+            CU(cudaEventSynchronize(ctx->ev1));
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1));
+            ms[k] = (double)t / r;
+        }
+        ctx->launches += reps + 1;
+    }
+    cudaFree(d);
+    return nk < nmax ? nk : nmax;
+}
+
+int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
+    if (!ctx || !ms || reps <= 0 || nmax <= 0) return fail(ctx, HOM_EINVAL, "bad argument");
+    cudaSetDevice(ctx->device);
+    int r = (ctx->prec == HOM_PREC_FP64) ? time_kernels_impl<double>(ctx, ctx->e64, reps, ms, nmax)
+                                         : time_kernels_impl<float>(ctx, ctx->e32, reps, ms, nmax);
+    if (r < 0) return r;
+    int rc = finish(ctx);
+    return rc ? rc : r;
+}
+
+int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes) {
+    if (!ctx) return HOM_EINVAL;
+    if (grid) for (int p = 0; p < 3; ++p) grid[p] = ctx->n[p];
+    if (precision) *precision = ctx->prec;
+    if (workspace_bytes) *workspace_bytes = ctx->workspace + (long long)ctx->x64.size() * 6 * ctx->V * 8;
+    return HOM_OK;
+}
+
+long long hom_kernel_launches(const hom_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+// ----- step entry points ----------------------------------------------------
+template <typename R>
+static int step_impl(hom_ctx *ctx, Engine<R> &E, int which, const void *in, void *out, const double *macro) {
+    const long long n = 6 * ctx->V;
+    R *din = (R *)ctx->xs, *dout = (R *)ctx->rhs;
+    cpx<R> *spec = E.spec;
+    cudaStream_t s = ctx->stream;
+    int rc;
+    switch (which) {
+        case 0:  // apply (Mandel)
+            rc = stage_in(ctx, in, sizeof(R) * n, din);
+            if (rc) return rc;
+            op_chain<R>(ctx, E, X3F_MATERIAL, din, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
+                        1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            return stage_out(ctx, out, sizeof(R) * n, dout);
+        case 1: {  // rhs (Mandel)
+            double m[6];
+            macro_to_mandel(macro, m);
+            op_chain<R>(ctx, E, X3F_MACRO, nullptr, m, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
+                        -1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            return stage_out(ctx, out, sizeof(R) * n, dout);
+        }
+        case 2:  // forward FFT
+            rc = stage_in(ctx, in, sizeof(R) * n, din);
+            if (rc) return rc;
+            Launch<R>::x3_fwd(E.g, s, X3F_RAW, din, E.phi, 0, 0, nullptr, spec, nullptr);
+            Launch<R>::x2(E.g, s, 0, spec, nullptr);
+            Launch<R>::x1(E.g, s, X1_FWD, spec, nullptr);
+            ctx->launches += 3;
+            return stage_out(ctx, out, cpx_size<R>() * 6 * ctx->S, spec);
+        case 3:  // inverse FFT
+            rc = stage_in(ctx, in, cpx_size<R>() * 6 * ctx->S, spec);
+            if (rc) return rc;
+            Launch<R>::x1(E.g, s, X1_INV, spec, nullptr);
+            Launch<R>::x2(E.g, s, 1, spec, nullptr);
+            Launch<R>::x3_inv(E.g, s, X3I_STORE, spec, dout, 1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            ctx->launches += 3;
+            return stage_out(ctx, out, sizeof(R) * n, dout);
+        default:  // projection (Mandel)
+            rc = stage_in(ctx, in, sizeof(R) * n, din);
+            if (rc) return rc;
+            op_chain<R>(ctx, E, X3F_RAW, din, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
+                        1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            return stage_out(ctx, out, sizeof(R) * n, dout);
+    }
+}
+
+static int step(hom_ctx *ctx, int which, const void *in, void *out, const double *macro) {
+    if (!ctx || !out || (which != 1 && !in) || (which == 1 && !macro)) return fail(ctx, HOM_EINVAL, "null argument");
+    cudaSetDevice(ctx->device);
+    int rc = (ctx->prec == HOM_PREC_FP64) ? step_impl<double>(ctx, ctx->e64, which, in, out, macro)
+                                          : step_impl<float>(ctx, ctx->e32, which, in, out, macro);
+    if (rc) return rc;
+    return finish(ctx);
+}
+
+int hom_apply(hom_ctx *ctx, const void *eps, void *out) { return step(ctx, 0, eps, out, nullptr); }
+int hom_rhs(hom_ctx *ctx, const double macro_strain[6], void *out) { return step(ctx, 1, nullptr, out, macro_strain); }
+int hom_fft_forward(hom_ctx *ctx, const void *field, void *spectrum) { return step(ctx, 2, field, spectrum, nullptr); }
+int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field) { return step(ctx, 3, spectrum, field, nullptr); }
+int hom_project(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 4, in, out, nullptr); }
+
+// ----- solve -------------------------------------------------------------------
+// ||A(x) - b|| / ||b|| in FP64 for x = ctx->x64[icase]; leaves b - A x in r64.
+static int true_residual(hom_ctx *ctx, double *x, double bnorm, double *res) {
+    const long long n = 6 * ctx->V;
+    op_chain<double>(ctx, ctx->e64, X3F_MATERIAL, x, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, ctx->r64,
+                     1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+    residual64(n, ctx->stream, ctx->b64, ctx->r64, ctx->r64, ctx->partials);
+    reduce_to(ctx->stream, ctx->partials, ew_blocks(n), ctx->d_scalar);
+    ctx->launches += 2;
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *res = (bnorm > 0) ? std::sqrt(*ctx->h_scalar) / bnorm : 0.0;
+    return HOM_OK;
+}
+
+static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, int max_it, const void *warm,
+                      hom_solve_info *info) {
+    const long long n = 6 * ctx->V;
+    cudaStream_t s = ctx->stream;
+    double m[6];
+    macro_to_mandel(mac_t, m);
+    for (int c = 0; c < 6; ++c) ctx->macros[6 * icase + c] = m[c];
+    double *x = ctx->x64[icase];
+    hom_solve_info inf{};
+    CU(cudaEventRecord(ctx->ev0, s));
+    // b in FP64 (eq. gallin with sigma_bar = 0)
+    op_chain<double>(ctx, ctx->e64, X3F_MACRO, nullptr, m, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, ctx->b64,
+                     -1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+    double b2 = 0.0;
+    int rc = dev_norm2<double>(ctx, ctx->b64, n, &b2);
+    if (rc) return rc;
+    const double bnorm = std::sqrt(b2);
+    // scale of the right-hand side: ||C : E_bar|| over the grid (units of E)
+    double ce2 = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
+        ce2 += sv * sv;
+    }
+    const double ntau = std::sqrt(ce2 * ctx->phi2_sum);
+    CU(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    int status = HOM_OK;
+    if (!std::isfinite(bnorm)) {
+        status = HOM_ENAN;
+    } else if (bnorm <= 1e-12 * ntau) {
+        // b vanishes up to round-off: zero fluctuation, 0 iterations
+        inf.sweeps = 0;
+    } else {
+        if (warm) {
+            // x0 = G(warm) (projected onto compatible fields), Mandel
+            double *st = ctx->r64;
+            if (!ctx->stage64) CU(cudaMalloc(&ctx->stage64, sizeof(double) * n));
+            if (ctx->prec == HOM_PREC_FP64) {
+                rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * icase, sizeof(double) * n, ctx->stage64);
+            } else {
+                rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * icase, sizeof(float) * n, ctx->xs);
+                if (!rc) convert_f2d(n, s, (const float *)ctx->xs, ctx->stage64, 0);
+            }
+            if (rc) return rc;
+            mandel_scale<double>(ctx->V, s, ctx->stage64, std::sqrt(2.0));
+            op_chain<double>(ctx, ctx->e64, X3F_RAW, ctx->stage64, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE,
+                             x, 1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            (void)st;
+        }
+        double tres = 1.0;
+        rc = true_residual(ctx, x, bnorm, &tres);
+        if (rc) return rc;
+        const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
+        for (int sw = 0; sw < sweeps_max && tres > tol; ++sw) {
+            // right-hand side of this sweep: r = b - A x (FP64), in the solve precision
+            double sweep_tol = tol * bnorm / (tres * bnorm);
+            if (sweep_tol > 0.5) sweep_tol = 0.5;
+            int it = 0, st = 0;
+            double est = 0.0;
+            if (ctx->prec == HOM_PREC_FP64) {
+                CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                rc = run_minres<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
+                if (rc) return rc;
+                Launch<double>::axpby(n, s, 1.0, (const double *)ctx->xs, 1.0, x);
+            } else {
+                convert_d2f(n, s, ctx->r64, (float *)ctx->rhs);
+                rc = run_minres<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
+                if (rc) return rc;
+                convert_f2d(n, s, (const float *)ctx->xs, x, 1);
+            }
+            ctx->launches += 2;
+            inf.iterations += it;
+            inf.est_residual = est * tres;     // relative to ||b||
+            inf.sweeps = sw + 1;
+            rc = true_residual(ctx, x, bnorm, &tres);
+            if (rc) return rc;
+            if (st == HOM_ENAN) { status = HOM_ENAN; break; }
+            if (st == HOM_NOT_CONVERGED && tres > tol) { status = HOM_NOT_CONVERGED; break; }
+        }
+        inf.true_residual = tres;
+        if (status == HOM_OK && tres > tol) status = HOM_NOT_CONVERGED;
+    }
+    // mean stress <phi C_m : (E_bar + x)>
+    Launch<double>::mean_stress(ctx->V, s, x, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
+    const int nb = ew_blocks(ctx->V);
+    for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
+    ctx->launches += 7;
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(ctx->ev1, s));
+    CU(cudaStreamSynchronize(s));
+    const double r2 = std::sqrt(2.0);
+    for (int c = 0; c < 6; ++c) {
+        double v = ctx->h_scalar[c] / (double)ctx->V * ctx->E;
+        if (c >= 3) v /= r2;
+        inf.sigma_mean[c] = v;
+        ctx->sig_mean[6 * icase + c] = v;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    inf.time_ms = ms;
+    inf.status = status;
+    if (info) *info = inf;
+    return status;
+}
+
+int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, int max_it, const void *warm_start,
+              hom_solve_info *info) {
+    if (!ctx || !macro_strain || ncase <= 0) return fail(ctx, HOM_EINVAL, "null argument or ncase <= 0");
+    if (!(tol > 0.0) || max_it < 0) return fail(ctx, HOM_EINVAL, "need tol > 0 and max_it >= 0");
+    for (int i = 0; i < 6 * ncase; ++i)
+        if (!std::isfinite(macro_strain[i])) return fail(ctx, HOM_ENAN, "macro strain not finite");
+    cudaSetDevice(ctx->device);
+    // per-case FP64 solutions
+    while ((int)ctx->x64.size() < ncase) {
+        double *p = nullptr;
+        CU(cudaMalloc(&p, sizeof(double) * 6 * ctx->V));
+        ctx->x64.push_back(p);
+    }
+    ctx->ncase = 0;
+    ctx->macros.assign(6 * ncase, 0.0);
+    ctx->sig_mean.assign(6 * ncase, 0.0);
+    int worst = HOM_OK;
+    for (int k = 0; k < ncase; ++k) {
+        int rc = solve_case(ctx, k, macro_strain + 6 * k, tol, max_it, warm_start, info ? info + k : nullptr);
+        if (rc < 0) {
+            if (info) info[k].status = rc;
+            return rc;
+        }
+        if (rc > worst) worst = rc;
+    }
+    ctx->ncase = ncase;
+    int rc = finish(ctx);
+    return rc ? rc : worst;
+}
+
+int hom_effective_stiffness(hom_ctx *ctx, double C[36]) {
+    if (!ctx || !C) return fail(ctx, HOM_EINVAL, "null argument");
+    const int nc = ctx->ncase;
+    if (nc < 6) return fail(ctx, HOM_EINVAL, "needs a prior hom_solve with >= 6 cases");
+    // Voigt strains gamma (6 x nc) and mean stresses S (6 x nc); C = S G^T (G G^T)^-1
+    std::vector<double> G(6 * nc), Sg(6 * nc);
+    const double r2 = std::sqrt(2.0);
+    for (int k = 0; k < nc; ++k)
+        for (int c = 0; c < 6; ++c) {
+            const double mm = ctx->macros[6 * k + c];
+            G[c * nc + k] = (c < 3) ? mm : mm * r2;   // Mandel sqrt2 e -> engineering 2e
+            Sg[c * nc + k] = ctx->sig_mean[6 * k + c];
+        }
+    double A[6][12];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < nc; ++k) s += G[i * nc + k] * G[j * nc + k];
+            A[i][j] = s;
+            A[i][6 + j] = (i == j);
+        }
+    for (int c = 0; c < 6; ++c) {   // Gauss-Jordan with partial pivoting
+        int piv = c;
+        for (int r = c + 1; r < 6; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (fabs(A[piv][c]) < 1e-300) return fail(ctx, HOM_EINVAL, "solved cases do not span six strain directions");
+        for (int j = 0; j < 12; ++j) std::swap(A[c][j], A[piv][j]);
+        const double d = A[c][c];
+        for (int j = 0; j < 12; ++j) A[c][j] /= d;
+        for (int r = 0; r < 6; ++r)
+            if (r != c) {
+                const double f = A[r][c];
+                for (int j = 0; j < 12; ++j) A[r][j] -= f * A[c][j];
+            }
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) {
+                double sg = 0;
+                for (int q = 0; q < nc; ++q) sg += Sg[i * nc + q] * G[k * nc + q];
+                s += sg * A[k][6 + j];
+            }
+            C[i * 6 + j] = s;
+        }
+    return HOM_OK;
+}
+
+int hom_fields(hom_ctx *ctx, int icase, void *strain, void *stress) {
+    if (!ctx) return HOM_EINVAL;
+    if (icase < 0 || icase >= ctx->ncase) return fail(ctx, HOM_EINVAL, "icase out of range of the last solve");
+    cudaSetDevice(ctx->device);
+    const long long n = 6 * ctx->V;
+    cudaStream_t s = ctx->stream;
+    const double *m = &ctx->macros[6 * icase];
+    const double *x = ctx->x64[icase];
+    if (ctx->prec == HOM_PREC_FP64) {
+        double *de = (double *)ctx->vbuf[0], *ds = (double *)ctx->vbuf[1];
+        Launch<double>::fields(ctx->V, s, x, ctx->e64.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
+                               stress ? ds : nullptr);
+        ctx->launches += 1;
+        if (strain) { int rc = stage_out(ctx, strain, sizeof(double) * n, de); if (rc) return rc; }
+        if (stress) { int rc = stage_out(ctx, stress, sizeof(double) * n, ds); if (rc) return rc; }
+    } else {
+        float *xf = (float *)ctx->xs, *de = (float *)ctx->vbuf[0], *ds = (float *)ctx->vbuf[1];
+        convert_d2f(n, s, x, xf);
+        Launch<float>::fields(ctx->V, s, xf, ctx->e32.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
+                              stress ? ds : nullptr);
+        ctx->launches += 2;
+        if (strain) { int rc = stage_out(ctx, strain, sizeof(float) * n, de); if (rc) return rc; }
+        if (stress) { int rc = stage_out(ctx, stress, sizeof(float) * n, ds); if (rc) return rc; }
+    }
+    return finish(ctx);
+}

@@ -1,0 +1,203 @@
+// hom_fft.cuh -- shared-memory mixed-radix FFT engine for the batched 3-D
+// real FFTs of the Galerkin operator (section 2.1: the transforms of
+// eq. (gal) are discrete Fourier transforms evaluated with an FFT).
+//
+// A CTA holds a batch of L lines of one axis in shared memory, element e of
+// line l at buf[e*L + l] (lines interleaved, so that the threads of a warp
+// touch consecutive words whatever the stage's index pattern), and runs
+// Stockham auto-sort stages between two buffers.  Each stage applies radix-R
+// butterflies (R in {2,3,4,5,8,16}) held in registers; twiddles come from a
+// per-axis table w[t] = exp(-2 pi i t / N) computed on the host in double.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hom {
+
+template <typename R> struct cpx_t;
+template <> struct cpx_t<float> { using type = float2; };
+template <> struct cpx_t<double> { using type = double2; };
+template <typename R> using cpx = typename cpx_t<R>::type;
+
+template <typename R> __device__ __forceinline__ cpx<R> mk(R x, R y) { cpx<R> c; c.x = x; c.y = y; return c; }
+template <typename R> __device__ __forceinline__ cpx<R> add(cpx<R> a, cpx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ cpx<R> sub(cpx<R> a, cpx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ cpx<R> mul(cpx<R> a, cpx<R> b) {
+    return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R> __device__ __forceinline__ cpx<R> conjc(cpx<R> a) { return mk<R>(a.x, -a.y); }
+template <typename R> __device__ __forceinline__ cpx<R> scale(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// multiply by s*i (s = +1 or -1)
+template <typename R> __device__ __forceinline__ cpx<R> mul_si(cpx<R> a, int s) {
+    return s > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+constexpr int kMaxStages = 8;
+
+struct AxisPlan {
+    int n;                    // transform length
+    int nstages;
+    int radix[kMaxStages];
+    const void *tw;           // n complex values exp(-2 pi i t / n) (float2 or double2)
+};
+
+// ---------------------------------------------------------------------------
+// In-register DFT codelets, kernel exp(S * 2 pi i j k / R), S = -1 forward.
+// Constants are closed-form values: cos(2pi/5) = (sqrt5-1)/4, etc.
+// ---------------------------------------------------------------------------
+template <typename R, int S> __device__ __forceinline__ void dft2(cpx<R> &a, cpx<R> &b) {
+    cpx<R> t = a;
+    a = add<R>(t, b);
+    b = sub<R>(t, b);
+}
+
+template <typename R, int S> __device__ __forceinline__ void dft3(cpx<R> *v) {
+    const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+    cpx<R> t = add<R>(v[1], v[2]), u = sub<R>(v[1], v[2]);
+    cpx<R> m = sub<R>(v[0], scale<R>(t, (R)0.5));
+    cpx<R> r = mul_si<R>(scale<R>(u, h), S);
+    v[0] = add<R>(v[0], t);
+    v[1] = add<R>(m, r);
+    v[2] = sub<R>(m, r);
+}
+
+template <typename R, int S> __device__ __forceinline__ void dft4(cpx<R> *v) {
+    cpx<R> a = add<R>(v[0], v[2]), b = sub<R>(v[0], v[2]);
+    cpx<R> c = add<R>(v[1], v[3]), d = mul_si<R>(sub<R>(v[1], v[3]), S);
+    v[0] = add<R>(a, c);
+    v[2] = sub<R>(a, c);
+    v[1] = add<R>(b, d);
+    v[3] = sub<R>(b, d);
+}
+
+template <typename R, int S> __device__ __forceinline__ void dft5(cpx<R> *v) {
+    const R c1 = (R)0.30901699437494742410;   // cos(2pi/5)
+    const R c2 = (R)-0.80901699437494742410;  // cos(4pi/5)
+    const R s1 = (R)0.95105651629515357212;   // sin(2pi/5)
+    const R s2 = (R)0.58778525229247312917;   // sin(4pi/5)
+    cpx<R> t1 = add<R>(v[1], v[4]), t2 = add<R>(v[2], v[3]);
+    cpx<R> u1 = sub<R>(v[1], v[4]), u2 = sub<R>(v[2], v[3]);
+    cpx<R> a = v[0];
+    cpx<R> m1 = mk<R>(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+    cpx<R> m2 = mk<R>(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+    cpx<R> n1 = mul_si<R>(mk<R>(s1 * u1.x + s2 * u2.x, s1 * u1.y + s2 * u2.y), S);
+    cpx<R> n2 = mul_si<R>(mk<R>(s2 * u1.x - s1 * u2.x, s2 * u1.y - s1 * u2.y), S);
+    v[0] = add<R>(a, add<R>(t1, t2));
+    v[1] = add<R>(m1, n1);
+    v[4] = sub<R>(m1, n1);
+    v[2] = add<R>(m2, n2);
+    v[3] = sub<R>(m2, n2);
+}
+
+// exp(S * 2 pi i k / 16) for k = 0..7
+template <typename R, int S> __device__ __forceinline__ cpx<R> w16(int k) {
+    const R c = (R)0.92387953251128675613;   // cos(pi/8)
+    const R s = (R)0.38268343236508977173;   // sin(pi/8)
+    const R h = (R)0.70710678118654752440;   // sqrt(1/2)
+    R re, im;
+    switch (k) {
+        case 0: re = 1; im = 0; break;
+        case 1: re = c; im = s; break;
+        case 2: re = h; im = h; break;
+        case 3: re = s; im = c; break;
+        case 4: re = 0; im = 1; break;
+        case 5: re = -s; im = c; break;
+        case 6: re = -h; im = h; break;
+        default: re = -c; im = s; break;
+    }
+    return mk<R>(re, S * im);
+}
+
+template <typename R, int S> __device__ __forceinline__ void dft8(cpx<R> *v) {
+    cpx<R> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<R, S>(e);
+    dft4<R, S>(o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cpx<R> t = (k == 0) ? o[0] : mul<R>(o[k], w16<R, S>(2 * k));
+        v[k] = add<R>(e[k], t);
+        v[k + 4] = sub<R>(e[k], t);
+    }
+}
+
+template <typename R, int S> __device__ __forceinline__ void dft16(cpx<R> *v) {
+    cpx<R> e[8], o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { e[k] = v[2 * k]; o[k] = v[2 * k + 1]; }
+    dft8<R, S>(e);
+    dft8<R, S>(o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cpx<R> t = (k == 0) ? o[0] : mul<R>(o[k], w16<R, S>(k));
+        v[k] = add<R>(e[k], t);
+        v[k + 8] = sub<R>(e[k], t);
+    }
+}
+
+template <typename R, int S, int RAD> __device__ __forceinline__ void dft(cpx<R> *v) {
+    if constexpr (RAD == 2) dft2<R, S>(v[0], v[1]);
+    else if constexpr (RAD == 3) dft3<R, S>(v);
+    else if constexpr (RAD == 4) dft4<R, S>(v);
+    else if constexpr (RAD == 5) dft5<R, S>(v);
+    else if constexpr (RAD == 8) dft8<R, S>(v);
+    else dft16<R, S>(v);
+}
+
+// ---------------------------------------------------------------------------
+// One Stockham stage over L interleaved lines: src -> dst.
+// Butterfly j (0 <= j < N/RAD) reads src[j + r N/RAD], multiplies input r by
+// w_{Ns RAD}^{(j mod Ns) r}, and writes dst[(j/Ns) Ns RAD + (j mod Ns) + r Ns].
+// ---------------------------------------------------------------------------
+template <typename R, int S, int RAD>
+__device__ __forceinline__ void stockham_stage(const cpx<R> *__restrict__ src, cpx<R> *__restrict__ dst,
+                                               int N, int Ns, int L, const cpx<R> *__restrict__ tw) {
+    const int nb = N / RAD;
+    const int total = nb * L;
+    const int twstep = N / (Ns * RAD);
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int j = b / L;
+        const int l = b - j * L;
+        cpx<R> v[RAD];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[r] = src[(j + r * nb) * L + l];
+        const int jm = j % Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                cpx<R> w = __ldg(&tw[jm * r * twstep]);
+                if (S > 0) w.y = -w.y;
+                v[r] = mul<R>(v[r], w);
+            }
+        }
+        dft<R, S, RAD>(v);
+        const int o = (j - jm) * RAD + jm;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) dst[(o + r * Ns) * L + l] = v[r];
+    }
+}
+
+// Full transform of L interleaved lines held in bufA.  Returns the buffer
+// holding the result (bufA or bufB).  All threads of the block must call it.
+template <typename R, int S>
+__device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, const AxisPlan &p) {
+    cpx<R> *src = bufA, *dst = bufB;
+    const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(p.tw);
+    int Ns = 1;
+    for (int s = 0; s < p.nstages; ++s) {
+        const int rad = p.radix[s];
+        switch (rad) {
+            case 2: stockham_stage<R, S, 2>(src, dst, p.n, Ns, L, tw); break;
+            case 3: stockham_stage<R, S, 3>(src, dst, p.n, Ns, L, tw); break;
+            case 4: stockham_stage<R, S, 4>(src, dst, p.n, Ns, L, tw); break;
+            case 5: stockham_stage<R, S, 5>(src, dst, p.n, Ns, L, tw); break;
+            case 8: stockham_stage<R, S, 8>(src, dst, p.n, Ns, L, tw); break;
+            default: stockham_stage<R, S, 16>(src, dst, p.n, Ns, L, tw); break;
+        }
+        __syncthreads();
+        Ns *= rad;
+        cpx<R> *t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
+}  // namespace hom

@@ -1,0 +1,273 @@
+"""Python binding of libhom.so (include/hom.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under the same name.  Buffers may be
+numpy arrays (host) or torch CUDA tensors (device; create the context with
+``device_ptrs=True``).  All arithmetic runs in the library's CUDA kernels;
+there is no CPU fallback, and importing this module on a machine where the
+library or a GPU is missing raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhom.so")
+
+HOM_OK, HOM_NOT_CONVERGED = 0, 1
+HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ENOMEM, HOM_ECUDA, HOM_ENAN, HOM_ETIMEOUT = -1, -2, -3, -4, -5, -6
+HOM_INPUT_PHASE_U8, HOM_INPUT_FRACTION_F32, HOM_INPUT_FRACTION_F64 = 0, 1, 2
+HOM_SMOOTH_NONE = 0
+HOM_DERIV_CONTINUOUS, HOM_DERIV_ROTATED = 0, 1
+HOM_SOLVER_GALERKIN_MINRES = 0
+HOM_PREC_FP32_FIELDS, HOM_PREC_FP64 = 0, 1
+
+# every symbol include/hom.h declares
+EXPORTED = [
+    "hom_default_options", "hom_create", "hom_solve", "hom_effective_stiffness",
+    "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
+    "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
+    "hom_last_error",
+]
+
+
+class hom_options(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int),
+                ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+class hom_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("sweeps", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("est_residual", ctypes.c_double), ("true_residual", ctypes.c_double),
+                ("sigma_mean", ctypes.c_double * 6), ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "status": self.status, "sweeps": self.sweeps,
+                "est_residual": self.est_residual, "true_residual": self.true_residual,
+                "sigma_mean": np.array(self.sigma_mean[:]), "time_ms": self.time_ms}
+
+
+class HomError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libhom error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhom.so; raises if it is missing (build with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhom.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.hom_default_options.argtypes = [ctypes.POINTER(hom_options)]
+    lib.hom_default_options.restype = None
+    lib.hom_create.argtypes = [ctypes.POINTER(vp), ip, vp, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(hom_options)]
+    lib.hom_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
+                              ctypes.POINTER(hom_solve_info)]
+    lib.hom_effective_stiffness.argtypes = [vp, dp]
+    lib.hom_fields.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.hom_apply.argtypes = [vp, vp, vp]
+    lib.hom_rhs.argtypes = [vp, dp, vp]
+    lib.hom_fft_forward.argtypes = [vp, vp, vp]
+    lib.hom_fft_inverse.argtypes = [vp, vp, vp]
+    lib.hom_project.argtypes = [vp, vp, vp]
+    lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    lib.hom_get_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hom_kernel_launches.argtypes = [vp]
+    lib.hom_kernel_launches.restype = ctypes.c_longlong
+    lib.hom_destroy.argtypes = [vp]
+    lib.hom_destroy.restype = None
+    lib.hom_last_error.argtypes = [vp]
+    lib.hom_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _check(ctx_handle, rc):
+    if rc < 0:
+        msg = load_library().hom_last_error(ctx_handle)
+        raise HomError(rc, msg.decode() if msg else "")
+    return rc
+
+
+class Context:
+    """Owning wrapper of a hom_ctx*; methods call the C entry points."""
+
+    def __init__(self, handle, grid, precision, device_ptrs):
+        self.handle = handle
+        self.grid = tuple(grid)
+        self.V = int(np.prod(grid))
+        self.precision = precision
+        self.device_ptrs = device_ptrs
+        self.dtype = np.float32 if precision == HOM_PREC_FP32_FIELDS else np.float64
+
+    def close(self):
+        if self.handle:
+            load_library().hom_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
+               smoothing=HOM_SMOOTH_NONE, derivative=HOM_DERIV_ROTATED,
+               precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
+               device=-1, refine=3) -> Context:
+    lib = load_library()
+    opt = hom_options()
+    lib.hom_default_options(ctypes.byref(opt))
+    opt.precision = precision
+    opt.device_ptrs = 1 if device_ptrs else 0
+    opt.stream = stream
+    opt.device = device
+    opt.refine = refine
+    h = ctypes.c_void_p()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),
+                        int(smoothing), int(derivative), ctypes.byref(opt))
+    if rc < 0:
+        msg = lib.hom_last_error(None)
+        raise HomError(rc, msg.decode() if msg else "")
+    return Context(h, grid, precision, device_ptrs)
+
+
+def hom_solve(ctx: Context, macro_strain, tol=1e-6, max_it=1000, warm_start=None):
+    """Returns (rc, [info dicts]).  macro_strain: (ncase, 6) tensor components."""
+    lib = load_library()
+    m = np.ascontiguousarray(np.asarray(macro_strain, dtype=np.float64).reshape(-1, 6))
+    ncase = m.shape[0]
+    infos = (hom_solve_info * ncase)()
+    rc = lib.hom_solve(ctx.handle, m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ncase,
+                       float(tol), int(max_it), _ptr(warm_start), infos)
+    _check(ctx.handle, rc)
+    return rc, [i.as_dict() for i in infos]
+
+
+def hom_effective_stiffness(ctx: Context) -> np.ndarray:
+    C = np.zeros(36)
+    _check(ctx.handle, load_library().hom_effective_stiffness(
+        ctx.handle, C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return C.reshape(6, 6)
+
+
+def _out(ctx, shape, out):
+    if out is not None:
+        return out
+    assert not ctx.device_ptrs, "pass device output buffers when device_ptrs is set"
+    return np.empty(shape, dtype=ctx.dtype)
+
+
+def hom_fields(ctx: Context, icase: int, strain=None, stress=None, want=("strain", "stress")):
+    if strain is None and "strain" in want:
+        strain = _out(ctx, (6,) + ctx.grid, None)
+    if stress is None and "stress" in want:
+        stress = _out(ctx, (6,) + ctx.grid, None)
+    _check(ctx.handle, load_library().hom_fields(ctx.handle, int(icase), _ptr(strain), _ptr(stress)))
+    return strain, stress
+
+
+def hom_apply(ctx: Context, eps, out=None):
+    out = _out(ctx, (6,) + ctx.grid, out)
+    _check(ctx.handle, load_library().hom_apply(ctx.handle, _ptr(eps), _ptr(out)))
+    return out
+
+
+def hom_rhs(ctx: Context, macro_strain, out=None):
+    out = _out(ctx, (6,) + ctx.grid, out)
+    m = np.ascontiguousarray(macro_strain, dtype=np.float64)
+    _check(ctx.handle, load_library().hom_rhs(ctx.handle, m.ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double)), _ptr(out)))
+    return out
+
+
+def spectrum_shape(ctx: Context):
+    n1, n2, n3 = ctx.grid
+    return (6, n1, n2, n3 // 2 + 1)
+
+
+def hom_fft_forward(ctx: Context, field, spectrum=None):
+    if spectrum is None:
+        assert not ctx.device_ptrs
+        spectrum = np.empty(spectrum_shape(ctx),
+                            dtype=np.complex64 if ctx.dtype == np.float32 else np.complex128)
+    _check(ctx.handle, load_library().hom_fft_forward(ctx.handle, _ptr(field), _ptr(spectrum)))
+    return spectrum
+
+
+def hom_fft_inverse(ctx: Context, spectrum, field=None):
+    field = _out(ctx, (6,) + ctx.grid, field)
+    _check(ctx.handle, load_library().hom_fft_inverse(ctx.handle, _ptr(spectrum), _ptr(field)))
+    return field
+
+
+def hom_project(ctx: Context, field, out=None):
+    out = _out(ctx, (6,) + ctx.grid, out)
+    _check(ctx.handle, load_library().hom_project(ctx.handle, _ptr(field), _ptr(out)))
+    return out
+
+
+KERNEL_NAMES = ["x3_fwd", "x2_fwd", "x1_gamma", "x2_inv", "x3_inv_dot", "alpha", "lanczos",
+                "givens", "update"]
+
+
+def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:
+    ms = np.zeros(16)
+    n = _check(ctx.handle, load_library().hom_time_kernels(
+        ctx.handle, int(reps), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 16))
+    return {KERNEL_NAMES[i]: float(ms[i]) for i in range(n)}
+
+
+def hom_get_info(ctx: Context):
+    g = (ctypes.c_int * 3)()
+    p = ctypes.c_int()
+    w = ctypes.c_longlong()
+    _check(ctx.handle, load_library().hom_get_info(ctx.handle, g, ctypes.byref(p), ctypes.byref(w)))
+    return tuple(g), p.value, w.value
+
+
+def hom_kernel_launches(ctx: Context) -> int:
+    return int(load_library().hom_kernel_launches(ctx.handle))
+
+
+def hom_destroy(ctx: Context):
+    ctx.close()
+
+
+def hom_last_error(ctx: Context | None = None) -> str:
+    s = load_library().hom_last_error(ctx.handle if ctx else None)
+    return s.decode() if s else ""

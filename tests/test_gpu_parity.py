@@ -1,0 +1,165 @@
+"""GPU parity: each step of the hot path through the C ABI against the FP64
+oracle, element by element, on seeded inputs.
+
+FP32 fields: max-abs error <= 2e-5 of the field's max |value| (FP32 FFT
+round-off grows like u log2 V with u = 6e-8; 2e-5 leaves a margin of ~10 at
+the sizes here).  FP64 fields: 1e-11."""
+import numpy as np
+import pytest
+
+import oracle
+import rve_inputs as ri
+from gpu_util import FP32_TOL, FP64_TOL, half_spectrum, rel_maxerr
+
+pytestmark = pytest.mark.gpu
+
+E_M, NU_M = 110e9, 0.3
+# several tiles and ragged tails on every axis; odd n3; mixed radices
+SHAPES = [(8, 8, 8), (24, 20, 18), (12, 10, 9), (32, 32, 32), (30, 16, 40), (2, 6, 4), (5, 3, 50)]
+PRECS = ["fp32", "fp64"]
+
+
+@pytest.fixture(scope="module")
+def hom():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2110_00733_gb300 import build, hom as h
+    build.build()
+    h.load_library()
+    return h
+
+
+def make(hom, phi, prec, deriv=1):
+    p = hom.HOM_PREC_FP32_FIELDS if prec == "fp32" else hom.HOM_PREC_FP64
+    return hom.hom_create(phi.shape, np.ascontiguousarray(phi, dtype=np.float64),
+                          hom.HOM_INPUT_FRACTION_F64, E_M, NU_M, derivative=deriv, precision=p)
+
+
+def tol(prec):
+    return FP32_TOL if prec == "fp32" else FP64_TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fft_forward_inverse(hom, shape, prec):
+    phi = ri.random_phi(shape, seed=1)
+    f = ri.random_field(shape, seed=sum(shape))
+    with make(hom, phi, prec) as ctx:
+        spec = hom.hom_fft_forward(ctx, f.astype(ctx.dtype))
+        ref = np.stack([oracle.fft3d(f[c].astype(complex)) for c in range(6)])
+        assert rel_maxerr(spec, half_spectrum(ref)) <= tol(prec)
+        back = hom.hom_fft_inverse(ctx, np.ascontiguousarray(half_spectrum(ref).astype(spec.dtype)))
+        assert rel_maxerr(back, f) <= tol(prec)
+
+
+@pytest.mark.parametrize("deriv", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_project_apply_rhs(hom, shape, prec, deriv):
+    phi = ri.random_phi(shape, seed=2)
+    f = ri.random_field(shape, seed=7)
+    with make(hom, phi, prec, deriv) as ctx:
+        got = hom.hom_project(ctx, f.astype(ctx.dtype))
+        assert rel_maxerr(got, oracle.project(shape, deriv, f)) <= tol(prec)
+        got = hom.hom_apply(ctx, f.astype(ctx.dtype))
+        ref = oracle.apply(phi, 1.0, NU_M, deriv, f) * E_M   # library works in units of E
+        assert rel_maxerr(got * E_M, ref) <= tol(prec)
+        Eb = np.array([1e-3, -2e-4, 3e-4, 5e-4, -1e-4, 2e-4])
+        got = hom.hom_rhs(ctx, Eb)
+        ref = oracle.rhs(phi, 1.0, NU_M, deriv, Eb)
+        assert rel_maxerr(got, ref) <= tol(prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("deriv", [1, 0])
+def test_solve_octet_matches_oracle(hom, prec, deriv):
+    """C_eff (6 unit strains) within 1e-4 relative; strain on solid voxels and
+    stress everywhere within 1e-4 (L2), eq. (difff)."""
+    phi, _ = ri.octet(16, 0.2)
+    phi = phi.astype(np.float64)
+    Cref, sols = oracle.effective_stiffness(phi, E_M, NU_M, deriv, tol=1e-11, max_it=5000)
+    with make(hom, phi, prec, deriv) as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-8, max_it=3000)
+        assert rc == hom.HOM_OK, [i["status"] for i in info]
+        C = hom.hom_effective_stiffness(ctx)
+        assert np.max(np.abs(C - Cref)) <= 1e-4 * np.max(np.abs(Cref))
+        for J in [0, 3]:
+            strain, stress = hom.hom_fields(ctx, J)
+            eps_ref = oracle.mandel_to_tensor(sols[J]["eps_tilde"]) + np.eye(6)[J][:, None, None, None]
+            solid = phi > 0
+            e_err = np.linalg.norm((strain - eps_ref)[:, solid]) / np.linalg.norm(eps_ref[:, solid])
+            assert e_err <= 1e-4
+            Cm = oracle.stiffness_mandel(E_M, NU_M)
+            em = oracle.tensor_to_mandel(eps_ref)
+            sig_ref = oracle.mandel_to_tensor(np.einsum("ij,j...->i...", Cm, em) * phi)
+            s_err = np.linalg.norm(stress - sig_ref) / np.linalg.norm(sig_ref)
+            assert s_err <= 1e-4
+            assert info[J]["true_residual"] <= 1e-8
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_laminate_closed_form_on_gpu(hom, prec):
+    """Layered cell: exact laminate C_eff (the oracle's own pin), now on the GPU."""
+    from test_oracle_solver import laminate_closed_form
+    phi = ri.laminate((12, 6, 5), (4, 2, 6), (1.0, 0.2, 0.55), axis=0)
+    with make(hom, phi, prec) as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-9, max_it=500)
+        assert rc == hom.HOM_OK
+        for J in range(6):
+            ref = laminate_closed_form([1.0, 0.2, 0.55], [4 / 12, 2 / 12, 6 / 12], np.eye(6)[J])
+            assert np.allclose(info[J]["sigma_mean"], ref, rtol=1e-5, atol=1e-5 * E_M)
+
+
+def test_homogeneous_cell_is_a_noop(hom):
+    phi = np.full((8, 6, 10), 0.4)
+    with make(hom, phi, "fp32") as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-6, max_it=100)
+        assert rc == hom.HOM_OK
+        assert all(i["iterations"] == 0 for i in info)
+        from test_oracle_solver import voigt_stiffness
+        assert np.allclose(hom.hom_effective_stiffness(ctx), 0.4 * voigt_stiffness(E_M, NU_M), rtol=1e-6)
+
+
+def test_errors_and_limits(hom):
+    phi = ri.random_phi((8, 8, 8), seed=3)
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create((7, 8, 8), np.zeros((7, 8, 8)), hom.HOM_INPUT_FRACTION_F64, E_M, NU_M)
+    assert e.value.code == hom.HOM_EUNSUPPORTED_GRID
+    bad = phi.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create(bad.shape, bad, hom.HOM_INPUT_FRACTION_F64, E_M, NU_M)
+    assert e.value.code == hom.HOM_EINVAL
+    with pytest.raises(hom.HomError):
+        hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F64, -1.0, NU_M)
+    with make(hom, phi, "fp32") as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6)[0], tol=1e-12, max_it=2)
+        assert rc == hom.HOM_NOT_CONVERGED and info[0]["status"] == hom.HOM_NOT_CONVERGED
+        with pytest.raises(hom.HomError):
+            hom.hom_effective_stiffness(ctx)       # fewer than 6 cases
+        with pytest.raises(hom.HomError):
+            hom.hom_fields(ctx, 3)
+
+
+def test_largest_axis_and_device_pointers(hom):
+    """n = 512 on one axis (largest supported transform) and device buffers."""
+    import torch
+    shape = (4, 6, 512)
+    phi = ri.random_phi(shape, seed=4)
+    f = ri.random_field(shape, seed=5)
+    ctx = hom.hom_create(shape, torch.tensor(phi, device="cuda"), hom.HOM_INPUT_FRACTION_F64, E_M, NU_M,
+                         precision=hom.HOM_PREC_FP32_FIELDS, device_ptrs=True)
+    try:
+        fin = torch.tensor(f, dtype=torch.float32, device="cuda")
+        out = torch.empty_like(fin)
+        hom.hom_apply(ctx, fin, out)
+        torch.cuda.synchronize()
+        ref = oracle.apply(phi, 1.0, NU_M, 1, f)
+        assert rel_maxerr(out.cpu().numpy(), ref) <= FP32_TOL
+        shape2 = (512, 4, 6)
+        phi2 = ri.random_phi(shape2, seed=6)
+        with make(hom, phi2, "fp32") as c2:
+            g = hom.hom_apply(c2, f.reshape((6,) + shape2).astype(np.float32))
+            assert rel_maxerr(g, oracle.apply(phi2, 1.0, NU_M, 1, f.reshape((6,) + shape2))) <= FP32_TOL
+    finally:
+        ctx.close()
