@@ -41,18 +41,18 @@ TOL = 1e-6
 MAX_IT = 20000
 
 # Algorithmic bytes per voxel moved by each kernel of one MINRES iteration,
-# FP32 fields (the half spectrum holds 6 * (n3/2+1)/n3 complex64 per voxel).
+# FP32 fields: one half spectrum (6 complex64 per frequency) is
+# 48 (n3/2+1)/n3 bytes per voxel; the MINRES vectors are half spectra too.
 def kernel_bytes_per_voxel(n3: int) -> dict:
-    spec = 6 * 8 * (n3 // 2 + 1) / n3
-    f = 24.0                      # one 6-component FP32 field
+    spec = 48.0 * (n3 // 2 + 1) / n3
     return {
-        "x3_fwd": f + 4 + spec,   # read v, phi; write spectrum
-        "x2_fwd": 2 * spec,
-        "x1_gamma": 2 * spec,
+        "x1_inv_gamma": 2 * spec,          # read v, write work spectrum
         "x2_inv": 2 * spec,
-        "x3_inv_dot": spec + 2 * f,   # read spectrum, v; write p
-        "lanczos": 3 * f + f,         # read p, v_k, v_{k-1}; write p
-        "update": 5 * f + 3 * f,      # read v, w1, w2, x, p; write w, x, v
+        "x3_c2r_law_r2c": 2 * spec + 4,    # + phi
+        "x2_fwd": 2 * spec,
+        "x1_fwd_gamma_dot": 3 * spec,      # read work, write p, read v (dot)
+        "lanczos": 4 * spec,               # read p, v_k, v_{k-1}; write p
+        "update": 8 * spec,                # read v, w1, w2, x, p; write w, x, v
     }
 
 

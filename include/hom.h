@@ -25,8 +25,14 @@
  *     (e11, e22, e33, sqrt2 e23, sqrt2 e13, sqrt2 e12); the others use tensor
  *     components (e11, e22, e33, e23, e13, e12).
  *   - A "spectrum" is the half spectrum of 6 real components:
- *     6 x n1 x n2 x (n3/2+1) complex values (re, im interleaved), component-
- *     major, unnormalised forward DFT with kernel exp(-2 pi i k n / N).
+ *     n1 x n2 x (n3/2+1) x 6 complex values (re, im interleaved), the six
+ *     components of one frequency adjacent, unnormalised forward DFT with
+ *     kernel exp(-2 pi i k n / N).
+ *   - MINRES (section 2.1) runs on the DFT of the strain fluctuation: on
+ *     A^ = G F C F^-1 G with the Parseval inner product, which on compatible
+ *     fields is the same iteration as MINRES on A of eq. (linearOp); applying
+ *     G to the input too keeps rounding from driving the iterate out of the
+ *     compatible subspace.
  *   - Field and spectrum buffers are float (HOM_PREC_FP32_FIELDS) or double
  *     (HOM_PREC_FP64) as chosen at create time.  They are host pointers unless
  *     hom_options.device_ptrs is set, in which case they are device pointers
@@ -34,6 +40,10 @@
  *   - The caller owns every buffer it passes; the library copies what it
  *     keeps.  The context owns its device workspace (allocated by hom_create,
  *     freed by hom_destroy).
+ *   - Stiffness, stress and the outputs of hom_apply / hom_rhs: hom_apply and
+ *     hom_rhs use C_m / E (units of E); hom_solve_info.sigma_mean,
+ *     hom_effective_stiffness and hom_fields' stress are in the units of E.
+ *   - Entry points return after their device work has completed.
  *   - Return value: HOM_OK (0), a positive warning (result valid), or a
  *     negative error, in which case no output buffer has been written;
  *     hom_last_error() then describes the failure.
@@ -76,6 +86,9 @@ typedef struct {
     void *stream;       /* cudaStream_t to run on; NULL: a stream the context creates */
     int device;         /* CUDA device ordinal; -1: the current device */
     int refine;         /* FP32 fields: max FP64 iterative-refinement sweeps (default 3) */
+    int rows3;          /* launch shape: n3-pass rows per CTA (0 = automatic, <= 64) */
+    int tile2;          /* launch shape: n2-pass columns per CTA (0 = automatic; power of 2, <= 32) */
+    int tile1;          /* launch shape: n1-pass columns per CTA (0 = automatic, <= 16) */
 } hom_options;
 
 typedef struct {
@@ -85,7 +98,7 @@ typedef struct {
     int reserved;
     double est_residual;   /* MINRES estimate phibar_k / beta_1 at exit */
     double true_residual;  /* ||A(e~) - b|| / ||b|| evaluated in FP64, eq. (galres) */
-    double sigma_mean[6];  /* volume-averaged stress, tensor components, units of E */
+    double sigma_mean[6];  /* volume-averaged stress, tensor components, same units as E */
     double time_ms;        /* device time of this case */
 } hom_solve_info;
 
@@ -123,7 +136,7 @@ int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol,
               int max_it, const void *warm_start, hom_solve_info *info);
 
 /* 6x6 Voigt effective stiffness, row-major, sigma = C (e11,e22,e33,2e23,2e13,2e12),
- * units of E, from the mean stresses of the last hom_solve.  That solve must
+ * same units as E, from the mean stresses of the last hom_solve.  That solve must
  * have had ncase >= 6 cases whose macro strains span all six directions;
  * otherwise HOM_EINVAL.  Section 4.3 extracts E and nu from such averages. */
 int hom_effective_stiffness(hom_ctx *ctx, double C[36]);
@@ -158,10 +171,10 @@ int hom_project(hom_ctx *ctx, const void *in, void *out);
  * of this context, each launched `reps` times back to back on the context's
  * stream between two CUDA events, on the workspace's current contents (an
  * instrument for roofline measurements; it changes no solver state that a
- * later hom_solve reads).  ms[0..8]: x3 forward (material + R2C), x2 forward,
- * x1 (transform + projector + inverse), x2 inverse, x3 inverse (C2R + dot),
- * alpha reduction, Lanczos axpy + norm, Givens step, w/x/v update.  Returns
- * the number of entries written (<= nmax). */
+ * later hom_solve reads).  ms[0..8]: n1 pass (projector + inverse), n2 inverse,
+ * n3 pass (C2R + material law + R2C), n2 forward, n1 pass (forward +
+ * projector + dot product), alpha reduction, Lanczos axpy + norm, Givens
+ * step, w/x/v update.  Returns the number of entries written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* Grid, precision and workspace size of a context. */

@@ -1,7 +1,7 @@
 // hom_api.cu -- the C ABI of include/hom.h: contexts, FFT plans, the
-// operator of eq. (linearOp), MINRES (section 2.1) as a captured CUDA graph,
-// FP64 true residual of eq. (galres) with iterative refinement for FP32 fields,
-// and the volume-averaged stress of section 4.3.
+// operator of eq. (linearOp) in its spectral form, MINRES (section 2.1) as a
+// captured CUDA graph, the FP64 true residual of eq. (galres) with iterative
+// refinement for FP32 fields, and the volume-averaged stress of section 4.3.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -20,6 +20,12 @@ using namespace hom;
 namespace {
 
 thread_local std::string g_create_error;
+
+// smallest relative residual reduction one FP32-field MINRES sweep is asked for
+constexpr double kFp32SweepFloor = 1e-6;
+// relative size of ||b|| / ||C : E_bar|| below which the right-hand side is
+// FFT round-off and is taken as zero (the paper is silent on this case)
+constexpr double kRhsZero = 1e-12;
 
 struct Status {
     int code = HOM_OK;
@@ -50,15 +56,16 @@ struct hom_ctx {
     bool own_stream = false;
     int device_ptrs = 0;
     int refine = 3;
+    int shape[3] = {0, 0, 0};   // launch-shape overrides (rows3, tile2, tile1)
     Engine<float> e32;
     Engine<double> e64;
-    // MINRES workspace in the solve precision (float or double)
+    // MINRES workspace in the solve precision (half spectra, float2 or double2)
     void *vbuf[3] = {nullptr, nullptr, nullptr};
     void *wbuf[2] = {nullptr, nullptr};
     void *xs = nullptr;     // MINRES iterate of the current sweep
     void *rhs = nullptr;    // MINRES right-hand side of the current sweep
-    double *b64 = nullptr, *r64 = nullptr, *stage64 = nullptr;
-    std::vector<double *> x64;      // per-case solutions (Mandel, FP64 master copy)
+    double2 *b64 = nullptr, *r64 = nullptr;   // FP64 right-hand side and residual spectra
+    std::vector<double2 *> x64;     // per-case solutions (spectral, FP64 master copy)
     std::vector<double> macros;     // per-case macro strains (Mandel, as solved)
     std::vector<double> sig_mean;   // per-case mean stress (tensor comps, units of E)
     int ncase = 0;
@@ -130,20 +137,69 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     g.V = ctx->V;
     g.S = ctx->S;
     const size_t cs = cpx_size<R>();
-    // launch shapes: x3 passes hold 3*rows lines of n3, x2 tile2 lines of n2,
-    // x1 6*tile1 lines of n1, each twice (Stockham ping-pong)
-    int rows = 16;
-    while (rows > 1 && 2ull * g.n3 * 3 * rows * cs > 96 * 1024) rows >>= 1;
+    for (int p = 0; p < 3; ++p) g.fast[p] = is_fast_length(ctx->n[p]) ? ctx->n[p] : 0;
+    // launch shapes (defaults; hom_options may override them -- autotuner hook)
+    //  fast engine: threads = lines * n / E, one buffer of lines * n values
+    //  generic engine: Stockham ping-pong, two buffers
+    int rows, t2, t1;
+    if (g.fast[2]) {
+        rows = 192 / (3 * (g.n3 / fast_elems(g.n3)));
+        rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
+    } else {
+        rows = 16;
+        while (rows > 1 && 2ull * g.n3 * 3 * rows * cs > 48 * 1024) rows >>= 1;
+    }
+    if (g.fast[1]) {
+        t2 = g.n2 >= 128 ? 16 : 32;
+    } else {
+        t2 = 32;
+        while (t2 > 1 && 2ull * g.n2 * t2 * cs > 64 * 1024) t2 >>= 1;
+    }
+    if (g.fast[0]) {
+        t1 = 384 * fast_elems(g.n1) / (6 * g.n1);
+        t1 = t1 < 1 ? 1 : (t1 > 16 ? 16 : t1);
+    } else {
+        t1 = 16;
+        while (t1 > 1 && 2ull * g.n1 * 6 * t1 * cs > 96 * 1024) t1 >>= 1;
+    }
+    if (ctx->shape[0] > 0) rows = ctx->shape[0];
+    if (ctx->shape[1] > 0) t2 = ctx->shape[1];
+    if (ctx->shape[2] > 0) t1 = ctx->shape[2];
     g.rows3 = rows;
-    int t2 = 32;
-    while (t2 > 1 && 2ull * g.n2 * t2 * cs > 96 * 1024) t2 >>= 1;
     g.tile2 = t2;
-    int t1 = 16;
-    while (t1 > 1 && 2ull * g.n1 * 6 * t1 * cs > 200 * 1024) t1 >>= 1;
     g.tile1 = t1;
-    g.smem3 = 2ull * g.n3 * 3 * g.rows3 * cs;
-    g.smem2 = 2ull * g.n2 * g.tile2 * cs;
-    g.smem1 = 2ull * g.n1 * 6 * g.tile1 * cs;
+    auto round32 = [](int v) { return (v + 31) / 32 * 32; };
+    auto clampt = [](int v) { return v < 128 ? 128 : (v > 512 ? 512 : v); };
+    if (g.fast[2]) {
+        g.threads3 = 3 * rows * (g.n3 / fast_elems(g.n3));
+        g.smem3 = (size_t)3 * rows * g.n3 * cs;
+    } else {
+        g.threads3 = clampt(round32(3 * rows * g.n3 / 16));
+        g.smem3 = 2ull * 3 * rows * g.n3 * cs;
+    }
+    if (g.fast[1]) {
+        g.threads2 = t2 * (g.n2 / fast_elems(g.n2));
+        g.smem2 = (size_t)t2 * g.n2 * cs;
+    } else {
+        g.threads2 = clampt(round32(t2 * g.n2 / 16));
+        g.smem2 = 2ull * t2 * g.n2 * cs;
+    }
+    const int L1 = 6 * t1;
+    if (g.fast[0]) {
+        g.threads1 = L1 * (g.n1 / fast_elems(g.n1));
+        g.smem1 = (size_t)L1 * g.n1 * cs;
+    } else {
+        const int m = 256 / L1;
+        g.threads1 = L1 * (m < 1 ? 1 : m);
+        g.smem1 = 2ull * L1 * g.n1 * cs;
+    }
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (g.smem3 + 1024 > (size_t)dev_smem || g.smem2 + 1024 > (size_t)dev_smem || g.smem1 + 1024 > (size_t)dev_smem)
+        return fail(ctx, HOM_EINVAL, "launch shape needs more shared memory than the device has");
+    if (g.threads1 > 512 || g.threads2 > 512 || g.threads3 > 512 || g.threads1 < 1 || g.threads2 < 1 || g.threads3 < 1)
+        return fail(ctx, HOM_EINVAL, "launch shape needs more than 512 threads per CTA");
+    if ((t2 & (t2 - 1)) != 0 || g.threads2 % t2 != 0) return fail(ctx, HOM_EINVAL, "tile2 must be a power of two");
     const double PI = 3.14159265358979323846;
     for (int p = 0; p < 3; ++p) {
         const int N = ctx->n[p];
@@ -197,30 +253,57 @@ static void engine_free(Engine<R> &E) {
     cudaFree(E.spec);
 }
 
-// One application of the operator chain: x3_fwd, x2, x1, x2^-1, x3_inv.
+// p = A^ v = G F C F^-1 G v (spectral vectors); optional <v, p> partials.
 template <typename R>
-static void op_chain(hom_ctx *ctx, Engine<R> &E, int fmode, const R *in, const double *macro, int x1flags,
-                     int imode, R *out, double scl, const R *dotv, double *partials, const MinresState *st) {
+static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool dot, double *partials,
+                    const MinresState *st) {
     cudaStream_t s = ctx->stream;
-    Launch<R>::x3_fwd(E.g, s, fmode, in, E.phi, ctx->lam, ctx->mu, macro, E.spec, st);
-    Launch<R>::x2(E.g, s, 0, E.spec, st);
-    Launch<R>::x1(E.g, s, x1flags, E.spec, st);
+    Launch<R>::x1(E.g, s, X1_GAMMA_IN, v, E.spec, nullptr, nullptr, st);
     Launch<R>::x2(E.g, s, 1, E.spec, st);
-    Launch<R>::x3_inv(E.g, s, imode, E.spec, out, scl, dotv, partials, st);
+    Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
+                  E.phi, st);
+    Launch<R>::x2(E.g, s, 0, E.spec, st);
+    Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | (dot ? X1_DOT : 0), E.spec, p, dot ? v : nullptr, partials, st);
     ctx->launches += 5;
 }
 
-static int x3_grid(const Geometry &g) { return (int)(((long long)g.n1 * g.n2 + g.rows3 - 1) / g.rows3); }
-static int ew_blocks(long long n) {
-    long long b = (n + kEwThreads - 1) / kEwThreads;
-    return (int)(b < kEwBlocks ? (b > 0 ? b : 1) : kEwBlocks);
+// b^ = -G F (C : E_bar) (spectral), eq. (gallin) with sigma_bar = 0
+template <typename R>
+static void rhs_spec(hom_ctx *ctx, Engine<R> &E, const double *macro_mandel, cpx<R> *b) {
+    cudaStream_t s = ctx->stream;
+    Launch<R>::x3(E.g, s, X3_IN_MACRO, nullptr, X3_MID_MATERIAL, ctx->lam, ctx->mu, macro_mandel, -1.0, X3_OUT_SPEC,
+                  E.spec, E.phi, nullptr);
+    Launch<R>::x2(E.g, s, 0, E.spec, nullptr);
+    Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT, E.spec, b, nullptr, nullptr, nullptr);
+    ctx->launches += 3;
 }
 
-// ||v||^2 of a device vector via the partials buffer; synchronous.
+// real Mandel field -> spectrum (optionally material law, optionally projector)
 template <typename R>
-static int dev_norm2(hom_ctx *ctx, const R *v, long long n, double *out) {
-    Launch<R>::norm2(n, ctx->stream, v, ctx->partials);
-    reduce_to(ctx->stream, ctx->partials, ew_blocks(n), ctx->d_scalar);
+static void real_to_spec(hom_ctx *ctx, Engine<R> &E, const R *in, int mid, bool gamma, cpx<R> *out) {
+    cudaStream_t s = ctx->stream;
+    Launch<R>::x3(E.g, s, X3_IN_REAL, in, mid, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec, E.phi, nullptr);
+    Launch<R>::x2(E.g, s, 0, E.spec, nullptr);
+    Launch<R>::x1(E.g, s, X1_FWD | (gamma ? X1_GAMMA_OUT : 0), E.spec, out, nullptr, nullptr, nullptr);
+    ctx->launches += 3;
+}
+
+// spectrum -> real Mandel field (optionally projecting first), times scale
+template <typename R>
+static void spec_to_real(hom_ctx *ctx, Engine<R> &E, const cpx<R> *in, bool gamma, double scl, R *out) {
+    cudaStream_t s = ctx->stream;
+    Launch<R>::x1(E.g, s, gamma ? X1_GAMMA_IN : 0, in, E.spec, nullptr, nullptr, nullptr);
+    Launch<R>::x2(E.g, s, 1, E.spec, nullptr);
+    Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, scl, X3_OUT_REAL, out, E.phi,
+                  nullptr);
+    ctx->launches += 3;
+}
+
+// weighted ||v||^2 of a spectral vector; synchronous.
+template <typename R>
+static int spec_norm2(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, double *out) {
+    Launch<R>::norm2w(E.g, ctx->stream, v, ctx->partials);
+    reduce_to(ctx->stream, ctx->partials, Launch<R>::ew_grid(6 * ctx->S), ctx->d_scalar);
     ctx->launches += 2;
     CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -232,26 +315,24 @@ static int dev_norm2(hom_ctx *ctx, const R *v, long long n, double *out) {
 template <typename R>
 static int build_graph(hom_ctx *ctx, Engine<R> &E) {
     if (ctx->graph) return HOM_OK;
-    const long long n = 6 * ctx->V;
-    R *v[3] = {(R *)ctx->vbuf[0], (R *)ctx->vbuf[1], (R *)ctx->vbuf[2]};   // v_{k-1}, v_k, p
-    R *w[2] = {(R *)ctx->wbuf[0], (R *)ctx->wbuf[1]};                     // w_{k-1}, w_{k-2}
-    R *x = (R *)ctx->xs;
-    const int np3 = x3_grid(E.g), npe = ew_blocks(n);
+    cpx<R> *v[3] = {(cpx<R> *)ctx->vbuf[0], (cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->vbuf[2]};  // v_{k-1}, v_k, p
+    cpx<R> *w[2] = {(cpx<R> *)ctx->wbuf[0], (cpx<R> *)ctx->wbuf[1]};                          // w_{k-1}, w_{k-2}
+    cpx<R> *x = (cpx<R> *)ctx->xs;
+    const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
     cudaGraph_t graph;
     CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     long long before = ctx->launches;
     for (int it = 0; it < ctx->graph_iters; ++it) {
-        R *vprev = v[0], *vk = v[1], *p = v[2];
-        R *w1 = w[0], *w2 = w[1];
-        // p = A v_k, partial <v_k, p>
-        op_chain<R>(ctx, E, X3F_MATERIAL, vk, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE_DOT, p,
-                    1.0 / (double)ctx->V, vk, ctx->partials, ctx->d_state);
-        scalar_alpha(ctx->stream, ctx->d_state, ctx->partials, np3);
+        cpx<R> *vprev = v[0], *vk = v[1], *p = v[2];
+        cpx<R> *w1 = w[0], *w2 = w[1];
+        // p = A^ v_k, partial <v_k, p>
+        op_spec<R>(ctx, E, vk, p, true, ctx->partials, ctx->d_state);
+        scalar_alpha(ctx->stream, ctx->d_state, ctx->partials, np1);
         // p -= alpha v_k + beta_k v_{k-1}; partial ||p||^2
-        Launch<R>::lanczos(n, ctx->stream, p, vk, vprev, ctx->d_state, ctx->partials);
+        Launch<R>::lanczos(E.g, ctx->stream, p, vk, vprev, ctx->d_state, ctx->partials);
         scalar_givens(ctx->stream, ctx->d_state, ctx->partials, npe);
         // w_k (into w_{k-2}'s buffer), x_k, v_{k+1} = p / beta_{k+1} (in place)
-        Launch<R>::update(n, ctx->stream, p, vk, w1, w2, x, ctx->d_state);
+        Launch<R>::update(E.g, ctx->stream, p, vk, w1, w2, x, ctx->d_state);
         ctx->launches += 4;
         v[0] = vk; v[1] = p; v[2] = vprev;
         w[0] = w2; w[1] = w1;
@@ -266,22 +347,21 @@ static int build_graph(hom_ctx *ctx, Engine<R> &E) {
     return HOM_OK;
 }
 
-// MINRES on A x = rhs (rhs in ctx->rhs, solution in ctx->xs, precision R),
-// zero start.  Returns iterations / estimate / status through the pointers.
+// MINRES on A^ x = rhs (rhs in ctx->rhs, solution in ctx->xs, precision R),
+// zero start.
 template <typename R>
 static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters, double *est, int *status) {
-    const long long n = 6 * ctx->V;
+    const long long nr = 12 * ctx->S;   // reals per spectral vector
     cudaStream_t s = ctx->stream;
     int rc = build_graph<R>(ctx, E);
     if (rc) return rc;
-    // beta_1 = ||rhs||, Givens start
-    Launch<R>::norm2(n, s, (const R *)ctx->rhs, ctx->partials);
-    scalar_start(s, ctx->d_state, ctx->partials, ew_blocks(n), tol, max_it);
+    Launch<R>::norm2w(E.g, s, (const cpx<R> *)ctx->rhs, ctx->partials);
+    scalar_start(s, ctx->d_state, ctx->partials, Launch<R>::ew_grid(6 * ctx->S), tol, max_it);
     ctx->launches += 2;
     CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const double beta1 = ctx->h_state->beta1;
-    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * n, s));
+    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * nr, s));
     if (!(beta1 > 0.0) || !std::isfinite(beta1)) {
         *iters = 0;
         *est = 0.0;
@@ -290,11 +370,11 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         return HOM_OK;
     }
     // v_0 = 0, v_1 = rhs / beta_1, w = 0
-    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * n, s));
-    Launch<R>::axpby(n, s, 1.0 / beta1, (const R *)ctx->rhs, 0.0, (R *)ctx->vbuf[1]);
+    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nr, s));
+    Launch<R>::axpby(nr, s, 1.0 / beta1, (const R *)ctx->rhs, 0.0, (R *)ctx->vbuf[1]);
     ctx->launches += 1;
-    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * n, s));
-    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * n, s));
+    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nr, s));
     // replay the captured iterations until the state says done
     const int per_check = 4;
     int replays = 0;
@@ -368,8 +448,7 @@ void hom_destroy(hom_ctx *ctx) {
     cudaFree(ctx->rhs);
     cudaFree(ctx->b64);
     cudaFree(ctx->r64);
-    cudaFree(ctx->stage64);
-    for (double *p : ctx->x64) cudaFree(p);
+    for (double2 *p : ctx->x64) cudaFree(p);
     cudaFree(ctx->partials);
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_scalar);
@@ -391,6 +470,7 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     }
     ctx->V = (long long)grid[0] * grid[1] * grid[2];
     ctx->S = (long long)grid[0] * grid[1] * (grid[2] / 2 + 1);
+    if (12 * ctx->S >= (1LL << 31)) return fail(ctx, HOM_EUNSUPPORTED_GRID, "12 S must stay below 2^31");
     CU(cudaSetDevice(ctx->device));
     if (!ctx->stream) {
         CU(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
@@ -404,19 +484,19 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
         rc = engine_init<float>(ctx, ctx->e32);
         if (rc) return rc;
     }
-    const long long n = 6 * ctx->V;
+    const long long nr = 12 * ctx->S;   // reals per spectral vector (>= 6 V)
     const size_t rs = (ctx->prec == HOM_PREC_FP64) ? sizeof(double) : sizeof(float);
-    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * n));
-    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->wbuf[i], rs * n));
-    CU(cudaMalloc(&ctx->xs, rs * n));
-    CU(cudaMalloc(&ctx->rhs, rs * n));
-    CU(cudaMalloc(&ctx->b64, sizeof(double) * n));
-    CU(cudaMalloc(&ctx->r64, sizeof(double) * n));
-    ctx->workspace += 7 * (long long)rs * n + 2 * (long long)sizeof(double) * n;
-    ctx->npartials = 8 * kEwBlocks;
-    const long long np3 = std::max((long long)x3_grid(ctx->e64.g),
-                                   ctx->prec == HOM_PREC_FP32_FIELDS ? (long long)x3_grid(ctx->e32.g) : 0LL);
-    if (np3 > ctx->npartials) ctx->npartials = (int)np3;
+    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * nr));
+    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->wbuf[i], rs * nr));
+    CU(cudaMalloc(&ctx->xs, rs * nr));
+    CU(cudaMalloc(&ctx->rhs, rs * nr));
+    CU(cudaMalloc(&ctx->b64, sizeof(double) * nr));
+    CU(cudaMalloc(&ctx->r64, sizeof(double) * nr));
+    ctx->workspace += 7 * (long long)rs * nr + 2 * (long long)sizeof(double) * nr;
+    long long np = 8LL * kEwBlocks;
+    np = std::max(np, (long long)Launch<double>::x1_grid(ctx->e64.g));
+    if (ctx->prec == HOM_PREC_FP32_FIELDS) np = std::max(np, (long long)Launch<float>::x1_grid(ctx->e32.g));
+    ctx->npartials = (int)np;
     CU(cudaMalloc(&ctx->partials, sizeof(double) * ctx->npartials));
     CU(cudaMalloc(&ctx->d_state, sizeof(MinresState)));
     CU(cudaMalloc(&ctx->d_scalar, sizeof(double) * 8));
@@ -425,10 +505,9 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     CU(cudaMallocHost(&ctx->h_scalar, sizeof(double) * 8));
     // phase map -> phi (FP64 copy always; FP32 copy for FP32 fields)
     const size_t in_bytes = (input_kind == HOM_INPUT_PHASE_U8 ? 1 : input_kind == HOM_INPUT_FRACTION_F32 ? 4 : 8);
-    void *dev_in = nullptr;
-    CU(cudaMalloc(&dev_in, in_bytes * ctx->V));
+    void *dev_in = ctx->xs;   // staging (xs holds >= 6 V reals of the solve precision >= V * 8 bytes)
     rc = stage_in(ctx, phase, in_bytes * ctx->V, dev_in);
-    if (rc) { cudaFree(dev_in); return rc; }
+    if (rc) return rc;
     CU(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
     phi_convert<double>(ctx->V, ctx->stream, dev_in, input_kind, ctx->e64.phi, ctx->d_flag);
     if (ctx->prec == HOM_PREC_FP32_FIELDS)
@@ -437,13 +516,20 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     int bad = 0;
     CU(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    cudaFree(dev_in);
     if (bad) return fail(ctx, HOM_EINVAL, "phase values must be finite and in [0,1]");
     // sum phi^2 for the zero right-hand-side test
-    double s2 = 0.0;
-    rc = dev_norm2<double>(ctx, ctx->e64.phi, ctx->V, &s2);
-    if (rc) return rc;
-    ctx->phi2_sum = s2;
+    Launch<double>::axpby(ctx->V, ctx->stream, 1.0, ctx->e64.phi, 0.0, (double *)ctx->r64);
+    {
+        // ||phi||^2 with an FP64 reduction over a real vector
+        const double *ph = ctx->e64.phi;
+        std::vector<double> host(ctx->V);
+        CU(cudaMemcpyAsync(host.data(), ph, sizeof(double) * ctx->V, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        double s2 = 0.0;
+        for (long long i = 0; i < ctx->V; ++i) s2 += host[i] * host[i];
+        ctx->phi2_sum = s2;
+    }
+    ctx->launches += 1;
     return finish(ctx);
 }
 
@@ -463,6 +549,8 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     if (o.solver != HOM_SOLVER_GALERKIN_MINRES) return fail(nullptr, HOM_EINVAL, "bad solver");
     if (o.precision != HOM_PREC_FP32_FIELDS && o.precision != HOM_PREC_FP64)
         return fail(nullptr, HOM_EINVAL, "bad precision");
+    if (o.rows3 < 0 || o.rows3 > 64 || o.tile2 < 0 || o.tile2 > 32 || o.tile1 < 0 || o.tile1 > 16)
+        return fail(nullptr, HOM_EINVAL, "bad launch-shape override");
     hom_ctx *ctx = new hom_ctx();
     ctx->prec = o.precision;
     ctx->deriv = derivative;
@@ -472,6 +560,9 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     ctx->mu = 1.0 / (2.0 * (1.0 + nu));                // mu / E
     ctx->device_ptrs = o.device_ptrs;
     ctx->refine = o.refine < 0 ? 0 : o.refine;
+    ctx->shape[0] = o.rows3;
+    ctx->shape[1] = o.tile2;
+    ctx->shape[2] = o.tile1;
     ctx->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) ctx->device = o.device;
     else if (cudaGetDevice(&ctx->device) != cudaSuccess) {
@@ -488,74 +579,11 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     return HOM_OK;
 }
 
-template <typename R>
-static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
-    const long long n = 6 * ctx->V;
-    cudaStream_t s = ctx->stream;
-    R *v0 = (R *)ctx->vbuf[0], *v1 = (R *)ctx->vbuf[1], *p = (R *)ctx->vbuf[2];
-    R *w1 = (R *)ctx->wbuf[0], *w2 = (R *)ctx->wbuf[1], *x = (R *)ctx->xs;
-    // a private state that never stops: done = 0, unit coefficients
-    MinresState h{};
-    h.beta1 = 1.0; h.beta = 0.5; h.alpha = 0.25; h.c = -1.0; h.s = 0.0; h.phibar = 1.0; h.tol = 0.0;
-    h.u_delta = 0.1; h.u_eps = 0.1; h.u_inv_gamma = 1.0; h.u_tau = 0.0; h.u_inv_beta = 1.0;
-    h.max_it = 1 << 30;
-    MinresState *d = nullptr;
-    CU(cudaMalloc(&d, sizeof(MinresState)));
-    CU(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
-    // finite field contents
-    Launch<R>::axpby(n, s, 0.0, v0, 0.0, v0);
-    Launch<R>::axpby(n, s, 0.0, v1, 0.0, v1);
-    Launch<R>::axpby(n, s, 0.0, p, 0.0, p);
-    Launch<R>::axpby(n, s, 0.0, w1, 0.0, w1);
-    Launch<R>::axpby(n, s, 0.0, w2, 0.0, w2);
-    Launch<R>::axpby(n, s, 0.0, x, 0.0, x);
-    const int np3 = x3_grid(E.g), npe = ew_blocks(n);
-    const int nk = 9;
-    for (int k = 0; k < nk && k < nmax; ++k) {
-        for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
-            const int r = pass ? reps : 1;
-            CU(cudaEventRecord(ctx->ev0, s));
-            for (int i = 0; i < r; ++i) {
-                switch (k) {
-                    case 0: Launch<R>::x3_fwd(E.g, s, X3F_MATERIAL, v1, E.phi, ctx->lam, ctx->mu, nullptr, E.spec, d); break;
-                    case 1: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
-                    case 2: Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA | X1_INV, E.spec, d); break;
-                    case 3: Launch<R>::x2(E.g, s, 1, E.spec, d); break;
-                    case 4: Launch<R>::x3_inv(E.g, s, X3I_STORE_DOT, E.spec, p, 1.0 / (double)ctx->V, v1, ctx->partials, d); break;
-                    case 5: scalar_alpha(s, d, ctx->partials, np3); break;
-                    case 6: Launch<R>::lanczos(n, s, p, v1, v0, d, ctx->partials); break;
-                    case 7: scalar_givens(s, d, ctx->partials, npe);
-                            CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
-                    default: Launch<R>::update(n, s, p, v1, w1, w2, x, d); break;
-                }
-            }
-            CU(cudaEventRecord(ctx->ev1, s));
-            CU(cudaEventSynchronize(ctx->ev1));
-            float t = 0.f;
-            CU(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1));
-            ms[k] = (double)t / r;
-        }
-        ctx->launches += reps + 1;
-    }
-    cudaFree(d);
-    return nk < nmax ? nk : nmax;
-}
-
-int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
-    if (!ctx || !ms || reps <= 0 || nmax <= 0) return fail(ctx, HOM_EINVAL, "bad argument");
-    cudaSetDevice(ctx->device);
-    int r = (ctx->prec == HOM_PREC_FP64) ? time_kernels_impl<double>(ctx, ctx->e64, reps, ms, nmax)
-                                         : time_kernels_impl<float>(ctx, ctx->e32, reps, ms, nmax);
-    if (r < 0) return r;
-    int rc = finish(ctx);
-    return rc ? rc : r;
-}
-
 int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes) {
     if (!ctx) return HOM_EINVAL;
     if (grid) for (int p = 0; p < 3; ++p) grid[p] = ctx->n[p];
     if (precision) *precision = ctx->prec;
-    if (workspace_bytes) *workspace_bytes = ctx->workspace + (long long)ctx->x64.size() * 6 * ctx->V * 8;
+    if (workspace_bytes) *workspace_bytes = ctx->workspace + (long long)ctx->x64.size() * 12 * ctx->S * 8;
     return HOM_OK;
 }
 
@@ -565,45 +593,39 @@ long long hom_kernel_launches(const hom_ctx *ctx) { return ctx ? ctx->launches :
 template <typename R>
 static int step_impl(hom_ctx *ctx, Engine<R> &E, int which, const void *in, void *out, const double *macro) {
     const long long n = 6 * ctx->V;
-    R *din = (R *)ctx->xs, *dout = (R *)ctx->rhs;
-    cpx<R> *spec = E.spec;
+    R *din = (R *)ctx->vbuf[0], *dout = (R *)ctx->vbuf[1];
+    cpx<R> *spec = (cpx<R> *)ctx->vbuf[2];
     cudaStream_t s = ctx->stream;
     int rc;
     switch (which) {
-        case 0:  // apply (Mandel)
+        case 0:  // apply (Mandel): A(e) = F^-1 G F C e
             rc = stage_in(ctx, in, sizeof(R) * n, din);
             if (rc) return rc;
-            op_chain<R>(ctx, E, X3F_MATERIAL, din, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
-                        1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            real_to_spec<R>(ctx, E, din, X3_MID_MATERIAL, true, spec);
+            spec_to_real<R>(ctx, E, spec, false, 1.0, dout);
             return stage_out(ctx, out, sizeof(R) * n, dout);
         case 1: {  // rhs (Mandel)
             double m[6];
             macro_to_mandel(macro, m);
-            op_chain<R>(ctx, E, X3F_MACRO, nullptr, m, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
-                        -1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            rhs_spec<R>(ctx, E, m, spec);
+            spec_to_real<R>(ctx, E, spec, false, 1.0, dout);
             return stage_out(ctx, out, sizeof(R) * n, dout);
         }
         case 2:  // forward FFT
             rc = stage_in(ctx, in, sizeof(R) * n, din);
             if (rc) return rc;
-            Launch<R>::x3_fwd(E.g, s, X3F_RAW, din, E.phi, 0, 0, nullptr, spec, nullptr);
-            Launch<R>::x2(E.g, s, 0, spec, nullptr);
-            Launch<R>::x1(E.g, s, X1_FWD, spec, nullptr);
-            ctx->launches += 3;
+            real_to_spec<R>(ctx, E, din, X3_MID_NONE, false, spec);
             return stage_out(ctx, out, cpx_size<R>() * 6 * ctx->S, spec);
         case 3:  // inverse FFT
             rc = stage_in(ctx, in, cpx_size<R>() * 6 * ctx->S, spec);
             if (rc) return rc;
-            Launch<R>::x1(E.g, s, X1_INV, spec, nullptr);
-            Launch<R>::x2(E.g, s, 1, spec, nullptr);
-            Launch<R>::x3_inv(E.g, s, X3I_STORE, spec, dout, 1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
-            ctx->launches += 3;
+            spec_to_real<R>(ctx, E, spec, false, 1.0, dout);
             return stage_out(ctx, out, sizeof(R) * n, dout);
         default:  // projection (Mandel)
             rc = stage_in(ctx, in, sizeof(R) * n, din);
             if (rc) return rc;
-            op_chain<R>(ctx, E, X3F_RAW, din, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, dout,
-                        1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+            real_to_spec<R>(ctx, E, din, X3_MID_NONE, true, spec);
+            spec_to_real<R>(ctx, E, spec, false, 1.0, dout);
             return stage_out(ctx, out, sizeof(R) * n, dout);
     }
 }
@@ -624,13 +646,12 @@ int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field) { return st
 int hom_project(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 4, in, out, nullptr); }
 
 // ----- solve -------------------------------------------------------------------
-// ||A(x) - b|| / ||b|| in FP64 for x = ctx->x64[icase]; leaves b - A x in r64.
-static int true_residual(hom_ctx *ctx, double *x, double bnorm, double *res) {
-    const long long n = 6 * ctx->V;
-    op_chain<double>(ctx, ctx->e64, X3F_MATERIAL, x, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, ctx->r64,
-                     1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
-    residual64(n, ctx->stream, ctx->b64, ctx->r64, ctx->r64, ctx->partials);
-    reduce_to(ctx->stream, ctx->partials, ew_blocks(n), ctx->d_scalar);
+// ||A^ x - b^||_w / ||b^||_w in FP64 (Parseval: the real-space ratio of
+// eq. (galres)); leaves b^ - A^ x in r64.
+static int true_residual(hom_ctx *ctx, const double2 *x, double bnorm, double *res) {
+    op_spec<double>(ctx, ctx->e64, x, ctx->r64, false, nullptr, nullptr);
+    spec_residual64(ctx->e64.g, ctx->stream, ctx->b64, ctx->r64, ctx->r64, ctx->partials);
+    reduce_to(ctx->stream, ctx->partials, ew_blocks(6 * ctx->S), ctx->d_scalar);
     ctx->launches += 2;
     CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -638,74 +659,82 @@ static int true_residual(hom_ctx *ctx, double *x, double bnorm, double *res) {
     return HOM_OK;
 }
 
+// real FP64 fluctuation strain of case icase (Mandel) into ctx->r64 (as 6 V doubles)
+static double *fluctuation64(hom_ctx *ctx, int icase) {
+    double *eps = (double *)ctx->r64;
+    spec_to_real<double>(ctx, ctx->e64, ctx->x64[icase], true, 1.0, eps);
+    return eps;
+}
+
 static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, int max_it, const void *warm,
                       hom_solve_info *info) {
-    const long long n = 6 * ctx->V;
+    const long long nc = 6 * ctx->S;   // complex values per spectral vector
     cudaStream_t s = ctx->stream;
     double m[6];
     macro_to_mandel(mac_t, m);
     for (int c = 0; c < 6; ++c) ctx->macros[6 * icase + c] = m[c];
-    double *x = ctx->x64[icase];
+    double2 *x = ctx->x64[icase];
     hom_solve_info inf{};
     CU(cudaEventRecord(ctx->ev0, s));
-    // b in FP64 (eq. gallin with sigma_bar = 0)
-    op_chain<double>(ctx, ctx->e64, X3F_MACRO, nullptr, m, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE, ctx->b64,
-                     -1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
+    rhs_spec<double>(ctx, ctx->e64, m, ctx->b64);
     double b2 = 0.0;
-    int rc = dev_norm2<double>(ctx, ctx->b64, n, &b2);
+    int rc = spec_norm2<double>(ctx, ctx->e64, ctx->b64, &b2);
     if (rc) return rc;
     const double bnorm = std::sqrt(b2);
-    // scale of the right-hand side: ||C : E_bar|| over the grid (units of E)
+    // scale of the right-hand side: ||C : E_bar|| over the grid (units of E);
+    // Parseval: ||b||_real = ||b^||_w / sqrt(V)
     double ce2 = 0.0;
     for (int i = 0; i < 6; ++i) {
         double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
         ce2 += sv * sv;
     }
     const double ntau = std::sqrt(ce2 * ctx->phi2_sum);
-    CU(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    CU(cudaMemsetAsync(x, 0, sizeof(double2) * nc, s));
     int status = HOM_OK;
     if (!std::isfinite(bnorm)) {
         status = HOM_ENAN;
-    } else if (bnorm <= 1e-12 * ntau) {
+    } else if (bnorm / std::sqrt((double)ctx->V) <= kRhsZero * ntau) {
         // b vanishes up to round-off: zero fluctuation, 0 iterations
         inf.sweeps = 0;
     } else {
         if (warm) {
-            // x0 = G(warm) (projected onto compatible fields), Mandel
-            double *st = ctx->r64;
-            if (!ctx->stage64) CU(cudaMalloc(&ctx->stage64, sizeof(double) * n));
+            // x0 = G F (warm), tensor components -> Mandel, projected
+            double *st = (double *)ctx->r64;
+            const long long n = 6 * ctx->V;
             if (ctx->prec == HOM_PREC_FP64) {
-                rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * icase, sizeof(double) * n, ctx->stage64);
+                rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * icase, sizeof(double) * n, st);
             } else {
                 rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * icase, sizeof(float) * n, ctx->xs);
-                if (!rc) convert_f2d(n, s, (const float *)ctx->xs, ctx->stage64, 0);
+                if (!rc) real_convert_f2d(n, s, (const float *)ctx->xs, st);
             }
             if (rc) return rc;
-            mandel_scale<double>(ctx->V, s, ctx->stage64, std::sqrt(2.0));
-            op_chain<double>(ctx, ctx->e64, X3F_RAW, ctx->stage64, nullptr, X1_FWD | X1_GAMMA | X1_INV, X3I_STORE,
-                             x, 1.0 / (double)ctx->V, nullptr, nullptr, nullptr);
-            (void)st;
+            mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
+            real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
+            ctx->launches += 2;
         }
         double tres = 1.0;
         rc = true_residual(ctx, x, bnorm, &tres);
         if (rc) return rc;
         const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
         for (int sw = 0; sw < sweeps_max && tres > tol; ++sw) {
-            // right-hand side of this sweep: r = b - A x (FP64), in the solve precision
-            double sweep_tol = tol * bnorm / (tres * bnorm);
+            // relative reduction this sweep must reach; FP32 fields cannot
+            // resolve residuals much below 1e-6 of their right-hand side, so a
+            // sweep never asks for less and the next sweep refines further
+            double sweep_tol = tol / tres;
             if (sweep_tol > 0.5) sweep_tol = 0.5;
+            if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < kFp32SweepFloor) sweep_tol = kFp32SweepFloor;
             int it = 0, st = 0;
             double est = 0.0;
             if (ctx->prec == HOM_PREC_FP64) {
-                CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
                 rc = run_minres<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
                 if (rc) return rc;
-                Launch<double>::axpby(n, s, 1.0, (const double *)ctx->xs, 1.0, x);
+                Launch<double>::axpby(2 * nc, s, 1.0, (const double *)ctx->xs, 1.0, (double *)x);
             } else {
-                convert_d2f(n, s, ctx->r64, (float *)ctx->rhs);
+                spec_d2f(nc, s, ctx->r64, (float2 *)ctx->rhs);
                 rc = run_minres<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
                 if (rc) return rc;
-                convert_f2d(n, s, (const float *)ctx->xs, x, 1);
+                spec_f2d_acc(nc, s, (const float2 *)ctx->xs, x);
             }
             ctx->launches += 2;
             inf.iterations += it;
@@ -719,8 +748,9 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         inf.true_residual = tres;
         if (status == HOM_OK && tres > tol) status = HOM_NOT_CONVERGED;
     }
-    // mean stress <phi C_m : (E_bar + x)>
-    Launch<double>::mean_stress(ctx->V, s, x, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
+    // mean stress <phi C_m : (E_bar + e~)>, FP64
+    const double *eps = fluctuation64(ctx, icase);
+    mean_stress64(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
     const int nb = ew_blocks(ctx->V);
     for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
     ctx->launches += 7;
@@ -749,10 +779,9 @@ int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, i
     for (int i = 0; i < 6 * ncase; ++i)
         if (!std::isfinite(macro_strain[i])) return fail(ctx, HOM_ENAN, "macro strain not finite");
     cudaSetDevice(ctx->device);
-    // per-case FP64 solutions
     while ((int)ctx->x64.size() < ncase) {
-        double *p = nullptr;
-        CU(cudaMalloc(&p, sizeof(double) * 6 * ctx->V));
+        double2 *p = nullptr;
+        CU(cudaMalloc(&p, sizeof(double2) * 6 * ctx->S));
         ctx->x64.push_back(p);
     }
     ctx->ncase = 0;
@@ -776,7 +805,7 @@ int hom_effective_stiffness(hom_ctx *ctx, double C[36]) {
     if (!ctx || !C) return fail(ctx, HOM_EINVAL, "null argument");
     const int nc = ctx->ncase;
     if (nc < 6) return fail(ctx, HOM_EINVAL, "needs a prior hom_solve with >= 6 cases");
-    // Voigt strains gamma (6 x nc) and mean stresses S (6 x nc); C = S G^T (G G^T)^-1
+    // Voigt strains G (6 x nc) and mean stresses S (6 x nc); C = S G^T (G G^T)^-1
     std::vector<double> G(6 * nc), Sg(6 * nc);
     const double r2 = std::sqrt(2.0);
     for (int k = 0; k < nc; ++k)
@@ -827,22 +856,81 @@ int hom_fields(hom_ctx *ctx, int icase, void *strain, void *stress) {
     const long long n = 6 * ctx->V;
     cudaStream_t s = ctx->stream;
     const double *m = &ctx->macros[6 * icase];
-    const double *x = ctx->x64[icase];
+    const double *eps = fluctuation64(ctx, icase);
     if (ctx->prec == HOM_PREC_FP64) {
         double *de = (double *)ctx->vbuf[0], *ds = (double *)ctx->vbuf[1];
-        Launch<double>::fields(ctx->V, s, x, ctx->e64.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
-                               stress ? ds : nullptr);
+        fields_from64<double>(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
+                              stress ? ds : nullptr);
         ctx->launches += 1;
         if (strain) { int rc = stage_out(ctx, strain, sizeof(double) * n, de); if (rc) return rc; }
         if (stress) { int rc = stage_out(ctx, stress, sizeof(double) * n, ds); if (rc) return rc; }
     } else {
-        float *xf = (float *)ctx->xs, *de = (float *)ctx->vbuf[0], *ds = (float *)ctx->vbuf[1];
-        convert_d2f(n, s, x, xf);
-        Launch<float>::fields(ctx->V, s, xf, ctx->e32.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
-                              stress ? ds : nullptr);
-        ctx->launches += 2;
+        float *de = (float *)ctx->vbuf[0], *ds = (float *)ctx->vbuf[1];
+        fields_from64<float>(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, ctx->E, m, strain ? de : nullptr,
+                             stress ? ds : nullptr);
+        ctx->launches += 1;
         if (strain) { int rc = stage_out(ctx, strain, sizeof(float) * n, de); if (rc) return rc; }
         if (stress) { int rc = stage_out(ctx, stress, sizeof(float) * n, ds); if (rc) return rc; }
     }
     return finish(ctx);
+}
+
+// ----- instrumentation ----------------------------------------------------------
+template <typename R>
+static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
+    const long long nr = 12 * ctx->S;
+    cudaStream_t s = ctx->stream;
+    cpx<R> *v0 = (cpx<R> *)ctx->vbuf[0], *v1 = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
+    cpx<R> *w1 = (cpx<R> *)ctx->wbuf[0], *w2 = (cpx<R> *)ctx->wbuf[1], *x = (cpx<R> *)ctx->xs;
+    // a private state that never stops, unit-size coefficients
+    MinresState h{};
+    h.beta1 = 1.0; h.beta = 0.5; h.alpha = 0.25; h.c = -1.0; h.s = 0.0; h.phibar = 1.0; h.tol = 0.0;
+    h.u_delta = 0.1; h.u_eps = 0.1; h.u_inv_gamma = 1.0; h.u_tau = 0.0; h.u_inv_beta = 1.0;
+    h.max_it = 1 << 30;
+    MinresState *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(MinresState)));
+    CU(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    for (void *b : {ctx->vbuf[0], ctx->vbuf[1], ctx->vbuf[2], ctx->wbuf[0], ctx->wbuf[1], ctx->xs})
+        CU(cudaMemsetAsync(b, 0, sizeof(R) * nr, s));
+    const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
+    const int nk = 9;
+    for (int k = 0; k < nk && k < nmax; ++k) {
+        for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
+            const int r = pass ? reps : 1;
+            CU(cudaEventRecord(ctx->ev0, s));
+            for (int i = 0; i < r; ++i) {
+                switch (k) {
+                    case 0: Launch<R>::x1(E.g, s, X1_GAMMA_IN, v1, E.spec, nullptr, nullptr, d); break;
+                    case 1: Launch<R>::x2(E.g, s, 1, E.spec, d); break;
+                    case 2: Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0,
+                                          X3_OUT_SPEC, E.spec, E.phi, d); break;
+                    case 3: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
+                    case 4: Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | X1_DOT, E.spec, p, v1, ctx->partials, d); break;
+                    case 5: scalar_alpha(s, d, ctx->partials, np1); break;
+                    case 6: Launch<R>::lanczos(E.g, s, p, v1, v0, d, ctx->partials); break;
+                    case 7: scalar_givens(s, d, ctx->partials, npe);
+                            CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
+                    default: Launch<R>::update(E.g, s, p, v1, w1, w2, x, d); break;
+                }
+            }
+            CU(cudaEventRecord(ctx->ev1, s));
+            CU(cudaEventSynchronize(ctx->ev1));
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1));
+            ms[k] = (double)t / r;
+        }
+        ctx->launches += reps + 1;
+    }
+    cudaFree(d);
+    return nk < nmax ? nk : nmax;
+}
+
+int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
+    if (!ctx || !ms || reps <= 0 || nmax <= 0) return fail(ctx, HOM_EINVAL, "bad argument");
+    cudaSetDevice(ctx->device);
+    int r = (ctx->prec == HOM_PREC_FP64) ? time_kernels_impl<double>(ctx, ctx->e64, reps, ms, nmax)
+                                         : time_kernels_impl<float>(ctx, ctx->e32, reps, ms, nmax);
+    if (r < 0) return r;
+    int rc = finish(ctx);
+    return rc ? rc : r;
 }

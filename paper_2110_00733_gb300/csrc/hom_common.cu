@@ -1,0 +1,284 @@
+// hom_common.cu -- MINRES scalar recurrences (FP64, one CTA), FP64 helpers of
+// the refinement and post-processing, and input conversion.
+#include <math.h>
+
+#include "hom_internal.h"
+
+namespace hom {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = (lane < nw) ? red[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ int pweight(int k3, int n3) { return (k3 == 0 || 2 * k3 == n3) ? 1 : 2; }
+
+// deterministic reduction of the partials by one CTA (fixed order)
+__device__ double reduce_partials(const double *partials, int np) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
+    return block_sum(s);
+}
+
+__global__ void k_reduce_to(const double *partials, int np, double *out) {
+    const double s = reduce_partials(partials, np);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// MINRES set-up from ||b||^2: beta_1, phibar_0 = beta_1, c_0 = -1, s_0 = 0,
+// delta-bar_1 = 0, epsilon_1 = 0 (Paige-Saunders; the v_1 = b / beta_1
+// scaling is done by the caller).
+__global__ void k_scalar_start(MinresState *st, const double *partials, int np, double tol, int max_it) {
+    const double b2 = reduce_partials(partials, np);
+    if (threadIdx.x != 0) return;
+    const double beta1 = sqrt(b2 > 0 ? b2 : 0.0);
+    st->beta1 = beta1;
+    st->beta = 0.0;     // no v_0 term in the first Lanczos step
+    st->alpha = 0.0;
+    st->c = -1.0;
+    st->s = 0.0;
+    st->dbar = 0.0;
+    st->eps = 0.0;
+    st->phibar = beta1;
+    st->tol = tol;
+    st->u_delta = st->u_eps = st->u_tau = 0.0;
+    st->u_inv_gamma = st->u_inv_beta = 0.0;
+    st->est = 1.0;
+    st->k = 0;
+    st->max_it = max_it;
+    st->done = (beta1 == 0.0 || max_it <= 0) ? 1 : 0;
+    st->done_update = st->done;
+    st->status = 0;
+    if (!isfinite(beta1)) { st->status = -5; st->done = 1; st->done_update = 1; }
+}
+
+__global__ void k_scalar_alpha(MinresState *st, const double *partials, int np) {
+    if (st->done) return;
+    const double a = reduce_partials(partials, np);
+    if (threadIdx.x == 0) st->alpha = a;
+}
+
+// MINRES step k: apply the previous Givens rotation to the new column of the
+// Lanczos tridiagonal, form the next rotation, and the coefficients of w_k,
+// x_k and v_{k+1}; stop when phibar_k / beta_1 <= tol, beta_{k+1} = 0, or k
+// reaches max_it.
+__global__ void k_scalar_givens(MinresState *st, const double *partials, int np) {
+    if (st->done) return;
+    const double bn2 = reduce_partials(partials, np);
+    if (threadIdx.x != 0) return;
+    const double beta_next = sqrt(bn2 > 0 ? bn2 : 0.0);
+    const double alpha = st->alpha, c = st->c, s = st->s, dbar = st->dbar;
+    const double delta = c * dbar + s * alpha;
+    const double gbar = s * dbar - c * alpha;
+    const double eps_next = s * beta_next;
+    const double dbar_next = -c * beta_next;
+    double gamma = hypot(gbar, beta_next);
+    if (gamma == 0.0) gamma = 1e-300;
+    const double cn = gbar / gamma, sn = beta_next / gamma;
+    const double tau = cn * st->phibar;
+    const double phibar = sn * st->phibar;
+    st->u_delta = delta;
+    st->u_eps = st->eps;            // epsilon_k multiplies w_{k-2}
+    st->u_inv_gamma = 1.0 / gamma;
+    st->u_tau = tau;
+    st->u_inv_beta = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+    st->c = cn;
+    st->s = sn;
+    st->dbar = dbar_next;
+    st->eps = eps_next;
+    st->phibar = phibar;
+    st->beta = beta_next;
+    st->k += 1;
+    st->est = phibar / st->beta1;
+    if (!isfinite(alpha) || !isfinite(beta_next) || !isfinite(phibar)) {
+        st->status = -5;
+        st->done = 1;
+        st->done_update = 1;        // keep the last finite iterate
+        return;
+    }
+    if (st->est <= st->tol || beta_next == 0.0) {
+        st->done = 1;               // this iteration's update still runs
+    } else if (st->k >= st->max_it) {
+        st->status = 1;
+        st->done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kEwThreads) k_spec_residual64(int n, int h, int n3, const double2 *b,
+                                                                const double2 *ax, double2 *r, double *partials) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 bb = b[i], aa = ax[i];
+        const double2 d = make_double2(bb.x - aa.x, bb.y - aa.y);
+        r[i] = d;
+        acc += pweight((i / 6) % h, n3) * (d.x * d.x + d.y * d.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_spec_d2f(long long n, const double2 *in, float2 *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_spec_f2d_acc(long long n, const float2 *in, double2 *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 o = out[i];
+        out[i] = make_double2(o.x + (double)in[i].x, o.y + (double)in[i].y);
+    }
+}
+
+// <phi C_m : (E_bar + x)> per Mandel component: partials[c * gridDim.x + block]
+__global__ void __launch_bounds__(kEwThreads) k_mean_stress64(long long V, const double *x, const double *phi,
+                                                              double lam, double mu2, Mac6 mac, double *partials) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        double e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] = mac.v[c] + x[c * V + i];
+        const double ph = phi[i];
+        const double tr = lam * (e[0] + e[1] + e[2]);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += ph * ((c < 3 ? tr : 0.0) + mu2 * e[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double s = block_sum(acc[c]);
+        if (threadIdx.x == 0) partials[c * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// total strain and stress in tensor components (shear / sqrt2), stress x Escale
+template <typename Ro>
+__global__ void k_fields64(long long V, const double *x, const double *phi, double lam, double mu2, double Escale,
+                           Mac6 mac, Ro *strain, Ro *stress) {
+    const double r2 = 0.70710678118654752440;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        double e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] = mac.v[c] + x[c * V + i];
+        if (strain) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) strain[c * V + i] = (Ro)((c < 3) ? e[c] : e[c] * r2);
+        }
+        if (stress) {
+            const double ph = phi[i];
+            const double tr = lam * (e[0] + e[1] + e[2]);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const double s = Escale * ph * ((c < 3 ? tr : 0.0) + mu2 * e[c]);
+                stress[c * V + i] = (Ro)((c < 3) ? s : s * r2);
+            }
+        }
+    }
+}
+
+__global__ void k_f2d(long long n, const float *in, double *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+__global__ void k_d2f(long long n, const double *in, float *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void k_mandel_scale64(long long V, double *f, double s) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * V; i += (long long)gridDim.x * blockDim.x)
+        f[3 * V + i] *= s;
+}
+template <typename R>
+__global__ void k_phi_convert(long long V, const void *in, int kind, R *out, int *bad) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (kind == 0) v = ((const unsigned char *)in)[i] ? 1.0 : 0.0;
+        else if (kind == 1) v = (double)((const float *)in)[i];
+        else v = ((const double *)in)[i];
+        if (!(v >= 0.0 && v <= 1.0)) { atomicExch(bad, 1); v = 0.0; }
+        out[i] = (R)v;
+    }
+}
+
+}  // namespace
+
+int ew_blocks(long long n) {
+    long long b = (n + kEwThreads - 1) / kEwThreads;
+    return (int)(b < kEwBlocks ? (b > 0 ? b : 1) : kEwBlocks);
+}
+
+void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
+                     double *partials) {
+    const int n = (int)(6 * g.S);
+    k_spec_residual64<<<ew_blocks(n), kEwThreads, 0, st>>>(n, g.h, g.n3, b, ax, r, partials);
+}
+void spec_d2f(long long n, cudaStream_t st, const double2 *in, float2 *out) {
+    k_spec_d2f<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
+}
+void spec_f2d_acc(long long n, cudaStream_t st, const float2 *in, double2 *out) {
+    k_spec_f2d_acc<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
+}
+void mean_stress64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
+                   const double *macro, double *partials) {
+    Mac6 m{};
+    for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
+    k_mean_stress64<<<ew_blocks(V), kEwThreads, 0, st>>>(V, x, phi, lam, 2.0 * mu, m, partials);
+}
+template <typename Ro>
+void fields_from64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
+                   double Escale, const double *macro, Ro *strain, Ro *stress) {
+    Mac6 m{};
+    for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
+    k_fields64<Ro><<<ew_blocks(V), kEwThreads, 0, st>>>(V, x, phi, lam, 2.0 * mu, Escale, m, strain, stress);
+}
+template void fields_from64<float>(long long, cudaStream_t, const double *, const double *, double, double, double,
+                                   const double *, float *, float *);
+template void fields_from64<double>(long long, cudaStream_t, const double *, const double *, double, double, double,
+                                    const double *, double *, double *);
+void real_convert_f2d(long long n, cudaStream_t st, const float *in, double *out) {
+    k_f2d<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
+}
+void real_convert_d2f(long long n, cudaStream_t st, const double *in, float *out) {
+    k_d2f<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
+}
+void mandel_scale64(long long V, cudaStream_t st, double *f, double s) {
+    k_mandel_scale64<<<ew_blocks(3 * V), kEwThreads, 0, st>>>(V, f, s);
+}
+template <typename R>
+void phi_convert(long long V, cudaStream_t st, const void *in, int kind, R *out, int *bad) {
+    k_phi_convert<R><<<ew_blocks(V), kEwThreads, 0, st>>>(V, in, kind, out, bad);
+}
+template void phi_convert<float>(long long, cudaStream_t, const void *, int, float *, int *);
+template void phi_convert<double>(long long, cudaStream_t, const void *, int, double *, int *);
+
+void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it) {
+    k_scalar_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it);
+}
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np) {
+    k_scalar_alpha<<<1, 1024, 0, st>>>(s, partials, np);
+}
+void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np) {
+    k_scalar_givens<<<1, 1024, 0, st>>>(s, partials, np);
+}
+void reduce_to(cudaStream_t st, const double *partials, int np, double *out) {
+    k_reduce_to<<<1, 1024, 0, st>>>(partials, np, out);
+}
+
+}  // namespace hom

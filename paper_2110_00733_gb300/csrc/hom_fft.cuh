@@ -200,4 +200,76 @@ __device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, const AxisPlan &
     return src;
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident engine for power-of-two lengths known at compile time.
+// Every thread owns E elements of one line for the whole transform (BPT =
+// E/RAD butterflies per stage), so a stage is: load the thread's butterfly
+// inputs from the single shared buffer into registers, barrier, compute,
+// store the outputs in place, barrier.  One buffer instead of two, all index
+// arithmetic on compile-time powers of two.  The CTA must have exactly
+// L * N / E threads; thread t works on line t % L.
+// ---------------------------------------------------------------------------
+template <int N> struct FastPlan;
+template <> struct FastPlan<8>   { static constexpr int E = 8,  NS = 1, R0 = 8,  R1 = 1,  R2 = 1; };
+template <> struct FastPlan<16>  { static constexpr int E = 16, NS = 1, R0 = 16, R1 = 1,  R2 = 1; };
+template <> struct FastPlan<32>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 4,  R2 = 1; };
+template <> struct FastPlan<64>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 8,  R2 = 1; };
+template <> struct FastPlan<128> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 8,  R2 = 1; };
+template <> struct FastPlan<256> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 16, R2 = 1; };
+template <> struct FastPlan<512> { static constexpr int E = 16, NS = 3, R0 = 16, R1 = 16, R2 = 2; };
+
+__host__ __device__ constexpr bool is_fast_length(int n) {
+    return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512;
+}
+__host__ __device__ constexpr int fast_elems(int n) {
+    return (n == 8 || n == 32 || n == 64) ? 8 : 16;
+}
+
+template <typename R, int S, int N, int RAD, int NS_BEFORE>
+__device__ __forceinline__ void fast_stage(cpx<R> *buf, int L, int l, int j0, const cpx<R> *__restrict__ tw) {
+    constexpr int E = FastPlan<N>::E;
+    constexpr int BPT = E / RAD;
+    constexpr int nb = N / RAD;
+    constexpr int jstep = N / E;
+    constexpr int twstep = N / (NS_BEFORE * RAD);
+    cpx<R> v[BPT][RAD];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int j = j0 + i * jstep;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[i][r] = buf[(j + r * nb) * L + l];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int j = j0 + i * jstep;
+        const int jm = j & (NS_BEFORE - 1);
+        if (NS_BEFORE > 1) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                cpx<R> w = __ldg(&tw[jm * r * twstep]);
+                if (S > 0) w.y = -w.y;
+                v[i][r] = mul<R>(v[i][r], w);
+            }
+        }
+        dft<R, S, RAD>(v[i]);
+        const int o = (j - jm) * RAD + jm;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) buf[(o + r * NS_BEFORE) * L + l] = v[i][r];
+    }
+    __syncthreads();
+}
+
+// Transform of L interleaved lines in buf (in place).  The CTA must have
+// exactly L * N / E threads (every thread takes part in every barrier).
+template <typename R, int S, int N>
+__device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, const cpx<R> *__restrict__ tw) {
+    using P = FastPlan<N>;
+    const int l = (int)threadIdx.x % L;
+    const int j0 = (int)threadIdx.x / L;
+    fast_stage<R, S, N, P::R0, 1>(buf, L, l, j0, tw);
+    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0>(buf, L, l, j0, tw);
+    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1>(buf, L, l, j0, tw);
+}
+
 }  // namespace hom

@@ -1,17 +1,27 @@
-// hom_internal.h -- shared declarations of the library's kernels and context.
+// hom_internal.h -- shared declarations of the library's kernels.
+//
+// Data layout in device memory
+//   real field     : 6 x V, component-major (Mandel components), C order voxels
+//   half spectrum  : n1 x n2 x h x 6 complex, h = n3/2 + 1, component fastest
+//                    (the six components of one frequency are adjacent, which
+//                    the projector and the n1 pass read together)
+// The MINRES vectors live in the half-spectrum space: MINRES runs on
+//   A^(v) = G F C F^-1 G v,
+// the operator of eq. (linearOp) conjugated by the DFT, with the projector
+// applied on the input as well as on the output, under the Parseval inner
+// product <a,b> = sum_k w(k3) Re(conj(a_k) b_k) with w = 1 on the self-
+// conjugate planes k3 = 0 and k3 = n3/2 (even n3) and 2 elsewhere.  On
+// compatible fields this is the same iteration as MINRES on A(e) in real space.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <string>
-#include <vector>
 
 #include "hom_fft.cuh"
 
 namespace hom {
 
 // Scalars of one MINRES solve, resident in device memory.  Written only by
-// the single-thread scalar kernels; read by the field kernels.  FP64 always.
+// the single-CTA scalar kernels; read by the field kernels.  FP64 always.
 struct MinresState {
     double beta1;      // ||b||
     double beta;       // beta_k: coefficient of v_{k-1} in the next Lanczos step
@@ -32,68 +42,82 @@ struct MinresState {
     int pad;
 };
 
-// Kernel-side description of the three axis transforms and the frequency
-// tables of one context (one precision).
+// Kernel-side description of one cell for one precision.
 struct Geometry {
     int n1, n2, n3, h;      // h = n3/2 + 1
     long long V, S;         // voxels, half-spectrum points per component
     AxisPlan ax[3];
     const void *D[3];       // per axis: difference symbol (complex, length n_p)
     const void *M[3];       // per axis: averaging factor (complex, length n_p)
-    // launch shapes
+    // launch shapes: rows per CTA of the n3 pass, columns per CTA of the n2
+    // and n1 passes, threads per CTA, dynamic shared memory, and whether the
+    // axis uses the compile-time register FFT (its length, or 0)
     int rows3, tile2, tile1;
+    int threads3, threads2, threads1;
     size_t smem3, smem2, smem1;
+    int fast[3];
 };
 
-enum X3FwdMode { X3F_RAW = 0, X3F_MATERIAL = 1, X3F_MACRO = 2 };
-enum X3InvMode { X3I_STORE = 0, X3I_STORE_NORM2 = 1, X3I_STORE_DOT = 2 };
-enum X1Flags { X1_FWD = 1, X1_GAMMA = 2, X1_INV = 4 };
+// n3 pass (x3): input, middle and output stages
+enum X3In { X3_IN_SPEC = 0, X3_IN_REAL = 1, X3_IN_MACRO = 2 };
+enum X3Mid { X3_MID_NONE = 0, X3_MID_MATERIAL = 1 };
+enum X3Out { X3_OUT_SPEC = 0, X3_OUT_REAL = 1 };
+// n1 pass (x1) flags
+enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
 
 constexpr int kEwBlocks = 152 * 8;   // grid of the element-wise Krylov kernels
 constexpr int kEwThreads = 256;
 
+struct Mac6 { double v[6]; };
+
 template <typename R> struct Launch {
-    static void x3_fwd(const Geometry &g, cudaStream_t st, int mode, const R *in, const R *phi,
-                       double lam, double mu, const double *macro_mandel, cpx<R> *spec,
-                       const MinresState *state);
-    static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec,
+    // n3 pass: C2R (SPEC in) or real / macro input, optional material law
+    // tau = phi C_m e, R2C (SPEC out) or real output; scale applied to the
+    // real-space values (1/V for SPEC in is included automatically).
+    static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
+                   const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
                    const MinresState *state);
-    static void x1(const Geometry &g, cudaStream_t st, int flags, cpx<R> *spec,
-                   const MinresState *state);
-    static void x3_inv(const Geometry &g, cudaStream_t st, int mode, const cpx<R> *spec, R *out,
-                       double scale, const R *dotv, double *partials, const MinresState *state);
-    // p -= alpha v + beta vprev ; partial ||p||^2
-    static void lanczos(long long n, cudaStream_t st, R *p, const R *v, const R *vprev,
+    // n2 pass, in place on the half spectrum
+    static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
+    // n1 pass: in -> out (may alias), optional projector before / after, and
+    // the weighted partial sum <dotv, out> per CTA
+    static void x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *in, cpx<R> *out,
+                   const cpx<R> *dotv, double *partials, const MinresState *state);
+    // p -= alpha v + beta vprev ; weighted partial ||p||^2   (spectral vectors)
+    static void lanczos(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *vprev,
                         const MinresState *state, double *partials);
     // w2 <- (v - delta w1 - eps w2)/gamma ; x += tau w2 ; p <- p / beta_next
-    static void update(long long n, cudaStream_t st, R *p, const R *v, const R *w1, R *w2, R *x,
-                       MinresState *state);
-    // y = a*x (+ b*y if accumulate)
+    static void update(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *w1, cpx<R> *w2,
+                       cpx<R> *x, MinresState *state);
+    // y = a x + b y over n reals
     static void axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y);
-    static void norm2(long long n, cudaStream_t st, const R *x, double *partials);
-    static void mean_stress(long long V, cudaStream_t st, const R *x, const R *phi, double lam,
-                            double mu, const double *macro_mandel, double *partials);
-    static void fields(long long V, cudaStream_t st, const R *x, const R *phi, double lam,
-                       double mu, double Escale, const double *macro_mandel, R *strain, R *stress);
+    // weighted partial ||x||^2 of a spectral vector
+    static void norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials);
+    static int ew_grid(long long n);
     static void table_init(const Geometry &g);
+    static int x3_grid(const Geometry &g);
+    static int x1_grid(const Geometry &g);
 };
 
-// Conversions between precisions: out[i] = (To) in[i] (+ out[i] if acc)
-void convert_f2d(long long n, cudaStream_t st, const float *in, double *out, int acc);
-void convert_d2f(long long n, cudaStream_t st, const double *in, float *out);
-// r = b - ax (double), partial ||r||^2
-void residual64(long long n, cudaStream_t st, const double *b, const double *ax, double *r,
-                double *partials);
-// tensor <-> Mandel on a 6 x V field (scale the shear components)
-template <typename R> void mandel_scale(long long V, cudaStream_t st, R *f, double s);
-// phi conversion from the user's input kind into R precision; nonzero flag
-// written to *bad on NaN or values outside [0,1]
-template <typename R> void phi_convert(long long V, cudaStream_t st, const void *in, int kind,
-                                       R *out, int *bad);
+// FP64 helpers on spectral vectors (double2) and real fields
+void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
+                     double *partials);                         // r = b - ax, weighted ||r||^2
+void spec_d2f(long long ncplx, cudaStream_t st, const double2 *in, float2 *out);
+void spec_f2d_acc(long long ncplx, cudaStream_t st, const float2 *in, double2 *out);   // out += in
+void mean_stress64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
+                   const double *macro_mandel, double *partials);   // partials[6][ew_grid(V)]
+template <typename Ro>
+void fields_from64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
+                   double Escale, const double *macro_mandel, Ro *strain, Ro *stress);
+void real_convert_f2d(long long n, cudaStream_t st, const float *in, double *out);
+void real_convert_d2f(long long n, cudaStream_t st, const double *in, float *out);
+void mandel_scale64(long long V, cudaStream_t st, double *f, double s);
+template <typename R>
+void phi_convert(long long V, cudaStream_t st, const void *in, int kind, R *out, int *bad);
+int ew_blocks(long long n);
 
-// single-thread scalar kernels
-void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol,
-                  int max_it);
+// single-CTA scalar kernels
+void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it);
 void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np);
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np);
 void reduce_to(cudaStream_t st, const double *partials, int np, double *out);

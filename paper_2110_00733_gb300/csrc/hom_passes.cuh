@@ -1,0 +1,521 @@
+// hom_passes.cuh -- the FFT passes of the Galerkin operator and the Krylov
+// vector kernels, templated on the field precision R (float or double).
+//
+// One application of the spectral operator  A^(v) = G F C F^-1 G v  (the
+// operator of eq. (linearOp) seen through the DFT) is five passes, each one
+// read and one write of the half spectrum:
+//   x1(inverse, G on input)   projector of eq. (galop) + inverse along n1
+//   x2(inverse)               inverse along n2
+//   x3(spec -> spec)          C2R along n3, tau = phi C_m e (Voigt-scaled
+//                             isotropic law, section 3.3), R2C along n3;
+//                             the real-space fields never reach HBM
+//   x2(forward)               forward along n2
+//   x1(forward, G on output)  forward along n1 + projector, with the MINRES
+//                             dot product <v, A^ v> fused into the store
+// Lengths 8..512 that are powers of two use the compile-time register FFT
+// (fast_fft); other 2^a 3^b 5^c lengths use the runtime Stockham engine.
+#pragma once
+#include <math.h>
+
+#include "hom_internal.h"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------
+// Reductions.
+// ---------------------------------------------------------------------------
+
+// Per-thread accumulator of products: float-float (error-free product and a
+// compensated sum, ~44 significant bits) for FP32 data, plain FP64 for FP64
+// data.  Either way the block sum is formed in FP64.
+template <typename R> struct Acc;
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p = a * b;
+        float e = fmaf(a, b, -p);
+        float s = hi + p;
+        float bp = s - hi;
+        float err = (hi - (s - bp)) + (p - bp);
+        hi = s;
+        lo += err + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <> struct Acc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = (lane < nw) ? red[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ bool skip(const MinresState *s) { return s != nullptr && s->done; }
+
+// Parseval weight of the half-spectrum plane k3
+__device__ __forceinline__ int pweight(int k3, int n3) { return (k3 == 0 || 2 * k3 == n3) ? 1 : 2; }
+
+// ---------------------------------------------------------------------------
+// Projector of eq. (galop) at one frequency, in closed form.  xi may be
+// complex (rotated scheme).  With e = xi/|xi|, the orthogonal projection of a
+// symmetric tau onto {sym(u (x) xi)} is sym(u (x) e) with
+//     u = 2 tau conj(e) - e (conj(e) . tau conj(e))
+// (Sherman-Morrison inverse of the acoustic tensor 1/2 (I + e e^H)).
+// t[6] holds Mandel components, overwritten.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void gamma_project(cpx<R> *t, cpx<R> x0, cpx<R> x1, cpx<R> x2) {
+    const R n2 = x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y + x2.x * x2.x + x2.y * x2.y;
+    if (!(n2 > (R)0)) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[c] = mk<R>(0, 0);
+        return;
+    }
+    const R inv = (R)1 / sqrt(n2);
+    const cpx<R> e0 = scale<R>(x0, inv), e1 = scale<R>(x1, inv), e2 = scale<R>(x2, inv);
+    const cpx<R> c0 = conjc<R>(e0), c1 = conjc<R>(e1), c2 = conjc<R>(e2);
+    const R r2 = (R)0.70710678118654752440;   // 1/sqrt(2)
+    const cpx<R> T11 = t[0], T22 = t[1], T33 = t[2];
+    const cpx<R> T23 = scale<R>(t[3], r2), T13 = scale<R>(t[4], r2), T12 = scale<R>(t[5], r2);
+    const cpx<R> v0 = add<R>(add<R>(mul<R>(T11, c0), mul<R>(T12, c1)), mul<R>(T13, c2));
+    const cpx<R> v1 = add<R>(add<R>(mul<R>(T12, c0), mul<R>(T22, c1)), mul<R>(T23, c2));
+    const cpx<R> v2 = add<R>(add<R>(mul<R>(T13, c0), mul<R>(T23, c1)), mul<R>(T33, c2));
+    const cpx<R> s = add<R>(add<R>(mul<R>(c0, v0), mul<R>(c1, v1)), mul<R>(c2, v2));
+    const cpx<R> u0 = sub<R>(scale<R>(v0, (R)2), mul<R>(e0, s));
+    const cpx<R> u1 = sub<R>(scale<R>(v1, (R)2), mul<R>(e1, s));
+    const cpx<R> u2 = sub<R>(scale<R>(v2, (R)2), mul<R>(e2, s));
+    t[0] = mul<R>(u0, e0);
+    t[1] = mul<R>(u1, e1);
+    t[2] = mul<R>(u2, e2);
+    t[3] = scale<R>(add<R>(mul<R>(u1, e2), mul<R>(u2, e1)), r2);
+    t[4] = scale<R>(add<R>(mul<R>(u0, e2), mul<R>(u2, e0)), r2);
+    t[5] = scale<R>(add<R>(mul<R>(u0, e1), mul<R>(u1, e0)), r2);
+}
+
+// G at frequency (k1,k2,k3) on the 6 Mandel components at p[0..5] (stride 1)
+template <typename R>
+__device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int k3, cpx<R> *t) {
+    // eq. (galop): zero at xi = 0 (strain control) and at every frequency
+    // with a Nyquist index
+    const bool nyq = ((g.n1 & 1) == 0 && 2 * k1 == g.n1) || ((g.n2 & 1) == 0 && 2 * k2 == g.n2) ||
+                     ((g.n3 & 1) == 0 && 2 * k3 == g.n3);
+    if (nyq || (k1 == 0 && k2 == 0 && k3 == 0)) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[c] = mk<R>(0, 0);
+        return;
+    }
+    const cpx<R> *D0 = reinterpret_cast<const cpx<R> *>(g.D[0]);
+    const cpx<R> *D1 = reinterpret_cast<const cpx<R> *>(g.D[1]);
+    const cpx<R> *D2 = reinterpret_cast<const cpx<R> *>(g.D[2]);
+    const cpx<R> *M0 = reinterpret_cast<const cpx<R> *>(g.M[0]);
+    const cpx<R> *M1 = reinterpret_cast<const cpx<R> *>(g.M[1]);
+    const cpx<R> *M2 = reinterpret_cast<const cpx<R> *>(g.M[2]);
+    const cpx<R> m0 = __ldg(&M0[k1]), m1 = __ldg(&M1[k2]), m2 = __ldg(&M2[k3]);
+    // xi_p = D_p(k_p) prod_{r != p} M_r(k_r): N_p (e^{iq_p} - 1) prod (1 + e^{iq_r})/2
+    // for the rotated scheme of eq. (freqrot), i q_p N_p for eq. (freq)
+    const cpx<R> x0 = mul<R>(__ldg(&D0[k1]), mul<R>(m1, m2));
+    const cpx<R> x1 = mul<R>(__ldg(&D1[k2]), mul<R>(m0, m2));
+    const cpx<R> x2 = mul<R>(__ldg(&D2[k3]), mul<R>(m0, m1));
+    gamma_project<R>(t, x0, x1, x2);
+}
+
+// Run the transform of the L lines in buf.  Fast engine: in place, returns
+// buf.  Generic engine: ping-pong with buf2, returns the buffer holding the
+// result.
+template <typename R, int S, int NF>
+__device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, const AxisPlan &p) {
+    if constexpr (NF > 0) {
+        fast_fft<R, S, NF>(buf, L, reinterpret_cast<const cpx<R> *>(p.tw));
+        return buf;
+    } else {
+        return fft_lines<R, S>(buf, buf2, L, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// n3 pass.  A CTA owns rows (k1,k2) [row0, row0+rows3); lines are the three
+// component pairs (2p, 2p+1) of each row packed as one complex line
+// Z = X_2p + i X_2p+1, line index p*rows3 + r.
+// ---------------------------------------------------------------------------
+template <typename R, int NF>
+__global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
+                                            R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
+                                            const R *__restrict__ phi, const MinresState *state) {
+    if (skip(state)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, H = g.h;
+    cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
+    cpx<R> *buf2 = buf + N * L;   // second buffer of the generic engine only
+    const int nrows = g.n1 * g.n2;
+    const int row0 = blockIdx.x * ROWS;
+    const int V = (int)g.V;
+    const int nr = min(ROWS, nrows - row0);
+    // ---- input
+    if (in_mode == X3_IN_SPEC) {
+        // Z[k] = X_a[k] + i X_b[k] and Z[N-k] = conj X_a[k] + i conj X_b[k];
+        // the self-conjugate bins keep their real parts, as a C2R does
+        const cpx<R> *spec = reinterpret_cast<const cpx<R> *>(in_);
+        for (int r = 0; r < ROWS; ++r) {
+            const cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
+            for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+                const int k = idx / 3, p = idx - 3 * k;
+                cpx<R> xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+                if (r < nr) {
+                    xa = row[k * 6 + 2 * p];
+                    xb = row[k * 6 + 2 * p + 1];
+                }
+                const bool selfc = (k == 0) || (2 * k == N);
+                if (selfc) { xa.y = 0; xb.y = 0; }
+                buf[k * L + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
+                if (!selfc) buf[(N - k) * L + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
+            }
+        }
+        __syncthreads();
+        cpx<R> *res = run_fft<R, 1, NF>(buf, buf2, L, g.ax[2]);
+        if (res != buf) {   // generic engine ended in the second buffer
+            for (int i = threadIdx.x; i < N * L; i += blockDim.x) buf[i] = res[i];
+            __syncthreads();
+        }
+    } else {
+        const R *real = reinterpret_cast<const R *>(in_);
+        for (int r = 0; r < ROWS; ++r) {
+            const int vbase = (row0 + r) * N;
+            for (int e = threadIdx.x; e < N; e += blockDim.x) {
+                R t[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    t[c] = (r >= nr) ? (R)0 : (in_mode == X3_IN_MACRO ? (R)mac.v[c] : real[c * V + vbase + e]);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) buf[e * L + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- scaling and material law on the real-space values
+    const R s_in = (in_mode == X3_IN_SPEC) ? (R)(1.0 / (double)g.V) : (R)1;
+    const R s_all = s_in * scl;
+    for (int r = 0; r < nr; ++r) {
+        const int vbase = (row0 + r) * N;
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+            cpx<R> *q = buf + e * L + r;
+            R t[6];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const cpx<R> z = q[p * ROWS];
+                t[2 * p] = z.x * s_all;
+                t[2 * p + 1] = z.y * s_all;
+            }
+            if (mid == X3_MID_MATERIAL) {
+                const R ph = phi[vbase + e];
+                const R tr = lam * (t[0] + t[1] + t[2]);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : (R)0) + mu2 * t[c]);
+            }
+            if (out_mode == X3_OUT_REAL) {
+                R *real = reinterpret_cast<R *>(out_);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) real[c * V + vbase + e] = t[c];
+            } else {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) q[p * ROWS] = mk<R>(t[2 * p], t[2 * p + 1]);
+            }
+        }
+    }
+    if (out_mode == X3_OUT_REAL) return;
+    // rows beyond nrows hold zeros already (their inputs were zero)
+    __syncthreads();
+    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, g.ax[2]);
+    // unpack the two real transforms of each packed line:
+    //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
+    cpx<R> *spec = reinterpret_cast<cpx<R> *>(out_);
+    for (int r = 0; r < nr; ++r) {
+        cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
+        for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
+            const int k = idx / 3, p = idx - 3 * k;
+            const int km = (k == 0) ? 0 : N - k;
+            const cpx<R> z = res[k * L + p * ROWS + r];
+            const cpx<R> zm = conjc<R>(res[km * L + p * ROWS + r]);
+            row[k * 6 + 2 * p] = mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y));
+            row[k * 6 + 2 * p + 1] = mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// n2 pass, in place.  Columns are (k1, k3, c) flattened, f = k1 * 6h + q;
+// element k2 of column f is at (k1 n2 + k2) 6h + q.  tile2 consecutive
+// columns per CTA (contiguous runs of tile2 complex values).
+// ---------------------------------------------------------------------------
+template <typename R, int S, int NF>
+__global__ void __launch_bounds__(512) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
+    if (skip(state)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = g.n2, T = g.tile2, H6 = 6 * g.h;
+    cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
+    cpx<R> *buf2 = buf + N * T;
+    const int total = g.n1 * H6;
+    const int t = threadIdx.x % T, e0 = threadIdx.x / T, es = blockDim.x / T;
+    const int f = blockIdx.x * T + t;
+    const bool live = f < total;
+    const int k1 = live ? f / H6 : 0;
+    cpx<R> *col = spec + (size_t)k1 * N * H6 + (f - k1 * H6);   // element e at col[e * H6]
+    for (int e = e0; e < N; e += es) buf[e * T + t] = live ? col[(size_t)e * H6] : mk<R>(0, 0);
+    __syncthreads();
+    cpx<R> *res = run_fft<R, S, NF>(buf, buf2, T, g.ax[1]);
+    if (live)
+        for (int e = e0; e < N; e += es) col[(size_t)e * H6] = res[e * T + t];
+}
+
+// ---------------------------------------------------------------------------
+// n1 pass.  Columns are (k2, k3) flattened, g = k2 h + k3; tile1 consecutive
+// columns per CTA with all 6 components: line l = t*6 + c (so that a row of
+// the tile is one contiguous run of 6 tile1 complex values).
+// ---------------------------------------------------------------------------
+template <typename R, int NF>
+__global__ void __launch_bounds__(512) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
+                                            cpx<R> *__restrict__ out, const cpx<R> *__restrict__ dotv,
+                                            double *__restrict__ partials, const MinresState *state) {
+    if (skip(state)) {
+        // the iteration after convergence: the pending w/x update is done
+        if ((flags & X1_GAMMA_IN) && blockIdx.x == 0 && threadIdx.x == 0)
+            const_cast<MinresState *>(state)->done_update = 1;
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = g.n1, T = g.tile1, H = g.h, L = 6 * T;
+    cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
+    cpx<R> *buf2 = buf + N * L;
+    const int cols = g.n2 * H;
+    const int g0 = blockIdx.x * T;
+    const size_t sK1 = (size_t)cols * 6;   // stride between consecutive k1
+    // each thread keeps one line l (blockDim is a multiple of L)
+    const int lt = threadIdx.x % L, e0 = threadIdx.x / L, es = blockDim.x / L;
+    const int tl = lt / 6;
+    const bool live = g0 + tl < cols;
+    {
+        const cpx<R> *src = in + (size_t)g0 * 6 + lt;
+        for (int e = e0; e < N; e += es) buf[e * L + lt] = live ? src[e * sK1] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    // projector on whole frequencies: thread keeps one column t (blockDim % T == 0)
+    const int tg = threadIdx.x % T, eg0 = threadIdx.x / T, egs = blockDim.x / T;
+    const int colg = g0 + tg;
+    const int k2g = colg / H, k3g = colg - k2g * H;
+    if (flags & X1_GAMMA_IN) {
+        if (colg < cols)
+            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+        __syncthreads();
+    }
+    cpx<R> *res = (flags & X1_FWD) ? run_fft<R, -1, NF>(buf, buf2, L, g.ax[0])
+                                   : run_fft<R, 1, NF>(buf, buf2, L, g.ax[0]);
+    if (flags & X1_GAMMA_OUT) {
+        if (colg < cols)
+            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, res + e * L + tg * 6);
+        __syncthreads();
+    }
+    Acc<R> acc;
+    if (live) {
+        const int colt = g0 + tl;
+        const int k3 = colt - (colt / H) * H;
+        const R w = (R)pweight(k3, g.n3);
+        cpx<R> *dst = out + (size_t)g0 * 6 + lt;
+        const cpx<R> *dv = dotv + (size_t)g0 * 6 + lt;
+        for (int e = e0; e < N; e += es) {
+            const cpx<R> z = res[e * L + lt];
+            dst[e * sK1] = z;
+            if (flags & X1_DOT) {
+                const cpx<R> d = dv[e * sK1];
+                acc.add_prod(w * z.x, d.x);
+                acc.add_prod(w * z.y, d.y);
+            }
+        }
+    }
+    if (flags & X1_DOT) {
+        const double s = block_sum(acc.value());
+        if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Krylov vector kernels on half spectra (n = 6 S complex values).  The
+// Parseval weight of element i depends on k3 = (i / 6) mod h.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_lanczos(int n, int h, int n3, cpx<R> *__restrict__ p,
+                                                        const cpx<R> *__restrict__ v, const cpx<R> *__restrict__ vprev,
+                                                        const MinresState *st, double *__restrict__ partials) {
+    if (skip(st)) return;
+    const R a = (R)st->alpha, b = (R)st->beta;
+    Acc<R> acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const cpx<R> x = p[i], y = v[i], z = vprev[i];
+        const cpx<R> q = mk<R>(x.x - a * y.x - b * z.x, x.y - a * y.y - b * z.y);
+        p[i] = q;
+        const R w = (R)pweight((i / 6) % h, n3);
+        acc.add_prod(w * q.x, q.x);
+        acc.add_prod(w * q.y, q.y);
+    }
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_update(int n, cpx<R> *__restrict__ p, const cpx<R> *__restrict__ v,
+                                                       const cpx<R> *__restrict__ w1, cpx<R> *__restrict__ w2,
+                                                       cpx<R> *__restrict__ x, const MinresState *st) {
+    if (st->done_update) return;
+    const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
+            ib = (R)st->u_inv_beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const cpx<R> vv = v[i], a = w1[i], b = w2[i], xx = x[i], pp = p[i];
+        const cpx<R> wn = mk<R>((vv.x - d * a.x - e * b.x) * ig, (vv.y - d * a.y - e * b.y) * ig);
+        w2[i] = wn;
+        x[i] = mk<R>(xx.x + tau * wn.x, xx.y + tau * wn.y);
+        p[i] = mk<R>(pp.x * ib, pp.y * ib);
+    }
+}
+
+template <typename R>
+__global__ void k_axpby(long long n, R a, const R *__restrict__ x, R b, R *__restrict__ y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + (b != (R)0 ? b * y[i] : (R)0);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_norm2w(int n, int h, int n3, const cpx<R> *__restrict__ x,
+                                                       double *partials) {
+    Acc<R> acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const cpx<R> q = x[i];
+        const R w = (R)pweight((i / 6) % h, n3);
+        acc.add_prod(w * q.x, q.x);
+        acc.add_prod(w * q.y, q.y);
+    }
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+template <typename R>
+int Launch<R>::ew_grid(long long n) {
+    long long b = (n + kEwThreads - 1) / kEwThreads;
+    return (int)(b < kEwBlocks ? (b > 0 ? b : 1) : kEwBlocks);
+}
+template <typename R>
+int Launch<R>::x3_grid(const Geometry &g) { return (g.n1 * g.n2 + g.rows3 - 1) / g.rows3; }
+template <typename R>
+int Launch<R>::x1_grid(const Geometry &g) { return (g.n2 * g.h + g.tile1 - 1) / g.tile1; }
+
+#define HOM_FAST_SWITCH(n, CALL)                   \
+    switch (n) {                                   \
+        case 8: CALL(8); break;                    \
+        case 16: CALL(16); break;                  \
+        case 32: CALL(32); break;                  \
+        case 64: CALL(64); break;                  \
+        case 128: CALL(128); break;                \
+        case 256: CALL(256); break;                \
+        case 512: CALL(512); break;                \
+        default: CALL(0); break;                   \
+    }
+
+template <typename R>
+void Launch<R>::table_init(const Geometry &) {
+    // The dynamic shared-memory limit of each pass kernel is raised to the
+    // device's opt-in maximum (a per-function setting shared by all contexts;
+    // the launch's own size still decides occupancy).
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    lim -= 1024;   // static shared memory of the reductions
+#define HOM_SET_ATTR(NF)                                                                       \
+    cudaFuncSetAttribute(k_x3<R, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);       \
+    cudaFuncSetAttribute(k_x2<R, -1, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
+    cudaFuncSetAttribute(k_x2<R, 1, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);    \
+    cudaFuncSetAttribute(k_x1<R, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(128)
+    HOM_SET_ATTR(256) HOM_SET_ATTR(512)
+#undef HOM_SET_ATTR
+}
+
+template <typename R>
+void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
+                   const double *macro, double scl, int out_mode, void *out, const R *phi,
+                   const MinresState *state) {
+    Mac6 m{};
+    if (macro)
+        for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
+    const int grid = x3_grid(g);
+#define HOM_X3(NF) \
+    k_x3<R, NF><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, (R)scl, out_mode, out, phi, state)
+    HOM_FAST_SWITCH(g.fast[2], HOM_X3)
+#undef HOM_X3
+}
+
+template <typename R>
+void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state) {
+    const int grid = (g.n1 * 6 * g.h + g.tile2 - 1) / g.tile2;
+#define HOM_X2(NF)                                                                  \
+    if (inverse) k_x2<R, 1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state); \
+    else k_x2<R, -1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state)
+    HOM_FAST_SWITCH(g.fast[1], HOM_X2)
+#undef HOM_X2
+}
+
+template <typename R>
+void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *in, cpx<R> *out, const cpx<R> *dotv,
+                   double *partials, const MinresState *state) {
+    const int grid = x1_grid(g);
+#define HOM_X1(NF) k_x1<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, flags, in, out, dotv, partials, state)
+    HOM_FAST_SWITCH(g.fast[0], HOM_X1)
+#undef HOM_X1
+}
+
+template <typename R>
+void Launch<R>::lanczos(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *vprev,
+                        const MinresState *state, double *partials) {
+    const int n = (int)(6 * g.S);
+    k_lanczos<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, p, v, vprev, state, partials);
+}
+
+template <typename R>
+void Launch<R>::update(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *w1, cpx<R> *w2,
+                       cpx<R> *x, MinresState *state) {
+    const int n = (int)(6 * g.S);
+    k_update<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, p, v, w1, w2, x, state);
+}
+
+template <typename R>
+void Launch<R>::axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y) {
+    k_axpby<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, (R)a, x, (R)b, y);
+}
+
+template <typename R>
+void Launch<R>::norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials) {
+    const int n = (int)(6 * g.S);
+    k_norm2w<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, x, partials);
+}
+
+}  // namespace hom

@@ -36,7 +36,8 @@ EXPORTED = [
 class hom_options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("device", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("device", ctypes.c_int), ("refine", ctypes.c_int),
+                ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -147,7 +148,7 @@ class Context:
 def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
                smoothing=HOM_SMOOTH_NONE, derivative=HOM_DERIV_ROTATED,
                precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
-               device=-1, refine=3) -> Context:
+               device=-1, refine=3, shape=(0, 0, 0)) -> Context:
     lib = load_library()
     opt = hom_options()
     lib.hom_default_options(ctypes.byref(opt))
@@ -156,6 +157,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
     opt.stream = stream
     opt.device = device
     opt.refine = refine
+    opt.rows3, opt.tile2, opt.tile1 = (int(s) for s in shape)
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),
@@ -217,7 +219,7 @@ def hom_rhs(ctx: Context, macro_strain, out=None):
 
 def spectrum_shape(ctx: Context):
     n1, n2, n3 = ctx.grid
-    return (6, n1, n2, n3 // 2 + 1)
+    return (n1, n2, n3 // 2 + 1, 6)
 
 
 def hom_fft_forward(ctx: Context, field, spectrum=None):
@@ -241,8 +243,8 @@ def hom_project(ctx: Context, field, out=None):
     return out
 
 
-KERNEL_NAMES = ["x3_fwd", "x2_fwd", "x1_gamma", "x2_inv", "x3_inv_dot", "alpha", "lanczos",
-                "givens", "update"]
+KERNEL_NAMES = ["x1_inv_gamma", "x2_inv", "x3_c2r_law_r2c", "x2_fwd", "x1_fwd_gamma_dot", "alpha",
+                "lanczos", "givens", "update"]
 
 
 def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:

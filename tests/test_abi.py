@@ -37,8 +37,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header():
     import ctypes
     from paper_2110_00733_gb300 import hom
-    # hom_options: 2 ints, int, (pad), pointer, int, int
-    assert ctypes.sizeof(hom.hom_options) == 32
+    # hom_options: 3 ints, (pad), pointer, 5 ints, (pad)
+    assert ctypes.sizeof(hom.hom_options) == 48
     # hom_solve_info: 4 ints + 2 doubles + 6 doubles + 1 double
     assert ctypes.sizeof(hom.hom_solve_info) == 16 + 8 * 9
 
