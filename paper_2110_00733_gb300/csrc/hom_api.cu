@@ -143,7 +143,7 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     //  generic engine: Stockham ping-pong, two buffers
     int rows, t2, t1;
     if (g.fast[2]) {
-        rows = 192 / (3 * (g.n3 / fast_elems(g.n3)));
+        rows = 96 / (3 * (g.n3 / fast_elems(g.n3)));
         rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
     } else {
         rows = 16;
@@ -156,7 +156,7 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
         while (t2 > 1 && 2ull * g.n2 * t2 * cs > 64 * 1024) t2 >>= 1;
     }
     if (g.fast[0]) {
-        t1 = 384 * fast_elems(g.n1) / (6 * g.n1);
+        t1 = 192 * fast_elems(g.n1) / (6 * g.n1);
         t1 = t1 < 1 ? 1 : (t1 > 16 ? 16 : t1);
     } else {
         t1 = 16;
@@ -170,12 +170,13 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     g.tile1 = t1;
     auto round32 = [](int v) { return (v + 31) / 32 * 32; };
     auto clampt = [](int v) { return v < 128 ? 128 : (v > 512 ? 512 : v); };
+    const int es3 = (3 * rows) | 1;   // element stride of the n3 tile (odd)
     if (g.fast[2]) {
         g.threads3 = 3 * rows * (g.n3 / fast_elems(g.n3));
-        g.smem3 = (size_t)3 * rows * g.n3 * cs;
+        g.smem3 = (size_t)es3 * g.n3 * cs;
     } else {
         g.threads3 = clampt(round32(3 * rows * g.n3 / 16));
-        g.smem3 = 2ull * 3 * rows * g.n3 * cs;
+        g.smem3 = 2ull * es3 * g.n3 * cs;
     }
     if (g.fast[1]) {
         g.threads2 = t2 * (g.n2 / fast_elems(g.n2));

@@ -3,8 +3,8 @@
 // eq. (gal) are discrete Fourier transforms evaluated with an FFT).
 //
 // A CTA holds a batch of L lines of one axis in shared memory, element e of
-// line l at buf[e*L + l] (lines interleaved, so that the threads of a warp
-// touch consecutive words whatever the stage's index pattern), and runs
+// line l at buf[e*ES + l] with ES >= L (lines interleaved, so that the threads
+// of a warp touch consecutive words whatever the stage's index pattern), and runs
 // Stockham auto-sort stages between two buffers.  Each stage applies radix-R
 // butterflies (R in {2,3,4,5,8,16}) held in registers; twiddles come from a
 // per-axis table w[t] = exp(-2 pi i t / N) computed on the host in double.
@@ -150,7 +150,7 @@ template <typename R, int S, int RAD> __device__ __forceinline__ void dft(cpx<R>
 // ---------------------------------------------------------------------------
 template <typename R, int S, int RAD>
 __device__ __forceinline__ void stockham_stage(const cpx<R> *__restrict__ src, cpx<R> *__restrict__ dst,
-                                               int N, int Ns, int L, const cpx<R> *__restrict__ tw) {
+                                               int N, int Ns, int L, int ES, const cpx<R> *__restrict__ tw) {
     const int nb = N / RAD;
     const int total = nb * L;
     const int twstep = N / (Ns * RAD);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void stockham_stage(const cpx<R> *__restrict__ src, c
         const int l = b - j * L;
         cpx<R> v[RAD];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[r] = src[(j + r * nb) * L + l];
+        for (int r = 0; r < RAD; ++r) v[r] = src[(j + r * nb) * ES + l];
         const int jm = j % Ns;
         if (Ns > 1) {
 #pragma unroll
@@ -172,26 +172,26 @@ __device__ __forceinline__ void stockham_stage(const cpx<R> *__restrict__ src, c
         dft<R, S, RAD>(v);
         const int o = (j - jm) * RAD + jm;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) dst[(o + r * Ns) * L + l] = v[r];
+        for (int r = 0; r < RAD; ++r) dst[(o + r * Ns) * ES + l] = v[r];
     }
 }
 
 // Full transform of L interleaved lines held in bufA.  Returns the buffer
 // holding the result (bufA or bufB).  All threads of the block must call it.
 template <typename R, int S>
-__device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, const AxisPlan &p) {
+__device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, int ES, const AxisPlan &p) {
     cpx<R> *src = bufA, *dst = bufB;
     const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(p.tw);
     int Ns = 1;
     for (int s = 0; s < p.nstages; ++s) {
         const int rad = p.radix[s];
         switch (rad) {
-            case 2: stockham_stage<R, S, 2>(src, dst, p.n, Ns, L, tw); break;
-            case 3: stockham_stage<R, S, 3>(src, dst, p.n, Ns, L, tw); break;
-            case 4: stockham_stage<R, S, 4>(src, dst, p.n, Ns, L, tw); break;
-            case 5: stockham_stage<R, S, 5>(src, dst, p.n, Ns, L, tw); break;
-            case 8: stockham_stage<R, S, 8>(src, dst, p.n, Ns, L, tw); break;
-            default: stockham_stage<R, S, 16>(src, dst, p.n, Ns, L, tw); break;
+            case 2: stockham_stage<R, S, 2>(src, dst, p.n, Ns, L, ES, tw); break;
+            case 3: stockham_stage<R, S, 3>(src, dst, p.n, Ns, L, ES, tw); break;
+            case 4: stockham_stage<R, S, 4>(src, dst, p.n, Ns, L, ES, tw); break;
+            case 5: stockham_stage<R, S, 5>(src, dst, p.n, Ns, L, ES, tw); break;
+            case 8: stockham_stage<R, S, 8>(src, dst, p.n, Ns, L, ES, tw); break;
+            default: stockham_stage<R, S, 16>(src, dst, p.n, Ns, L, ES, tw); break;
         }
         __syncthreads();
         Ns *= rad;
@@ -226,7 +226,7 @@ __host__ __device__ constexpr int fast_elems(int n) {
 }
 
 template <typename R, int S, int N, int RAD, int NS_BEFORE>
-__device__ __forceinline__ void fast_stage(cpx<R> *buf, int L, int l, int j0, const cpx<R> *__restrict__ tw) {
+__device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, const cpx<R> *__restrict__ tw) {
     constexpr int E = FastPlan<N>::E;
     constexpr int BPT = E / RAD;
     constexpr int nb = N / RAD;
@@ -237,7 +237,7 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int L, int l, int j0, co
     for (int i = 0; i < BPT; ++i) {
         const int j = j0 + i * jstep;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[i][r] = buf[(j + r * nb) * L + l];
+        for (int r = 0; r < RAD; ++r) v[i][r] = buf[(j + r * nb) * ES + l];
     }
     __syncthreads();
 #pragma unroll
@@ -255,21 +255,22 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int L, int l, int j0, co
         dft<R, S, RAD>(v[i]);
         const int o = (j - jm) * RAD + jm;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) buf[(o + r * NS_BEFORE) * L + l] = v[i][r];
+        for (int r = 0; r < RAD; ++r) buf[(o + r * NS_BEFORE) * ES + l] = v[i][r];
     }
     __syncthreads();
 }
 
-// Transform of L interleaved lines in buf (in place).  The CTA must have
-// exactly L * N / E threads (every thread takes part in every barrier).
+// Transform of L interleaved lines in buf (in place), element e of line l
+// at buf[e * ES + l] (ES >= L).  The CTA must have exactly L * N / E threads
+// (every thread takes part in every barrier).
 template <typename R, int S, int N>
-__device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, const cpx<R> *__restrict__ tw) {
+__device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R> *__restrict__ tw) {
     using P = FastPlan<N>;
     const int l = (int)threadIdx.x % L;
     const int j0 = (int)threadIdx.x / L;
-    fast_stage<R, S, N, P::R0, 1>(buf, L, l, j0, tw);
-    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0>(buf, L, l, j0, tw);
-    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1>(buf, L, l, j0, tw);
+    fast_stage<R, S, N, P::R0, 1>(buf, ES, l, j0, tw);
+    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0>(buf, ES, l, j0, tw);
+    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1>(buf, ES, l, j0, tw);
 }
 
 }  // namespace hom

@@ -144,14 +144,43 @@ __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int 
 // buf.  Generic engine: ping-pong with buf2, returns the buffer holding the
 // result.
 template <typename R, int S, int NF>
-__device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, const AxisPlan &p) {
+__device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, int ES, const AxisPlan &p) {
     if constexpr (NF > 0) {
-        fast_fft<R, S, NF>(buf, L, reinterpret_cast<const cpx<R> *>(p.tw));
+        fast_fft<R, S, NF>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw));
         return buf;
     } else {
-        return fft_lines<R, S>(buf, buf2, L, p);
+        return fft_lines<R, S>(buf, buf2, L, ES, p);
     }
 }
+
+// Six adjacent complex values (one frequency, or one k of a row) as 16-byte
+// accesses: pairs (2p, 2p+1) for FP32, single values for FP64.
+template <typename R> struct Six;
+template <> struct Six<float> {
+    __device__ static void load_pair(const float2 *src, int p, float2 &a, float2 &b) {
+        const float4 v = reinterpret_cast<const float4 *>(src)[p];
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+    }
+    __device__ static void store_pair(float2 *dst, int p, float2 a, float2 b) {
+        reinterpret_cast<float4 *>(dst)[p] = make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+template <> struct Six<double> {
+    __device__ static void load_pair(const double2 *src, int p, double2 &a, double2 &b) {
+        a = src[2 * p];
+        b = src[2 * p + 1];
+    }
+    __device__ static void store_pair(double2 *dst, int p, double2 a, double2 b) {
+        dst[2 * p] = a;
+        dst[2 * p + 1] = b;
+    }
+};
+
+// Register cap of the pass kernels: FP32 kernels are held to 64 registers
+// (two 512-thread CTAs' worth per SM) so that more CTAs stay resident to hide
+// HBM latency; FP64 kernels keep their data in registers instead.
+#define HOM_PASS_BOUNDS(R) __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 
 // ---------------------------------------------------------------------------
 // n3 pass.  A CTA owns rows (k1,k2) [row0, row0+rows3); lines are the three
@@ -159,14 +188,16 @@ __device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, con
 // Z = X_2p + i X_2p+1, line index p*rows3 + r.
 // ---------------------------------------------------------------------------
 template <typename R, int NF>
-__global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
-                                            R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
-                                            const R *__restrict__ phi, const MinresState *state) {
+__global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
+                                        R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
+                                        const R *__restrict__ phi, const MinresState *state) {
     if (skip(state)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, H = g.h;
+    // element stride ES = L rounded up to odd: the per-element phases below
+    // stride by ES across a warp and stay free of bank conflicts
+    const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, ES = L | 1, H = g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
-    cpx<R> *buf2 = buf + N * L;   // second buffer of the generic engine only
+    cpx<R> *buf2 = buf + N * ES;   // second buffer of the generic engine only
     const int nrows = g.n1 * g.n2;
     const int row0 = blockIdx.x * ROWS;
     const int V = (int)g.V;
@@ -178,23 +209,22 @@ __global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void 
         const cpx<R> *spec = reinterpret_cast<const cpx<R> *>(in_);
         for (int r = 0; r < ROWS; ++r) {
             const cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
-            for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
-                const int k = idx / 3, p = idx - 3 * k;
-                cpx<R> xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-                if (r < nr) {
-                    xa = row[k * 6 + 2 * p];
-                    xb = row[k * 6 + 2 * p + 1];
-                }
+            for (int k = threadIdx.x; k < H; k += blockDim.x) {
                 const bool selfc = (k == 0) || (2 * k == N);
-                if (selfc) { xa.y = 0; xb.y = 0; }
-                buf[k * L + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
-                if (!selfc) buf[(N - k) * L + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    cpx<R> xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+                    if (r < nr) Six<R>::load_pair(row + 6 * k, p, xa, xb);
+                    if (selfc) { xa.y = 0; xb.y = 0; }
+                    buf[k * ES + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
+                    if (!selfc) buf[(N - k) * ES + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
+                }
             }
         }
         __syncthreads();
-        cpx<R> *res = run_fft<R, 1, NF>(buf, buf2, L, g.ax[2]);
+        cpx<R> *res = run_fft<R, 1, NF>(buf, buf2, L, ES, g.ax[2]);
         if (res != buf) {   // generic engine ended in the second buffer
-            for (int i = threadIdx.x; i < N * L; i += blockDim.x) buf[i] = res[i];
+            for (int i = threadIdx.x; i < N * ES; i += blockDim.x) buf[i] = res[i];
             __syncthreads();
         }
     } else {
@@ -207,7 +237,7 @@ __global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void 
                 for (int c = 0; c < 6; ++c)
                     t[c] = (r >= nr) ? (R)0 : (in_mode == X3_IN_MACRO ? (R)mac.v[c] : real[c * V + vbase + e]);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) buf[e * L + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
+                for (int p = 0; p < 3; ++p) buf[e * ES + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
             }
         }
         __syncthreads();
@@ -218,7 +248,7 @@ __global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void 
     for (int r = 0; r < nr; ++r) {
         const int vbase = (row0 + r) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
-            cpx<R> *q = buf + e * L + r;
+            cpx<R> *q = buf + e * ES + r;
             R t[6];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
@@ -245,19 +275,21 @@ __global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void 
     if (out_mode == X3_OUT_REAL) return;
     // rows beyond nrows hold zeros already (their inputs were zero)
     __syncthreads();
-    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, g.ax[2]);
+    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, ES, g.ax[2]);
     // unpack the two real transforms of each packed line:
     //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
     cpx<R> *spec = reinterpret_cast<cpx<R> *>(out_);
     for (int r = 0; r < nr; ++r) {
         cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
-        for (int idx = threadIdx.x; idx < 3 * H; idx += blockDim.x) {
-            const int k = idx / 3, p = idx - 3 * k;
+        for (int k = threadIdx.x; k < H; k += blockDim.x) {
             const int km = (k == 0) ? 0 : N - k;
-            const cpx<R> z = res[k * L + p * ROWS + r];
-            const cpx<R> zm = conjc<R>(res[km * L + p * ROWS + r]);
-            row[k * 6 + 2 * p] = mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y));
-            row[k * 6 + 2 * p + 1] = mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x));
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const cpx<R> z = res[k * ES + p * ROWS + r];
+                const cpx<R> zm = conjc<R>(res[km * ES + p * ROWS + r]);
+                Six<R>::store_pair(row + 6 * k, p, mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y)),
+                                   mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x)));
+            }
         }
     }
 }
@@ -268,7 +300,7 @@ __global__ void __launch_bounds__(512) k_x3(Geometry g, int in_mode, const void 
 // columns per CTA (contiguous runs of tile2 complex values).
 // ---------------------------------------------------------------------------
 template <typename R, int S, int NF>
-__global__ void __launch_bounds__(512) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
+__global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
     if (skip(state)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = g.n2, T = g.tile2, H6 = 6 * g.h;
@@ -282,7 +314,7 @@ __global__ void __launch_bounds__(512) k_x2(Geometry g, cpx<R> *__restrict__ spe
     cpx<R> *col = spec + (size_t)k1 * N * H6 + (f - k1 * H6);   // element e at col[e * H6]
     for (int e = e0; e < N; e += es) buf[e * T + t] = live ? col[(size_t)e * H6] : mk<R>(0, 0);
     __syncthreads();
-    cpx<R> *res = run_fft<R, S, NF>(buf, buf2, T, g.ax[1]);
+    cpx<R> *res = run_fft<R, S, NF>(buf, buf2, T, T, g.ax[1]);
     if (live)
         for (int e = e0; e < N; e += es) col[(size_t)e * H6] = res[e * T + t];
 }
@@ -293,7 +325,7 @@ __global__ void __launch_bounds__(512) k_x2(Geometry g, cpx<R> *__restrict__ spe
 // the tile is one contiguous run of 6 tile1 complex values).
 // ---------------------------------------------------------------------------
 template <typename R, int NF>
-__global__ void __launch_bounds__(512) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
+__global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
                                             cpx<R> *__restrict__ out, const cpx<R> *__restrict__ dotv,
                                             double *__restrict__ partials, const MinresState *state) {
     if (skip(state)) {
@@ -327,8 +359,8 @@ __global__ void __launch_bounds__(512) k_x1(Geometry g, int flags, const cpx<R> 
             for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
         __syncthreads();
     }
-    cpx<R> *res = (flags & X1_FWD) ? run_fft<R, -1, NF>(buf, buf2, L, g.ax[0])
-                                   : run_fft<R, 1, NF>(buf, buf2, L, g.ax[0]);
+    cpx<R> *res = (flags & X1_FWD) ? run_fft<R, -1, NF>(buf, buf2, L, L, g.ax[0])
+                                   : run_fft<R, 1, NF>(buf, buf2, L, L, g.ax[0]);
     if (flags & X1_GAMMA_OUT) {
         if (colg < cols)
             for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, res + e * L + tg * 6);
@@ -450,14 +482,20 @@ void Launch<R>::table_init(const Geometry &) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     lim -= 1024;   // static shared memory of the reductions
-#define HOM_SET_ATTR(NF)                                                                       \
-    cudaFuncSetAttribute(k_x3<R, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);       \
-    cudaFuncSetAttribute(k_x2<R, -1, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
-    cudaFuncSetAttribute(k_x2<R, 1, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);    \
-    cudaFuncSetAttribute(k_x1<R, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    // and the L1/shared carve-out to the largest shared share, so that the
+    // number of resident CTAs is set by registers, not by a small carve-out
+#define HOM_SET_ATTR1(K)                                                                        \
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);                  \
+    cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+#define HOM_SET_ATTR(NF)                \
+    HOM_SET_ATTR1((k_x3<R, NF>))        \
+    HOM_SET_ATTR1((k_x2<R, -1, NF>))    \
+    HOM_SET_ATTR1((k_x2<R, 1, NF>))     \
+    HOM_SET_ATTR1((k_x1<R, NF>))
     HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(128)
     HOM_SET_ATTR(256) HOM_SET_ATTR(512)
 #undef HOM_SET_ATTR
+#undef HOM_SET_ATTR1
 }
 
 template <typename R>
