@@ -64,7 +64,7 @@ enum {
     HOM_ENOMEM = -3,                /* device allocation failed */
     HOM_ECUDA = -4,                 /* CUDA runtime error */
     HOM_ENAN = -5,                  /* NaN/Inf met in the input or a Krylov scalar */
-    HOM_ETIMEOUT = -6               /* reserved: a bounded device wait gave up */
+    HOM_ETIMEOUT = -6               /* a bounded device wait (TMA completion) gave up */
 };
 
 enum { HOM_INPUT_PHASE_U8 = 0,      /* uint8 phase id: 0 empty, nonzero solid */
@@ -89,6 +89,8 @@ typedef struct {
     int rows3;          /* launch shape: n3-pass rows per CTA (0 = automatic, <= 64) */
     int tile2;          /* launch shape: n2-pass columns per CTA (0 = automatic; power of 2, <= 32) */
     int tile1;          /* launch shape: n1-pass columns per CTA (0 = automatic, <= 16) */
+    int staging;        /* 0: persistent TMA-staged n1/n2 passes where supported
+                           (FP32, power-of-two n1, n2 in [64, 256]); 1: plain loads */
 } hom_options;
 
 typedef struct {

@@ -57,6 +57,8 @@ struct hom_ctx {
     int device_ptrs = 0;
     int refine = 3;
     int shape[3] = {0, 0, 0};   // launch-shape overrides (rows3, tile2, tile1)
+    int staging = 0;            // 0: TMA-staged passes where supported, 1: plain loads
+    int *d_err = nullptr;       // set by a pass whose bounded wait gave up
     Engine<float> e32;
     Engine<double> e64;
     // MINRES workspace in the solve precision (half spectra, float2 or double2)
@@ -239,12 +241,28 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     CU(cudaMalloc(&E.spec, cs * 6 * ctx->S));
     ctx->workspace += sizeof(R) * ctx->V + cs * 6 * ctx->S;
     Launch<R>::table_init(g);
+    // persistent TMA-staged n2 / n1 passes: FP32, register-FFT lengths <= 256
+    g.tma = 0;
+    g.err = ctx->d_err;
+    g.tma_cache = nullptr;
+    if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 256 &&
+        g.fast[1] >= 64 && g.fast[1] <= 256 && g.tile2 % 2 == 0) {
+        g.tma = 1;
+        g.smem2_tma = 2ull * g.n2 * g.tile2 * cs;
+        g.smem1_tma = 2ull * 6 * g.tile1 * g.n1 * cs;
+        g.smem1d_tma = 2 * g.smem1_tma;
+        if (g.smem1d_tma + 1024 > (size_t)dev_smem || g.smem2_tma + 1024 > (size_t)dev_smem) g.tma = 0;
+        if (g.tma && Launch<R>::tma_grids(g)) g.tma_cache = tma_cache_new();
+        else g.tma = 0;
+    }
     CU(cudaGetLastError());
     return HOM_OK;
 }
 
 template <typename R>
 static void engine_free(Engine<R> &E) {
+    tma_cache_free(E.g.tma_cache);
+    E.g.tma_cache = nullptr;
     for (int p = 0; p < 3; ++p) {
         cudaFree(E.tw[p]);
         cudaFree(E.D[p]);
@@ -416,6 +434,12 @@ static int stage_out(hom_ctx *ctx, void *user, size_t bytes, const void *dev) {
 static int finish(hom_ctx *ctx) {
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
+    int e = 0;
+    CU(cudaMemcpy(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CU(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return fail(ctx, HOM_ETIMEOUT, "a bounded device wait gave up (TMA copy did not complete)");
+    }
     return HOM_OK;
 }
 
@@ -454,6 +478,7 @@ void hom_destroy(hom_ctx *ctx) {
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_scalar);
     cudaFree(ctx->d_flag);
+    cudaFree(ctx->d_err);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -479,6 +504,8 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     }
     CU(cudaEventCreate(&ctx->ev0));
     CU(cudaEventCreate(&ctx->ev1));
+    CU(cudaMalloc(&ctx->d_err, sizeof(int)));
+    CU(cudaMemset(ctx->d_err, 0, sizeof(int)));
     int rc = engine_init<double>(ctx, ctx->e64);
     if (rc) return rc;
     if (ctx->prec == HOM_PREC_FP32_FIELDS) {
@@ -564,6 +591,7 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     ctx->shape[0] = o.rows3;
     ctx->shape[1] = o.tile2;
     ctx->shape[2] = o.tile1;
+    ctx->staging = o.staging;
     ctx->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) ctx->device = o.device;
     else if (cudaGetDevice(&ctx->device) != cudaSuccess) {
@@ -596,7 +624,6 @@ static int step_impl(hom_ctx *ctx, Engine<R> &E, int which, const void *in, void
     const long long n = 6 * ctx->V;
     R *din = (R *)ctx->vbuf[0], *dout = (R *)ctx->vbuf[1];
     cpx<R> *spec = (cpx<R> *)ctx->vbuf[2];
-    cudaStream_t s = ctx->stream;
     int rc;
     switch (which) {
         case 0:  // apply (Mandel): A(e) = F^-1 G F C e

@@ -2,6 +2,9 @@
 // the refinement and post-processing, and input conversion.
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "hom_internal.h"
 
 namespace hom {
@@ -218,6 +221,91 @@ __global__ void k_phi_convert(long long V, const void *in, int kind, R *out, int
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Tensor maps of the TMA passes (host).  The encoder is the driver's
+// cuTensorMapEncodeTiled, reached through the runtime's entry-point query so
+// the library does not link libcuda directly.
+// ---------------------------------------------------------------------------
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+struct TmaEntry {
+    const void *ptr;
+    int kind;
+    CUtensorMap map;
+};
+struct TmaCache {
+    std::vector<TmaEntry *> entries;
+};
+}  // namespace
+
+bool tma_available() { return encoder() != nullptr; }
+
+void *tma_cache_new() { return new TmaCache(); }
+
+void tma_cache_free(void *c) {
+    TmaCache *tc = static_cast<TmaCache *>(c);
+    if (!tc) return;
+    for (TmaEntry *e : tc->entries) delete e;
+    delete tc;
+}
+
+// Half spectrum n1 x n2 x h x 6 of 8-byte units (elem_units per complex).
+//  TMA_X2: 3-D (6h, n2, n1), box (tile2, n2, 1): one tile2-wide run of
+//          columns over all k2 of one k1 plane.
+//  TMA_X1: 2-D (6 n2 h, n1), box (6 tile1, n1): tile1 (k2,k3) columns with
+//          their 6 components over all k1.
+const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int units) {
+    TmaCache *tc = static_cast<TmaCache *>(g.tma_cache);
+    for (TmaEntry *e : tc->entries)
+        if (e->ptr == ptr && e->kind == kind) return &e->map;
+    EncodeTiledFn fn = encoder();
+    if (!fn) return nullptr;
+    TmaEntry *e = new TmaEntry();
+    e->ptr = ptr;
+    e->kind = kind;
+    const cuuint64_t u = (cuuint64_t)units;
+    const cuuint64_t h6 = 6ull * g.h * u;
+    CUresult r;
+    if (kind == TMA_X2) {
+        cuuint64_t dims[3] = {h6, (cuuint64_t)g.n2, (cuuint64_t)g.n1};
+        cuuint64_t strides[2] = {h6 * 8, h6 * 8 * g.n2};
+        cuuint32_t box[3] = {(cuuint32_t)(g.tile2 * units), (cuuint32_t)g.n2, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        r = fn(&e->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[2] = {h6 * g.n2, (cuuint64_t)g.n1};
+        cuuint64_t strides[1] = {h6 * g.n2 * 8};
+        cuuint32_t box[2] = {(cuuint32_t)(6 * g.tile1 * units), (cuuint32_t)g.n1};
+        cuuint32_t es[2] = {1, 1};
+        r = fn(&e->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) {
+        delete e;
+        return nullptr;
+    }
+    tc->entries.push_back(e);
+    return &e->map;
+}
 
 int ew_blocks(long long n) {
     long long b = (n + kEwThreads - 1) / kEwThreads;

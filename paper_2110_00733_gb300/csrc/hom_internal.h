@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "hom_fft.cuh"
+#include "hom_tma.cuh"
 
 namespace hom {
 
@@ -56,7 +57,25 @@ struct Geometry {
     int threads3, threads2, threads1;
     size_t smem3, smem2, smem1;
     int fast[3];
+    // persistent TMA-staged n2 / n1 passes (FP32, power-of-two n <= 256):
+    // enabled flag, persistent grid sizes, shared memory, host-side cache of
+    // tensor maps (never dereferenced on the device) and the device word a
+    // pass sets when a bounded wait gives up
+    int tma;
+    int grid2_tma, grid1_tma, grid1d_tma;
+    size_t smem2_tma, smem1_tma, smem1d_tma;
+    void *tma_cache;
+    int *err;
 };
+
+// tensor-map kinds of the TMA passes
+enum TmaKind { TMA_X2 = 0, TMA_X1 = 1 };
+// Host: the cached tensor map of `ptr` (a half spectrum of this geometry) for
+// the given pass; nullptr if the driver entry point is unavailable.
+const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int elem_units);
+void *tma_cache_new();
+bool tma_available();
+void tma_cache_free(void *cache);
 
 // n3 pass (x3): input, middle and output stages
 enum X3In { X3_IN_SPEC = 0, X3_IN_REAL = 1, X3_IN_MACRO = 2 };
@@ -97,6 +116,7 @@ template <typename R> struct Launch {
     static void table_init(const Geometry &g);
     static int x3_grid(const Geometry &g);
     static int x1_grid(const Geometry &g);
+    static int tma_grids(Geometry &g);
 };
 
 // FP64 helpers on spectral vectors (double2) and real fields

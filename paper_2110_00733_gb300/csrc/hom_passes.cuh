@@ -192,7 +192,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state) {
     if (skip(state)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
     // stride by ES across a warp and stay free of bank conflicts
     const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, ES = L | 1, H = g.h;
@@ -302,7 +302,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
 template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
     if (skip(state)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = g.n2, T = g.tile2, H6 = 6 * g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * T;
@@ -334,7 +334,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
             const_cast<MinresState *>(state)->done_update = 1;
         return;
     }
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = g.n1, T = g.tile1, H = g.h, L = 6 * T;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * L;
@@ -386,6 +386,168 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
     if (flags & X1_DOT) {
         const double s = block_sum(acc.value());
         if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent TMA-staged n2 and n1 passes (FP32, n <= 256, fast engine).
+// Each CTA loops over tiles with two shared-memory stages: while the FFT runs
+// on stage s, the TMA load of the next tile fills stage s^1; results leave by
+// TMA store.  One thread issues all copies; completion is tracked by one
+// mbarrier per stage.  Every wait is bounded: on time-out the CTA records
+// the failure in *g.err, waits (bounded) for its own load in flight and
+// returns, and the host reports HOM_ETIMEOUT.
+// ---------------------------------------------------------------------------
+template <typename R, int S, int NF>
+__global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ CUtensorMap tm, int qtiles,
+                                            const MinresState *state) {
+    if (skip(state)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int N = g.n2, T = g.tile2;
+    const int ntiles = g.n1 * qtiles;
+    cpx<R> *const base = reinterpret_cast<cpx<R> *>(smem_raw);
+    const int per = N * T;   // stage s starts at base + s * per
+    const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
+    const bool leader = threadIdx.x == 0;
+    if (leader) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    if (leader && tile < ntiles) {
+        mbar_expect_tx(&bar[0], bytes);
+        tma_load_3d(base, &tm, (tile % qtiles) * T, 0, tile / qtiles, &bar[0]);
+    }
+    const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[1].tw);
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int s = i & 1;
+        const int next = tile + gridDim.x;
+        if (leader && next < ntiles) {
+            bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
+            mbar_expect_tx(&bar[s ^ 1], bytes);
+            tma_load_3d(base + (s ^ 1) * per, &tm, (next % qtiles) * T, 0, next / qtiles, &bar[s ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
+                atomicExch(g.err, 1);
+                mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
+                bulk_wait_all();
+            }
+            return;
+        }
+        cpx<R> *buf = base + s * per;
+        fast_fft<R, S, NF>(buf, T, T, tw);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (leader) {
+            tma_store_3d(&tm, (tile % qtiles) * T, 0, tile / qtiles, buf);
+            bulk_commit();
+        }
+    }
+    if (leader) bulk_wait_all();
+}
+
+template <typename R, int NF>
+__global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_constant__ CUtensorMap tin,
+                                            const __grid_constant__ CUtensorMap tout,
+                                            const __grid_constant__ CUtensorMap tdot, double *__restrict__ partials,
+                                            const MinresState *state) {
+    if (skip(state)) {
+        if ((flags & X1_GAMMA_IN) && blockIdx.x == 0 && threadIdx.x == 0)
+            const_cast<MinresState *>(state)->done_update = 1;
+        return;
+    }
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int N = g.n1, T = g.tile1, H = g.h, L = 6 * T;
+    const int cols = g.n2 * H;
+    const int ntiles = (cols + T - 1) / T;
+    const bool dot = (flags & X1_DOT) != 0;
+    const int tile_elems = N * L;
+    cpx<R> *base = reinterpret_cast<cpx<R> *>(smem_raw);
+    // stage s: data tile at base + s * per, dot tile (if any) right after it
+    const int per = tile_elems * (dot ? 2 : 1);
+    const uint32_t bytes = (uint32_t)(tile_elems * sizeof(cpx<R>)) * (dot ? 2u : 1u);
+    const bool leader = threadIdx.x == 0;
+    if (leader) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int s) {
+        mbar_expect_tx(&bar[s], bytes);
+        tma_load_2d(base + s * per, &tin, 6 * T * t, 0, &bar[s]);
+        if (dot) tma_load_2d(base + s * per + tile_elems, &tdot, 6 * T * t, 0, &bar[s]);
+    };
+    int tile = blockIdx.x;
+    if (leader && tile < ntiles) issue(tile, 0);
+    const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[0].tw);
+    const int lt = threadIdx.x % L, e0 = threadIdx.x / L, es = blockDim.x / L;
+    const int tg = threadIdx.x % T, eg0 = threadIdx.x / T, egs = blockDim.x / T;
+    Acc<R> acc;
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int s = i & 1;
+        const int next = tile + gridDim.x;
+        if (leader && next < ntiles) {
+            bulk_wait_read_all();
+            issue(next, s ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
+                atomicExch(g.err, 1);
+                mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
+                bulk_wait_all();
+            }
+            return;
+        }
+        cpx<R> *buf = base + s * per;
+        const int g0 = tile * T;
+        const int colg = g0 + tg;
+        const int k2g = colg / H, k3g = colg - k2g * H;
+        if (flags & X1_GAMMA_IN) {
+            if (colg < cols)
+                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+            __syncthreads();
+        }
+        if (flags & X1_FWD) fast_fft<R, -1, NF>(buf, L, L, tw);
+        else fast_fft<R, 1, NF>(buf, L, L, tw);
+        if (flags & X1_GAMMA_OUT) {
+            if (colg < cols)
+                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+            __syncthreads();
+        }
+        if (dot) {
+            const int colt = g0 + lt / 6;
+            if (colt < cols) {
+                const int k3 = colt % H;
+                const R w = (R)pweight(k3, g.n3);
+                const cpx<R> *dv = buf + tile_elems;
+                for (int e = e0; e < N; e += es) {
+                    const cpx<R> z = buf[e * L + lt], d = dv[e * L + lt];
+                    acc.add_prod(w * z.x, d.x);
+                    acc.add_prod(w * z.y, d.y);
+                }
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (leader) {
+            tma_store_2d(&tout, 6 * T * tile, 0, buf);
+            bulk_commit();
+        }
+    }
+    if (leader) bulk_wait_all();
+    if (dot) {
+        const double sum = block_sum(acc.value());
+        if (threadIdx.x == 0) partials[blockIdx.x] = sum;
     }
 }
 
@@ -458,8 +620,11 @@ int Launch<R>::ew_grid(long long n) {
 }
 template <typename R>
 int Launch<R>::x3_grid(const Geometry &g) { return (g.n1 * g.n2 + g.rows3 - 1) / g.rows3; }
+// number of partial sums the dot-product variant of the n1 pass writes
 template <typename R>
-int Launch<R>::x1_grid(const Geometry &g) { return (g.n2 * g.h + g.tile1 - 1) / g.tile1; }
+int Launch<R>::x1_grid(const Geometry &g) {
+    return g.tma ? g.grid1d_tma : (g.n2 * g.h + g.tile1 - 1) / g.tile1;
+}
 
 #define HOM_FAST_SWITCH(n, CALL)                   \
     switch (n) {                                   \
@@ -494,8 +659,56 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x1<R, NF>))
     HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(128)
     HOM_SET_ATTR(256) HOM_SET_ATTR(512)
+    if constexpr (sizeof(R) == 4) {
+#define HOM_SET_TMA(NF)                   \
+    HOM_SET_ATTR1((k_x2_tma<R, -1, NF>))  \
+    HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
+    HOM_SET_ATTR1((k_x1_tma<R, NF>))
+        HOM_SET_TMA(64) HOM_SET_TMA(128) HOM_SET_TMA(256)
+#undef HOM_SET_TMA
+    }
 #undef HOM_SET_ATTR
 #undef HOM_SET_ATTR1
+}
+
+// persistent-grid sizes of the TMA passes: resident CTAs per SM x SMs
+template <typename R>
+int Launch<R>::tma_grids(Geometry &g) {
+    if constexpr (sizeof(R) != 4) {
+        g.tma = 0;
+        return 0;
+    } else {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int b2 = 0, b1 = 0, b1d = 0;
+        auto occ = [&](auto kern, int threads, size_t smem) {
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+            return nb;
+        };
+        switch (g.fast[1]) {
+            case 64: b2 = occ(k_x2_tma<R, -1, 64>, g.threads2, g.smem2_tma); break;
+            case 128: b2 = occ(k_x2_tma<R, -1, 128>, g.threads2, g.smem2_tma); break;
+            default: b2 = occ(k_x2_tma<R, -1, 256>, g.threads2, g.smem2_tma); break;
+        }
+        switch (g.fast[0]) {
+            case 64: b1 = occ(k_x1_tma<R, 64>, g.threads1, g.smem1_tma);
+                     b1d = occ(k_x1_tma<R, 64>, g.threads1, g.smem1d_tma); break;
+            case 128: b1 = occ(k_x1_tma<R, 128>, g.threads1, g.smem1_tma);
+                      b1d = occ(k_x1_tma<R, 128>, g.threads1, g.smem1d_tma); break;
+            default: b1 = occ(k_x1_tma<R, 256>, g.threads1, g.smem1_tma);
+                     b1d = occ(k_x1_tma<R, 256>, g.threads1, g.smem1d_tma); break;
+        }
+        if (b2 < 1 || b1 < 1 || b1d < 1) {
+            g.tma = 0;
+            return 0;
+        }
+        g.grid2_tma = b2 * sms;
+        g.grid1_tma = b1 * sms;
+        g.grid1d_tma = b1d * sms;
+        return 1;
+    }
 }
 
 template <typename R>
@@ -514,6 +727,22 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
 
 template <typename R>
 void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state) {
+    if constexpr (sizeof(R) == 4) {
+        if (g.tma) {
+            const CUtensorMap *tm = tma_map(g, spec, TMA_X2, 1);
+            const int qtiles = (6 * g.h + g.tile2 - 1) / g.tile2;
+#define HOM_X2T(NF)                                                                                         \
+    if (inverse) k_x2_tma<R, 1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state);    \
+    else k_x2_tma<R, -1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state)
+            switch (g.fast[1]) {
+                case 64: HOM_X2T(64); break;
+                case 128: HOM_X2T(128); break;
+                default: HOM_X2T(256); break;
+            }
+#undef HOM_X2T
+            return;
+        }
+    }
     const int grid = (g.n1 * 6 * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2(NF)                                                                  \
     if (inverse) k_x2<R, 1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state); \
@@ -525,7 +754,25 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
 template <typename R>
 void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *in, cpx<R> *out, const cpx<R> *dotv,
                    double *partials, const MinresState *state) {
-    const int grid = x1_grid(g);
+    if constexpr (sizeof(R) == 4) {
+        if (g.tma) {
+            const bool dot = (flags & X1_DOT) != 0;
+            const CUtensorMap *ti = tma_map(g, in, TMA_X1, 1);
+            const CUtensorMap *to = tma_map(g, out, TMA_X1, 1);
+            const CUtensorMap *td = dot ? tma_map(g, dotv, TMA_X1, 1) : ti;
+            const int grid = dot ? g.grid1d_tma : g.grid1_tma;
+            const size_t sm = dot ? g.smem1d_tma : g.smem1_tma;
+#define HOM_X1T(NF) k_x1_tma<R, NF><<<grid, g.threads1, sm, st>>>(g, flags, *ti, *to, *td, partials, state)
+            switch (g.fast[0]) {
+                case 64: HOM_X1T(64); break;
+                case 128: HOM_X1T(128); break;
+                default: HOM_X1T(256); break;
+            }
+#undef HOM_X1T
+            return;
+        }
+    }
+    const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1;
 #define HOM_X1(NF) k_x1<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, flags, in, out, dotv, partials, state)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1)
 #undef HOM_X1

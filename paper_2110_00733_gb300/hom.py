@@ -37,7 +37,8 @@ class hom_options(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("refine", ctypes.c_int),
-                ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int)]
+                ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int),
+                ("staging", ctypes.c_int)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -148,7 +149,7 @@ class Context:
 def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
                smoothing=HOM_SMOOTH_NONE, derivative=HOM_DERIV_ROTATED,
                precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
-               device=-1, refine=3, shape=(0, 0, 0)) -> Context:
+               device=-1, refine=3, shape=(0, 0, 0), staging=0) -> Context:
     lib = load_library()
     opt = hom_options()
     lib.hom_default_options(ctypes.byref(opt))
@@ -158,6 +159,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
     opt.device = device
     opt.refine = refine
     opt.rows3, opt.tile2, opt.tile1 = (int(s) for s in shape)
+    opt.staging = int(staging)
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),

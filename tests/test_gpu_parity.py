@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 E_M, NU_M = 110e9, 0.3
 # several tiles and ragged tails on every axis; odd n3; mixed radices
-SHAPES = [(8, 8, 8), (24, 20, 18), (12, 10, 9), (32, 32, 32), (30, 16, 40), (2, 6, 4), (5, 3, 50)]
+SHAPES = [(8, 8, 8), (24, 20, 18), (12, 10, 9), (32, 32, 32), (30, 16, 40), (2, 6, 4), (5, 3, 50),
+          (64, 64, 12), (128, 64, 10)]   # the last two run the TMA-staged n1/n2 passes in FP32
 PRECS = ["fp32", "fp64"]
 
 
@@ -171,3 +172,33 @@ def test_largest_axis_and_device_pointers(hom):
             assert rel_maxerr(g, oracle.apply(phi2, 1.0, NU_M, 1, f.reshape((6,) + shape2))) <= FP32_TOL
     finally:
         ctx.close()
+
+
+def test_tma_staging_matches_plain_loads(hom):
+    """The persistent TMA-staged n1/n2 passes compute exactly what the plain-
+    load passes compute (same FFT code, different data movement)."""
+    shape = (256, 128, 16)
+    phi = ri.random_phi(shape, seed=8)
+    f = ri.random_field(shape, seed=9).astype(np.float32)
+    outs = []
+    for staging in (0, 1):
+        with hom.hom_create(shape, phi, hom.HOM_INPUT_FRACTION_F64, E_M, NU_M, staging=staging) as ctx:
+            outs.append(hom.hom_apply(ctx, f))
+            spec = hom.hom_fft_forward(ctx, f)
+            outs.append(spec)
+    assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[1], outs[3])
+
+
+def test_solve_tma_octet_matches_oracle(hom):
+    """FP32 solve on a grid whose n1/n2 passes are TMA-staged (64^3 octet)."""
+    phi, _ = ri.octet(64, 0.2)
+    phi = phi.astype(np.float64)
+    Eb = np.array([1.0, 0, 0, 0, 0, 0])
+    ref = oracle.solve(phi, E_M, NU_M, 1, Eb, tol=1e-10, max_it=6000)
+    assert ref["true_residual"] < 1e-9
+    with make(hom, phi, "fp32") as ctx:
+        rc, info = hom.hom_solve(ctx, Eb, tol=1e-7, max_it=6000)
+        assert rc == hom.HOM_OK, info
+        err = np.max(np.abs(info[0]["sigma_mean"] - ref["sigma_mean"])) / np.max(np.abs(ref["sigma_mean"]))
+        assert err <= 1e-4, err
