@@ -145,7 +145,7 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     //  generic engine: Stockham ping-pong, two buffers
     int rows, t2, t1;
     if (g.fast[2]) {
-        rows = 96 / (3 * (g.n3 / fast_elems(g.n3)));
+        rows = 48 / (3 * (g.n3 / fast_elems(g.n3)));
         rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
     } else {
         rows = 16;
@@ -175,7 +175,7 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     const int es3 = (3 * rows) | 1;   // element stride of the n3 tile (odd)
     if (g.fast[2]) {
         g.threads3 = 3 * rows * (g.n3 / fast_elems(g.n3));
-        g.smem3 = (size_t)es3 * g.n3 * cs;
+        g.smem3 = ((size_t)es3 * g.n3 + g.n3 / 16 + 1) * cs;   // + one pad slot per 16 elements
     } else {
         g.threads3 = clampt(round32(3 * rows * g.n3 / 16));
         g.smem3 = 2ull * es3 * g.n3 * cs;

@@ -225,7 +225,12 @@ __host__ __device__ constexpr int fast_elems(int n) {
     return (n == 8 || n == 32 || n == 64) ? 8 : 16;
 }
 
-template <typename R, int S, int N, int RAD, int NS_BEFORE>
+// Position of element e of a line in a tile with element stride ES; with
+// PAD, one slot is skipped every 16 elements so that the stride-16 writes of
+// a radix-16 stage spread over the shared-memory banks.
+template <int PAD> __device__ __forceinline__ int epos(int e, int ES) { return e * ES + (PAD ? (e >> 4) : 0); }
+
+template <typename R, int S, int N, int RAD, int NS_BEFORE, int PAD>
 __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, const cpx<R> *__restrict__ tw) {
     constexpr int E = FastPlan<N>::E;
     constexpr int BPT = E / RAD;
@@ -237,7 +242,7 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, c
     for (int i = 0; i < BPT; ++i) {
         const int j = j0 + i * jstep;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[i][r] = buf[(j + r * nb) * ES + l];
+        for (int r = 0; r < RAD; ++r) v[i][r] = buf[epos<PAD>(j + r * nb, ES) + l];
     }
     __syncthreads();
 #pragma unroll
@@ -255,22 +260,22 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, c
         dft<R, S, RAD>(v[i]);
         const int o = (j - jm) * RAD + jm;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) buf[(o + r * NS_BEFORE) * ES + l] = v[i][r];
+        for (int r = 0; r < RAD; ++r) buf[epos<PAD>(o + r * NS_BEFORE, ES) + l] = v[i][r];
     }
     __syncthreads();
 }
 
 // Transform of L interleaved lines in buf (in place), element e of line l
-// at buf[e * ES + l] (ES >= L).  The CTA must have exactly L * N / E threads
-// (every thread takes part in every barrier).
-template <typename R, int S, int N>
+// at buf[epos<PAD>(e, ES) + l] (ES >= L).  The CTA must have exactly
+// L * N / E threads (every thread takes part in every barrier).
+template <typename R, int S, int N, int PAD = 0>
 __device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R> *__restrict__ tw) {
     using P = FastPlan<N>;
     const int l = (int)threadIdx.x % L;
     const int j0 = (int)threadIdx.x / L;
-    fast_stage<R, S, N, P::R0, 1>(buf, ES, l, j0, tw);
-    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0>(buf, ES, l, j0, tw);
-    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1>(buf, ES, l, j0, tw);
+    fast_stage<R, S, N, P::R0, 1, PAD>(buf, ES, l, j0, tw);
+    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD>(buf, ES, l, j0, tw);
+    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD>(buf, ES, l, j0, tw);
 }
 
 }  // namespace hom

@@ -143,10 +143,10 @@ __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int 
 // Run the transform of the L lines in buf.  Fast engine: in place, returns
 // buf.  Generic engine: ping-pong with buf2, returns the buffer holding the
 // result.
-template <typename R, int S, int NF>
+template <typename R, int S, int NF, int PAD = 0>
 __device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, int ES, const AxisPlan &p) {
     if constexpr (NF > 0) {
-        fast_fft<R, S, NF>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw));
+        fast_fft<R, S, NF, PAD>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw));
         return buf;
     } else {
         return fft_lines<R, S>(buf, buf2, L, ES, p);
@@ -194,10 +194,13 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
-    // stride by ES across a warp and stay free of bank conflicts
+    // stride by ES across a warp and stay free of bank conflicts; the fast
+    // engine also skips one slot every 16 elements (PAD)
+    constexpr int PAD = NF > 0 ? 1 : 0;
     const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, ES = L | 1, H = g.h;
+    auto ep = [ES](int e) { return epos<PAD>(e, ES); };
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
-    cpx<R> *buf2 = buf + N * ES;   // second buffer of the generic engine only
+    cpx<R> *buf2 = buf + ep(N);   // second buffer of the generic engine only
     const int nrows = g.n1 * g.n2;
     const int row0 = blockIdx.x * ROWS;
     const int V = (int)g.V;
@@ -216,13 +219,13 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
                     cpx<R> xa = mk<R>(0, 0), xb = mk<R>(0, 0);
                     if (r < nr) Six<R>::load_pair(row + 6 * k, p, xa, xb);
                     if (selfc) { xa.y = 0; xb.y = 0; }
-                    buf[k * ES + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
-                    if (!selfc) buf[(N - k) * ES + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
+                    buf[ep(k) + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
+                    if (!selfc) buf[ep(N - k) + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
                 }
             }
         }
         __syncthreads();
-        cpx<R> *res = run_fft<R, 1, NF>(buf, buf2, L, ES, g.ax[2]);
+        cpx<R> *res = run_fft<R, 1, NF, PAD>(buf, buf2, L, ES, g.ax[2]);
         if (res != buf) {   // generic engine ended in the second buffer
             for (int i = threadIdx.x; i < N * ES; i += blockDim.x) buf[i] = res[i];
             __syncthreads();
@@ -237,7 +240,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
                 for (int c = 0; c < 6; ++c)
                     t[c] = (r >= nr) ? (R)0 : (in_mode == X3_IN_MACRO ? (R)mac.v[c] : real[c * V + vbase + e]);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) buf[e * ES + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
+                for (int p = 0; p < 3; ++p) buf[ep(e) + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
             }
         }
         __syncthreads();
@@ -248,7 +251,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     for (int r = 0; r < nr; ++r) {
         const int vbase = (row0 + r) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
-            cpx<R> *q = buf + e * ES + r;
+            cpx<R> *q = buf + ep(e) + r;
             R t[6];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
@@ -275,7 +278,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     if (out_mode == X3_OUT_REAL) return;
     // rows beyond nrows hold zeros already (their inputs were zero)
     __syncthreads();
-    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, ES, g.ax[2]);
+    cpx<R> *res = run_fft<R, -1, NF, PAD>(buf, buf2, L, ES, g.ax[2]);
     // unpack the two real transforms of each packed line:
     //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
     cpx<R> *spec = reinterpret_cast<cpx<R> *>(out_);
@@ -285,8 +288,8 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
             const int km = (k == 0) ? 0 : N - k;
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                const cpx<R> z = res[k * ES + p * ROWS + r];
-                const cpx<R> zm = conjc<R>(res[km * ES + p * ROWS + r]);
+                const cpx<R> z = res[ep(k) + p * ROWS + r];
+                const cpx<R> zm = conjc<R>(res[ep(km) + p * ROWS + r]);
                 Six<R>::store_pair(row + 6 * k, p, mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y)),
                                    mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x)));
             }
