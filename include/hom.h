@@ -179,6 +179,33 @@ int hom_project(hom_ctx *ctx, const void *in, void *out);
  * step, w/x/v update.  Returns the number of entries written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
+/* A(eps) of hom_apply for a small cell, allocating no device memory.  The
+ * paper has no counterpart: this is a calling convention for callers that
+ * must not call cudaMalloc -- a thread recording a CUDA graph by stream
+ * capture (cudaMalloc is not permitted while capturing and may synchronise
+ * the device), or an application whose device memory belongs to its own pool
+ * and which forbids stray allocations.  hom_create allocates its workspace,
+ * so those callers use this entry point instead.
+ *   grid[3]     n1, n2, n3, each in [2, 64] and 2^a 3^b 5^c, with
+ *               n1 n2 n3 <= 32768 (for example 32^3); larger grids give
+ *               HOM_EUNSUPPORTED_GRID.
+ *   phi         device pointer, V floats in [0,1] (not checked here).
+ *   E, nu       as hom_create; the operator uses C_m / E (units of E).
+ *   derivative  HOM_DERIV_CONTINUOUS or HOM_DERIV_ROTATED.
+ *   eps, out    device pointers, 6 x V floats, MANDEL fields; FP32.
+ *   stream      cudaStream_t (NULL: the legacy default stream); the call
+ *               returns after synchronising it.
+ * The work spectrum and the FFT tables live in fixed file-scope device arrays
+ * (about 1.6 MB, held on every GPU that loads the library until the process
+ * exits).  The first call on a device looks up their device addresses
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the arrays: calls whose device
+ * work overlaps in time race and must not be issued.  Nothing is kept
+ * between calls.  Errors: HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ECUDA, with
+ * hom_last_error(NULL) describing them. */
+int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, int derivative,
+                      const float *eps, float *out, void *stream);
+
 /* Grid, precision and workspace size of a context. */
 int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes);
 

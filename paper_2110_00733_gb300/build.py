@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libhom.so")
-SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu"]
+SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu", "hom_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

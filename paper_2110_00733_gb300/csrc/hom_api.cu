@@ -90,6 +90,11 @@ struct hom_ctx {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// message for hom_last_error(NULL) from entry points that take no context
+namespace hom {
+void hom_set_error(const char *msg) { g_create_error = msg ? msg : ""; }
+}  // namespace hom
+
 static int fail(hom_ctx *c, int code, const std::string &m) {
     if (c) c->err = m;
     else g_create_error = m;

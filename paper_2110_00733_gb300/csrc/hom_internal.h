@@ -135,6 +135,8 @@ void mandel_scale64(long long V, cudaStream_t st, double *f, double s);
 template <typename R>
 void phi_convert(long long V, cudaStream_t st, const void *in, int kind, R *out, int *bad);
 int ew_blocks(long long n);
+// sets the message hom_last_error(NULL) returns
+void hom_set_error(const char *msg);
 
 // single-CTA scalar kernels
 void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it);

@@ -29,7 +29,7 @@ EXPORTED = [
     "hom_default_options", "hom_create", "hom_solve", "hom_effective_stiffness",
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
-    "hom_last_error",
+    "hom_last_error", "hom_apply_noalloc",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.hom_fft_inverse.argtypes = [vp, vp, vp]
     lib.hom_project.argtypes = [vp, vp, vp]
     lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    lib.hom_apply_noalloc.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.hom_get_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
     lib.hom_kernel_launches.argtypes = [vp]
     lib.hom_kernel_launches.restype = ctypes.c_longlong
@@ -275,3 +276,13 @@ def hom_destroy(ctx: Context):
 def hom_last_error(ctx: Context | None = None) -> str:
     s = load_library().hom_last_error(ctx.handle if ctx else None)
     return s.decode() if s else ""
+
+
+def hom_apply_noalloc(grid, phi, eps, out, E=1.0, nu=0.3, derivative=HOM_DERIV_ROTATED, stream=None):
+    """A(eps) for a small cell without device allocation; phi, eps, out are
+    torch CUDA tensors (float32) on the current device."""
+    lib = load_library()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    rc = lib.hom_apply_noalloc(g, _ptr(phi), float(E), float(nu), int(derivative), _ptr(eps), _ptr(out), stream)
+    _check(None, rc)
+    return out
