@@ -77,6 +77,10 @@ def _load():
                                   dp, dp, dp, dp]
         lib.orc_solve.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_modb_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_modb_rhs.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_modb_precond.argtypes = [ip, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_modb_fields.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
         _lib = lib
         return lib
 
@@ -261,3 +265,82 @@ def effective_stiffness(phi, E, nu, deriv, tol=1e-10, max_it=5000):
         C[:, J] = s["sigma_mean"] / gamma
         sols.append(s)
     return C, sols
+
+
+# --------------------------------------------------------------------------
+# MoDBFFT (section 2.2): penalised displacement FFT, strain control
+# --------------------------------------------------------------------------
+
+def _c(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a, a.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def modb_apply(phi, E, nu, alpha, u_hat) -> np.ndarray:
+    """A^alpha(u^) of eq. (modbfftfop); u_hat: (3, N1, N2, N3) full complex spectrum."""
+    lib = _load()
+    p = _phi(phi)
+    u, up = _c(np.asarray(u_hat).reshape((3,) + p.shape))
+    out = np.zeros_like(u)
+    lib.orc_modb_apply(_ip(p.shape), _dp(p), float(E), float(nu), float(alpha), up,
+                       out.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def modb_rhs(phi, E, nu, Ebar_tensor) -> np.ndarray:
+    """b^alpha of eq. (modbfftfrhs) for a macro strain (tensor comps)."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    out = np.zeros((3,) + p.shape, dtype=np.complex128)
+    lib.orc_modb_rhs(_ip(p.shape), _dp(p), float(E), float(nu), _dp(Eb),
+                     out.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def modb_precond(shape, phibar, E, nu, v) -> np.ndarray:
+    """[xi . Cbar . xi]^-1 v of eq. (precf), Cbar = phibar C_m."""
+    lib = _load()
+    vv, vp = _c(np.asarray(v).reshape((3,) + tuple(shape)))
+    out = np.zeros_like(vv)
+    lib.orc_modb_precond(_ip(shape), float(phibar), float(E), float(nu), vp,
+                         out.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def modb_fields(phi, E, nu, Ebar_tensor, u_hat):
+    """(fluctuation strain 6xV Mandel, mean stress tensor comps) of a solution."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    u, up = _c(np.asarray(u_hat).reshape((3,) + p.shape))
+    eps = np.zeros((6,) + p.shape)
+    sig = np.zeros(6)
+    lib.orc_modb_fields(_ip(p.shape), _dp(p), float(E), float(nu), _dp(Eb), up, _dp(eps), _dp(sig))
+    return eps, mandel_to_tensor(sig)
+
+
+def modb_solve_dense(phi, E, nu, alpha, Ebar_tensor):
+    """Direct solve of the MoDBFFT system on a small grid.  The unknown is a
+    real displacement fluctuation (its DFT is Hermitian), so the operator of
+    eq. (modbfftfop) is assembled over the real basis of 3 x V displacement
+    values: column j is the inverse DFT of A^alpha(DFT(e_j)).  Frequencies
+    with xi = 0 carry no equation, which leaves a null space (rigid
+    translations and the all-Nyquist modes); the minimum-norm least-squares
+    solution removes it.  Returns (u_hat, mean stress tensor comps)."""
+    p = _phi(phi)
+    shape = p.shape
+    V = p.size
+    n = 3 * V
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        uh = np.fft.fftn(e.reshape((3,) + shape), axes=(1, 2, 3))
+        r = modb_apply(p, E, nu, alpha, uh)
+        A[:, j] = np.real(np.fft.ifftn(r, axes=(1, 2, 3))).reshape(-1)
+    b = np.real(np.fft.ifftn(modb_rhs(p, E, nu, Ebar_tensor), axes=(1, 2, 3))).reshape(-1)
+    u = np.linalg.lstsq(A, b, rcond=1e-12)[0]
+    uh = np.fft.fftn(u.reshape((3,) + shape), axes=(1, 2, 3))
+    eps, sig = modb_fields(p, E, nu, Ebar_tensor, uh)
+    return uh, sig

@@ -530,3 +530,188 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* MoDBFFT (section 2.2): penalised displacement FFT, strain control.         */
+/* Unknown: the DFT of the displacement fluctuation, 3 complex components per */
+/* frequency (full spectrum here), continuous frequencies of eq. (freq) with  */
+/* the Nyquist component of xi set to 0.  Frequencies with xi = 0 carry no    */
+/* unknown (u^ = 0 there) and no equation.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* continuous xi with the Nyquist components zeroed */
+static void modb_xi(const int n[3], const int k[3], cplx xi[3]) {
+    for (int p = 0; p < 3; ++p) {
+        double q = 2.0 * PI * signed_index(k[p], n[p]) / n[p];
+        xi[p] = is_nyquist(k[p], n[p]) ? 0.0 : I * q * n[p];
+    }
+}
+
+static int xi_zero(const cplx xi[3]) { return xi[0] == 0.0 && xi[1] == 0.0 && xi[2] == 0.0; }
+
+/* out = A^alpha(u^), eq. (modbfftfop) without the stress-control rows:
+ *   F{ (1 - chi_v) C : F^-1{ u^ (x)^s xi } } . xi + F{ chi_v F^-1{ alpha (u^ (x)^s xi) . xi } }
+ * with chi_v = [phi == 0] (eq. indicator) and C = phi C_m.  u, out: 3 x V
+ * complex (re,im), full spectrum.  alpha in the units of E. */
+void orc_modb_apply(const int n[3], const double *phi, double E, double nu, double alpha,
+                    const double *u_ri, double *out_ri) {
+    long V = (long)n[0] * n[1] * n[2];
+    const cplx *u = (const cplx *)u_ri;
+    cplx *out = (cplx *)out_ri;
+    double Cm[36];
+    orc_stiffness_mandel(E, nu, Cm);
+    cplx *eps = (cplx *)malloc(sizeof(cplx) * 6 * V);   /* Mandel */
+    cplx *g = (cplx *)malloc(sizeof(cplx) * 3 * V);
+    const double r2 = sqrt(2.0);
+    /* strain sym(u (x) xi) and penalty vector alpha sym(u (x) xi) . xi per frequency */
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n[1] * n[2])), (int)((f / n[2]) % n[1]), (int)(f % n[2])};
+        cplx xi[3], uu[3], e[3][3];
+        modb_xi(n, k, xi);
+        int zero = xi_zero(xi);
+        for (int i = 0; i < 3; ++i) uu[i] = zero ? 0.0 : u[(long)i * V + f];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) e[i][j] = 0.5 * (uu[i] * xi[j] + uu[j] * xi[i]);
+        for (int c = 0; c < 6; ++c) eps[(long)c * V + f] = (c < 3) ? e[MI[c]][MJ[c]] : r2 * e[MI[c]][MJ[c]];
+        for (int i = 0; i < 3; ++i) {
+            cplx s = 0;
+            for (int j = 0; j < 3; ++j) s += e[i][j] * xi[j];
+            g[(long)i * V + f] = alpha * s;
+        }
+    }
+    for (int c = 0; c < 6; ++c) orc_fft3d(n, (double *)(eps + (long)c * V), +1);
+    for (int c = 0; c < 3; ++c) orc_fft3d(n, (double *)(g + (long)c * V), +1);
+    /* real space: tau = phi C_m : eps, h = chi_v g  (the 1/V of the inverse DFT applied here) */
+    for (long x = 0; x < V; ++x) {
+        double ev[6], tv[6];
+        for (int c = 0; c < 6; ++c) ev[c] = creal(eps[(long)c * V + x]) / (double)V;
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * ev[j];
+            tv[i] = phi[x] * s;
+        }
+        for (int c = 0; c < 6; ++c) eps[(long)c * V + x] = tv[c];
+        double chi = (phi[x] == 0.0) ? 1.0 : 0.0;
+        for (int c = 0; c < 3; ++c) g[(long)c * V + x] = chi * creal(g[(long)c * V + x]) / (double)V;
+    }
+    for (int c = 0; c < 6; ++c) orc_fft3d(n, (double *)(eps + (long)c * V), -1);
+    for (int c = 0; c < 3; ++c) orc_fft3d(n, (double *)(g + (long)c * V), -1);
+    /* out = tau^ . xi + h^, zero where xi = 0 */
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n[1] * n[2])), (int)((f / n[2]) % n[1]), (int)(f % n[2])};
+        cplx xi[3], tm[6], t[3][3];
+        modb_xi(n, k, xi);
+        if (xi_zero(xi)) {
+            for (int i = 0; i < 3; ++i) out[(long)i * V + f] = 0.0;
+            continue;
+        }
+        for (int c = 0; c < 6; ++c) tm[c] = eps[(long)c * V + f];
+        mandel_to_tensor(tm, t);
+        for (int i = 0; i < 3; ++i) {
+            cplx s = g[(long)i * V + f];
+            for (int j = 0; j < 3; ++j) s += t[i][j] * xi[j];
+            out[(long)i * V + f] = s;
+        }
+    }
+    free(eps);
+    free(g);
+}
+
+/* b^ = -F{ C : E_bar } . xi  (eq. modbfftfrhs, sigma_bar = 0), 3 x V complex */
+void orc_modb_rhs(const int n[3], const double *phi, double E, double nu, const double Ebar[6],
+                  double *out_ri) {
+    long V = (long)n[0] * n[1] * n[2];
+    cplx *out = (cplx *)out_ri;
+    double Cm[36], s[6];
+    orc_stiffness_mandel(E, nu, Cm);
+    for (int i = 0; i < 6; ++i) {
+        s[i] = 0;
+        for (int j = 0; j < 6; ++j) s[i] += Cm[i * 6 + j] * Ebar[j];
+    }
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
+    for (int c = 0; c < 6; ++c)
+        for (long x = 0; x < V; ++x) tau[(long)c * V + x] = phi[x] * s[c];
+    for (int c = 0; c < 6; ++c) orc_fft3d(n, (double *)(tau + (long)c * V), -1);
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n[1] * n[2])), (int)((f / n[2]) % n[1]), (int)(f % n[2])};
+        cplx xi[3], tm[6], t[3][3];
+        modb_xi(n, k, xi);
+        for (int c = 0; c < 6; ++c) tm[c] = tau[(long)c * V + f];
+        mandel_to_tensor(tm, t);
+        for (int i = 0; i < 3; ++i) {
+            cplx v = 0;
+            if (!xi_zero(xi))
+                for (int j = 0; j < 3; ++j) v += t[i][j] * xi[j];
+            out[(long)i * V + f] = -v;
+        }
+    }
+    free(tau);
+}
+
+/* Preconditioner of eq. (precf): out(k) = [xi . Cbar . xi]^-1 in(k), Cbar =
+ * <phi> C_m (eq. avstiff), solved per frequency by Gaussian elimination;
+ * zero where xi = 0. */
+void orc_modb_precond(const int n[3], double phibar, double E, double nu, const double *in_ri,
+                      double *out_ri) {
+    long V = (long)n[0] * n[1] * n[2];
+    const cplx *in = (const cplx *)in_ri;
+    cplx *out = (cplx *)out_ri;
+    double lam = phibar * E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double mu = phibar * E / (2.0 * (1.0 + nu));
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n[1] * n[2])), (int)((f / n[2]) % n[1]), (int)(f % n[2])};
+        cplx xi[3], K[3][3], v[3], u[3];
+        modb_xi(n, k, xi);
+        if (xi_zero(xi)) {
+            for (int i = 0; i < 3; ++i) out[(long)i * V + f] = 0.0;
+            continue;
+        }
+        /* (xi . C . xi)_ik = sum_jl xi_j C_ijkl xi_l, isotropic C */
+        cplx xx = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+        for (int i = 0; i < 3; ++i)
+            for (int kk = 0; kk < 3; ++kk)
+                K[i][kk] = (lam + mu) * xi[i] * xi[kk] + (i == kk ? mu * xx : 0.0);
+        for (int i = 0; i < 3; ++i) v[i] = in[(long)i * V + f];
+        if (!solve3(K, v, u)) u[0] = u[1] = u[2] = 0.0;
+        for (int i = 0; i < 3; ++i) out[(long)i * V + f] = u[i];
+    }
+}
+
+/* Fluctuation strain F^-1{ u^ (x)^s xi } (6 x V Mandel, real part) and the
+ * mean stress <C : (E_bar + eps)> (Mandel) of a MoDBFFT solution. */
+void orc_modb_fields(const int n[3], const double *phi, double E, double nu, const double Ebar[6],
+                     const double *u_ri, double *eps_out, double sig_mean[6]) {
+    long V = (long)n[0] * n[1] * n[2];
+    const cplx *u = (const cplx *)u_ri;
+    cplx *e6 = (cplx *)malloc(sizeof(cplx) * 6 * V);
+    const double r2 = sqrt(2.0);
+    for (long f = 0; f < V; ++f) {
+        int k[3] = {(int)(f / ((long)n[1] * n[2])), (int)((f / n[2]) % n[1]), (int)(f % n[2])};
+        cplx xi[3], uu[3];
+        modb_xi(n, k, xi);
+        int zero = xi_zero(xi);
+        for (int i = 0; i < 3; ++i) uu[i] = zero ? 0.0 : u[(long)i * V + f];
+        for (int c = 0; c < 6; ++c) {
+            cplx v = 0.5 * (uu[MI[c]] * xi[MJ[c]] + uu[MJ[c]] * xi[MI[c]]);
+            e6[(long)c * V + f] = (c < 3) ? v : r2 * v;
+        }
+    }
+    for (int c = 0; c < 6; ++c) orc_fft3d(n, (double *)(e6 + (long)c * V), +1);
+    double Cm[36];
+    orc_stiffness_mandel(E, nu, Cm);
+    for (int i = 0; i < 6; ++i) sig_mean[i] = 0.0;
+    for (long x = 0; x < V; ++x) {
+        double ev[6];
+        for (int c = 0; c < 6; ++c) {
+            ev[c] = creal(e6[(long)c * V + x]) / (double)V;
+            eps_out[(long)c * V + x] = ev[c];
+        }
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * (Ebar[j] + ev[j]);
+            sig_mean[i] += phi[x] * s;
+        }
+    }
+    for (int i = 0; i < 6; ++i) sig_mean[i] /= (double)V;
+    free(e6);
+}
