@@ -73,7 +73,8 @@ enum { HOM_INPUT_PHASE_U8 = 0,      /* uint8 phase id: 0 empty, nonzero solid */
 enum { HOM_SMOOTH_NONE = 0 };       /* phi used as given (plain or Voigt-smoothed) */
 enum { HOM_DERIV_CONTINUOUS = 0,    /* xi_p = i q_p N_p, eq. (freq) */
        HOM_DERIV_ROTATED = 1 };     /* rotated forward difference, eq. (freqrot) */
-enum { HOM_SOLVER_GALERKIN_MINRES = 0 };
+enum { HOM_SOLVER_GALERKIN_MINRES = 0,   /* section 2.1 */
+       HOM_SOLVER_MODBFFT_CG = 1 };      /* section 2.2: penalised displacement FFT, PCG */
 enum { HOM_PREC_FP32_FIELDS = 0,    /* FP32 fields and FFTs, FP64 Krylov scalars */
        HOM_PREC_FP64 = 1 };         /* FP64 everywhere */
 
@@ -91,6 +92,7 @@ typedef struct {
     int tile1;          /* launch shape: n1-pass columns per CTA (0 = automatic, <= 16) */
     int staging;        /* 0: persistent TMA-staged n1/n2 passes where supported
                            (FP32, power-of-two n1, n2 in [64, 256]); 1: plain loads */
+    double alpha;       /* MoDBFFT penalty alpha / E (0: 1e-4, section 4.2) */
 } hom_options;
 
 typedef struct {
@@ -121,7 +123,10 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
                double E, double nu, int smoothing, int derivative,
                const hom_options *opt);
 
-/* Solve eq. (gallin) for ncase macro strains (strain control).
+/* Solve eq. (gallin) for ncase macro strains (strain control) -- or, for a
+ * context created with HOM_SOLVER_MODBFFT_CG, the MoDBFFT system of
+ * eqs. (modbfftf)/(modbfftfop) by preconditioned CG (section 2.2), with
+ * est_residual / true_residual the ratio of eq. (modbfftresres).
  *   macro_strain  ncase x 6 tensor components, host memory.
  *   tol           relative residual of eq. (galres), e.g. 1e-6.
  *   max_it        MINRES iteration cap per case (per refinement sweep).
@@ -205,6 +210,21 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
  * hom_last_error(NULL) describing them. */
 int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, int derivative,
                       const float *eps, float *out, void *stream);
+
+/* MoDBFFT step entry points (contexts created with HOM_SOLVER_MODBFFT_CG).
+ * A "displacement spectrum" is n1 x n2 x (n3/2+1) x 3 complex values: the
+ * DFT of a real displacement fluctuation, with continuous frequencies
+ * (eq. freq) whose Nyquist components are 0; frequencies with xi = 0 carry
+ * no unknown.  Units of E. */
+
+/* out = A^alpha(u), eq. (modbfftfop) with strain control. */
+int hom_modb_apply(hom_ctx *ctx, const void *u_spectrum, void *out_spectrum);
+
+/* out = b^alpha for one macro strain (6 tensor components), eq. (modbfftfrhs). */
+int hom_modb_rhs(hom_ctx *ctx, const double macro_strain[6], void *out_spectrum);
+
+/* out = [xi . Cbar . xi]^-1 in, eq. (precf) with Cbar = <phi> C_m (eq. avstiff). */
+int hom_modb_precond(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum);
 
 /* Grid, precision and workspace size of a context. */
 int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes);

@@ -35,8 +35,10 @@ struct Status {
 // Per-precision engine: tables, phase map and spectrum workspace of one cell.
 template <typename R> struct Engine {
     Geometry g{};
+    Geometry gm{};             // MoDBFFT chain: 10 components per frequency
     R *phi = nullptr;
     cpx<R> *spec = nullptr;
+    cpx<R> *spec10 = nullptr;  // MoDBFFT work spectrum
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *D[3] = {nullptr, nullptr, nullptr};
     void *M[3] = {nullptr, nullptr, nullptr};
@@ -58,6 +60,13 @@ struct hom_ctx {
     int refine = 3;
     int shape[3] = {0, 0, 0};   // launch-shape overrides (rows3, tile2, tile1)
     int staging = 0;            // 0: TMA-staged passes where supported, 1: plain loads
+    int solver = HOM_SOLVER_GALERKIN_MINRES;
+    double alpha = 1e-4;        // MoDBFFT penalty / E
+    double phibar = 0.0;        // mean of phi (MoDBFFT preconditioner, eq. avstiff)
+    CgState *d_cg = nullptr;
+    CgState *h_cg = nullptr;    // pinned
+    cudaGraphExec_t cg_graph = nullptr;
+    long long cg_graph_kernels = 0;
     int *d_err = nullptr;       // set by a pass whose bounded wait gave up
     Engine<float> e32;
     Engine<double> e64;
@@ -134,27 +143,22 @@ static bool factor_radices(int n, AxisPlan &p) {
 
 template <typename R> static size_t cpx_size() { return sizeof(R) * 2; }
 
+// Launch shapes of the three passes for a spectrum with nc components per
+// frequency (defaults; hom_options may override them -- autotuner hook).
+//  fast engine: threads = lines * n / E, one buffer of lines * n values
+//  generic engine: Stockham ping-pong, two buffers
 template <typename R>
-static int engine_init(hom_ctx *ctx, Engine<R> &E) {
-    Geometry &g = E.g;
-    g.n1 = ctx->n[0];
-    g.n2 = ctx->n[1];
-    g.n3 = ctx->n[2];
-    g.h = g.n3 / 2 + 1;
-    g.V = ctx->V;
-    g.S = ctx->S;
+static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     const size_t cs = cpx_size<R>();
-    for (int p = 0; p < 3; ++p) g.fast[p] = is_fast_length(ctx->n[p]) ? ctx->n[p] : 0;
-    // launch shapes (defaults; hom_options may override them -- autotuner hook)
-    //  fast engine: threads = lines * n / E, one buffer of lines * n values
-    //  generic engine: Stockham ping-pong, two buffers
+    const int np = nc / 2;   // component pairs of the n3 pass
+    g.nc = nc;
     int rows, t2, t1;
     if (g.fast[2]) {
-        rows = 48 / (3 * (g.n3 / fast_elems(g.n3)));
+        rows = 48 / (np * (g.n3 / fast_elems(g.n3)));
         rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
     } else {
         rows = 16;
-        while (rows > 1 && 2ull * g.n3 * 3 * rows * cs > 48 * 1024) rows >>= 1;
+        while (rows > 1 && 2ull * g.n3 * np * rows * cs > 48 * 1024) rows >>= 1;
     }
     if (g.fast[1]) {
         t2 = g.n2 >= 128 ? 16 : 32;
@@ -163,26 +167,28 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
         while (t2 > 1 && 2ull * g.n2 * t2 * cs > 64 * 1024) t2 >>= 1;
     }
     if (g.fast[0]) {
-        t1 = 192 * fast_elems(g.n1) / (6 * g.n1);
+        t1 = 192 * fast_elems(g.n1) / (nc * g.n1);
         t1 = t1 < 1 ? 1 : (t1 > 16 ? 16 : t1);
     } else {
         t1 = 16;
-        while (t1 > 1 && 2ull * g.n1 * 6 * t1 * cs > 96 * 1024) t1 >>= 1;
+        while (t1 > 1 && 2ull * g.n1 * nc * t1 * cs > 96 * 1024) t1 >>= 1;
     }
-    if (ctx->shape[0] > 0) rows = ctx->shape[0];
-    if (ctx->shape[1] > 0) t2 = ctx->shape[1];
-    if (ctx->shape[2] > 0) t1 = ctx->shape[2];
+    if (nc == 6) {
+        if (ctx->shape[0] > 0) rows = ctx->shape[0];
+        if (ctx->shape[1] > 0) t2 = ctx->shape[1];
+        if (ctx->shape[2] > 0) t1 = ctx->shape[2];
+    }
     g.rows3 = rows;
     g.tile2 = t2;
     g.tile1 = t1;
     auto round32 = [](int v) { return (v + 31) / 32 * 32; };
     auto clampt = [](int v) { return v < 128 ? 128 : (v > 512 ? 512 : v); };
-    const int es3 = (3 * rows) | 1;   // element stride of the n3 tile (odd)
+    const int es3 = (np * rows) | 1;   // element stride of the n3 tile (odd)
     if (g.fast[2]) {
-        g.threads3 = 3 * rows * (g.n3 / fast_elems(g.n3));
+        g.threads3 = np * rows * (g.n3 / fast_elems(g.n3));
         g.smem3 = ((size_t)es3 * g.n3 + g.n3 / 16 + 1) * cs;   // + one pad slot per 16 elements
     } else {
-        g.threads3 = clampt(round32(3 * rows * g.n3 / 16));
+        g.threads3 = clampt(round32(np * rows * g.n3 / 16));
         g.smem3 = 2ull * es3 * g.n3 * cs;
     }
     if (g.fast[1]) {
@@ -192,7 +198,7 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
         g.threads2 = clampt(round32(t2 * g.n2 / 16));
         g.smem2 = 2ull * t2 * g.n2 * cs;
     }
-    const int L1 = 6 * t1;
+    const int L1 = nc * t1;
     if (g.fast[0]) {
         g.threads1 = L1 * (g.n1 / fast_elems(g.n1));
         g.smem1 = (size_t)L1 * g.n1 * cs;
@@ -208,6 +214,34 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     if (g.threads1 > 512 || g.threads2 > 512 || g.threads3 > 512 || g.threads1 < 1 || g.threads2 < 1 || g.threads3 < 1)
         return fail(ctx, HOM_EINVAL, "launch shape needs more than 512 threads per CTA");
     if ((t2 & (t2 - 1)) != 0 || g.threads2 % t2 != 0) return fail(ctx, HOM_EINVAL, "tile2 must be a power of two");
+    // persistent TMA-staged n2 / n1 passes: FP32, register-FFT lengths <= 256
+    g.tma = 0;
+    g.err = ctx->d_err;
+    g.tma_cache = nullptr;
+    if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 256 &&
+        g.fast[1] >= 64 && g.fast[1] <= 256 && g.tile2 % 2 == 0) {
+        g.tma = 1;
+        g.smem2_tma = 2ull * g.n2 * g.tile2 * cs;
+        g.smem1_tma = 2ull * nc * g.tile1 * g.n1 * cs;
+        g.smem1d_tma = 2 * g.smem1_tma;
+        if (g.smem1d_tma + 1024 > (size_t)dev_smem || g.smem2_tma + 1024 > (size_t)dev_smem) g.tma = 0;
+        if (g.tma && Launch<R>::tma_grids(g)) g.tma_cache = tma_cache_new();
+        else g.tma = 0;
+    }
+    return HOM_OK;
+}
+
+template <typename R>
+static int engine_init(hom_ctx *ctx, Engine<R> &E) {
+    Geometry &g = E.g;
+    g.n1 = ctx->n[0];
+    g.n2 = ctx->n[1];
+    g.n3 = ctx->n[2];
+    g.h = g.n3 / 2 + 1;
+    g.V = ctx->V;
+    g.S = ctx->S;
+    const size_t cs = cpx_size<R>();
+    for (int p = 0; p < 3; ++p) g.fast[p] = is_fast_length(ctx->n[p]) ? ctx->n[p] : 0;
     const double PI = 3.14159265358979323846;
     for (int p = 0; p < 3; ++p) {
         const int N = ctx->n[p];
@@ -246,20 +280,8 @@ static int engine_init(hom_ctx *ctx, Engine<R> &E) {
     CU(cudaMalloc(&E.spec, cs * 6 * ctx->S));
     ctx->workspace += sizeof(R) * ctx->V + cs * 6 * ctx->S;
     Launch<R>::table_init(g);
-    // persistent TMA-staged n2 / n1 passes: FP32, register-FFT lengths <= 256
-    g.tma = 0;
-    g.err = ctx->d_err;
-    g.tma_cache = nullptr;
-    if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 256 &&
-        g.fast[1] >= 64 && g.fast[1] <= 256 && g.tile2 % 2 == 0) {
-        g.tma = 1;
-        g.smem2_tma = 2ull * g.n2 * g.tile2 * cs;
-        g.smem1_tma = 2ull * 6 * g.tile1 * g.n1 * cs;
-        g.smem1d_tma = 2 * g.smem1_tma;
-        if (g.smem1d_tma + 1024 > (size_t)dev_smem || g.smem2_tma + 1024 > (size_t)dev_smem) g.tma = 0;
-        if (g.tma && Launch<R>::tma_grids(g)) g.tma_cache = tma_cache_new();
-        else g.tma = 0;
-    }
+    int rc = set_shapes<R>(ctx, g, 6);
+    if (rc) return rc;
     CU(cudaGetLastError());
     return HOM_OK;
 }
@@ -268,6 +290,9 @@ template <typename R>
 static void engine_free(Engine<R> &E) {
     tma_cache_free(E.g.tma_cache);
     E.g.tma_cache = nullptr;
+    tma_cache_free(E.gm.tma_cache);
+    E.gm.tma_cache = nullptr;
+    cudaFree(E.spec10);
     for (int p = 0; p < 3; ++p) {
         cudaFree(E.tw[p]);
         cudaFree(E.D[p]);
@@ -418,6 +443,140 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     return HOM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// MoDBFFT (section 2.2)
+// ---------------------------------------------------------------------------
+template <typename R>
+static int engine_init_modb(hom_ctx *ctx, Engine<R> &E) {
+    E.gm = E.g;
+    E.gm.tma_cache = nullptr;
+    int rc = set_shapes<R>(ctx, E.gm, 10);
+    if (rc) return rc;
+    CU(cudaMalloc(&E.spec10, cpx_size<R>() * 10 * ctx->S));
+    ctx->workspace += cpx_size<R>() * 10 * ctx->S;
+    return HOM_OK;
+}
+
+// out3 = A^alpha(u3), eq. (modbfftfop); optional <dotv, out3> partials
+template <typename R>
+static void op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, const cpx<R> *dotv, double *partials,
+                    const MinresState *st) {
+    cudaStream_t s = ctx->stream;
+    const Geometry &g = E.gm;
+    Launch<R>::modb_expand(g, s, ctx->alpha, 1, u, E.spec10, 10, st);
+    Launch<R>::x1(g, s, 0, E.spec10, E.spec10, nullptr, nullptr, st);
+    Launch<R>::x2(g, s, 1, E.spec10, st);
+    Launch<R>::x3(g, s, X3_IN_SPEC, E.spec10, X3_MID_MODB, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec10,
+                  E.phi, st);
+    Launch<R>::x2(g, s, 0, E.spec10, st);
+    Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, st);
+    Launch<R>::modb_contract(g, s, E.spec10, out, dotv, partials, st);
+    ctx->launches += 7;
+}
+
+// b3 = -F{C : E_bar} . xi, eq. (modbfftfrhs) with sigma_bar = 0
+template <typename R>
+static void rhs_modb(hom_ctx *ctx, Engine<R> &E, const double *macro_mandel, cpx<R> *b) {
+    cudaStream_t s = ctx->stream;
+    const Geometry &g = E.gm;
+    Launch<R>::x3(g, s, X3_IN_MACRO, nullptr, X3_MID_MATERIAL, ctx->lam, ctx->mu, macro_mandel, -1.0, X3_OUT_SPEC,
+                  E.spec10, E.phi, nullptr);
+    Launch<R>::x2(g, s, 0, E.spec10, nullptr);
+    Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, nullptr);
+    Launch<R>::modb_contract(g, s, E.spec10, b, nullptr, nullptr, nullptr);
+    ctx->launches += 4;
+}
+
+// mean stiffness of eq. (avstiff) in units of E
+static void cbar(const hom_ctx *ctx, double *lam_b, double *mu_b) {
+    *lam_b = ctx->phibar * ctx->lam;
+    *mu_b = ctx->phibar * ctx->mu;
+}
+
+// One PCG iteration per graph replay: q = A p (with <p, q>), step, x/r/z,
+// direction.  Buffers: x = xs, r = vbuf[0], p = vbuf[1], q = vbuf[2], z = wbuf[0].
+template <typename R>
+static int build_cg_graph(hom_ctx *ctx, Engine<R> &E) {
+    if (ctx->cg_graph) return HOM_OK;
+    cpx<R> *x = (cpx<R> *)ctx->xs, *r = (cpx<R> *)ctx->vbuf[0], *p = (cpx<R> *)ctx->vbuf[1];
+    cpx<R> *q = (cpx<R> *)ctx->vbuf[2], *z = (cpx<R> *)ctx->wbuf[0];
+    const int np = Launch<R>::ew_grid(E.g.S);
+    const MinresState *flags = reinterpret_cast<const MinresState *>(ctx->d_cg);
+    double lam_b, mu_b;
+    cbar(ctx, &lam_b, &mu_b);
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = ctx->launches;
+    for (int it = 0; it < 4; ++it) {
+        op_modb<R>(ctx, E, p, q, p, ctx->partials, flags);
+        scalar_cg_alpha(ctx->stream, ctx->d_cg, ctx->partials, np);
+        Launch<R>::cg_xr(E.g, ctx->stream, lam_b, mu_b, x, r, p, q, z, ctx->d_cg, ctx->partials);
+        scalar_cg_beta(ctx->stream, ctx->d_cg, ctx->partials, np);
+        Launch<R>::cg_p(E.g, ctx->stream, p, z, ctx->d_cg);
+        ctx->launches += 4;
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ctx->cg_graph_kernels = ctx->launches - before;
+    ctx->launches = before;
+    e = cudaGraphInstantiate(&ctx->cg_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HOM_OK;
+}
+
+// PCG on A^alpha x = rhs (ctx->rhs, 3-component spectrum), zero start;
+// solution in ctx->xs.  As the paper does (section 2.2) the preconditioned CG
+// recurrences are used although A^alpha is not symmetric where chi_v is
+// non-zero; the FP64 true residual checks the result.
+template <typename R>
+static int run_cg(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters, double *est, int *status) {
+    const long long nr = 6 * ctx->S;   // reals per 3-component spectral vector
+    cudaStream_t s = ctx->stream;
+    int rc = build_cg_graph<R>(ctx, E);
+    if (rc) return rc;
+    cpx<R> *x = (cpx<R> *)ctx->xs, *r = (cpx<R> *)ctx->vbuf[0], *p = (cpx<R> *)ctx->vbuf[1];
+    cpx<R> *q = (cpx<R> *)ctx->vbuf[2], *z = (cpx<R> *)ctx->wbuf[0];
+    double lam_b, mu_b;
+    cbar(ctx, &lam_b, &mu_b);
+    CU(cudaMemsetAsync(x, 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(p, 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(q, 0, sizeof(R) * nr, s));
+    CU(cudaMemcpyAsync(r, ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
+    // z0 = M r0 and <r0, z0>, ||r0||^2 through one step of length 0
+    memset(ctx->h_cg, 0, sizeof(CgState));
+    CU(cudaMemcpyAsync(ctx->d_cg, ctx->h_cg, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    const int np = Launch<R>::ew_grid(E.g.S);
+    Launch<R>::cg_xr(E.g, s, lam_b, mu_b, x, r, p, q, z, ctx->d_cg, ctx->partials);
+    scalar_cg_start(s, ctx->d_cg, ctx->partials, np, tol, max_it);
+    Launch<R>::cg_p(E.g, s, p, z, ctx->d_cg);   // p0 = z0 (b = 0)
+    ctx->launches += 3;
+    CU(cudaMemcpyAsync(ctx->h_cg, ctx->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (ctx->h_cg->done) {
+        *iters = 0;
+        *est = 0.0;
+        *status = ctx->h_cg->status == -5 ? HOM_ENAN : HOM_OK;
+        return HOM_OK;
+    }
+    const int per_check = 4;
+    int replays = 0;
+    const int max_replays = (max_it + 3) / 4 + 1;
+    while (true) {
+        for (int k = 0; k < per_check && replays < max_replays; ++k, ++replays) {
+            CU(cudaGraphLaunch(ctx->cg_graph, s));
+            ctx->launches += ctx->cg_graph_kernels;
+        }
+        CU(cudaMemcpyAsync(ctx->h_cg, ctx->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (ctx->h_cg->done || replays >= max_replays) break;
+    }
+    *iters = ctx->h_cg->k;
+    *est = ctx->h_cg->est;
+    *status = ctx->h_cg->status == -5 ? HOM_ENAN : (ctx->h_cg->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
+    return HOM_OK;
+}
+
 static void macro_to_mandel(const double *t, double *m) {
     const double r2 = std::sqrt(2.0);
     for (int c = 0; c < 6; ++c) m[c] = (c < 3) ? t[c] : t[c] * r2;
@@ -470,6 +629,9 @@ void hom_destroy(hom_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->cg_graph) cudaGraphExecDestroy(ctx->cg_graph);
+    cudaFree(ctx->d_cg);
+    if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
     engine_free(ctx->e32);
     engine_free(ctx->e64);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->vbuf[i]);
@@ -517,6 +679,16 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
         rc = engine_init<float>(ctx, ctx->e32);
         if (rc) return rc;
     }
+    if (ctx->solver == HOM_SOLVER_MODBFFT_CG) {
+        rc = engine_init_modb<double>(ctx, ctx->e64);
+        if (rc) return rc;
+        if (ctx->prec == HOM_PREC_FP32_FIELDS) {
+            rc = engine_init_modb<float>(ctx, ctx->e32);
+            if (rc) return rc;
+        }
+        CU(cudaMalloc(&ctx->d_cg, sizeof(CgState)));
+        CU(cudaMallocHost(&ctx->h_cg, sizeof(CgState)));
+    }
     const long long nr = 12 * ctx->S;   // reals per spectral vector (>= 6 V)
     const size_t rs = (ctx->prec == HOM_PREC_FP64) ? sizeof(double) : sizeof(float);
     for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * nr));
@@ -558,9 +730,13 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
         std::vector<double> host(ctx->V);
         CU(cudaMemcpyAsync(host.data(), ph, sizeof(double) * ctx->V, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
-        double s2 = 0.0;
-        for (long long i = 0; i < ctx->V; ++i) s2 += host[i] * host[i];
+        double s2 = 0.0, s1 = 0.0;
+        for (long long i = 0; i < ctx->V; ++i) {
+            s2 += host[i] * host[i];
+            s1 += host[i];
+        }
         ctx->phi2_sum = s2;
+        ctx->phibar = s1 / (double)ctx->V;
     }
     ctx->launches += 1;
     return finish(ctx);
@@ -579,7 +755,9 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     hom_options o;
     hom_default_options(&o);
     if (opt) o = *opt;
-    if (o.solver != HOM_SOLVER_GALERKIN_MINRES) return fail(nullptr, HOM_EINVAL, "bad solver");
+    if (o.solver != HOM_SOLVER_GALERKIN_MINRES && o.solver != HOM_SOLVER_MODBFFT_CG)
+        return fail(nullptr, HOM_EINVAL, "bad solver");
+    if (!(o.alpha >= 0.0) || !std::isfinite(o.alpha)) return fail(nullptr, HOM_EINVAL, "bad alpha");
     if (o.precision != HOM_PREC_FP32_FIELDS && o.precision != HOM_PREC_FP64)
         return fail(nullptr, HOM_EINVAL, "bad precision");
     if (o.rows3 < 0 || o.rows3 > 64 || o.tile2 < 0 || o.tile2 > 32 || o.tile1 < 0 || o.tile1 > 16)
@@ -597,6 +775,8 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     ctx->shape[1] = o.tile2;
     ctx->shape[2] = o.tile1;
     ctx->staging = o.staging;
+    ctx->solver = o.solver;
+    ctx->alpha = (o.alpha > 0.0) ? o.alpha : 1e-4;
     ctx->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) ctx->device = o.device;
     else if (cudaGetDevice(&ctx->device) != cudaSuccess) {
@@ -672,6 +852,44 @@ static int step(hom_ctx *ctx, int which, const void *in, void *out, const double
     return finish(ctx);
 }
 
+template <typename R>
+static int modb_step_impl(hom_ctx *ctx, Engine<R> &E, int which, const void *in, void *out, const double *macro) {
+    const size_t bytes = cpx_size<R>() * 3 * ctx->S;
+    cpx<R> *din = (cpx<R> *)ctx->vbuf[0], *dout = (cpx<R> *)ctx->vbuf[1];
+    int rc;
+    if (which == 0) {
+        rc = stage_in(ctx, in, bytes, din);
+        if (rc) return rc;
+        op_modb<R>(ctx, E, din, dout, nullptr, nullptr, nullptr);
+    } else if (which == 1) {
+        double m[6];
+        macro_to_mandel(macro, m);
+        rhs_modb<R>(ctx, E, m, dout);
+    } else {
+        rc = stage_in(ctx, in, bytes, din);
+        if (rc) return rc;
+        double lam_b, mu_b;
+        cbar(ctx, &lam_b, &mu_b);
+        Launch<R>::modb_precond(E.g, ctx->stream, lam_b, mu_b, din, dout);
+        ctx->launches += 1;
+    }
+    return stage_out(ctx, out, bytes, dout);
+}
+
+static int modb_step(hom_ctx *ctx, int which, const void *in, void *out, const double *macro) {
+    if (!ctx || !out || (which != 1 && !in) || (which == 1 && !macro)) return fail(ctx, HOM_EINVAL, "null argument");
+    if (ctx->solver != HOM_SOLVER_MODBFFT_CG) return fail(ctx, HOM_EINVAL, "context was not created for MoDBFFT");
+    cudaSetDevice(ctx->device);
+    int rc = (ctx->prec == HOM_PREC_FP64) ? modb_step_impl<double>(ctx, ctx->e64, which, in, out, macro)
+                                          : modb_step_impl<float>(ctx, ctx->e32, which, in, out, macro);
+    if (rc) return rc;
+    return finish(ctx);
+}
+
+int hom_modb_apply(hom_ctx *ctx, const void *u, void *out) { return modb_step(ctx, 0, u, out, nullptr); }
+int hom_modb_rhs(hom_ctx *ctx, const double macro_strain[6], void *out) { return modb_step(ctx, 1, nullptr, out, macro_strain); }
+int hom_modb_precond(hom_ctx *ctx, const void *in, void *out) { return modb_step(ctx, 2, in, out, nullptr); }
+
 int hom_apply(hom_ctx *ctx, const void *eps, void *out) { return step(ctx, 0, eps, out, nullptr); }
 int hom_rhs(hom_ctx *ctx, const double macro_strain[6], void *out) { return step(ctx, 1, nullptr, out, macro_strain); }
 int hom_fft_forward(hom_ctx *ctx, const void *field, void *spectrum) { return step(ctx, 2, field, spectrum, nullptr); }
@@ -692,11 +910,125 @@ static int true_residual(hom_ctx *ctx, const double2 *x, double bnorm, double *r
     return HOM_OK;
 }
 
-// real FP64 fluctuation strain of case icase (Mandel) into ctx->r64 (as 6 V doubles)
+// real FP64 fluctuation strain of case icase (Mandel) into ctx->r64 (as 6 V doubles):
+// Galerkin: F^-1 G x^;  MoDBFFT: F^-1 sym(u^ (x) xi)
 static double *fluctuation64(hom_ctx *ctx, int icase) {
     double *eps = (double *)ctx->r64;
-    spec_to_real<double>(ctx, ctx->e64, ctx->x64[icase], true, 1.0, eps);
+    if (ctx->solver == HOM_SOLVER_MODBFFT_CG) {
+        Launch<double>::modb_expand(ctx->e64.g, ctx->stream, 0.0, 0, ctx->x64[icase], ctx->e64.spec, 6, nullptr);
+        ctx->launches += 1;
+        spec_to_real<double>(ctx, ctx->e64, ctx->e64.spec, false, 1.0, eps);
+    } else {
+        spec_to_real<double>(ctx, ctx->e64, ctx->x64[icase], true, 1.0, eps);
+    }
     return eps;
+}
+
+// MoDBFFT solve of one case (section 2.2): FP64 right-hand side and true
+// residual of eq. (modbfftresres); PCG sweeps in the field precision,
+// refined against the FP64 residual.
+static int solve_case_modb(hom_ctx *ctx, int icase, const double *m, double tol, int max_it, double2 *x,
+                           hom_solve_info *inf, int *status_out) {
+    const long long nc3 = 3 * ctx->S;   // complex values per displacement spectrum
+    cudaStream_t s = ctx->stream;
+    rhs_modb<double>(ctx, ctx->e64, m, ctx->b64);
+    Launch<double>::norm2w(ctx->e64.g, s, ctx->b64, ctx->partials, 3);
+    reduce_to(s, ctx->partials, ew_blocks(3 * ctx->S), ctx->d_scalar);
+    ctx->launches += 2;
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemsetAsync(x, 0, sizeof(double2) * nc3, s));
+    CU(cudaStreamSynchronize(s));
+    const double bnorm = std::sqrt(*ctx->h_scalar);
+    // scale of the right-hand side: ||C : E_bar|| max|xi| sqrt(V) (Parseval)
+    double ce2 = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
+        ce2 += sv * sv;
+    }
+    const double nmax = std::max(ctx->n[0], std::max(ctx->n[1], ctx->n[2]));
+    const double scale = std::sqrt(ce2 * ctx->phi2_sum * (double)ctx->V) * 3.14159265358979323846 * nmax;
+    int status = HOM_OK;
+    if (!std::isfinite(bnorm)) {
+        *status_out = HOM_ENAN;
+        return HOM_OK;
+    }
+    if (bnorm <= kRhsZero * scale) {
+        inf->sweeps = 0;
+        *status_out = HOM_OK;
+        return HOM_OK;
+    }
+    auto residual = [&](double *res) -> int {
+        op_modb<double>(ctx, ctx->e64, x, ctx->r64, nullptr, nullptr, nullptr);
+        spec_residual64(ctx->e64.g, s, ctx->b64, ctx->r64, ctx->r64, ctx->partials, 3);
+        reduce_to(s, ctx->partials, ew_blocks(3 * ctx->S), ctx->d_scalar);
+        ctx->launches += 2;
+        CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        *res = std::sqrt(*ctx->h_scalar) / bnorm;
+        return HOM_OK;
+    };
+    double tres = 1.0;
+    int rc = residual(&tres);
+    if (rc) return rc;
+    const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
+    for (int sw = 0; sw < sweeps_max && tres > tol; ++sw) {
+        double sweep_tol = tol / tres;
+        if (sweep_tol > 0.5) sweep_tol = 0.5;
+        if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < kFp32SweepFloor) sweep_tol = kFp32SweepFloor;
+        int it = 0, st = 0;
+        double est = 0.0;
+        if (ctx->prec == HOM_PREC_FP64) {
+            CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double2) * nc3, cudaMemcpyDeviceToDevice, s));
+            rc = run_cg<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
+            if (rc) return rc;
+            Launch<double>::axpby(2 * nc3, s, 1.0, (const double *)ctx->xs, 1.0, (double *)x);
+        } else {
+            spec_d2f(nc3, s, ctx->r64, (float2 *)ctx->rhs);
+            rc = run_cg<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
+            if (rc) return rc;
+            spec_f2d_acc(nc3, s, (const float2 *)ctx->xs, x);
+        }
+        ctx->launches += 2;
+        inf->iterations += it;
+        inf->est_residual = est * tres;
+        inf->sweeps = sw + 1;
+        rc = residual(&tres);
+        if (rc) return rc;
+        if (st == HOM_ENAN) { status = HOM_ENAN; break; }
+        if (st == HOM_NOT_CONVERGED && tres > tol) { status = HOM_NOT_CONVERGED; break; }
+    }
+    inf->true_residual = tres;
+    if (status == HOM_OK && tres > tol) status = HOM_NOT_CONVERGED;
+    *status_out = status;
+    return HOM_OK;
+}
+
+// mean stress <phi C_m : (E_bar + e~)> in FP64, timing, info record
+static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom_solve_info *inf, int status,
+                       hom_solve_info *info) {
+    (void)x;
+    cudaStream_t s = ctx->stream;
+    const double *eps = fluctuation64(ctx, icase);
+    mean_stress64(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
+    const int nb = ew_blocks(ctx->V);
+    for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
+    ctx->launches += 7;
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(ctx->ev1, s));
+    CU(cudaStreamSynchronize(s));
+    const double r2 = std::sqrt(2.0);
+    for (int c = 0; c < 6; ++c) {
+        double v = ctx->h_scalar[c] / (double)ctx->V * ctx->E;
+        if (c >= 3) v /= r2;
+        inf->sigma_mean[c] = v;
+        ctx->sig_mean[6 * icase + c] = v;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    inf->time_ms = ms;
+    inf->status = status;
+    if (info) *info = *inf;
+    return status;
 }
 
 static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, int max_it, const void *warm,
@@ -709,6 +1041,13 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
     double2 *x = ctx->x64[icase];
     hom_solve_info inf{};
     CU(cudaEventRecord(ctx->ev0, s));
+    if (ctx->solver == HOM_SOLVER_MODBFFT_CG) {
+        if (warm) return fail(ctx, HOM_EINVAL, "warm starts are for the Galerkin solver");
+        int status = HOM_OK;
+        int rc = solve_case_modb(ctx, icase, m, tol, max_it, x, &inf, &status);
+        if (rc) return rc;
+        return finish_case(ctx, icase, m, x, &inf, status, info);
+    }
     rhs_spec<double>(ctx, ctx->e64, m, ctx->b64);
     double b2 = 0.0;
     int rc = spec_norm2<double>(ctx, ctx->e64, ctx->b64, &b2);
@@ -781,28 +1120,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         inf.true_residual = tres;
         if (status == HOM_OK && tres > tol) status = HOM_NOT_CONVERGED;
     }
-    // mean stress <phi C_m : (E_bar + e~)>, FP64
-    const double *eps = fluctuation64(ctx, icase);
-    mean_stress64(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
-    const int nb = ew_blocks(ctx->V);
-    for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
-    ctx->launches += 7;
-    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(cudaEventRecord(ctx->ev1, s));
-    CU(cudaStreamSynchronize(s));
-    const double r2 = std::sqrt(2.0);
-    for (int c = 0; c < 6; ++c) {
-        double v = ctx->h_scalar[c] / (double)ctx->V * ctx->E;
-        if (c >= 3) v /= r2;
-        inf.sigma_mean[c] = v;
-        ctx->sig_mean[6 * icase + c] = v;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    inf.time_ms = ms;
-    inf.status = status;
-    if (info) *info = inf;
-    return status;
+    return finish_case(ctx, icase, m, x, &inf, status, info);
 }
 
 int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, int max_it, const void *warm_start,

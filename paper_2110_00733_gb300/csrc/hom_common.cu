@@ -126,14 +126,59 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
     }
 }
 
-__global__ void __launch_bounds__(kEwThreads) k_spec_residual64(int n, int h, int n3, const double2 *b,
+// PCG (MoDBFFT, section 2.2): rho_0 = <r0, M r0>, ||r0||^2 from the two
+// halves of the partials; p_0 = z_0 is copied by the caller.
+__global__ void k_scalar_cg_start(CgState *st, const double *partials, int np, double tol, int max_it) {
+    const double rz = reduce_partials(partials, np);
+    const double rr = reduce_partials(partials + np, np);
+    if (threadIdx.x != 0) return;
+    st->rho = rz;
+    st->rr0 = rr;
+    st->rr = rr;
+    st->a = st->b = 0.0;
+    st->tol = tol;
+    st->est = 1.0;
+    st->k = 0;
+    st->max_it = max_it;
+    st->status = isfinite(rz) && isfinite(rr) ? 0 : -5;
+    st->done = (rr == 0.0 || max_it <= 0 || st->status) ? 1 : 0;
+    st->done_update = st->done;
+}
+
+// step length a = rho / <p, A p>
+__global__ void k_scalar_cg_alpha(CgState *st, const double *partials, int np) {
+    if (st->done) return;
+    const double pq = reduce_partials(partials, np);
+    if (threadIdx.x != 0) return;
+    const double a = st->rho / pq;
+    if (!isfinite(a)) { st->status = -5; st->done = 1; return; }
+    st->a = a;
+}
+
+// after x, r, z: rho' = <r, z>, b = rho'/rho; stop at ||r||/||r0|| <= tol
+__global__ void k_scalar_cg_beta(CgState *st, const double *partials, int np) {
+    if (st->done) return;
+    const double rz = reduce_partials(partials, np);
+    const double rr = reduce_partials(partials + np, np);
+    if (threadIdx.x != 0) return;
+    st->k += 1;
+    st->rr = rr;
+    st->est = sqrt(rr / st->rr0);
+    if (!isfinite(rz) || !isfinite(rr)) { st->status = -5; st->done = 1; return; }
+    st->b = rz / st->rho;
+    st->rho = rz;
+    if (st->est <= st->tol) st->done = 1;
+    else if (st->k >= st->max_it) { st->status = 1; st->done = 1; }
+}
+
+__global__ void __launch_bounds__(kEwThreads) k_spec_residual64(int n, int h, int n3, int nc, const double2 *b,
                                                                 const double2 *ax, double2 *r, double *partials) {
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double2 bb = b[i], aa = ax[i];
         const double2 d = make_double2(bb.x - aa.x, bb.y - aa.y);
         r[i] = d;
-        acc += pweight((i / 6) % h, n3) * (d.x * d.x + d.y * d.y);
+        acc += pweight((i / nc) % h, n3) * (d.x * d.x + d.y * d.y);
     }
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -280,7 +325,7 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
     e->ptr = ptr;
     e->kind = kind;
     const cuuint64_t u = (cuuint64_t)units;
-    const cuuint64_t h6 = 6ull * g.h * u;
+    const cuuint64_t h6 = (cuuint64_t)g.nc * g.h * u;   // components x h, in 8-byte units
     CUresult r;
     if (kind == TMA_X2) {
         cuuint64_t dims[3] = {h6, (cuuint64_t)g.n2, (cuuint64_t)g.n1};
@@ -293,7 +338,7 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
     } else {
         cuuint64_t dims[2] = {h6 * g.n2, (cuuint64_t)g.n1};
         cuuint64_t strides[1] = {h6 * g.n2 * 8};
-        cuuint32_t box[2] = {(cuuint32_t)(6 * g.tile1 * units), (cuuint32_t)g.n1};
+        cuuint32_t box[2] = {(cuuint32_t)(g.nc * g.tile1 * units), (cuuint32_t)g.n1};
         cuuint32_t es[2] = {1, 1};
         r = fn(&e->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -313,9 +358,9 @@ int ew_blocks(long long n) {
 }
 
 void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
-                     double *partials) {
-    const int n = (int)(6 * g.S);
-    k_spec_residual64<<<ew_blocks(n), kEwThreads, 0, st>>>(n, g.h, g.n3, b, ax, r, partials);
+                     double *partials, int nc) {
+    const int n = (int)(nc * g.S);
+    k_spec_residual64<<<ew_blocks(n), kEwThreads, 0, st>>>(n, g.h, g.n3, nc, b, ax, r, partials);
 }
 void spec_d2f(long long n, cudaStream_t st, const double2 *in, float2 *out) {
     k_spec_d2f<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
@@ -364,6 +409,15 @@ void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int n
 }
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np) {
     k_scalar_givens<<<1, 1024, 0, st>>>(s, partials, np);
+}
+void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it) {
+    k_scalar_cg_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it);
+}
+void scalar_cg_alpha(cudaStream_t st, CgState *s, const double *partials, int np) {
+    k_scalar_cg_alpha<<<1, 1024, 0, st>>>(s, partials, np);
+}
+void scalar_cg_beta(cudaStream_t st, CgState *s, const double *partials, int np) {
+    k_scalar_cg_beta<<<1, 1024, 0, st>>>(s, partials, np);
 }
 void reduce_to(cudaStream_t st, const double *partials, int np, double *out) {
     k_reduce_to<<<1, 1024, 0, st>>>(partials, np, out);

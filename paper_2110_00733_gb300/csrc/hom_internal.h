@@ -24,6 +24,13 @@ namespace hom {
 // Scalars of one MINRES solve, resident in device memory.  Written only by
 // the single-CTA scalar kernels; read by the field kernels.  FP64 always.
 struct MinresState {
+    int done;          // no further operator / Krylov work (first field: the
+                       // pass kernels read it through any solver's state)
+    int done_update;   // the last w/x update has been applied
+    int k;             // iterations done
+    int max_it;
+    int status;        // 0 ok, 1 max_it, -5 NaN
+    int pad;
     double beta1;      // ||b||
     double beta;       // beta_k: coefficient of v_{k-1} in the next Lanczos step
     double alpha;      // alpha_k
@@ -35,12 +42,18 @@ struct MinresState {
     // coefficients of the w / x / v update of the current iteration
     double u_delta, u_eps, u_inv_gamma, u_tau, u_inv_beta;
     double est;        // phibar_k / beta_1
-    int k;             // iterations done
-    int max_it;
-    int done;          // no further operator / Lanczos work
-    int done_update;   // the last w/x update has been applied
-    int status;        // 0 ok, 1 max_it, -5 NaN
-    int pad;
+};
+
+// Scalars of one preconditioned CG solve (MoDBFFT, section 2.2); same
+// leading flags as MinresState.
+struct CgState {
+    int done, done_update, k, max_it, status, pad;
+    double rho;        // <r, M r>
+    double rr0;        // ||r_0||^2
+    double rr;         // ||r_k||^2
+    double a, b;       // step length and direction update of this iteration
+    double tol;
+    double est;        // ||r_k|| / ||r_0||
 };
 
 // Kernel-side description of one cell for one precision.
@@ -57,6 +70,7 @@ struct Geometry {
     int threads3, threads2, threads1;
     size_t smem3, smem2, smem1;
     int fast[3];
+    int nc;                 // complex components per frequency in the spectrum (6, or 10 for MoDBFFT)
     // persistent TMA-staged n2 / n1 passes (FP32, power-of-two n <= 256):
     // enabled flag, persistent grid sizes, shared memory, host-side cache of
     // tensor maps (never dereferenced on the device) and the device word a
@@ -79,7 +93,8 @@ void tma_cache_free(void *cache);
 
 // n3 pass (x3): input, middle and output stages
 enum X3In { X3_IN_SPEC = 0, X3_IN_REAL = 1, X3_IN_MACRO = 2 };
-enum X3Mid { X3_MID_NONE = 0, X3_MID_MATERIAL = 1 };
+enum X3Mid { X3_MID_NONE = 0, X3_MID_MATERIAL = 1,
+             X3_MID_MODB = 2 };   // 10 components: tau = phi C_m eps (0-5), chi_v g (6-8), 0 (9)
 enum X3Out { X3_OUT_SPEC = 0, X3_OUT_REAL = 1 };
 // n1 pass (x1) flags
 enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
@@ -110,8 +125,18 @@ template <typename R> struct Launch {
                        cpx<R> *x, MinresState *state);
     // y = a x + b y over n reals
     static void axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y);
-    // weighted partial ||x||^2 of a spectral vector
-    static void norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials);
+    // weighted partial ||x||^2 of a spectral vector with nc components per frequency
+    static void norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials, int nc = 6);
+    // MoDBFFT point-wise kernels (hom_modb.cuh); 3-component half spectra
+    static void modb_expand(const Geometry &g, cudaStream_t st, double alpha, int with_penalty, const cpx<R> *u,
+                            cpx<R> *out, int nc_out, const MinresState *state);
+    static void modb_contract(const Geometry &g, cudaStream_t st, const cpx<R> *in10, cpx<R> *out3,
+                              const cpx<R> *dotv, double *partials, const MinresState *state);
+    static void modb_precond(const Geometry &g, cudaStream_t st, double lam_b, double mu_b, const cpx<R> *in,
+                             cpx<R> *out);
+    static void cg_xr(const Geometry &g, cudaStream_t st, double lam_b, double mu_b, cpx<R> *x, cpx<R> *r,
+                      const cpx<R> *p, const cpx<R> *q, cpx<R> *z, const CgState *state, double *partials);
+    static void cg_p(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *z, const CgState *state);
     static int ew_grid(long long n);
     static void table_init(const Geometry &g);
     static int x3_grid(const Geometry &g);
@@ -121,7 +146,7 @@ template <typename R> struct Launch {
 
 // FP64 helpers on spectral vectors (double2) and real fields
 void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
-                     double *partials);                         // r = b - ax, weighted ||r||^2
+                     double *partials, int nc = 6);             // r = b - ax, weighted ||r||^2
 void spec_d2f(long long ncplx, cudaStream_t st, const double2 *in, float2 *out);
 void spec_f2d_acc(long long ncplx, cudaStream_t st, const float2 *in, double2 *out);   // out += in
 void mean_stress64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
@@ -142,6 +167,10 @@ void hom_set_error(const char *msg);
 void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it);
 void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np);
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np);
+// PCG scalars (MoDBFFT): start from <r0,z0>, ||r0||^2; step length; direction
+void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it);
+void scalar_cg_alpha(cudaStream_t st, CgState *s, const double *partials, int np);
+void scalar_cg_beta(cudaStream_t st, CgState *s, const double *partials, int np);
 void reduce_to(cudaStream_t st, const double *partials, int np, double *out);
 
 }  // namespace hom

@@ -219,6 +219,7 @@ int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, 
         g.threads1 = L1 * (m < 1 ? 1 : m);
         g.smem1 = 2ull * L1 * g.n1 * cs;
     }
+    g.nc = 6;
     g.tma = 0;
     g.tma_cache = nullptr;
     g.err = nullptr;

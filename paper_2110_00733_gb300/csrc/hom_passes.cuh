@@ -187,7 +187,7 @@ template <> struct Six<double> {
 // component pairs (2p, 2p+1) of each row packed as one complex line
 // Z = X_2p + i X_2p+1, line index p*rows3 + r.
 // ---------------------------------------------------------------------------
-template <typename R, int NF>
+template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state) {
@@ -197,7 +197,8 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     // stride by ES across a warp and stay free of bank conflicts; the fast
     // engine also skips one slot every 16 elements (PAD)
     constexpr int PAD = NF > 0 ? 1 : 0;
-    const int N = g.n3, ROWS = g.rows3, L = 3 * ROWS, ES = L | 1, H = g.h;
+    constexpr int NC = 2 * NP;   // components per frequency
+    const int N = g.n3, ROWS = g.rows3, L = NP * ROWS, ES = L | 1, H = g.h;
     auto ep = [ES](int e) { return epos<PAD>(e, ES); };
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + ep(N);   // second buffer of the generic engine only
@@ -211,13 +212,13 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
         // the self-conjugate bins keep their real parts, as a C2R does
         const cpx<R> *spec = reinterpret_cast<const cpx<R> *>(in_);
         for (int r = 0; r < ROWS; ++r) {
-            const cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
+            const cpx<R> *row = spec + (size_t)(row0 + r) * H * NC;
             for (int k = threadIdx.x; k < H; k += blockDim.x) {
                 const bool selfc = (k == 0) || (2 * k == N);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) {
+                for (int p = 0; p < NP; ++p) {
                     cpx<R> xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-                    if (r < nr) Six<R>::load_pair(row + 6 * k, p, xa, xb);
+                    if (r < nr) Six<R>::load_pair(row + NC * k, p, xa, xb);
                     if (selfc) { xa.y = 0; xb.y = 0; }
                     buf[ep(k) + p * ROWS + r] = mk<R>(xa.x - xb.y, xa.y + xb.x);
                     if (!selfc) buf[ep(N - k) + p * ROWS + r] = mk<R>(xa.x + xb.y, xb.x - xa.y);
@@ -235,12 +236,13 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
         for (int r = 0; r < ROWS; ++r) {
             const int vbase = (row0 + r) * N;
             for (int e = threadIdx.x; e < N; e += blockDim.x) {
-                R t[6];
+                R t[NC];
 #pragma unroll
-                for (int c = 0; c < 6; ++c)
-                    t[c] = (r >= nr) ? (R)0 : (in_mode == X3_IN_MACRO ? (R)mac.v[c] : real[c * V + vbase + e]);
+                for (int c = 0; c < NC; ++c)
+                    t[c] = (r >= nr || c >= 6) ? (R)0
+                                               : (in_mode == X3_IN_MACRO ? (R)mac.v[c] : real[c * V + vbase + e]);
 #pragma unroll
-                for (int p = 0; p < 3; ++p) buf[ep(e) + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
+                for (int p = 0; p < NP; ++p) buf[ep(e) + p * ROWS + r] = mk<R>(t[2 * p], t[2 * p + 1]);
             }
         }
         __syncthreads();
@@ -252,26 +254,34 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
         const int vbase = (row0 + r) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
             cpx<R> *q = buf + ep(e) + r;
-            R t[6];
+            R t[NC];
 #pragma unroll
-            for (int p = 0; p < 3; ++p) {
+            for (int p = 0; p < NP; ++p) {
                 const cpx<R> z = q[p * ROWS];
                 t[2 * p] = z.x * s_all;
                 t[2 * p + 1] = z.y * s_all;
             }
-            if (mid == X3_MID_MATERIAL) {
+            if (mid == X3_MID_MATERIAL || mid == X3_MID_MODB) {
                 const R ph = phi[vbase + e];
                 const R tr = lam * (t[0] + t[1] + t[2]);
 #pragma unroll
                 for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : (R)0) + mu2 * t[c]);
+                if constexpr (NC == 10) {
+                    // MoDBFFT penalty vector on the empty phase: chi_v g, eq. (modbfftfop)
+                    const R chi = (ph == (R)0) ? (R)1 : (R)0;
+                    t[6] *= chi;
+                    t[7] *= chi;
+                    t[8] *= chi;
+                    t[9] = 0;
+                }
             }
             if (out_mode == X3_OUT_REAL) {
                 R *real = reinterpret_cast<R *>(out_);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) real[c * V + vbase + e] = t[c];
+                for (int c = 0; c < 6; ++c) real[c * V + vbase + e] = t[c];   // (NC == 6 only)
             } else {
 #pragma unroll
-                for (int p = 0; p < 3; ++p) q[p * ROWS] = mk<R>(t[2 * p], t[2 * p + 1]);
+                for (int p = 0; p < NP; ++p) q[p * ROWS] = mk<R>(t[2 * p], t[2 * p + 1]);
             }
         }
     }
@@ -283,14 +293,14 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
     cpx<R> *spec = reinterpret_cast<cpx<R> *>(out_);
     for (int r = 0; r < nr; ++r) {
-        cpx<R> *row = spec + (size_t)(row0 + r) * H * 6;
+        cpx<R> *row = spec + (size_t)(row0 + r) * H * NC;
         for (int k = threadIdx.x; k < H; k += blockDim.x) {
             const int km = (k == 0) ? 0 : N - k;
 #pragma unroll
-            for (int p = 0; p < 3; ++p) {
+            for (int p = 0; p < NP; ++p) {
                 const cpx<R> z = res[ep(k) + p * ROWS + r];
                 const cpx<R> zm = conjc<R>(res[ep(km) + p * ROWS + r]);
-                Six<R>::store_pair(row + 6 * k, p, mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y)),
+                Six<R>::store_pair(row + NC * k, p, mk<R>((R)0.5 * (z.x + zm.x), (R)0.5 * (z.y + zm.y)),
                                    mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x)));
             }
         }
@@ -306,7 +316,7 @@ template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
     if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int N = g.n2, T = g.tile2, H6 = 6 * g.h;
+    const int N = g.n2, T = g.tile2, H6 = g.nc * g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * T;
     const int total = g.n1 * H6;
@@ -338,18 +348,18 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
         return;
     }
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int N = g.n1, T = g.tile1, H = g.h, L = 6 * T;
+    const int NC = g.nc, N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * L;
     const int cols = g.n2 * H;
     const int g0 = blockIdx.x * T;
-    const size_t sK1 = (size_t)cols * 6;   // stride between consecutive k1
+    const size_t sK1 = (size_t)cols * NC;   // stride between consecutive k1
     // each thread keeps one line l (blockDim is a multiple of L)
     const int lt = threadIdx.x % L, e0 = threadIdx.x / L, es = blockDim.x / L;
-    const int tl = lt / 6;
+    const int tl = lt / NC;
     const bool live = g0 + tl < cols;
     {
-        const cpx<R> *src = in + (size_t)g0 * 6 + lt;
+        const cpx<R> *src = in + (size_t)g0 * NC + lt;
         for (int e = e0; e < N; e += es) buf[e * L + lt] = live ? src[e * sK1] : mk<R>(0, 0);
     }
     __syncthreads();
@@ -359,14 +369,14 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
     const int k2g = colg / H, k3g = colg - k2g * H;
     if (flags & X1_GAMMA_IN) {
         if (colg < cols)
-            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC);
         __syncthreads();
     }
     cpx<R> *res = (flags & X1_FWD) ? run_fft<R, -1, NF>(buf, buf2, L, L, g.ax[0])
                                    : run_fft<R, 1, NF>(buf, buf2, L, L, g.ax[0]);
     if (flags & X1_GAMMA_OUT) {
         if (colg < cols)
-            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, res + e * L + tg * 6);
+            for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, res + e * L + tg * NC);
         __syncthreads();
     }
     Acc<R> acc;
@@ -374,8 +384,8 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
         const int colt = g0 + tl;
         const int k3 = colt - (colt / H) * H;
         const R w = (R)pweight(k3, g.n3);
-        cpx<R> *dst = out + (size_t)g0 * 6 + lt;
-        const cpx<R> *dv = dotv + (size_t)g0 * 6 + lt;
+        cpx<R> *dst = out + (size_t)g0 * NC + lt;
+        const cpx<R> *dv = dotv + (size_t)g0 * NC + lt;
         for (int e = e0; e < N; e += es) {
             const cpx<R> z = res[e * L + lt];
             dst[e * sK1] = z;
@@ -467,7 +477,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
     }
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
-    const int N = g.n1, T = g.tile1, H = g.h, L = 6 * T;
+    const int NC = g.nc, N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     const int cols = g.n2 * H;
     const int ntiles = (cols + T - 1) / T;
     const bool dot = (flags & X1_DOT) != 0;
@@ -485,8 +495,8 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
     __syncthreads();
     auto issue = [&](int t, int s) {
         mbar_expect_tx(&bar[s], bytes);
-        tma_load_2d(base + s * per, &tin, 6 * T * t, 0, &bar[s]);
-        if (dot) tma_load_2d(base + s * per + tile_elems, &tdot, 6 * T * t, 0, &bar[s]);
+        tma_load_2d(base + s * per, &tin, NC * T * t, 0, &bar[s]);
+        if (dot) tma_load_2d(base + s * per + tile_elems, &tdot, NC * T * t, 0, &bar[s]);
     };
     int tile = blockIdx.x;
     if (leader && tile < ntiles) issue(tile, 0);
@@ -517,18 +527,18 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
         const int k2g = colg / H, k3g = colg - k2g * H;
         if (flags & X1_GAMMA_IN) {
             if (colg < cols)
-                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC);
             __syncthreads();
         }
         if (flags & X1_FWD) fast_fft<R, -1, NF>(buf, L, L, tw);
         else fast_fft<R, 1, NF>(buf, L, L, tw);
         if (flags & X1_GAMMA_OUT) {
             if (colg < cols)
-                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * 6);
+                for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC);
             __syncthreads();
         }
         if (dot) {
-            const int colt = g0 + lt / 6;
+            const int colt = g0 + lt / NC;
             if (colt < cols) {
                 const int k3 = colt % H;
                 const R w = (R)pweight(k3, g.n3);
@@ -543,7 +553,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
         fence_proxy_async_smem();
         __syncthreads();
         if (leader) {
-            tma_store_2d(&tout, 6 * T * tile, 0, buf);
+            tma_store_2d(&tout, NC * T * tile, 0, buf);
             bulk_commit();
         }
     }
@@ -600,12 +610,12 @@ __global__ void k_axpby(long long n, R a, const R *__restrict__ x, R b, R *__res
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kEwThreads) k_norm2w(int n, int h, int n3, const cpx<R> *__restrict__ x,
+__global__ void __launch_bounds__(kEwThreads) k_norm2w(int n, int h, int n3, int nc, const cpx<R> *__restrict__ x,
                                                        double *partials) {
     Acc<R> acc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const cpx<R> q = x[i];
-        const R w = (R)pweight((i / 6) % h, n3);
+        const R w = (R)pweight((i / nc) % h, n3);
         acc.add_prod(w * q.x, q.x);
         acc.add_prod(w * q.y, q.y);
     }
@@ -656,7 +666,8 @@ void Launch<R>::table_init(const Geometry &) {
     cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);                  \
     cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 #define HOM_SET_ATTR(NF)                \
-    HOM_SET_ATTR1((k_x3<R, NF>))        \
+    HOM_SET_ATTR1((k_x3<R, NF, 3>))     \
+    HOM_SET_ATTR1((k_x3<R, NF, 5>))     \
     HOM_SET_ATTR1((k_x2<R, -1, NF>))    \
     HOM_SET_ATTR1((k_x2<R, 1, NF>))     \
     HOM_SET_ATTR1((k_x1<R, NF>))
@@ -722,8 +733,13 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
     if (macro)
         for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
     const int grid = x3_grid(g);
-#define HOM_X3(NF) \
-    k_x3<R, NF><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, (R)scl, out_mode, out, phi, state)
+#define HOM_X3(NF)                                                                                          \
+    if (g.nc == 10)                                                                                         \
+        k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
+                                                            (R)scl, out_mode, out, phi, state);                \
+    else                                                                                                    \
+        k_x3<R, NF, 3><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
+                                                            (R)scl, out_mode, out, phi, state)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }
@@ -733,7 +749,7 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
     if constexpr (sizeof(R) == 4) {
         if (g.tma) {
             const CUtensorMap *tm = tma_map(g, spec, TMA_X2, 1);
-            const int qtiles = (6 * g.h + g.tile2 - 1) / g.tile2;
+            const int qtiles = (g.nc * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2T(NF)                                                                                         \
     if (inverse) k_x2_tma<R, 1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state);    \
     else k_x2_tma<R, -1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state)
@@ -746,7 +762,7 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
             return;
         }
     }
-    const int grid = (g.n1 * 6 * g.h + g.tile2 - 1) / g.tile2;
+    const int grid = (g.n1 * g.nc * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2(NF)                                                                  \
     if (inverse) k_x2<R, 1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state); \
     else k_x2<R, -1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state)
@@ -801,9 +817,11 @@ void Launch<R>::axpby(long long n, cudaStream_t st, double a, const R *x, double
 }
 
 template <typename R>
-void Launch<R>::norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials) {
-    const int n = (int)(6 * g.S);
-    k_norm2w<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, x, partials);
+void Launch<R>::norm2w(const Geometry &g, cudaStream_t st, const cpx<R> *x, double *partials, int nc) {
+    const int n = (int)(nc * g.S);
+    k_norm2w<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, nc, x, partials);
 }
 
 }  // namespace hom
+
+#include "hom_modb.cuh"

@@ -21,7 +21,7 @@ HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ENOMEM, HOM_ECUDA, HOM_ENAN, HOM_ETIMEOUT
 HOM_INPUT_PHASE_U8, HOM_INPUT_FRACTION_F32, HOM_INPUT_FRACTION_F64 = 0, 1, 2
 HOM_SMOOTH_NONE = 0
 HOM_DERIV_CONTINUOUS, HOM_DERIV_ROTATED = 0, 1
-HOM_SOLVER_GALERKIN_MINRES = 0
+HOM_SOLVER_GALERKIN_MINRES, HOM_SOLVER_MODBFFT_CG = 0, 1
 HOM_PREC_FP32_FIELDS, HOM_PREC_FP64 = 0, 1
 
 # every symbol include/hom.h declares
@@ -29,7 +29,7 @@ EXPORTED = [
     "hom_default_options", "hom_create", "hom_solve", "hom_effective_stiffness",
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
-    "hom_last_error", "hom_apply_noalloc",
+    "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
 ]
 
 
@@ -38,7 +38,7 @@ class hom_options(ctypes.Structure):
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("refine", ctypes.c_int),
                 ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int),
-                ("staging", ctypes.c_int)]
+                ("staging", ctypes.c_int), ("alpha", ctypes.c_double)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH):
     lib.hom_project.argtypes = [vp, vp, vp]
     lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
     lib.hom_apply_noalloc.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp, vp]
+    lib.hom_modb_apply.argtypes = [vp, vp, vp]
+    lib.hom_modb_rhs.argtypes = [vp, dp, vp]
+    lib.hom_modb_precond.argtypes = [vp, vp, vp]
     lib.hom_get_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
     lib.hom_kernel_launches.argtypes = [vp]
     lib.hom_kernel_launches.restype = ctypes.c_longlong
@@ -150,7 +153,8 @@ class Context:
 def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
                smoothing=HOM_SMOOTH_NONE, derivative=HOM_DERIV_ROTATED,
                precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
-               device=-1, refine=3, shape=(0, 0, 0), staging=0) -> Context:
+               device=-1, refine=3, shape=(0, 0, 0), staging=0,
+               solver=HOM_SOLVER_GALERKIN_MINRES, alpha=0.0) -> Context:
     lib = load_library()
     opt = hom_options()
     lib.hom_default_options(ctypes.byref(opt))
@@ -161,6 +165,8 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
     opt.refine = refine
     opt.rows3, opt.tile2, opt.tile1 = (int(s) for s in shape)
     opt.staging = int(staging)
+    opt.solver = int(solver)
+    opt.alpha = float(alpha)
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),
@@ -223,6 +229,38 @@ def hom_rhs(ctx: Context, macro_strain, out=None):
 def spectrum_shape(ctx: Context):
     n1, n2, n3 = ctx.grid
     return (n1, n2, n3 // 2 + 1, 6)
+
+
+def displacement_shape(ctx: Context):
+    n1, n2, n3 = ctx.grid
+    return (n1, n2, n3 // 2 + 1, 3)
+
+
+def _cdtype(ctx):
+    return np.complex64 if ctx.dtype == np.float32 else np.complex128
+
+
+def hom_modb_apply(ctx: Context, u, out=None):
+    if out is None:
+        out = np.empty(displacement_shape(ctx), dtype=_cdtype(ctx))
+    _check(ctx.handle, load_library().hom_modb_apply(ctx.handle, _ptr(u), _ptr(out)))
+    return out
+
+
+def hom_modb_rhs(ctx: Context, macro_strain, out=None):
+    if out is None:
+        out = np.empty(displacement_shape(ctx), dtype=_cdtype(ctx))
+    m = np.ascontiguousarray(macro_strain, dtype=np.float64)
+    _check(ctx.handle, load_library().hom_modb_rhs(ctx.handle, m.ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double)), _ptr(out)))
+    return out
+
+
+def hom_modb_precond(ctx: Context, v, out=None):
+    if out is None:
+        out = np.empty(displacement_shape(ctx), dtype=_cdtype(ctx))
+    _check(ctx.handle, load_library().hom_modb_precond(ctx.handle, _ptr(v), _ptr(out)))
+    return out
 
 
 def hom_fft_forward(ctx: Context, field, spectrum=None):

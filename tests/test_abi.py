@@ -34,13 +34,31 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(hom.EXPORTED) == declared_symbols()
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the header's structs have the C compiler's sizes and
+    field offsets."""
     import ctypes
+    import subprocess
     from paper_2110_00733_gb300 import hom
-    # hom_options: 3 ints, (pad), pointer, 5 ints, (pad)
-    assert ctypes.sizeof(hom.hom_options) == 48
-    # hom_solve_info: 4 ints + 2 doubles + 6 doubles + 1 double
-    assert ctypes.sizeof(hom.hom_solve_info) == 16 + 8 * 9
+    src = tmp_path / "layout.c"
+    fields_o = [f for f, _ in hom.hom_options._fields_]
+    fields_i = [f for f, _ in hom.hom_solve_info._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hom.h"', "int main(void) {",
+             'printf("%zu %zu\\n", sizeof(hom_options), sizeof(hom_solve_info));']
+    lines += [f'printf("%zu\\n", offsetof(hom_options, {f}));' for f in fields_o]
+    lines += [f'printf("%zu\\n", offsetof(hom_solve_info, {f}));' for f in fields_i]
+    lines += ["return 0; }"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    so, si = int(out[0]), int(out[1])
+    assert ctypes.sizeof(hom.hom_options) == so
+    assert ctypes.sizeof(hom.hom_solve_info) == si
+    offs = [int(v) for v in out[2:]]
+    py = [getattr(hom.hom_options, f).offset for f in fields_o] + \
+         [getattr(hom.hom_solve_info, f).offset for f in fields_i]
+    assert offs == py
 
 
 def test_missing_library_fails_loudly(tmp_path):
