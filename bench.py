@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--rho", type=float, default=0.10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "modbfft", "batch", "config2", "asprinted"],
+                    help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
+                         "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
 
 
@@ -348,10 +352,153 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """16 octet cells, densities uniform in [0.03, 0.30], grids drawn from
+    {64, 96, 128, 160}^3 (seeds 0-15), six unit strains each, solved at once
+    by hom_solve_batch with autotuned launch shapes; FP32 fields, tol 1e-6.
+    Value: sum over cells and cases of V x iterations / wall time."""
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    specs = [(int(rng.choice([64, 96, 128, 160])), float(rng.uniform(0.03, 0.30))) for _ in range(16)]
+    phis = [ri.octet(n, rho)[0] for n, rho in specs]
+    ctxs = [hom.hom_create(p.shape, p, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, autotune=True) for p in phis]
+    macros = np.eye(6)
+    for _ in range(args.warmup):
+        hom.hom_solve_batch(ctxs, macros, tol=TOL, max_it=MAX_IT)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vox_it = 0
+    for _ in range(args.steps):
+        rc, infos = hom.hom_solve_batch(ctxs, macros, tol=TOL, max_it=MAX_IT)
+        for (n, _), cell in zip(specs, infos):
+            vox_it += n ** 3 * sum(i["iterations"] for i in cell)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    worst = max(i["true_residual"] for cell in infos for i in cell)
+    print(json.dumps({"metric": "minres_voxel_iters_per_s", "value": vox_it / dt, "unit": "voxel-iter/s",
+                      "workload": "batch_16_octet_cells_x6", "cells": specs, "steps": args.steps,
+                      "ms_per_step": 1e3 * dt / args.steps, "worst_true_residual": worst,
+                      "iterations": [[i["iterations"] for i in cell] for cell in infos]}), flush=True)
+    for c in ctxs:
+        c.close()
+    return 0
+
+
+def run_modbfft(args):
+    """The headline cell solved with MoDBFFT (section 2.2): PCG iterations."""
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n = args.n
+    phi, _ = ri.octet(n, args.rho)
+    ctx = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+                         derivative=hom.HOM_DERIV_CONTINUOUS, solver=hom.HOM_SOLVER_MODBFFT_CG)
+    for _ in range(args.warmup):
+        hom.hom_solve(ctx, MACRO, tol=TOL, max_it=MAX_IT)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        rc, info = hom.hom_solve(ctx, MACRO, tol=TOL, max_it=MAX_IT)
+        its += info[0]["iterations"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"metric": "pcg_voxel_iters_per_s", "value": n ** 3 * its / dt, "unit": "voxel-iter/s",
+                      "workload": f"modbfft_octet_{n}^3_rho{args.rho:.2f}_E11_tol1e-6", "rc": rc,
+                      "iterations_per_step": its / args.steps, "ms_per_step": 1e3 * dt / args.steps,
+                      "true_residual": info[0]["true_residual"], "sweeps": info[0]["sweeps"],
+                      "sigma11_pa": float(info[0]["sigma_mean"][0])}), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_config2(args):
+    """Octet cells at 128^3, densities {3, 7, 15, 30} %, both solvers
+    (Galerkin-MINRES with rotated frequencies; MoDBFFT-PCG with continuous
+    frequencies, alpha = 1e-4 E), FP64 fields versus FP32 fields with FP64
+    Krylov scalars, six unit strains -> the 6x6 effective stiffness.  One JSON
+    line per (density, solver) with both precisions and their difference."""
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n = 128
+    for rho in (0.03, 0.07, 0.15, 0.30):
+        phi, _ = ri.octet(n, rho)
+        for solver, deriv, name in ((hom.HOM_SOLVER_GALERKIN_MINRES, hom.HOM_DERIV_ROTATED, "galerkin_minres"),
+                                    (hom.HOM_SOLVER_MODBFFT_CG, hom.HOM_DERIV_CONTINUOUS, "modbfft_pcg")):
+            res = {}
+            for prec, pname in ((hom.HOM_PREC_FP64, "fp64"), (hom.HOM_PREC_FP32_FIELDS, "fp32")):
+                ctx = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, derivative=deriv,
+                                     precision=prec, solver=solver)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, info = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=6000)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                C = hom.hom_effective_stiffness(ctx)
+                ctx.close()
+                res[pname] = {"rc": rc, "seconds": dt, "iterations": [i["iterations"] for i in info],
+                              "true_residual_max": max(i["true_residual"] for i in info),
+                              "C11_pa": C[0, 0], "C12_pa": C[0, 1], "C44_pa": C[3, 3], "C": C}
+            err = float(np.max(np.abs(res["fp32"]["C"] - res["fp64"]["C"])) / np.max(np.abs(res["fp64"]["C"])))
+            for v in res.values():
+                v.pop("C")
+            print(json.dumps({"workload": f"config2_octet_128^3_rho{rho:.2f}", "solver": name,
+                              "fp32_vs_fp64_Ceff_rel_err": err, **res}), flush=True)
+    return 0
+
+
+def run_asprinted(args):
+    """Synthetic as-printed lattice: 2x2x2 octet cells at 512^3 (134 M voxels),
+    12 % density, strut surface moved by a Gaussian random field (correlation
+    3 voxels, std 1 voxel), spherical pores (radius 2-8 voxels, 1 % of the
+    solid), Voigt fractions; FP32 fields, six unit strains, tol 1e-6."""
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    phi, r = ri.as_printed(args.n, cells=2, rho=0.12, seed=0)
+    tgen = time.perf_counter() - t0
+    ctx = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, info = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=MAX_IT)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    C = hom.hom_effective_stiffness(ctx)
+    its = [i["iterations"] for i in info]
+    V = args.n ** 3
+    print(json.dumps({"workload": f"as_printed_2x2x2_octet_{args.n}^3_rho0.12", "rc": rc,
+                      "generation_s": tgen, "phi_mean": float(phi.mean()), "solve_s": dt,
+                      "iterations": its, "voxel_iters_per_s": V * sum(its) / dt,
+                      "true_residual_max": max(i["true_residual"] for i in info),
+                      "C_eff_pa": C.tolist()}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "config2":
+        return run_config2(args)
+    if args.workload == "asprinted":
+        return run_asprinted(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "modbfft":
+        return run_modbfft(args)
     return run_ours(args)
 
 

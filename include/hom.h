@@ -93,6 +93,9 @@ typedef struct {
     int staging;        /* 0: persistent TMA-staged n1/n2 passes where supported
                            (FP32, power-of-two n1, n2 in [64, 256]); 1: plain loads */
     double alpha;       /* MoDBFFT penalty alpha / E (0: 1e-4, section 4.2) */
+    int autotune;       /* nonzero (and no explicit rows3/tile2/tile1): launch
+                           shapes from hom_autotune for this grid and precision */
+    int reserved;
 } hom_options;
 
 typedef struct {
@@ -225,6 +228,23 @@ int hom_modb_rhs(hom_ctx *ctx, const double macro_strain[6], void *out_spectrum)
 
 /* out = [xi . Cbar . xi]^-1 in, eq. (precf) with Cbar = <phi> C_m (eq. avstiff). */
 int hom_modb_precond(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum);
+
+/* Solve the same ncase macro strains on ncell cells at once.  ctxs[i] are
+ * independent contexts (own streams and workspaces, any grid sizes); one
+ * host thread per cell runs hom_solve on it and the device overlaps the
+ * cells' kernels.  info: NULL or ncell x ncase records (cell-major).
+ * Returns the worst status over the cells (negative errors first).  Each
+ * context then holds its own solutions as after hom_solve. */
+int hom_solve_batch(hom_ctx *const *ctxs, int ncell, const double *macro_strain, int ncase, double tol,
+                    int max_it, hom_solve_info *info);
+
+/* Launch-shape autotuner: for a grid and precision, time the kernels of one
+ * MINRES iteration (scratch contexts, random phase map, CUDA events) for
+ * candidate tiles of each FFT pass and write the fastest
+ * (rows3, tile2, tile1) to shape[3].  Cached per process and, when the
+ * environment variable HOM_TUNE_CACHE names a file, on disk.  Allocates and
+ * frees scratch contexts. */
+int hom_autotune(const int grid[3], int precision, int shape[3]);
 
 /* Grid, precision and workspace size of a context. */
 int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes);

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libhom.so")
-SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu", "hom_noalloc.cu"]
+SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu", "hom_noalloc.cu",
+           "hom_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -59,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")

@@ -755,6 +755,14 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     hom_options o;
     hom_default_options(&o);
     if (opt) o = *opt;
+    if (o.autotune && o.rows3 == 0 && o.tile2 == 0 && o.tile1 == 0) {
+        int shp[3] = {0, 0, 0};
+        if (hom_autotune(grid, o.precision, shp) == HOM_OK) {
+            o.rows3 = shp[0];
+            o.tile2 = shp[1];
+            o.tile1 = shp[2];
+        }
+    }
     if (o.solver != HOM_SOLVER_GALERKIN_MINRES && o.solver != HOM_SOLVER_MODBFFT_CG)
         return fail(nullptr, HOM_EINVAL, "bad solver");
     if (!(o.alpha >= 0.0) || !std::isfinite(o.alpha)) return fail(nullptr, HOM_EINVAL, "bad alpha");

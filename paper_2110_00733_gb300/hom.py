@@ -30,6 +30,7 @@ EXPORTED = [
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
+    "hom_solve_batch", "hom_autotune",
 ]
 
 
@@ -38,7 +39,8 @@ class hom_options(ctypes.Structure):
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("refine", ctypes.c_int),
                 ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int),
-                ("staging", ctypes.c_int), ("alpha", ctypes.c_double)]
+                ("staging", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -88,6 +90,9 @@ def load_library(path: str = LIB_PATH):
     lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
     lib.hom_apply_noalloc.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.hom_modb_apply.argtypes = [vp, vp, vp]
+    lib.hom_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, ctypes.POINTER(hom_solve_info)]
+    lib.hom_autotune.argtypes = [ip, ctypes.c_int, ip]
     lib.hom_modb_rhs.argtypes = [vp, dp, vp]
     lib.hom_modb_precond.argtypes = [vp, vp, vp]
     lib.hom_get_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
@@ -154,7 +159,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
                smoothing=HOM_SMOOTH_NONE, derivative=HOM_DERIV_ROTATED,
                precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
                device=-1, refine=3, shape=(0, 0, 0), staging=0,
-               solver=HOM_SOLVER_GALERKIN_MINRES, alpha=0.0) -> Context:
+               solver=HOM_SOLVER_GALERKIN_MINRES, alpha=0.0, autotune=False) -> Context:
     lib = load_library()
     opt = hom_options()
     lib.hom_default_options(ctypes.byref(opt))
@@ -167,6 +172,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
     opt.staging = int(staging)
     opt.solver = int(solver)
     opt.alpha = float(alpha)
+    opt.autotune = 1 if autotune else 0
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),
@@ -324,3 +330,25 @@ def hom_apply_noalloc(grid, phi, eps, out, E=1.0, nu=0.3, derivative=HOM_DERIV_R
     rc = lib.hom_apply_noalloc(g, _ptr(phi), float(E), float(nu), int(derivative), _ptr(eps), _ptr(out), stream)
     _check(None, rc)
     return out
+
+
+def hom_solve_batch(ctxs, macro_strain, tol=1e-6, max_it=1000):
+    """Solve the same macro strains on several cells at once.  Returns
+    (rc, [[info per case] per cell])."""
+    lib = load_library()
+    m = np.ascontiguousarray(np.asarray(macro_strain, dtype=np.float64).reshape(-1, 6))
+    ncase, ncell = m.shape[0], len(ctxs)
+    handles = (ctypes.c_void_p * ncell)(*[c.handle for c in ctxs])
+    infos = (hom_solve_info * (ncase * ncell))()
+    rc = lib.hom_solve_batch(handles, ncell, m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ncase,
+                             float(tol), int(max_it), infos)
+    _check(None, rc)
+    return rc, [[infos[i * ncase + k].as_dict() for k in range(ncase)] for i in range(ncell)]
+
+
+def hom_autotune(grid, precision=HOM_PREC_FP32_FIELDS):
+    lib = load_library()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid])
+    out = (ctypes.c_int * 3)()
+    _check(None, lib.hom_autotune(g, int(precision), out))
+    return tuple(out)

@@ -11,6 +11,9 @@ oracle's tests and the GPU library's tests and benchmark draw inputs from.
 * ``laminate(n, ...)``: layered phase map normal to x1 (closed-form pins).
 * ``random_phi(n, ...)``: i.i.d. phases for operator parity tests.
 * ``unit_sphere_strain(rng)``: macro strain uniform on the Mandel unit sphere.
+* ``as_printed(n, ...)``: a synthetic stand-in for the scanned as-printed cell
+  of section 6: octet cells whose strut surface is moved by a Gaussian random
+  field, with random spherical pores.
 """
 from __future__ import annotations
 
@@ -129,3 +132,62 @@ def unit_sphere_strain(rng) -> np.ndarray:
     t = m.copy()
     t[3:] /= np.sqrt(2.0)
     return t
+
+
+def gaussian_random_field(n, seed: int, corr_len: float = 3.0, std: float = 1.0):
+    """Periodic Gaussian random field on an n^3 grid (voxel units): seeded
+    white noise filtered by exp(-|k|^2 l^2 / 4), i.e. covariance
+    exp(-d^2 / (2 l^2)) up to normalisation, rescaled to the given standard
+    deviation."""
+    g = _grid(n)
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(g).astype(np.float32)
+    k = [np.fft.fftfreq(m) * 2 * np.pi for m in g]
+    kz = np.fft.rfftfreq(g[2]) * 2 * np.pi
+    k2 = k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + kz[None, None, :] ** 2
+    filt = np.exp(-k2 * corr_len ** 2 / 4.0).astype(np.float32)
+    f = np.fft.irfftn(np.fft.rfftn(w) * filt, s=g).astype(np.float32)
+    f -= f.mean()
+    f *= std / f.std()
+    return f
+
+
+def add_pores(phi, seed: int, porosity: float = 0.01, rmin: float = 2.0, rmax: float = 8.0):
+    """Carve spheres of radius U[rmin, rmax] voxels, centres drawn uniformly
+    and kept only inside the solid (phi >= 0.5), until the removed solid
+    volume reaches `porosity` of the solid volume.  Periodic.  In place."""
+    rng = np.random.default_rng(seed)
+    g = phi.shape
+    target = porosity * float(phi.sum(dtype=np.float64))
+    removed = 0.0
+    tries = 0
+    while removed < target and tries < 1000000:
+        tries += 1
+        c = [int(rng.integers(0, m)) for m in g]
+        if phi[c[0], c[1], c[2]] < 0.5:
+            continue
+        r = rng.uniform(rmin, rmax)
+        R = int(np.ceil(r))
+        idx = [np.arange(c[a] - R, c[a] + R + 1) % g[a] for a in range(3)]
+        d = [np.arange(-R, R + 1, dtype=np.float32) ** 2 for _ in range(3)]
+        inside = (d[0][:, None, None] + d[1][None, :, None] + d[2][None, None, :]) <= r * r
+        block = phi[np.ix_(idx[0], idx[1], idx[2])]
+        removed += float(block[inside].sum(dtype=np.float64))
+        block[inside] = 0.0
+        phi[np.ix_(idx[0], idx[1], idx[2])] = block
+    return phi
+
+
+def as_printed(n: int = 512, cells: int = 2, rho: float = 0.12, seed: int = 0, corr_len: float = 3.0,
+               std: float = 1.0, porosity: float = 0.01):
+    """Synthetic as-printed lattice: `cells`^3 octet cells on an n^3 grid whose
+    strut surface moves by a Gaussian random field (correlation length
+    `corr_len`, standard deviation `std`, both in voxels), Voigt fractions
+    from 4^3 sub-samples at the target density, then spherical pores
+    removing `porosity` of the solid.  Returns (phi float32, radius)."""
+    g = _grid(n)
+    grf = gaussian_random_field(g, seed, corr_len, std)
+    # a distance perturbation of one voxel is cells / n unit-cell lengths
+    phi, r = octet(g, rho, sub=4, cells=cells, dist_perturb=grf * (cells / g[0]))
+    add_pores(phi, seed + 1, porosity)
+    return phi, r

@@ -1,0 +1,29 @@
+"""Input generators: geometry only (none of the method's arithmetic)."""
+import numpy as np
+
+import rve_inputs as ri
+
+
+def test_octet_density_and_symmetry():
+    phi, r = ri.octet(24, 0.15)
+    assert abs(phi.mean() - 0.15) < 2e-3
+    assert 0 < r < 0.2
+    # cubic symmetry of the FCC truss: axis permutations map the cell onto itself
+    assert np.allclose(phi, phi.transpose(1, 0, 2), atol=1e-6)
+    assert np.allclose(phi, phi.transpose(2, 1, 0), atol=1e-6)
+
+
+def test_grf_statistics():
+    f = ri.gaussian_random_field(64, seed=3, corr_len=3.0, std=1.0)
+    assert abs(f.mean()) < 1e-5 and abs(f.std() - 1.0) < 1e-4
+    # correlation at lag 3 voxels: exp(-9 / (2 * 9)) = 0.61 for the Gaussian covariance
+    c3 = np.mean(f * np.roll(f, 3, axis=0))
+    assert 0.5 < c3 < 0.72
+
+
+def test_as_printed_small():
+    phi, r = ri.as_printed(64, cells=2, rho=0.12, seed=5)
+    assert 0.10 < phi.mean() < 0.125          # 12 % before pores, about 1 % of it carved
+    assert phi.min() >= 0 and phi.max() <= 1
+    rough, _ = ri.octet(64, 0.12, cells=2)
+    assert np.abs(phi - rough).mean() > 1e-3  # the surface moved
