@@ -96,6 +96,10 @@ typedef struct {
     int autotune;       /* nonzero (and no explicit rows3/tile2/tile1): launch
                            shapes from hom_autotune for this grid and precision */
     int reserved;
+    double sweep_floor; /* FP32 fields: smallest relative residual reduction one
+                           refinement sweep is asked for (0: 1e-6 for MINRES,
+                           1e-3 for PCG); the FP64 true residual is recomputed
+                           after every sweep */
 } hom_options;
 
 typedef struct {

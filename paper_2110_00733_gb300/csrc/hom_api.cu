@@ -23,6 +23,10 @@ thread_local std::string g_create_error;
 
 // smallest relative residual reduction one FP32-field MINRES sweep is asked for
 constexpr double kFp32SweepFloor = 1e-6;
+// PCG on A^alpha (not symmetric where chi_v is non-zero) in FP32 drifts away
+// from the FP64 residual sooner than MINRES: shorter sweeps, restarted from
+// the FP64 true residual, keep it converging
+constexpr double kFp32CgSweepFloor = 1e-3;
 // relative size of ||b|| / ||C : E_bar|| below which the right-hand side is
 // FFT round-off and is taken as zero (the paper is silent on this case)
 constexpr double kRhsZero = 1e-12;
@@ -58,6 +62,7 @@ struct hom_ctx {
     bool own_stream = false;
     int device_ptrs = 0;
     int refine = 3;
+    double sweep_floor = kFp32SweepFloor;
     int shape[3] = {0, 0, 0};   // launch-shape overrides (rows3, tile2, tile1)
     int staging = 0;            // 0: TMA-staged passes where supported, 1: plain loads
     int solver = HOM_SOLVER_GALERKIN_MINRES;
@@ -770,6 +775,8 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
         return fail(nullptr, HOM_EINVAL, "bad precision");
     if (o.rows3 < 0 || o.rows3 > 64 || o.tile2 < 0 || o.tile2 > 32 || o.tile1 < 0 || o.tile1 > 16)
         return fail(nullptr, HOM_EINVAL, "bad launch-shape override");
+    if (!(o.sweep_floor >= 0.0 && o.sweep_floor < 1.0))
+        return fail(nullptr, HOM_EINVAL, "sweep_floor must be in [0, 1)");
     hom_ctx *ctx = new hom_ctx();
     ctx->prec = o.precision;
     ctx->deriv = derivative;
@@ -779,6 +786,8 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     ctx->mu = 1.0 / (2.0 * (1.0 + nu));                // mu / E
     ctx->device_ptrs = o.device_ptrs;
     ctx->refine = o.refine < 0 ? 0 : o.refine;
+    ctx->sweep_floor = o.sweep_floor > 0.0 ? o.sweep_floor
+                                            : (o.solver == HOM_SOLVER_MODBFFT_CG ? kFp32CgSweepFloor : kFp32SweepFloor);
     ctx->shape[0] = o.rows3;
     ctx->shape[1] = o.tile2;
     ctx->shape[2] = o.tile1;
@@ -978,32 +987,45 @@ static int solve_case_modb(hom_ctx *ctx, int icase, const double *m, double tol,
     double tres = 1.0;
     int rc = residual(&tres);
     if (rc) return rc;
+    // FP32 fields: sweeps share the iteration budget; a sweep that raised the
+    // FP64 true residual is taken back and ends the solve
     const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
-    for (int sw = 0; sw < sweeps_max && tres > tol; ++sw) {
+    int budget = max_it;
+    for (int sw = 0; sw < sweeps_max && tres > tol && budget > 0; ++sw) {
         double sweep_tol = tol / tres;
         if (sweep_tol > 0.5) sweep_tol = 0.5;
-        if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < kFp32SweepFloor) sweep_tol = kFp32SweepFloor;
+        if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < ctx->sweep_floor) sweep_tol = ctx->sweep_floor;
         int it = 0, st = 0;
         double est = 0.0;
         if (ctx->prec == HOM_PREC_FP64) {
             CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double2) * nc3, cudaMemcpyDeviceToDevice, s));
-            rc = run_cg<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
+            rc = run_cg<double>(ctx, ctx->e64, sweep_tol, budget, &it, &est, &st);
             if (rc) return rc;
             Launch<double>::axpby(2 * nc3, s, 1.0, (const double *)ctx->xs, 1.0, (double *)x);
         } else {
             spec_d2f(nc3, s, ctx->r64, (float2 *)ctx->rhs);
-            rc = run_cg<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
+            rc = run_cg<float>(ctx, ctx->e32, sweep_tol, budget, &it, &est, &st);
             if (rc) return rc;
             spec_f2d_acc(nc3, s, (const float2 *)ctx->xs, x);
         }
         ctx->launches += 2;
+        budget -= it;
         inf->iterations += it;
         inf->est_residual = est * tres;
         inf->sweeps = sw + 1;
+        const double prev = tres;
         rc = residual(&tres);
         if (rc) return rc;
         if (st == HOM_ENAN) { status = HOM_ENAN; break; }
-        if (st == HOM_NOT_CONVERGED && tres > tol) { status = HOM_NOT_CONVERGED; break; }
+        if (ctx->prec == HOM_PREC_FP32_FIELDS && !(tres < prev)) {
+            spec_f2d_acc(nc3, s, (const float2 *)ctx->xs, x, -1.0);
+            ctx->launches += 1;
+            rc = residual(&tres);
+            if (rc) return rc;
+            status = HOM_NOT_CONVERGED;
+            break;
+        }
+        if (st == HOM_NOT_CONVERGED && tres > tol && ctx->prec == HOM_PREC_FP64) { status = HOM_NOT_CONVERGED; break; }
     }
     inf->true_residual = tres;
     if (status == HOM_OK && tres > tol) status = HOM_NOT_CONVERGED;
@@ -1102,7 +1124,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
             // sweep never asks for less and the next sweep refines further
             double sweep_tol = tol / tres;
             if (sweep_tol > 0.5) sweep_tol = 0.5;
-            if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < kFp32SweepFloor) sweep_tol = kFp32SweepFloor;
+            if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < ctx->sweep_floor) sweep_tol = ctx->sweep_floor;
             int it = 0, st = 0;
             double est = 0.0;
             if (ctx->prec == HOM_PREC_FP64) {

@@ -189,10 +189,10 @@ __global__ void k_spec_d2f(long long n, const double2 *in, float2 *out) {
         out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
-__global__ void k_spec_f2d_acc(long long n, const float2 *in, double2 *out) {
+__global__ void k_spec_f2d_acc(long long n, const float2 *in, double2 *out, double a) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double2 o = out[i];
-        out[i] = make_double2(o.x + (double)in[i].x, o.y + (double)in[i].y);
+        out[i] = make_double2(o.x + a * (double)in[i].x, o.y + a * (double)in[i].y);
     }
 }
 
@@ -365,8 +365,8 @@ void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const
 void spec_d2f(long long n, cudaStream_t st, const double2 *in, float2 *out) {
     k_spec_d2f<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
 }
-void spec_f2d_acc(long long n, cudaStream_t st, const float2 *in, double2 *out) {
-    k_spec_f2d_acc<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);
+void spec_f2d_acc(long long n, cudaStream_t st, const float2 *in, double2 *out, double a) {
+    k_spec_f2d_acc<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out, a);
 }
 void mean_stress64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
                    const double *macro, double *partials) {

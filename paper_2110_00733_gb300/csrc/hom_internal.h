@@ -148,7 +148,8 @@ template <typename R> struct Launch {
 void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
                      double *partials, int nc = 6);             // r = b - ax, weighted ||r||^2
 void spec_d2f(long long ncplx, cudaStream_t st, const double2 *in, float2 *out);
-void spec_f2d_acc(long long ncplx, cudaStream_t st, const float2 *in, double2 *out);   // out += in
+void spec_f2d_acc(long long ncplx, cudaStream_t st, const float2 *in, double2 *out,
+                  double a = 1.0);   // out += a in
 void mean_stress64(long long V, cudaStream_t st, const double *x, const double *phi, double lam, double mu,
                    const double *macro_mandel, double *partials);   // partials[6][ew_grid(V)]
 template <typename Ro>
