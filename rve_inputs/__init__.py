@@ -55,6 +55,7 @@ def _load():
                                       ctypes.c_int, fp]
             lib.octet_phi.restype = ctypes.c_double
             lib.octet_center_distance.argtypes = [fp, ip, ctypes.c_int]
+            lib.octet_phi_at_radius.argtypes = [fp, ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, fp]
             _lib = lib
     return _lib
 
@@ -84,6 +85,20 @@ def octet(n, rho: float, sub: int = 4, cells: int = 1, dist_perturb=None):
     if r < 0:
         raise RuntimeError("octet voxelizer could not bracket the strut radius")
     return phi, float(r)
+
+
+def octet_at_radius(n, r: float, sub: int = 4, cells: int = 1, dist_perturb=None):
+    """phi for a given strut radius, every voxel sub-sampled (slow; tests)."""
+    lib = _load()
+    g = _grid(n)
+    phi = np.zeros(g, dtype=np.float32)
+    pert = None
+    if dist_perturb is not None:
+        pert = np.ascontiguousarray(dist_perturb, dtype=np.float32).reshape(g)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.octet_phi_at_radius(phi.ctypes.data_as(fp), (ctypes.c_int * 3)(*g), int(cells), float(r), int(sub),
+                            None if pert is None else pert.ctypes.data_as(fp))
+    return phi
 
 
 def octet_center_distance(n, cells: int = 1):
@@ -146,7 +161,7 @@ def gaussian_random_field(n, seed: int, corr_len: float = 3.0, std: float = 1.0)
     kz = np.fft.rfftfreq(g[2]) * 2 * np.pi
     k2 = k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + kz[None, None, :] ** 2
     filt = np.exp(-k2 * corr_len ** 2 / 4.0).astype(np.float32)
-    f = np.fft.irfftn(np.fft.rfftn(w) * filt, s=g).astype(np.float32)
+    f = np.fft.irfftn(np.fft.rfftn(w) * filt, s=g, axes=(0, 1, 2)).astype(np.float32)
     f -= f.mean()
     f *= std / f.std()
     return f
@@ -182,9 +197,11 @@ def as_printed(n: int = 512, cells: int = 2, rho: float = 0.12, seed: int = 0, c
                std: float = 1.0, porosity: float = 0.01):
     """Synthetic as-printed lattice: `cells`^3 octet cells on an n^3 grid whose
     strut surface moves by a Gaussian random field (correlation length
-    `corr_len`, standard deviation `std`, both in voxels), Voigt fractions
-    from 4^3 sub-samples at the target density, then spherical pores
-    removing `porosity` of the solid.  Returns (phi float32, radius)."""
+    `corr_len`, standard deviation `std`, both in voxels; interpolated
+    trilinearly to the sub-sample points and added to the axis distance),
+    Voigt fractions from 4^3 sub-samples at the target density, then
+    spherical pores removing `porosity` of the solid.  Returns
+    (phi float32, radius)."""
     g = _grid(n)
     grf = gaussian_random_field(g, seed, corr_len, std)
     # a distance perturbation of one voxel is cells / n unit-cell lengths

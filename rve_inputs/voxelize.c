@@ -67,11 +67,52 @@ static double dist_at(const int n[3], int cells, double gi, double gj, double gk
     return octet_axis_distance(p);
 }
 
+/* Perturbation at grid position (gi, gj, gk): trilinear interpolation of the
+ * per-voxel values p, which sit at the voxel centres (i + 1/2, ...); periodic. */
+static double pert_at(const float *p, const int n[3], double gi, double gj, double gk) {
+    const double g[3] = {gi - 0.5, gj - 0.5, gk - 0.5};
+    int i0[3], i1[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = floor(g[a]);
+        t[a] = g[a] - f;
+        int b = (int)f % n[a];
+        if (b < 0) b += n[a];
+        i0[a] = b;
+        i1[a] = (b + 1) % n[a];
+    }
+    double acc = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const int x = (c & 4) ? i1[0] : i0[0], y = (c & 2) ? i1[1] : i0[1], z = (c & 1) ? i1[2] : i0[2];
+        const double w = ((c & 4) ? t[0] : 1.0 - t[0]) * ((c & 2) ? t[1] : 1.0 - t[1]) *
+                         ((c & 1) ? t[2] : 1.0 - t[2]);
+        acc += w * p[((long)x * n[1] + y) * n[2] + z];
+    }
+    return acc;
+}
+
+/* Largest change of p between voxel v and any of its 26 periodic neighbours:
+ * bounds how far the interpolated perturbation inside voxel v strays from its
+ * centre value. */
+static float pert_spread(const float *p, const int n[3], long v) {
+    int i = (int)(v / ((long)n[1] * n[2])), j = (int)((v / n[2]) % n[1]), k = (int)(v % n[2]);
+    float m = 0.f;
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b)
+            for (int c = -1; c <= 1; ++c) {
+                int x = (i + a + n[0]) % n[0], y = (j + b + n[1]) % n[1], z = (k + c + n[2]) % n[2];
+                float d = fabsf(p[((long)x * n[1] + y) * n[2] + z] - p[v]);
+                if (d > m) m = d;
+            }
+    return m;
+}
+
 /*
  * phi: output, V floats.  n: grid.  cells: unit cells per box edge.
  * rho: target relative density.  sub: sub-samples per voxel edge (4 for 4^3).
- * dist_perturb: optional V floats added to the axis distance of every point of
- *   the voxel (unit-cell units), may be NULL (used for as-printed surfaces).
+ * dist_perturb: optional V floats (unit-cell units, one per voxel centre),
+ *   interpolated trilinearly to every sub-sample point and added to its axis
+ *   distance; may be NULL (used for as-printed surfaces).
  * Returns the strut radius in unit-cell units (negative on failure).
  */
 double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
@@ -79,14 +120,22 @@ double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
     long V = (long)n[0] * n[1] * n[2];
     int S = sub * sub * sub;
     float *dc = (float *)malloc(sizeof(float) * V);
-    if (!dc) return -1.0;
-    /* 1. axis distance at voxel centres */
+    float *sp = (float *)malloc(sizeof(float) * V);
+    if (!dc || !sp) {
+        free(dc);
+        free(sp);
+        return -1.0;
+    }
+    /* 1. axis distance at voxel centres, and how far the perturbation may
+     *    move it inside the voxel (sub-point distances lie within
+     *    dc +- (sp + delta), delta the geometric half diagonal below) */
 #pragma omp parallel for schedule(static)
     for (long v = 0; v < V; ++v) {
         int i = (int)(v / ((long)n[1] * n[2])), j = (int)((v / n[2]) % n[1]), k = (int)(v % n[2]);
         double d = dist_at(n, cells, i + 0.5, j + 0.5, k + 0.5);
         if (dist_perturb) d += dist_perturb[v];
         dc[v] = (float)d;
+        sp[v] = dist_perturb ? pert_spread(dist_perturb, n, v) : 0.f;
     }
     /* 2. plain-voxel estimate of the radius: quantile of the centre distances */
     float *sorted = (float *)malloc(sizeof(float) * V);
@@ -106,15 +155,16 @@ double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
     for (int attempt = 0; attempt < 12 && radius < 0; ++attempt, band *= 2.0) {
         double lo = r0 - band, hi = r0 + band;
         long n_inner = 0, n_band = 0;
+        /* inner: every sub-point certainly below lo; band: sub-sampled */
         for (long v = 0; v < V; ++v) {
-            if (dc[v] < lo) ++n_inner;
-            else if (dc[v] <= hi) ++n_band;
+            if (dc[v] + sp[v] < lo) ++n_inner;
+            else if (dc[v] - sp[v] <= hi) ++n_band;
         }
         float *bd = (float *)malloc(sizeof(float) * (size_t)n_band * S);
         long *bidx = (long *)malloc(sizeof(long) * (size_t)(n_band > 0 ? n_band : 1));
         long c = 0;
         for (long v = 0; v < V; ++v)
-            if (dc[v] >= lo && dc[v] <= hi) bidx[c++] = v;
+            if (dc[v] + sp[v] >= lo && dc[v] - sp[v] <= hi) bidx[c++] = v;
 #pragma omp parallel for schedule(dynamic, 256)
         for (long b = 0; b < n_band; ++b) {
             long v = bidx[b];
@@ -123,9 +173,10 @@ double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
             for (int a = 0; a < sub; ++a)
                 for (int bb = 0; bb < sub; ++bb)
                     for (int cc = 0; cc < sub; ++cc) {
-                        double d = dist_at(n, cells, i + (a + 0.5) / sub, j + (bb + 0.5) / sub,
-                                           k + (cc + 0.5) / sub);
-                        if (dist_perturb) d += dist_perturb[v];
+                        const double gi = i + (a + 0.5) / sub, gj = j + (bb + 0.5) / sub,
+                                     gk = k + (cc + 0.5) / sub;
+                        double d = dist_at(n, cells, gi, gj, gk);
+                        if (dist_perturb) d += pert_at(dist_perturb, n, gi, gj, gk);
                         bd[b * S + s++] = (float)d;
                     }
         }
@@ -148,7 +199,7 @@ double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
             if (cnt >= 1 && cnt < nb && sb[cnt - 1] < sb[cnt] &&
                 r >= lo + delta && r <= hi - delta) {
                 radius = r;
-                for (long v = 0; v < V; ++v) phi[v] = (dc[v] < lo) ? 1.0f : 0.0f;
+                for (long v = 0; v < V; ++v) phi[v] = (dc[v] + sp[v] < lo) ? 1.0f : 0.0f;
 #pragma omp parallel for schedule(static)
                 for (long b = 0; b < n_band; ++b) {
                     int cnt = 0;
@@ -162,7 +213,29 @@ double octet_phi(float *phi, const int n[3], int cells, double rho, int sub,
         free(bidx);
     }
     free(dc);
+    free(sp);
     return radius;
+}
+
+/* phi for a given radius by sub-sampling every voxel (no band shortcut);
+ * used by tests of octet_phi. */
+void octet_phi_at_radius(float *phi, const int n[3], int cells, double r, int sub, const float *dist_perturb) {
+    long V = (long)n[0] * n[1] * n[2];
+    int S = sub * sub * sub;
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < V; ++v) {
+        int i = (int)(v / ((long)n[1] * n[2])), j = (int)((v / n[2]) % n[1]), k = (int)(v % n[2]);
+        int cnt = 0;
+        for (int a = 0; a < sub; ++a)
+            for (int bb = 0; bb < sub; ++bb)
+                for (int cc = 0; cc < sub; ++cc) {
+                    const double gi = i + (a + 0.5) / sub, gj = j + (bb + 0.5) / sub, gk = k + (cc + 0.5) / sub;
+                    double d = dist_at(n, cells, gi, gj, gk);
+                    if (dist_perturb) d += pert_at(dist_perturb, n, gi, gj, gk);
+                    cnt += ((float)d < r);
+                }
+        phi[v] = (float)cnt / (float)S;
+    }
 }
 
 /* Axis distance field at voxel centres (for tests of the geometry). */

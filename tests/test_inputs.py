@@ -27,3 +27,17 @@ def test_as_printed_small():
     assert phi.min() >= 0 and phi.max() <= 1
     rough, _ = ri.octet(64, 0.12, cells=2)
     assert np.abs(phi - rough).mean() > 1e-3  # the surface moved
+
+
+def test_band_voxelizer_matches_full_sampling():
+    """The radius search classifies voxels far from the surface without
+    sub-sampling them; with the random-field perturbation that shortcut must
+    still give exactly what sub-sampling every voxel gives."""
+    n = 32
+    grf = ri.gaussian_random_field(n, seed=2) * (2.0 / n)
+    phi, r = ri.octet(n, 0.12, cells=2, dist_perturb=grf)
+    full = ri.octet_at_radius(n, r, cells=2, dist_perturb=grf)
+    assert np.array_equal(phi, full)
+    assert abs(phi.mean() - 0.12) < 1.0 / (64 * n ** 3) + 1e-7
+    plain, r0 = ri.octet(n, 0.12, cells=2)
+    assert np.array_equal(plain, ri.octet_at_radius(n, r0, cells=2))
