@@ -51,8 +51,8 @@ def kernel_bytes_per_voxel(n3: int) -> dict:
         "x3_c2r_law_r2c": 2 * spec + 4,    # + phi
         "x2_fwd": 2 * spec,
         "x1_fwd_gamma_dot": 3 * spec,      # read work, write p, read v (dot)
-        "lanczos": 4 * spec,               # read p, v_k, v_{k-1}; write p
-        "update": 8 * spec,                # read v, w1, w2, x, p; write w, x, v
+        # read p, u_k, u_{k-1}, w_{k-2}, w_{k-3}, x; write u_{k+1}, w_{k-1}, x
+        "lanczos_update": 9 * spec,
     }
 
 

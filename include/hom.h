@@ -185,10 +185,11 @@ int hom_project(hom_ctx *ctx, const void *in, void *out);
  * of this context, each launched `reps` times back to back on the context's
  * stream between two CUDA events, on the workspace's current contents (an
  * instrument for roofline measurements; it changes no solver state that a
- * later hom_solve reads).  ms[0..8]: n1 pass (projector + inverse), n2 inverse,
+ * later hom_solve reads).  ms[0..7]: n1 pass (projector + inverse), n2 inverse,
  * n3 pass (C2R + material law + R2C), n2 forward, n1 pass (forward +
- * projector + dot product), alpha reduction, Lanczos axpy + norm, Givens
- * step, w/x/v update.  Returns the number of entries written (<= nmax). */
+ * projector + dot product), alpha reduction, Lanczos step + norm fused with
+ * the lagged w/x update, Givens step.  Returns the number of entries
+ * written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* A(eps) of hom_apply for a small cell, allocating no device memory.  The

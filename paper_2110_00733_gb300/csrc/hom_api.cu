@@ -365,31 +365,31 @@ static int spec_norm2(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, double *out) 
     return HOM_OK;
 }
 
-// Capture graph_iters MINRES iterations (pointer rotation period 6) once.
+// Capture graph_iters MINRES iterations once (graph_iters even: the buffer
+// roles repeat every 2 steps).  Unnormalised Lanczos vectors u_k = beta_k v_k
+// alternate between vbuf[1] (odd k) and vbuf[0] (even k); p = A u_k is
+// vbuf[2]; w_j sits in wbuf[0] for even j and wbuf[1] for odd j.
 template <typename R>
 static int build_graph(hom_ctx *ctx, Engine<R> &E) {
     if (ctx->graph) return HOM_OK;
-    cpx<R> *v[3] = {(cpx<R> *)ctx->vbuf[0], (cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->vbuf[2]};  // v_{k-1}, v_k, p
-    cpx<R> *w[2] = {(cpx<R> *)ctx->wbuf[0], (cpx<R> *)ctx->wbuf[1]};                          // w_{k-1}, w_{k-2}
+    cpx<R> *ua = (cpx<R> *)ctx->vbuf[0], *ub = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
+    cpx<R> *wc = (cpx<R> *)ctx->wbuf[0], *wd = (cpx<R> *)ctx->wbuf[1];
     cpx<R> *x = (cpx<R> *)ctx->xs;
     const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
     cudaGraph_t graph;
     CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     long long before = ctx->launches;
     for (int it = 0; it < ctx->graph_iters; ++it) {
-        cpx<R> *vprev = v[0], *vk = v[1], *p = v[2];
-        cpx<R> *w1 = w[0], *w2 = w[1];
-        // p = A^ v_k, partial <v_k, p>
-        op_spec<R>(ctx, E, vk, p, true, ctx->partials, ctx->d_state);
+        const bool odd = (it % 2) == 0;          // step k = it + 1 (mod 2)
+        cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
+        cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;   // w_{k-2}, w_{k-3}
+        // p = A^ u_k, partial <u_k, p>
+        op_spec<R>(ctx, E, uk, p, true, ctx->partials, ctx->d_state);
         scalar_alpha(ctx->stream, ctx->d_state, ctx->partials, np1);
-        // p -= alpha v_k + beta_k v_{k-1}; partial ||p||^2
-        Launch<R>::lanczos(E.g, ctx->stream, p, vk, vprev, ctx->d_state, ctx->partials);
+        // u_{k+1} over u_{k-1}, partial ||u_{k+1}||^2, lagged w_{k-1} / x update
+        Launch<R>::lanczos_update(E.g, ctx->stream, p, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
         scalar_givens(ctx->stream, ctx->d_state, ctx->partials, npe);
-        // w_k (into w_{k-2}'s buffer), x_k, v_{k+1} = p / beta_{k+1} (in place)
-        Launch<R>::update(E.g, ctx->stream, p, vk, w1, w2, x, ctx->d_state);
-        ctx->launches += 4;
-        v[0] = vk; v[1] = p; v[2] = vprev;
-        w[0] = w2; w[1] = w1;
+        ctx->launches += 3;
     }
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -423,10 +423,9 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         CU(cudaStreamSynchronize(s));
         return HOM_OK;
     }
-    // v_0 = 0, v_1 = rhs / beta_1, w = 0
+    // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0
     CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nr, s));
-    Launch<R>::axpby(nr, s, 1.0 / beta1, (const R *)ctx->rhs, 0.0, (R *)ctx->vbuf[1]);
-    ctx->launches += 1;
+    CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nr, s));
     CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nr, s));
     // replay the captured iterations until the state says done
@@ -442,6 +441,10 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         CU(cudaStreamSynchronize(s));
         if (ctx->h_state->done || replays >= max_replays) break;
     }
+    // the last step's lagged w / x update
+    Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->wbuf[0],
+                            (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state);
+    ctx->launches += 1;
     *iters = ctx->h_state->k;
     *est = ctx->h_state->est;
     *status = ctx->h_state->status == -5 ? HOM_ENAN : (ctx->h_state->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
@@ -1265,8 +1268,10 @@ static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, i
     cpx<R> *w1 = (cpx<R> *)ctx->wbuf[0], *w2 = (cpx<R> *)ctx->wbuf[1], *x = (cpx<R> *)ctx->xs;
     // a private state that never stops, unit-size coefficients
     MinresState h{};
-    h.beta1 = 1.0; h.beta = 0.5; h.alpha = 0.25; h.c = -1.0; h.s = 0.0; h.phibar = 1.0; h.tol = 0.0;
+    h.beta1 = 1.0; h.beta = 0.5; h.beta_prev = 0.5; h.alpha = 0.25; h.c = -1.0; h.s = 0.0; h.phibar = 1.0;
+    h.tol = 0.0;
     h.u_delta = 0.1; h.u_eps = 0.1; h.u_inv_gamma = 1.0; h.u_tau = 0.0; h.u_inv_beta = 1.0;
+    h.k = 1;                  // the lagged w / x update runs
     h.max_it = 1 << 30;
     MinresState *d = nullptr;
     CU(cudaMalloc(&d, sizeof(MinresState)));
@@ -1274,7 +1279,7 @@ static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, i
     for (void *b : {ctx->vbuf[0], ctx->vbuf[1], ctx->vbuf[2], ctx->wbuf[0], ctx->wbuf[1], ctx->xs})
         CU(cudaMemsetAsync(b, 0, sizeof(R) * nr, s));
     const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
-    const int nk = 9;
+    const int nk = 8;
     for (int k = 0; k < nk && k < nmax; ++k) {
         for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
             const int r = pass ? reps : 1;
@@ -1288,10 +1293,9 @@ static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, i
                     case 3: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
                     case 4: Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | X1_DOT, E.spec, p, v1, ctx->partials, d); break;
                     case 5: scalar_alpha(s, d, ctx->partials, np1); break;
-                    case 6: Launch<R>::lanczos(E.g, s, p, v1, v0, d, ctx->partials); break;
-                    case 7: scalar_givens(s, d, ctx->partials, npe);
-                            CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
-                    default: Launch<R>::update(E.g, s, p, v1, w1, w2, x, d); break;
+                    case 6: Launch<R>::lanczos_update(E.g, s, p, v1, v0, w1, w2, x, d, ctx->partials); break;
+                    default: scalar_givens(s, d, ctx->partials, npe);
+                             CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
                 }
             }
             CU(cudaEventRecord(ctx->ev1, s));

@@ -48,14 +48,15 @@ __global__ void k_reduce_to(const double *partials, int np, double *out) {
 }
 
 // MINRES set-up from ||b||^2: beta_1, phibar_0 = beta_1, c_0 = -1, s_0 = 0,
-// delta-bar_1 = 0, epsilon_1 = 0 (Paige-Saunders; the v_1 = b / beta_1
-// scaling is done by the caller).
+// delta-bar_1 = 0, epsilon_1 = 0 (Paige-Saunders).  The Lanczos vectors are
+// kept unnormalised, u_k = beta_k v_k, so u_1 = b and beta_0 = 0.
 __global__ void k_scalar_start(MinresState *st, const double *partials, int np, double tol, int max_it) {
     const double b2 = reduce_partials(partials, np);
     if (threadIdx.x != 0) return;
     const double beta1 = sqrt(b2 > 0 ? b2 : 0.0);
     st->beta1 = beta1;
-    st->beta = 0.0;     // no v_0 term in the first Lanczos step
+    st->beta = beta1;
+    st->beta_prev = 0.0;   // no v_0 term in the first Lanczos step
     st->alpha = 0.0;
     st->c = -1.0;
     st->s = 0.0;
@@ -74,16 +75,18 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
     if (!isfinite(beta1)) { st->status = -5; st->done = 1; st->done_update = 1; }
 }
 
+// alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2
 __global__ void k_scalar_alpha(MinresState *st, const double *partials, int np) {
     if (st->done) return;
     const double a = reduce_partials(partials, np);
-    if (threadIdx.x == 0) st->alpha = a;
+    if (threadIdx.x == 0) st->alpha = a / (st->beta * st->beta);
 }
 
 // MINRES step k: apply the previous Givens rotation to the new column of the
-// Lanczos tridiagonal, form the next rotation, and the coefficients of w_k,
-// x_k and v_{k+1}; stop when phibar_k / beta_1 <= tol, beta_{k+1} = 0, or k
-// reaches max_it.
+// Lanczos tridiagonal, form the next rotation, and the coefficients of the
+// w_k / x_k update (applied by the next step's kernel, or by the flush after
+// the loop); stop when phibar_k / beta_1 <= tol, beta_{k+1} = 0, or k reaches
+// max_it.
 __global__ void k_scalar_givens(MinresState *st, const double *partials, int np) {
     if (st->done) return;
     const double bn2 = reduce_partials(partials, np);
@@ -103,12 +106,13 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
     st->u_eps = st->eps;            // epsilon_k multiplies w_{k-2}
     st->u_inv_gamma = 1.0 / gamma;
     st->u_tau = tau;
-    st->u_inv_beta = (beta_next > 0.0) ? 1.0 / beta_next : 0.0;
+    st->u_inv_beta = 1.0 / st->beta;   // v_k = u_k / beta_k in the lagged update
     st->c = cn;
     st->s = sn;
     st->dbar = dbar_next;
     st->eps = eps_next;
     st->phibar = phibar;
+    st->beta_prev = st->beta;
     st->beta = beta_next;
     st->k += 1;
     st->est = phibar / st->beta1;
@@ -119,7 +123,7 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
         return;
     }
     if (st->est <= st->tol || beta_next == 0.0) {
-        st->done = 1;               // this iteration's update still runs
+        st->done = 1;               // the flush still applies this step's update
     } else if (st->k >= st->max_it) {
         st->status = 1;
         st->done = 1;

@@ -26,20 +26,23 @@ namespace hom {
 struct MinresState {
     int done;          // no further operator / Krylov work (first field: the
                        // pass kernels read it through any solver's state)
-    int done_update;   // the last w/x update has been applied
+    int done_update;   // set with done on a NaN: keep the last finite iterate (no flush)
     int k;             // iterations done
     int max_it;
     int status;        // 0 ok, 1 max_it, -5 NaN
     int pad;
     double beta1;      // ||b||
-    double beta;       // beta_k: coefficient of v_{k-1} in the next Lanczos step
+    double beta;       // beta_k = ||u_k||: the stored Lanczos vector u_k = beta_k v_k
+    double beta_prev;  // beta_{k-1} (0 before the second step: no v_0 term)
     double alpha;      // alpha_k
     double c, s;       // previous Givens rotation
     double dbar;       // delta-bar_{k+1}
     double eps;        // epsilon_{k+1}
     double phibar;     // phi-bar_k
     double tol;
-    // coefficients of the w / x / v update of the current iteration
+    // coefficients of the w / x update of the last finished iteration k,
+    // applied one iteration later: w_k = (u_k u_inv_beta - u_delta w_{k-1}
+    // - u_eps w_{k-2}) u_inv_gamma, x += u_tau w_k
     double u_delta, u_eps, u_inv_gamma, u_tau, u_inv_beta;
     double est;        // phibar_k / beta_1
 };
@@ -117,12 +120,17 @@ template <typename R> struct Launch {
     // the weighted partial sum <dotv, out> per CTA
     static void x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *in, cpx<R> *out,
                    const cpx<R> *dotv, double *partials, const MinresState *state);
-    // p -= alpha v + beta vprev ; weighted partial ||p||^2   (spectral vectors)
-    static void lanczos(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *vprev,
-                        const MinresState *state, double *partials);
-    // w2 <- (v - delta w1 - eps w2)/gamma ; x += tau w2 ; p <- p / beta_next
-    static void update(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *w1, cpx<R> *w2,
-                       cpx<R> *x, MinresState *state);
+    // MINRES step k on unnormalised Lanczos vectors u_j = beta_j v_j, p = A u_k:
+    //   um <- (p - alpha u_k - beta_k^2/beta_{k-1} um) / beta_k   (= u_{k+1}),
+    //   weighted partial ||u_{k+1}||^2, and the lagged update of step k-1
+    //   (k > 1): wb <- (um_old/beta_{k-1} - delta wa - eps wb) / gamma,
+    //   x += tau wb.  wa = w_{k-2}, wb = w_{k-3} on entry.
+    static void lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> *p, const cpx<R> *uk, cpx<R> *um,
+                               const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials);
+    // the lagged update of the last step K after the loop; u_K sits in ub
+    // for odd K, in ua for even K; w_{K-1} in wd for even K, wc for odd K
+    static void minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
+                             cpx<R> *wd, cpx<R> *x, MinresState *state);
     // y = a x + b y over n reals
     static void axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y);
     // weighted partial ||x||^2 of a spectral vector with nc components per frequency

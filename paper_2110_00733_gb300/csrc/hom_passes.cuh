@@ -341,12 +341,7 @@ template <typename R, int NF>
 __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
                                             cpx<R> *__restrict__ out, const cpx<R> *__restrict__ dotv,
                                             double *__restrict__ partials, const MinresState *state) {
-    if (skip(state)) {
-        // the iteration after convergence: the pending w/x update is done
-        if ((flags & X1_GAMMA_IN) && blockIdx.x == 0 && threadIdx.x == 0)
-            const_cast<MinresState *>(state)->done_update = 1;
-        return;
-    }
+    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int NC = g.nc, N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
@@ -470,11 +465,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
                                             const __grid_constant__ CUtensorMap tout,
                                             const __grid_constant__ CUtensorMap tdot, double *__restrict__ partials,
                                             const MinresState *state) {
-    if (skip(state)) {
-        if ((flags & X1_GAMMA_IN) && blockIdx.x == 0 && threadIdx.x == 0)
-            const_cast<MinresState *>(state)->done_update = 1;
-        return;
-    }
+    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     const int NC = g.nc, N = g.n1, T = g.tile1, H = g.h, L = NC * T;
@@ -568,17 +559,32 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
 // Krylov vector kernels on half spectra (n = 6 S complex values).  The
 // Parseval weight of element i depends on k3 = (i / 6) mod h.
 // ---------------------------------------------------------------------------
+// MINRES step on unnormalised Lanczos vectors (see Launch::lanczos_update).
+// Scalars come from the FP64 state: beta_k, beta_{k-1}, alpha_k, and the
+// coefficients of the lagged w / x update of step k-1.
 template <typename R>
-__global__ void __launch_bounds__(kEwThreads) k_lanczos(int n, int h, int n3, cpx<R> *__restrict__ p,
-                                                        const cpx<R> *__restrict__ v, const cpx<R> *__restrict__ vprev,
-                                                        const MinresState *st, double *__restrict__ partials) {
+__global__ void __launch_bounds__(kEwThreads) k_lanczos_update(int n, int h, int n3, const cpx<R> *__restrict__ p,
+                                                               const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
+                                                               const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
+                                                               cpx<R> *__restrict__ x, const MinresState *st,
+                                                               double *__restrict__ partials) {
     if (skip(st)) return;
-    const R a = (R)st->alpha, b = (R)st->beta;
+    const double bk = st->beta, bkm = st->beta_prev;
+    const R cp = (R)(1.0 / bk), cu = (R)(-st->alpha / bk), cv = (R)(bkm > 0.0 ? -bk / bkm : 0.0);
+    const bool lagged = st->k > 0;
+    const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
+            ib = (R)st->u_inv_beta;
     Acc<R> acc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const cpx<R> x = p[i], y = v[i], z = vprev[i];
-        const cpx<R> q = mk<R>(x.x - a * y.x - b * z.x, x.y - a * y.y - b * z.y);
-        p[i] = q;
+        const cpx<R> pp = p[i], u = uk[i], uo = um[i];
+        const cpx<R> q = mk<R>(cp * pp.x + cu * u.x + cv * uo.x, cp * pp.y + cu * u.y + cv * uo.y);
+        um[i] = q;
+        if (lagged) {
+            const cpx<R> a = wa[i], b = wb[i], xx = x[i];
+            const cpx<R> wn = mk<R>((uo.x * ib - d * a.x - e * b.x) * ig, (uo.y * ib - d * a.y - e * b.y) * ig);
+            wb[i] = wn;
+            x[i] = mk<R>(xx.x + tau * wn.x, xx.y + tau * wn.y);
+        }
         const R w = (R)pweight((i / 6) % h, n3);
         acc.add_prod(w * q.x, q.x);
         acc.add_prod(w * q.y, q.y);
@@ -587,19 +593,25 @@ __global__ void __launch_bounds__(kEwThreads) k_lanczos(int n, int h, int n3, cp
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The lagged w / x update of the last step K; skipped when there is none
+// or the state kept the last finite iterate.
 template <typename R>
-__global__ void __launch_bounds__(kEwThreads) k_update(int n, cpx<R> *__restrict__ p, const cpx<R> *__restrict__ v,
-                                                       const cpx<R> *__restrict__ w1, cpx<R> *__restrict__ w2,
-                                                       cpx<R> *__restrict__ x, const MinresState *st) {
-    if (st->done_update) return;
+__global__ void __launch_bounds__(kEwThreads) k_minres_flush(int n, const cpx<R> *__restrict__ ua,
+                                                             const cpx<R> *__restrict__ ub, cpx<R> *__restrict__ wc,
+                                                             cpx<R> *__restrict__ wd, cpx<R> *__restrict__ x,
+                                                             const MinresState *st) {
+    const int K = st->k;
+    if (st->done_update || K <= 0) return;
+    const cpx<R> *u = (K & 1) ? ub : ua;
+    const cpx<R> *wa = (K & 1) ? wc : wd;      // w_{K-1}
+    cpx<R> *wb = (K & 1) ? wd : wc;            // w_{K-2}, overwritten by w_K
     const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
             ib = (R)st->u_inv_beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const cpx<R> vv = v[i], a = w1[i], b = w2[i], xx = x[i], pp = p[i];
-        const cpx<R> wn = mk<R>((vv.x - d * a.x - e * b.x) * ig, (vv.y - d * a.y - e * b.y) * ig);
-        w2[i] = wn;
+        const cpx<R> uu = u[i], a = wa[i], b = wb[i], xx = x[i];
+        const cpx<R> wn = mk<R>((uu.x * ib - d * a.x - e * b.x) * ig, (uu.y * ib - d * a.y - e * b.y) * ig);
+        wb[i] = wn;
         x[i] = mk<R>(xx.x + tau * wn.x, xx.y + tau * wn.y);
-        p[i] = mk<R>(pp.x * ib, pp.y * ib);
     }
 }
 
@@ -798,17 +810,17 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 }
 
 template <typename R>
-void Launch<R>::lanczos(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *vprev,
-                        const MinresState *state, double *partials) {
+void Launch<R>::lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> *p, const cpx<R> *uk, cpx<R> *um,
+                               const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials) {
     const int n = (int)(6 * g.S);
-    k_lanczos<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, p, v, vprev, state, partials);
+    k_lanczos_update<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.h, g.n3, p, uk, um, wa, wb, x, state, partials);
 }
 
 template <typename R>
-void Launch<R>::update(const Geometry &g, cudaStream_t st, cpx<R> *p, const cpx<R> *v, const cpx<R> *w1, cpx<R> *w2,
-                       cpx<R> *x, MinresState *state) {
+void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
+                             cpx<R> *wd, cpx<R> *x, MinresState *state) {
     const int n = (int)(6 * g.S);
-    k_update<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, p, v, w1, w2, x, state);
+    k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, ua, ub, wc, wd, x, state);
 }
 
 template <typename R>

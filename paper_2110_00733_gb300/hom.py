@@ -294,7 +294,7 @@ def hom_project(ctx: Context, field, out=None):
 
 
 KERNEL_NAMES = ["x1_inv_gamma", "x2_inv", "x3_c2r_law_r2c", "x2_fwd", "x1_fwd_gamma_dot", "alpha",
-                "lanczos", "givens", "update"]
+                "lanczos_update", "givens"]
 
 
 def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:

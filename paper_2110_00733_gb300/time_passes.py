@@ -26,7 +26,7 @@ from paper_2110_00733_gb300 import hom  # noqa: E402
 def bytes_per_voxel(n3: int) -> dict:
     spec = 48.0 * (n3 // 2 + 1) / n3
     return {"x1_inv_gamma": 2 * spec, "x2_inv": 2 * spec, "x3_c2r_law_r2c": 2 * spec + 4,
-            "x2_fwd": 2 * spec, "x1_fwd_gamma_dot": 3 * spec, "lanczos": 4 * spec, "update": 8 * spec}
+            "x2_fwd": 2 * spec, "x1_fwd_gamma_dot": 3 * spec, "lanczos_update": 9 * spec}
 
 
 def main():
