@@ -142,9 +142,9 @@ def forward(P, phi, Ebar, specs=None, store=None):
 
     x = st(phi[..., None].astype(np.float64))
     s1 = conv("e1b", conv("e1a", x))
-    s2 = conv("e2b", conv("e2a", avgpool2(s1)))
-    s3 = conv("e3b", conv("e3a", avgpool2(s2)))
-    bn = conv("bnb", conv("bna", avgpool2(s3)))
+    s2 = conv("e2b", conv("e2a", st(avgpool2(s1))))
+    s3 = conv("e3b", conv("e3a", st(avgpool2(s2))))
+    bn = conv("bnb", conv("bna", st(avgpool2(s3))))
     d3 = conv("d3b", conv("d3a", np.concatenate([s3, upsample2(bn)], axis=-1)))
     d2 = conv("d2b", conv("d2a", np.concatenate([s2, upsample2(d3)], axis=-1)))
     d1 = conv("d1b", conv("d1a", np.concatenate([s1, upsample2(d2)], axis=-1)))

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libhom.so")
 SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu", "hom_noalloc.cu",
-           "hom_batch.cu"]
+           "hom_batch.cu", "net_kernels.cu", "net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -35,8 +35,11 @@ def _stale() -> bool:
     for f in os.listdir(CSRC):
         if os.path.getmtime(os.path.join(CSRC, f)) > t:
             return True
-    hdr = os.path.join(os.path.dirname(HERE), "include", "hom.h")
-    return os.path.exists(hdr) and os.path.getmtime(hdr) > t
+    for name in ("hom.h", "hom_net.h"):
+        hdr = os.path.join(os.path.dirname(HERE), "include", name)
+        if os.path.exists(hdr) and os.path.getmtime(hdr) > t:
+            return True
+    return False
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -56,6 +56,7 @@ def _load():
             lib.octet_phi.restype = ctypes.c_double
             lib.octet_center_distance.argtypes = [fp, ip, ctypes.c_int]
             lib.octet_phi_at_radius.argtypes = [fp, ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, fp]
+            lib.octet_subpoint_distances.argtypes = [fp, ip, ctypes.c_int, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -99,6 +100,42 @@ def octet_at_radius(n, r: float, sub: int = 4, cells: int = 1, dist_perturb=None
     lib.octet_phi_at_radius(phi.ctypes.data_as(fp), (ctypes.c_int * 3)(*g), int(cells), float(r), int(sub),
                             None if pert is None else pert.ctypes.data_as(fp))
     return phi
+
+
+class OctetFamily:
+    """Octet cells of one grid at many densities: the sub-sample distances are
+    computed once; a density is then a radius (the matching quantile of all
+    sub-sample distances, midway between neighbours; where equal distances
+    make the exact count unreachable, the nearer end of the run of ties, as
+    octet() does) and a threshold."""
+
+    def __init__(self, n, sub: int = 4, cells: int = 1):
+        lib = _load()
+        self.grid = _grid(n)
+        self.S = sub ** 3
+        V = int(np.prod(self.grid))
+        d = np.zeros(V * self.S, dtype=np.float32)
+        lib.octet_subpoint_distances(d.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                     (ctypes.c_int * 3)(*self.grid), int(cells), int(sub))
+        self.d = d.reshape(V, self.S)
+        self.sorted = np.sort(d)
+
+    def radius(self, rho: float) -> float:
+        sd = self.sorted
+        k = int(round(rho * sd.size))
+        k = min(max(k, 1), sd.size - 1)
+        a = int(np.searchsorted(sd, sd[k - 1], side="left"))     # first of the ties
+        b = int(np.searchsorted(sd, sd[k - 1], side="right"))    # past the ties
+        cnt = a if k - a <= b - k else b
+        if cnt < 1:
+            cnt = b
+        if cnt >= sd.size:
+            cnt = a
+        return 0.5 * (float(sd[cnt - 1]) + float(sd[cnt]))
+
+    def phi(self, rho: float):
+        r = np.float32(self.radius(rho))
+        return ((self.d < r).sum(axis=1, dtype=np.int32).astype(np.float32) / self.S).reshape(self.grid)
 
 
 def octet_center_distance(n, cells: int = 1):

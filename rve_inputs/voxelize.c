@@ -238,6 +238,23 @@ void octet_phi_at_radius(float *phi, const int n[3], int cells, double r, int su
     }
 }
 
+/* Axis distances of every voxel's sub^3 sub-sample points: out[v * sub^3 + s]
+ * (V sub^3 floats); a density family is then a threshold per radius. */
+void octet_subpoint_distances(float *out, const int n[3], int cells, int sub) {
+    long V = (long)n[0] * n[1] * n[2];
+    int S = sub * sub * sub;
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < V; ++v) {
+        int i = (int)(v / ((long)n[1] * n[2])), j = (int)((v / n[2]) % n[1]), k = (int)(v % n[2]);
+        int s = 0;
+        for (int a = 0; a < sub; ++a)
+            for (int bb = 0; bb < sub; ++bb)
+                for (int cc = 0; cc < sub; ++cc)
+                    out[v * S + s++] = (float)dist_at(n, cells, i + (a + 0.5) / sub, j + (bb + 0.5) / sub,
+                                                      k + (cc + 0.5) / sub);
+    }
+}
+
 /* Axis distance field at voxel centres (for tests of the geometry). */
 void octet_center_distance(float *out, const int n[3], int cells) {
     long V = (long)n[0] * n[1] * n[2];

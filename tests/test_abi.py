@@ -8,8 +8,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "hom.h")).read()
+def declared_symbols(header="hom.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(hom_[a-z0-9_]+)\s*\(", src)))
 
@@ -32,6 +32,14 @@ def test_library_exports_every_declared_symbol(lib):
     for s in declared_symbols():
         assert hasattr(lib, s), s
     assert sorted(hom.EXPORTED) == declared_symbols()
+
+
+def test_library_exports_every_network_symbol(lib):
+    from paper_2110_00733_gb300 import net
+    for s in declared_symbols("hom_net.h"):
+        assert hasattr(lib, s), s
+    assert sorted(net.EXPORTED) == declared_symbols("hom_net.h")
+    assert sum(27 * ci * co + co for _, ci, co in net.LAYERS) > 500000
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -1,0 +1,180 @@
+"""GPU parity of the warm-start network's kernels against the FP64 network
+oracle: convolutions (forward, input gradient through the flipped weights,
+weight gradient), the whole network's prediction and parameter gradients,
+and one Adam step.
+
+Tolerances.  Both sides use the same BF16 inputs and weights, so a single
+convolution differs only by FP32 versus FP64 accumulation (relative 1e-6 of
+the largest term) plus the BF16 rounding of a stored output (one BF16 unit,
+2^-8 relative).  Through the whole network the stored tensors are rounded at
+the same points on both sides (the oracle's store emulation), but an
+FP32/FP64 difference can still flip a rounding and the flips propagate: the
+oracle itself with FP32 instead of FP64 accumulation moves the parameter
+gradients of this 16^3 problem by 0.6-1.2 % (norm-wise; the 2^3 bottleneck
+sums only 16 voxels).  Network-level checks therefore ask for 5 % norm-wise
+and a cosine of at least 0.998 per parameter tensor; a wrong wiring (a
+channel slice, an offset, a missing term) gives errors of order one."""
+import numpy as np
+import pytest
+
+from oracle import net_oracle as no
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2110_00733_gb300 import build, net
+    build.build()
+    net.load_library()
+    return torch, net
+
+
+def bf16_tensor(torch, a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda").to(torch.bfloat16).contiguous()
+
+
+def to_np(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def rnd(rng, shape, scale=1.0):
+    return no.bf16(rng.standard_normal(shape) * scale)
+
+
+CASES = [  # (batch, grid, c0, c1, cout)
+    (1, (8, 8, 8), 16, 0, 16),
+    (2, (4, 6, 10), 32, 0, 48),
+    (1, (8, 4, 6), 48, 64, 48),     # concatenation with an upsampled coarse source
+    (2, (6, 6, 6), 16, 32, 112),    # 7 n8 tiles per chunk, two chunks; ragged last CTA
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_conv_forward_and_wgrad(env, case):
+    torch, net = env
+    B, g, c0, c1, cout = case
+    rng = np.random.default_rng(sum(g) + c0 + cout)
+    x0 = rnd(rng, (B,) + g + (c0,))
+    half = tuple(v // 2 for v in g)
+    x1 = rnd(rng, (B,) + half + (c1,)) if c1 else None
+    W = rnd(rng, (27, cout, c0 + c1), 0.1)
+    b = rng.standard_normal(cout).astype(np.float32)
+    xin = x0 if x1 is None else np.concatenate([x0, no.upsample2(x1)], axis=-1)
+    ref = no.conv3d(xin, W, b.astype(np.float64))
+    s0 = bf16_tensor(torch, x0)
+    s1 = bf16_tensor(torch, x1) if x1 is not None else None
+    Wt = bf16_tensor(torch, W)
+    bt = torch.tensor(b, device="cuda")
+    # FP32 output, with bias
+    out = torch.zeros((B,) + g + (cout,), dtype=torch.float32, device="cuda")
+    net.conv3d(g, s0, Wt, cout, src1=s1, bias=bt, out=out)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # BF16 output with ReLU: within one BF16 unit of the rounded reference
+    outb = torch.zeros((B,) + g + (cout,), dtype=torch.bfloat16, device="cuda")
+    net.conv3d(g, s0, Wt, cout, src1=s1, bias=bt, relu=True, out=outb)
+    r = np.maximum(ref, 0.0)
+    assert np.all(np.abs(to_np(outb) - r) <= 2.0 ** -8 * np.abs(r) + 1e-5 * np.max(r))
+    # weight gradient against the oracle's
+    G = rnd(rng, (B,) + g + (cout,))
+    dW = torch.zeros((27, cout, c0 + c1), dtype=torch.float32, device="cuda")
+    if cout <= 64:
+        net.conv3d_wgrad(g, bf16_tensor(torch, G), s0, dW, src1=s1)
+        refW, _ = no.conv3d_wgrad(G, xin)
+        assert np.max(np.abs(dW.cpu().numpy() - refW)) <= 1e-5 * np.max(np.abs(refW))
+
+
+def test_input_gradient_is_the_flipped_convolution(env):
+    """dX = conv(G, W') with W'[t][ci][co] = W[26-t][co][ci] equals the
+    oracle's input gradient."""
+    torch, net = env
+    rng = np.random.default_rng(11)
+    B, g, cin, cout = 2, (6, 8, 4), 48, 32
+    W = rnd(rng, (27, cout, cin), 0.1)
+    G = rnd(rng, (B,) + g + (cout,))
+    Wp = np.ascontiguousarray(W[::-1].transpose(0, 2, 1))
+    out = torch.zeros((B,) + g + (cin,), dtype=torch.float32, device="cuda")
+    net.conv3d(g, bf16_tensor(torch, G), bf16_tensor(torch, Wp), cin, out=out)
+    ref = no.conv3d_dgrad(G, W)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def _net_problem(seed, n=16, B=2):
+    rng = np.random.default_rng(seed)
+    specs = no.layer_specs()
+    P = no.init_params(specs, rng)
+    for k in P:
+        P[k] = no.bf16(P[k] + (0.02 * rng.standard_normal(P[k].shape) if k.endswith(".b") else 0.0))
+    phi = rng.random((B, n, n, n))
+    phi[phi < 0.4] = 0.0
+    E = np.array([no.bf16(rng.standard_normal(6)) for _ in range(B)])        # Mandel
+    target = rng.standard_normal((B, n, n, n, 6))
+    return specs, P, phi, E, target
+
+
+def _tensor_comps(mandel_last):
+    """[..., 6] Mandel -> [..., 6] tensor components."""
+    t = mandel_last.copy()
+    t[..., 3:] /= np.sqrt(2.0)
+    return t
+
+
+def test_network_prediction_and_gradients(env):
+    torch, net = env
+    specs, P, phi, E, target = _net_problem(21)
+    B, n = phi.shape[0], phi.shape[1]
+    g = (n, n, n)
+    x0_ref, cache = no.forward(P, no.bf16(phi), E, specs, store=no.bf16)
+    loss_ref, gx = no.loss_and_grad_out(x0_ref, target)
+    G_ref = no.backward(P, cache, gx, specs, store=no.bf16)
+    Et = _tensor_comps(E)                                  # the ABI takes tensor components
+    with net.Net(seed=0) as m:
+        m.set_params(net.flatten(P))
+        phit = torch.tensor(phi.reshape(B, -1), dtype=torch.float32, device="cuda")
+        x0 = torch.zeros((B, 6, n ** 3), dtype=torch.float32, device="cuda")
+        m.forward(g, phit, Et, x0)
+        got = np.moveaxis(x0.cpu().numpy().reshape(B, 6, n, n, n), 1, -1).astype(np.float64)
+        ref = _tensor_comps(x0_ref)
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+        tgt = torch.tensor(np.ascontiguousarray(np.moveaxis(_tensor_comps(target), -1, 1).reshape(B, 6, -1)),
+                           dtype=torch.float32, device="cuda").contiguous()
+        grads, loss = m.gradients(g, phit, Et, tgt)
+        assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+        Gg = net.unflatten(grads)
+        for k in G_ref:
+            a, b = Gg[k].ravel(), G_ref[k].ravel()
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+            assert err <= 5e-2 and cos >= 0.998, (k, err, cos)
+        # one Adam step from zero moments moves every parameter by lr g / (|g| + eps)
+        before = m.get_params().astype(np.float64)
+        lr = 1e-3
+        m.train_step(g, phit, Et, tgt, lr)
+        after = m.get_params().astype(np.float64)
+        expect = before - lr * grads / (np.abs(grads) + 1e-8)
+        assert np.max(np.abs(after - expect)) <= 1e-6 + 1e-3 * lr
+
+
+def test_training_lowers_the_loss_and_state_round_trips(env, tmp_path):
+    torch, net = env
+    rng = np.random.default_rng(5)
+    B, n = 2, 16
+    g = (n, n, n)
+    phi = torch.tensor(rng.random((B, n ** 3)), dtype=torch.float32, device="cuda")
+    E = rng.standard_normal((B, 6))
+    tgt = torch.tensor(rng.standard_normal((B, 6, n ** 3)) * 0.1, dtype=torch.float32, device="cuda")
+    with net.Net(seed=3) as m:
+        losses = [m.train_step(g, phi, E, tgt, 3e-3) for _ in range(30)]
+        assert losses[-1] < 0.8 * losses[0], losses
+        m.save(tmp_path / "net.bin")
+        x_a = torch.zeros((B, 6, n ** 3), device="cuda")
+        m.forward(g, phi, E, x_a)
+        with net.Net(seed=99) as m2:
+            m2.load(tmp_path / "net.bin")
+            x_b = torch.zeros_like(x_a)
+            m2.forward(g, phi, E, x_b)
+            assert torch.equal(x_a, x_b)
+            assert m2.train_step(g, phi, E, tgt, 3e-3) == pytest.approx(m.train_step(g, phi, E, tgt, 3e-3), rel=1e-6)

@@ -41,3 +41,11 @@ def test_band_voxelizer_matches_full_sampling():
     assert abs(phi.mean() - 0.12) < 1.0 / (64 * n ** 3) + 1e-7
     plain, r0 = ri.octet(n, 0.12, cells=2)
     assert np.array_equal(plain, ri.octet_at_radius(n, r0, cells=2))
+
+
+def test_octet_family_matches_the_voxelizer():
+    fam = ri.OctetFamily(24)
+    for rho in (0.05, 0.15, 0.3):
+        phi, r = ri.octet(24, rho)
+        assert fam.radius(rho) == r
+        assert np.array_equal(fam.phi(rho), phi)
