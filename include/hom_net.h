@@ -70,6 +70,12 @@ int hom_net_forward(hom_net *net, int batch, const int grid[3], const float *phi
 int hom_net_train_step(hom_net *net, int batch, const int grid[3], const float *phi, const double *macro,
                        const float *target, float lr, double *loss);
 
+/* Weight of the squared error per voxel: vw + (1 - vw) phi, i.e. 1 in the
+ * solid and vw in empty space (default vw = 1: plain mean squared error).
+ * Strains in empty voxels are not unique (only the zero-start MINRES iterate
+ * defines them), so vw < 1 lets the network spend its capacity on the solid. */
+int hom_net_set_void_weight(hom_net *net, double void_weight);
+
 /* Loss and parameter gradients (host array in parameter order) without a
  * step: for checks against an independent implementation. */
 int hom_net_gradients(hom_net *net, int batch, const int grid[3], const float *phi, const double *macro,

@@ -157,10 +157,13 @@ def forward(P, phi, Ebar, specs=None, store=None):
     return x0, cache
 
 
-def loss_and_grad_out(x0, target):
-    """Mean squared error over all components and voxels, and d loss / d x0."""
+def loss_and_grad_out(x0, target, weight=None):
+    """Mean squared error over all components and voxels (each voxel's terms
+    times weight[b, z, y, x] if given), and d loss / d x0."""
     d = x0 - target
-    return float(np.mean(d * d)), 2.0 * d / d.size
+    w = np.ones(x0.shape[:4]) if weight is None else weight
+    wd = w[..., None] * d
+    return float(np.sum(wd * d) / d.size), 2.0 * wd / d.size
 
 
 def backward(P, cache, gx0, specs=None, store=None):

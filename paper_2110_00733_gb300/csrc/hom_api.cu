@@ -27,6 +27,8 @@ constexpr double kFp32SweepFloor = 1e-6;
 // from the FP64 residual sooner than MINRES: shorter sweeps, restarted from
 // the FP64 true residual, keep it converging
 constexpr double kFp32CgSweepFloor = 1e-3;
+// a warm start whose FP32-estimated residual is below this gets the FP64 one
+constexpr double kWarmFp64Below = 1e-3;
 // relative size of ||b|| / ||C : E_bar|| below which the right-hand side is
 // FFT round-off and is taken as zero (the paper is silent on this case)
 constexpr double kRhsZero = 1e-12;
@@ -81,6 +83,7 @@ struct hom_ctx {
     void *xs = nullptr;     // MINRES iterate of the current sweep
     void *rhs = nullptr;    // MINRES right-hand side of the current sweep
     double2 *b64 = nullptr, *r64 = nullptr;   // FP64 right-hand side and residual spectra
+    double2 *phihat = nullptr;                // FP64 DFT of phi (half spectrum, one component)
     std::vector<double2 *> x64;     // per-case solutions (spectral, FP64 master copy)
     std::vector<double> macros;     // per-case macro strains (Mandel, as solved)
     std::vector<double> sig_mean;   // per-case mean stress (tensor comps, units of E)
@@ -648,6 +651,7 @@ void hom_destroy(hom_ctx *ctx) {
     cudaFree(ctx->rhs);
     cudaFree(ctx->b64);
     cudaFree(ctx->r64);
+    cudaFree(ctx->phihat);
     for (double2 *p : ctx->x64) cudaFree(p);
     cudaFree(ctx->partials);
     cudaFree(ctx->d_state);
@@ -704,6 +708,7 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     CU(cudaMalloc(&ctx->xs, rs * nr));
     CU(cudaMalloc(&ctx->rhs, rs * nr));
     CU(cudaMalloc(&ctx->b64, sizeof(double) * nr));
+    CU(cudaMalloc(&ctx->phihat, sizeof(double2) * ctx->S));
     CU(cudaMalloc(&ctx->r64, sizeof(double) * nr));
     ctx->workspace += 7 * (long long)rs * nr + 2 * (long long)sizeof(double) * nr;
     long long np = 8LL * kEwBlocks;
@@ -747,6 +752,16 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
         ctx->phibar = s1 / (double)ctx->V;
     }
     ctx->launches += 1;
+    // phi^ = F{phi} (FP64): the field [phi, 0, 0, 0, 0, 0] through the forward
+    // passes, component 0 kept
+    {
+        double *f6 = (double *)ctx->r64;
+        CU(cudaMemsetAsync(f6, 0, sizeof(double) * 6 * ctx->V, ctx->stream));
+        CU(cudaMemcpyAsync(f6, ctx->e64.phi, sizeof(double) * ctx->V, cudaMemcpyDeviceToDevice, ctx->stream));
+        real_to_spec<double>(ctx, ctx->e64, f6, X3_MID_NONE, false, ctx->b64);
+        CU(cudaMemcpy2DAsync(ctx->phihat, sizeof(double2), ctx->b64, 6 * sizeof(double2), sizeof(double2), ctx->S,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     return finish(ctx);
 }
 
@@ -987,9 +1002,9 @@ static int solve_case_modb(hom_ctx *ctx, int icase, const double *m, double tol,
         *res = std::sqrt(*ctx->h_scalar) / bnorm;
         return HOM_OK;
     };
-    double tres = 1.0;
-    int rc = residual(&tres);
-    if (rc) return rc;
+    double tres = 1.0;   // x = 0: r = b
+    CU(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * nc3, cudaMemcpyDeviceToDevice, s));
+    int rc = HOM_OK;
     // FP32 fields: sweeps share the iteration budget; a sweep that raised the
     // FP64 true residual is taken back and ends the solve
     const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
@@ -1039,19 +1054,38 @@ static int solve_case_modb(hom_ctx *ctx, int icase, const double *m, double tol,
 // mean stress <phi C_m : (E_bar + e~)> in FP64, timing, info record
 static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom_solve_info *inf, int status,
                        hom_solve_info *info) {
-    (void)x;
     cudaStream_t s = ctx->stream;
-    const double *eps = fluctuation64(ctx, icase);
-    mean_stress64(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
-    const int nb = ew_blocks(ctx->V);
-    for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
-    ctx->launches += 7;
-    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(cudaEventRecord(ctx->ev1, s));
-    CU(cudaStreamSynchronize(s));
     const double r2 = std::sqrt(2.0);
+    double sig[6];
+    if (ctx->solver == HOM_SOLVER_GALERKIN_MINRES) {
+        // <sigma> = phibar C_m : E_bar + C_m : <phi eps~>, with <phi eps~> by
+        // Parseval from phi^ and the projected spectrum: one point-wise pass
+        const int nb = Launch<double>::phi_dot(ctx->e64.g, s, x, ctx->phihat, ctx->partials);
+        for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
+        ctx->launches += 7;
+        CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecord(ctx->ev1, s));
+        CU(cudaStreamSynchronize(s));
+        const double VV = (double)ctx->V * (double)ctx->V;
+        double mf[6];
+        for (int c = 0; c < 6; ++c) mf[c] = ctx->h_scalar[c] / VV;
+        const double trE = m[0] + m[1] + m[2], trF = mf[0] + mf[1] + mf[2];
+        for (int c = 0; c < 6; ++c)
+            sig[c] = ctx->phibar * ((c < 3 ? ctx->lam * trE : 0.0) + 2.0 * ctx->mu * m[c]) +
+                     (c < 3 ? ctx->lam * trF : 0.0) + 2.0 * ctx->mu * mf[c];
+    } else {
+        const double *eps = fluctuation64(ctx, icase);
+        mean_stress64(ctx->V, s, eps, ctx->e64.phi, ctx->lam, ctx->mu, m, ctx->partials);
+        const int nb = ew_blocks(ctx->V);
+        for (int c = 0; c < 6; ++c) reduce_to(s, ctx->partials + c * nb, nb, ctx->d_scalar + c);
+        ctx->launches += 7;
+        CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecord(ctx->ev1, s));
+        CU(cudaStreamSynchronize(s));
+        for (int c = 0; c < 6; ++c) sig[c] = ctx->h_scalar[c] / (double)ctx->V;
+    }
     for (int c = 0; c < 6; ++c) {
-        double v = ctx->h_scalar[c] / (double)ctx->V * ctx->E;
+        double v = sig[c] * ctx->E;
         if (c >= 3) v /= r2;
         inf->sigma_mean[c] = v;
         ctx->sig_mean[6 * icase + c] = v;
@@ -1102,24 +1136,46 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         // b vanishes up to round-off: zero fluctuation, 0 iterations
         inf.sweeps = 0;
     } else {
-        if (warm) {
-            // x0 = G F (warm), tensor components -> Mandel, projected
+        double tres = 1.0;
+        const long long n = 6 * ctx->V;
+        if (warm && ctx->prec == HOM_PREC_FP64) {
+            // x0 = G F (warm), tensor components -> Mandel, projected; FP64 residual
             double *st = (double *)ctx->r64;
-            const long long n = 6 * ctx->V;
-            if (ctx->prec == HOM_PREC_FP64) {
-                rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * icase, sizeof(double) * n, st);
-            } else {
-                rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * icase, sizeof(float) * n, ctx->xs);
-                if (!rc) real_convert_f2d(n, s, (const float *)ctx->xs, st);
-            }
+            rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * icase, sizeof(double) * n, st);
             if (rc) return rc;
             mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
             real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
             ctx->launches += 2;
+            rc = true_residual(ctx, x, bnorm, &tres);
+            if (rc) return rc;
+        } else if (warm) {
+            // FP32 fields: the projection and the residual that starts the
+            // first FP32 sweep are FP32 operator applications (an FP64 pass is
+            // many times slower on this part); the FP64 true residual after
+            // the sweep still decides convergence.  An FP32 residual carries
+            // round-off of about 1e-7 of b, so a start already that close is
+            // measured with the FP64 operator instead.
+            float *wr = (float *)ctx->xs;
+            cpx<float> *x32 = (cpx<float> *)ctx->vbuf[0], *p32 = (cpx<float> *)ctx->vbuf[1];
+            rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * icase, sizeof(float) * n, wr);
+            if (rc) return rc;
+            Launch<float>::axpby(3 * ctx->V, s, std::sqrt(2.0), wr + 3 * ctx->V, 0.0, wr + 3 * ctx->V);
+            real_to_spec<float>(ctx, ctx->e32, wr, X3_MID_NONE, true, x32);
+            spec_f2d_acc(nc, s, x32, x);
+            op_spec<float>(ctx, ctx->e32, x32, p32, false, nullptr, nullptr);
+            spec_residual_mixed(ctx->e64.g, s, ctx->b64, p32, ctx->r64, ctx->partials);
+            reduce_to(s, ctx->partials, ew_blocks(6 * ctx->S), ctx->d_scalar);
+            ctx->launches += 5;
+            CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            tres = std::sqrt(*ctx->h_scalar) / bnorm;
+            if (tres < kWarmFp64Below) {
+                rc = true_residual(ctx, x, bnorm, &tres);
+                if (rc) return rc;
+            }
+        } else {   // x = 0: r = b
+            CU(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
         }
-        double tres = 1.0;
-        rc = true_residual(ctx, x, bnorm, &tres);
-        if (rc) return rc;
         const int sweeps_max = (ctx->prec == HOM_PREC_FP64) ? 1 : 1 + ctx->refine;
         for (int sw = 0; sw < sweeps_max && tres > tol; ++sw) {
             // relative reduction this sweep must reach; FP32 fields cannot

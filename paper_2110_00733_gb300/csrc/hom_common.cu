@@ -175,6 +175,22 @@ __global__ void k_scalar_cg_beta(CgState *st, const double *partials, int np) {
     else if (st->k >= st->max_it) { st->status = 1; st->done = 1; }
 }
 
+// r = b - ax with ax from an FP32 operator (the residual that starts an FP32
+// sweep from a warm start)
+__global__ void __launch_bounds__(kEwThreads) k_spec_residual_mixed(int n, int h, int n3, int nc, const double2 *b,
+                                                                    const float2 *ax, double2 *r, double *partials) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 bb = b[i];
+        const float2 aa = ax[i];
+        const double2 d = make_double2(bb.x - (double)aa.x, bb.y - (double)aa.y);
+        r[i] = d;
+        acc += pweight((i / nc) % h, n3) * (d.x * d.x + d.y * d.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(kEwThreads) k_spec_residual64(int n, int h, int n3, int nc, const double2 *b,
                                                                 const double2 *ax, double2 *r, double *partials) {
     double acc = 0.0;
@@ -365,6 +381,11 @@ void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const
                      double *partials, int nc) {
     const int n = (int)(nc * g.S);
     k_spec_residual64<<<ew_blocks(n), kEwThreads, 0, st>>>(n, g.h, g.n3, nc, b, ax, r, partials);
+}
+void spec_residual_mixed(const Geometry &g, cudaStream_t st, const double2 *b, const float2 *ax, double2 *r,
+                         double *partials) {
+    const int n = (int)(6 * g.S);
+    k_spec_residual_mixed<<<ew_blocks(n), kEwThreads, 0, st>>>(n, g.h, g.n3, 6, b, ax, r, partials);
 }
 void spec_d2f(long long n, cudaStream_t st, const double2 *in, float2 *out) {
     k_spec_d2f<<<ew_blocks(n), kEwThreads, 0, st>>>(n, in, out);

@@ -131,6 +131,9 @@ template <typename R> struct Launch {
     // for odd K, in ua for even K; w_{K-1} in wd for even K, wc for odd K
     static void minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
                              cpx<R> *wd, cpx<R> *x, MinresState *state);
+    // Parseval partials of <phi, (G x^)_c>, c = 0..5 (see k_phi_dot); returns
+    // the number of blocks (partials[c * nb + block])
+    static int phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials);
     // y = a x + b y over n reals
     static void axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y);
     // weighted partial ||x||^2 of a spectral vector with nc components per frequency
@@ -155,6 +158,8 @@ template <typename R> struct Launch {
 // FP64 helpers on spectral vectors (double2) and real fields
 void spec_residual64(const Geometry &g, cudaStream_t st, const double2 *b, const double2 *ax, double2 *r,
                      double *partials, int nc = 6);             // r = b - ax, weighted ||r||^2
+void spec_residual_mixed(const Geometry &g, cudaStream_t st, const double2 *b, const float2 *ax, double2 *r,
+                         double *partials);                     // r = b - ax (ax FP32), weighted ||r||^2
 void spec_d2f(long long ncplx, cudaStream_t st, const double2 *in, float2 *out);
 void spec_f2d_acc(long long ncplx, cudaStream_t st, const float2 *in, double2 *out,
                   double a = 1.0);   // out += a in

@@ -615,6 +615,33 @@ __global__ void __launch_bounds__(kEwThreads) k_minres_flush(int n, const cpx<R>
     }
 }
 
+// Parseval sums for the mean of phi times the projected fluctuation:
+// partials[c][block] = sum over half-spectrum points of w Re(conj(phi^) (G x^)_c),
+// w the half-spectrum weight; (1/V^2) times the total is <phi eps~_c>.
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_phi_dot(Geometry g, const cpx<R> *__restrict__ x,
+                                                        const cpx<R> *__restrict__ phihat, double *__restrict__ partials) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < g.S; f += (long long)gridDim.x * blockDim.x) {
+        const int k3 = (int)(f % g.h);
+        const long long r = f / g.h;
+        const int k2 = (int)(r % g.n2), k1 = (int)(r / g.n2);
+        cpx<R> t[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[c] = x[6 * f + c];
+        gamma_at<R>(g, k1, k2, k3, t);
+        const cpx<R> ph = phihat[f];
+        const double w = (double)pweight(k3, g.n3);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += w * ((double)ph.x * (double)t[c].x + (double)ph.y * (double)t[c].y);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const double sum = block_sum(acc[c]);
+        if (threadIdx.x == 0) partials[c * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
 template <typename R>
 __global__ void k_axpby(long long n, R a, const R *__restrict__ x, R b, R *__restrict__ y) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -821,6 +848,13 @@ void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *u
                              cpx<R> *wd, cpx<R> *x, MinresState *state) {
     const int n = (int)(6 * g.S);
     k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, ua, ub, wc, wd, x, state);
+}
+
+template <typename R>
+int Launch<R>::phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials) {
+    const int nb = ew_grid(g.S);
+    k_phi_dot<R><<<nb, kEwThreads, 0, st>>>(g, x, phihat, partials);
+    return nb;
 }
 
 template <typename R>

@@ -152,16 +152,18 @@ __device__ __forceinline__ double block_sum_d(double v) {
 }
 
 // Loss and head gradient: d_c = x0_c - target_c (Mandel), loss partials of
-// sum d^2, G[v][6c+J] = scale d_c E_J (channels 36..47 zero).
+// sum w d^2 with the voxel weight w = vw + (1 - vw) phi (1 everywhere for
+// vw = 1), G[v][6c+J] = scale w d_c E_J (channels 36..47 zero).
 __global__ void k_loss_grad(int B, long long V, const float *__restrict__ M, const float *__restrict__ E,
-                            const float *__restrict__ target, float scale, bf16 *__restrict__ G,
-                            double *__restrict__ partials) {
+                            const float *__restrict__ target, const float *__restrict__ phi, float vw, float scale,
+                            bf16 *__restrict__ G, double *__restrict__ partials) {
     double acc = 0.0;
     const long long total = V * B;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(i / V);
         const long long v = i - b * V;
         const float *m = M + i * 48;
+        const float w = vw + (1.f - vw) * phi[i];
         float e[6], g[6];
         for (int j = 0; j < 6; ++j) e[j] = E[b * 6 + j];
         for (int c = 0; c < 6; ++c) {
@@ -170,8 +172,8 @@ __global__ void k_loss_grad(int B, long long V, const float *__restrict__ M, con
             float tv = target[((long long)b * 6 + c) * V + v];
             if (c >= 3) tv *= kSqrt2;
             const float d = x - tv;
-            acc += (double)d * d;
-            g[c] = scale * d;
+            acc += (double)w * d * d;
+            g[c] = scale * w * d;
         }
         bf16 *o = G + i * 48;
         for (int c = 0; c < 6; ++c)
@@ -361,6 +363,7 @@ struct hom_net {
     size_t partial_floats = 0, colpart_floats = 0, mw_floats = 0;
     double *losspart = nullptr, *dloss = nullptr;
     int ecap = 0;
+    float void_weight = 1.f;
 };
 
 namespace {
@@ -617,11 +620,12 @@ int check_grid(const int g[3], int B) {
     return HOM_OK;
 }
 
-int loss_and_head_grad(hom_net *n, int B, const int g[3], const float *target, double *loss) {
+int loss_and_head_grad(hom_net *n, int B, const int g[3], const float *phi, const float *target, double *loss) {
     const long long V = (long long)g[0] * g[1] * g[2];
     const int nb = ew_blocks(V * B);
     const float scale = (float)(2.0 / (6.0 * (double)V * B));
-    k_loss_grad<<<nb, kEw, 0, n->stream>>>(B, V, n->M, n->dE, target, scale, n->G[HEAD], n->losspart);
+    k_loss_grad<<<nb, kEw, 0, n->stream>>>(B, V, n->M, n->dE, target, phi, n->void_weight, scale, n->G[HEAD],
+                                           n->losspart);
     k_sum_partials<<<1, 256, 0, n->stream>>>(n->losspart, nb, n->dloss);
     n->launches += 2;
     NCU(cudaGetLastError());
@@ -643,7 +647,7 @@ int train_common(hom_net *n, int B, const int g[3], const float *phi, const doub
     k_prep_input<<<ew_blocks(level_vox(n, B, g, 0)), kEw, 0, n->stream>>>(B, g[0], g[1], g[2], 1, phi, n->x);
     ++n->launches;
     if ((rc = forward(n, B, g))) return rc;
-    if ((rc = loss_and_head_grad(n, B, g, target, loss))) return rc;
+    if ((rc = loss_and_head_grad(n, B, g, phi, target, loss))) return rc;
     return backward(n, B, g);
 }
 
@@ -726,6 +730,12 @@ void hom_net_destroy(hom_net *n) {
 }
 
 long long hom_net_param_count(const hom_net *n) { return n ? n->nparam : 0; }
+
+int hom_net_set_void_weight(hom_net *n, double void_weight) {
+    if (!n || !(void_weight >= 0.0 && void_weight <= 1.0)) return set_err(HOM_EINVAL, "void weight must be in [0, 1]");
+    n->void_weight = (float)void_weight;
+    return HOM_OK;
+}
 long long hom_net_kernel_launches(const hom_net *n) { return n ? n->launches : 0; }
 
 int hom_net_get_params(const hom_net *n, float *host) {

@@ -14,7 +14,7 @@ EXPORTED = [
     "hom_net_create", "hom_net_destroy", "hom_net_last_error", "hom_net_param_count", "hom_net_get_params",
     "hom_net_set_params", "hom_net_save", "hom_net_load", "hom_net_forward", "hom_net_train_step",
     "hom_net_gradients", "hom_net_warm_start", "hom_net_kernel_launches", "hom_net_conv3d",
-    "hom_net_conv3d_wgrad",
+    "hom_net_conv3d_wgrad", "hom_net_set_void_weight",
 ]
 
 # layer names, input and output channels, in parameter order
@@ -37,6 +37,7 @@ def load_library():
     lib.hom_net_destroy.restype = None
     lib.hom_net_last_error.argtypes = []
     lib.hom_net_last_error.restype = ctypes.c_char_p
+    lib.hom_net_set_void_weight.argtypes = [vp, ctypes.c_double]
     lib.hom_net_param_count.argtypes = [vp]
     lib.hom_net_param_count.restype = ctypes.c_longlong
     lib.hom_net_get_params.argtypes = [vp, fp]
@@ -98,6 +99,9 @@ class Net:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_void_weight(self, vw):
+        _check(load_library().hom_net_set_void_weight(self.handle, float(vw)))
 
     def param_count(self):
         return int(load_library().hom_net_param_count(self.handle))

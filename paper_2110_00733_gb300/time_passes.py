@@ -1,7 +1,7 @@
 """Time the kernels of one MINRES iteration through hom_time_kernels.
 
     python -m paper_2110_00733_gb300.time_passes [--shape 256,256,256] [--reps 20]
-                                                 [--staging 0|1] [--shape3 r,t2,t1]
+                                                 [--staging 0|1] [--shape3 r,t2,t1] [--fp64]
 
 Prints a JSON object {kernel: milliseconds} and each kernel's HBM rate from
 its algorithmic bytes.  Used for launch-shape sweeps and, with --reps 1, as
@@ -35,16 +35,18 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--staging", type=int, default=0)
     ap.add_argument("--shape3", default="0,0,0")
+    ap.add_argument("--fp64", action="store_true", help="FP64 fields (bytes below are for FP32)")
     a = ap.parse_args()
     shape = tuple(int(v) for v in a.shape.split(","))
     rng = np.random.default_rng(0)
     phi = (rng.random(shape) > 0.5).astype(np.float32)
     ctx = hom.hom_create(shape, phi, hom.HOM_INPUT_FRACTION_F32, 110e9, 0.3, staging=a.staging,
-                         shape=tuple(int(v) for v in a.shape3.split(",")))
+                         shape=tuple(int(v) for v in a.shape3.split(",")),
+                         precision=hom.HOM_PREC_FP64 if a.fp64 else hom.HOM_PREC_FP32_FIELDS)
     t = hom.hom_time_kernels(ctx, reps=a.reps)
     ctx.close()
     V = int(np.prod(shape))
-    bpv = bytes_per_voxel(shape[2])
+    bpv = {k: v * (2 if a.fp64 else 1) for k, v in bytes_per_voxel(shape[2]).items()}
     out = {"shape": shape, "ms": t,
            "gbs": {k: bpv[k] * V / (t[k] * 1e-3) / 1e9 for k in bpv if t.get(k, 0) > 0}}
     print(json.dumps(out))

@@ -4,7 +4,7 @@ solves.
 
     python -m paper_2110_00733_gb300.warmstart [--train 2000] [--n 64]
         [--epochs 12] [--batch 8] [--eval 128,256] [--eval-cells 3]
-        [--save net.bin] [--load net.bin]
+        [--void-weight 1.0] [--save net.bin] [--load net.bin]
 
 Training set (seed i): octet cell on an n^3 grid at density U[0.03, 0.30],
 macro strain uniform on the Mandel unit sphere, FP32-field Galerkin-MINRES
@@ -145,6 +145,8 @@ def main(argv=None):
     ap.add_argument("--eval", default="128,256")
     ap.add_argument("--eval-cells", type=int, default=3)
     ap.add_argument("--fp64-baseline", action="store_true")
+    ap.add_argument("--void-weight", type=float, default=1.0,
+                    help="loss weight of empty voxels (1: plain mean squared error)")
     ap.add_argument("--save", default=None)
     ap.add_argument("--load", default=None)
     a = ap.parse_args(argv)
@@ -154,7 +156,8 @@ def main(argv=None):
     torch.cuda.set_device(0)
     emit = lambda d: print(json.dumps(d), flush=True)   # noqa: E731
     model = hnet.Net(seed=1)
-    emit({"params": model.param_count()})
+    model.set_void_weight(a.void_weight)
+    emit({"params": model.param_count(), "void_weight": a.void_weight})
     if a.load:
         model.load(a.load)
     else:
