@@ -23,6 +23,10 @@ thread_local std::string g_create_error;
 
 // smallest relative residual reduction one FP32-field MINRES sweep is asked for
 constexpr double kFp32SweepFloor = 1e-6;
+// a sweep aims below the tolerance by this factor: the FP64 true residual
+// after an FP32 sweep differs a little from the recurrence's estimate, and
+// landing just above tol costs a restarted sweep
+constexpr double kSweepTarget = 0.5;
 // PCG on A^alpha (not symmetric where chi_v is non-zero) in FP32 drifts away
 // from the FP64 residual sooner than MINRES: shorter sweeps, restarted from
 // the FP64 true residual, keep it converging
@@ -1181,7 +1185,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
             // relative reduction this sweep must reach; FP32 fields cannot
             // resolve residuals much below 1e-6 of their right-hand side, so a
             // sweep never asks for less and the next sweep refines further
-            double sweep_tol = tol / tres;
+            double sweep_tol = (ctx->prec == HOM_PREC_FP32_FIELDS ? kSweepTarget : 1.0) * tol / tres;
             if (sweep_tol > 0.5) sweep_tol = 0.5;
             if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < ctx->sweep_floor) sweep_tol = ctx->sweep_floor;
             int it = 0, st = 0;

@@ -108,13 +108,25 @@ template <typename R, int S> __device__ __forceinline__ cpx<R> w16(int k) {
     return mk<R>(re, S * im);
 }
 
+// a * exp(S 2 pi i k / 16) with the trivial factors spelled out: k = 4 is a
+// multiplication by S i, k = 2 and 6 by sqrt(1/2) (+-1 + S i).  (IEEE rules
+// keep a compiler from dropping the products with 0 and 1 by itself.)
+template <typename R, int S> __device__ __forceinline__ cpx<R> mul_w16(cpx<R> a, int k) {
+    const R h = (R)0.70710678118654752440;
+    if (k == 0) return a;
+    if (k == 4) return mul_si<R>(a, S);
+    if (k == 2) return mk<R>(h * (a.x - (R)S * a.y), h * (a.y + (R)S * a.x));
+    if (k == 6) return mk<R>(-h * (a.x + (R)S * a.y), h * ((R)S * a.x - a.y));
+    return mul<R>(a, w16<R, S>(k));
+}
+
 template <typename R, int S> __device__ __forceinline__ void dft8(cpx<R> *v) {
     cpx<R> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
     dft4<R, S>(e);
     dft4<R, S>(o);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        cpx<R> t = (k == 0) ? o[0] : mul<R>(o[k], w16<R, S>(2 * k));
+        const cpx<R> t = mul_w16<R, S>(o[k], 2 * k);
         v[k] = add<R>(e[k], t);
         v[k + 4] = sub<R>(e[k], t);
     }
@@ -128,7 +140,7 @@ template <typename R, int S> __device__ __forceinline__ void dft16(cpx<R> *v) {
     dft8<R, S>(o);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        cpx<R> t = (k == 0) ? o[0] : mul<R>(o[k], w16<R, S>(k));
+        const cpx<R> t = mul_w16<R, S>(o[k], k);
         v[k] = add<R>(e[k], t);
         v[k + 8] = sub<R>(e[k], t);
     }

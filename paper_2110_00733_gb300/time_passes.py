@@ -5,7 +5,17 @@
 
 Prints a JSON object {kernel: milliseconds} and each kernel's HBM rate from
 its algorithmic bytes.  Used for launch-shape sweeps and, with --reps 1, as
-a small driver for ncu captures of the pass kernels.
+a small driver for ncu captures of the pass kernels:
+
+    ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+        --clock-control none -k "regex:k_x|k_lanczos" -c 12 --csv --log-file traffic.csv \
+        python -m paper_2110_00733_gb300.time_passes --shape 256,128,256 --reps 1
+    python -m paper_2110_00733_gb300.time_passes --traffic traffic.csv --shape 256,128,256
+
+The second command turns the capture (each kernel launched twice: warm-up
+and one timed launch; the first launch of each is used) into
+profiles/traffic.json, which bench.py reads while the CUDA sources are
+unchanged.
 """
 from __future__ import annotations
 
@@ -36,8 +46,11 @@ def main():
     ap.add_argument("--staging", type=int, default=0)
     ap.add_argument("--shape3", default="0,0,0")
     ap.add_argument("--fp64", action="store_true", help="FP64 fields (bytes below are for FP32)")
+    ap.add_argument("--traffic", default=None, help="ncu CSV to summarise into profiles/traffic.json")
     a = ap.parse_args()
     shape = tuple(int(v) for v in a.shape.split(","))
+    if a.traffic:
+        return write_traffic(a.traffic, shape)
     rng = np.random.default_rng(0)
     phi = (rng.random(shape) > 0.5).astype(np.float32)
     ctx = hom.hom_create(shape, phi, hom.HOM_INPUT_FRACTION_F32, 110e9, 0.3, staging=a.staging,
@@ -52,5 +65,57 @@ def main():
     print(json.dumps(out))
 
 
+# kernel launches of one MINRES iteration in hom_time_kernels order
+ORDER = ["x1_inv_gamma", "x2_inv", "x3_c2r_law_r2c", "x2_fwd", "x1_fwd_gamma_dot", "lanczos_update"]
+
+
+def write_traffic(csv_path, shape):
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[start]
+    ki, ii, mi, vi, ui = (hdr.index(k) for k in ("Kernel Name", "ID", "Metric Name", "Metric Value", "Metric Unit"))
+    launches = {}
+    for r in rows[start + 1:]:
+        if len(r) <= vi:
+            continue
+        d = launches.setdefault(int(r[ii]), {"name": r[ki]})
+        scale = {"byte": 1e-6, "Kbyte": 1e-3, "Mbyte": 1.0, "Gbyte": 1e3}.get(r[ui], 1.0)
+        if r[mi].startswith("dram__bytes"):
+            d[r[mi]] = float(r[vi].replace(",", "")) * scale
+    seq = [launches[k] for k in sorted(launches)]
+    # hom_time_kernels launches each kernel twice (warm-up, then --reps 1)
+    firsts = seq[0::2]
+    V = int(np.prod(shape))
+    out = {"source_hash": source_hash(), "grid": list(shape),
+           "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                      "--clock-control none -k \"regex:k_x|k_lanczos\" -c 12 --csv --log-file traffic.csv "
+                      f"python -m paper_2110_00733_gb300.time_passes --shape {','.join(map(str, shape))} --reps 1",
+           "note": "bytes per voxel on this grid (work spectrum larger than L2); traffic scales with the voxel "
+                   "count at fixed n3, so bench.py multiplies by n^3 for the 256^3 workload",
+           "kernels": {}}
+    for name, d in zip(ORDER, firsts):
+        rd, wr = d.get("dram__bytes_read.sum", 0.0), d.get("dram__bytes_write.sum", 0.0)
+        out["kernels"][name] = {"ncu_kernel": d["name"].split("(")[0], "dram_read_mb": round(rd, 1),
+                                "dram_write_mb": round(wr, 1), "dram_bytes_per_voxel": (rd + wr) * 1e6 / V}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out["kernels"], indent=1))
+    return 0
+
+
+def source_hash():
+    """Hash of the CUDA sources (the same rule as bench.py)."""
+    import hashlib
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_2110_00733_gb300", "csrc")
+    for fn in sorted(os.listdir(cdir)):
+        with open(os.path.join(cdir, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 if __name__ == "__main__":
-    main()
+    sys.exit(main())
