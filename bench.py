@@ -176,10 +176,13 @@ def kernel_traffic(name, n):
 
 
 def source_hash():
+    """Hash of the solver's kernel sources (the network's files do not change
+    the solver kernels' traffic)."""
     import hashlib
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_2110_00733_gb300", "csrc")
-    for fn in sorted(os.listdir(cdir)):
+    for fn in ("hom_fft.cuh", "hom_tma.cuh", "hom_passes.cuh", "hom_modb.cuh", "hom_internal.h",
+               "hom_kernels_f32.cu", "hom_kernels_f64.cu"):
         with open(os.path.join(cdir, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())

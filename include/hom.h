@@ -98,7 +98,9 @@ typedef struct {
     int reserved;
     double sweep_floor; /* FP32 fields: smallest relative residual reduction one
                            refinement sweep is asked for (0: 1e-6 for MINRES,
-                           1e-3 for PCG); the FP64 true residual is recomputed
+                           5e-7 for its first sweep from a zero start, 1e-3
+                           for PCG); a sweep aims at half the remaining
+                           tolerance, and the FP64 true residual is recomputed
                            after every sweep */
 } hom_options;
 

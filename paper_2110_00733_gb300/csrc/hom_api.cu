@@ -23,6 +23,9 @@ thread_local std::string g_create_error;
 
 // smallest relative residual reduction one FP32-field MINRES sweep is asked for
 constexpr double kFp32SweepFloor = 1e-6;
+// ... except the first sweep of a zero start (its right-hand side is b
+// itself), which may aim at 5e-7
+constexpr double kFp32FirstSweepFloor = 5e-7;
 // a sweep aims below the tolerance by this factor: the FP64 true residual
 // after an FP32 sweep differs a little from the recurrence's estimate, and
 // landing just above tol costs a restarted sweep
@@ -1187,7 +1190,9 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
             // sweep never asks for less and the next sweep refines further
             double sweep_tol = (ctx->prec == HOM_PREC_FP32_FIELDS ? kSweepTarget : 1.0) * tol / tres;
             if (sweep_tol > 0.5) sweep_tol = 0.5;
-            if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < ctx->sweep_floor) sweep_tol = ctx->sweep_floor;
+            const double floor = (sw == 0 && !warm && ctx->sweep_floor == kFp32SweepFloor)
+                                     ? kFp32FirstSweepFloor : ctx->sweep_floor;
+            if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < floor) sweep_tol = floor;
             int it = 0, st = 0;
             double est = 0.0;
             if (ctx->prec == HOM_PREC_FP64) {

@@ -491,8 +491,14 @@ ConvArgs layer_args(hom_net *n, int l, int B, const int g[3]) {
 }
 
 int run_conv(hom_net *n, const ConvArgs &a) {
-    if (conv3_forward(a, n->stream)) return set_err(HOM_EINVAL, "convolution shape not supported");
+    if (conv3_forward_tc(a, n->stream)) return set_err(HOM_EINVAL, "convolution shape not supported");
     ++n->launches;
+    return HOM_OK;
+}
+
+// after a synchronisation: a tensor-core convolution that gave up a bounded wait
+int tc_status() {
+    if (conv3_tc_error(1)) return set_err(HOM_ETIMEOUT, "a bounded wait in a tensor-core convolution gave up");
     return HOM_OK;
 }
 
@@ -815,7 +821,7 @@ int hom_net_forward(hom_net *n, int B, const int g[3], const float *phi, const d
     ++n->launches;
     NCU(cudaGetLastError());
     NCU(cudaStreamSynchronize(n->stream));
-    return HOM_OK;
+    return tc_status();
 }
 
 int hom_net_train_step(hom_net *n, int B, const int g[3], const float *phi, const double *macro, const float *target,
@@ -832,7 +838,7 @@ int hom_net_train_step(hom_net *n, int B, const int g[3], const float *phi, cons
     ++n->launches;
     if ((rc = pack_all(n))) return rc;
     NCU(cudaStreamSynchronize(n->stream));
-    return HOM_OK;
+    return tc_status();
 }
 
 int hom_net_gradients(hom_net *n, int B, const int g[3], const float *phi, const double *macro, const float *target,
@@ -842,7 +848,7 @@ int hom_net_gradients(hom_net *n, int B, const int g[3], const float *phi, const
     if (rc) return rc;
     NCU(cudaStreamSynchronize(n->stream));
     NCU(cudaMemcpy(grads, n->grads, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost));
-    return HOM_OK;
+    return tc_status();
 }
 
 int hom_net_warm_start(hom_net *n, const int grid[3], int s, const float *phi, int ncase, const double *macro,
@@ -866,7 +872,7 @@ int hom_net_warm_start(hom_net *n, const int grid[3], int s, const float *phi, i
     ++n->launches;
     NCU(cudaGetLastError());
     NCU(cudaStreamSynchronize(n->stream));
-    return HOM_OK;
+    return tc_status();
 }
 
 int hom_net_conv3d(int batch, const int grid[3], const unsigned short *src0, int c0s, const unsigned short *src1,
@@ -889,10 +895,11 @@ int hom_net_conv3d(int batch, const int grid[3], const unsigned short *src0, int
     if (out_f32) a.out_f32 = static_cast<float *>(out);
     else a.out_bf16 = static_cast<bf16 *>(out);
     if (grid[0] <= 0 || grid[1] <= 0 || grid[2] <= 0) return set_err(HOM_EUNSUPPORTED_GRID, "empty grid");
-    if (conv3_forward(a, (cudaStream_t)stream)) return set_err(HOM_EINVAL, "channel counts must be multiples of 16");
+    if (conv3_forward_tc(a, (cudaStream_t)stream))
+        return set_err(HOM_EINVAL, "channel counts must be multiples of 16 (cout <= 256)");
     NCU(cudaGetLastError());
     NCU(cudaStreamSynchronize((cudaStream_t)stream));
-    return HOM_OK;
+    return tc_status();
 }
 
 int hom_net_conv3d_wgrad(int batch, const int grid[3], const unsigned short *G, int cout, const unsigned short *src0,

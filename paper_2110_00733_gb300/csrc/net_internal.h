@@ -35,7 +35,9 @@ struct WgradArgs {
     int S;
 };
 
-int conv3_forward(const ConvArgs &a, cudaStream_t st);
+int conv3_forward_tc(const ConvArgs &a, cudaStream_t st);   // tcgen05, cout <= 256
+// nonzero if a tcgen05 convolution gave up a bounded wait (clears it if asked)
+int conv3_tc_error(int clear);
 int conv3_wgrad(const WgradArgs &a, cudaStream_t st);
 
 }  // namespace hnet

@@ -1,7 +1,7 @@
-// net_kernels.cu -- kernels of the warm-start network: periodic 3x3x3
-// convolutions as implicit GEMMs on the BF16 tensor cores (mma.sync
-// m16n8k16, FP32 accumulation), their weight gradients, and the point-wise
-// pieces (pooling, gradient assembly, loss, Adam).
+// net_kernels.cu -- weight gradients of the warm-start network's periodic
+// 3x3x3 convolutions on the BF16 tensor cores (mma.sync m16n8k16, FP32
+// accumulation; the forward and input-gradient convolutions run on tcgen05 in
+// net_tc.cu).
 //
 // Tensors are channels-last BF16, [batch][n1][n2][n3][C] with C a multiple
 // of 16 (padding channels hold zeros).  A convolution output voxel v and tap
@@ -19,8 +19,6 @@ namespace hnet {
 namespace {
 
 constexpr int kConvThreads = 128;     // 4 warps
-constexpr int kBM = 128;              // output voxels per CTA
-constexpr int kStages = 4;            // cp.async pipeline depth
 constexpr int kRowA = 24;             // smem row of a 16-channel chunk: 16 + 8 pad (48 B, odd 16-B count)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -37,14 +35,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -77,127 +67,6 @@ __device__ __forceinline__ const __nv_bfloat16 *conv_row(const ConvArgs &a, int 
     const int h1 = a.n1 >> 1, h2 = a.n2 >> 1, h3 = a.n3 >> 1;
     const long long v = (((long long)b * h1 + (zz >> 1)) * h2 + (yy >> 1)) * h3 + (xx >> 1);
     return a.src1 + v * a.c1s + (kc - k0) * 16;
-}
-
-// Implicit-GEMM convolution: M = voxels (kBM per CTA), N = 8 NT output
-// channels (blockIdx.y selects the chunk), K = 27 taps x input channels in
-// chunks of 16.  Each K chunk stages A (kBM rows x 16 channels, gathered per
-// tap with periodic wrap) and B (8 NT rows x 16 channels of W[t]) by cp.async
-// through a kStages-deep ring; each warp owns 32 rows (two m16 tiles) and all
-// NT n8 tiles.
-template <int NT>
-__global__ void __launch_bounds__(kConvThreads) k_conv3(ConvArgs a) {
-    __shared__ __align__(128) __nv_bfloat16 sA[kStages][kBM * kRowA];
-    __shared__ __align__(128) __nv_bfloat16 sB[kStages][8 * NT * kRowA];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long V = (long long)a.n1 * a.n2 * a.n3;
-    const long long total = V * a.B;
-    const long long m0 = (long long)blockIdx.x * kBM;
-    const int co0 = blockIdx.y * 8 * NT;
-    const int cin_s = a.c0s + a.c1s;
-    const int kcs = cin_s >> 4;
-    const int nk = 27 * kcs;
-
-    // the A row this thread stages (one row, two 16-byte halves)
-    const long long mrow = m0 + tid;
-    const bool row_ok = mrow < total;
-    int rb = 0, rz = 0, ry = 0, rx = 0;
-    if (row_ok) {
-        long long r = mrow;
-        rx = (int)(r % a.n3); r /= a.n3;
-        ry = (int)(r % a.n2); r /= a.n2;
-        rz = (int)(r % a.n1); rb = (int)(r / a.n1);
-    }
-
-    auto stage_load = [&](int ks, int buf) {
-        const int t = ks / kcs, kc = ks - t * kcs;
-        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        const __nv_bfloat16 *src = row_ok ? conv_row(a, rb, rz, ry, rx, dz, dy, dx, kc) : a.src0;
-        const uint32_t dst = smem_addr(&sA[buf][tid * kRowA]);
-        cp_async16(dst, src, row_ok ? 16 : 0);
-        cp_async16(dst + 16, src + 8, row_ok ? 16 : 0);
-        if (tid < 16 * NT) {
-            const int r = tid >> 1, h = tid & 1;
-            const __nv_bfloat16 *w = a.W + ((long long)t * a.cout + co0 + r) * cin_s + kc * 16 + h * 8;
-            cp_async16(smem_addr(&sB[buf][r * kRowA + h * 8]), w, 16);
-        }
-    };
-
-    float acc[2][NT][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-#pragma unroll
-    for (int s = 0; s < kStages - 1; ++s) {
-        if (s < nk) stage_load(s, s);
-        cp_async_commit();
-    }
-    for (int ks = 0; ks < nk; ++ks) {
-        cp_async_wait<kStages - 2>();
-        __syncthreads();
-        const int nxt = ks + kStages - 1;
-        if (nxt < nk) stage_load(nxt, nxt % kStages);
-        cp_async_commit();
-        const int buf = ks % kStages;
-        uint32_t af[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int row = warp * 32 + mt * 16 + (lane & 15);
-            ldsm_x4(smem_addr(&sA[buf][row * kRowA + (lane >> 4) * 8]), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
-        }
-#pragma unroll
-        for (int np = 0; np < NT / 2; ++np) {
-            const int n = np * 16 + (lane & 7) + ((lane >> 4) << 3);
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4(smem_addr(&sB[buf][n * kRowA + ((lane >> 3) & 1) * 8]), b0, b1, b2, b3);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                mma16816(acc[mt][2 * np], af[mt], b0, b1);
-                mma16816(acc[mt][2 * np + 1], af[mt], b2, b3);
-            }
-        }
-        if (NT & 1) {
-            const int n = (NT - 1) * 8 + (lane & 7);
-            uint32_t b0, b1;
-            ldsm_x2(smem_addr(&sB[buf][n * kRowA + ((lane >> 3) & 1) * 8]), b0, b1);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][NT - 1], af[mt], b0, b1);
-        }
-    }
-    cp_async_wait<0>();
-
-    // epilogue: bias, ReLU, store (rows g and g + 8 of each m16 tile)
-    const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const long long m = m0 + warp * 32 + mt * 16 + g + half * 8;
-            if (m >= total) continue;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int co = co0 + nt * 8 + 2 * tq;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (a.bias) {
-                    v0 += a.bias[co];
-                    v1 += a.bias[co + 1];
-                }
-                if (a.relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                if (a.out_f32) {
-                    *reinterpret_cast<float2 *>(a.out_f32 + m * a.cout + co) = make_float2(v0, v1);
-                } else {
-                    *reinterpret_cast<__nv_bfloat162 *>(a.out_bf16 + m * a.cout + co) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
-        }
-    }
 }
 
 // Weight gradient: partial[s][t][co][ci] = sum over the voxels of split s of
@@ -317,29 +186,6 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad3(WgradArgs a) {
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-int conv3_forward(const ConvArgs &a, cudaStream_t st) {
-    if ((a.cout & 15) || (a.c0s & 15) || (a.c1s & 15) || a.c0s <= 0) return -1;
-    if (a.c1s && (!a.src1 || (a.n1 | a.n2 | a.n3) & 1)) return -1;
-    const long long total = (long long)a.n1 * a.n2 * a.n3 * a.B;
-    const unsigned gx = (unsigned)((total + kBM - 1) / kBM);
-    // output-channel chunks of 8 NT, NT <= 8
-    const int n8 = a.cout / 8;
-    const int chunks = (n8 + 7) / 8;
-    if (n8 % chunks) return -1;
-    const int nt = n8 / chunks;
-    const dim3 grid(gx, chunks);
-    switch (nt) {
-        case 2: k_conv3<2><<<grid, kConvThreads, 0, st>>>(a); break;
-        case 4: k_conv3<4><<<grid, kConvThreads, 0, st>>>(a); break;
-        case 5: k_conv3<5><<<grid, kConvThreads, 0, st>>>(a); break;
-        case 6: k_conv3<6><<<grid, kConvThreads, 0, st>>>(a); break;
-        case 7: k_conv3<7><<<grid, kConvThreads, 0, st>>>(a); break;
-        case 8: k_conv3<8><<<grid, kConvThreads, 0, st>>>(a); break;
-        default: return -1;
-    }
-    return 0;
-}
-
 int conv3_wgrad(const WgradArgs &a, cudaStream_t st) {
     const ConvArgs &c = a.in;
     if ((a.cout & 15) || a.cout > 64 || (c.c0s & 15) || (c.c1s & 15) || a.S <= 0) return -1;

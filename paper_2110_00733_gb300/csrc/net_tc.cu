@@ -1,0 +1,316 @@
+// net_tc.cu -- periodic 3x3x3 convolution as an implicit GEMM on the 5th-
+// generation tensor cores: tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulator in tensor memory), issued by one thread, completion tracked on
+// mbarriers with tcgen05.commit, the result read back with tcgen05.ld.
+//
+// CTA tile: M = 128 output voxels x N = all output channels (<= 256, a
+// multiple of 16) x K = 27 taps x input channels, consumed 64 K at a time
+// through a 4-stage ring.  Warp-specialised: four producer warps gather the
+// operands with cp.async (two chunks in flight per thread), fence them for
+// the tensor core and arrive on the stage's "full" barrier; a fifth warp
+// waits on it, issues the MMAs and commits to the stage's "empty" barrier,
+// which the producers wait on before reusing the stage.
+// Each K chunk is staged by cp.async (16-byte rows, the gathered input rows
+// with periodic wrap and the half-resolution second source as in the
+// mma.sync kernel) into the canonical no-swizzle K-major layout of the MMA:
+// core matrices of 8 rows x 16 bytes, K-adjacent core matrices LBO = 128 B
+// apart, 8-row groups SBO = 1024 B apart.
+//
+// Every wait is bounded; on a timeout the kernel records it in g_tc_err,
+// waits (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "net_internal.h"
+
+namespace hnet {
+
+__device__ int g_tc_err;
+
+namespace {
+
+constexpr int kProducers = 128;   // 4 warps: operand staging, then the epilogue (one TMEM lane quarter each)
+constexpr int kThreads = kProducers + 32;   // + 1 warp that issues the MMAs
+constexpr int kBM = 128;          // M per CTA (tcgen05 M = 128, cta_group::1)
+constexpr int kBK = 64;           // K elements per stage (4 MMAs of K = 16)
+constexpr int kStages = 4;
+constexpr int kLBO = 128;         // K-adjacent core matrices
+constexpr int kSBO = kBK / 8 * 128;   // 8-row groups (kBK/8 K-chunks of 128 B)
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// shared-memory matrix descriptor: start >> 4, LBO >> 4, SBO >> 4, version 1
+// (bit 46), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// 8 input channels (16 bytes) of K chunk q (K = 8q .. 8q+7) for voxel (b,z,y,x)
+__device__ __forceinline__ const __nv_bfloat16 *k8_src(const ConvArgs &a, int cin_s, int b, int z, int y, int x,
+                                                      int q) {
+    const int k = 8 * q;
+    const int t = k / cin_s, ci = k - t * cin_s;
+    const int zz = wrapi(z + t / 9 - 1, a.n1), yy = wrapi(y + (t / 3) % 3 - 1, a.n2), xx = wrapi(x + t % 3 - 1, a.n3);
+    if (ci < a.c0s) {
+        const long long v = (((long long)b * a.n1 + zz) * a.n2 + yy) * a.n3 + xx;
+        return a.src0 + v * a.c0s + ci;
+    }
+    const long long v = (((long long)b * (a.n1 >> 1) + (zz >> 1)) * (a.n2 >> 1) + (yy >> 1)) * (a.n3 >> 1) + (xx >> 1);
+    return a.src1 + v * a.c1s + (ci - a.c0s);
+}
+
+__global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs a, int ncols) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.cout;
+    const int cin_s = a.c0s + a.c1s;
+    const int ktot = 27 * cin_s;                       // multiple of 16
+    const int nk = (ktot + kBK - 1) / kBK;
+    const int a_bytes = kBM / 8 * kSBO;                // 16 KB
+    const int b_bytes = N / 8 * kSBO;
+    const int stage_bytes = a_bytes + b_bytes;
+    const long long V = (long long)a.n1 * a.n2 * a.n3;
+    const long long total = V * a.B;
+    const long long m0 = (long long)blockIdx.x * kBM;
+    constexpr int kMma = kProducers / 32;              // the MMA warp
+
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], kProducers);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kMma) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            int ncommit[kStages] = {};
+            const uint32_t idesc = instr_desc(N);
+            bool ok = true;
+            for (int c = 0; c < nk && ok; ++c) {
+                const int s = c % kStages;
+                ok = mbar_wait(&full[s], (uint32_t)(c / kStages) & 1u) && !abort_flag;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ab = saddr(smem + s * stage_bytes), bb = ab + a_bytes;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    mma_bf16(tmem, smem_desc(ab + kk * 2 * kLBO), smem_desc(bb + kk * 2 * kLBO), idesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);
+                ++ncommit[s];
+            }
+            if (ok) {
+                mma_commit(&done);
+            } else {
+                abort_flag = 1;
+                atomicExch(&g_tc_err, 1);
+                // let the issued MMAs drain (bounded) before the accumulator is freed
+                for (int s = 0; s < kStages; ++s)
+                    if (ncommit[s] > 0) mbar_wait(&empty[s], (uint32_t)(ncommit[s] - 1) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- producers: operand staging
+        const long long mrow = m0 + tid;
+        const bool row_ok = mrow < total;
+        int rb = 0, rz = 0, ry = 0, rx = 0;
+        if (row_ok) {
+            long long r = mrow;
+            rx = (int)(r % a.n3); r /= a.n3;
+            ry = (int)(r % a.n2); r /= a.n2;
+            rz = (int)(r % a.n1); rb = (int)(r / a.n1);
+        }
+        bool ok = true;
+        for (int c = 0; c < nk + kStages - 2 && ok; ++c) {
+            if (c < nk) {
+                const int s = c % kStages;
+                if (c >= kStages) ok = mbar_wait(&empty[s], (uint32_t)(c / kStages - 1) & 1u) && !abort_flag;
+                if (!ok) break;
+                unsigned char *base = smem + s * stage_bytes;
+                const uint32_t ab = saddr(base), bb = saddr(base + a_bytes);
+#pragma unroll
+                for (int j = 0; j < kBK / 8; ++j) {
+                    const int q = c * (kBK / 8) + j;
+                    const bool in = row_ok && 8 * q < ktot;
+                    const __nv_bfloat16 *src = in ? k8_src(a, cin_s, rb, rz, ry, rx, q) : a.src0;
+                    cp_async16(ab + (tid >> 3) * kSBO + j * kLBO + (tid & 7) * 16, src, in ? 16 : 0);
+                }
+                for (int i = tid; i < N * (kBK / 8); i += kProducers) {
+                    const int n = i / (kBK / 8), j = i - n * (kBK / 8);
+                    const int k = 8 * (c * (kBK / 8) + j);
+                    const bool in = k < ktot;
+                    const int t = in ? k / cin_s : 0, ci = in ? k - t * cin_s : 0;
+                    const __nv_bfloat16 *src = a.W + ((long long)t * N + n) * cin_s + ci;
+                    cp_async16(bb + (n >> 3) * kSBO + j * kLBO + (n & 7) * 16, src, in ? 16 : 0);
+                }
+            }
+            cp_async_commit();
+            // chunk c - (kStages - 2) has landed for this thread: fence it for
+            // the tensor core and report it
+            cp_async_wait<kStages - 2>();
+            const int r = c - (kStages - 2);
+            if (r >= 0 && r < nk) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[r % kStages])) : "memory");
+            }
+        }
+        cp_async_wait<0>();
+        if (!ok) abort_flag = 1;
+        // ---- epilogue: all MMAs done -> TMEM -> bias, ReLU -> global
+        if (ok) ok = mbar_wait(&done, 0u) && !abort_flag;
+        if (ok) {
+            tc_fence_after();
+            const long long m = m0 + tid;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                if (m < total) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (a.bias) v[i] += a.bias[c0 + i];
+                        if (a.relu) v[i] = fmaxf(v[i], 0.f);
+                    }
+                    if (a.out_f32) {
+                        float4 *o = reinterpret_cast<float4 *>(a.out_f32 + m * N + c0);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    } else {
+                        __nv_bfloat162 h[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(a.out_bf16 + m * N + c0);
+                        o[0] = *reinterpret_cast<uint4 *>(&h[0]);
+                        o[1] = *reinterpret_cast<uint4 *>(&h[4]);
+                    }
+                }
+            }
+        } else if (tid == 0) {
+            atomicExch(&g_tc_err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+}  // namespace
+
+int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
+    if ((a.cout & 15) || a.cout > 256 || a.cout < 16 || (a.c0s & 15) || (a.c1s & 15) || a.c0s <= 0) return -1;
+    if (a.c1s && (!a.src1 || (a.n1 | a.n2 | a.n3) & 1)) return -1;
+    int ncols = 32;
+    while (ncols < a.cout) ncols <<= 1;
+    const size_t smem = (size_t)kStages * (kBM / 8 * kSBO + a.cout / 8 * kSBO);
+    static bool attr = false;
+    if (!attr) {
+        int dev = 0, lim = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        attr = true;
+    }
+    const long long total = (long long)a.n1 * a.n2 * a.n3 * a.B;
+    k_conv3_tc<<<(unsigned)((total + kBM - 1) / kBM), kThreads, smem, st>>>(a, ncols);
+    return 0;
+}
+
+int conv3_tc_error(int clear) {
+    int e = 0;
+    cudaMemcpyFromSymbol(&e, g_tc_err, sizeof(int));
+    if (clear && e) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tc_err, &z, sizeof(int));
+    }
+    return e;
+}
+
+}  // namespace hnet

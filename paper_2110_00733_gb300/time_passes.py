@@ -8,14 +8,15 @@ its algorithmic bytes.  Used for launch-shape sweeps and, with --reps 1, as
 a small driver for ncu captures of the pass kernels:
 
     ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
-        --clock-control none -k "regex:k_x|k_lanczos" -c 12 --csv --log-file traffic.csv \
+        --clock-control none -k "regex:k_x|k_lanczos" -c 15 --csv --log-file traffic.csv \
         python -m paper_2110_00733_gb300.time_passes --shape 256,128,256 --reps 1
     python -m paper_2110_00733_gb300.time_passes --traffic traffic.csv --shape 256,128,256
 
-The second command turns the capture (each kernel launched twice: warm-up
-and one timed launch; the first launch of each is used) into
-profiles/traffic.json, which bench.py reads while the CUDA sources are
-unchanged.
+The second command turns the capture into profiles/traffic.json, which
+bench.py reads while the solver's kernel sources are unchanged: the FP32
+launches are kept (context creation runs three FP64 passes first), each
+kernel of the iteration appears twice (warm-up and one timed launch) and the
+first of each is used.
 """
 from __future__ import annotations
 
@@ -83,13 +84,13 @@ def write_traffic(csv_path, shape):
         scale = {"byte": 1e-6, "Kbyte": 1e-3, "Mbyte": 1.0, "Gbyte": 1e3}.get(r[ui], 1.0)
         if r[mi].startswith("dram__bytes"):
             d[r[mi]] = float(r[vi].replace(",", "")) * scale
-    seq = [launches[k] for k in sorted(launches)]
+    seq = [launches[k] for k in sorted(launches) if "<float" in launches[k]["name"]]
     # hom_time_kernels launches each kernel twice (warm-up, then --reps 1)
     firsts = seq[0::2]
     V = int(np.prod(shape))
     out = {"source_hash": source_hash(), "grid": list(shape),
            "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                      "--clock-control none -k \"regex:k_x|k_lanczos\" -c 12 --csv --log-file traffic.csv "
+                      "--clock-control none -k \"regex:k_x|k_lanczos\" -c 15 --csv --log-file traffic.csv "
                       f"python -m paper_2110_00733_gb300.time_passes --shape {','.join(map(str, shape))} --reps 1",
            "note": "bytes per voxel on this grid (work spectrum larger than L2); traffic scales with the voxel "
                    "count at fixed n3, so bench.py multiplies by n^3 for the 256^3 workload",
@@ -106,11 +107,13 @@ def write_traffic(csv_path, shape):
 
 
 def source_hash():
-    """Hash of the CUDA sources (the same rule as bench.py)."""
+    """Hash of the solver's kernel sources (the network's files do not change
+    the solver kernels' traffic)."""
     import hashlib
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_2110_00733_gb300", "csrc")
-    for fn in sorted(os.listdir(cdir)):
+    for fn in ("hom_fft.cuh", "hom_tma.cuh", "hom_passes.cuh", "hom_modb.cuh", "hom_internal.h",
+               "hom_kernels_f32.cu", "hom_kernels_f64.cu"):
         with open(os.path.join(cdir, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
