@@ -497,12 +497,22 @@ template <typename R>
 static void rhs_modb(hom_ctx *ctx, Engine<R> &E, const double *macro_mandel, cpx<R> *b) {
     cudaStream_t s = ctx->stream;
     const Geometry &g = E.gm;
-    Launch<R>::x3(g, s, X3_IN_MACRO, nullptr, X3_MID_MATERIAL, ctx->lam, ctx->mu, macro_mandel, -1.0, X3_OUT_SPEC,
-                  E.spec10, E.phi, nullptr);
-    Launch<R>::x2(g, s, 0, E.spec10, nullptr);
-    Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, nullptr);
+    if constexpr (sizeof(R) == 8) {
+        // F{C : E_bar} = phi^ (C_m : E_bar): no transform needed
+        double tau[6];
+        const double tr = macro_mandel[0] + macro_mandel[1] + macro_mandel[2];
+        for (int c = 0; c < 6; ++c) tau[c] = (c < 3 ? ctx->lam * tr : 0.0) + 2.0 * ctx->mu * macro_mandel[c];
+        Launch<R>::phihat_tau10(g, s, ctx->phihat, tau, E.spec10);
+        ctx->launches += 1;
+    } else {
+        Launch<R>::x3(g, s, X3_IN_MACRO, nullptr, X3_MID_MATERIAL, ctx->lam, ctx->mu, macro_mandel, -1.0,
+                      X3_OUT_SPEC, E.spec10, E.phi, nullptr);
+        Launch<R>::x2(g, s, 0, E.spec10, nullptr);
+        Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, nullptr);
+        ctx->launches += 3;
+    }
     Launch<R>::modb_contract(g, s, E.spec10, b, nullptr, nullptr, nullptr);
-    ctx->launches += 4;
+    ctx->launches += 1;
 }
 
 // mean stiffness of eq. (avstiff) in units of E
@@ -1122,7 +1132,14 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         if (rc) return rc;
         return finish_case(ctx, icase, m, x, &inf, status, info);
     }
-    rhs_spec<double>(ctx, ctx->e64, m, ctx->b64);
+    {
+        // F{C : E_bar} = phi^ (C_m : E_bar): one point-wise FP64 pass
+        double tau[6];
+        const double tr = m[0] + m[1] + m[2];
+        for (int c = 0; c < 6; ++c) tau[c] = (c < 3 ? ctx->lam * tr : 0.0) + 2.0 * ctx->mu * m[c];
+        Launch<double>::rhs_phihat(ctx->e64.g, s, ctx->phihat, tau, ctx->b64);
+        ctx->launches += 1;
+    }
     double b2 = 0.0;
     int rc = spec_norm2<double>(ctx, ctx->e64, ctx->b64, &b2);
     if (rc) return rc;

@@ -134,6 +134,11 @@ template <typename R> struct Launch {
     // Parseval partials of <phi, (G x^)_c>, c = 0..5 (see k_phi_dot); returns
     // the number of blocks (partials[c * nb + block])
     static int phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials);
+    // b^ = -G (phi^ tau) for the constant tensor tau = C_m : E_bar (Mandel)
+    static void rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau, cpx<R> *out);
+    // out10 = (-phi^ tau, 0, 0, 0, 0): the MoDBFFT stress input of C : E_bar
+    static void phihat_tau10(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau,
+                             cpx<R> *out10);
     // y = a x + b y over n reals
     static void axpby(long long n, cudaStream_t st, double a, const R *x, double b, R *y);
     // weighted partial ||x||^2 of a spectral vector with nc components per frequency

@@ -642,6 +642,40 @@ __global__ void __launch_bounds__(kEwThreads) k_phi_dot(Geometry g, const cpx<R>
     }
 }
 
+// Right-hand side from the DFT of phi: F{phi C_m : E_bar} = phi^ tau with the
+// constant tau = C_m : E_bar, so b^ = -G (phi^ tau), eq. (gallin), one point-wise
+// pass (tau: Mandel, units of E).
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_rhs_phihat(Geometry g, const cpx<R> *__restrict__ phihat, Mac6 tau,
+                                                           cpx<R> *__restrict__ out) {
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < g.S; f += (long long)gridDim.x * blockDim.x) {
+        const int k3 = (int)(f % g.h);
+        const long long r = f / g.h;
+        const int k2 = (int)(r % g.n2), k1 = (int)(r / g.n2);
+        const cpx<R> ph = phihat[f];
+        cpx<R> t[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[c] = mk<R>(-(R)tau.v[c] * ph.x, -(R)tau.v[c] * ph.y);
+        gamma_at<R>(g, k1, k2, k3, t);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) out[6 * f + c] = t[c];
+    }
+}
+
+// 10-component MoDBFFT input whose stress part is F{phi C_m : E_bar} =
+// phi^ tau (times -1) and whose penalty part is zero
+template <typename R>
+__global__ void __launch_bounds__(kEwThreads) k_phihat_tau10(long long S, const cpx<R> *__restrict__ phihat, Mac6 tau,
+                                                             cpx<R> *__restrict__ out10) {
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < S; f += (long long)gridDim.x * blockDim.x) {
+        const cpx<R> ph = phihat[f];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) out10[10 * f + c] = mk<R>(-(R)tau.v[c] * ph.x, -(R)tau.v[c] * ph.y);
+#pragma unroll
+        for (int c = 6; c < 10; ++c) out10[10 * f + c] = mk<R>(0, 0);
+    }
+}
+
 template <typename R>
 __global__ void k_axpby(long long n, R a, const R *__restrict__ x, R b, R *__restrict__ y) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -855,6 +889,20 @@ int Launch<R>::phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, cons
     const int nb = ew_grid(g.S);
     k_phi_dot<R><<<nb, kEwThreads, 0, st>>>(g, x, phihat, partials);
     return nb;
+}
+
+template <typename R>
+void Launch<R>::rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau, cpx<R> *out) {
+    Mac6 m{};
+    for (int c = 0; c < 6; ++c) m.v[c] = tau[c];
+    k_rhs_phihat<R><<<ew_grid(g.S), kEwThreads, 0, st>>>(g, phihat, m, out);
+}
+
+template <typename R>
+void Launch<R>::phihat_tau10(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau, cpx<R> *out10) {
+    Mac6 m{};
+    for (int c = 0; c < 6; ++c) m.v[c] = tau[c];
+    k_phihat_tau10<R><<<ew_grid(g.S), kEwThreads, 0, st>>>(g.S, phihat, m, out10);
 }
 
 template <typename R>
