@@ -282,6 +282,200 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tc(ConvArgs a, int ncols) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+
+// ---------------------------------------------------------------------------
+// Halo-tile variant for grids that a 4 x 4 x 8 brick tiles: the CTA's 128
+// output voxels are one brick; for each 16-channel chunk of the input the
+// periodic 6 x 6 x 10 halo is loaded once (cp.async), and each tap's A
+// operand (128 rows x 16 K) is copied out of it in shared memory, so every
+// input row leaves L2 once per CTA instead of once per tap.  One MMA
+// (K = 16) per (chunk, tap) stage; A/B in the no-swizzle K-major layout with
+// LBO = 128 B, SBO = 256 B.
+// ---------------------------------------------------------------------------
+constexpr int kHZ = 6, kHY = 6, kHX = 10, kHalo = kHZ * kHY * kHX;   // halo rows
+constexpr int kHSt = 4;                      // stage ring
+constexpr int kHLag = 2;                     // stages of B loads in flight per thread
+constexpr int kHSBO = 256;                   // K = 16: two K core matrices per 8-row group
+
+__device__ __forceinline__ uint64_t smem_desc_h(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kHSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
+
+__global__ void __launch_bounds__(kThreads) k_conv3_tch(ConvArgs a, int ncols) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kHSt], empty[kHSt], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.cout;
+    const int cin_s = a.c0s + a.c1s;
+    const int nch = cin_s / 16;
+    const int nst = nch * 27;                          // stages: (chunk, tap)
+    const int a_bytes = kBM / 8 * kHSBO;               // 4 KB
+    const int b_bytes = N / 8 * kHSBO;
+    const int stage_bytes = a_bytes + b_bytes;
+    unsigned char *halo = smem;                        // kHalo rows x 32 B
+    unsigned char *ring = smem + kHalo * 32;
+    // this CTA's brick
+    const int bx3 = a.n3 / 8, by2 = a.n2 / 4, bz1 = a.n1 / 4;
+    int r = blockIdx.x;
+    const int xb = r % bx3; r /= bx3;
+    const int yb = r % by2; r /= by2;
+    const int zb = r % bz1;
+    const int b = r / bz1;
+    const int z0 = zb * 4, y0 = yb * 4, x0 = xb * 8;
+    constexpr int kMma = kProducers / 32;
+
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < kHSt; ++q) {
+            mbar_init(&full[q], kProducers);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kMma) {
+        if (lane == 0) {
+            int ncommit[kHSt] = {};
+            const uint32_t idesc = instr_desc(N);
+            bool ok = true;
+            for (int c = 0; c < nst && ok; ++c) {
+                const int q = c % kHSt;
+                ok = mbar_wait(&full[q], (uint32_t)(c / kHSt) & 1u) && !abort_flag;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ab = saddr(ring + q * stage_bytes), bb = ab + a_bytes;
+                mma_bf16(tmem, smem_desc_h(ab), smem_desc_h(bb), idesc, c > 0 ? 1u : 0u);
+                mma_commit(&empty[q]);
+                ++ncommit[q];
+            }
+            if (ok) {
+                mma_commit(&done);
+            } else {
+                abort_flag = 1;
+                atomicExch(&g_tc_err, 1);
+                for (int q = 0; q < kHSt; ++q)
+                    if (ncommit[q] > 0) mbar_wait(&empty[q], (uint32_t)(ncommit[q] - 1) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // my output row m = tid: brick offsets (bz, by, bx)
+        const int bz = tid >> 5, by = (tid >> 3) & 3, bx = tid & 7;
+        bool ok = true;
+        int stage = 0, arrived = 0;
+        auto arrive_upto = [&](int upto) {   // stages [arrived, upto) have landed
+            if (arrived < upto) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (; arrived < upto; ++arrived)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[arrived % kHSt]))
+                             : "memory");
+        };
+        // every producer passes the same named barriers: after a failed wait a
+        // thread keeps going through them and only skips the work
+        for (int cc = 0; cc < nch; ++cc) {
+            // the halo of channel chunk cc (all earlier copies out of it are done)
+            bar_producers();
+            if (ok) {
+                const bool first = cc * 16 < a.c0s;
+                for (int h = tid; h < kHalo; h += kProducers) {
+                    const int hx = h % kHX, hy = (h / kHX) % kHY, hz = h / (kHX * kHY);
+                    const int zz = wrapi(z0 - 1 + hz, a.n1), yy = wrapi(y0 - 1 + hy, a.n2),
+                              xx = wrapi(x0 - 1 + hx, a.n3);
+                    const __nv_bfloat16 *src;
+                    if (first) {
+                        const long long v = (((long long)b * a.n1 + zz) * a.n2 + yy) * a.n3 + xx;
+                        src = a.src0 + v * a.c0s + cc * 16;
+                    } else {
+                        const long long v = (((long long)b * (a.n1 >> 1) + (zz >> 1)) * (a.n2 >> 1) + (yy >> 1)) *
+                                                (a.n3 >> 1) + (xx >> 1);
+                        src = a.src1 + v * a.c1s + (cc * 16 - a.c0s);
+                    }
+                    cp_async16(saddr(halo + h * 32), src, 16);
+                    cp_async16(saddr(halo + h * 32 + 16), src + 8, 16);
+                }
+            }
+            cp_async_commit();
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (ok) arrive_upto(stage);         // B loads of earlier stages completed too
+            bar_producers();
+            for (int t = 0; t < 27; ++t, ++stage) {
+                if (!ok) continue;
+                const int q = stage % kHSt;
+                if (stage >= kHSt) ok = mbar_wait(&empty[q], (uint32_t)(stage / kHSt - 1) & 1u) && !abort_flag;
+                if (!ok) continue;
+                unsigned char *base = ring + q * stage_bytes;
+                // A: my row's 16 channels at the tap's halo position
+                const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                const int h = ((bz + dz) * kHY + (by + dy)) * kHX + (bx + dx);
+                const uint4 lo = *reinterpret_cast<const uint4 *>(halo + h * 32);
+                const uint4 hi = *reinterpret_cast<const uint4 *>(halo + h * 32 + 16);
+                *reinterpret_cast<uint4 *>(base + (tid >> 3) * kHSBO + (tid & 7) * 16) = lo;
+                *reinterpret_cast<uint4 *>(base + (tid >> 3) * kHSBO + kLBO + (tid & 7) * 16) = hi;
+                // B: W[t][n][cc*16 .. +16]
+                const uint32_t bb = saddr(base + a_bytes);
+                for (int i = tid; i < N * 2; i += kProducers) {
+                    const int n = i >> 1, j = i & 1;
+                    const __nv_bfloat16 *src = a.W + ((long long)t * N + n) * cin_s + cc * 16 + j * 8;
+                    cp_async16(bb + (n >> 3) * kHSBO + j * kLBO + (n & 7) * 16, src, 16);
+                }
+                cp_async_commit();
+                cp_async_wait<kHLag>();
+                arrive_upto(stage + 1 - kHLag);
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (ok) arrive_upto(nst);
+        if (!ok) abort_flag = 1;
+        if (ok) ok = mbar_wait(&done, 0u) && !abort_flag;
+        if (ok) {
+            tc_fence_after();
+            const long long m = (((long long)b * a.n1 + z0 + bz) * a.n2 + y0 + by) * a.n3 + x0 + bx;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (a.bias) v[i] += a.bias[c0 + i];
+                    if (a.relu) v[i] = fmaxf(v[i], 0.f);
+                }
+                if (a.out_f32) {
+                    float4 *o = reinterpret_cast<float4 *>(a.out_f32 + m * N + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                } else {
+                    __nv_bfloat162 hv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out_bf16 + m * N + c0);
+                    o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
+                    o[1] = *reinterpret_cast<uint4 *>(&hv[4]);
+                }
+            }
+        } else if (tid == 0) {
+            atomicExch(&g_tc_err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 }  // namespace
 
 int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
@@ -289,15 +483,26 @@ int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
     if (a.c1s && (!a.src1 || (a.n1 | a.n2 | a.n3) & 1)) return -1;
     int ncols = 32;
     while (ncols < a.cout) ncols <<= 1;
-    const size_t smem = (size_t)kStages * (kBM / 8 * kSBO + a.cout / 8 * kSBO);
     static bool attr = false;
     if (!attr) {
         int dev = 0, lim = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        cudaFuncSetAttribute(k_conv3_tch, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
         attr = true;
     }
+    if (a.n1 % 4 == 0 && a.n2 % 4 == 0 && a.n3 % 8 == 0) {
+        // halo tiles; at least enough shared memory per CTA that the CTAs
+        // resident on an SM never ask for more than its 512 TMEM columns
+        size_t smem = (size_t)kHalo * 32 + (size_t)kHSt * (kBM / 8 * kHSBO + a.cout / 8 * kHSBO);
+        const size_t floor = 233472 / (512 / ncols + 1) + 1024;
+        if (smem < floor) smem = floor;
+        const long long bricks = (long long)(a.n1 / 4) * (a.n2 / 4) * (a.n3 / 8) * a.B;
+        k_conv3_tch<<<(unsigned)bricks, kThreads, smem, st>>>(a, ncols);
+        return 0;
+    }
+    const size_t smem = (size_t)kStages * (kBM / 8 * kSBO + a.cout / 8 * kSBO);
     const long long total = (long long)a.n1 * a.n2 * a.n3 * a.B;
     k_conv3_tc<<<(unsigned)((total + kBM - 1) / kBM), kThreads, smem, st>>>(a, ncols);
     return 0;

@@ -48,7 +48,9 @@ CASES = [  # (batch, grid, c0, c1, cout)
     (1, (8, 8, 8), 16, 0, 16),
     (2, (4, 6, 10), 32, 0, 48),
     (1, (8, 4, 6), 48, 64, 48),     # concatenation with an upsampled coarse source
-    (2, (6, 6, 6), 16, 32, 112),    # 7 n8 tiles per chunk, two chunks; ragged last CTA
+    (2, (6, 6, 6), 16, 32, 112),    # 112 output channels; ragged last CTA
+    (2, (8, 8, 16), 48, 64, 48),    # halo tiles (4x4x8 bricks), upsampled second source
+    (1, (4, 8, 8), 16, 32, 112),    # halo tiles, 112 output channels
 ]
 
 
