@@ -103,6 +103,7 @@ struct hom_ctx {
     double *h_scalar = nullptr;      // pinned
     int *d_flag = nullptr;
     cudaGraphExec_t graph = nullptr;
+    bool graph_loops = false;        // graph is a device-side WHILE loop over the body
     int graph_iters = 6;
     long long graph_kernels = 0;
     long long launches = 0;
@@ -380,15 +381,11 @@ static int spec_norm2(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, double *out) 
 // alternate between vbuf[1] (odd k) and vbuf[0] (even k); p = A u_k is
 // vbuf[2]; w_j sits in wbuf[0] for even j and wbuf[1] for odd j.
 template <typename R>
-static int build_graph(hom_ctx *ctx, Engine<R> &E) {
-    if (ctx->graph) return HOM_OK;
+static void capture_body(hom_ctx *ctx, Engine<R> &E) {
     cpx<R> *ua = (cpx<R> *)ctx->vbuf[0], *ub = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
     cpx<R> *wc = (cpx<R> *)ctx->wbuf[0], *wd = (cpx<R> *)ctx->wbuf[1];
     cpx<R> *x = (cpx<R> *)ctx->xs;
     const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
-    cudaGraph_t graph;
-    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    long long before = ctx->launches;
     for (int it = 0; it < ctx->graph_iters; ++it) {
         const bool odd = (it % 2) == 0;          // step k = it + 1 (mod 2)
         cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
@@ -401,13 +398,59 @@ static int build_graph(hom_ctx *ctx, Engine<R> &E) {
         scalar_givens(ctx->stream, ctx->d_state, ctx->partials, npe);
         ctx->launches += 3;
     }
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+}
+
+// The solve loop as one graph: a WHILE node whose body is graph_iters
+// iterations plus the loop condition, so a whole MINRES sweep is one graph
+// launch with no host polling; where conditional nodes are not available,
+// a graph of the body alone that the host replays.
+template <typename R>
+static int build_graph(hom_ctx *ctx, Engine<R> &E) {
+    if (ctx->graph) return HOM_OK;
+    const long long before = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    bool loops = false;
+    if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        cudaGraphNode_t node;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                CU(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+                capture_body<R>(ctx, E);
+                loop_cond(ctx->stream, h, ctx->d_state);
+                ctx->launches += 1;
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &body);
+                if (e != cudaSuccess) {
+                    cudaGraphDestroy(graph);
+                    return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                }
+                loops = true;
+            }
+        }
+        if (!loops) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+    }
+    if (!loops) {
+        CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        capture_body<R>(ctx, E);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
     ctx->graph_kernels = ctx->launches - before;
-    ctx->launches = before;   // counted per replay instead
-    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    ctx->launches = before;   // counted per body run instead
+    cudaError_t e = cudaGraphInstantiate(&ctx->graph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->graph_loops = loops;
     return HOM_OK;
 }
 
@@ -419,8 +462,9 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     cudaStream_t s = ctx->stream;
     int rc = build_graph<R>(ctx, E);
     if (rc) return rc;
+    const int max_replays = (max_it + ctx->graph_iters - 1) / ctx->graph_iters + 1;
     Launch<R>::norm2w(E.g, s, (const cpx<R> *)ctx->rhs, ctx->partials);
-    scalar_start(s, ctx->d_state, ctx->partials, Launch<R>::ew_grid(6 * ctx->S), tol, max_it);
+    scalar_start(s, ctx->d_state, ctx->partials, Launch<R>::ew_grid(6 * ctx->S), tol, max_it, max_replays);
     ctx->launches += 2;
     CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -438,18 +482,25 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nr, s));
     CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nr, s));
-    // replay the captured iterations until the state says done
-    const int per_check = 4;
-    int replays = 0;
-    const int max_replays = (max_it + ctx->graph_iters - 1) / ctx->graph_iters + 1;
-    while (true) {
-        for (int r = 0; r < per_check && replays < max_replays; ++r, ++replays) {
-            CU(cudaGraphLaunch(ctx->graph, s));
-            ctx->launches += ctx->graph_kernels;
-        }
+    if (ctx->graph_loops) {
+        // one launch: the device repeats the body until done (or the cap)
+        CU(cudaGraphLaunch(ctx->graph, s));
         CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        if (ctx->h_state->done || replays >= max_replays) break;
+        ctx->launches += (long long)ctx->h_state->bodies * ctx->graph_kernels;
+    } else {
+        // replay the captured body until the state says done
+        const int per_check = 4;
+        int replays = 0;
+        while (true) {
+            for (int r = 0; r < per_check && replays < max_replays; ++r, ++replays) {
+                CU(cudaGraphLaunch(ctx->graph, s));
+                ctx->launches += ctx->graph_kernels;
+            }
+            CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            if (ctx->h_state->done || replays >= max_replays) break;
+        }
     }
     // the last step's lagged w / x update
     Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->wbuf[0],

@@ -50,7 +50,8 @@ __global__ void k_reduce_to(const double *partials, int np, double *out) {
 // MINRES set-up from ||b||^2: beta_1, phibar_0 = beta_1, c_0 = -1, s_0 = 0,
 // delta-bar_1 = 0, epsilon_1 = 0 (Paige-Saunders).  The Lanczos vectors are
 // kept unnormalised, u_k = beta_k v_k, so u_1 = b and beta_0 = 0.
-__global__ void k_scalar_start(MinresState *st, const double *partials, int np, double tol, int max_it) {
+__global__ void k_scalar_start(MinresState *st, const double *partials, int np, double tol, int max_it,
+                               int max_bodies) {
     const double b2 = reduce_partials(partials, np);
     if (threadIdx.x != 0) return;
     const double beta1 = sqrt(b2 > 0 ? b2 : 0.0);
@@ -69,6 +70,8 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
     st->est = 1.0;
     st->k = 0;
     st->max_it = max_it;
+    st->bodies = 0;
+    st->max_bodies = max_bodies;
     st->done = (beta1 == 0.0 || max_it <= 0) ? 1 : 0;
     st->done_update = st->done;
     st->status = 0;
@@ -128,6 +131,14 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
         st->status = 1;
         st->done = 1;
     }
+}
+
+// Condition of the device-side MINRES loop: one more body while not done
+// and below the cap (the cap ends the loop even if done were never set).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, MinresState *st) {
+    if (threadIdx.x != 0) return;
+    st->bodies += 1;
+    cudaGraphSetConditional(h, (!st->done && st->bodies < st->max_bodies) ? 1u : 0u);
 }
 
 // PCG (MoDBFFT, section 2.2): rho_0 = <r0, M r0>, ||r0||^2 from the two
@@ -426,8 +437,12 @@ void phi_convert(long long V, cudaStream_t st, const void *in, int kind, R *out,
 template void phi_convert<float>(long long, cudaStream_t, const void *, int, float *, int *);
 template void phi_convert<double>(long long, cudaStream_t, const void *, int, double *, int *);
 
-void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it) {
-    k_scalar_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it);
+void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it,
+                  int max_bodies) {
+    k_scalar_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it, max_bodies);
+}
+void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s) {
+    k_loop_cond<<<1, 32, 0, st>>>(h, s);
 }
 void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np) {
     k_scalar_alpha<<<1, 1024, 0, st>>>(s, partials, np);

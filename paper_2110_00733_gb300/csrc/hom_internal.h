@@ -45,6 +45,8 @@ struct MinresState {
     // - u_eps w_{k-2}) u_inv_gamma, x += u_tau w_k
     double u_delta, u_eps, u_inv_gamma, u_tau, u_inv_beta;
     double est;        // phibar_k / beta_1
+    int bodies;        // captured bodies run by the device-side loop
+    int max_bodies;    // hard cap of that loop
 };
 
 // Scalars of one preconditioned CG solve (MoDBFFT, section 2.2); same
@@ -183,7 +185,11 @@ int ew_blocks(long long n);
 void hom_set_error(const char *msg);
 
 // single-CTA scalar kernels
-void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it);
+void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it,
+                  int max_bodies = 0);
+// end of a captured MINRES body inside a WHILE graph node: count the body and
+// keep looping while the state is not done and the cap is not reached
+void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s);
 void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np);
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np);
 // PCG scalars (MoDBFFT): start from <r0,z0>, ||r0||^2; step length; direction
