@@ -138,16 +138,25 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
  * est_residual / true_residual the ratio of eq. (modbfftresres).
  *   macro_strain  ncase x 6 tensor components, host memory.
  *   tol           relative residual of eq. (galres), e.g. 1e-6.
- *   max_it        MINRES iteration cap per case (per refinement sweep).
+ *   max_it        MINRES iteration cap per case (per refinement sweep; the
+ *                 MoDBFFT sweeps share it).
  *   warm_start    NULL (zero start) or ncase x 6 x V fluctuation fields, tensor
  *                 components, host or device per device_ptrs; it is projected
- *                 onto compatible fields before use.
+ *                 onto compatible fields before use (with FP32 fields the
+ *                 projection and the first residual use the FP32 operator; a
+ *                 start within 1e-3 of b gets the FP64 residual instead).
  *   info          NULL or ncase records.
  * Returns HOM_OK if every case met tol, HOM_NOT_CONVERGED if one hit max_it,
  * or a negative error.  The solutions stay in the context for
  * hom_fields / hom_effective_stiffness until the next hom_solve.
  * A right-hand side that vanishes up to round-off (e.g. a homogeneous cell)
- * gives the zero fluctuation with 0 iterations. */
+ * gives the zero fluctuation with 0 iterations.
+ * Precision: with HOM_PREC_FP32_FIELDS the fields and transforms are FP32;
+ * the Krylov scalars, the right-hand side, the true residual after every
+ * refinement sweep and the mean stress (by Parseval from the FP64 DFT of phi)
+ * are FP64.  Each MINRES sweep runs on the device as one graph launch.
+ * Not thread-safe for one context; distinct contexts may be used from
+ * distinct threads (see hom_solve_batch). */
 int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol,
               int max_it, const void *warm_start, hom_solve_info *info);
 
