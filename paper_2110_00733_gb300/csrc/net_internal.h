@@ -38,6 +38,7 @@ struct WgradArgs {
 int conv3_forward_tc(const ConvArgs &a, cudaStream_t st);   // tcgen05, cout <= 256
 // nonzero if a tcgen05 convolution gave up a bounded wait (clears it if asked)
 int conv3_tc_error(int clear);
-int conv3_wgrad(const WgradArgs &a, cudaStream_t st);
+int conv3_wgrad(const WgradArgs &a, cudaStream_t st);      // tcgen05 where bricks tile the grid, else mma.sync
+int conv3_wgrad_tc(const WgradArgs &a, cudaStream_t st);   // -1 if the shape does not suit it
 
 }  // namespace hnet

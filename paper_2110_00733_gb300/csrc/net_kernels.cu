@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad3(WgradArgs a) {
 
 // ------------------------------------------------------------------ launchers
 int conv3_wgrad(const WgradArgs &a, cudaStream_t st) {
+    if (conv3_wgrad_tc(a, st) == 0) return 0;
     const ConvArgs &c = a.in;
     if ((a.cout & 15) || a.cout > 64 || (c.c0s & 15) || (c.c1s & 15) || a.S <= 0) return -1;
     const dim3 grid(a.S, 27, (c.c0s + c.c1s) / 16);

@@ -476,6 +476,204 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tch(ConvArgs a, int ncols) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05: dW[t][co][ci] = sum_v G[v][co] X[v + d_t][ci].
+// D rows are (tap, input channel) pairs, 8 taps x 16 channels = 128 per tap
+// group (4 groups cover 27 taps), N = c_out, K = the 128 voxels of a brick.
+// Both operands are MN-major, which is their natural layout: a 16-byte row
+// of a core matrix is 8 channels of one voxel (X rows out of the halo, G
+// rows out of the output gradient), 8 voxels per core matrix; MN-adjacent
+// core matrices 2048 B apart, K-adjacent ones 128 B.  Without swizzling the
+// descriptor of an MN-major operand takes the K-direction stride as its
+// leading byte offset and the MN-direction stride as its stride byte offset
+// (as for K-major operands, where the 8-row groups run along MN).  A CTA takes
+// one 16-channel chunk of the input and a range of bricks, keeps the four
+// group accumulators in tensor memory, and writes its split's partial sums.
+// ---------------------------------------------------------------------------
+constexpr int kWgMn = 2048;        // MN-adjacent core matrices (16 K-groups x 128 B): SBO
+constexpr int kWgK = 128;          // K-adjacent core matrices: LBO
+constexpr int kWgATile = 16 * kWgMn;   // 128 rows x 128 K, 32 KB
+
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kWgK >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kWgMn >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16, FP32 accumulator, BF16 A and B, both MN-major (bits 15, 16)
+__device__ __forceinline__ uint32_t instr_desc_mn(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, int bricks_per_cta) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], empty[2], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const ConvArgs &a = w.in;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = w.cout;
+    const int cin_s = a.c0s + a.c1s;
+    const int cc = blockIdx.y;
+    const int split = blockIdx.x;
+    const int bx3 = a.n3 / 8, by2 = a.n2 / 4, bz1 = a.n1 / 4;
+    const long long nbricks = (long long)bx3 * by2 * bz1 * a.B;
+    const long long bb0 = (long long)split * bricks_per_cta;
+    const long long bb1 = bb0 + bricks_per_cta < nbricks ? bb0 + bricks_per_cta : nbricks;
+    constexpr int kMma = kProducers / 32;
+    if (bb0 >= bb1) {   // no voxels in this split: its partial sums are zero
+        for (int i = tid; i < 27 * N * 16; i += kThreads) {
+            const int ci = i % 16, r = i / 16, co = r % N, t = r / N;
+            w.partial[(((long long)split * 27 + t) * N + co) * cin_s + cc * 16 + ci] = 0.f;
+        }
+        return;
+    }
+    unsigned char *halo = smem;                              // kHalo rows x 32 B
+    unsigned char *gt = smem + kHalo * 32;                   // G tile: N/8 x 2048 B
+    unsigned char *ring = gt + (N / 8) * kWgMn;           // two A tiles
+
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&full[q], kProducers);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int nst = (int)(bb1 - bb0) * 4;                    // (brick, tap group) stages
+
+    if (warp == kMma) {
+        if (lane == 0) {
+            int ncommit[2] = {0, 0};
+            const uint32_t idesc = instr_desc_mn(N);
+            const uint32_t gb = saddr(gt);
+            bool ok = true;
+            for (int c = 0; c < nst && ok; ++c) {
+                const int q = c & 1, grp = c & 3;
+                ok = mbar_wait(&full[q], (uint32_t)(c >> 1) & 1u) && !abort_flag;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ab = saddr(ring + q * kWgATile);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)   // K = 16 voxels = 2 K-adjacent core matrices per MMA
+                    mma_bf16(tmem + (uint32_t)(grp * N), smem_desc_mn(ab + j * 2 * kWgK),
+                             smem_desc_mn(gb + j * 2 * kWgK), idesc, (c >= 4 || j > 0) ? 1u : 0u);
+                mma_commit(&empty[q]);
+                ++ncommit[q];
+            }
+            if (ok) {
+                mma_commit(&done);
+            } else {
+                abort_flag = 1;
+                atomicExch(&g_tc_err, 1);
+                for (int q = 0; q < 2; ++q)
+                    if (ncommit[q] > 0) mbar_wait(&empty[q], (uint32_t)(ncommit[q] - 1) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // producer row = voxel tid of the brick: offsets (bz, by, bx)
+        const int bz = tid >> 5, by = (tid >> 3) & 3, bx = tid & 7;
+        const bool first = cc * 16 < a.c0s;
+        bool ok = true;
+        int c = 0;
+        for (long long br = bb0; br < bb1; ++br) {
+            long long rr = br;
+            const int xb = (int)(rr % bx3); rr /= bx3;
+            const int yb = (int)(rr % by2); rr /= by2;
+            const int zb = (int)(rr % bz1);
+            const int b = (int)(rr / bz1);
+            const int z0 = zb * 4, y0 = yb * 4, x0 = xb * 8;
+            // the previous brick's MMAs read the G tile: wait for the last of them
+            if (ok && c > 0) ok = mbar_wait(&empty[(c - 1) & 1], (uint32_t)((c - 1) >> 1) & 1u) && !abort_flag;
+            bar_producers();
+            if (ok) {
+                for (int h = tid; h < kHalo; h += kProducers) {
+                    const int hx = h % kHX, hy = (h / kHX) % kHY, hz = h / (kHX * kHY);
+                    const int zz = wrapi(z0 - 1 + hz, a.n1), yy = wrapi(y0 - 1 + hy, a.n2),
+                              xx = wrapi(x0 - 1 + hx, a.n3);
+                    const __nv_bfloat16 *src;
+                    if (first) {
+                        const long long v = (((long long)b * a.n1 + zz) * a.n2 + yy) * a.n3 + xx;
+                        src = a.src0 + v * a.c0s + cc * 16;
+                    } else {
+                        const long long v = (((long long)b * (a.n1 >> 1) + (zz >> 1)) * (a.n2 >> 1) + (yy >> 1)) *
+                                                (a.n3 >> 1) + (xx >> 1);
+                        src = a.src1 + v * a.c1s + (cc * 16 - a.c0s);
+                    }
+                    cp_async16(saddr(halo + h * 32), src, 16);
+                    cp_async16(saddr(halo + h * 32 + 16), src + 8, 16);
+                }
+                // G rows of my voxel: N/8 chunks of 8 output channels
+                const long long v = (((long long)b * a.n1 + z0 + bz) * a.n2 + y0 + by) * a.n3 + x0 + bx;
+                const __nv_bfloat16 *g = w.G + v * N;
+                for (int ng = 0; ng < N / 8; ++ng)
+                    cp_async16(saddr(gt + ng * kWgMn + (tid >> 3) * kWgK + (tid & 7) * 16), g + ng * 8, 16);
+            }
+            cp_async_commit();
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            bar_producers();
+            for (int grp = 0; grp < 4; ++grp, ++c) {
+                if (!ok) continue;
+                const int q = c & 1;
+                if (c >= 2) ok = mbar_wait(&empty[q], (uint32_t)((c >> 1) - 1) & 1u) && !abort_flag;
+                if (!ok) continue;
+                unsigned char *at = ring + q * kWgATile;
+                // A rows (tap, channel half) x K = my voxel: 16 bytes each
+#pragma unroll
+                for (int mg = 0; mg < 16; ++mg) {
+                    const int t = grp * 8 + (mg >> 1);
+                    if (t < 27) {
+                        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                        const int h = ((bz + dz) * kHY + (by + dy)) * kHX + (bx + dx);
+                        *reinterpret_cast<uint4 *>(at + mg * kWgMn + (tid >> 3) * kWgK + (tid & 7) * 16) =
+                            *reinterpret_cast<const uint4 *>(halo + h * 32 + (mg & 1) * 16);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[q])) : "memory");
+            }
+        }
+        if (!ok) abort_flag = 1;
+        if (ok) ok = mbar_wait(&done, 0u) && !abort_flag;
+        if (ok) {
+            tc_fence_after();
+            const int row = warp * 32 + lane;               // (tap in group, channel)
+            const int tl = row >> 4, ci = row & 15;
+            for (int grp = 0; grp < 4; ++grp) {
+                const int t = grp * 8 + tl;
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(grp * N + c0), v);
+                    if (t < 27) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            w.partial[(((long long)split * 27 + t) * N + c0 + i) * cin_s + cc * 16 + ci] = v[i];
+                    }
+                }
+            }
+        } else if (tid == 0) {
+            atomicExch(&g_tc_err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 }  // namespace
 
 int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
@@ -505,6 +703,30 @@ int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
     const size_t smem = (size_t)kStages * (kBM / 8 * kSBO + a.cout / 8 * kSBO);
     const long long total = (long long)a.n1 * a.n2 * a.n3 * a.B;
     k_conv3_tc<<<(unsigned)((total + kBM - 1) / kBM), kThreads, smem, st>>>(a, ncols);
+    return 0;
+}
+
+int conv3_wgrad_tc(const WgradArgs &w, cudaStream_t st) {
+    const ConvArgs &a = w.in;
+    if ((w.cout & 15) || w.cout > 64 || w.cout < 16 || (a.c0s & 15) || (a.c1s & 15) || w.S <= 0) return -1;
+    if (a.n1 % 4 || a.n2 % 4 || a.n3 % 8) return -1;
+    int ncols = 32;
+    while (ncols < 4 * w.cout) ncols <<= 1;
+    static bool attr = false;
+    if (!attr) {
+        int dev = 0, lim = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(k_wgrad3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        attr = true;
+    }
+    size_t smem = (size_t)kHalo * 32 + (size_t)(w.cout / 8) * kWgMn + 2 * (size_t)kWgATile;
+    const size_t floor = 233472 / (512 / ncols + 1) + 1024;    // TMEM columns per SM stay <= 512
+    if (smem < floor) smem = floor;
+    const long long nbricks = (long long)(a.n1 / 4) * (a.n2 / 4) * (a.n3 / 8) * a.B;
+    const int bpc = (int)((nbricks + w.S - 1) / w.S);
+    const dim3 grid(w.S, (a.c0s + a.c1s) / 16);
+    k_wgrad3_tc<<<grid, kThreads, smem, st>>>(w, ncols, bpc);
     return 0;
 }
 

@@ -51,6 +51,8 @@ CASES = [  # (batch, grid, c0, c1, cout)
     (2, (6, 6, 6), 16, 32, 112),    # 112 output channels; ragged last CTA
     (2, (8, 8, 16), 48, 64, 48),    # halo tiles (4x4x8 bricks), upsampled second source
     (1, (4, 8, 8), 16, 32, 112),    # halo tiles, 112 output channels
+    (1, (20, 12, 24), 16, 0, 64),   # weight gradient over 2 voxel splits of 23 and 22 bricks
+    (2, (8, 8, 8), 32, 16, 32),     # 16-channel upsampled second source
 ]
 
 
