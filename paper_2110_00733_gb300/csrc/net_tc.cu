@@ -478,6 +478,385 @@ __global__ void __launch_bounds__(kThreads) k_conv3_tch(ConvArgs a, int ncols) {
 
 
 // ---------------------------------------------------------------------------
+// Halo tiles read in place.  The halo of a 16-channel chunk is stored as
+// three copies, one per tap offset dy, each [6 z][4 y][10 x] rows of 16 bytes
+// (channels 0-7 and 8-15 in two planes).  In copy dy the row of voxel
+// (bz, by, bx) at tap (dz, dy, dx) is (bz + dz) * 40 + by * 10 + bx + dx: the
+// 8 voxels of a brick row are 8 consecutive rows (one core matrix), the 16
+// row groups (bz, by) lie 160 B apart, and the tap only moves the start.  So
+// the A operand of every tap is a canonical K-major layout (SBO = 160 B,
+// LBO = one plane) read straight from the halo: no per-tap copies, and the
+// 27 MMAs of a chunk follow one another with one handoff per chunk.  B holds
+// the chunk's weights for all 27 taps (K-major, N x 32 bytes per tap).
+// ---------------------------------------------------------------------------
+constexpr int kDY = 4;                           // y rows of one copy
+constexpr int kDRows = kHZ * kDY * kHX;          // 240 rows per copy
+constexpr int kDPlane = kDRows * 16;             // one channel half of one copy
+constexpr int kDHalo = 3 * 2 * kDPlane;          // 23040 B
+constexpr int kDSBO = kHX * 16;                  // (bz, by) row groups
+
+__device__ __forceinline__ uint64_t smem_desc_d(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kDPlane >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kDSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// the 27 tap MMAs of one chunk: A read in place from the halo copies, B the
+// chunk's weights (32 N bytes per tap).  The descriptors are built once; a
+// tap only adds its start offset (>> 4) to the address field, which stays
+// inside its 14 bits because shared memory ends below 256 KB.
+__device__ __forceinline__ void tap_mmas(uint32_t d, uint32_t ab, uint32_t bb, int N, uint32_t idesc, bool acc) {
+    const uint64_t ad = smem_desc_d(ab), bd = smem_desc_h(bb);
+    const uint64_t bstep = (uint64_t)(2 * N);          // 32 N bytes >> 4
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        constexpr int kRow = kDY * kHX;
+        const int off = ((t / 3) % 3) * 2 * kDPlane + ((t / 9) * kRow + t % 3) * 16;
+        mma_bf16(d, ad + (uint64_t)(off >> 4), bd + bstep * t, idesc, (acc || t > 0) ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_conv3_tcd(ConvArgs a, int ncols, int ring) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], empty[2], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.cout;
+    const int cin_s = a.c0s + a.c1s;
+    const int nch = cin_s / 16;
+    const int b_bytes = 27 * 32 * N;
+    const int stage_bytes = kDHalo + b_bytes;
+    const int bx3 = a.n3 / 8, by2 = a.n2 / 4, bz1 = a.n1 / 4;
+    int r = blockIdx.x;
+    const int xb = r % bx3; r /= bx3;
+    const int yb = r % by2; r /= by2;
+    const int zb = r % bz1;
+    const int b = r / bz1;
+    const int z0 = zb * 4, y0 = yb * 4, x0 = xb * 8;
+    constexpr int kMma = kProducers / 32;
+
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&full[q], kProducers);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kMma) {
+        if (lane == 0) {
+            int ncommit[2] = {0, 0};
+            const uint32_t idesc = instr_desc(N);
+            bool ok = true;
+            for (int cc = 0; cc < nch && ok; ++cc) {
+                const int q = cc % ring;
+                ok = mbar_wait(&full[q], (uint32_t)(cc / ring) & 1u) && !abort_flag;
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ab = saddr(smem + q * stage_bytes), bb = ab + kDHalo;
+                tap_mmas(tmem, ab, bb, N, idesc, cc > 0);
+                mma_commit(&empty[q]);
+                ++ncommit[q];
+            }
+            if (ok) {
+                mma_commit(&done);
+            } else {
+                abort_flag = 1;
+                atomicExch(&g_tc_err, 1);
+                for (int q = 0; q < 2; ++q)
+                    if (ncommit[q] > 0) mbar_wait(&empty[q], (uint32_t)(ncommit[q] - 1) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // my halo rows: (copy, row) pairs tid + 128 k of the 3 x 240, with the
+        // periodic source voxel of each (full resolution and half resolution)
+        constexpr int kMine = (3 * kDRows + kProducers - 1) / kProducers;   // 6
+        int vfull[kMine], vhalf[kMine], dst[kMine];
+        const int h1 = a.n1 >> 1, h2 = a.n2 >> 1, h3 = a.n3 >> 1;
+#pragma unroll
+        for (int k = 0; k < kMine; ++k) {
+            const int i = tid + k * kProducers;
+            const int dy = i / kDRows, row = i - dy * kDRows;
+            const int xr = row % kHX, yr = (row / kHX) % kDY, zr = row / (kHX * kDY);
+            const int zz = wrapi(z0 - 1 + zr, a.n1), yy = wrapi(y0 - 1 + yr + dy, a.n2),
+                      xx = wrapi(x0 - 1 + xr, a.n3);
+            vfull[k] = (zz * a.n2 + yy) * a.n3 + xx;
+            vhalf[k] = ((zz >> 1) * h2 + (yy >> 1)) * h3 + (xx >> 1);
+            dst[k] = dy * 2 * kDPlane + row * 16;
+        }
+        const __nv_bfloat16 *s0 = a.src0 + (long long)b * a.n1 * a.n2 * a.n3 * a.c0s;
+        const __nv_bfloat16 *s1 = a.c1s ? a.src1 + (long long)b * h1 * h2 * h3 * a.c1s : nullptr;
+        bool ok = true;
+        for (int cc = 0; cc < nch; ++cc) {
+            const int q = cc % ring;
+            if (!ok) continue;
+            if (cc >= ring) ok = mbar_wait(&empty[q], (uint32_t)(cc / ring - 1) & 1u) && !abort_flag;
+            if (!ok) continue;
+            unsigned char *st = smem + q * stage_bytes;
+            const bool first = cc * 16 < a.c0s;
+#pragma unroll
+            for (int k = 0; k < kMine; ++k) {
+                if (tid + k * kProducers < 3 * kDRows) {
+                    const __nv_bfloat16 *src = first ? s0 + (long long)vfull[k] * a.c0s + cc * 16
+                                                     : s1 + (long long)vhalf[k] * a.c1s + (cc * 16 - a.c0s);
+                    cp_async16(saddr(st + dst[k]), src, 16);
+                    cp_async16(saddr(st + dst[k] + kDPlane), src + 8, 16);
+                }
+            }
+            // weights of the chunk, all 27 taps: W[t][n][cc*16 .. +16]
+            const uint32_t bb = saddr(st + kDHalo);
+            for (int i = tid; i < 54 * N; i += kProducers) {
+                const int t = i / (2 * N), rem = i - t * 2 * N, n = rem >> 1, j = rem & 1;
+                const __nv_bfloat16 *src = a.W + ((long long)t * N + n) * cin_s + cc * 16 + j * 8;
+                cp_async16(bb + t * 32 * N + (n >> 3) * kHSBO + j * kLBO + (n & 7) * 16, src, 16);
+            }
+            cp_async_commit();
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[q])) : "memory");
+        }
+        if (!ok) abort_flag = 1;
+        if (ok) ok = mbar_wait(&done, 0u) && !abort_flag;
+        if (ok) {
+            tc_fence_after();
+            const int bz = tid >> 5, by = (tid >> 3) & 3, bx = tid & 7;
+            const long long m = (((long long)b * a.n1 + z0 + bz) * a.n2 + y0 + by) * a.n3 + x0 + bx;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (a.bias) v[i] += a.bias[c0 + i];
+                    if (a.relu) v[i] = fmaxf(v[i], 0.f);
+                }
+                if (a.out_f32) {
+                    float4 *o = reinterpret_cast<float4 *>(a.out_f32 + m * N + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                } else {
+                    __nv_bfloat162 hv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out_bf16 + m * N + c0);
+                    o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
+                    o[1] = *reinterpret_cast<uint4 *>(&hv[4]);
+                }
+            }
+        } else if (tid == 0) {
+            atomicExch(&g_tc_err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Persistent form of the in-place halo convolution: a CTA keeps the weights
+// of all its chunks in shared memory and walks bricks blockIdx.x, +gridDim.x,
+// ...  Halo stages (brick, chunk) go through a 2-slot ring and the brick's
+// accumulator alternates between two TMEM column ranges, so the loads of
+// brick j overlap the MMAs of brick j-1 and the epilogue of brick j-1 runs
+// while the loads of brick j are in flight.  Barriers: hfull/hempty per halo
+// slot (producers / MMA commit), afull/aempty per accumulator (MMA commit /
+// producers after reading it).
+__global__ void __launch_bounds__(kThreads) k_conv3_tcp(ConvArgs a, int ncols) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t hfull[2], hempty[2], afull[2], aempty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.cout;
+    const int cin_s = a.c0s + a.c1s;
+    const int nch = cin_s / 16;
+    const int w_bytes = nch * 27 * 32 * N;
+    unsigned char *halo = smem + w_bytes;              // 2 slots of kDHalo
+    const int bx3 = a.n3 / 8, by2 = a.n2 / 4, bz1 = a.n1 / 4;
+    const int nbricks = bx3 * by2 * bz1 * a.B;
+    const int nb = blockIdx.x < nbricks ? (nbricks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    constexpr int kMma = kProducers / 32;
+    if (nb == 0) return;
+
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&hfull[q], kProducers);
+            mbar_init(&hempty[q], 1);
+            mbar_init(&afull[q], 1);
+            mbar_init(&aempty[q], kProducers);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kMma) {
+        if (lane == 0) {
+            int nh[2] = {0, 0}, na[2] = {0, 0};   // commits per barrier
+            const uint32_t idesc = instr_desc(N);
+            const uint32_t wb = saddr(smem);
+            bool ok = true;
+            for (int j = 0; j < nb && ok; ++j) {
+                const int s = j & 1;
+                if (j >= 2) ok = mbar_wait(&aempty[s], (uint32_t)((j >> 1) - 1) & 1u) && !abort_flag;
+                if (!ok) break;
+                tc_fence_after();
+                for (int cc = 0; cc < nch && ok; ++cc) {
+                    const int k = j * nch + cc, q = k & 1;
+                    ok = mbar_wait(&hfull[q], (uint32_t)(k >> 1) & 1u) && !abort_flag;
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t ab = saddr(halo + q * kDHalo), bb = wb + cc * 27 * 32 * N;
+                    tap_mmas(tmem + (uint32_t)(s * N), ab, bb, N, idesc, cc > 0);
+                    mma_commit(&hempty[q]);
+                    ++nh[q];
+                }
+                if (!ok) break;
+                mma_commit(&afull[s]);
+                ++na[s];
+            }
+            if (!ok) {
+                abort_flag = 1;
+                atomicExch(&g_tc_err, 1);
+                for (int q = 0; q < 2; ++q) {
+                    if (nh[q] > 0) mbar_wait(&hempty[q], (uint32_t)(nh[q] - 1) & 1u);
+                    if (na[q] > 0) mbar_wait(&afull[q], (uint32_t)(na[q] - 1) & 1u);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // my halo rows: (copy, row) pairs tid + 128 k of the 3 x 240
+        constexpr int kMine = (3 * kDRows + kProducers - 1) / kProducers;   // 6
+        int rz[kMine], ry[kMine], rx[kMine], dst[kMine];
+#pragma unroll
+        for (int k = 0; k < kMine; ++k) {
+            const int i = tid + k * kProducers;
+            const int dy = i / kDRows, row = i - dy * kDRows;
+            rx[k] = row % kHX - 1;
+            ry[k] = (row / kHX) % kDY + dy - 1;
+            rz[k] = row / (kHX * kDY) - 1;
+            dst[k] = dy * 2 * kDPlane + row * 16;
+        }
+        const int h1 = a.n1 >> 1, h2 = a.n2 >> 1, h3 = a.n3 >> 1;
+        const int bz = tid >> 5, by = (tid >> 3) & 3, bx = tid & 7;
+        // weights of every chunk and tap: W[t][n][cc*16 .. +16], joined to the first halo group
+        {
+            const uint32_t wb = saddr(smem);
+            for (int i = tid; i < 54 * N * nch; i += kProducers) {
+                const int cc = i / (54 * N), i2 = i - cc * 54 * N;
+                const int t = i2 / (2 * N), rem = i2 - t * 2 * N, n = rem >> 1, jj = rem & 1;
+                const __nv_bfloat16 *src = a.W + ((long long)t * N + n) * cin_s + cc * 16 + jj * 8;
+                cp_async16(wb + (cc * 27 + t) * 32 * N + (n >> 3) * kHSBO + jj * kLBO + (n & 7) * 16, src, 16);
+            }
+        }
+        bool ok = true;
+        int vfull[kMine], vhalf[kMine];
+        int pb = 0, pz0 = 0, py0 = 0, px0 = 0;              // the previous brick, for its epilogue
+        auto epilogue = [&](int j) {                        // brick j's accumulator to the output
+            const int s = j & 1;
+            ok = mbar_wait(&afull[s], (uint32_t)(j >> 1) & 1u) && !abort_flag;
+            if (!ok) return;
+            tc_fence_after();
+            const long long m = (((long long)pb * a.n1 + pz0 + bz) * a.n2 + py0 + by) * a.n3 + px0 + bx;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * N + c0), v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (a.bias) v[i] += a.bias[c0 + i];
+                    if (a.relu) v[i] = fmaxf(v[i], 0.f);
+                }
+                if (a.out_f32) {
+                    float4 *o = reinterpret_cast<float4 *>(a.out_f32 + m * N + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                } else {
+                    __nv_bfloat162 hv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) hv[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out_bf16 + m * N + c0);
+                    o[0] = *reinterpret_cast<uint4 *>(&hv[0]);
+                    o[1] = *reinterpret_cast<uint4 *>(&hv[4]);
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&aempty[s])) : "memory");
+        };
+        for (int j = 0; j < nb && ok; ++j) {
+            int r = (int)blockIdx.x + j * (int)gridDim.x;
+            const int xb = r % bx3; r /= bx3;
+            const int yb = r % by2; r /= by2;
+            const int zb = r % bz1;
+            const int b = r / bz1;
+            const int z0 = zb * 4, y0 = yb * 4, x0 = xb * 8;
+#pragma unroll
+            for (int k = 0; k < kMine; ++k) {
+                const int zz = wrapi(z0 + rz[k], a.n1), yy = wrapi(y0 + ry[k], a.n2), xx = wrapi(x0 + rx[k], a.n3);
+                vfull[k] = (zz * a.n2 + yy) * a.n3 + xx;
+                vhalf[k] = ((zz >> 1) * h2 + (yy >> 1)) * h3 + (xx >> 1);
+            }
+            const __nv_bfloat16 *s0 = a.src0 + (long long)b * a.n1 * a.n2 * a.n3 * a.c0s;
+            const __nv_bfloat16 *s1 = a.c1s ? a.src1 + (long long)b * h1 * h2 * h3 * a.c1s : nullptr;
+            for (int cc = 0; cc < nch && ok; ++cc) {
+                const int k = j * nch + cc, q = k & 1;
+                if (k >= 2) ok = mbar_wait(&hempty[q], (uint32_t)((k >> 1) - 1) & 1u) && !abort_flag;
+                if (!ok) break;
+                unsigned char *st = halo + q * kDHalo;
+                const bool first = cc * 16 < a.c0s;
+#pragma unroll
+                for (int kk = 0; kk < kMine; ++kk) {
+                    if (tid + kk * kProducers < 3 * kDRows) {
+                        const __nv_bfloat16 *src = first ? s0 + (long long)vfull[kk] * a.c0s + cc * 16
+                                                         : s1 + (long long)vhalf[kk] * a.c1s + (cc * 16 - a.c0s);
+                        cp_async16(saddr(st + dst[kk]), src, 16);
+                        cp_async16(saddr(st + dst[kk] + kDPlane), src + 8, 16);
+                    }
+                }
+                cp_async_commit();
+                if (cc == 0 && j > 0) epilogue(j - 1);   // overlaps the loads just issued
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                if (!ok) break;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&hfull[q])) : "memory");
+            }
+            pb = b; pz0 = z0; py0 = y0; px0 = x0;
+        }
+        if (ok) epilogue(nb - 1);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (!ok) {
+            abort_flag = 1;
+            if (tid == 0) atomicExch(&g_tc_err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient on tcgen05: dW[t][co][ci] = sum_v G[v][co] X[v + d_t][ci].
 // D rows are (tap, input channel) pairs, 8 taps x 16 channels = 128 per tap
 // group (4 groups cover 27 taps), N = c_out, K = the 128 voxels of a brick.
@@ -506,6 +885,25 @@ __device__ __forceinline__ uint32_t instr_desc_mn(int n) {
            ((uint32_t)(kBM >> 4) << 24);
 }
 
+// A tile of tap group GRP for one voxel: rows (tap, channel half) of the
+// voxel's column, taken from the two halo planes at the taps' offsets (all
+// loads issued before the stores)
+template <int GRP>
+__device__ __forceinline__ void wg_copy(unsigned char *at, const unsigned char *hv) {
+    constexpr int kNt = GRP < 3 ? 8 : 3;
+    constexpr int kPlane = kHalo * 16;
+    uint4 r[2 * kNt];
+#pragma unroll
+    for (int k = 0; k < kNt; ++k) {
+        const int t = GRP * 8 + k;
+        const int off = (((t / 9) * kHY + (t / 3) % 3) * kHX + t % 3) * 16;
+        r[2 * k] = *reinterpret_cast<const uint4 *>(hv + off);
+        r[2 * k + 1] = *reinterpret_cast<const uint4 *>(hv + kPlane + off);
+    }
+#pragma unroll
+    for (int m = 0; m < 2 * kNt; ++m) *reinterpret_cast<uint4 *>(at + m * kWgMn) = r[m];
+}
+
 __global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, int bricks_per_cta) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[2], empty[2], done;
@@ -529,9 +927,13 @@ __global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, 
         }
         return;
     }
-    unsigned char *halo = smem;                              // kHalo rows x 32 B
-    unsigned char *gt = smem + kHalo * 32;                   // G tile: N/8 x 2048 B
-    unsigned char *ring = gt + (N / 8) * kWgMn;           // two A tiles
+    // two bricks in flight: halo[2] (two planes of 16-byte rows, channels
+    // 0-7 and 8-15), G tile[2], and the two A-tile stages
+    constexpr int kPlane = kHalo * 16;
+    const int gbytes = (N / 8) * kWgMn;
+    unsigned char *halo = smem;                              // 2 x 2 planes
+    unsigned char *gt = smem + 4 * kPlane;                   // 2 x G tile
+    unsigned char *ring = gt + 2 * gbytes;                   // 2 x A tile
 
     if (warp == kMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
@@ -558,7 +960,6 @@ __global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, 
         if (lane == 0) {
             int ncommit[2] = {0, 0};
             const uint32_t idesc = instr_desc_mn(N);
-            const uint32_t gb = saddr(gt);
             bool ok = true;
             for (int c = 0; c < nst && ok; ++c) {
                 const int q = c & 1, grp = c & 3;
@@ -566,6 +967,7 @@ __global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, 
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t ab = saddr(ring + q * kWgATile);
+                const uint32_t gb = saddr(gt + ((c >> 2) & 1) * gbytes);
 #pragma unroll
                 for (int j = 0; j < 8; ++j)   // K = 16 voxels = 2 K-adjacent core matrices per MMA
                     mma_bf16(tmem + (uint32_t)(grp * N), smem_desc_mn(ab + j * 2 * kWgK),
@@ -586,66 +988,75 @@ __global__ void __launch_bounds__(kThreads) k_wgrad3_tc(WgradArgs w, int ncols, 
     } else {
         // producer row = voxel tid of the brick: offsets (bz, by, bx)
         const int bz = tid >> 5, by = (tid >> 3) & 3, bx = tid & 7;
+        const int hrow = ((bz * kHY + by) * kHX + bx) * 16;   // my voxel's halo row at tap offset 0
         const bool first = cc * 16 < a.c0s;
-        bool ok = true;
-        int c = 0;
-        for (long long br = bb0; br < bb1; ++br) {
+        // my halo rows (at most 3 of the 360) and their positions in the halo
+        int hz[3], hy[3], hx[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int h = tid + r * kProducers;
+            hx[r] = h % kHX;
+            hy[r] = (h / kHX) % kHY;
+            hz[r] = h / (kHX * kHY);
+        }
+        // the chunk's source: full resolution, or the half-resolution second
+        // source read with nearest-neighbour upsampling
+        const int sh = first ? 0 : 1;
+        const int m1 = a.n1 >> sh, m2 = a.n2 >> sh, m3 = a.n3 >> sh;
+        const int cs = first ? a.c0s : a.c1s;
+        const __nv_bfloat16 *sbase = first ? a.src0 + cc * 16 : a.src1 + (cc * 16 - a.c0s);
+        // halo of brick br into halo buffer hb, my G row into G buffer hb
+        auto load_brick = [&](long long br, int hb) {
             long long rr = br;
             const int xb = (int)(rr % bx3); rr /= bx3;
             const int yb = (int)(rr % by2); rr /= by2;
             const int zb = (int)(rr % bz1);
             const int b = (int)(rr / bz1);
             const int z0 = zb * 4, y0 = yb * 4, x0 = xb * 8;
-            // the previous brick's MMAs read the G tile: wait for the last of them
-            if (ok && c > 0) ok = mbar_wait(&empty[(c - 1) & 1], (uint32_t)((c - 1) >> 1) & 1u) && !abort_flag;
-            bar_producers();
-            if (ok) {
-                for (int h = tid; h < kHalo; h += kProducers) {
-                    const int hx = h % kHX, hy = (h / kHX) % kHY, hz = h / (kHX * kHY);
-                    const int zz = wrapi(z0 - 1 + hz, a.n1), yy = wrapi(y0 - 1 + hy, a.n2),
-                              xx = wrapi(x0 - 1 + hx, a.n3);
-                    const __nv_bfloat16 *src;
-                    if (first) {
-                        const long long v = (((long long)b * a.n1 + zz) * a.n2 + yy) * a.n3 + xx;
-                        src = a.src0 + v * a.c0s + cc * 16;
-                    } else {
-                        const long long v = (((long long)b * (a.n1 >> 1) + (zz >> 1)) * (a.n2 >> 1) + (yy >> 1)) *
-                                                (a.n3 >> 1) + (xx >> 1);
-                        src = a.src1 + v * a.c1s + (cc * 16 - a.c0s);
-                    }
-                    cp_async16(saddr(halo + h * 32), src, 16);
-                    cp_async16(saddr(halo + h * 32 + 16), src + 8, 16);
+            const __nv_bfloat16 *src_b = sbase + (long long)b * m1 * m2 * m3 * cs;
+            unsigned char *hp = halo + hb * 2 * kPlane + tid * 16;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                if (tid + r * kProducers < kHalo) {
+                    const int zz = wrapi(z0 - 1 + hz[r], a.n1) >> sh, yy = wrapi(y0 - 1 + hy[r], a.n2) >> sh,
+                              xx = wrapi(x0 - 1 + hx[r], a.n3) >> sh;
+                    const __nv_bfloat16 *src = src_b + (long long)((zz * m2 + yy) * m3 + xx) * cs;
+                    cp_async16(saddr(hp + r * kProducers * 16), src, 16);
+                    cp_async16(saddr(hp + kPlane + r * kProducers * 16), src + 8, 16);
                 }
-                // G rows of my voxel: N/8 chunks of 8 output channels
-                const long long v = (((long long)b * a.n1 + z0 + bz) * a.n2 + y0 + by) * a.n3 + x0 + bx;
-                const __nv_bfloat16 *g = w.G + v * N;
-                for (int ng = 0; ng < N / 8; ++ng)
-                    cp_async16(saddr(gt + ng * kWgMn + (tid >> 3) * kWgK + (tid & 7) * 16), g + ng * 8, 16);
             }
+            const long long v = (((long long)b * a.n1 + z0 + bz) * a.n2 + y0 + by) * a.n3 + x0 + bx;
+            const __nv_bfloat16 *g = w.G + v * N;
+            unsigned char *gp = gt + hb * gbytes + (tid >> 3) * kWgK + (tid & 7) * 16;
+            for (int ng = 0; ng < N / 8; ++ng) cp_async16(saddr(gp + ng * kWgMn), g + ng * 8, 16);
             cp_async_commit();
+        };
+        bool ok = true;
+        load_brick(bb0, 0);
+        for (long long br = bb0; br < bb1; ++br) {
+            const int i = (int)(br - bb0), hb = i & 1;
             asm volatile("cp.async.wait_all;" ::: "memory");
-            bar_producers();
-            for (int grp = 0; grp < 4; ++grp, ++c) {
+            bar_producers();     // brick br's halo and G tile are in; brick br-1's copies are done
+            const unsigned char *hp = halo + hb * 2 * kPlane;
+            for (int grp = 0; grp < 4; ++grp) {
+                const int c = 4 * i + grp, q = c & 1;
                 if (!ok) continue;
-                const int q = c & 1;
                 if (c >= 2) ok = mbar_wait(&empty[q], (uint32_t)((c >> 1) - 1) & 1u) && !abort_flag;
                 if (!ok) continue;
-                unsigned char *at = ring + q * kWgATile;
-                // A rows (tap, channel half) x K = my voxel: 16 bytes each
-#pragma unroll
-                for (int mg = 0; mg < 16; ++mg) {
-                    const int t = grp * 8 + (mg >> 1);
-                    if (t < 27) {
-                        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-                        const int h = ((bz + dz) * kHY + (by + dy)) * kHX + (bx + dx);
-                        *reinterpret_cast<uint4 *>(at + mg * kWgMn + (tid >> 3) * kWgK + (tid & 7) * 16) =
-                            *reinterpret_cast<const uint4 *>(halo + h * 32 + (mg & 1) * 16);
-                    }
+                // stage c-2 is the last MMA of brick br-1: its buffers take brick br+1
+                if (grp == 1 && br + 1 < bb1) load_brick(br + 1, hb ^ 1);
+                unsigned char *at = ring + q * kWgATile + (tid >> 3) * kWgK + (tid & 7) * 16;
+                switch (grp) {
+                    case 0: wg_copy<0>(at, hp + hrow); break;
+                    case 1: wg_copy<1>(at, hp + hrow); break;
+                    case 2: wg_copy<2>(at, hp + hrow); break;
+                    default: wg_copy<3>(at, hp + hrow); break;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&full[q])) : "memory");
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         if (!ok) abort_flag = 1;
         if (ok) ok = mbar_wait(&done, 0u) && !abort_flag;
         if (ok) {
@@ -688,7 +1099,57 @@ int conv3_forward_tc(const ConvArgs &a, cudaStream_t st) {
         cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
         cudaFuncSetAttribute(k_conv3_tch, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        cudaFuncSetAttribute(k_conv3_tcd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        cudaFuncSetAttribute(k_conv3_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        // all of the unified L1/shared array as shared memory, so that the
+        // CTAs that the shared-memory budget allows are resident together
+        cudaFuncSetAttribute(k_conv3_tcd, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_conv3_tcp, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_conv3_tch, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         attr = true;
+    }
+    const bool bricks_tile = a.n1 % 4 == 0 && a.n2 % 4 == 0 && a.n3 % 8 == 0;
+    const size_t w_bytes = (size_t)(a.c0s + a.c1s) / 16 * 27 * 32 * a.cout;
+    if (bricks_tile && a.cout <= 128 && w_bytes <= 96 * 1024) {
+        // persistent CTAs with the weights resident; two TMEM accumulators
+        int ncols2 = 32;
+        while (ncols2 < 2 * a.cout) ncols2 <<= 1;
+        size_t smem = w_bytes + 2 * (size_t)kDHalo;
+        const size_t floor = 233472 / (512 / ncols2 + 1) + 1024;
+        if (smem < floor) smem = floor;
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        }
+        // CTAs per SM that shared memory, registers and tensor memory allow
+        static int regs = 0;
+        if (!regs) {
+            cudaFuncAttributes fa{};
+            cudaFuncGetAttributes(&fa, k_conv3_tcp);
+            regs = fa.numRegs > 0 ? (fa.numRegs + 7) / 8 * 8 : 255;
+        }
+        int per_sm = (int)(233472 / (smem + 2048));
+        per_sm = per_sm < 65536 / (regs * kThreads) ? per_sm : 65536 / (regs * kThreads);
+        per_sm = per_sm < 512 / ncols2 ? per_sm : 512 / ncols2;
+        if (per_sm < 1) per_sm = 1;
+        const long long bricks = (long long)(a.n1 / 4) * (a.n2 / 4) * (a.n3 / 8) * a.B;
+        const long long grid = bricks < (long long)per_sm * nsm ? bricks : (long long)per_sm * nsm;
+        k_conv3_tcp<<<(unsigned)grid, kThreads, smem, st>>>(a, ncols2);
+        return 0;
+    }
+    if (bricks_tile && a.cout <= 128) {
+        // halo tiles read in place: two chunk stages where they fit in about
+        // half of the shared memory, else one
+        const size_t stage = (size_t)kDHalo + 27 * 32 * (size_t)a.cout;
+        const int ring = (a.c0s + a.c1s > 16 && 2 * stage <= 116 * 1024) ? 2 : 1;
+        size_t smem = ring * stage;
+        const size_t floor = 233472 / (512 / ncols + 1) + 1024;
+        if (smem < floor) smem = floor;
+        const long long bricks = (long long)(a.n1 / 4) * (a.n2 / 4) * (a.n3 / 8) * a.B;
+        k_conv3_tcd<<<(unsigned)bricks, kThreads, smem, st>>>(a, ncols, ring);
+        return 0;
     }
     if (a.n1 % 4 == 0 && a.n2 % 4 == 0 && a.n3 % 8 == 0) {
         // halo tiles; at least enough shared memory per CTA that the CTAs
@@ -718,9 +1179,10 @@ int conv3_wgrad_tc(const WgradArgs &w, cudaStream_t st) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncSetAttribute(k_wgrad3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - 1024);
+        cudaFuncSetAttribute(k_wgrad3_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         attr = true;
     }
-    size_t smem = (size_t)kHalo * 32 + (size_t)(w.cout / 8) * kWgMn + 2 * (size_t)kWgATile;
+    size_t smem = 2 * ((size_t)kHalo * 32 + (size_t)(w.cout / 8) * kWgMn) + 2 * (size_t)kWgATile;
     const size_t floor = 233472 / (512 / ncols + 1) + 1024;    // TMEM columns per SM stay <= 512
     if (smem < floor) smem = floor;
     const long long nbricks = (long long)(a.n1 / 4) * (a.n2 / 4) * (a.n3 / 8) * a.B;
