@@ -62,10 +62,11 @@ __global__ void k_prep_input(int B, int m1, int m2, int m3, int s, const float *
             for (int bb = 0; bb < s; ++bb)
                 for (int cc = 0; cc < s; ++cc)
                     acc += phi[b * Vf + ((long long)(c1 * s + a) * n2 + c2 * s + bb) * n3 + c3 * s + cc];
-        bf16 *o = x + i * 16;
-        o[0] = __float2bfloat16(acc * inv);
-#pragma unroll
-        for (int k = 1; k < 16; ++k) o[k] = __float2bfloat16(0.f);
+        // the voxel's 16 channels as two 16-byte stores
+        const unsigned short h0 = __bfloat16_as_ushort(__float2bfloat16(acc * inv));
+        uint4 *o = reinterpret_cast<uint4 *>(x + i * 16);
+        o[0] = make_uint4(h0, 0u, 0u, 0u);
+        o[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -153,32 +154,38 @@ __device__ __forceinline__ double block_sum_d(double v) {
 
 // Loss and head gradient: d_c = x0_c - target_c (Mandel), loss partials of
 // sum w d^2 with the voxel weight w = vw + (1 - vw) phi (1 everywhere for
-// vw = 1), G[v][6c+J] = scale w d_c E_J (channels 36..47 zero).
+// vw = 1), G[v][6c+J] = scale w d_c E_J (channels 36..47 zero).  Six
+// consecutive threads take the six components of one voxel, so a warp reads
+// and writes contiguous runs of M and G.
 __global__ void k_loss_grad(int B, long long V, const float *__restrict__ M, const float *__restrict__ E,
                             const float *__restrict__ target, const float *__restrict__ phi, float vw, float scale,
                             bf16 *__restrict__ G, double *__restrict__ partials) {
     double acc = 0.0;
-    const long long total = V * B;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long total = V * B * 6;
+    for (long long i6 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i6 < total;
+         i6 += (long long)gridDim.x * blockDim.x) {
+        const long long i = i6 / 6;
+        const int c = (int)(i6 - i * 6);
         const int b = (int)(i / V);
         const long long v = i - b * V;
-        const float *m = M + i * 48;
+        const float2 *m = reinterpret_cast<const float2 *>(M + i * 48 + 6 * c);
+        const float *e = E + b * 6;
+        const float2 m0 = m[0], m1 = m[1], m2 = m[2];
+        const float x = m0.x * e[0] + m0.y * e[1] + m1.x * e[2] + m1.y * e[3] + m2.x * e[4] + m2.y * e[5];
+        float tv = target[((long long)b * 6 + c) * V + v];
+        if (c >= 3) tv *= kSqrt2;
         const float w = vw + (1.f - vw) * phi[i];
-        float e[6], g[6];
-        for (int j = 0; j < 6; ++j) e[j] = E[b * 6 + j];
-        for (int c = 0; c < 6; ++c) {
-            float x = 0.f;
-            for (int j = 0; j < 6; ++j) x += m[6 * c + j] * e[j];
-            float tv = target[((long long)b * 6 + c) * V + v];
-            if (c >= 3) tv *= kSqrt2;
-            const float d = x - tv;
-            acc += (double)w * d * d;
-            g[c] = scale * w * d;
+        const float d = x - tv;
+        acc += (double)w * d * d;
+        const float g = scale * w * d;
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(G + i * 48 + 6 * c);
+        o[0] = __floats2bfloat162_rn(g * e[0], g * e[1]);
+        o[1] = __floats2bfloat162_rn(g * e[2], g * e[3]);
+        o[2] = __floats2bfloat162_rn(g * e[4], g * e[5]);
+        if (c == 5) {
+            uint2 *z = reinterpret_cast<uint2 *>(G + i * 48 + 36);
+            z[0] = z[1] = z[2] = make_uint2(0u, 0u);
         }
-        bf16 *o = G + i * 48;
-        for (int c = 0; c < 6; ++c)
-            for (int j = 0; j < 6; ++j) o[6 * c + j] = __float2bfloat16(g[c] * e[j]);
-        for (int k = 36; k < 48; ++k) o[k] = __float2bfloat16(0.f);
     }
     const double s = block_sum_d(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -206,14 +213,24 @@ struct Assemble {
     bf16 *G;
 };
 
+__device__ __forceinline__ void add8(float *g, const bf16 *p, float w) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    const bf16 *h = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] += w * bf(h[k]);
+}
+
+// one thread per voxel and 8 channels (channel counts, strides and offsets
+// are multiples of 8, so every access is one 16-byte load or store)
 __global__ void k_assemble(Assemble a) {
     const long long V = (long long)a.n1 * a.n2 * a.n3;
-    const long long total = V * a.B * a.C;
+    const int C8 = a.C >> 3;
+    const long long total = V * a.B * C8;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % a.C);
-        const long long r = i / a.C;   // voxel (b, z, y, x) on this grid
-        float g = 0.f;
-        if (a.A) g += bf(a.A[r * a.a_stride + a.a_off + c]);
+        const long long r = i / C8;    // voxel (b, z, y, x) on this grid
+        const int c = (int)(i - r * C8) * 8;
+        float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (a.A) add8(g, a.A + r * a.a_stride + a.a_off + c, 1.f);
         if (a.U || a.P) {
             long long q = r;
             const int x = (int)(q % a.n3); q /= a.n3;
@@ -222,23 +239,36 @@ __global__ void k_assemble(Assemble a) {
             const int b = (int)(q / a.n1);
             if (a.U) {
                 const int f1 = 2 * a.n1, f2 = 2 * a.n2, f3 = 2 * a.n3;
-                float s = 0.f;
+                float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int dz = 0; dz < 2; ++dz)
                     for (int dy = 0; dy < 2; ++dy)
                         for (int dx = 0; dx < 2; ++dx) {
                             const long long fv = (((long long)b * f1 + 2 * z + dz) * f2 + 2 * y + dy) * f3 + 2 * x + dx;
-                            s += bf(a.U[fv * a.u_stride + a.u_off + c]);
+                            add8(s, a.U + fv * a.u_stride + a.u_off + c, 1.f);
                         }
-                g += s;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) g[k] += s[k];
             }
             if (a.P) {
                 const int h1 = a.n1 / 2, h2 = a.n2 / 2, h3 = a.n3 / 2;
                 const long long pv = (((long long)b * h1 + z / 2) * h2 + y / 2) * h3 + x / 2;
-                g += bf(a.P[pv * a.p_stride + c]) * 0.125f;
+                const uint4 pw = *reinterpret_cast<const uint4 *>(a.P + pv * a.p_stride + c);
+                const bf16 *ph = reinterpret_cast<const bf16 *>(&pw);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) g[k] += bf(ph[k]) * 0.125f;
             }
         }
-        if (a.Y && !(bf(a.Y[i]) > 0.f)) g = 0.f;
-        a.G[i] = __float2bfloat16(g);
+        if (a.Y) {
+            const uint4 yw = *reinterpret_cast<const uint4 *>(a.Y + r * a.C + c);
+            const bf16 *yh = reinterpret_cast<const bf16 *>(&yw);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (!(bf(yh[k]) > 0.f)) g[k] = 0.f;
+        }
+        __nv_bfloat162 o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = __floats2bfloat162_rn(g[2 * k], g[2 * k + 1]);
+        *reinterpret_cast<uint4 *>(a.G + r * a.C + c) = *reinterpret_cast<const uint4 *>(o);
     }
 }
 
@@ -260,12 +290,14 @@ __global__ void k_colsum(long long rows, int C, const bf16 *__restrict__ G, floa
     }
 }
 
+// one warp per column: lanes stride over the partials, then a warp sum
 __global__ void k_colsum_reduce(int nb, int C, int cout, const float *partials, float *out) {
-    const int c = threadIdx.x;
+    const int c = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
     if (c >= cout) return;
     float s = 0.f;
-    for (int b = 0; b < nb; ++b) s += partials[(long long)b * C + c];
-    out[c] = s;
+    for (int b = lane; b < nb; b += 32) s += partials[(long long)b * C + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = s;
 }
 
 // dW[t][co][ci] (logical sizes) = sum over splits of the padded partials
@@ -539,7 +571,9 @@ int assemble(hom_net *n, int l, int B, const int g[3], const bf16 *A, int a_stri
     a.P = P;
     a.p_stride = p_stride;
     a.G = n->G[l];
-    k_assemble<<<ew_blocks(level_vox(n, B, g, L.d.level) * L.cout_p), kEw, 0, n->stream>>>(a);
+    if ((a.C | a_stride | a_off | u_stride | u_off | p_stride) & 7)
+        return set_err(HOM_EINVAL, "channel layout not a multiple of 8");
+    k_assemble<<<ew_blocks(level_vox(n, B, g, L.d.level) * L.cout_p / 8), kEw, 0, n->stream>>>(a);
     ++n->launches;
     return HOM_OK;
 }
@@ -560,7 +594,7 @@ int layer_back(hom_net *n, int l, int B, const int g[3]) {
         w.S, L.cout_p, L.cin_s, L.d.cout, L.d.cin, n->partial, n->grads + L.off);
     const int nb = ew_blocks(vox);
     k_colsum<<<nb, kEw, kEw * sizeof(float), n->stream>>>(vox, L.cout_p, n->G[l], n->colpart);
-    k_colsum_reduce<<<1, 64, 0, n->stream>>>(nb, L.cout_p, L.d.cout, n->colpart,
+    k_colsum_reduce<<<(L.d.cout + 7) / 8, 256, 0, n->stream>>>(nb, L.cout_p, L.d.cout, n->colpart,
                                              n->grads + L.off + 27LL * L.d.cout * L.d.cin);
     n->launches += 4;
     if (l != E1A) {
