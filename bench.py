@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--rho", type=float, default=0.10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="replay the MINRES loop body from the host (same kernels; lets ncu list them)")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "modbfft", "batch", "config2", "asprinted"],
@@ -255,7 +257,7 @@ def run_ours(args):
     phi_dev = torch.from_numpy(phi).cuda()
     ctx = hom.hom_create(phi.shape, phi_dev, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
                          derivative=hom.HOM_DERIV_ROTATED, precision=hom.HOM_PREC_FP32_FIELDS,
-                         device_ptrs=True, stream=stream.cuda_stream, device=local)
+                         device_ptrs=True, stream=stream.cuda_stream, device=local, host_loop=args.host_loop)
 
     def barrier():
         if dist:
@@ -341,7 +343,8 @@ def run_ours(args):
                 "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic octet-truss cell (seeded generator)",
-                "config": dict(config(n, args.rho), parallelism=f"replicas{ws}"),
+                "config": dict(config(n, args.rho), parallelism=f"replicas{ws}",
+                               **({"loop": "host-replayed body"} if args.host_loop else {})),
                 "iterations_per_step": iters / args.steps,
                 "time_to_tol_ms": 1e3 * t_max / args.steps,
                 "true_residual": last["true_residual"], "sweeps": last["sweeps"],

@@ -95,7 +95,11 @@ typedef struct {
     double alpha;       /* MoDBFFT penalty alpha / E (0: 1e-4, section 4.2) */
     int autotune;       /* nonzero (and no explicit rows3/tile2/tile1): launch
                            shapes from hom_autotune for this grid and precision */
-    int reserved;
+    int host_loop;      /* nonzero: the host replays the captured loop body
+                           (six iterations per launch, a state read every
+                           four launches) instead of one device-side WHILE
+                           graph per sweep; the same kernels, for tools that
+                           cannot see kernels inside conditional graphs */
     double sweep_floor; /* FP32 fields: smallest relative residual reduction one
                            refinement sweep is asked for (0: 1e-6 for MINRES,
                            5e-7 for its first sweep from a zero start, 1e-3

@@ -104,6 +104,7 @@ struct hom_ctx {
     int *d_flag = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // graph is a device-side WHILE loop over the body
+    bool host_loop = false;          // asked for the host-replayed body
     int graph_iters = 6;
     long long graph_kernels = 0;
     long long launches = 0;
@@ -410,7 +411,7 @@ static int build_graph(hom_ctx *ctx, Engine<R> &E) {
     const long long before = ctx->launches;
     cudaGraph_t graph = nullptr;
     bool loops = false;
-    if (cudaGraphCreate(&graph, 0) == cudaSuccess) {
+    if (!ctx->host_loop && cudaGraphCreate(&graph, 0) == cudaSuccess) {
         cudaGraphConditionalHandle h;
         cudaGraphNodeParams np = {};
         np.type = cudaGraphNodeTypeConditional;
@@ -878,6 +879,7 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     ctx->shape[1] = o.tile2;
     ctx->shape[2] = o.tile1;
     ctx->staging = o.staging;
+    ctx->host_loop = o.host_loop != 0;
     ctx->solver = o.solver;
     ctx->alpha = (o.alpha > 0.0) ? o.alpha : 1e-4;
     ctx->stream = (cudaStream_t)o.stream;

@@ -40,7 +40,7 @@ class hom_options(ctypes.Structure):
                 ("device", ctypes.c_int), ("refine", ctypes.c_int),
                 ("rows3", ctypes.c_int), ("tile2", ctypes.c_int), ("tile1", ctypes.c_int),
                 ("staging", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("host_loop", ctypes.c_int),
                 ("sweep_floor", ctypes.c_double)]
 
 
@@ -161,7 +161,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
                precision=HOM_PREC_FP32_FIELDS, device_ptrs=False, stream=None,
                device=-1, refine=3, shape=(0, 0, 0), staging=0,
                solver=HOM_SOLVER_GALERKIN_MINRES, alpha=0.0, autotune=False,
-               sweep_floor=0.0) -> Context:
+               sweep_floor=0.0, host_loop=False) -> Context:
     lib = load_library()
     opt = hom_options()
     lib.hom_default_options(ctypes.byref(opt))
@@ -176,6 +176,7 @@ def hom_create(grid, phase, input_kind=HOM_INPUT_FRACTION_F32, E=1.0, nu=0.3,
     opt.alpha = float(alpha)
     opt.autotune = 1 if autotune else 0
     opt.sweep_floor = float(sweep_floor)
+    opt.host_loop = 1 if host_loop else 0
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
     rc = lib.hom_create(ctypes.byref(h), g, _ptr(phase), int(input_kind), float(E), float(nu),

@@ -76,3 +76,20 @@ def test_modbfft_homogeneous_cell(hom, prec):
         rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-8, max_it=100)
         assert rc == hom.HOM_OK and all(i["iterations"] == 0 for i in info)
         assert np.allclose(hom.hom_effective_stiffness(ctx), voigt_stiffness(E_M, NU_M), rtol=1e-9)
+
+
+def test_host_replayed_loop_matches_device_loop(hom):
+    """host_loop replays the same captured body from the host: the same
+    kernels in the same order give the same iterates, so iteration counts and
+    stresses agree exactly."""
+    phi, _ = ri.octet(32, 0.15)
+    E = np.eye(6)[[0, 3]]
+    out = []
+    for host_loop in (False, True):
+        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, host_loop=host_loop) as ctx:
+            rc, info = hom.hom_solve(ctx, E, tol=1e-6, max_it=5000)
+            assert rc == hom.HOM_OK
+            out.append(info)
+    for a, b in zip(*out):
+        assert a["iterations"] == b["iterations"]
+        assert np.array_equal(a["sigma_mean"], b["sigma_mean"])
