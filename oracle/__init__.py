@@ -76,6 +76,14 @@ def _load():
                                   ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
                                   dp, dp, dp, dp]
         lib.orc_solve.restype = ctypes.c_int
+        lib.orc_apply_mixed.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.orc_rhs_mixed.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.orc_solve_mixed.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                        ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.orc_solve_mixed.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_modb_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.orc_modb_rhs.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -246,6 +254,61 @@ def solve(phi, E, nu, deriv, Ebar_tensor, tol=1e-10, max_it=5000, history=False)
     if history:
         out["history"] = hist[: it + 1].copy()
     return out
+
+
+def apply_mixed(phi, E, nu, deriv, mask, eps_mandel) -> np.ndarray:
+    """A(eps) with the projector of eq. (galop) for the stress-controlled
+    Mandel components in `mask` (bit c = component c of 11, 22, 33, 23, 13, 12)."""
+    lib = _load()
+    p = _phi(phi)
+    e = np.ascontiguousarray(eps_mandel, dtype=np.float64).reshape((6,) + p.shape)
+    out = np.empty_like(e)
+    lib.orc_apply_mixed(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), int(mask), _dp(e), _dp(out))
+    return out
+
+
+def rhs_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor) -> np.ndarray:
+    """b of eq. (gallin) under mixed control: strain components outside
+    `mask` from Ebar, stress components in `mask` from Sbar (tensor
+    components; the other entries of each are ignored)."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    Sb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Sbar_tensor, dtype=np.float64)))
+    out = np.empty((6,) + p.shape)
+    lib.orc_rhs_mixed(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), int(mask), _dp(Eb), _dp(Sb),
+                      _dp(out))
+    return out
+
+
+def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, max_it=5000):
+    """Galerkin-MINRES solve under mixed macroscopic control (eq. galop,
+    eq. gallin): Mandel components in `mask` are stress-controlled (mean
+    stress Sbar), the others strain-controlled (mean strain Ebar), tensor
+    components in and out.
+
+    Returns dict with eps_tilde (6,N1,N2,N3 Mandel, including the mean of the
+    stress-controlled components), sigma_mean and eps_mean (tensor comps),
+    iterations, est_residual, true_residual."""
+    lib = _load()
+    p = _phi(phi)
+    Eb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+    Sb = np.ascontiguousarray(tensor_to_mandel(np.asarray(Sbar_tensor, dtype=np.float64)))
+    eps = np.zeros((6,) + p.shape)
+    sig = np.zeros(6)
+    em = np.zeros(6)
+    info = np.zeros(3)
+    hist = np.zeros(max_it + 1)
+    lib.orc_solve_mixed(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), int(mask), _dp(Eb), _dp(Sb),
+                        float(tol), int(max_it), _dp(eps), _dp(sig), _dp(em), _dp(info), _dp(hist))
+    return {
+        "eps_tilde": eps,
+        "sigma_mean": mandel_to_tensor(sig),
+        "eps_mean": mandel_to_tensor(em),
+        "iterations": int(info[0]),
+        "est_residual": float(info[1]),
+        "true_residual": float(info[2]),
+    }
 
 
 UNIT_CASES = np.eye(6)  # tensor components; shear cases have e_ab = e_ba = 1

@@ -279,6 +279,7 @@ typedef struct {
     const double *phi;     /* V values in [0,1] */
     double Cm[36];         /* Mandel stiffness of the lattice material */
     int deriv;             /* 0 continuous, 1 rotated */
+    int mask;              /* stress-controlled Mandel components KL (bit c) */
 } orc_problem;
 
 /* tau = C(x) : eps at every voxel (eps, tau: 6 x V Mandel). If eps_is_macro,
@@ -307,9 +308,15 @@ static void project_field(const orc_problem *P, cplx *tau, double *out) {
         int k[3] = {(int)(f / ((long)n2 * n3)), (int)((f / n3) % n2), (int)(f % n3)};
         double o[12], t[12], xi[6];
         int nyq = is_nyquist(k[0], n1) || is_nyquist(k[1], n2) || is_nyquist(k[2], n3);
-        if (nyq || (k[0] == 0 && k[1] == 0 && k[2] == 0)) {
-            /* eq. (galop): 0 at the Nyquist frequencies and, for strain-
-             * controlled components, at xi = 0 */
+        if (k[0] == 0 && k[1] == 0 && k[2] == 0) {
+            /* eq. (galop) at xi = 0: the symmetric identity on the stress-
+             * controlled components KL, 0 on the strain-controlled kl */
+            for (int c = 0; c < 6; ++c)
+                if (!((P->mask >> c) & 1)) tau[(long)c * V + f] = 0;
+            continue;
+        }
+        if (nyq) {
+            /* eq. (galop): 0 at the Nyquist frequencies */
             for (int c = 0; c < 6; ++c) tau[(long)c * V + f] = 0;
             continue;
         }
@@ -325,12 +332,14 @@ static void project_field(const orc_problem *P, cplx *tau, double *out) {
     for (long i = 0; i < 6 * V; ++i) out[i] = creal(tau[i]) / (double)V;
 }
 
-/* A(eps) = F^-1{ G : F{ C : eps } },  eq. (linearOp). */
-void orc_apply(const int n[3], const double *phi, double E, double nu, int deriv,
-               const double *eps, double *out) {
+/* A(eps) = F^-1{ G : F{ C : eps } },  eq. (linearOp), with the projector of
+ * eq. (galop) for the stress-controlled components in mask (bit c = Mandel
+ * component c; 0 = pure strain control). */
+void orc_apply_mixed(const int n[3], const double *phi, double E, double nu, int deriv, int mask,
+                     const double *eps, double *out) {
     orc_problem P;
     memcpy(P.n, n, sizeof P.n);
-    P.phi = phi; P.deriv = deriv;
+    P.phi = phi; P.deriv = deriv; P.mask = mask;
     orc_stiffness_mandel(E, nu, P.Cm);
     long V = (long)n[0] * n[1] * n[2];
     cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
@@ -339,26 +348,45 @@ void orc_apply(const int n[3], const double *phi, double E, double nu, int deriv
     free(tau);
 }
 
-/* b = -F^-1{ G : F{ C : Ebar } }  (strain control, sigma_bar = 0), eq. (gallin). */
-void orc_rhs(const int n[3], const double *phi, double E, double nu, int deriv,
-             const double Ebar[6], double *out) {
+void orc_apply(const int n[3], const double *phi, double E, double nu, int deriv,
+               const double *eps, double *out) {
+    orc_apply_mixed(n, phi, E, nu, deriv, 0, eps, out);
+}
+
+/* b = -F^-1{ G : F{ C : Ebar - sigma_bar } }, eq. (gallin): Ebar carries the
+ * prescribed strain components kl (its KL entries are ignored) and Sbar the
+ * prescribed stress components KL (its kl entries are ignored), both Mandel. */
+void orc_rhs_mixed(const int n[3], const double *phi, double E, double nu, int deriv, int mask,
+                   const double Ebar[6], const double Sbar[6], double *out) {
     orc_problem P;
     memcpy(P.n, n, sizeof P.n);
-    P.phi = phi; P.deriv = deriv;
+    P.phi = phi; P.deriv = deriv; P.mask = mask;
     orc_stiffness_mandel(E, nu, P.Cm);
     long V = (long)n[0] * n[1] * n[2];
+    double Ekl[6];
+    for (int c = 0; c < 6; ++c) Ekl[c] = ((mask >> c) & 1) ? 0.0 : Ebar[c];
     cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
-    constitutive(&P, Ebar, 1, tau);
+    constitutive(&P, Ekl, 1, tau);
+    for (int c = 0; c < 6; ++c)
+        if ((mask >> c) & 1)
+            for (long x = 0; x < V; ++x) tau[(long)c * V + x] -= Sbar[c];
     project_field(&P, tau, out);
     for (long i = 0; i < 6 * V; ++i) out[i] = -out[i];
     free(tau);
+}
+
+/* b for pure strain control (sigma_bar = 0). */
+void orc_rhs(const int n[3], const double *phi, double E, double nu, int deriv,
+             const double Ebar[6], double *out) {
+    const double zero[6] = {0, 0, 0, 0, 0, 0};
+    orc_rhs_mixed(n, phi, E, nu, deriv, 0, Ebar, zero, out);
 }
 
 /* Projection alone, F^-1 G F applied to a real 6 x V field (no material). */
 void orc_project(const int n[3], int deriv, const double *in, double *out) {
     orc_problem P;
     memcpy(P.n, n, sizeof P.n);
-    P.phi = NULL; P.deriv = deriv;
+    P.phi = NULL; P.deriv = deriv; P.mask = 0;
     long V = (long)n[0] * n[1] * n[2];
     cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
     for (long i = 0; i < 6 * V; ++i) tau[i] = in[i];
@@ -458,42 +486,53 @@ typedef struct {
     const double *phi;
     double E, nu;
     int deriv;
+    int mask;
 } apply_ctx;
 
 static void apply_cb(void *ctx, const double *x, double *y) {
     apply_ctx *a = (apply_ctx *)ctx;
-    orc_apply(a->n, a->phi, a->E, a->nu, a->deriv, x, y);
+    orc_apply_mixed(a->n, a->phi, a->E, a->nu, a->deriv, a->mask, x, y);
 }
 
-/* Solves A(eps_tilde) = b for one macro strain Ebar (Mandel), writes the
- * fluctuation eps_tilde (6 x V Mandel), the volume-averaged stress
- * <C : (Ebar + eps_tilde)> (Mandel, sig_mean[6]) and, in info[0..2], the
- * iteration count, the estimated and the true relative residual. */
-int orc_solve(const int n[3], const double *phi, double E, double nu, int deriv,
-              const double Ebar[6], double tol, int max_it,
-              double *eps_tilde, double sig_mean[6], double info[3], double *hist) {
+/* Solves A(eps_tilde) = b of eq. (gallin) under mixed control: the Mandel
+ * components in mask (bit c) are stress-controlled with prescribed mean
+ * stress Sbar[c], the others strain-controlled with prescribed mean strain
+ * Ebar[c] (mask = 0: pure strain control).  Writes the solution eps_tilde
+ * (6 x V Mandel; its mean carries the unknown mean strain of the stress-
+ * controlled components), the volume-averaged stress <C : (Ebar_kl +
+ * eps_tilde)> (sig_mean[6]) and strain Ebar_kl + <eps_tilde> (eps_mean[6],
+ * may be NULL), all Mandel, and, in info[0..2], the iteration count, the
+ * estimated and the true relative residual. */
+int orc_solve_mixed(const int n[3], const double *phi, double E, double nu, int deriv, int mask,
+                    const double Ebar[6], const double Sbar[6], double tol, int max_it,
+                    double *eps_tilde, double sig_mean[6], double eps_mean[6], double info[3], double *hist) {
     long V = (long)n[0] * n[1] * n[2];
     long N6 = 6 * V;
     double *b = (double *)malloc(sizeof(double) * N6);
     double *r = (double *)malloc(sizeof(double) * N6);
-    orc_rhs(n, phi, E, nu, deriv, Ebar, b);
-    apply_ctx ctx = {n, phi, E, nu, deriv};
+    double Ekl[6];
+    for (int c = 0; c < 6; ++c) Ekl[c] = ((mask >> c) & 1) ? 0.0 : Ebar[c];
+    orc_rhs_mixed(n, phi, E, nu, deriv, mask, Ebar, Sbar, b);
+    apply_ctx ctx = {n, phi, E, nu, deriv, mask};
     double Cm[36];
     orc_stiffness_mandel(E, nu, Cm);
-    /* ||C : Ebar|| over the grid, the scale of the right-hand side */
-    double ce2 = 0.0, phi2 = 0.0;
+    /* scale of the right-hand side: ||C : Ebar_kl|| over the grid plus
+     * ||sigma_bar_KL|| over the grid */
+    double ce2 = 0.0, phi2 = 0.0, s2 = 0.0;
     for (int i = 0; i < 6; ++i) {
         double s = 0;
-        for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * Ebar[j];
+        for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * Ekl[j];
         ce2 += s * s;
+        if ((mask >> i) & 1) s2 += Sbar[i] * Sbar[i];
     }
     for (long x = 0; x < V; ++x) phi2 += phi[x] * phi[x];
-    double ntau = sqrt(ce2 * phi2);
+    double ntau = sqrt(ce2 * phi2) + sqrt(s2 * (double)V);
     double est;
     int it;
     if (sqrt(dot(N6, b, b)) <= ORC_RHS_ZERO * ntau) {
-        /* b vanishes up to FFT round-off (e.g. a homogeneous cell, or a load
-         * the layout carries without any fluctuation): eps_tilde = 0. */
+        /* b vanishes up to FFT round-off (e.g. a homogeneous cell under strain
+         * control, or a load the layout carries without any fluctuation):
+         * eps_tilde = 0. */
         for (long i = 0; i < N6; ++i) { eps_tilde[i] = 0.0; b[i] = 0.0; }
         if (hist) hist[0] = 0.0;
         est = 0.0;
@@ -502,25 +541,38 @@ int orc_solve(const int n[3], const double *phi, double E, double nu, int deriv,
         it = orc_minres(N6, apply_cb, &ctx, b, eps_tilde, tol, max_it, &est, hist);
     }
     /* true residual ||A eps - b|| / ||b|| */
-    orc_apply(n, phi, E, nu, deriv, eps_tilde, r);
+    orc_apply_mixed(n, phi, E, nu, deriv, mask, eps_tilde, r);
     double nb = sqrt(dot(N6, b, b)), nr = 0;
     for (long i = 0; i < N6; ++i) { double d = r[i] - b[i]; nr += d * d; }
     nr = sqrt(nr);
     info[0] = it;
     info[1] = est;
     info[2] = (nb > 0) ? nr / nb : 0.0;
-    /* mean stress */
+    /* mean stress and mean strain */
     for (int i = 0; i < 6; ++i) sig_mean[i] = 0.0;
+    double em[6] = {0, 0, 0, 0, 0, 0};
     for (long x = 0; x < V; ++x) {
         for (int i = 0; i < 6; ++i) {
             double s = 0;
-            for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * (Ebar[j] + eps_tilde[(long)j * V + x]);
+            for (int j = 0; j < 6; ++j) s += Cm[i * 6 + j] * (Ekl[j] + eps_tilde[(long)j * V + x]);
             sig_mean[i] += phi[x] * s;
+            em[i] += eps_tilde[(long)i * V + x];
         }
     }
     for (int i = 0; i < 6; ++i) sig_mean[i] /= (double)V;
+    if (eps_mean)
+        for (int i = 0; i < 6; ++i) eps_mean[i] = Ekl[i] + em[i] / (double)V;
     free(b); free(r);
     return it;
+}
+
+/* Pure strain control: orc_solve_mixed with no stress-controlled component. */
+int orc_solve(const int n[3], const double *phi, double E, double nu, int deriv,
+              const double Ebar[6], double tol, int max_it,
+              double *eps_tilde, double sig_mean[6], double info[3], double *hist) {
+    const double zero[6] = {0, 0, 0, 0, 0, 0};
+    return orc_solve_mixed(n, phi, E, nu, deriv, 0, Ebar, zero, tol, max_it, eps_tilde, sig_mean, NULL, info,
+                           hist);
 }
 
 int orc_num_threads(void) {
