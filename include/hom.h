@@ -102,8 +102,10 @@ typedef struct {
                            cannot see kernels inside conditional graphs */
     double sweep_floor; /* FP32 fields: smallest relative residual reduction one
                            refinement sweep is asked for (0: 1e-6 for MINRES,
-                           5e-7 for its first sweep from a zero start, 1e-3
-                           for PCG); a sweep aims at half the remaining
+                           5e-7 for its first sweep from a zero start; under
+                           stress control 1e-4 for the first sweep and 1e-2
+                           for later ones; 1e-3 for PCG); a sweep aims at
+                           half the remaining
                            tolerance, and the FP64 true residual is recomputed
                            after every sweep */
 } hom_options;
@@ -117,6 +119,9 @@ typedef struct {
     double true_residual;  /* ||A(e~) - b|| / ||b|| evaluated in FP64, eq. (galres) */
     double sigma_mean[6];  /* volume-averaged stress, tensor components, same units as E */
     double time_ms;        /* device time of this case */
+    double eps_mean[6];    /* volume-averaged strain, tensor components: the macro
+                              strain, with the solved mean of the stress-controlled
+                              components of hom_solve_mixed */
 } hom_solve_info;
 
 /* Fill *opt with the defaults. */
@@ -164,10 +169,32 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
 int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol,
               int max_it, const void *warm_start, hom_solve_info *info);
 
+/* Galerkin-MINRES under mixed macroscopic control (section 2.1, eq. (galop)
+ * and eq. (gallin)): the Mandel components whose bit is set in stress_mask
+ * (bit 0..5 = 11, 22, 33, 23, 13, 12) are stress-controlled, the others
+ * strain-controlled.  The projector at xi = 0 is the identity on the stress-
+ * controlled components KL and zero on the strain-controlled kl, and the
+ * right-hand side is b = -G : F{C : E_bar - S_bar}; the solution's mean then
+ * carries the unknown mean strain of the KL components, reported in
+ * info[].eps_mean and included in hom_fields.
+ *   macro_strain  ncase x 6 tensor components: prescribed mean strain of the
+ *                 kl components (entries of KL components ignored).
+ *   macro_stress  ncase x 6 tensor components, same units as E: prescribed
+ *                 mean stress of the KL components (kl entries ignored).
+ *   stress_mask   0..63; 0 is pure strain control (as hom_solve); 63 with
+ *                 macro_stress = s e1 (x) e1 is uniaxial stress, whose mean
+ *                 strain gives E = s / e11 and nu = -e22 / e11 (section 4.3).
+ * tol, max_it, warm_start and info as for hom_solve (warm_start must be NULL
+ * unless stress_mask is 0).  Galerkin contexts only (HOM_EINVAL for MoDBFFT).
+ * Returns as hom_solve. */
+int hom_solve_mixed(hom_ctx *ctx, const double *macro_strain, const double *macro_stress, int stress_mask,
+                    int ncase, double tol, int max_it, const void *warm_start, hom_solve_info *info);
+
 /* 6x6 Voigt effective stiffness, row-major, sigma = C (e11,e22,e33,2e23,2e13,2e12),
- * same units as E, from the mean stresses of the last hom_solve.  That solve must
- * have had ncase >= 6 cases whose macro strains span all six directions;
- * otherwise HOM_EINVAL.  Section 4.3 extracts E and nu from such averages. */
+ * same units as E, fitted to the mean stresses and mean strains of the last
+ * hom_solve or hom_solve_mixed.  That solve must have had ncase >= 6 cases
+ * whose mean strains span all six directions; otherwise HOM_EINVAL.  Section
+ * 4.3 extracts E and nu from such averages. */
 int hom_effective_stiffness(hom_ctx *ctx, double C[36]);
 
 /* Total strain E_bar + e~ and stress C(x):(E_bar + e~) of case icase of the

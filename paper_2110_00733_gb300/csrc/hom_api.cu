@@ -34,6 +34,15 @@ constexpr double kSweepTarget = 0.5;
 // from the FP64 residual sooner than MINRES: shorter sweeps, restarted from
 // the FP64 true residual, keep it converging
 constexpr double kFp32CgSweepFloor = 1e-3;
+// Under stress control (hom_solve_mixed) the solution carries the mean strain
+// of a compliant lattice, large against the right-hand side, and an FP32
+// MINRES sweep on a cell with void loses track of its true residual below
+// about 1e-5 (its estimate keeps falling while the FP64 residual stalls):
+// the first FP32 sweep asks for a reduction of 1e-4, later sweeps, whose
+// right-hand side is the residual FP32 left behind, for 1e-2, and the FP64
+// true residual restarts each.
+constexpr double kFp32MixedSweepFloor = 1e-4;
+constexpr double kFp32MixedLaterSweepFloor = 1e-2;
 // a warm start whose FP32-estimated residual is below this gets the FP64 one
 constexpr double kWarmFp64Below = 1e-3;
 // relative size of ||b|| / ||C : E_bar|| below which the right-hand side is
@@ -92,7 +101,8 @@ struct hom_ctx {
     double2 *b64 = nullptr, *r64 = nullptr;   // FP64 right-hand side and residual spectra
     double2 *phihat = nullptr;                // FP64 DFT of phi (half spectrum, one component)
     std::vector<double2 *> x64;     // per-case solutions (spectral, FP64 master copy)
-    std::vector<double> macros;     // per-case macro strains (Mandel, as solved)
+    std::vector<double> macros;     // per-case prescribed macro strains (Mandel; 0 on stress-controlled components)
+    std::vector<double> eps_means;  // per-case mean strains (Mandel, including solved stress-controlled means)
     std::vector<double> sig_mean;   // per-case mean stress (tensor comps, units of E)
     int ncase = 0;
     double *partials = nullptr;
@@ -1160,6 +1170,22 @@ static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom
         inf->sigma_mean[c] = v;
         ctx->sig_mean[6 * icase + c] = v;
     }
+    // mean strain: the prescribed components, plus x^(0) / V (the solved mean)
+    // on the stress-controlled ones, which the projector keeps at xi = 0
+    double em[6];
+    for (int c = 0; c < 6; ++c) em[c] = m[c];
+    const int mask = ctx->e64.g.mask0;
+    if (mask && ctx->solver == HOM_SOLVER_GALERKIN_MINRES) {
+        double2 x0[6];
+        CU(cudaMemcpyAsync(x0, x, sizeof(x0), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int c = 0; c < 6; ++c)
+            if ((mask >> c) & 1) em[c] += x0[c].x / (double)ctx->V;
+    }
+    for (int c = 0; c < 6; ++c) {
+        ctx->eps_means[6 * icase + c] = em[c];
+        inf->eps_mean[c] = (c >= 3) ? em[c] / r2 : em[c];
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     inf->time_ms = ms;
@@ -1168,12 +1194,26 @@ static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom
     return status;
 }
 
-static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, int max_it, const void *warm,
-                      hom_solve_info *info) {
+// One load case.  sbar_t: prescribed mean stress (tensor components, same
+// units as E) of the stress-controlled components in ctx->e64.g.mask0, or
+// nullptr for pure strain control.
+static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double *sbar_t, double tol, int max_it,
+                      const void *warm, hom_solve_info *info) {
     const long long nc = 6 * ctx->S;   // complex values per spectral vector
     cudaStream_t s = ctx->stream;
-    double m[6];
+    const int mask = ctx->e64.g.mask0;
+    double m[6], sbar_v[6] = {0, 0, 0, 0, 0, 0};
     macro_to_mandel(mac_t, m);
+    if (mask) {
+        double sb[6];
+        macro_to_mandel(sbar_t, sb);
+        for (int c = 0; c < 6; ++c) {
+            if ((mask >> c) & 1) {
+                m[c] = 0.0;                                   // an unknown, not a load
+                sbar_v[c] = (double)ctx->V * sb[c] / ctx->E;  // F{sigma_bar} at xi = 0, units of E
+            }
+        }
+    }
     for (int c = 0; c < 6; ++c) ctx->macros[6 * icase + c] = m[c];
     double2 *x = ctx->x64[icase];
     hom_solve_info inf{};
@@ -1190,7 +1230,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         double tau[6];
         const double tr = m[0] + m[1] + m[2];
         for (int c = 0; c < 6; ++c) tau[c] = (c < 3 ? ctx->lam * tr : 0.0) + 2.0 * ctx->mu * m[c];
-        Launch<double>::rhs_phihat(ctx->e64.g, s, ctx->phihat, tau, ctx->b64);
+        Launch<double>::rhs_phihat(ctx->e64.g, s, ctx->phihat, tau, mask ? sbar_v : nullptr, ctx->b64);
         ctx->launches += 1;
     }
     double b2 = 0.0;
@@ -1204,7 +1244,10 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
         double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
         ce2 += sv * sv;
     }
-    const double ntau = std::sqrt(ce2 * ctx->phi2_sum);
+    // plus ||sigma_bar_KL|| over the grid for stress-controlled components
+    double s2 = 0.0;
+    for (int c = 0; c < 6; ++c) s2 += sbar_v[c] * sbar_v[c];
+    const double ntau = std::sqrt(ce2 * ctx->phi2_sum) + std::sqrt(s2 / (double)ctx->V);
     CU(cudaMemsetAsync(x, 0, sizeof(double2) * nc, s));
     int status = HOM_OK;
     if (!std::isfinite(bnorm)) {
@@ -1260,8 +1303,10 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
             // sweep never asks for less and the next sweep refines further
             double sweep_tol = (ctx->prec == HOM_PREC_FP32_FIELDS ? kSweepTarget : 1.0) * tol / tres;
             if (sweep_tol > 0.5) sweep_tol = 0.5;
-            const double floor = (sw == 0 && !warm && ctx->sweep_floor == kFp32SweepFloor)
-                                     ? kFp32FirstSweepFloor : ctx->sweep_floor;
+            double floor = (sw == 0 && !warm && ctx->sweep_floor == kFp32SweepFloor)
+                               ? kFp32FirstSweepFloor : ctx->sweep_floor;
+            if (mask && ctx->sweep_floor == kFp32SweepFloor)
+                floor = sw == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
             if (ctx->prec == HOM_PREC_FP32_FIELDS && sweep_tol < floor) sweep_tol = floor;
             int it = 0, st = 0;
             double est = 0.0;
@@ -1280,9 +1325,20 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
             inf.iterations += it;
             inf.est_residual = est * tres;     // relative to ||b||
             inf.sweeps = sw + 1;
+            const double prev = tres;
             rc = true_residual(ctx, x, bnorm, &tres);
             if (rc) return rc;
             if (st == HOM_ENAN) { status = HOM_ENAN; break; }
+            if (ctx->prec == HOM_PREC_FP32_FIELDS && !(tres < prev)) {
+                // an FP32 sweep past the accuracy FP32 fields can carry (seen
+                // under stress control): take it back and stop
+                spec_f2d_acc(nc, s, (const float2 *)ctx->xs, x, -1.0);
+                ctx->launches += 1;
+                rc = true_residual(ctx, x, bnorm, &tres);
+                if (rc) return rc;
+                status = HOM_NOT_CONVERGED;
+                break;
+            }
             if (st == HOM_NOT_CONVERGED && tres > tol) { status = HOM_NOT_CONVERGED; break; }
         }
         inf.true_residual = tres;
@@ -1291,13 +1347,22 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, double tol, 
     return finish_case(ctx, icase, m, x, &inf, status, info);
 }
 
-int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, int max_it, const void *warm_start,
-              hom_solve_info *info) {
-    if (!ctx || !macro_strain || ncase <= 0) return fail(ctx, HOM_EINVAL, "null argument or ncase <= 0");
-    if (!(tol > 0.0) || max_it < 0) return fail(ctx, HOM_EINVAL, "need tol > 0 and max_it >= 0");
-    for (int i = 0; i < 6 * ncase; ++i)
-        if (!std::isfinite(macro_strain[i])) return fail(ctx, HOM_ENAN, "macro strain not finite");
+// the projector's stress-controlled components at xi = 0; a change rebuilds
+// the captured solve graph, whose kernels take the geometry by value
+static void set_stress_mask(hom_ctx *ctx, int mask) {
+    if (ctx->e64.g.mask0 == mask && ctx->e32.g.mask0 == mask) return;
+    ctx->e64.g.mask0 = mask;
+    ctx->e32.g.mask0 = mask;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+}
+
+static int solve_cases(hom_ctx *ctx, const double *macro_strain, const double *macro_stress, int mask, int ncase,
+                       double tol, int max_it, const void *warm_start, hom_solve_info *info) {
     cudaSetDevice(ctx->device);
+    set_stress_mask(ctx, mask);
     while ((int)ctx->x64.size() < ncase) {
         double2 *p = nullptr;
         CU(cudaMalloc(&p, sizeof(double2) * 6 * ctx->S));
@@ -1305,10 +1370,12 @@ int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, i
     }
     ctx->ncase = 0;
     ctx->macros.assign(6 * ncase, 0.0);
+    ctx->eps_means.assign(6 * ncase, 0.0);
     ctx->sig_mean.assign(6 * ncase, 0.0);
     int worst = HOM_OK;
     for (int k = 0; k < ncase; ++k) {
-        int rc = solve_case(ctx, k, macro_strain + 6 * k, tol, max_it, warm_start, info ? info + k : nullptr);
+        int rc = solve_case(ctx, k, macro_strain + 6 * k, macro_stress ? macro_stress + 6 * k : nullptr, tol, max_it,
+                            warm_start, info ? info + k : nullptr);
         if (rc < 0) {
             if (info) info[k].status = rc;
             return rc;
@@ -1320,6 +1387,30 @@ int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, i
     return rc ? rc : worst;
 }
 
+int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol, int max_it, const void *warm_start,
+              hom_solve_info *info) {
+    if (!ctx || !macro_strain || ncase <= 0) return fail(ctx, HOM_EINVAL, "null argument or ncase <= 0");
+    if (!(tol > 0.0) || max_it < 0) return fail(ctx, HOM_EINVAL, "need tol > 0 and max_it >= 0");
+    for (int i = 0; i < 6 * ncase; ++i)
+        if (!std::isfinite(macro_strain[i])) return fail(ctx, HOM_ENAN, "macro strain not finite");
+    return solve_cases(ctx, macro_strain, nullptr, 0, ncase, tol, max_it, warm_start, info);
+}
+
+int hom_solve_mixed(hom_ctx *ctx, const double *macro_strain, const double *macro_stress, int stress_mask,
+                    int ncase, double tol, int max_it, const void *warm_start, hom_solve_info *info) {
+    if (!ctx || !macro_strain || !macro_stress || ncase <= 0)
+        return fail(ctx, HOM_EINVAL, "null argument or ncase <= 0");
+    if (!(tol > 0.0) || max_it < 0) return fail(ctx, HOM_EINVAL, "need tol > 0 and max_it >= 0");
+    if (stress_mask < 0 || stress_mask > 63) return fail(ctx, HOM_EINVAL, "stress_mask must be in 0..63");
+    if (ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
+        return fail(ctx, HOM_EINVAL, "mixed control is for the Galerkin solver");
+    if (stress_mask && warm_start) return fail(ctx, HOM_EINVAL, "warm starts need pure strain control");
+    for (int i = 0; i < 6 * ncase; ++i)
+        if (!std::isfinite(macro_strain[i]) || !std::isfinite(macro_stress[i]))
+            return fail(ctx, HOM_ENAN, "macro strain or stress not finite");
+    return solve_cases(ctx, macro_strain, macro_stress, stress_mask, ncase, tol, max_it, warm_start, info);
+}
+
 int hom_effective_stiffness(hom_ctx *ctx, double C[36]) {
     if (!ctx || !C) return fail(ctx, HOM_EINVAL, "null argument");
     const int nc = ctx->ncase;
@@ -1329,7 +1420,7 @@ int hom_effective_stiffness(hom_ctx *ctx, double C[36]) {
     const double r2 = std::sqrt(2.0);
     for (int k = 0; k < nc; ++k)
         for (int c = 0; c < 6; ++c) {
-            const double mm = ctx->macros[6 * k + c];
+            const double mm = ctx->eps_means[6 * k + c];
             G[c * nc + k] = (c < 3) ? mm : mm * r2;   // Mandel sqrt2 e -> engineering 2e
             Sg[c * nc + k] = ctx->sig_mean[6 * k + c];
         }

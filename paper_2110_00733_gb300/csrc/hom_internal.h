@@ -76,6 +76,7 @@ struct Geometry {
     size_t smem3, smem2, smem1;
     int fast[3];
     int nc;                 // complex components per frequency in the spectrum (6, or 10 for MoDBFFT)
+    int mask0;              // stress-controlled Mandel components (bit c): the projector keeps them at xi = 0
     // persistent TMA-staged n2 / n1 passes (FP32, power-of-two n <= 256):
     // enabled flag, persistent grid sizes, shared memory, host-side cache of
     // tensor maps (never dereferenced on the device) and the device word a
@@ -137,7 +138,10 @@ template <typename R> struct Launch {
     // the number of blocks (partials[c * nb + block])
     static int phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials);
     // b^ = -G (phi^ tau) for the constant tensor tau = C_m : E_bar (Mandel)
-    static void rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau, cpx<R> *out);
+    // sbar_v: V times the prescribed mean stress of the stress-controlled
+    // components (Mandel, units of E), added at xi = 0; nullptr for none
+    static void rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau,
+                           const double *sbar_v, cpx<R> *out);
     // out10 = (-phi^ tau, 0, 0, 0, 0): the MoDBFFT stress input of C : E_bar
     static void phihat_tau10(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau,
                              cpx<R> *out10);

@@ -116,11 +116,18 @@ __device__ __forceinline__ void gamma_project(cpx<R> *t, cpx<R> x0, cpx<R> x1, c
 // G at frequency (k1,k2,k3) on the 6 Mandel components at p[0..5] (stride 1)
 template <typename R>
 __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int k3, cpx<R> *t) {
-    // eq. (galop): zero at xi = 0 (strain control) and at every frequency
-    // with a Nyquist index
+    // eq. (galop): at xi = 0 the identity on the stress-controlled components
+    // (g.mask0) and zero on the strain-controlled ones; zero at every
+    // frequency with a Nyquist index
+    if (k1 == 0 && k2 == 0 && k3 == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (!((g.mask0 >> c) & 1)) t[c] = mk<R>(0, 0);
+        return;
+    }
     const bool nyq = ((g.n1 & 1) == 0 && 2 * k1 == g.n1) || ((g.n2 & 1) == 0 && 2 * k2 == g.n2) ||
                      ((g.n3 & 1) == 0 && 2 * k3 == g.n3);
-    if (nyq || (k1 == 0 && k2 == 0 && k3 == 0)) {
+    if (nyq) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) t[c] = mk<R>(0, 0);
         return;
@@ -647,7 +654,7 @@ __global__ void __launch_bounds__(kEwThreads) k_phi_dot(Geometry g, const cpx<R>
 // pass (tau: Mandel, units of E).
 template <typename R>
 __global__ void __launch_bounds__(kEwThreads) k_rhs_phihat(Geometry g, const cpx<R> *__restrict__ phihat, Mac6 tau,
-                                                           cpx<R> *__restrict__ out) {
+                                                           Mac6 sbar_v, cpx<R> *__restrict__ out) {
     for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < g.S; f += (long long)gridDim.x * blockDim.x) {
         const int k3 = (int)(f % g.h);
         const long long r = f / g.h;
@@ -656,6 +663,11 @@ __global__ void __launch_bounds__(kEwThreads) k_rhs_phihat(Geometry g, const cpx
         cpx<R> t[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) t[c] = mk<R>(-(R)tau.v[c] * ph.x, -(R)tau.v[c] * ph.y);
+        // F{sigma_bar} = V sigma_bar at xi = 0 only: b^ = -G (phi^ tau - F{sigma_bar})
+        if (f == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) t[c].x += (R)sbar_v.v[c];
+        }
         gamma_at<R>(g, k1, k2, k3, t);
 #pragma unroll
         for (int c = 0; c < 6; ++c) out[6 * f + c] = t[c];
@@ -892,10 +904,14 @@ int Launch<R>::phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, cons
 }
 
 template <typename R>
-void Launch<R>::rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau, cpx<R> *out) {
-    Mac6 m{};
-    for (int c = 0; c < 6; ++c) m.v[c] = tau[c];
-    k_rhs_phihat<R><<<ew_grid(g.S), kEwThreads, 0, st>>>(g, phihat, m, out);
+void Launch<R>::rhs_phihat(const Geometry &g, cudaStream_t st, const cpx<R> *phihat, const double *tau,
+                           const double *sbar_v, cpx<R> *out) {
+    Mac6 m{}, sv{};
+    for (int c = 0; c < 6; ++c) {
+        m.v[c] = tau[c];
+        sv.v[c] = sbar_v ? sbar_v[c] : 0.0;
+    }
+    k_rhs_phihat<R><<<ew_grid(g.S), kEwThreads, 0, st>>>(g, phihat, m, sv, out);
 }
 
 template <typename R>

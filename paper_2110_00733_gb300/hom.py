@@ -30,7 +30,7 @@ EXPORTED = [
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
-    "hom_solve_batch", "hom_autotune",
+    "hom_solve_batch", "hom_autotune", "hom_solve_mixed",
 ]
 
 
@@ -48,12 +48,14 @@ class hom_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
                 ("sweeps", ctypes.c_int), ("reserved", ctypes.c_int),
                 ("est_residual", ctypes.c_double), ("true_residual", ctypes.c_double),
-                ("sigma_mean", ctypes.c_double * 6), ("time_ms", ctypes.c_double)]
+                ("sigma_mean", ctypes.c_double * 6), ("time_ms", ctypes.c_double),
+                ("eps_mean", ctypes.c_double * 6)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "status": self.status, "sweeps": self.sweeps,
                 "est_residual": self.est_residual, "true_residual": self.true_residual,
-                "sigma_mean": np.array(self.sigma_mean[:]), "time_ms": self.time_ms}
+                "sigma_mean": np.array(self.sigma_mean[:]), "time_ms": self.time_ms,
+                "eps_mean": np.array(self.eps_mean[:])}
 
 
 class HomError(RuntimeError):
@@ -81,6 +83,8 @@ def load_library(path: str = LIB_PATH):
                                ctypes.POINTER(hom_options)]
     lib.hom_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
                               ctypes.POINTER(hom_solve_info)]
+    lib.hom_solve_mixed.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
+                                    ctypes.POINTER(hom_solve_info)]
     lib.hom_effective_stiffness.argtypes = [vp, dp]
     lib.hom_fields.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.hom_apply.argtypes = [vp, vp, vp]
@@ -195,6 +199,26 @@ def hom_solve(ctx: Context, macro_strain, tol=1e-6, max_it=1000, warm_start=None
     infos = (hom_solve_info * ncase)()
     rc = lib.hom_solve(ctx.handle, m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ncase,
                        float(tol), int(max_it), _ptr(warm_start), infos)
+    _check(ctx.handle, rc)
+    return rc, [i.as_dict() for i in infos]
+
+
+def hom_solve_mixed(ctx: Context, macro_strain, macro_stress, stress_mask, tol=1e-6, max_it=1000,
+                    warm_start=None):
+    """Mixed macroscopic control: Mandel components whose bit is set in
+    stress_mask (bit 0..5 = 11, 22, 33, 23, 13, 12) take their mean stress
+    from macro_stress, the others their mean strain from macro_strain (both
+    (ncase, 6) tensor components).  Returns (rc, [info dicts]); each info
+    carries sigma_mean and eps_mean."""
+    lib = load_library()
+    m = np.ascontiguousarray(np.asarray(macro_strain, dtype=np.float64).reshape(-1, 6))
+    sg = np.ascontiguousarray(np.asarray(macro_stress, dtype=np.float64).reshape(-1, 6))
+    assert m.shape == sg.shape
+    ncase = m.shape[0]
+    infos = (hom_solve_info * ncase)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.hom_solve_mixed(ctx.handle, m.ctypes.data_as(dp), sg.ctypes.data_as(dp), int(stress_mask), ncase,
+                             float(tol), int(max_it), _ptr(warm_start), infos)
     _check(ctx.handle, rc)
     return rc, [i.as_dict() for i in infos]
 
