@@ -72,7 +72,7 @@ def parse():
                     help="replay the MINRES loop body from the host (same kernels; lets ncu list them)")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "modbfft", "batch", "config2", "asprinted"],
+                    choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
                          "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
@@ -424,6 +424,65 @@ def run_modbfft(args):
     return 0
 
 
+def run_uniaxial(args):
+    """Mixed macroscopic control on the headline cell (eq. galop): uniaxial
+    stress (all six components stress-controlled, s11 = 1 MPa) gives E and nu
+    from one solve; they are compared with E = 1/S11 and nu = -S21/S11 of the
+    compliance from six strain-controlled solves, and with a prescribed e11
+    whose lateral faces are stress-free.  FP32 fields, tol 1e-6; the
+    uniaxial-stress solve also runs once with FP64 fields."""
+    import numpy as np
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n = args.n
+    phi, _ = ri.octet(n, args.rho)
+    s11 = 1.0e6
+    Sbar = np.array([[s11, 0, 0, 0, 0, 0]])
+    zero = np.zeros((1, 6))
+    out = {"metric": "mixed_control_voxel_iters_per_s", "unit": "voxel-iter/s",
+           "workload": f"uniaxial_stress_octet_{n}^3_rho{args.rho:.2f}_tol1e-6"}
+    with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M) as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=MAX_IT)
+        S = np.linalg.inv(hom.hom_effective_stiffness(ctx))
+        out["strain_control"] = {"E_pa": 1.0 / S[0, 0], "nu": -S[1, 0] / S[0, 0],
+                                 "iterations": [i["iterations"] for i in info]}
+        for _ in range(args.warmup):
+            hom.hom_solve_mixed(ctx, zero, Sbar, 63, tol=TOL, max_it=MAX_IT)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = 0
+        for _ in range(args.steps):
+            rc, info = hom.hom_solve_mixed(ctx, zero, Sbar, 63, tol=TOL, max_it=MAX_IT)
+            its += info[0]["iterations"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e = info[0]["eps_mean"]
+        out.update({"value": n ** 3 * its / dt, "ms_per_step": 1e3 * dt / args.steps, "rc": rc,
+                    "iterations_per_step": its / args.steps, "sweeps": info[0]["sweeps"],
+                    "true_residual": info[0]["true_residual"],
+                    "uniaxial_stress": {"E_pa": s11 / e[0], "nu": -e[1] / e[0],
+                                        "sigma_mean_pa": [float(v) for v in info[0]["sigma_mean"]]}})
+        rc2, info2 = hom.hom_solve_mixed(ctx, np.array([[1e-3, 0, 0, 0, 0, 0]]), zero, 62, tol=TOL, max_it=MAX_IT)
+        e2 = info2[0]["eps_mean"]
+        out["free_lateral_faces"] = {"E_pa": info2[0]["sigma_mean"][0] / e2[0], "nu": -e2[1] / e2[0],
+                                     "iterations": info2[0]["iterations"], "rc": rc2}
+    with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+                        precision=hom.HOM_PREC_FP64) as ctx:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc3, info3 = hom.hom_solve_mixed(ctx, zero, Sbar, 63, tol=TOL, max_it=MAX_IT)
+        torch.cuda.synchronize()
+        e3 = info3[0]["eps_mean"]
+        out["uniaxial_stress_fp64"] = {"E_pa": s11 / e3[0], "nu": -e3[1] / e3[0],
+                                       "iterations": info3[0]["iterations"], "rc": rc3,
+                                       "ms": 1e3 * (time.perf_counter() - t0)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_config2(args):
     """Octet cells at 128^3, densities {3, 7, 15, 30} %, both solvers
     (Galerkin-MINRES with rotated frequencies; MoDBFFT-PCG with continuous
@@ -503,6 +562,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "uniaxial":
+        return run_uniaxial(args)
     if args.workload == "modbfft":
         return run_modbfft(args)
     return run_ours(args)
