@@ -81,8 +81,11 @@ def _load():
         lib.orc_rhs_mixed.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.orc_solve_mixed.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double,
-                                        ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.orc_cg.argtypes = [ctypes.c_long, lib.MATVEC, ctypes.c_void_p,
+                               dp, dp, ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.orc_cg.restype = ctypes.c_int
         lib.orc_solve_mixed.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_modb_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -281,11 +284,31 @@ def rhs_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor) -> np.ndarray:
     return out
 
 
-def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, max_it=5000):
-    """Galerkin-MINRES solve under mixed macroscopic control (eq. galop,
-    eq. gallin): Mandel components in `mask` are stress-controlled (mean
-    stress Sbar), the others strain-controlled (mean strain Ebar), tensor
-    components in and out.
+def cg(matvec, b, tol=1e-12, max_it=1000):
+    """Oracle conjugate gradients on a Python matvec (used to pin it)."""
+    lib = _load()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = b.size
+    x = np.zeros(n)
+    hist = np.zeros(max_it + 1)
+    rel = ctypes.c_double(0.0)
+
+    def cb(_ctx, xp, yp):
+        xv = np.ctypeslib.as_array(xp, shape=(n,))
+        yv = np.ctypeslib.as_array(yp, shape=(n,))
+        yv[:] = matvec(xv.copy())
+
+    cfun = lib.MATVEC(cb)
+    it = lib.orc_cg(n, cfun, None, _dp(b), _dp(x), float(tol), int(max_it), ctypes.byref(rel), _dp(hist))
+    return x, int(it), float(rel.value), hist[: it + 1]
+
+
+def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, max_it=5000, method="minres",
+                history=False):
+    """Galerkin solve under mixed macroscopic control (eq. galop, eq.
+    gallin) by MINRES or CG: Mandel components in `mask` are stress-
+    controlled (mean stress Sbar), the others strain-controlled (mean strain
+    Ebar), tensor components in and out.
 
     Returns dict with eps_tilde (6,N1,N2,N3 Mandel, including the mean of the
     stress-controlled components), sigma_mean and eps_mean (tensor comps),
@@ -299,9 +322,11 @@ def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, ma
     em = np.zeros(6)
     info = np.zeros(3)
     hist = np.zeros(max_it + 1)
+    assert method in ("minres", "cg")
     lib.orc_solve_mixed(_ip(p.shape), _dp(p), float(E), float(nu), int(deriv), int(mask), _dp(Eb), _dp(Sb),
-                        float(tol), int(max_it), _dp(eps), _dp(sig), _dp(em), _dp(info), _dp(hist))
-    return {
+                        1 if method == "cg" else 0, float(tol), int(max_it), _dp(eps), _dp(sig), _dp(em),
+                        _dp(info), _dp(hist))
+    out = {
         "eps_tilde": eps,
         "sigma_mean": mandel_to_tensor(sig),
         "eps_mean": mandel_to_tensor(em),
@@ -309,6 +334,9 @@ def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, ma
         "est_residual": float(info[1]),
         "true_residual": float(info[2]),
     }
+    if history:
+        out["history"] = hist[: out["iterations"] + 1].copy()
+    return out
 
 
 UNIT_CASES = np.eye(6)  # tensor components; shear cases have e_ab = e_ba = 1

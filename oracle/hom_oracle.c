@@ -474,6 +474,47 @@ int orc_minres(long n, orc_matvec_fn A, void *ctx, const double *b, double *x,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Conjugate gradients (Hestenes & Stiefel 1952), the solver the paper names */
+/* for the Galerkin system of a cell without void (section 2.1) and shows to */
+/* fail once empty voxels make the system singular.  x0 = 0; stops when the  */
+/* recursively updated relative residual ||r_k|| / ||b|| <= tol.             */
+/* ------------------------------------------------------------------------ */
+int orc_cg(long n, orc_matvec_fn A, void *ctx, const double *b, double *x,
+           double tol, int max_it, double *rel_res, double *hist) {
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    for (long i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; p[i] = b[i]; }
+    double rho = dot(n, r, r);
+    const double nb = sqrt(rho);
+    if (hist) hist[0] = 1.0;
+    *rel_res = 1.0;
+    int k = 0;
+    if (nb == 0.0) {
+        *rel_res = 0.0;
+        free(r); free(p); free(q);
+        return 0;
+    }
+    while (k < max_it) {
+        ++k;
+        A(ctx, p, q);                                          /* q = A p_k */
+        const double pq = dot(n, p, q);
+        if (!(pq > 0.0)) break;                                /* not positive definite on p */
+        const double alpha = rho / pq;
+        for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        const double rho_next = dot(n, r, r);
+        *rel_res = sqrt(rho_next) / nb;
+        if (hist) hist[k] = *rel_res;
+        if (*rel_res <= tol) break;
+        const double beta = rho_next / rho;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rho = rho_next;
+    }
+    free(r); free(p); free(q);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Full solve: b, MINRES, true residual (eq. galres), mean stress.           */
 /* ------------------------------------------------------------------------ */
 
@@ -497,14 +538,14 @@ static void apply_cb(void *ctx, const double *x, double *y) {
 /* Solves A(eps_tilde) = b of eq. (gallin) under mixed control: the Mandel
  * components in mask (bit c) are stress-controlled with prescribed mean
  * stress Sbar[c], the others strain-controlled with prescribed mean strain
- * Ebar[c] (mask = 0: pure strain control).  Writes the solution eps_tilde
+ * Ebar[c] (mask = 0: pure strain control); method 0 MINRES, 1 CG.  Writes the solution eps_tilde
  * (6 x V Mandel; its mean carries the unknown mean strain of the stress-
  * controlled components), the volume-averaged stress <C : (Ebar_kl +
  * eps_tilde)> (sig_mean[6]) and strain Ebar_kl + <eps_tilde> (eps_mean[6],
  * may be NULL), all Mandel, and, in info[0..2], the iteration count, the
  * estimated and the true relative residual. */
 int orc_solve_mixed(const int n[3], const double *phi, double E, double nu, int deriv, int mask,
-                    const double Ebar[6], const double Sbar[6], double tol, int max_it,
+                    const double Ebar[6], const double Sbar[6], int method, double tol, int max_it,
                     double *eps_tilde, double sig_mean[6], double eps_mean[6], double info[3], double *hist) {
     long V = (long)n[0] * n[1] * n[2];
     long N6 = 6 * V;
@@ -538,7 +579,8 @@ int orc_solve_mixed(const int n[3], const double *phi, double E, double nu, int 
         est = 0.0;
         it = 0;
     } else {
-        it = orc_minres(N6, apply_cb, &ctx, b, eps_tilde, tol, max_it, &est, hist);
+        it = (method == 1) ? orc_cg(N6, apply_cb, &ctx, b, eps_tilde, tol, max_it, &est, hist)
+                           : orc_minres(N6, apply_cb, &ctx, b, eps_tilde, tol, max_it, &est, hist);
     }
     /* true residual ||A eps - b|| / ||b|| */
     orc_apply_mixed(n, phi, E, nu, deriv, mask, eps_tilde, r);
@@ -571,7 +613,7 @@ int orc_solve(const int n[3], const double *phi, double E, double nu, int deriv,
               const double Ebar[6], double tol, int max_it,
               double *eps_tilde, double sig_mean[6], double info[3], double *hist) {
     const double zero[6] = {0, 0, 0, 0, 0, 0};
-    return orc_solve_mixed(n, phi, E, nu, deriv, 0, Ebar, zero, tol, max_it, eps_tilde, sig_mean, NULL, info,
+    return orc_solve_mixed(n, phi, E, nu, deriv, 0, Ebar, zero, 0, tol, max_it, eps_tilde, sig_mean, NULL, info,
                            hist);
 }
 
