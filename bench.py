@@ -21,6 +21,7 @@ repository) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import statistics
@@ -72,7 +73,7 @@ def parse():
                     help="replay the MINRES loop body from the host (same kernels; lets ncu list them)")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial"],
+                    choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
                          "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
@@ -483,6 +484,44 @@ def run_uniaxial(args):
     return 0
 
 
+def run_ablation(args):
+    """Krylov solver and frequency scheme (section 2.1): MINRES and CG on the
+    Galerkin system, rotated and continuous frequencies, on octet cells with
+    void and with the void filled by a 5 % phase; iterations and time to
+    1e-6, max_it 5000, FP32 fields, and FP64 fields as well on the cells with
+    void."""
+    import numpy as np
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n = args.n if args.n != 256 else 128
+    for rho in (0.10, 0.20):
+        phi, _ = ri.octet(n, rho)
+        for fill in (0.0, 0.05):
+            ph = (fill + (1.0 - fill) * phi).astype(np.float32)
+            rows = {}
+            precs = [("fp32", hom.HOM_PREC_FP32_FIELDS)] + ([("fp64", hom.HOM_PREC_FP64)] if fill == 0.0 else [])
+            for (pname, prec), (deriv, dname), (solver, sname) in itertools.product(
+                    precs, ((hom.HOM_DERIV_ROTATED, "rotated"), (hom.HOM_DERIV_CONTINUOUS, "continuous")),
+                    ((hom.HOM_SOLVER_GALERKIN_MINRES, "minres"), (hom.HOM_SOLVER_GALERKIN_CG, "cg"))):
+                with hom.hom_create(ph.shape, ph, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, derivative=deriv,
+                                    solver=solver, precision=prec) as ctx:
+                    hom.hom_solve(ctx, MACRO, tol=TOL, max_it=200)          # graph capture, warm-up
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    rc, info = hom.hom_solve(ctx, MACRO, tol=TOL, max_it=5000)
+                    torch.cuda.synchronize()
+                    rows[f"{sname}_{dname}_{pname}"] = {
+                        "rc": rc, "iterations": info[0]["iterations"], "sweeps": info[0]["sweeps"],
+                        "true_residual": info[0]["true_residual"], "ms": 1e3 * (time.perf_counter() - t0),
+                        "sigma11_pa": float(info[0]["sigma_mean"][0])}
+            print(json.dumps({"workload": f"ablation_octet_{n}^3_rho{rho:.2f}_fill{fill:.2f}_E11_tol1e-6", **rows}),
+                  flush=True)
+    return 0
+
+
 def run_config2(args):
     """Octet cells at 128^3, densities {3, 7, 15, 30} %, both solvers
     (Galerkin-MINRES with rotated frequencies; MoDBFFT-PCG with continuous
@@ -564,6 +603,8 @@ def main():
         return run_batch(args)
     if args.workload == "uniaxial":
         return run_uniaxial(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     if args.workload == "modbfft":
         return run_modbfft(args)
     return run_ours(args)

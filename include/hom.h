@@ -74,7 +74,12 @@ enum { HOM_SMOOTH_NONE = 0 };       /* phi used as given (plain or Voigt-smoothe
 enum { HOM_DERIV_CONTINUOUS = 0,    /* xi_p = i q_p N_p, eq. (freq) */
        HOM_DERIV_ROTATED = 1 };     /* rotated forward difference, eq. (freqrot) */
 enum { HOM_SOLVER_GALERKIN_MINRES = 0,   /* section 2.1 */
-       HOM_SOLVER_MODBFFT_CG = 1 };      /* section 2.2: penalised displacement FFT, PCG */
+       HOM_SOLVER_MODBFFT_CG = 1,        /* section 2.2: penalised displacement FFT, PCG */
+       HOM_SOLVER_GALERKIN_CG = 2 };     /* section 2.1: CG on the Galerkin system, the
+                                            solver the paper names for cells without void
+                                            and reports failing with empty voxels; kept for
+                                            that comparison (same operator, refinement
+                                            sweeps and outputs as MINRES) */
 enum { HOM_PREC_FP32_FIELDS = 0,    /* FP32 fields and FFTs, FP64 Krylov scalars */
        HOM_PREC_FP64 = 1 };         /* FP64 everywhere */
 

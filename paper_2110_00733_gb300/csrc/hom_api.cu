@@ -14,6 +14,7 @@
 
 #include "../../include/hom.h"
 #include "hom_internal.h"
+#include "hom_cg.h"
 
 using namespace hom;
 
@@ -667,6 +668,92 @@ static int run_cg(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters
     return HOM_OK;
 }
 
+// Galerkin CG (section 2.1): graph_iters iterations per captured graph,
+// replayed by the host.  Buffers: x = xs, r = vbuf[0], p = vbuf[1],
+// q = A^ p = vbuf[2]; the scalars are the CgState kernels (no preconditioner).
+template <typename R>
+static int build_gcg_graph(hom_ctx *ctx, Engine<R> &E) {
+    if (ctx->cg_graph) return HOM_OK;
+    cpx<R> *x = (cpx<R> *)ctx->xs, *r = (cpx<R> *)ctx->vbuf[0], *p = (cpx<R> *)ctx->vbuf[1];
+    cpx<R> *q = (cpx<R> *)ctx->vbuf[2];
+    const long long n = 6 * ctx->S;
+    const int np1 = Launch<R>::x1_grid(E.g), npc = gcg_blocks(n);
+    const MinresState *flags = reinterpret_cast<const MinresState *>(ctx->d_cg);
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = ctx->launches;
+    for (int it = 0; it < ctx->graph_iters; ++it) {
+        op_spec<R>(ctx, E, p, q, true, ctx->partials, flags);   // q = A^ p, partial <p, q>
+        scalar_cg_alpha(ctx->stream, ctx->d_cg, ctx->partials, np1);
+        gcg_xr<R>(n, E.g.h, E.g.n3, ctx->stream, p, q, x, r, ctx->d_cg, ctx->partials);
+        scalar_cg_beta(ctx->stream, ctx->d_cg, ctx->partials, npc);
+        gcg_p<R>(n, ctx->stream, r, p, ctx->d_cg);
+        ctx->launches += 4;
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    ctx->cg_graph_kernels = ctx->launches - before;
+    ctx->launches = before;
+    e = cudaGraphInstantiate(&ctx->cg_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HOM_OK;
+}
+
+// CG on A^ x = rhs from x = 0; stops at ||r_k|| / ||r_0|| <= tol (recursive
+// residual) or max_it
+template <typename R>
+static int run_gcg(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters, double *est, int *status) {
+    const long long n = 6 * ctx->S, nr = 2 * n;
+    cudaStream_t s = ctx->stream;
+    int rc = build_gcg_graph<R>(ctx, E);
+    if (rc) return rc;
+    cpx<R> *x = (cpx<R> *)ctx->xs, *r = (cpx<R> *)ctx->vbuf[0], *p = (cpx<R> *)ctx->vbuf[1];
+    cpx<R> *q = (cpx<R> *)ctx->vbuf[2];
+    CU(cudaMemsetAsync(x, 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(p, 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(q, 0, sizeof(R) * nr, s));
+    CU(cudaMemcpyAsync(r, ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
+    // ||r_0||^2 through one step of length 0, then p_0 = r_0 (b = 0)
+    memset(ctx->h_cg, 0, sizeof(CgState));
+    CU(cudaMemcpyAsync(ctx->d_cg, ctx->h_cg, sizeof(CgState), cudaMemcpyHostToDevice, s));
+    gcg_xr<R>(n, E.g.h, E.g.n3, s, p, q, x, r, ctx->d_cg, ctx->partials);
+    scalar_cg_start(s, ctx->d_cg, ctx->partials, gcg_blocks(n), tol, max_it);
+    gcg_p<R>(n, s, r, p, ctx->d_cg);
+    ctx->launches += 3;
+    CU(cudaMemcpyAsync(ctx->h_cg, ctx->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (ctx->h_cg->done) {
+        *iters = 0;
+        *est = 0.0;
+        *status = ctx->h_cg->status == -5 ? HOM_ENAN : HOM_OK;
+        return HOM_OK;
+    }
+    const int per_check = 4;
+    int replays = 0;
+    const int max_replays = (max_it + ctx->graph_iters - 1) / ctx->graph_iters + 1;
+    while (true) {
+        for (int k = 0; k < per_check && replays < max_replays; ++k, ++replays) {
+            CU(cudaGraphLaunch(ctx->cg_graph, s));
+            ctx->launches += ctx->cg_graph_kernels;
+        }
+        CU(cudaMemcpyAsync(ctx->h_cg, ctx->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (ctx->h_cg->done || replays >= max_replays) break;
+    }
+    *iters = ctx->h_cg->k;
+    *est = ctx->h_cg->est;
+    *status = ctx->h_cg->status == -5 ? HOM_ENAN : (ctx->h_cg->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
+    return HOM_OK;
+}
+
+// the Krylov solver of a Galerkin context
+template <typename R>
+static int run_krylov(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *iters, double *est, int *status) {
+    return ctx->solver == HOM_SOLVER_GALERKIN_CG ? run_gcg<R>(ctx, E, tol, max_it, iters, est, status)
+                                                 : run_minres<R>(ctx, E, tol, max_it, iters, est, status);
+}
+
 static void macro_to_mandel(const double *t, double *m) {
     const double r2 = std::sqrt(2.0);
     for (int c = 0; c < 6; ++c) m[c] = (c < 3) ? t[c] : t[c] * r2;
@@ -777,6 +864,8 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
             rc = engine_init_modb<float>(ctx, ctx->e32);
             if (rc) return rc;
         }
+    }
+    if (ctx->solver != HOM_SOLVER_GALERKIN_MINRES) {
         CU(cudaMalloc(&ctx->d_cg, sizeof(CgState)));
         CU(cudaMallocHost(&ctx->h_cg, sizeof(CgState)));
     }
@@ -865,7 +954,8 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
             o.tile1 = shp[2];
         }
     }
-    if (o.solver != HOM_SOLVER_GALERKIN_MINRES && o.solver != HOM_SOLVER_MODBFFT_CG)
+    if (o.solver != HOM_SOLVER_GALERKIN_MINRES && o.solver != HOM_SOLVER_MODBFFT_CG &&
+        o.solver != HOM_SOLVER_GALERKIN_CG)
         return fail(nullptr, HOM_EINVAL, "bad solver");
     if (!(o.alpha >= 0.0) || !std::isfinite(o.alpha)) return fail(nullptr, HOM_EINVAL, "bad alpha");
     if (o.precision != HOM_PREC_FP32_FIELDS && o.precision != HOM_PREC_FP64)
@@ -1137,7 +1227,7 @@ static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom
     cudaStream_t s = ctx->stream;
     const double r2 = std::sqrt(2.0);
     double sig[6];
-    if (ctx->solver == HOM_SOLVER_GALERKIN_MINRES) {
+    if (ctx->solver != HOM_SOLVER_MODBFFT_CG) {
         // <sigma> = phibar C_m : E_bar + C_m : <phi eps~>, with <phi eps~> by
         // Parseval from phi^ and the projected spectrum: one point-wise pass
         const int nb = Launch<double>::phi_dot(ctx->e64.g, s, x, ctx->phihat, ctx->partials);
@@ -1175,7 +1265,7 @@ static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom
     double em[6];
     for (int c = 0; c < 6; ++c) em[c] = m[c];
     const int mask = ctx->e64.g.mask0;
-    if (mask && ctx->solver == HOM_SOLVER_GALERKIN_MINRES) {
+    if (mask && ctx->solver != HOM_SOLVER_MODBFFT_CG) {
         double2 x0[6];
         CU(cudaMemcpyAsync(x0, x, sizeof(x0), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
@@ -1312,12 +1402,12 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
             double est = 0.0;
             if (ctx->prec == HOM_PREC_FP64) {
                 CU(cudaMemcpyAsync(ctx->rhs, ctx->r64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
-                rc = run_minres<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
+                rc = run_krylov<double>(ctx, ctx->e64, sweep_tol, max_it, &it, &est, &st);
                 if (rc) return rc;
                 Launch<double>::axpby(2 * nc, s, 1.0, (const double *)ctx->xs, 1.0, (double *)x);
             } else {
                 spec_d2f(nc, s, ctx->r64, (float2 *)ctx->rhs);
-                rc = run_minres<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
+                rc = run_krylov<float>(ctx, ctx->e32, sweep_tol, max_it, &it, &est, &st);
                 if (rc) return rc;
                 spec_f2d_acc(nc, s, (const float2 *)ctx->xs, x);
             }
@@ -1356,6 +1446,10 @@ static void set_stress_mask(hom_ctx *ctx, int mask) {
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
+    }
+    if (ctx->cg_graph && ctx->solver == HOM_SOLVER_GALERKIN_CG) {
+        cudaGraphExecDestroy(ctx->cg_graph);
+        ctx->cg_graph = nullptr;
     }
 }
 
@@ -1402,8 +1496,8 @@ int hom_solve_mixed(hom_ctx *ctx, const double *macro_strain, const double *macr
         return fail(ctx, HOM_EINVAL, "null argument or ncase <= 0");
     if (!(tol > 0.0) || max_it < 0) return fail(ctx, HOM_EINVAL, "need tol > 0 and max_it >= 0");
     if (stress_mask < 0 || stress_mask > 63) return fail(ctx, HOM_EINVAL, "stress_mask must be in 0..63");
-    if (ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
-        return fail(ctx, HOM_EINVAL, "mixed control is for the Galerkin solver");
+    if (ctx->solver == HOM_SOLVER_MODBFFT_CG)
+        return fail(ctx, HOM_EINVAL, "mixed control is for the Galerkin solvers");
     if (stress_mask && warm_start) return fail(ctx, HOM_EINVAL, "warm starts need pure strain control");
     for (int i = 0; i < 6 * ncase; ++i)
         if (!std::isfinite(macro_strain[i]) || !std::isfinite(macro_stress[i]))

@@ -21,7 +21,7 @@ HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ENOMEM, HOM_ECUDA, HOM_ENAN, HOM_ETIMEOUT
 HOM_INPUT_PHASE_U8, HOM_INPUT_FRACTION_F32, HOM_INPUT_FRACTION_F64 = 0, 1, 2
 HOM_SMOOTH_NONE = 0
 HOM_DERIV_CONTINUOUS, HOM_DERIV_ROTATED = 0, 1
-HOM_SOLVER_GALERKIN_MINRES, HOM_SOLVER_MODBFFT_CG = 0, 1
+HOM_SOLVER_GALERKIN_MINRES, HOM_SOLVER_MODBFFT_CG, HOM_SOLVER_GALERKIN_CG = 0, 1, 2
 HOM_PREC_FP32_FIELDS, HOM_PREC_FP64 = 0, 1
 
 # every symbol include/hom.h declares
