@@ -87,6 +87,7 @@ def _load():
                                dp, dp, ctypes.c_double, ctypes.c_int, dp, dp]
         lib.orc_cg.restype = ctypes.c_int
         lib.orc_solve_mixed.restype = ctypes.c_int
+        lib.orc_pfs.argtypes = [ip, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_modb_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.orc_modb_rhs.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -336,6 +337,19 @@ def solve_mixed(phi, E, nu, deriv, mask, Ebar_tensor, Sbar_tensor, tol=1e-10, ma
     }
     if history:
         out["history"] = hist[: out["iterations"] + 1].copy()
+    return out
+
+
+def pfs(omega_fine, ratio, ell, eps=1.0, threshold=0.05) -> np.ndarray:
+    """Phase-field smoothening (section 3.2, eq. phase3): the indicator
+    omega on the fine grid filtered by 1 / (1 + (ell^2/eps) |q|^2) (ell in
+    fine voxels), averaged over ratio^3 blocks, values below threshold set
+    to 0.  Returns the phase map on the simulation grid."""
+    lib = _load()
+    w = np.ascontiguousarray(omega_fine, dtype=np.float64)
+    assert w.ndim == 3 and all(n % ratio == 0 for n in w.shape)
+    out = np.empty(tuple(n // ratio for n in w.shape))
+    lib.orc_pfs(_ip(w.shape), _dp(w), int(ratio), float(ell), float(eps), float(threshold), _dp(out))
     return out
 
 

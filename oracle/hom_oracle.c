@@ -809,3 +809,45 @@ void orc_modb_fields(const int n[3], const double *phi, double E, double nu, con
     for (int i = 0; i < 6; ++i) sig_mean[i] /= (double)V;
     free(e6);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Phase-field smoothening (PFS, section 3.2).  The phase map minimises       */
+/* eq. (phase); its Euler-Lagrange equation (phase2) is solved in Fourier     */
+/* space, eq. (phase3): phi^(xi) = omega^(xi) / (1 + (l^2/eps) |xi|^2) with   */
+/* the continuous frequencies of eq. (freq) (xi = i q N / L, so xi . xi =     */
+/* -|q N / L|^2).  The indicator omega is given on a fine grid (ratio r times */
+/* the simulation grid along every axis); with voxel size d on the fine grid */
+/* and l in units of d, (l^2/eps) |xi|^2 = (l^2/eps) sum_p q_p^2 with         */
+/* q_p = 2 pi m_p / N_p, m_p the signed frequency index.  The fine phase map  */
+/* is averaged over r^3 blocks onto the simulation grid, and values below     */
+/* the threshold (5 % in the paper) are set to 0.                             */
+/* ------------------------------------------------------------------------ */
+void orc_pfs(const int nf[3], const double *omega, int ratio, double ell, double eps, double threshold,
+             double *phi_coarse) {
+    long Vf = (long)nf[0] * nf[1] * nf[2];
+    cplx *w = (cplx *)malloc(sizeof(cplx) * Vf);
+    for (long i = 0; i < Vf; ++i) w[i] = omega[i];
+    orc_fft3d(nf, (double *)w, -1);
+    const double c = ell * ell / eps;
+    for (long f = 0; f < Vf; ++f) {
+        int k[3] = {(int)(f / ((long)nf[1] * nf[2])), (int)((f / nf[2]) % nf[1]), (int)(f % nf[2])};
+        double q2 = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            double q = 2.0 * PI * (double)signed_index(k[p], nf[p]) / (double)nf[p];
+            q2 += q * q;
+        }
+        w[f] /= (1.0 + c * q2);
+    }
+    orc_fft3d(nf, (double *)w, +1);
+    const int nc[3] = {nf[0] / ratio, nf[1] / ratio, nf[2] / ratio};
+    const double inv = 1.0 / ((double)ratio * ratio * ratio * (double)Vf);
+    for (long i = 0; i < (long)nc[0] * nc[1] * nc[2]; ++i) phi_coarse[i] = 0.0;
+    for (long f = 0; f < Vf; ++f) {
+        int x[3] = {(int)(f / ((long)nf[1] * nf[2])), (int)((f / nf[2]) % nf[1]), (int)(f % nf[2])};
+        long cidx = ((long)(x[0] / ratio) * nc[1] + x[1] / ratio) * nc[2] + x[2] / ratio;
+        phi_coarse[cidx] += creal(w[f]) * inv;
+    }
+    for (long i = 0; i < (long)nc[0] * nc[1] * nc[2]; ++i)
+        if (phi_coarse[i] < threshold) phi_coarse[i] = 0.0;
+    free(w);
+}
