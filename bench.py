@@ -73,7 +73,8 @@ def parse():
                     help="replay the MINRES loop body from the host (same kernels; lets ncu list them)")
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation"],
+                    choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation",
+                             "smoothing"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
                          "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
@@ -522,6 +523,49 @@ def run_ablation(args):
     return 0
 
 
+def run_smoothing(args):
+    """Phase maps of section 3 on one octet (rho = 0.15, 128^3 simulation
+    grid): plain voxels (PV: the indicator at voxel centres), the Voigt rule
+    on a 4^3 sub-grid (VFG), Voigt analytic (VA), phase-field smoothening of
+    the indicator on the 2x finer grid with l = half a coarse voxel (PFS),
+    and PFS of the VA map (CS).  Each map gets one uniaxial-stress solve
+    (hom_solve_mixed, FP32 fields, tol 1e-6): E, nu, iterations, time."""
+    import numpy as np
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n, rho = 128, 0.15
+    vfg, r = ri.octet(n, rho)
+    d = ri.octet_center_distance(n).astype(np.float64)
+    maps = {"PV": (d < r).astype(np.float64), "VFG": vfg.astype(np.float64), "VA": ri.va_phase(r - d, 1.0 / n)}
+    df = ri.octet_center_distance(2 * n).astype(np.float64)
+    omega = (df < r).astype(np.uint8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    maps["PFS"] = hom.hom_pfs(omega, 2, 1.0, 1.0, 0.05)
+    torch.cuda.synchronize()
+    pfs_ms = 1e3 * (time.perf_counter() - t0)
+    maps["CS"] = hom.hom_pfs(maps["VA"], 1, 0.5, 1.0, 0.05)
+    out = {"workload": f"smoothing_octet_{n}^3_rho{rho:.2f}_uniaxial_stress_tol1e-6", "pfs_fine_grid": [2 * n] * 3,
+           "pfs_ms": pfs_ms}
+    Sbar = np.array([[1.0e6, 0, 0, 0, 0, 0]])
+    for name, phi in maps.items():
+        with hom.hom_create(phi.shape, np.ascontiguousarray(phi, dtype=np.float64), hom.HOM_INPUT_FRACTION_F64,
+                            E_M, NU_M) as ctx:
+            hom.hom_solve_mixed(ctx, np.zeros((1, 6)), Sbar, 63, tol=TOL, max_it=200)     # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = hom.hom_solve_mixed(ctx, np.zeros((1, 6)), Sbar, 63, tol=TOL, max_it=MAX_IT)
+            torch.cuda.synchronize()
+            e = info[0]["eps_mean"]
+            out[name] = {"mean_phi": float(phi.mean()), "E_pa": 1.0e6 / e[0], "nu": -e[1] / e[0], "rc": rc,
+                         "iterations": info[0]["iterations"], "ms": 1e3 * (time.perf_counter() - t0)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_config2(args):
     """Octet cells at 128^3, densities {3, 7, 15, 30} %, both solvers
     (Galerkin-MINRES with rotated frequencies; MoDBFFT-PCG with continuous
@@ -605,6 +649,8 @@ def main():
         return run_uniaxial(args)
     if args.workload == "ablation":
         return run_ablation(args)
+    if args.workload == "smoothing":
+        return run_smoothing(args)
     if args.workload == "modbfft":
         return run_modbfft(args)
     return run_ours(args)

@@ -70,7 +70,8 @@ enum {
 enum { HOM_INPUT_PHASE_U8 = 0,      /* uint8 phase id: 0 empty, nonzero solid */
        HOM_INPUT_FRACTION_F32 = 1,  /* float solid fraction phi in [0,1] */
        HOM_INPUT_FRACTION_F64 = 2 };/* double solid fraction phi in [0,1] */
-enum { HOM_SMOOTH_NONE = 0 };       /* phi used as given (plain or Voigt-smoothed) */
+enum { HOM_SMOOTH_NONE = 0 };       /* phi used as given (plain, Voigt-smoothed, or the
+                                       phase-field map of hom_pfs) */
 enum { HOM_DERIV_CONTINUOUS = 0,    /* xi_p = i q_p N_p, eq. (freq) */
        HOM_DERIV_ROTATED = 1 };     /* rotated forward difference, eq. (freqrot) */
 enum { HOM_SOLVER_GALERKIN_MINRES = 0,   /* section 2.1 */
@@ -173,6 +174,27 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
  * distinct threads (see hom_solve_batch). */
 int hom_solve(hom_ctx *ctx, const double *macro_strain, int ncase, double tol,
               int max_it, const void *warm_start, hom_solve_info *info);
+
+/* Phase-field smoothening (section 3.2): the phase map of eq. (phase), solved
+ * in Fourier space by eq. (phase3), phi^(xi) = omega^(xi) / (1 + (ell^2/eps)
+ * |xi|^2) with the continuous frequencies of eq. (freq), on a fine grid, then
+ * averaged over ratio^3 blocks onto the simulation grid fine / ratio, values
+ * below threshold set to 0 (the paper: ell = half a coarse voxel, eps = 1,
+ * threshold 0.05, ratio 2..20).
+ *   fine         fine grid, each size a multiple of ratio and supported by
+ *                hom_create.
+ *   omega        the indicator (or any phase map in [0, 1]) on the fine grid,
+ *                C order, of input_kind (HOM_INPUT_*); host memory, or device
+ *                memory if device_ptrs is nonzero.
+ *   ell          length in fine voxels (ratio / 2 for half a coarse voxel).
+ *   phi_out      (fine/ratio)^3 doubles, C order, host or device per
+ *                device_ptrs; pass it to hom_create as HOM_INPUT_FRACTION_F64.
+ * Runs on a temporary FP64 context of the fine grid (about 100 bytes per fine
+ * voxel of device memory while it runs).  Returns HOM_OK or a negative error;
+ * hom_last_error(NULL) has the message.  The mean of phi_out equals the mean
+ * of omega when threshold is 0 (the filter keeps xi = 0). */
+int hom_pfs(const int fine[3], const void *omega, int input_kind, int ratio, double ell, double eps,
+            double threshold, int device_ptrs, double *phi_out);
 
 /* Galerkin-MINRES under mixed macroscopic control (section 2.1, eq. (galop)
  * and eq. (gallin)): the Mandel components whose bit is set in stress_mask

@@ -819,8 +819,8 @@ void orc_modb_fields(const int n[3], const double *phi, double E, double nu, con
 /* the simulation grid along every axis); with voxel size d on the fine grid */
 /* and l in units of d, (l^2/eps) |xi|^2 = (l^2/eps) sum_p q_p^2 with         */
 /* q_p = 2 pi m_p / N_p, m_p the signed frequency index.  The fine phase map  */
-/* is averaged over r^3 blocks onto the simulation grid, and values below     */
-/* the threshold (5 % in the paper) are set to 0.                             */
+/* is averaged over r^3 blocks onto the simulation grid, values below the     */
+/* threshold (5 % in the paper) are set to 0, and round-off above 1 to 1.     */
 /* ------------------------------------------------------------------------ */
 void orc_pfs(const int nf[3], const double *omega, int ratio, double ell, double eps, double threshold,
              double *phi_coarse) {
@@ -847,7 +847,9 @@ void orc_pfs(const int nf[3], const double *omega, int ratio, double ell, double
         long cidx = ((long)(x[0] / ratio) * nc[1] + x[1] / ratio) * nc[2] + x[2] / ratio;
         phi_coarse[cidx] += creal(w[f]) * inv;
     }
-    for (long i = 0; i < (long)nc[0] * nc[1] * nc[2]; ++i)
+    for (long i = 0; i < (long)nc[0] * nc[1] * nc[2]; ++i) {
         if (phi_coarse[i] < threshold) phi_coarse[i] = 0.0;
+        if (phi_coarse[i] > 1.0) phi_coarse[i] = 1.0;   /* phi lies in [0, 1]; FFT round-off */
+    }
     free(w);
 }

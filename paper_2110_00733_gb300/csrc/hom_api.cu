@@ -15,6 +15,7 @@
 #include "../../include/hom.h"
 #include "hom_internal.h"
 #include "hom_cg.h"
+#include "hom_pfs.h"
 
 using namespace hom;
 
@@ -996,6 +997,47 @@ int hom_create(hom_ctx **out, const int grid[3], const void *phase, int input_ki
     }
     *out = ctx;
     return HOM_OK;
+}
+
+// Phase-field smoothening (section 3.2) on a temporary FP64 context of the
+// fine grid: its creation already holds phi^ = F{omega}; filter it (eq.
+// (phase3), continuous frequencies), transform back as component 0 of a
+// Mandel spectrum, and average r^3 blocks with the threshold.
+static int pfs_impl(hom_ctx *ctx, const int fine[3], int ratio, double ell, double eps, double threshold,
+                    double *phi_out) {
+    cudaStream_t s = ctx->stream;
+    pfs_filter(fine[0], fine[1], fine[2], ell * ell / eps, ctx->phihat, s);
+    CU(cudaMemsetAsync(ctx->b64, 0, sizeof(double2) * 6 * ctx->S, s));
+    CU(cudaMemcpy2DAsync(ctx->b64, 6 * sizeof(double2), ctx->phihat, sizeof(double2), sizeof(double2), ctx->S,
+                         cudaMemcpyDeviceToDevice, s));
+    spec_to_real<double>(ctx, ctx->e64, (const cpx<double> *)ctx->b64, false, 1.0, (double *)ctx->r64);
+    double *coarse = (double *)ctx->vbuf[0];
+    pfs_coarsen(fine[0], fine[1], fine[2], ratio, threshold, (const double *)ctx->r64, coarse, s);
+    ctx->launches += 2;
+    const long long Vc = (long long)(fine[0] / ratio) * (fine[1] / ratio) * (fine[2] / ratio);
+    int rc = stage_out(ctx, phi_out, sizeof(double) * Vc, coarse);
+    if (rc) return rc;
+    return finish(ctx);
+}
+
+int hom_pfs(const int fine[3], const void *omega, int input_kind, int ratio, double ell, double eps,
+            double threshold, int device_ptrs, double *phi_out) {
+    if (!fine || !omega || !phi_out) return fail(nullptr, HOM_EINVAL, "null argument");
+    if (ratio < 1 || fine[0] % ratio || fine[1] % ratio || fine[2] % ratio)
+        return fail(nullptr, HOM_EINVAL, "every fine grid size must be a multiple of ratio");
+    if (!(ell >= 0.0) || !std::isfinite(ell) || !(eps > 0.0) || !std::isfinite(eps) || !std::isfinite(threshold))
+        return fail(nullptr, HOM_EINVAL, "need ell >= 0, eps > 0 and a finite threshold");
+    hom_options o;
+    hom_default_options(&o);
+    o.precision = HOM_PREC_FP64;
+    o.device_ptrs = device_ptrs;
+    hom_ctx *ctx = nullptr;
+    int rc = hom_create(&ctx, fine, omega, input_kind, 1.0, 0.3, HOM_SMOOTH_NONE, HOM_DERIV_CONTINUOUS, &o);
+    if (rc) return rc;
+    rc = pfs_impl(ctx, fine, ratio, ell, eps, threshold, phi_out);
+    if (rc) g_create_error = ctx->err;
+    hom_destroy(ctx);
+    return rc;
 }
 
 int hom_get_info(const hom_ctx *ctx, int grid[3], int *precision, long long *workspace_bytes) {

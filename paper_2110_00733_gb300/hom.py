@@ -30,7 +30,7 @@ EXPORTED = [
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
-    "hom_solve_batch", "hom_autotune", "hom_solve_mixed",
+    "hom_solve_batch", "hom_autotune", "hom_solve_mixed", "hom_pfs",
 ]
 
 
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
                               ctypes.POINTER(hom_solve_info)]
     lib.hom_solve_mixed.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
                                     ctypes.POINTER(hom_solve_info)]
+    lib.hom_pfs.argtypes = [ip, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int, vp]
     lib.hom_effective_stiffness.argtypes = [vp, dp]
     lib.hom_fields.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.hom_apply.argtypes = [vp, vp, vp]
@@ -221,6 +223,32 @@ def hom_solve_mixed(ctx: Context, macro_strain, macro_stress, stress_mask, tol=1
                              float(tol), int(max_it), _ptr(warm_start), infos)
     _check(ctx.handle, rc)
     return rc, [i.as_dict() for i in infos]
+
+
+def hom_pfs(omega_fine, ratio, ell, eps=1.0, threshold=0.05, input_kind=None, out=None):
+    """Phase-field smoothening (section 3.2) of the fine-grid phase map
+    omega_fine (numpy array, or a CUDA tensor for device pointers) onto the
+    grid shape // ratio; ell in fine voxels.  Returns the coarse phase map
+    (float64; `out` receives it for CUDA input)."""
+    lib = load_library()
+    shape = tuple(int(v) for v in omega_fine.shape)
+    dev = hasattr(omega_fine, "is_cuda") and omega_fine.is_cuda
+    if input_kind is None:
+        dt = str(omega_fine.dtype)
+        input_kind = (HOM_INPUT_PHASE_U8 if "uint8" in dt else
+                      HOM_INPUT_FRACTION_F32 if "float32" in dt else HOM_INPUT_FRACTION_F64)
+    coarse = tuple(n // ratio for n in shape)
+    if not dev:
+        omega_fine = np.ascontiguousarray(omega_fine)
+        out = np.empty(coarse, dtype=np.float64)
+    assert out is not None, "pass a CUDA float64 output tensor for CUDA input"
+    g = (ctypes.c_int * 3)(*shape)
+    rc = lib.hom_pfs(g, _ptr(omega_fine), int(input_kind), int(ratio), float(ell), float(eps), float(threshold),
+                     1 if dev else 0, _ptr(out))
+    if rc < 0:
+        msg = lib.hom_last_error(None)
+        raise HomError(rc, msg.decode() if msg else "")
+    return out
 
 
 def hom_effective_stiffness(ctx: Context) -> np.ndarray:

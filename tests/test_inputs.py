@@ -49,3 +49,29 @@ def test_octet_family_matches_the_voxelizer():
         phi, r = ri.octet(24, rho)
         assert fam.radius(rho) == r
         assert np.array_equal(fam.phi(rho), phi)
+
+
+def test_va_phase_is_the_volume_fraction_at_a_planar_surface():
+    """Material x < a: the voxel [i, i+1) holds the fraction clip(a - i, 0, 1)
+    of material, and the Voigt analytic map reproduces it exactly."""
+    for a in (3.0, 3.2, 3.5, 3.87, 4.0):
+        centres = np.arange(8) + 0.5
+        phi = ri.va_phase(a - centres, 1.0)
+        expect = np.clip(a - np.arange(8), 0.0, 1.0)
+        assert np.allclose(phi, expect, rtol=0, atol=1e-15)
+
+
+def test_octet_va_approaches_the_subsampled_voigt_map():
+    """The paper finds the Voigt analytic map almost identical to the fine-
+    grid Voigt rule (section 3.3): the mean density of the two agrees to 0.5 %
+    at 64^3 (it is 1.5 % at 32^3) and the voxel-wise difference shrinks with
+    the grid."""
+    diffs = []
+    for n in (32, 64):
+        va, r = ri.octet_va(n, 0.15)
+        vfg = ri.octet_at_radius(n, r, sub=8)
+        assert va.min() >= 0.0 and va.max() <= 1.0
+        diffs.append(float(np.abs(va - vfg).mean()))
+        if n == 64:
+            assert abs(va.mean() - vfg.mean()) <= 5e-3 * vfg.mean()
+    assert diffs[1] < diffs[0]
