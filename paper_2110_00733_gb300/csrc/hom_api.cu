@@ -904,23 +904,18 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     CU(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     if (bad) return fail(ctx, HOM_EINVAL, "phase values must be finite and in [0,1]");
-    // sum phi^2 for the zero right-hand-side test
-    Launch<double>::axpby(ctx->V, ctx->stream, 1.0, ctx->e64.phi, 0.0, (double *)ctx->r64);
+    // sum phi and phi^2 (mean density, scale of the zero right-hand-side
+    // test): FP64 reductions on the device
     {
-        // ||phi||^2 with an FP64 reduction over a real vector
-        const double *ph = ctx->e64.phi;
-        std::vector<double> host(ctx->V);
-        CU(cudaMemcpyAsync(host.data(), ph, sizeof(double) * ctx->V, cudaMemcpyDeviceToHost, ctx->stream));
+        const int nb = phi_sums(ctx->V, ctx->e64.phi, ctx->partials, ctx->stream);
+        reduce_to(ctx->stream, ctx->partials, nb, ctx->d_scalar);
+        reduce_to(ctx->stream, ctx->partials + nb, nb, ctx->d_scalar + 1);
+        ctx->launches += 3;
+        CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
-        double s2 = 0.0, s1 = 0.0;
-        for (long long i = 0; i < ctx->V; ++i) {
-            s2 += host[i] * host[i];
-            s1 += host[i];
-        }
-        ctx->phi2_sum = s2;
-        ctx->phibar = s1 / (double)ctx->V;
+        ctx->phibar = ctx->h_scalar[0] / (double)ctx->V;
+        ctx->phi2_sum = ctx->h_scalar[1];
     }
-    ctx->launches += 1;
     // phi^ = F{phi} (FP64): the field [phi, 0, 0, 0, 0, 0] through the forward
     // passes, component 0 kept
     {

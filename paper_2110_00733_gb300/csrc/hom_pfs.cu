@@ -54,12 +54,49 @@ __global__ void __launch_bounds__(kPfsThreads) k_pfs_coarsen(int n1, int n2, int
     }
 }
 
+// partial sums of phi and phi^2 (FP64): partials[b] and partials[nb + b]
+__global__ void __launch_bounds__(kPfsThreads) k_phi_sums(long long V, const double *__restrict__ phi,
+                                                          double *partials) {
+    __shared__ double red[2][kPfsThreads / 32];
+    double s1 = 0.0, s2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        const double p = phi[i];
+        s1 += p;
+        s2 += p * p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s1;
+        red[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kPfsThreads / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = b;
+    }
+}
+
 int pfs_blocks(long long n) {
     const long long b = (n + kPfsThreads - 1) / kPfsThreads;
     return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
 }
 
 }  // namespace
+
+int phi_sums(long long V, const double *phi, double *partials, cudaStream_t s) {
+    const int nb = pfs_blocks(V);
+    k_phi_sums<<<nb, kPfsThreads, 0, s>>>(V, phi, partials);
+    return nb;
+}
 
 void pfs_filter(int n1, int n2, int n3, double c, double2 *spec, cudaStream_t s) {
     const long long S = (long long)n1 * n2 * (n3 / 2 + 1);
