@@ -88,6 +88,12 @@ def _load():
         lib.orc_cg.restype = ctypes.c_int
         lib.orc_solve_mixed.restype = ctypes.c_int
         lib.orc_pfs.argtypes = [ip, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        lib.orc_j2_point.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, dp, dp, ctypes.c_double, dp, dp, dp, dp]
+        lib.orc_j2_increment.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.orc_j2_increment.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_modb_apply.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.orc_modb_rhs.argtypes = [ip, dp, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -351,6 +357,53 @@ def pfs(omega_fine, ratio, ell, eps=1.0, threshold=0.05) -> np.ndarray:
     out = np.empty(tuple(n // ratio for n in w.shape))
     lib.orc_pfs(_ip(w.shape), _dp(w), int(ratio), float(ell), float(eps), float(threshold), _dp(out))
     return out
+
+
+def j2_point(E, nu, sy, H, phi, eps_mandel, epsp_mandel, alpha):
+    """Radial return of small-strain J2 plasticity with linear isotropic
+    hardening for one voxel (stress and consistent tangent times phi),
+    Mandel components.  Returns (sigma, tangent 6x6, plastic strain, alpha)."""
+    lib = _load()
+    e = np.ascontiguousarray(eps_mandel, dtype=np.float64)
+    ep = np.ascontiguousarray(epsp_mandel, dtype=np.float64)
+    sig, Ct, epn, al = np.zeros(6), np.zeros(36), np.zeros(6), ctypes.c_double(0.0)
+    lib.orc_j2_point(float(E), float(nu), float(sy), float(H), float(phi), _dp(e), _dp(ep), float(alpha),
+                     _dp(sig), _dp(Ct), _dp(epn), ctypes.byref(al))
+    return sig, Ct.reshape(6, 6), epn, al.value
+
+
+class J2Cell:
+    """Elastoplastic cell for the Newton extension (section 2.1.1): total
+    strain and plastic strain (6 x V Mandel), hardening variable (V)."""
+
+    def __init__(self, phi, E, nu, sy, H=0.0, deriv=1):
+        self.phi = _phi(phi)
+        self.E, self.nu, self.sy, self.H, self.deriv = float(E), float(nu), float(sy), float(H), int(deriv)
+        shape = (6,) + self.phi.shape
+        self.eps = np.zeros(shape)
+        self.epsp = np.zeros(shape)
+        self.alpha = np.zeros(self.phi.shape)
+        self.Ebar = np.zeros(6)             # applied macro strain (tensor components)
+
+    def increment(self, mask, Ebar_tensor, Sbar_tensor, tol_lin=1e-6, tol_newton=5e-3, max_newton=30,
+                  max_lin=5000):
+        """One load increment to the macro strain Ebar (components outside
+        mask) and mean stress Sbar (components in mask), tensor components.
+        Returns dict with sigma_mean, eps_mean (tensor), newton and linear
+        iterations, r_newton, residual (||b|| / ||b_0|| at exit), accepted."""
+        lib = _load()
+        Et = np.ascontiguousarray(tensor_to_mandel(self.Ebar))
+        En = np.ascontiguousarray(tensor_to_mandel(np.asarray(Ebar_tensor, dtype=np.float64)))
+        Sn = np.ascontiguousarray(tensor_to_mandel(np.asarray(Sbar_tensor, dtype=np.float64)))
+        sig, em, info = np.zeros(6), np.zeros(6), np.zeros(5)
+        lib.orc_j2_increment(_ip(self.phi.shape), _dp(self.phi), self.E, self.nu, self.sy, self.H, self.deriv,
+                             int(mask), _dp(self.eps), _dp(self.epsp), _dp(self.alpha), _dp(Et), _dp(En), _dp(Sn),
+                             float(tol_lin), float(tol_newton), int(max_newton), int(max_lin), _dp(sig), _dp(em),
+                             _dp(info))
+        self.Ebar = np.asarray(Ebar_tensor, dtype=np.float64).copy()
+        return {"sigma_mean": mandel_to_tensor(sig), "eps_mean": mandel_to_tensor(em),
+                "newton": int(info[0]), "linear": int(info[1]), "r_newton": float(info[2]),
+                "residual": float(info[3]), "accepted": bool(info[4])}
 
 
 UNIT_CASES = np.eye(6)  # tensor components; shear cases have e_ab = e_ba = 1

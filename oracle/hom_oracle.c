@@ -853,3 +853,190 @@ void orc_pfs(const int nf[3], const double *omega, int ratio, double ell, double
     }
     free(w);
 }
+
+/* ------------------------------------------------------------------------ */
+/* J2 plasticity and the Newton extension of the Galerkin scheme (section     */
+/* 2.1.1).  The lattice material is small-strain von Mises plasticity with    */
+/* linear isotropic hardening H (H = 0: the perfectly plastic law of section */
+/* 5); a voxel's stress and tangent are those of the pristine material times */
+/* phi (section 3.2).  Return mapping and consistent tangent are the radial  */
+/* return of Simo & Hughes (Computational Inelasticity, 1998, section 3.3),  */
+/* in Mandel components with m = (1,1,1,0,0,0).                               */
+/* ------------------------------------------------------------------------ */
+void orc_j2_point(double E, double nu, double sy, double H, double phi, const double eps[6],
+                  const double epsp_n[6], double alpha_n, double sig[6], double Ct[36], double epsp[6],
+                  double *alpha) {
+    const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = E / (2.0 * (1.0 + nu));
+    const double kappa = lam + 2.0 * mu / 3.0;
+    const double m[6] = {1, 1, 1, 0, 0, 0};
+    double ee[6], st[6], s[6], n[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 6; ++c) ee[c] = eps[c] - epsp_n[c];
+    const double tr = ee[0] + ee[1] + ee[2];
+    for (int c = 0; c < 6; ++c) st[c] = lam * tr * m[c] + 2.0 * mu * ee[c];        /* trial stress */
+    const double p = (st[0] + st[1] + st[2]) / 3.0;
+    double ns = 0.0;
+    for (int c = 0; c < 6; ++c) { s[c] = st[c] - p * m[c]; ns += s[c] * s[c]; }
+    ns = sqrt(ns);
+    const double f = ns - sqrt(2.0 / 3.0) * (sy + H * alpha_n);                     /* trial yield function */
+    double theta = 1.0, thetab = 0.0;
+    for (int c = 0; c < 6; ++c) { sig[c] = st[c]; epsp[c] = epsp_n[c]; }
+    *alpha = alpha_n;
+    if (f > 0.0 && ns > 0.0) {
+        const double dg = f / (2.0 * mu + 2.0 * H / 3.0);                              /* consistency */
+        for (int c = 0; c < 6; ++c) {
+            n[c] = s[c] / ns;
+            sig[c] = st[c] - 2.0 * mu * dg * n[c];
+            epsp[c] = epsp_n[c] + dg * n[c];
+        }
+        *alpha = alpha_n + sqrt(2.0 / 3.0) * dg;
+        theta = 1.0 - 2.0 * mu * dg / ns;
+        thetab = 1.0 / (1.0 + H / (3.0 * mu)) - (1.0 - theta);
+    }
+    /* C = kappa m (x) m + 2 mu theta (I - m (x) m / 3) - 2 mu thetab n (x) n */
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            Ct[i * 6 + j] = phi * (kappa * m[i] * m[j] + 2.0 * mu * theta * ((i == j) - m[i] * m[j] / 3.0) -
+                                   2.0 * mu * thetab * n[i] * n[j]);
+    for (int c = 0; c < 6; ++c) sig[c] *= phi;
+}
+
+typedef struct {
+    const int *n;
+    const double *Ct;       /* 36 per voxel: the tangent of the last return mapping */
+    int deriv, mask;
+} tangent_ctx;
+
+/* A_i(v) = F^-1{ G : F{ C^{i-1}(x) : v } } with the mixed projector, eq. (galnonlin) */
+static void tangent_cb(void *c, const double *x, double *y) {
+    tangent_ctx *t = (tangent_ctx *)c;
+    orc_problem P;
+    memcpy(P.n, t->n, sizeof P.n);
+    P.phi = NULL; P.deriv = t->deriv; P.mask = t->mask;
+    long V = (long)P.n[0] * P.n[1] * P.n[2];
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * 6 * V);
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < V; ++v)
+        for (int i = 0; i < 6; ++i) {
+            double s = 0;
+            for (int j = 0; j < 6; ++j) s += t->Ct[v * 36 + i * 6 + j] * x[(long)j * V + v];
+            tau[(long)i * V + v] = s;
+        }
+    project_field(&P, tau, y);
+    free(tau);
+}
+
+typedef struct {
+    const int *n;
+    const double *phi;
+    double E, nu, sy, H;
+    int deriv, mask;
+    const double *epsp, *alpha, *Sbar;
+} j2_problem;
+
+/* stress and tangent at eps (history at t) and b = -F^-1{ G : F{ sigma - Sbar } }
+ * (right-hand side of eq. galnonlin); returns ||b|| */
+static double j2_residual(const j2_problem *J, const double *eps, double *sig, double *Ct, double *b) {
+    long V = (long)J->n[0] * J->n[1] * J->n[2], N6 = 6 * V;
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < V; ++v) {
+        double e[6], ep[6], s6[6], epn[6], aln;
+        for (int c = 0; c < 6; ++c) { e[c] = eps[(long)c * V + v]; ep[c] = J->epsp[(long)c * V + v]; }
+        orc_j2_point(J->E, J->nu, J->sy, J->H, J->phi[v], e, ep, J->alpha[v], s6, Ct + v * 36, epn, &aln);
+        for (int c = 0; c < 6; ++c) sig[(long)c * V + v] = s6[c];
+    }
+    orc_problem P;
+    memcpy(P.n, J->n, sizeof P.n);
+    P.phi = NULL; P.deriv = J->deriv; P.mask = J->mask;
+    cplx *tau = (cplx *)malloc(sizeof(cplx) * N6);
+    for (int c = 0; c < 6; ++c)
+        for (long v = 0; v < V; ++v)
+            tau[(long)c * V + v] = sig[(long)c * V + v] - (((J->mask >> c) & 1) ? J->Sbar[c] : 0.0);
+    project_field(&P, tau, b);
+    free(tau);
+    for (long i = 0; i < N6; ++i) b[i] = -b[i];
+    return sqrt(dot(N6, b, b));
+}
+
+/* One load increment t -> t + dt by an inexact damped Newton method (section
+ * 2.1.1).  eps: total strain field (6 x V Mandel) at t on entry, at t + dt on
+ * return; epsp (6 x V) and alpha (V): plastic history at t, updated on
+ * return.  The kl components follow the macro strain from Ebar_t to Ebar_n
+ * (the first iterate adds the difference uniformly), the KL components in
+ * mask carry the mean stress Sbar_n.  Each Newton step solves eq.
+ * (galnonlin) by MINRES to ||A dE - b_i|| <= tol_lin ||b_0|| (eq. galrlin)
+ * and is damped by halving its length (at most 7 times) until ||b|| falls;
+ * the increment is accepted when ||dE||_inf <= tol_newton ||eps^i - eps^t||_inf
+ * (eq. galrnewton) after a step whose linear residual met tol_lin.  info:
+ * Newton iterations, linear iterations, last r_newton, ||b|| / ||b_0|| at
+ * exit, accepted (1/0). */
+int orc_j2_increment(const int n[3], const double *phi, double E, double nu, double sy, double H, int deriv,
+                     int mask, double *eps, double *epsp, double *alpha, const double Ebar_t[6],
+                     const double Ebar_n[6], const double Sbar_n[6], double tol_lin, double tol_newton,
+                     int max_newton, int max_lin, double sig_mean[6], double eps_mean[6], double info[5]) {
+    long V = (long)n[0] * n[1] * n[2], N6 = 6 * V;
+    double *eps_t = (double *)malloc(sizeof(double) * N6);
+    double *sig = (double *)malloc(sizeof(double) * N6);
+    double *Ct = (double *)malloc(sizeof(double) * 36 * V);
+    double *b = (double *)malloc(sizeof(double) * N6);
+    double *de = (double *)malloc(sizeof(double) * N6);
+    double *etry = (double *)malloc(sizeof(double) * N6);
+    double *btry = (double *)malloc(sizeof(double) * N6);
+    double *Ctry = (double *)malloc(sizeof(double) * 36 * V);
+    memcpy(eps_t, eps, sizeof(double) * N6);
+    for (int c = 0; c < 6; ++c)
+        if (!((mask >> c) & 1))
+            for (long v = 0; v < V; ++v) eps[(long)c * V + v] += Ebar_n[c] - Ebar_t[c];
+    j2_problem J = {n, phi, E, nu, sy, H, deriv, mask, epsp, alpha, Sbar_n};
+    double nb = j2_residual(&J, eps, sig, Ct, b);
+    const double b0 = nb;
+    double rn = 0.0;
+    int it = 0, lin = 0, done = (nb == 0.0);
+    while (!done && it < max_newton) {
+        ++it;
+        tangent_ctx tc = {n, Ct, deriv, mask};
+        double est;
+        const double tol_i = tol_lin * b0 / nb;
+        const int k = orc_minres(N6, tangent_cb, &tc, b, de, tol_i < 0.5 ? tol_i : 0.5, max_lin, &est, NULL);
+        lin += k;
+        const int lin_ok = est * nb <= tol_lin * b0 * (1.0 + 1e-9) || tol_i >= 0.5;
+        double t = 1.0, nt = 0.0;
+        for (int tries = 0; tries < 8; ++tries) {
+            for (long i = 0; i < N6; ++i) etry[i] = eps[i] + t * de[i];
+            nt = j2_residual(&J, etry, sig, Ctry, btry);
+            if (nt < (1.0 - 1e-4 * t) * nb || tries == 7) break;
+            t *= 0.5;
+        }
+        double dmax = 0.0, emax = 0.0;
+        for (long i = 0; i < N6; ++i) {
+            const double d = fabs(etry[i] - eps[i]), e = fabs(etry[i] - eps_t[i]);
+            if (d > dmax) dmax = d;
+            if (e > emax) emax = e;
+        }
+        memcpy(eps, etry, sizeof(double) * N6);
+        memcpy(b, btry, sizeof(double) * N6);
+        memcpy(Ct, Ctry, sizeof(double) * 36 * V);
+        nb = nt;
+        rn = emax > 0.0 ? dmax / emax : 0.0;
+        if (lin_ok && rn <= tol_newton) done = 1;
+    }
+    /* history, mean stress and strain at the accepted iterate */
+    double *ep_new = de, *al_new = (double *)malloc(sizeof(double) * V);
+    for (int c = 0; c < 6; ++c) { sig_mean[c] = 0.0; eps_mean[c] = 0.0; }
+    for (long v = 0; v < V; ++v) {
+        double e[6], ep[6], s6[6], ct[36], epn[6], aln;
+        for (int c = 0; c < 6; ++c) { e[c] = eps[(long)c * V + v]; ep[c] = epsp[(long)c * V + v]; }
+        orc_j2_point(E, nu, sy, H, phi[v], e, ep, alpha[v], s6, ct, epn, &aln);
+        for (int c = 0; c < 6; ++c) {
+            ep_new[(long)c * V + v] = epn[c];
+            sig_mean[c] += s6[c];
+            eps_mean[c] += e[c];
+        }
+        al_new[v] = aln;
+    }
+    memcpy(epsp, ep_new, sizeof(double) * N6);
+    memcpy(alpha, al_new, sizeof(double) * V);
+    for (int c = 0; c < 6; ++c) { sig_mean[c] /= (double)V; eps_mean[c] /= (double)V; }
+    info[0] = it; info[1] = lin; info[2] = rn; info[3] = b0 > 0.0 ? nb / b0 : 0.0; info[4] = done;
+    free(eps_t); free(sig); free(Ct); free(b); free(de); free(etry); free(btry); free(Ctry); free(al_new);
+    return it;
+}
