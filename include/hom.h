@@ -217,6 +217,60 @@ int hom_pfs(const int fine[3], const void *omega, int input_kind, int ratio, dou
 int hom_solve_mixed(hom_ctx *ctx, const double *macro_strain, const double *macro_stress, int stress_mask,
                     int ncase, double tol, int max_it, const void *warm_start, hom_solve_info *info);
 
+/* Elastoplastic cells: the Newton extension of the Galerkin scheme (section
+ * 2.1.1) for small-strain von Mises (J2) plasticity with linear isotropic
+ * hardening, the lattice material of section 5 (hardening = 0 is perfect
+ * plasticity).  A voxel's stress and consistent tangent are those of the
+ * material (radial return, Simo & Hughes 1998, section 3.3) times phi.
+ * FP64 Galerkin-MINRES contexts only (HOM_PREC_FP64, HOM_SOLVER_GALERKIN_MINRES;
+ * HOM_EINVAL otherwise).
+ *
+ * hom_j2_begin allocates the history on the device (about 600 bytes per
+ * voxel: total and plastic strain, hardening variable, tangent, Newton
+ * work fields) and zeroes it (virgin, unstrained cell); calling it again
+ * resets the history.  yield_stress > 0 and hardening >= 0 in the units of E. */
+int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening);
+
+typedef struct {
+    int status;            /* HOM_OK, or HOM_NOT_CONVERGED when max_newton ran out */
+    int newton;            /* Newton iterations of the increment */
+    int linear;            /* MINRES iterations over those Newton iterations */
+    int backtracks;        /* step halvings of the line search over the increment */
+    double r_newton;       /* ||d eps||_inf / ||eps^i - eps^t||_inf of the last step, eq. (galrnewton) */
+    double residual;       /* ||b_i|| / ||b_0|| at exit (right-hand side of eq. (galnonlin)) */
+    double sigma_mean[6];  /* mean stress at the end of the increment, tensor components, units of E */
+    double eps_mean[6];    /* mean total strain, tensor components */
+    double time_ms;        /* device time of the increment */
+} hom_j2_info;
+
+/* One load increment t -> t + dt by an inexact damped Newton method.
+ *   macro_strain  6 tensor components: the mean strain at t + dt of the
+ *                 strain-controlled components (the first iterate adds the
+ *                 change from the previous increment's macro_strain, zero
+ *                 after hom_j2_begin, uniformly).
+ *   macro_stress  6 tensor components, units of E: the mean stress at t + dt
+ *                 of the components set in stress_mask (bits as for
+ *                 hom_solve_mixed).
+ * Each Newton iteration solves eq. (galnonlin) with the tangent at the
+ * current iterate by MINRES to ||A dE - b_i|| <= tol_lin ||b_0|| (eq. galrlin;
+ * the relative tolerance a MINRES call is given is capped at 0.5), then
+ * halves the step (at most 7 times) until ||b|| falls by the factor
+ * 1 - 1e-4 t.  The increment is accepted when ||dE||_inf <= tol_newton
+ * ||eps^i - eps^t||_inf (eq. galrnewton) after a step whose linear solve met
+ * tol_lin; the plastic history then moves to t + dt.  When max_newton runs
+ * out the last iterate is taken all the same and the status says so.
+ * Returns HOM_OK, HOM_NOT_CONVERGED or a negative error. */
+int hom_j2_increment(hom_ctx *ctx, const double macro_strain[6], const double macro_stress[6], int stress_mask,
+                     double tol_lin, double tol_newton, int max_newton, int max_lin, hom_j2_info *info);
+
+/* Total strain, plastic strain (each 6 x V tensor components, double) and
+ * hardening variable (V doubles) of the history; host or device pointers
+ * per device_ptrs; any may be NULL. */
+int hom_j2_state(hom_ctx *ctx, double *strain, double *plastic_strain, double *alpha);
+
+/* Frees the history (also done by hom_destroy). */
+int hom_j2_end(hom_ctx *ctx);
+
 /* 6x6 Voigt effective stiffness, row-major, sigma = C (e11,e22,e33,2e23,2e13,2e12),
  * same units as E, fitted to the mean stresses and mean strains of the last
  * hom_solve or hom_solve_mixed.  That solve must have had ncase >= 6 cases

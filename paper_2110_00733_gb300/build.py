@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libhom.so")
 SOURCES = ["hom_kernels_f32.cu", "hom_kernels_f64.cu", "hom_common.cu", "hom_api.cu", "hom_noalloc.cu",
-           "hom_batch.cu", "hom_cg.cu", "hom_pfs.cu", "net_kernels.cu", "net.cu", "net_tc.cu"]
+           "hom_batch.cu", "hom_cg.cu", "hom_pfs.cu", "hom_j2.cu", "net_kernels.cu", "net.cu", "net_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -10,12 +10,14 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hom.h"
 #include "hom_internal.h"
 #include "hom_cg.h"
 #include "hom_pfs.h"
+#include "hom_j2.h"
 
 using namespace hom;
 
@@ -68,6 +70,24 @@ template <typename R> struct Engine {
     void *M[3] = {nullptr, nullptr, nullptr};
 };
 
+// History and Newton work fields of an elastoplastic cell (hom_j2_*), FP64
+// real fields 6 x V Mandel, component-major.
+struct J2State {
+    bool active = false;
+    J2Material mat{};          // units of E (E = 1)
+    double *eps = nullptr;     // total strain at the current iterate
+    double *eps_t = nullptr;   // total strain at t
+    double *etry = nullptr;    // line-search trial
+    double *epsp = nullptr;    // plastic strain at t
+    double *alpha = nullptr;   // hardening variable at t (V)
+    double *sig = nullptr;     // stress; inverse-FFT scratch inside the operator
+    double *de = nullptr;      // Newton step (real); tangent output inside the operator
+    double *Ct = nullptr;      // consistent tangent at the current iterate (36 V)
+    double *partials = nullptr;
+    double *h_partials = nullptr;   // pinned
+    double Ebar[6] = {0, 0, 0, 0, 0, 0};   // macro strain of the last increment (Mandel)
+};
+
 }  // namespace
 
 struct hom_ctx {
@@ -117,6 +137,9 @@ struct hom_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // graph is a device-side WHILE loop over the body
     bool host_loop = false;          // asked for the host-replayed body
+    bool tangent_op = false;         // operator of eq. (galnonlin) with the J2 tangent (FP64)
+    bool graph_tangent = false;      // the captured graph applies the tangent operator
+    J2State j2;
     int graph_iters = 6;
     long long graph_kernels = 0;
     long long launches = 0;
@@ -338,8 +361,24 @@ static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool
     cudaStream_t s = ctx->stream;
     Launch<R>::x1(E.g, s, X1_GAMMA_IN, v, E.spec, nullptr, nullptr, st);
     Launch<R>::x2(E.g, s, 1, E.spec, st);
-    Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
-                  E.phi, st);
+    if constexpr (std::is_same<R, double>::value) {
+        if (ctx->tangent_op) {
+            // A_i v = G F (C^{i-1}(x) : F^-1 G v), eq. (galnonlin): the point-wise
+            // 6x6 tangent between an inverse and a forward n3 pass
+            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL,
+                          ctx->j2.sig, E.phi, st);
+            j2_tangent_apply(ctx->V, ctx->j2.Ct, ctx->j2.sig, ctx->j2.de, s);
+            Launch<R>::x3(E.g, s, X3_IN_REAL, ctx->j2.de, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
+                          E.spec, E.phi, st);
+            ctx->launches += 2;
+        } else {
+            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
+                          E.spec, E.phi, st);
+        }
+    } else {
+        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
+                      E.spec, E.phi, st);
+    }
     Launch<R>::x2(E.g, s, 0, E.spec, st);
     Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | (dot ? X1_DOT : 0), E.spec, p, dot ? v : nullptr, partials, st);
     ctx->launches += 5;
@@ -419,7 +458,11 @@ static void capture_body(hom_ctx *ctx, Engine<R> &E) {
 // a graph of the body alone that the host replays.
 template <typename R>
 static int build_graph(hom_ctx *ctx, Engine<R> &E) {
-    if (ctx->graph) return HOM_OK;
+    if (ctx->graph && ctx->graph_tangent == ctx->tangent_op) return HOM_OK;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
     const long long before = ctx->launches;
     cudaGraph_t graph = nullptr;
     bool loops = false;
@@ -464,6 +507,7 @@ static int build_graph(hom_ctx *ctx, Engine<R> &E) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     ctx->graph_loops = loops;
+    ctx->graph_tangent = ctx->tangent_op;
     return HOM_OK;
 }
 
@@ -802,10 +846,24 @@ void hom_default_options(hom_options *opt) {
 
 const char *hom_last_error(const hom_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
+static void j2_free(hom_ctx *ctx) {
+    J2State &j = ctx->j2;
+    double *bufs[] = {j.eps, j.eps_t, j.etry, j.epsp, j.alpha, j.sig, j.de, j.Ct, j.partials};
+    for (double *p : bufs) cudaFree(p);
+    if (j.h_partials) cudaFreeHost(j.h_partials);
+    j = J2State{};
+    ctx->tangent_op = false;
+    if (ctx->graph && ctx->graph_tangent) {   // it holds the freed buffers
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+}
+
 void hom_destroy(hom_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    j2_free(ctx);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cg_graph) cudaGraphExecDestroy(ctx->cg_graph);
     cudaFree(ctx->d_cg);
@@ -1612,6 +1670,200 @@ int hom_fields(hom_ctx *ctx, int icase, void *strain, void *stress) {
         ctx->launches += 1;
         if (strain) { int rc = stage_out(ctx, strain, sizeof(float) * n, de); if (rc) return rc; }
         if (stress) { int rc = stage_out(ctx, stress, sizeof(float) * n, ds); if (rc) return rc; }
+    }
+    return finish(ctx);
+}
+
+// ----- elastoplastic cells (section 2.1.1) ---------------------------------------
+int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening) {
+    if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
+    if (ctx->prec != HOM_PREC_FP64 || ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
+        return fail(ctx, HOM_EINVAL, "elastoplastic cells need an FP64 Galerkin-MINRES context");
+    if (!(yield_stress > 0.0) || !(hardening >= 0.0) || !std::isfinite(yield_stress) || !std::isfinite(hardening))
+        return fail(ctx, HOM_EINVAL, "need yield_stress > 0 and hardening >= 0, finite");
+    cudaSetDevice(ctx->device);
+    J2State &j = ctx->j2;
+    const long long n6 = 6 * ctx->V;
+    if (!j.active) {
+        double **f6[] = {&j.eps, &j.eps_t, &j.etry, &j.epsp, &j.sig, &j.de};
+        for (double **p : f6) CU(cudaMalloc(p, sizeof(double) * n6));
+        CU(cudaMalloc(&j.alpha, sizeof(double) * ctx->V));
+        CU(cudaMalloc(&j.Ct, sizeof(double) * 36 * ctx->V));
+        CU(cudaMalloc(&j.partials, sizeof(double) * 6 * kJ2Blocks));
+        CU(cudaMallocHost(&j.h_partials, sizeof(double) * 6 * kJ2Blocks));
+        ctx->workspace += (long long)sizeof(double) * (6 * n6 + 37 * ctx->V);
+        j.active = true;
+    }
+    CU(cudaMemsetAsync(j.eps, 0, sizeof(double) * n6, ctx->stream));
+    CU(cudaMemsetAsync(j.epsp, 0, sizeof(double) * n6, ctx->stream));
+    CU(cudaMemsetAsync(j.alpha, 0, sizeof(double) * ctx->V, ctx->stream));
+    j.mat = J2Material{1.0, ctx->nu, yield_stress / ctx->E, hardening / ctx->E};
+    for (int c = 0; c < 6; ++c) j.Ebar[c] = 0.0;
+    return finish(ctx);
+}
+
+int hom_j2_end(hom_ctx *ctx) {
+    if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->j2.active)
+        ctx->workspace -= (long long)sizeof(double) * (36 * ctx->V + 37 * ctx->V);
+    j2_free(ctx);
+    return HOM_OK;
+}
+
+// stress and tangent at eps (history at t), b^ = -G F{sigma - S_bar} (the
+// right-hand side of eq. galnonlin, S_bar on the stress-controlled
+// components through xi = 0) into b64; returns ||b^||_w
+static int j2_residual(hom_ctx *ctx, const double *eps, const double sbar_v[6], double *nb) {
+    J2State &j = ctx->j2;
+    j2_return(ctx->V, j.mat, ctx->e64.phi, eps, j.epsp, j.alpha, j.sig, j.Ct, 0, ctx->stream);
+    real_to_spec<double>(ctx, ctx->e64, j.sig, X3_MID_NONE, true, ctx->b64);
+    j2_negate_add_dc(6 * ctx->S, ctx->b64, sbar_v, ctx->stream);
+    ctx->launches += 2;
+    double b2 = 0.0;
+    int rc = spec_norm2<double>(ctx, ctx->e64, ctx->b64, &b2);
+    if (rc) return rc;
+    *nb = std::sqrt(b2);
+    return HOM_OK;
+}
+
+static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sbar_t, int mask, double tol_lin,
+                             double tol_newton, int max_newton, int max_lin, hom_j2_info *inf) {
+    J2State &j = ctx->j2;
+    cudaStream_t s = ctx->stream;
+    const long long n6 = 6 * ctx->V;
+    double En[6], Sn[6], sbar_v[6], d[6];
+    macro_to_mandel(mac_t, En);
+    macro_to_mandel(sbar_t, Sn);
+    for (int c = 0; c < 6; ++c) {
+        const bool kl = (mask >> c) & 1;
+        sbar_v[c] = kl ? (double)ctx->V * Sn[c] / ctx->E : 0.0;   // F{S_bar} at xi = 0, units of E
+        d[c] = kl ? 0.0 : En[c] - j.Ebar[c];
+    }
+    CU(cudaEventRecord(ctx->ev0, s));
+    CU(cudaMemcpyAsync(j.eps_t, j.eps, sizeof(double) * n6, cudaMemcpyDeviceToDevice, s));
+    // predictor: the macro strain change added uniformly
+    j2_add_uniform(ctx->V, j.eps, d, s);
+    ctx->launches += 1;
+    double nb = 0.0;
+    int rc = j2_residual(ctx, j.eps, sbar_v, &nb);
+    if (rc) return rc;
+    if (!std::isfinite(nb)) return fail(ctx, HOM_ENAN, "J2 residual not finite");
+    const double b0 = nb;
+    double rn = 0.0;
+    int it = 0, lin = 0, back = 0;
+    bool done = (nb == 0.0);
+    while (!done && it < max_newton) {
+        ++it;
+        // A_i dE = b_i (eq. galnonlin) to ||A dE - b_i|| <= tol_lin ||b_0|| (eq. galrlin)
+        const double tol_i = tol_lin * b0 / nb;
+        CU(cudaMemcpyAsync(ctx->rhs, ctx->b64, sizeof(double2) * 6 * ctx->S, cudaMemcpyDeviceToDevice, s));
+        ctx->tangent_op = true;
+        int k = 0, st = 0;
+        double est = 0.0;
+        rc = run_minres<double>(ctx, ctx->e64, tol_i < 0.5 ? tol_i : 0.5, max_lin, &k, &est, &st);
+        ctx->tangent_op = false;
+        if (rc) return rc;
+        if (st == HOM_ENAN) return fail(ctx, HOM_ENAN, "J2 Newton system: MINRES breakdown");
+        lin += k;
+        const bool lin_ok = est * nb <= tol_lin * b0 * (1.0 + 1e-9) || tol_i >= 0.5;
+        spec_to_real<double>(ctx, ctx->e64, (const double2 *)ctx->xs, true, 1.0, j.de);
+        // damped step: halve until ||b|| falls
+        double t = 1.0, nt = 0.0;
+        for (int tries = 0; tries < 8; ++tries) {
+            CU(cudaMemcpyAsync(j.etry, j.eps, sizeof(double) * n6, cudaMemcpyDeviceToDevice, s));
+            Launch<double>::axpby(n6, s, t, j.de, 1.0, j.etry);
+            ctx->launches += 1;
+            rc = j2_residual(ctx, j.etry, sbar_v, &nt);
+            if (rc) return rc;
+            if (nt < (1.0 - 1e-4 * t) * nb || tries == 7) break;
+            t *= 0.5;
+            ++back;
+        }
+        if (!std::isfinite(nt)) return fail(ctx, HOM_ENAN, "J2 residual not finite");
+        // eq. (galrnewton): ||eps^{i+1} - eps^i||_inf against ||eps^{i+1} - eps^t||_inf
+        const double dmax = j2_absmax(n6, j.etry, j.eps, j.partials, j.h_partials, s);
+        const double emax = j2_absmax(n6, j.etry, j.eps_t, j.partials, j.h_partials, s);
+        ctx->launches += 2;
+        std::swap(j.eps, j.etry);
+        nb = nt;
+        rn = emax > 0.0 ? dmax / emax : 0.0;
+        if (lin_ok && rn <= tol_newton) done = true;
+    }
+    // history to t + dt, mean stress and strain at the accepted iterate
+    j2_return(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, nullptr, 1, s);
+    double sm[6], em[6];
+    j2_means(ctx->V, j.sig, j.partials, j.h_partials, sm, s);
+    j2_means(ctx->V, j.eps, j.partials, j.h_partials, em, s);
+    ctx->launches += 3;
+    CU(cudaEventRecord(ctx->ev1, s));
+    CU(cudaEventSynchronize(ctx->ev1));
+    for (int c = 0; c < 6; ++c) j.Ebar[c] = En[c];
+    const double r2 = std::sqrt(2.0);
+    for (int c = 0; c < 6; ++c) {
+        inf->sigma_mean[c] = sm[c] * ctx->E / (c >= 3 ? r2 : 1.0);
+        inf->eps_mean[c] = em[c] / (c >= 3 ? r2 : 1.0);
+    }
+    inf->newton = it;
+    inf->linear = lin;
+    inf->backtracks = back;
+    inf->r_newton = rn;
+    inf->residual = b0 > 0.0 ? nb / b0 : 0.0;
+    inf->status = done ? HOM_OK : HOM_NOT_CONVERGED;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    inf->time_ms = ms;
+    return HOM_OK;
+}
+
+int hom_j2_increment(hom_ctx *ctx, const double macro_strain[6], const double macro_stress[6], int stress_mask,
+                     double tol_lin, double tol_newton, int max_newton, int max_lin, hom_j2_info *info) {
+    if (!ctx || !macro_strain || !macro_stress) return fail(ctx, HOM_EINVAL, "null argument");
+    if (!ctx->j2.active) return fail(ctx, HOM_EINVAL, "hom_j2_begin first");
+    if (stress_mask < 0 || stress_mask > 63) return fail(ctx, HOM_EINVAL, "stress_mask must be in 0..63");
+    if (!(tol_lin > 0.0) || !(tol_newton > 0.0) || max_newton < 1 || max_lin < 1)
+        return fail(ctx, HOM_EINVAL, "need tol_lin, tol_newton > 0 and max_newton, max_lin >= 1");
+    for (int c = 0; c < 6; ++c)
+        if (!std::isfinite(macro_strain[c]) || !std::isfinite(macro_stress[c]))
+            return fail(ctx, HOM_ENAN, "macro strain or stress not finite");
+    cudaSetDevice(ctx->device);
+    set_stress_mask(ctx, stress_mask);
+    ctx->ncase = 0;   // the linear solutions are not kept
+    hom_j2_info inf{};
+    int rc = j2_increment_impl(ctx, macro_strain, macro_stress, stress_mask, tol_lin, tol_newton, max_newton,
+                               max_lin, &inf);
+    ctx->tangent_op = false;
+    if (rc) {
+        inf.status = rc;
+        if (info) *info = inf;
+        return rc;
+    }
+    rc = finish(ctx);
+    if (rc) inf.status = rc;
+    if (info) *info = inf;
+    return rc ? rc : inf.status;
+}
+
+int hom_j2_state(hom_ctx *ctx, double *strain, double *plastic_strain, double *alpha) {
+    if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
+    if (!ctx->j2.active) return fail(ctx, HOM_EINVAL, "hom_j2_begin first");
+    cudaSetDevice(ctx->device);
+    const long long n6 = 6 * ctx->V;
+    double *tmp = (double *)ctx->r64;   // >= 6 V doubles
+    const double *src[2] = {ctx->j2.eps, ctx->j2.epsp};
+    double *dst[2] = {strain, plastic_strain};
+    for (int f = 0; f < 2; ++f) {
+        if (!dst[f]) continue;
+        CU(cudaMemcpyAsync(tmp, src[f], sizeof(double) * n6, cudaMemcpyDeviceToDevice, ctx->stream));
+        mandel_scale64(ctx->V, ctx->stream, tmp, 1.0 / std::sqrt(2.0));   // Mandel -> tensor components
+        ctx->launches += 1;
+        int rc = stage_out(ctx, dst[f], sizeof(double) * n6, tmp);
+        if (rc) return rc;
+    }
+    if (alpha) {
+        int rc = stage_out(ctx, alpha, sizeof(double) * ctx->V, ctx->j2.alpha);
+        if (rc) return rc;
     }
     return finish(ctx);
 }

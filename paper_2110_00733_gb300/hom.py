@@ -31,6 +31,7 @@ EXPORTED = [
     "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
     "hom_solve_batch", "hom_autotune", "hom_solve_mixed", "hom_pfs",
+    "hom_j2_begin", "hom_j2_increment", "hom_j2_state", "hom_j2_end",
 ]
 
 
@@ -56,6 +57,19 @@ class hom_solve_info(ctypes.Structure):
                 "est_residual": self.est_residual, "true_residual": self.true_residual,
                 "sigma_mean": np.array(self.sigma_mean[:]), "time_ms": self.time_ms,
                 "eps_mean": np.array(self.eps_mean[:])}
+
+
+class hom_j2_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("newton", ctypes.c_int), ("linear", ctypes.c_int),
+                ("backtracks", ctypes.c_int), ("r_newton", ctypes.c_double), ("residual", ctypes.c_double),
+                ("sigma_mean", ctypes.c_double * 6), ("eps_mean", ctypes.c_double * 6),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"status": self.status, "newton": self.newton, "linear": self.linear,
+                "backtracks": self.backtracks, "r_newton": self.r_newton, "residual": self.residual,
+                "sigma_mean": np.array(self.sigma_mean[:]), "eps_mean": np.array(self.eps_mean[:]),
+                "time_ms": self.time_ms, "accepted": self.status == HOM_OK}
 
 
 class HomError(RuntimeError):
@@ -87,6 +101,11 @@ def load_library(path: str = LIB_PATH):
                                     ctypes.POINTER(hom_solve_info)]
     lib.hom_pfs.argtypes = [ip, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             ctypes.c_int, vp]
+    lib.hom_j2_begin.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.hom_j2_increment.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(hom_j2_info)]
+    lib.hom_j2_state.argtypes = [vp, vp, vp, vp]
+    lib.hom_j2_end.argtypes = [vp]
     lib.hom_effective_stiffness.argtypes = [vp, dp]
     lib.hom_fields.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.hom_apply.argtypes = [vp, vp, vp]
@@ -249,6 +268,44 @@ def hom_pfs(omega_fine, ratio, ell, eps=1.0, threshold=0.05, input_kind=None, ou
         msg = lib.hom_last_error(None)
         raise HomError(rc, msg.decode() if msg else "")
     return out
+
+
+def hom_j2_begin(ctx: Context, yield_stress, hardening=0.0):
+    """Zero J2 history (section 2.1.1 / section 5 material) on an FP64
+    Galerkin-MINRES context; stresses in the units of E."""
+    _check(ctx.handle, load_library().hom_j2_begin(ctx.handle, float(yield_stress), float(hardening)))
+
+
+def hom_j2_increment(ctx: Context, macro_strain, macro_stress, stress_mask, tol_lin=1e-6, tol_newton=5e-3,
+                     max_newton=30, max_lin=5000):
+    """One load increment by the damped Newton method; macro_strain and
+    macro_stress are 6 tensor components (mean strain of the components not
+    in stress_mask, mean stress of those in it).  Returns (rc, info dict)."""
+    lib = load_library()
+    dp = ctypes.POINTER(ctypes.c_double)
+    m = np.ascontiguousarray(np.asarray(macro_strain, dtype=np.float64).reshape(6))
+    sg = np.ascontiguousarray(np.asarray(macro_stress, dtype=np.float64).reshape(6))
+    info = hom_j2_info()
+    rc = lib.hom_j2_increment(ctx.handle, m.ctypes.data_as(dp), sg.ctypes.data_as(dp), int(stress_mask),
+                              float(tol_lin), float(tol_newton), int(max_newton), int(max_lin), ctypes.byref(info))
+    _check(ctx.handle, rc)
+    return rc, info.as_dict()
+
+
+def hom_j2_state(ctx: Context, strain=None, plastic_strain=None, alpha=None):
+    """Total and plastic strain (6 x grid, tensor components) and hardening
+    variable (grid) of the history, as float64 arrays (or into the given
+    device buffers for device_ptrs contexts)."""
+    if not ctx.device_ptrs:
+        strain = np.empty((6,) + ctx.grid) if strain is None else strain
+        plastic_strain = np.empty((6,) + ctx.grid) if plastic_strain is None else plastic_strain
+        alpha = np.empty(ctx.grid) if alpha is None else alpha
+    _check(ctx.handle, load_library().hom_j2_state(ctx.handle, _ptr(strain), _ptr(plastic_strain), _ptr(alpha)))
+    return strain, plastic_strain, alpha
+
+
+def hom_j2_end(ctx: Context):
+    _check(ctx.handle, load_library().hom_j2_end(ctx.handle))
 
 
 def hom_effective_stiffness(ctx: Context) -> np.ndarray:
