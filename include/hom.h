@@ -222,23 +222,29 @@ int hom_solve_mixed(hom_ctx *ctx, const double *macro_strain, const double *macr
  * hardening, the lattice material of section 5 (hardening = 0 is perfect
  * plasticity).  A voxel's stress and consistent tangent are those of the
  * material (radial return, Simo & Hughes 1998, section 3.3) times phi.
- * FP64 Galerkin-MINRES contexts only (HOM_PREC_FP64, HOM_SOLVER_GALERKIN_MINRES;
- * HOM_EINVAL otherwise).
+ * Galerkin-MINRES contexts only (HOM_EINVAL for the other solvers).  Strains,
+ * history, stresses and the Newton right-hand sides are FP64 in either
+ * precision; with HOM_PREC_FP32_FIELDS the Newton systems are solved by FP32
+ * MINRES sweeps with an FP32 copy of the tangent, refined (up to
+ * hom_options.refine more sweeps) against the FP64 residual of the tangent
+ * system, which decides whether a solve met tol_lin; with HOM_PREC_FP64 by
+ * FP64 MINRES.
  *
- * hom_j2_begin allocates the history on the device (about 600 bytes per
- * voxel: total and plastic strain, hardening variable, tangent, Newton
- * work fields) and zeroes it (virgin, unstrained cell); calling it again
- * resets the history.  yield_stress > 0 and hardening >= 0 in the units of E. */
+ * hom_j2_begin allocates the history on the device (total and plastic
+ * strain, hardening variable, tangent, Newton work fields: 584 bytes per
+ * voxel with FP64 fields, about 540 with FP32) and zeroes it (virgin, unstrained cell); calling it again
+ * resets the history.  yield_stress > 0 and hardening >= 0, same units as E. */
 int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening);
 
 typedef struct {
     int status;            /* HOM_OK, or HOM_NOT_CONVERGED when max_newton ran out */
     int newton;            /* Newton iterations of the increment */
-    int linear;            /* MINRES iterations over those Newton iterations */
+    int linear;            /* MINRES iterations over those Newton iterations (max_lin bounds
+                              each Newton system, refinement sweeps included) */
     int backtracks;        /* step halvings of the line search over the increment */
     double r_newton;       /* ||d eps||_inf / ||eps^i - eps^t||_inf of the last step, eq. (galrnewton) */
     double residual;       /* ||b_i|| / ||b_0|| at exit (right-hand side of eq. (galnonlin)) */
-    double sigma_mean[6];  /* mean stress at the end of the increment, tensor components, units of E */
+    double sigma_mean[6];  /* mean stress at the end of the increment, tensor components, same units as E */
     double eps_mean[6];    /* mean total strain, tensor components */
     double time_ms;        /* device time of the increment */
 } hom_j2_info;
@@ -248,7 +254,7 @@ typedef struct {
  *                 strain-controlled components (the first iterate adds the
  *                 change from the previous increment's macro_strain, zero
  *                 after hom_j2_begin, uniformly).
- *   macro_stress  6 tensor components, units of E: the mean stress at t + dt
+ *   macro_stress  6 tensor components, same units as E: the mean stress at t + dt
  *                 of the components set in stress_mask (bits as for
  *                 hom_solve_mixed).
  * Each Newton iteration solves eq. (galnonlin) with the tangent at the

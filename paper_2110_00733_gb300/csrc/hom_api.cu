@@ -82,7 +82,10 @@ struct J2State {
     double *alpha = nullptr;   // hardening variable at t (V)
     double *sig = nullptr;     // stress; inverse-FFT scratch inside the operator
     double *de = nullptr;      // Newton step (real); tangent output inside the operator
-    double *Ct = nullptr;      // consistent tangent at the current iterate (36 V)
+    double *Ct = nullptr;      // consistent tangent at the current iterate (36 V; FP64 fields)
+    float *Ct32 = nullptr;     // the same in FP32 (FP32 fields: the MINRES operator is FP32)
+    float *sig32 = nullptr, *de32 = nullptr;   // FP32 operator scratch (6 V each)
+    double2 *x64 = nullptr;    // FP32 fields: the Newton step accumulated over refinement sweeps (spectral)
     double *partials = nullptr;
     double *h_partials = nullptr;   // pinned
     double Ebar[6] = {0, 0, 0, 0, 0, 0};   // macro strain of the last increment (Mandel)
@@ -361,20 +364,27 @@ static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool
     cudaStream_t s = ctx->stream;
     Launch<R>::x1(E.g, s, X1_GAMMA_IN, v, E.spec, nullptr, nullptr, st);
     Launch<R>::x2(E.g, s, 1, E.spec, st);
-    if constexpr (std::is_same<R, double>::value) {
-        if (ctx->tangent_op) {
-            // A_i v = G F (C^{i-1}(x) : F^-1 G v), eq. (galnonlin): the point-wise
-            // 6x6 tangent between an inverse and a forward n3 pass
-            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL,
-                          ctx->j2.sig, E.phi, st);
-            j2_tangent_apply(ctx->V, ctx->j2.Ct, ctx->j2.sig, ctx->j2.de, s);
-            Launch<R>::x3(E.g, s, X3_IN_REAL, ctx->j2.de, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
-                          E.spec, E.phi, st);
-            ctx->launches += 2;
+    if (ctx->tangent_op) {
+        // A_i v = G F (C^{i-1}(x) : F^-1 G v), eq. (galnonlin): the point-wise
+        // 6x6 tangent between an inverse and a forward n3 pass
+        R *tin, *tout;
+        if constexpr (std::is_same<R, double>::value) {
+            tin = ctx->j2.sig; tout = ctx->j2.de;
         } else {
-            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
-                          E.spec, E.phi, st);
+            tin = ctx->j2.sig32; tout = ctx->j2.de32;
         }
+        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL, tin,
+                      E.phi, st);
+        // FP64 operator of FP32 fields (their true residual): the FP32 tangent in FP64 arithmetic
+        if constexpr (std::is_same<R, double>::value) {
+            if (ctx->j2.Ct) j2_tangent_apply<double, double>(ctx->V, ctx->j2.Ct, tin, tout, s);
+            else j2_tangent_apply<float, double>(ctx->V, ctx->j2.Ct32, tin, tout, s);
+        } else {
+            j2_tangent_apply<float, float>(ctx->V, ctx->j2.Ct32, tin, tout, s);
+        }
+        Launch<R>::x3(E.g, s, X3_IN_REAL, tout, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
+                      E.phi, st);
+        ctx->launches += 2;
     } else {
         Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
                       E.spec, E.phi, st);
@@ -850,6 +860,9 @@ static void j2_free(hom_ctx *ctx) {
     J2State &j = ctx->j2;
     double *bufs[] = {j.eps, j.eps_t, j.etry, j.epsp, j.alpha, j.sig, j.de, j.Ct, j.partials};
     for (double *p : bufs) cudaFree(p);
+    float *fbufs[] = {j.Ct32, j.sig32, j.de32};
+    for (float *p : fbufs) cudaFree(p);
+    cudaFree(j.x64);
     if (j.h_partials) cudaFreeHost(j.h_partials);
     j = J2State{};
     ctx->tangent_op = false;
@@ -1675,10 +1688,18 @@ int hom_fields(hom_ctx *ctx, int icase, void *strain, void *stress) {
 }
 
 // ----- elastoplastic cells (section 2.1.1) ---------------------------------------
+// device bytes of the history and Newton work fields
+static long long j2_bytes(const hom_ctx *ctx) {
+    const long long V = ctx->V;
+    return (long long)sizeof(double) * 37 * V +
+           (ctx->prec == HOM_PREC_FP64 ? (long long)sizeof(double) * 36 * V
+                                        : (long long)sizeof(float) * 48 * V + (long long)sizeof(double2) * 6 * ctx->S);
+}
+
 int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening) {
     if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
-    if (ctx->prec != HOM_PREC_FP64 || ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
-        return fail(ctx, HOM_EINVAL, "elastoplastic cells need an FP64 Galerkin-MINRES context");
+    if (ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
+        return fail(ctx, HOM_EINVAL, "elastoplastic cells need a Galerkin-MINRES context");
     if (!(yield_stress > 0.0) || !(hardening >= 0.0) || !std::isfinite(yield_stress) || !std::isfinite(hardening))
         return fail(ctx, HOM_EINVAL, "need yield_stress > 0 and hardening >= 0, finite");
     cudaSetDevice(ctx->device);
@@ -1688,10 +1709,17 @@ int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening) {
         double **f6[] = {&j.eps, &j.eps_t, &j.etry, &j.epsp, &j.sig, &j.de};
         for (double **p : f6) CU(cudaMalloc(p, sizeof(double) * n6));
         CU(cudaMalloc(&j.alpha, sizeof(double) * ctx->V));
-        CU(cudaMalloc(&j.Ct, sizeof(double) * 36 * ctx->V));
+        if (ctx->prec == HOM_PREC_FP64) {
+            CU(cudaMalloc(&j.Ct, sizeof(double) * 36 * ctx->V));
+        } else {
+            CU(cudaMalloc(&j.Ct32, sizeof(float) * 36 * ctx->V));
+            CU(cudaMalloc(&j.sig32, sizeof(float) * n6));
+            CU(cudaMalloc(&j.de32, sizeof(float) * n6));
+            CU(cudaMalloc(&j.x64, sizeof(double2) * 6 * ctx->S));
+        }
         CU(cudaMalloc(&j.partials, sizeof(double) * 6 * kJ2Blocks));
         CU(cudaMallocHost(&j.h_partials, sizeof(double) * 6 * kJ2Blocks));
-        ctx->workspace += (long long)sizeof(double) * (6 * n6 + 37 * ctx->V);
+        ctx->workspace += j2_bytes(ctx);
         j.active = true;
     }
     CU(cudaMemsetAsync(j.eps, 0, sizeof(double) * n6, ctx->stream));
@@ -1706,8 +1734,7 @@ int hom_j2_end(hom_ctx *ctx) {
     if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->j2.active)
-        ctx->workspace -= (long long)sizeof(double) * (36 * ctx->V + 37 * ctx->V);
+    if (ctx->j2.active) ctx->workspace -= j2_bytes(ctx);
     j2_free(ctx);
     return HOM_OK;
 }
@@ -1717,7 +1744,10 @@ int hom_j2_end(hom_ctx *ctx) {
 // components through xi = 0) into b64; returns ||b^||_w
 static int j2_residual(hom_ctx *ctx, const double *eps, const double sbar_v[6], double *nb) {
     J2State &j = ctx->j2;
-    j2_return(ctx->V, j.mat, ctx->e64.phi, eps, j.epsp, j.alpha, j.sig, j.Ct, 0, ctx->stream);
+    if (ctx->prec == HOM_PREC_FP64)
+        j2_return<double>(ctx->V, j.mat, ctx->e64.phi, eps, j.epsp, j.alpha, j.sig, j.Ct, 0, ctx->stream);
+    else
+        j2_return<float>(ctx->V, j.mat, ctx->e64.phi, eps, j.epsp, j.alpha, j.sig, j.Ct32, 0, ctx->stream);
     real_to_spec<double>(ctx, ctx->e64, j.sig, X3_MID_NONE, true, ctx->b64);
     j2_negate_add_dc(6 * ctx->S, ctx->b64, sbar_v, ctx->stream);
     ctx->launches += 2;
@@ -1732,7 +1762,8 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
                              double tol_newton, int max_newton, int max_lin, hom_j2_info *inf) {
     J2State &j = ctx->j2;
     cudaStream_t s = ctx->stream;
-    const long long n6 = 6 * ctx->V;
+    const long long n6 = 6 * ctx->V, nc = 6 * ctx->S;
+    const bool fp64 = ctx->prec == HOM_PREC_FP64;
     double En[6], Sn[6], sbar_v[6], d[6];
     macro_to_mandel(mac_t, En);
     macro_to_mandel(sbar_t, Sn);
@@ -1758,17 +1789,54 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
         ++it;
         // A_i dE = b_i (eq. galnonlin) to ||A dE - b_i|| <= tol_lin ||b_0|| (eq. galrlin)
         const double tol_i = tol_lin * b0 / nb;
-        CU(cudaMemcpyAsync(ctx->rhs, ctx->b64, sizeof(double2) * 6 * ctx->S, cudaMemcpyDeviceToDevice, s));
-        ctx->tangent_op = true;
+        const double tol_k = std::min(0.5, tol_i);
         int k = 0, st = 0;
         double est = 0.0;
-        rc = run_minres<double>(ctx, ctx->e64, tol_i < 0.5 ? tol_i : 0.5, max_lin, &k, &est, &st);
+        ctx->tangent_op = true;
+        const double2 *dx = (const double2 *)ctx->xs;
+        if (fp64) {
+            CU(cudaMemcpyAsync(ctx->rhs, ctx->b64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+            rc = run_minres<double>(ctx, ctx->e64, tol_k, max_lin, &k, &est, &st);
+            if (rc) return rc;
+            if (st == HOM_ENAN) return fail(ctx, HOM_ENAN, "J2 Newton system: MINRES breakdown");
+        } else {
+            // FP32 sweeps on the FP64 residual of the tangent system, whose
+            // FP64 value (not the FP32 recurrence's estimate, which on cells
+            // with void keeps falling below about 1e-5 while the true residual
+            // stalls) measures the solve; a sweep that raises it is taken back
+            CU(cudaMemsetAsync(j.x64, 0, sizeof(double2) * nc, s));
+            CU(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+            double tres = 1.0;
+            for (int sweep = 0; sweep <= ctx->refine && k < max_lin; ++sweep) {
+                const double floor_s = sweep == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
+                const double tol_s = std::min(0.5, std::max(kSweepTarget * tol_i / tres, floor_s));
+                spec_d2f(nc, s, ctx->r64, (float2 *)ctx->rhs);
+                ctx->launches += 1;
+                int ks = 0;
+                rc = run_minres<float>(ctx, ctx->e32, tol_s, max_lin - k, &ks, &est, &st);
+                if (rc) return rc;
+                if (st == HOM_ENAN) return fail(ctx, HOM_ENAN, "J2 Newton system: MINRES breakdown");
+                k += ks;
+                spec_f2d_acc(nc, s, (const float2 *)ctx->xs, j.x64);
+                ctx->launches += 1;
+                double tnew = 0.0;
+                rc = true_residual(ctx, j.x64, nb, &tnew);
+                if (rc) return rc;
+                if (!(tnew < tres)) {
+                    spec_f2d_acc(nc, s, (const float2 *)ctx->xs, j.x64, -1.0);
+                    ctx->launches += 1;
+                    break;
+                }
+                tres = tnew;
+                if (tres <= tol_i) break;
+            }
+            est = tres;
+            dx = j.x64;
+        }
         ctx->tangent_op = false;
-        if (rc) return rc;
-        if (st == HOM_ENAN) return fail(ctx, HOM_ENAN, "J2 Newton system: MINRES breakdown");
         lin += k;
         const bool lin_ok = est * nb <= tol_lin * b0 * (1.0 + 1e-9) || tol_i >= 0.5;
-        spec_to_real<double>(ctx, ctx->e64, (const double2 *)ctx->xs, true, 1.0, j.de);
+        spec_to_real<double>(ctx, ctx->e64, dx, true, 1.0, j.de);
         // damped step: halve until ||b|| falls
         double t = 1.0, nt = 0.0;
         for (int tries = 0; tries < 8; ++tries) {
@@ -1792,7 +1860,7 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
         if (lin_ok && rn <= tol_newton) done = true;
     }
     // history to t + dt, mean stress and strain at the accepted iterate
-    j2_return(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, nullptr, 1, s);
+    j2_return<double>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, nullptr, 1, s);
     double sm[6], em[6];
     j2_means(ctx->V, j.sig, j.partials, j.h_partials, sm, s);
     j2_means(ctx->V, j.eps, j.partials, j.h_partials, em, s);

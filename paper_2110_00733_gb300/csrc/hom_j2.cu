@@ -17,10 +17,11 @@ int j2_blocks(long long n) {
     return (int)(b < 1 ? 1 : (b > kJ2Blocks ? kJ2Blocks : b));
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kJ2Threads) k_j2_return(long long V, J2Material m, const double *__restrict__ phi,
                                                           const double *__restrict__ eps, double *epsp,
                                                           double *alpha, double *__restrict__ sig,
-                                                          double *__restrict__ Ct, int commit) {
+                                                          T *__restrict__ Ct, int commit) {
     const double lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu)), mu = m.E / (2.0 * (1.0 + m.nu));
     const double kappa = lam + 2.0 * mu / 3.0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
@@ -59,8 +60,8 @@ __global__ void __launch_bounds__(kJ2Threads) k_j2_return(long long V, J2Materia
             for (int i = 0; i < 6; ++i)
                 for (int j = 0; j < 6; ++j) {
                     const double mm = (i < 3 && j < 3) ? 1.0 : 0.0;
-                    Ct[(i * 6 + j) * V + v] = ph * (kappa * mm + 2.0 * mu * theta * ((i == j ? 1.0 : 0.0) - mm / 3.0) -
-                                                    2.0 * mu * thetab * n[i] * n[j]);
+                    Ct[(i * 6 + j) * V + v] = (T)(ph * (kappa * mm + 2.0 * mu * theta * ((i == j ? 1.0 : 0.0) - mm / 3.0) -
+                                                        2.0 * mu * thetab * n[i] * n[j]));
                 }
         }
         if (commit) {
@@ -70,15 +71,15 @@ __global__ void __launch_bounds__(kJ2Threads) k_j2_return(long long V, J2Materia
     }
 }
 
-__global__ void __launch_bounds__(kJ2Threads) k_j2_tangent_apply(long long V, const double *__restrict__ Ct,
-                                                                 const double *__restrict__ x,
-                                                                 double *__restrict__ y) {
+template <typename Tc, typename Tf>
+__global__ void __launch_bounds__(kJ2Threads) k_j2_tangent_apply(long long V, const Tc *__restrict__ Ct,
+                                                                 const Tf *__restrict__ x, Tf *__restrict__ y) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-        double xv[6];
+        Tf xv[6];
         for (int c = 0; c < 6; ++c) xv[c] = x[c * V + v];
         for (int i = 0; i < 6; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < 6; ++j) s += Ct[(i * 6 + j) * V + v] * xv[j];
+            Tf s = 0;
+            for (int j = 0; j < 6; ++j) s += (Tf)Ct[(i * 6 + j) * V + v] * xv[j];
             y[i * V + v] = s;
         }
     }
@@ -144,14 +145,23 @@ __global__ void __launch_bounds__(kJ2Threads) k_j2_means(long long V, const doub
 
 }  // namespace
 
+template <typename T>
 void j2_return(long long V, const J2Material &m, const double *phi, const double *eps, double *epsp, double *alpha,
-               double *sig, double *Ct, int commit, cudaStream_t s) {
-    k_j2_return<<<j2_blocks(V), kJ2Threads, 0, s>>>(V, m, phi, eps, epsp, alpha, sig, Ct, commit);
+               double *sig, T *Ct, int commit, cudaStream_t s) {
+    k_j2_return<T><<<j2_blocks(V), kJ2Threads, 0, s>>>(V, m, phi, eps, epsp, alpha, sig, Ct, commit);
 }
+template void j2_return<float>(long long, const J2Material &, const double *, const double *, double *, double *,
+                               double *, float *, int, cudaStream_t);
+template void j2_return<double>(long long, const J2Material &, const double *, const double *, double *, double *,
+                                double *, double *, int, cudaStream_t);
 
-void j2_tangent_apply(long long V, const double *Ct, const double *v, double *out, cudaStream_t s) {
-    k_j2_tangent_apply<<<j2_blocks(V), kJ2Threads, 0, s>>>(V, Ct, v, out);
+template <typename Tc, typename Tf>
+void j2_tangent_apply(long long V, const Tc *Ct, const Tf *v, Tf *out, cudaStream_t s) {
+    k_j2_tangent_apply<Tc, Tf><<<j2_blocks(V), kJ2Threads, 0, s>>>(V, Ct, v, out);
 }
+template void j2_tangent_apply<float, float>(long long, const float *, const float *, float *, cudaStream_t);
+template void j2_tangent_apply<double, double>(long long, const double *, const double *, double *, cudaStream_t);
+template void j2_tangent_apply<float, double>(long long, const float *, const double *, double *, cudaStream_t);
 
 void j2_add_uniform(long long V, double *eps, const double d[6], cudaStream_t s) {
     k_j2_add_uniform<<<j2_blocks(6 * V), kJ2Threads, 0, s>>>(V, eps, d[0], d[1], d[2], d[3], d[4], d[5]);

@@ -10,12 +10,15 @@ struct J2Material {
 
 // radial return at every voxel (fields 6 x V Mandel, component-major):
 // sig = phi sigma_J2(eps; epsp, alpha) and, if Ct is not null, the consistent
-// tangent (36 x V: entry (i, j) of voxel v at (6 i + j) V + v, times phi); commit != 0 writes the updated
-// plastic strain and hardening variable back into epsp and alpha
+// tangent in T (36 x V: entry (i, j) of voxel v at (6 i + j) V + v, times phi);
+// commit != 0 writes the updated plastic strain and hardening variable back
+// into epsp and alpha
+template <typename T>
 void j2_return(long long V, const J2Material &m, const double *phi, const double *eps, double *epsp, double *alpha,
-               double *sig, double *Ct, int commit, cudaStream_t s);
-// out = Ct : v at every voxel
-void j2_tangent_apply(long long V, const double *Ct, const double *v, double *out, cudaStream_t s);
+               double *sig, T *Ct, int commit, cudaStream_t s);
+// out = Ct : v at every voxel (tangent in Tc, fields and arithmetic in Tf)
+template <typename Tc, typename Tf>
+void j2_tangent_apply(long long V, const Tc *Ct, const Tf *v, Tf *out, cudaStream_t s);
 // eps[c] += d[c] at every voxel
 void j2_add_uniform(long long V, double *eps, const double d[6], cudaStream_t s);
 // b = -b over n complex values, plus sbar_v[c] at frequency 0 (component c)

@@ -2,7 +2,8 @@
 the J2 lattice material of section 5) against the FP64 oracle and against
 closed forms.
 
-Both sides run the same damped Newton method in FP64.  Where the cell has
+Both sides run the same damped Newton method in FP64 (the GPU's FP32-field
+mode differs only in solving the Newton systems in FP32).  Where the cell has
 no void (the octet with its empty voxels at 5 % of the material) the
 linearised systems are definite, the Newton iterates converge to
 tol_lin = 1e-9, tol_newton = 1e-7, and a perturbation of the inputs at
@@ -39,6 +40,9 @@ def hom():
     return h
 
 
+PRECS = {"fp64": 1, "fp32": 0}   # HOM_PREC_FP64, HOM_PREC_FP32_FIELDS
+
+
 def make(hom, phi, prec=None):
     p = hom.HOM_PREC_FP64 if prec is None else prec
     return hom.hom_create(phi.shape, np.ascontiguousarray(phi, dtype=np.float64), hom.HOM_INPUT_FRACTION_F64,
@@ -70,19 +74,27 @@ def compare(hom, ctx, cell, ref, got, where, mtol, ftol):
 
 @pytest.mark.parametrize("H", [E_M / 20, E_M / 100])
 @pytest.mark.parametrize("shape,load", [((16, 16, 16), "uniaxial"), ((12, 16, 10), "shear")])
-def test_increments_match_oracle(hom, shape, load, H):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_increments_match_oracle(hom, shape, load, H, prec):
+    """FP32 fields solve the Newton systems in FP32 (to 1e-6; Newton to
+    1e-5) while strains, history and residuals stay FP64: their accepted
+    iterates are compared with the oracle's tight ones at 2e-5 (means) and
+    1e-4 (fields)."""
     phi, _ = ri.octet(shape if len(set(shape)) > 1 else shape[0], 0.2)
     phi = 0.05 + 0.95 * phi.astype(np.float64)
     mask, path = LOADS[load]
     cell = oracle.J2Cell(phi, E_M, NU_M, SY, H)
-    with make(hom, phi) as ctx:
+    fp64 = prec == "fp64"
+    tl, tn = (TL, TN) if fp64 else (1e-6, 1e-5)
+    with make(hom, phi, PRECS[prec]) as ctx:
         hom.hom_j2_begin(ctx, SY, H)
         for Ebar in path:
             ref = cell.increment(mask, Ebar, np.zeros(6), tol_lin=TL, tol_newton=TN)
-            rc, got = hom.hom_j2_increment(ctx, Ebar, np.zeros(6), mask, tol_lin=TL, tol_newton=TN)
+            rc, got = hom.hom_j2_increment(ctx, Ebar, np.zeros(6), mask, tol_lin=tl, tol_newton=tn)
             assert ref["accepted"] and rc == hom.HOM_OK and got["accepted"]
-            assert abs(got["newton"] - ref["newton"]) <= 1
-            alpha = compare(hom, ctx, cell, ref, got, phi > 0, 1e-7, 1e-6)
+            if fp64:
+                assert abs(got["newton"] - ref["newton"]) <= 1
+            alpha = compare(hom, ctx, cell, ref, got, phi > 0, 1e-7 if fp64 else 2e-5, 1e-6 if fp64 else 1e-4)
         assert (alpha[phi > 0.5] > 0).mean() > 0.1      # the struts have yielded
 
 
@@ -102,14 +114,15 @@ def test_single_newton_steps_on_the_void_octet_match_oracle(hom):
             compare(hom, ctx, cell, ref, got, phi > 0, 2e-5, 2e-4)
 
 
-def test_plastic_increments_on_the_void_octet_meet_their_constraints(hom):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plastic_increments_on_the_void_octet_meet_their_constraints(hom, prec):
     """full increments with the default tolerances: accepted, lateral mean
     stresses zero, the prescribed e11 met, every voxel inside its yield
     surface, the struts yielded"""
     phi, _ = ri.octet(12, 0.2)
     phi = phi.astype(np.float64)
     H = E_M / 100
-    with make(hom, phi) as ctx:
+    with make(hom, phi, PRECS[prec]) as ctx:
         hom.hom_j2_begin(ctx, SY, H)
         for k in range(1, 4):
             e = -5e-3 * k
@@ -132,13 +145,15 @@ def test_plastic_increments_on_the_void_octet_meet_their_constraints(hom):
         assert np.all(np.sqrt((dev ** 2).sum(axis=0)) <= radius * (1 + 1e-8) + 1e-12 * r2)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("H", [0.0, E_M / 20])
-def test_homogeneous_uniaxial_loading_follows_the_closed_form(hom, H):
+def test_homogeneous_uniaxial_loading_follows_the_closed_form(hom, H, prec):
     """e11 prescribed, lateral means stress-free: below yield s = E e, beyond
     |s| = (sy + H |e|) / (1 + H / E) (uniaxial J2, sqrt(2/3) hardening
     convention), times phi; unloading is elastic."""
     c = 0.6
-    with make(hom, np.full((8, 8, 8), c)) as ctx:
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    with make(hom, np.full((8, 8, 8), c), PRECS[prec]) as ctx:
         hom.hom_j2_begin(ctx, SY, H)
         ey = SY / E_M
         for k in range(1, 9):
@@ -146,13 +161,13 @@ def test_homogeneous_uniaxial_loading_follows_the_closed_form(hom, H):
             rc, out = hom.hom_j2_increment(ctx, [e, 0, 0, 0, 0, 0], np.zeros(6), 0b111110)
             assert rc == hom.HOM_OK
             s = E_M * abs(e) if abs(e) <= ey else (SY + H * abs(e)) / (1 + H / E_M)
-            assert out["sigma_mean"][0] == pytest.approx(-c * s, rel=1e-9)
-            assert np.allclose(out["sigma_mean"][1:], 0, atol=1e-9 * c * s)
+            assert out["sigma_mean"][0] == pytest.approx(-c * s, rel=rel)
+            assert np.allclose(out["sigma_mean"][1:], 0, atol=rel * c * s)
         # elastic unloading by de = 1e-4 from the last state
         s_last = out["sigma_mean"][0]
         rc, out = hom.hom_j2_increment(ctx, [e + 1e-4, 0, 0, 0, 0, 0], np.zeros(6), 0b111110)
         assert rc == hom.HOM_OK
-        assert out["sigma_mean"][0] == pytest.approx(s_last + c * E_M * 1e-4, rel=1e-9)
+        assert out["sigma_mean"][0] == pytest.approx(s_last + c * E_M * 1e-4, rel=rel)
 
 
 def test_elastic_increment_equals_the_mixed_solve(hom):
@@ -196,7 +211,8 @@ def test_linear_solves_after_a_plastic_increment_are_unchanged(hom):
 
 def test_j2_rejections(hom):
     phi = np.full((8, 8, 8), 0.5)
-    with make(hom, phi, hom.HOM_PREC_FP32_FIELDS) as ctx:
+    with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F64, E_M, NU_M,
+                        solver=hom.HOM_SOLVER_MODBFFT_CG) as ctx:
         with pytest.raises(hom.HomError) as e:
             hom.hom_j2_begin(ctx, SY, 0.0)
         assert e.value.code == hom.HOM_EINVAL
