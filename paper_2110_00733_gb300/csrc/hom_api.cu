@@ -1807,8 +1807,9 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
             CU(cudaMemsetAsync(j.x64, 0, sizeof(double2) * nc, s));
             CU(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
             double tres = 1.0;
+            bool retried = false;
             for (int sweep = 0; sweep <= ctx->refine && k < max_lin; ++sweep) {
-                const double floor_s = sweep == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
+                const double floor_s = (sweep == 0 && !retried) ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
                 const double tol_s = std::min(0.5, std::max(kSweepTarget * tol_i / tres, floor_s));
                 spec_d2f(nc, s, ctx->r64, (float2 *)ctx->rhs);
                 ctx->launches += 1;
@@ -1825,6 +1826,15 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
                 if (!(tnew < tres)) {
                     spec_f2d_acc(nc, s, (const float2 *)ctx->xs, j.x64, -1.0);
                     ctx->launches += 1;
+                    // nothing gained yet: once more with the reduction of a
+                    // later sweep, where the FP32 estimate still holds
+                    if (sweep == 0 && !retried) {
+                        retried = true;
+                        sweep = -1;
+                        // the step is zero again: its residual is b
+                        CU(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+                        continue;
+                    }
                     break;
                 }
                 tres = tnew;
