@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation",
-                             "smoothing", "j2"],
+                             "smoothing", "j2", "j2curve"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
                          "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
@@ -540,6 +540,35 @@ def run_j2(args):
     return 0
 
 
+def run_j2curve(args):
+    """Compression curves of elastoplastic octets (section 5): relative
+    densities 10, 20 and 30 %, uniaxial compression to e11 = -10 % in 20
+    increments with free lateral faces, hardening E/100, FP32 fields, default
+    Newton tolerances (tol_newton 5e-3 as in section 5), max_newton 40.  One
+    JSON line per increment, printed as it completes.  The cell is 48^3
+    unless --n asks for a smaller one."""
+    import numpy as np
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    n = min(args.n, 48)
+    sy, H = 70e6, E_M / 100
+    for rho in (0.10, 0.20, 0.30):
+        phi, _ = ri.octet(n, rho)
+        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M) as ctx:
+            hom.hom_j2_begin(ctx, sy, H)
+            for k in range(1, 21):
+                e = -0.005 * k
+                rc, info = hom.hom_j2_increment(ctx, [e, 0, 0, 0, 0, 0], np.zeros(6), 0b111110, max_newton=40)
+                print(json.dumps({"workload": f"j2_curve_octet_{n}^3_e11_to_-0.10_in_20_H=E/100_fp32_fields",
+                                  "rho": rho, "e11": e, "rc": rc, "sigma11_pa": float(info["sigma_mean"][0]),
+                                  "newton": info["newton"], "linear": info["linear"],
+                                  "ms": info["time_ms"]}), flush=True)
+    return 0
+
+
 def run_ablation(args):
     """Krylov solver and frequency scheme (section 2.1): MINRES and CG on the
     Galerkin system, rotated and continuous frequencies, on octet cells with
@@ -708,6 +737,8 @@ def main():
         return run_smoothing(args)
     if args.workload == "j2":
         return run_j2(args)
+    if args.workload == "j2curve":
+        return run_j2curve(args)
     if args.workload == "modbfft":
         return run_modbfft(args)
     return run_ours(args)
