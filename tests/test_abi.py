@@ -21,7 +21,7 @@ def lib():
     return hom.load_library()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_solver_calls():
     syms = declared_symbols()
     for s in ["hom_create", "hom_solve", "hom_effective_stiffness", "hom_fields", "hom_destroy"]:
         assert s in syms
