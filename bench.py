@@ -508,7 +508,8 @@ def run_j2(args):
            "workload": f"j2_octet_{n}^3_rho{args.rho:.2f}_uniaxial_e11_4x-2.5e-3_H=E/100"}
     for name, prec in (("fp32_fields", hom.HOM_PREC_FP32_FIELDS), ("fp64", hom.HOM_PREC_FP64)):
         run = {"increments": []}
-        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, precision=prec) as ctx:
+        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, precision=prec,
+                            host_loop=args.host_loop) as ctx:
             hom.hom_j2_begin(ctx, sy, H)
             hom.hom_j2_increment(ctx, [-1e-4, 0, 0, 0, 0, 0], np.zeros(6), 0b111110)   # warm-up (elastic)
             hom.hom_j2_begin(ctx, sy, H)
@@ -557,7 +558,8 @@ def run_j2curve(args):
     sy, H = 70e6, E_M / 100
     for rho in (0.10, 0.20, 0.30):
         phi, _ = ri.octet(n, rho)
-        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M) as ctx:
+        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+                            host_loop=args.host_loop) as ctx:
             hom.hom_j2_begin(ctx, sy, H)
             for k in range(1, 21):
                 e = -0.005 * k
