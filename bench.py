@@ -154,6 +154,20 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(dist, t_local, units_local, device):
+    """(max over ranks of the timed-region seconds, sum over ranks of the
+    work units): the whole-job throughput is units / seconds.  Without a
+    process group the local values."""
+    if dist is None:
+        return float(t_local), float(units_local)
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -291,13 +305,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     t_local = ms / 1e3
-    if dist:
-        t = torch.tensor([t_local], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = ws * V * iters / t_max
+    t_max, units = reduce_over_ranks(dist, t_local, V * iters, "cuda")
+    value = units / t_max
 
     # per-kernel times (CUDA events on the library's stream) for the roofline
     ktimes = hom.hom_time_kernels(ctx, reps=20)

@@ -1,0 +1,79 @@
+"""Host logic of bench.py's multi-rank run on CPU: two gloo ranks (spawned
+processes, 127.0.0.1) that time different regions and process different
+amounts of work reduce to the slowest rank's time and the summed work; the
+reference arm prints on rank 0 only."""
+import io
+import contextlib
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ws, r, local = bench.dist_env()
+        t, u = bench.reduce_over_ranks(dist, [1.5, 2.25][rank], [1000.0, 3000.0][rank], "cpu")
+        dist.barrier()
+        q.put((rank, ws, r, local, t, u))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_max_time_and_summed_work():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, (r0, ws, r, local, t, u) in enumerate(got):
+        assert (r0, ws, r, local) == (rank, 2, rank, rank)
+        assert t == 2.25 and u == 4000.0
+
+
+def test_single_process_reduction_is_the_identity():
+    import bench
+    assert bench.reduce_over_ranks(None, 0.5, 123.0, "cpu") == (0.5, 123.0)
+
+
+@pytest.mark.parametrize("rank", [0, 1])
+def test_reference_arm_prints_one_line_on_rank_zero_only(monkeypatch, rank):
+    import json
+    import bench
+    monkeypatch.setenv("RANK", str(rank))
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--n", "8",
+                                      "--steps", "1", "--warmup", "0"])
+    args = bench.parse()
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        assert bench.run_reference(args) == 0
+    lines = out.getvalue().splitlines()
+    if rank:
+        assert lines == []
+    else:
+        assert len(lines) == 1
+        line = json.loads(lines[0])
+        assert line["impl"] == "reference" and line["value"] > 0
+        assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["value"] == line["value"]
