@@ -551,30 +551,31 @@ def run_j2(args):
 
 
 def run_j2curve(args):
-    """Compression curves of elastoplastic octets (section 5): relative
-    densities 10, 20 and 30 %, uniaxial compression to e11 = -10 % in 20
-    increments with free lateral faces, hardening E/100, FP32 fields, default
-    Newton tolerances (tol_newton 5e-3 as in section 5), max_newton 40.  One
-    JSON line per increment, printed as it completes.  The cell is 48^3
-    unless --n asks for a smaller one."""
+    """Compression curves of section 5: octets of relative density 10, 20
+    and 30 % at about 15 voxels per strut diameter (grids 160, 108 and 90;
+    --n caps them), the lattice material of sections 4 and 5 (PA12: E =
+    1.7 GPa, nu = 0.4; J2 perfect plasticity, yield stress 70 MPa), uniaxial
+    compression to e11 = -10 % in 20 increments with free lateral faces,
+    Newton tolerance 5e-3, FP32 fields.  One JSON line per increment,
+    printed as it completes."""
     import numpy as np
     import torch
     from paper_2110_00733_gb300 import build, hom
     build.build()
     import rve_inputs as ri
     torch.cuda.set_device(0)
-    n = min(args.n, 48)
-    sy, H = 70e6, E_M / 100
-    for rho in (0.10, 0.20, 0.30):
+    e_pa12, nu_pa12, sy = 1.7e9, 0.4, 70e6
+    for rho, n_full in ((0.10, 160), (0.20, 108), (0.30, 90)):
+        n = min(args.n, n_full)
         phi, _ = ri.octet(n, rho)
-        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M,
+        with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, e_pa12, nu_pa12,
                             host_loop=args.host_loop) as ctx:
-            hom.hom_j2_begin(ctx, sy, H)
+            hom.hom_j2_begin(ctx, sy, 0.0)
             for k in range(1, 21):
                 e = -0.005 * k
                 rc, info = hom.hom_j2_increment(ctx, [e, 0, 0, 0, 0, 0], np.zeros(6), 0b111110, max_newton=40)
-                print(json.dumps({"workload": f"j2_curve_octet_{n}^3_e11_to_-0.10_in_20_H=E/100_fp32_fields",
-                                  "rho": rho, "e11": e, "rc": rc, "sigma11_pa": float(info["sigma_mean"][0]),
+                print(json.dumps({"workload": f"j2_curve_octet_{n}^3_rho{rho:.2f}_pa12_perfect_plasticity_fp32_fields",
+                                  "e11": e, "rc": rc, "sigma11_pa": float(info["sigma_mean"][0]),
                                   "newton": info["newton"], "linear": info["linear"],
                                   "ms": info["time_ms"]}), flush=True)
     return 0
