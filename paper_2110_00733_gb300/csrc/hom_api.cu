@@ -1696,6 +1696,25 @@ static long long j2_bytes(const hom_ctx *ctx) {
                                         : (long long)sizeof(float) * 48 * V + (long long)sizeof(double2) * 6 * ctx->S);
 }
 
+static int j2_alloc(hom_ctx *ctx) {
+    J2State &j = ctx->j2;
+    const long long n6 = 6 * ctx->V;
+    double **f6[] = {&j.eps, &j.eps_t, &j.etry, &j.epsp, &j.sig, &j.de};
+    for (double **p : f6) CU(cudaMalloc(p, sizeof(double) * n6));
+    CU(cudaMalloc(&j.alpha, sizeof(double) * ctx->V));
+    if (ctx->prec == HOM_PREC_FP64) {
+        CU(cudaMalloc(&j.Ct, sizeof(double) * 36 * ctx->V));
+    } else {
+        CU(cudaMalloc(&j.Ct32, sizeof(float) * 36 * ctx->V));
+        CU(cudaMalloc(&j.sig32, sizeof(float) * n6));
+        CU(cudaMalloc(&j.de32, sizeof(float) * n6));
+        CU(cudaMalloc(&j.x64, sizeof(double2) * 6 * ctx->S));
+    }
+    CU(cudaMalloc(&j.partials, sizeof(double) * 6 * kJ2Blocks));
+    CU(cudaMallocHost(&j.h_partials, sizeof(double) * 6 * kJ2Blocks));
+    return HOM_OK;
+}
+
 int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening) {
     if (!ctx) return fail(nullptr, HOM_EINVAL, "null context");
     if (ctx->solver != HOM_SOLVER_GALERKIN_MINRES)
@@ -1706,19 +1725,11 @@ int hom_j2_begin(hom_ctx *ctx, double yield_stress, double hardening) {
     J2State &j = ctx->j2;
     const long long n6 = 6 * ctx->V;
     if (!j.active) {
-        double **f6[] = {&j.eps, &j.eps_t, &j.etry, &j.epsp, &j.sig, &j.de};
-        for (double **p : f6) CU(cudaMalloc(p, sizeof(double) * n6));
-        CU(cudaMalloc(&j.alpha, sizeof(double) * ctx->V));
-        if (ctx->prec == HOM_PREC_FP64) {
-            CU(cudaMalloc(&j.Ct, sizeof(double) * 36 * ctx->V));
-        } else {
-            CU(cudaMalloc(&j.Ct32, sizeof(float) * 36 * ctx->V));
-            CU(cudaMalloc(&j.sig32, sizeof(float) * n6));
-            CU(cudaMalloc(&j.de32, sizeof(float) * n6));
-            CU(cudaMalloc(&j.x64, sizeof(double2) * 6 * ctx->S));
+        const int rc = j2_alloc(ctx);
+        if (rc) {
+            j2_free(ctx);
+            return rc;
         }
-        CU(cudaMalloc(&j.partials, sizeof(double) * 6 * kJ2Blocks));
-        CU(cudaMallocHost(&j.h_partials, sizeof(double) * 6 * kJ2Blocks));
         ctx->workspace += j2_bytes(ctx);
         j.active = true;
     }
