@@ -265,7 +265,8 @@ typedef struct {
  * ||eps^i - eps^t||_inf (eq. galrnewton) after a step whose linear solve met
  * tol_lin; the plastic history then moves to t + dt.  When max_newton runs
  * out the last iterate is taken all the same and the status says so.
- * Returns HOM_OK, HOM_NOT_CONVERGED or a negative error. */
+ * Returns HOM_OK, HOM_NOT_CONVERGED or a negative error, after which the
+ * history is that of t (the increment is not applied). */
 int hom_j2_increment(hom_ctx *ctx, const double macro_strain[6], const double macro_stress[6], int stress_mask,
                      double tol_lin, double tol_newton, int max_newton, int max_lin, hom_j2_info *info);
 

@@ -89,6 +89,7 @@ struct J2State {
     double *partials = nullptr;
     double *h_partials = nullptr;   // pinned
     double Ebar[6] = {0, 0, 0, 0, 0, 0};   // macro strain of the last increment (Mandel)
+    bool moved = false;        // the running increment has changed eps (eps_t holds t)
 };
 
 }  // namespace
@@ -1783,9 +1784,11 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
         sbar_v[c] = kl ? (double)ctx->V * Sn[c] / ctx->E : 0.0;   // F{S_bar} at xi = 0, units of E
         d[c] = kl ? 0.0 : En[c] - j.Ebar[c];
     }
+    j.moved = false;
     CU(cudaEventRecord(ctx->ev0, s));
     CU(cudaMemcpyAsync(j.eps_t, j.eps, sizeof(double) * n6, cudaMemcpyDeviceToDevice, s));
     // predictor: the macro strain change added uniformly
+    j.moved = true;
     j2_add_uniform(ctx->V, j.eps, d, s);
     ctx->launches += 1;
     double nb = 0.0;
@@ -1924,6 +1927,13 @@ int hom_j2_increment(hom_ctx *ctx, const double macro_strain[6], const double ma
                                max_lin, &inf);
     ctx->tangent_op = false;
     if (rc) {
+        // the history is written only at the end of an increment: putting
+        // the strain at t back leaves the cell as it was
+        if (ctx->j2.moved) {
+            cudaMemcpyAsync(ctx->j2.eps, ctx->j2.eps_t, sizeof(double) * 6 * ctx->V, cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+            cudaStreamSynchronize(ctx->stream);
+        }
         inf.status = rc;
         if (info) *info = inf;
         return rc;
