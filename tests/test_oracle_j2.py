@@ -100,3 +100,39 @@ def test_plastic_increments_on_an_octet_meet_their_constraints():
         assert np.all(np.abs(out["sigma_mean"][1:]) <= 1e-4 * s11)
         assert out["eps_mean"][0] == pytest.approx(e, rel=1e-10)
     assert (cell.alpha[phi > 0.5] > 0).mean() > 0.5
+
+
+@pytest.mark.parametrize("H", [0.0, E_M / 50])
+def test_consistent_tangent_eigen_structure(H):
+    """For associative J2 with isotropic hardening the consistent tangent of
+    the radial return is symmetric; in a plastic state it maps the flow
+    direction n (the unit deviatoric stress) to phi 2 mu H / (3 mu + H) n,
+    the hardening stiffness of the continuum law (zero for perfect
+    plasticity), and the volumetric direction m to phi 3 kappa m (J2 flow is
+    isochoric); in an elastic state it is phi C_m."""
+    lam = E_M * NU_M / ((1 + NU_M) * (1 - 2 * NU_M))
+    mu = E_M / (2 * (1 + NU_M))
+    kappa = lam + 2 * mu / 3
+    rng = np.random.default_rng(7)
+    seen = {True: 0, False: 0}
+    for k in range(40):
+        scale = 3e-3 if k % 2 else 2e-4                # plastic and elastic states
+        eps = rng.standard_normal(6) * scale
+        epsp = np.zeros(6)
+        phi = 0.3 + 0.7 * rng.random()
+        sig, Ct, _, a1 = oracle.j2_point(E_M, NU_M, SY, H, phi, eps, epsp, 0.0)
+        assert np.abs(Ct - Ct.T).max() <= 1e-14 * np.abs(Ct).max()
+        assert np.allclose(Ct @ M, phi * 3 * kappa * M, rtol=0, atol=1e-12 * phi * kappa)
+        plastic = a1 > 0
+        seen[plastic] += 1
+        if plastic:
+            s = sig / phi
+            dev = s - s[:3].mean() * M
+            n = dev / np.linalg.norm(dev)
+            assert np.allclose(Ct @ n, phi * 2 * mu * H / (3 * mu + H) * n, rtol=0, atol=1e-12 * phi * mu)
+        else:
+            Cm = np.zeros((6, 6))
+            Cm[:3, :3] = lam
+            Cm += 2 * mu * np.eye(6)
+            assert np.allclose(Ct, phi * Cm, rtol=0, atol=1e-12 * phi * mu)
+    assert seen[True] > 5 and seen[False] > 5
