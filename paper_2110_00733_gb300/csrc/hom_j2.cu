@@ -2,7 +2,9 @@
 // hardening for the Newton extension of the Galerkin scheme (section 2.1.1):
 // the radial return and its consistent tangent (Simo & Hughes 1998, section
 // 3.3) at every voxel, stress and tangent times phi (section 3.2), and the
-// point-wise helpers of the Newton loop.  FP64 throughout.
+// point-wise helpers of the Newton loop.  The return map and the helpers run
+// in FP64; the tangent is stored in FP64, or in FP32 for the FP32 MINRES
+// solves of the Newton systems, and applied in the precision of the field.
 #include <cuda_runtime.h>
 
 #include "hom_j2.h"
@@ -60,8 +62,9 @@ __global__ void __launch_bounds__(kJ2Threads) k_j2_return(long long V, J2Materia
             for (int i = 0; i < 6; ++i)
                 for (int j = 0; j < 6; ++j) {
                     const double mm = (i < 3 && j < 3) ? 1.0 : 0.0;
-                    Ct[(i * 6 + j) * V + v] = (T)(ph * (kappa * mm + 2.0 * mu * theta * ((i == j ? 1.0 : 0.0) - mm / 3.0) -
-                                                        2.0 * mu * thetab * n[i] * n[j]));
+                    const double cij = kappa * mm + 2.0 * mu * theta * ((i == j ? 1.0 : 0.0) - mm / 3.0) -
+                                       2.0 * mu * thetab * n[i] * n[j];
+                    Ct[(i * 6 + j) * V + v] = (T)(ph * cij);
                 }
         }
         if (commit) {
