@@ -218,6 +218,20 @@ def cpu_oracle_sample(phi64, iters):
     return s["iterations"], dt, oracle.num_threads()
 
 
+def j2_cpu_sample(phi64, E, nu, sy, H, e11, max_lin):
+    """The oracle's J2 Newton step on the same cell: the first increment to
+    e11 with lateral faces free, one Newton iteration whose MINRES solve is
+    capped at max_lin iterations (its right-hand side, line search and
+    history update included).  Returns (MINRES iterations, seconds, threads)."""
+    import oracle
+    cell = oracle.J2Cell(phi64, E, nu, sy, H)
+    t0 = time.perf_counter()
+    out = cell.increment(0b111110, [e11, 0, 0, 0, 0, 0], np.zeros(6), tol_lin=1e-30, max_newton=1,
+                         max_lin=max_lin)
+    dt = time.perf_counter() - t0
+    return out["linear"], dt, oracle.num_threads()
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -540,6 +554,11 @@ def run_j2(args):
                         "gpu_launches": hom.hom_kernel_launches(ctx) - launches0,
                         "yielded_fraction_of_struts": float((alpha[phi > 0.5] > 0).mean())})
         out[name] = run
+    lin_cpu, dt_cpu, cores = j2_cpu_sample(phi.astype(np.float64), E_M, NU_M, sy, H, -2.5e-3, 20)
+    out["cpu_baseline"] = {"value": n ** 3 * lin_cpu / dt_cpu, "unit": "voxel-iter/s", "cores": cores,
+                           "kind": "oracle",
+                           "sample": f"{n}^3, first increment, one Newton iteration with {lin_cpu} FP64 "
+                                     f"MINRES iterations plus residuals and line search ({dt_cpu:.1f} s)"}
     # the line's value: the faster of the runs whose increments all converged
     ok = [k for k in ("fp32_fields", "fp64") if all(i["rc"] == 0 for i in out[k]["increments"])]
     best = min(ok, key=lambda k: out[k]["ms_total"]) if ok else "fp64"

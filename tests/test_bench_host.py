@@ -1,7 +1,8 @@
-"""Host logic of bench.py's multi-rank run on CPU: two gloo ranks (spawned
-processes, 127.0.0.1) that time different regions and process different
-amounts of work reduce to the slowest rank's time and the summed work; the
-reference arm prints on rank 0 only."""
+"""Host logic of bench.py, on CPU: two gloo ranks (spawned processes,
+127.0.0.1) that time different regions and process different amounts of
+work reduce to the slowest rank's time and the summed work; the reference
+arm prints on rank 0 only; the bounded oracle sample beside the j2 line
+counts what it ran."""
 import io
 import contextlib
 import os
@@ -77,3 +78,14 @@ def test_reference_arm_prints_one_line_on_rank_zero_only(monkeypatch, rank):
         line = json.loads(lines[0])
         assert line["impl"] == "reference" and line["value"] > 0
         assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["value"] == line["value"]
+
+
+def test_j2_cpu_sample_counts_the_oracle_minres_iterations():
+    """the bounded oracle sample beside the j2 bench line runs one Newton
+    iteration with at most max_lin MINRES iterations"""
+    import numpy as np
+    import bench
+    import rve_inputs as ri
+    phi, _ = ri.octet(12, 0.2)
+    lin, dt, cores = bench.j2_cpu_sample(phi.astype(np.float64), 110e9, 0.3, 70e6, 1.1e9, -2.5e-3, 7)
+    assert lin == 7 and dt > 0 and cores >= 1
