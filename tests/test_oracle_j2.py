@@ -136,3 +136,30 @@ def test_consistent_tangent_eigen_structure(H):
             Cm += 2 * mu * np.eye(6)
             assert np.allclose(Ct, phi * Cm, rtol=0, atol=1e-12 * phi * mu)
     assert seen[True] > 5 and seen[False] > 5
+
+
+def test_section5_compression_curve_with_the_paper_material():
+    """Section 5's test on a dense octet (rho = 0.3, 12^3): PA12 (E = 1.7
+    GPa, nu = 0.4), perfect plasticity at 70 MPa, compression to -10 % in 20
+    increments with stress-free lateral faces.  Every increment is accepted;
+    the first ones are elastic, so the stress is proportional to the strain
+    with the slope of the pinned linear mixed solve; past yield the curve
+    flattens (a plastic regime with a small apparent hardening rate)."""
+    E, nu, sy = 1.7e9, 0.4, 70e6
+    phi, _ = ri.octet(12, 0.3)
+    phi = phi.astype(np.float64)
+    cell = oracle.J2Cell(phi, E, nu, sy, 0.0)
+    s11 = []
+    for k in range(1, 21):
+        out = cell.increment(0b111110, [-0.005 * k, 0, 0, 0, 0, 0], np.zeros(6))
+        assert out["accepted"]
+        assert np.all(np.abs(out["sigma_mean"][1:]) <= 1e-4 * abs(out["sigma_mean"][0]))
+        s11.append(out["sigma_mean"][0])
+    lin = oracle.solve_mixed(phi, E, nu, 1, 0b111110, [-0.005, 0, 0, 0, 0, 0], np.zeros(6), tol=1e-10)
+    assert s11[0] == pytest.approx(lin["sigma_mean"][0], rel=1e-5)
+    assert s11[1] == pytest.approx(2 * s11[0], rel=1e-5)
+    assert all(b < a for a, b in zip(s11, s11[1:]))                  # monotone in compression
+    elastic_slope = s11[0] / -0.005
+    final_slope = (s11[-1] - s11[-2]) / -0.005
+    assert 0 < final_slope < 0.3 * elastic_slope
+    assert (cell.alpha[phi > 0.5] > 0).any()
