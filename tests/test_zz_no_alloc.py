@@ -1,15 +1,20 @@
 """hom_apply_noalloc: the allocation-free entry point for callers that must
-not call cudaMalloc (a thread recording a CUDA graph by stream capture, or an
-application whose device memory belongs to its own pool).
+not call cudaMalloc (an application whose device memory belongs to its own
+pool or is reserved up front, or a latency-critical loop in which cudaMalloc,
+which may synchronise the device, is not acceptable).
 
 Checked through the C ABI against the existing hom_apply entry point, within
 the FP32 parity tolerance, on two calls in a row (the scratch arrays are
-shared by every call and keep the previous call's contents).  This file is
+shared by every call and keep the previous call's contents), and against the
+FP64 oracle's A(eps) of eq. (linearOp) for both derivative schemes, on the
+legacy default stream and on a side stream.  The call only enqueues its
+kernels, so each check synchronises before reading the output.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test."""
 import numpy as np
 import pytest
 
+import oracle
 import rve_inputs as ri
 from gpu_util import FP32_TOL, rel_maxerr
 
@@ -39,10 +44,38 @@ def test_noalloc_matches_hom_apply_twice(hom):
             ref = hom.hom_apply(ctx, f)
             eps = torch.tensor(f, device="cuda")
             out = torch.full_like(eps, float("nan"))
+            torch.cuda.synchronize()
             hom.hom_apply_noalloc(shape, phi_d, eps, out, E=E_M, nu=NU_M)
+            torch.cuda.synchronize()
             got = out.cpu().numpy()
             assert np.all(np.isfinite(got))
             assert rel_maxerr(got, ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+@pytest.mark.parametrize("deriv", [0, 1])
+@pytest.mark.parametrize("shape", [(32, 24, 20), (64, 16, 32)])
+def test_noalloc_matches_oracle(hom, shape, deriv, side_stream):
+    """A(eps) against the oracle; (64, 16, 32) runs the register FFT of length
+    64 on n1 and 32 on n3, (32, 24, 20) the generic mixed-radix engine on n2."""
+    import torch
+    phi = ri.random_phi(shape, seed=31).astype(np.float32)
+    f = ri.random_field(shape, seed=32)
+    ref = oracle.apply(phi.astype(np.float64), 1.0, NU_M, deriv, f)   # units of E, like the entry point
+    phi_d = torch.tensor(phi, device="cuda")
+    eps = torch.tensor(f, dtype=torch.float32, device="cuda")
+    out = torch.full_like(eps, float("nan"))
+    torch.cuda.synchronize()
+    if side_stream:
+        s = torch.cuda.Stream()
+        hom.hom_apply_noalloc(shape, phi_d, eps, out, E=E_M, nu=NU_M, derivative=deriv, stream=s.cuda_stream)
+        s.synchronize()
+    else:
+        hom.hom_apply_noalloc(shape, phi_d, eps, out, E=E_M, nu=NU_M, derivative=deriv)
+        torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert rel_maxerr(got, ref) <= FP32_TOL
 
 
 def test_noalloc_rejects_grids_beyond_the_limit(hom):
