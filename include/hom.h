@@ -43,7 +43,8 @@
  *   - Stiffness, stress and the outputs of hom_apply / hom_rhs: hom_apply and
  *     hom_rhs use C_m / E (units of E); hom_solve_info.sigma_mean,
  *     hom_effective_stiffness and hom_fields' stress are in the units of E.
- *   - Entry points return after their device work has completed.
+ *   - Entry points return after their device work has completed (except
+ *     hom_apply_noalloc, which only enqueues it).
  *   - Return value: HOM_OK (0), a positive warning (result valid), or a
  *     negative error, in which case no output buffer has been written;
  *     hom_last_error() then describes the failure.
@@ -324,11 +325,12 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* A(eps) of hom_apply for a small cell, allocating no device memory.  The
  * paper has no counterpart: this is a calling convention for callers that
- * must not call cudaMalloc -- a thread recording a CUDA graph by stream
- * capture (cudaMalloc is not permitted while capturing and may synchronise
- * the device), or an application whose device memory belongs to its own pool
- * and which forbids stray allocations.  hom_create allocates its workspace,
- * so those callers use this entry point instead.
+ * must not call cudaMalloc -- an application whose device memory belongs to
+ * its own pool or is reserved up front (a framework's caching allocator, a
+ * real-time or embedded system that forbids allocations after start-up), or
+ * a latency-critical loop in which cudaMalloc, which may synchronise the
+ * device, is not acceptable.  hom_create allocates its workspace, so those
+ * callers use this entry point instead.
  *   grid[3]     n1, n2, n3, each in [2, 64] and 2^a 3^b 5^c, with
  *               n1 n2 n3 <= 32768 (for example 32^3); larger grids give
  *               HOM_EUNSUPPORTED_GRID.
@@ -336,15 +338,20 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
  *   E, nu       as hom_create; the operator uses C_m / E (units of E).
  *   derivative  HOM_DERIV_CONTINUOUS or HOM_DERIV_ROTATED.
  *   eps, out    device pointers, 6 x V floats, MANDEL fields; FP32.
- *   stream      cudaStream_t (NULL: the legacy default stream); the call
- *               returns after synchronising it.
+ *   stream      cudaStream_t (NULL: the legacy default stream).  Unlike the
+ *               other entry points, the call only enqueues its kernels on
+ *               this stream and returns without waiting for them: the caller
+ *               synchronises the stream (or orders its later work after it)
+ *               before reading out.
  * The work spectrum and the FFT tables live in fixed file-scope device arrays
  * (about 1.6 MB, held on every GPU that loads the library until the process
  * exits).  The first call on a device looks up their device addresses
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the arrays: calls whose device
- * work overlaps in time race and must not be issued.  Nothing is kept
- * between calls.  Errors: HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ECUDA, with
+ * before any stream capture.  All calls share the arrays and each call
+ * rewrites what it reads: calls whose device work overlaps in time (on two
+ * streams, or two host threads) race and must not be issued.  Errors:
+ * HOM_EINVAL, HOM_EUNSUPPORTED_GRID, HOM_ECUDA (launch failures, or a CUDA
+ * error already pending before the call, which is left pending), with
  * hom_last_error(NULL) describing them. */
 int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, int derivative,
                       const float *eps, float *out, void *stream);

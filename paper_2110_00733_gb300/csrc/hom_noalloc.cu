@@ -1,14 +1,13 @@
 // hom_noalloc.cu -- hom_apply_noalloc: A(eps) for small cells without any
 // device allocation.
 //
-// Who needs this: callers that must not call cudaMalloc.  One example is a
-// host thread that is recording a CUDA graph by stream capture: cudaMalloc is
-// not a stream operation, is not permitted while capturing, and may
-// synchronise the device.  Another is an application whose device memory is
-// owned by its own pool (a framework's caching allocator, a real-time system
-// that reserves everything up front) and that does not allow stray device
-// allocations.  hom_create allocates its workspace, so those callers cannot
-// use it.
+// Who needs this: callers that must not call cudaMalloc.  An application whose
+// device memory is owned by its own pool (a framework's caching allocator, a
+// real-time or embedded system that reserves all of its memory at start-up
+// and forbids allocations afterwards) cannot let a library allocate behind
+// its back; and in a latency-critical loop cudaMalloc, which may synchronise
+// the device, is not acceptable either.  hom_create allocates its workspace,
+// so those callers cannot use it.
 //
 // Here the work spectrum and the FFT / frequency tables live in file-scope
 // __device__ arrays of fixed size.  Every GPU that loads the library holds
@@ -19,10 +18,15 @@
 // device work overlaps (for example on two streams) race with each other.
 // Nothing needs to start at zero: each call rewrites the tables and every
 // spectrum entry it reads.
+//
+// The call only enqueues its kernels on the caller's stream and returns; the
+// caller synchronises that stream (or orders later work after it) before
+// reading `out`.
 #include <math.h>
 
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/hom.h"
 #include "hom_internal.h"
@@ -100,18 +104,32 @@ bool radices(int n, AxisPlan &p) {
 
 int setup_device(int dev, DevicePtrs **out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (dev < 0 || dev >= kMaxDevices) return HOM_EINVAL;
+    if (dev < 0 || dev >= kMaxDevices) {
+        hom_set_error("hom_apply_noalloc: device ordinal beyond the 64 devices this entry point serves");
+        return HOM_EINVAL;
+    }
     DevicePtrs &d = g_dev[dev];
     if (!d.ready) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch_spec) != cudaSuccess) return HOM_ECUDA;
-        d.spec = static_cast<float2 *>(p);
-        p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch_tab) != cudaSuccess) return HOM_ECUDA;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch_spec);
+        if (e == cudaSuccess) {
+            d.spec = static_cast<float2 *>(p);
+            p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_scratch_tab);
+        }
+        if (e != cudaSuccess) {
+            hom_set_error((std::string("hom_apply_noalloc: device set-up (cudaGetSymbolAddress) failed: ") +
+                           cudaGetErrorString(e)).c_str());
+            return HOM_ECUDA;
+        }
         d.tab = static_cast<float2 *>(p);
         Geometry g{};
         Launch<float>::table_init(g);   // shared-memory limits of the pass kernels
-        if (cudaGetLastError() != cudaSuccess) return HOM_ECUDA;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            hom_set_error((std::string("hom_apply_noalloc: device set-up failed: ") + cudaGetErrorString(e)).c_str());
+            return HOM_ECUDA;
+        }
         d.ready = true;
     }
     *out = &d;
@@ -149,12 +167,18 @@ int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, 
         hom_set_error("hom_apply_noalloc: no CUDA device");
         return HOM_ECUDA;
     }
+    // an error left pending by the caller's own earlier work is reported as
+    // such (and left pending), so that it is neither taken for this call's
+    // nor cleared
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        hom_set_error((std::string("hom_apply_noalloc: a CUDA error was already pending before the call: ") +
+                       cudaGetErrorString(pending)).c_str());
+        return HOM_ECUDA;
+    }
     DevicePtrs *d = nullptr;
     int rc = setup_device(dev, &d);
-    if (rc) {
-        hom_set_error("hom_apply_noalloc: device set-up (cudaGetSymbolAddress) failed");
-        return rc;
-    }
+    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     g.n1 = grid[0];
     g.n2 = grid[1];
@@ -234,8 +258,8 @@ int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, 
     Launch<float>::x1(g, st, 0, spec, spec, nullptr, nullptr, nullptr);
     Launch<float>::x2(g, st, 1, spec, nullptr);
     Launch<float>::x3(g, st, X3_IN_SPEC, spec, X3_MID_NONE, lam, mu, nullptr, 1.0, X3_OUT_REAL, out, phi, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // launch errors only: the call does not wait for its kernels
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         hom_set_error(cudaGetErrorString(e));
         return HOM_ECUDA;

@@ -437,10 +437,14 @@ def hom_last_error(ctx: Context | None = None) -> str:
 
 def hom_apply_noalloc(grid, phi, eps, out, E=1.0, nu=0.3, derivative=HOM_DERIV_ROTATED, stream=None):
     """A(eps) for a small cell without device allocation; phi, eps, out are
-    torch CUDA tensors (float32) on the current device."""
+    torch CUDA tensors (float32) on the current device.  stream: a raw
+    cudaStream_t handle (int, e.g. torch.cuda.Stream().cuda_stream) or None
+    for the legacy default stream.  The call only enqueues the work: the
+    caller synchronises the stream before reading out."""
     lib = load_library()
     g = (ctypes.c_int * 3)(*[int(v) for v in grid])
-    rc = lib.hom_apply_noalloc(g, _ptr(phi), float(E), float(nu), int(derivative), _ptr(eps), _ptr(out), stream)
+    rc = lib.hom_apply_noalloc(g, _ptr(phi), float(E), float(nu), int(derivative), _ptr(eps), _ptr(out),
+                               None if stream is None else ctypes.c_void_p(int(stream)))
     _check(None, rc)
     return out
 

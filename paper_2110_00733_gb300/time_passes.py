@@ -1,11 +1,10 @@
 """Time the kernels of one MINRES iteration through hom_time_kernels.
 
     python -m paper_2110_00733_gb300.time_passes [--shape 256,256,256] [--reps 20]
-                                                 [--staging 0|1] [--shape3 r,t2,t1] [--fp64]
 
 Prints a JSON object {kernel: milliseconds} and each kernel's HBM rate from
-its algorithmic bytes.  Used for launch-shape sweeps and, with --reps 1, as
-a small driver for ncu captures of the pass kernels:
+its algorithmic bytes (the per-kernel figures of the roofline table).  With
+--reps 1 it is a small driver for ncu captures of the pass kernels:
 
     ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
         --clock-control none -k "regex:k_x|k_lanczos" -c 15 --csv --log-file traffic.csv \
@@ -44,9 +43,6 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--shape", default="256,256,256")
     ap.add_argument("--reps", type=int, default=20)
-    ap.add_argument("--staging", type=int, default=0)
-    ap.add_argument("--shape3", default="0,0,0")
-    ap.add_argument("--fp64", action="store_true", help="FP64 fields (bytes below are for FP32)")
     ap.add_argument("--traffic", default=None, help="ncu CSV to summarise into profiles/traffic.json")
     a = ap.parse_args()
     shape = tuple(int(v) for v in a.shape.split(","))
@@ -54,13 +50,11 @@ def main():
         return write_traffic(a.traffic, shape)
     rng = np.random.default_rng(0)
     phi = (rng.random(shape) > 0.5).astype(np.float32)
-    ctx = hom.hom_create(shape, phi, hom.HOM_INPUT_FRACTION_F32, 110e9, 0.3, staging=a.staging,
-                         shape=tuple(int(v) for v in a.shape3.split(",")),
-                         precision=hom.HOM_PREC_FP64 if a.fp64 else hom.HOM_PREC_FP32_FIELDS)
+    ctx = hom.hom_create(shape, phi, hom.HOM_INPUT_FRACTION_F32, 110e9, 0.3)
     t = hom.hom_time_kernels(ctx, reps=a.reps)
     ctx.close()
     V = int(np.prod(shape))
-    bpv = {k: v * (2 if a.fp64 else 1) for k, v in bytes_per_voxel(shape[2]).items()}
+    bpv = bytes_per_voxel(shape[2])
     out = {"shape": shape, "ms": t,
            "gbs": {k: bpv[k] * V / (t[k] * 1e-3) / 1e9 for k in bpv if t.get(k, 0) > 0}}
     print(json.dumps(out))
