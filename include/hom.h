@@ -312,14 +312,21 @@ int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field);
  * material), MANDEL fields. */
 int hom_project(hom_ctx *ctx, const void *in, void *out);
 
+/* out = G F C F^-1 G in on spectra (see conventions): the operator of
+ * eq. (linearOp) conjugated by the DFT, with the projector of eq. (galop) on
+ * the input as well, as the MINRES iteration applies it (section 2.1).
+ * Mandel components; units of E. */
+int hom_apply_spectrum(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum);
+
 /* Average device time in milliseconds of each kernel of one MINRES iteration
  * of this context, each launched `reps` times back to back on the context's
  * stream between two CUDA events, on the workspace's current contents (an
  * instrument for roofline measurements; it changes no solver state that a
- * later hom_solve reads).  ms[0..7]: n1 pass (projector + inverse), n2 inverse,
- * n3 pass (C2R + material law + R2C), n2 forward, n1 pass (forward +
- * projector + dot product), alpha reduction, Lanczos step + norm fused with
- * the lagged w/x update, Givens step.  Returns the number of entries
+ * later hom_solve reads).  ms[0..5], the elastic MINRES step in launch
+ * order: n2 inverse, n3 pass (C2R + material law with the strain-energy sums
+ * of alpha + R2C), alpha reduction, n2 forward, fused n1 pass (forward +
+ * projector, Lanczos step + norm, lagged w/x update, projector + inverse of
+ * the next Lanczos vector), Givens step.  Returns the number of entries
  * written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 

@@ -123,6 +123,7 @@ struct hom_ctx {
     void *vbuf[3] = {nullptr, nullptr, nullptr};
     void *wbuf[2] = {nullptr, nullptr};
     void *xs = nullptr;     // MINRES iterate of the current sweep
+    long long krylov_reals = 0;   // reals allocated per Krylov buffer (vbuf, wbuf, xs)
     void *rhs = nullptr;    // MINRES right-hand side of the current sweep
     double2 *b64 = nullptr, *r64 = nullptr;   // FP64 right-hand side and residual spectra
     double2 *phihat = nullptr;                // FP64 DFT of phi (half spectrum, one component)
@@ -270,6 +271,11 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     if (g.threads1 > 512 || g.threads2 > 512 || g.threads3 > 512 || g.threads1 < 1 || g.threads2 < 1 || g.threads3 < 1)
         return fail(ctx, HOM_EINVAL, "launch shape needs more than 512 threads per CTA");
     if ((t2 & (t2 - 1)) != 0 || g.threads2 % t2 != 0) return fail(ctx, HOM_EINVAL, "tile2 must be a power of two");
+    if (nc == 6 && g.threads1 > 384)
+        return fail(ctx, HOM_EINVAL, "launch shape needs more than 384 threads per CTA in the fused n1 pass");
+    g.kvec = (long long)((g.n2 * g.h + t1 - 1) / t1) * g.n1 * nc * t1;
+    g.x3r = (sizeof(R) == 4 && nc == 6 && x3r_length(g.n3) && ctx->shape[0] == 0 &&
+             x3r_smem(g.n3) + 1024 <= (size_t)dev_smem) ? 1 : 0;
     // persistent TMA-staged n2 / n1 passes: FP32, register-FFT lengths <= 256
     g.tma = 0;
     g.err = ctx->d_err;
@@ -441,24 +447,48 @@ static int spec_norm2(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, double *out) 
 
 // Capture graph_iters MINRES iterations once (graph_iters even: the buffer
 // roles repeat every 2 steps).  Unnormalised Lanczos vectors u_k = beta_k v_k
-// alternate between vbuf[1] (odd k) and vbuf[0] (even k); p = A u_k is
-// vbuf[2]; w_j sits in wbuf[0] for even j and wbuf[1] for odd j.
+// alternate between vbuf[1] (odd k) and vbuf[0] (even k); w_j sits in
+// wbuf[0] for even j and wbuf[1] for odd j.
+//
+// Elastic operator (fused chain, six launches per step): the work spectrum
+// enters a step holding the inverse n1 transform of G u_k (left there by
+// the previous step, or by run_minres before the first); the n2 inverse,
+// the n3 pass with the material law and the strain-energy sums that give
+// alpha_k = <u_k, A^ u_k> / beta_k^2, the alpha reduction, the n2 forward,
+// the fused n1 pass (projector, Lanczos step, lagged w / x update, projector
+// and inverse n1 transform of u_{k+1}) and the Givens step.
+// Tangent operator of the J2 extension: op_spec (p = A^ u_k in vbuf[2], with
+// the dot product), the alpha reduction, the Lanczos / update kernel and the
+// Givens step.
 template <typename R>
 static void capture_body(hom_ctx *ctx, Engine<R> &E) {
     cpx<R> *ua = (cpx<R> *)ctx->vbuf[0], *ub = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
     cpx<R> *wc = (cpx<R> *)ctx->wbuf[0], *wd = (cpx<R> *)ctx->wbuf[1];
     cpx<R> *x = (cpx<R> *)ctx->xs;
     const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
+    const int np3 = Launch<R>::x3_epart_grid(E.g), npl = Launch<R>::x1_lanczos_grid(E.g);
+    cudaStream_t s = ctx->stream;
     for (int it = 0; it < ctx->graph_iters; ++it) {
         const bool odd = (it % 2) == 0;          // step k = it + 1 (mod 2)
         cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
         cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;   // w_{k-2}, w_{k-3}
+        if (!ctx->tangent_op) {
+            Launch<R>::x2(E.g, s, 1, E.spec, ctx->d_state);
+            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
+                          E.spec, E.phi, ctx->d_state, ctx->partials);
+            scalar_alpha(s, ctx->d_state, ctx->partials, np3, (double)ctx->V);
+            Launch<R>::x2(E.g, s, 0, E.spec, ctx->d_state);
+            Launch<R>::x1_lanczos(E.g, s, E.spec, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
+            scalar_givens(s, ctx->d_state, ctx->partials, npl);
+            ctx->launches += 6;
+            continue;
+        }
         // p = A^ u_k, partial <u_k, p>
         op_spec<R>(ctx, E, uk, p, true, ctx->partials, ctx->d_state);
-        scalar_alpha(ctx->stream, ctx->d_state, ctx->partials, np1);
+        scalar_alpha(s, ctx->d_state, ctx->partials, np1);
         // u_{k+1} over u_{k-1}, partial ||u_{k+1}||^2, lagged w_{k-1} / x update
-        Launch<R>::lanczos_update(E.g, ctx->stream, p, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
-        scalar_givens(ctx->stream, ctx->d_state, ctx->partials, npe);
+        Launch<R>::lanczos_update(E.g, s, p, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
+        scalar_givens(s, ctx->d_state, ctx->partials, npe);
         ctx->launches += 3;
     }
 }
@@ -537,7 +567,10 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const double beta1 = ctx->h_state->beta1;
-    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * nr, s));
+    const bool fused = !ctx->tangent_op;
+    // Krylov vectors in the fused chain's padded tile order (zero padding)
+    const long long nv = fused ? 2 * E.g.kvec : nr;
+    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * nv, s));
     if (!(beta1 > 0.0) || !std::isfinite(beta1)) {
         *iters = 0;
         *est = 0.0;
@@ -546,10 +579,18 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         return HOM_OK;
     }
     // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0
-    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nr, s));
-    CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
-    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nr, s));
-    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nv, s));
+    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nv, s));
+    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nv, s));
+    if (fused) {
+        CU(cudaMemsetAsync(ctx->vbuf[1], 0, sizeof(R) * nv, s));
+        Launch<R>::to_tiles(E.g, s, (const cpx<R> *)ctx->rhs, (cpx<R> *)ctx->vbuf[1]);
+        // the fused chain enters each step with F_1^-1 G u_k in the work spectrum
+        Launch<R>::x1(E.g, s, X1_GAMMA_IN, (const cpx<R> *)ctx->rhs, E.spec, nullptr, nullptr, nullptr);
+        ctx->launches += 2;
+    } else {
+        CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
+    }
     if (ctx->graph_loops) {
         // one launch: the device repeats the body until done (or the cap)
         CU(cudaGraphLaunch(ctx->graph, s));
@@ -572,8 +613,13 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     }
     // the last step's lagged w / x update
     Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->wbuf[0],
-                            (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state);
+                            (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state, nv / 2);
     ctx->launches += 1;
+    if (fused) {   // the iterate back in the standard half-spectrum order
+        Launch<R>::from_tiles(E.g, s, (const cpx<R> *)ctx->xs, (cpx<R> *)ctx->vbuf[2]);
+        CU(cudaMemcpyAsync(ctx->xs, ctx->vbuf[2], sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
+        ctx->launches += 1;
+    }
     *iters = ctx->h_state->k;
     *est = ctx->h_state->est;
     *status = ctx->h_state->status == -5 ? HOM_ENAN : (ctx->h_state->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
@@ -944,17 +990,27 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     }
     const long long nr = 12 * ctx->S;   // reals per spectral vector (>= 6 V)
     const size_t rs = (ctx->prec == HOM_PREC_FP64) ? sizeof(double) : sizeof(float);
-    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * nr));
-    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->wbuf[i], rs * nr));
-    CU(cudaMalloc(&ctx->xs, rs * nr));
+    // Krylov vectors: a half spectrum, or the padded n1-tile order of the fused chain
+    const long long kv = (ctx->prec == HOM_PREC_FP64) ? ctx->e64.g.kvec : ctx->e32.g.kvec;
+    const long long nk = std::max(nr, 2 * kv);
+    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * nk));
+    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->wbuf[i], rs * nk));
+    CU(cudaMalloc(&ctx->xs, rs * nk));
+    ctx->krylov_reals = nk;
     CU(cudaMalloc(&ctx->rhs, rs * nr));
     CU(cudaMalloc(&ctx->b64, sizeof(double) * nr));
     CU(cudaMalloc(&ctx->phihat, sizeof(double2) * ctx->S));
     CU(cudaMalloc(&ctx->r64, sizeof(double) * nr));
-    ctx->workspace += 7 * (long long)rs * nr + 2 * (long long)sizeof(double) * nr;
+    ctx->workspace += 6 * (long long)rs * nk + (long long)rs * nr + 2 * (long long)sizeof(double) * nr;
     long long np = 8LL * kEwBlocks;
     np = std::max(np, (long long)Launch<double>::x1_grid(ctx->e64.g));
-    if (ctx->prec == HOM_PREC_FP32_FIELDS) np = std::max(np, (long long)Launch<float>::x1_grid(ctx->e32.g));
+    np = std::max(np, (long long)Launch<double>::x3_grid(ctx->e64.g));
+    np = std::max(np, (long long)Launch<double>::x1_lanczos_grid(ctx->e64.g));
+    if (ctx->prec == HOM_PREC_FP32_FIELDS) {
+        np = std::max(np, (long long)Launch<float>::x1_grid(ctx->e32.g));
+        np = std::max(np, (long long)Launch<float>::x3_grid(ctx->e32.g));
+        np = std::max(np, (long long)Launch<float>::x1_lanczos_grid(ctx->e32.g));
+    }
     ctx->npartials = (int)np;
     CU(cudaMalloc(&ctx->partials, sizeof(double) * ctx->npartials));
     CU(cudaMalloc(&ctx->d_state, sizeof(MinresState)));
@@ -1143,6 +1199,13 @@ static int step_impl(hom_ctx *ctx, Engine<R> &E, int which, const void *in, void
             if (rc) return rc;
             real_to_spec<R>(ctx, E, din, X3_MID_NONE, false, spec);
             return stage_out(ctx, out, cpx_size<R>() * 6 * ctx->S, spec);
+        case 5: {  // spectral operator A^ = G F C F^-1 G on a spectrum
+            cpx<R> *sout = (cpx<R> *)ctx->vbuf[0];
+            rc = stage_in(ctx, in, cpx_size<R>() * 6 * ctx->S, spec);
+            if (rc) return rc;
+            op_spec<R>(ctx, E, spec, sout, false, nullptr, nullptr);
+            return stage_out(ctx, out, cpx_size<R>() * 6 * ctx->S, sout);
+        }
         case 3:  // inverse FFT
             rc = stage_in(ctx, in, cpx_size<R>() * 6 * ctx->S, spec);
             if (rc) return rc;
@@ -1209,6 +1272,7 @@ int hom_rhs(hom_ctx *ctx, const double macro_strain[6], void *out) { return step
 int hom_fft_forward(hom_ctx *ctx, const void *field, void *spectrum) { return step(ctx, 2, field, spectrum, nullptr); }
 int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field) { return step(ctx, 3, spectrum, field, nullptr); }
 int hom_project(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 4, in, out, nullptr); }
+int hom_apply_spectrum(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 5, in, out, nullptr); }
 
 // ----- solve -------------------------------------------------------------------
 // ||A^ x - b^||_w / ||b^||_w in FP64 (Parseval: the real-space ratio of
@@ -1972,7 +2036,7 @@ template <typename R>
 static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
     const long long nr = 12 * ctx->S;
     cudaStream_t s = ctx->stream;
-    cpx<R> *v0 = (cpx<R> *)ctx->vbuf[0], *v1 = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
+    cpx<R> *v0 = (cpx<R> *)ctx->vbuf[0], *v1 = (cpx<R> *)ctx->vbuf[1];
     cpx<R> *w1 = (cpx<R> *)ctx->wbuf[0], *w2 = (cpx<R> *)ctx->wbuf[1], *x = (cpx<R> *)ctx->xs;
     // a private state that never stops, unit-size coefficients
     MinresState h{};
@@ -1985,24 +2049,24 @@ static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, i
     CU(cudaMalloc(&d, sizeof(MinresState)));
     CU(cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice));
     for (void *b : {ctx->vbuf[0], ctx->vbuf[1], ctx->vbuf[2], ctx->wbuf[0], ctx->wbuf[1], ctx->xs})
-        CU(cudaMemsetAsync(b, 0, sizeof(R) * nr, s));
-    const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
-    const int nk = 8;
+        CU(cudaMemsetAsync(b, 0, sizeof(R) * ctx->krylov_reals, s));
+    const int np3 = Launch<R>::x3_epart_grid(E.g), npl = Launch<R>::x1_lanczos_grid(E.g);
+    const int nk = 6;
+    Launch<R>::x1(E.g, s, X1_GAMMA_IN, v1, E.spec, nullptr, nullptr, d);
     for (int k = 0; k < nk && k < nmax; ++k) {
         for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
             const int r = pass ? reps : 1;
             CU(cudaEventRecord(ctx->ev0, s));
             for (int i = 0; i < r; ++i) {
                 switch (k) {
-                    case 0: Launch<R>::x1(E.g, s, X1_GAMMA_IN, v1, E.spec, nullptr, nullptr, d); break;
-                    case 1: Launch<R>::x2(E.g, s, 1, E.spec, d); break;
-                    case 2: Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0,
-                                          X3_OUT_SPEC, E.spec, E.phi, d); break;
+                    case 0: Launch<R>::x2(E.g, s, 1, E.spec, d); break;
+                    case 1: Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0,
+                                          X3_OUT_SPEC, E.spec, E.phi, d, ctx->partials); break;
+                    case 2: scalar_alpha(s, d, ctx->partials, np3, (double)ctx->V);
+                            CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
                     case 3: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
-                    case 4: Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | X1_DOT, E.spec, p, v1, ctx->partials, d); break;
-                    case 5: scalar_alpha(s, d, ctx->partials, np1); break;
-                    case 6: Launch<R>::lanczos_update(E.g, s, p, v1, v0, w1, w2, x, d, ctx->partials); break;
-                    default: scalar_givens(s, d, ctx->partials, npe);
+                    case 4: Launch<R>::x1_lanczos(E.g, s, E.spec, v1, v0, w1, w2, x, d, ctx->partials); break;
+                    default: scalar_givens(s, d, ctx->partials, npl);
                              CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
                 }
             }

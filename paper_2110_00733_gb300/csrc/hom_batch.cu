@@ -69,10 +69,10 @@ int time_shape(const int grid[3], int precision, const std::vector<float> &phi, 
     double ms[16] = {0};
     rc = hom_time_kernels(ctx, 5, ms, 16);
     hom_destroy(ctx);
-    if (rc < 5) return rc < 0 ? rc : HOM_ECUDA;
-    out[0] = ms[0] + ms[4];
-    out[1] = ms[1] + ms[3];
-    out[2] = ms[2];
+    if (rc < 6) return rc < 0 ? rc : HOM_ECUDA;
+    out[0] = ms[4];           // fused n1 pass
+    out[1] = ms[0] + ms[3];   // n2 inverse and forward
+    out[2] = ms[1];           // n3 pass
     return HOM_OK;
 }
 

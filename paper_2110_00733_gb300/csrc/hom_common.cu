@@ -78,11 +78,12 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
     if (!isfinite(beta1)) { st->status = -5; st->done = 1; st->done_update = 1; }
 }
 
-// alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2
-__global__ void k_scalar_alpha(MinresState *st, const double *partials, int np) {
+// alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2; the partials sum to
+// <u_k, A u_k> / scale (scale = V for the strain-energy sums of the n3 pass)
+__global__ void k_scalar_alpha(MinresState *st, const double *partials, int np, double scale) {
     if (st->done) return;
     const double a = reduce_partials(partials, np);
-    if (threadIdx.x == 0) st->alpha = a / (st->beta * st->beta);
+    if (threadIdx.x == 0) st->alpha = scale * a / (st->beta * st->beta);
 }
 
 // MINRES step k: apply the previous Givens rotation to the new column of the
@@ -444,8 +445,8 @@ void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int n
 void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s) {
     k_loop_cond<<<1, 32, 0, st>>>(h, s);
 }
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np) {
-    k_scalar_alpha<<<1, 1024, 0, st>>>(s, partials, np);
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale) {
+    k_scalar_alpha<<<1, 1024, 0, st>>>(s, partials, np, scale);
 }
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np) {
     k_scalar_givens<<<1, 1024, 0, st>>>(s, partials, np);

@@ -82,11 +82,27 @@ struct Geometry {
     // tensor maps (never dereferenced on the device) and the device word a
     // pass sets when a bounded wait gives up
     int tma;
+    // fused MINRES chain: complex elements of one Krylov vector stored in
+    // n1-tile order (tiles of tile1 (k2,k3) columns, each tile a contiguous
+    // n1 x 6 tile1 block laid out as the pass's shared-memory tile)
+    long long kvec;
+    // register-resident n3 pass (k_x3r: FP32, n3 in {64, 128, 256}) for
+    // spectrum-to-spectrum applications
+    int x3r;
     int grid2_tma, grid1_tma, grid1d_tma;
     size_t smem2_tma, smem1_tma, smem1d_tma;
     void *tma_cache;
     int *err;
 };
+
+// register-resident n3 pass (k_x3r): supported lengths, rows per 128-thread
+// CTA, and its shared memory (per row, the transpose slab of 3 lines x Q x
+// (P + 1) complex values, N = P Q)
+__host__ __device__ constexpr bool x3r_length(int n) { return n == 64 || n == 128 || n == 256; }
+__host__ __device__ constexpr int x3r_rows(int n) { return n == 256 ? 8 : 16; }
+__host__ __device__ constexpr size_t x3r_smem(int n) {
+    return (size_t)x3r_rows(n) * 3 * (n == 64 ? 8 * 9 : (n == 128 ? 16 * 9 : 16 * 17)) * sizeof(float2);
+}
 
 // tensor-map kinds of the TMA passes
 enum TmaKind { TMA_X2 = 0, TMA_X1 = 1 };
@@ -114,9 +130,11 @@ template <typename R> struct Launch {
     // n3 pass: C2R (SPEC in) or real / macro input, optional material law
     // tau = phi C_m e, R2C (SPEC out) or real output; scale applied to the
     // real-space values (1/V for SPEC in is included automatically).
+    // epart (6-component spectra only): per-CTA sums of the strain energy
+    // e : C : e of the scaled real-space input (x3_grid(g) values).
     static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
-                   const MinresState *state);
+                   const MinresState *state, double *epart = nullptr);
     // n2 pass, in place on the half spectrum
     static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
     // n1 pass: in -> out (may alias), optional projector before / after, and
@@ -130,10 +148,21 @@ template <typename R> struct Launch {
     //   x += tau wb.  wa = w_{k-2}, wb = w_{k-3} on entry.
     static void lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> *p, const cpx<R> *uk, cpx<R> *um,
                                const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials);
+    // fused n1 pass of a MINRES step (see k_x1_lanczos): spec holds the
+    // forward n3 / n2 transforms of C e_k on entry and the inverse n1
+    // transform of G u_{k+1} on exit; um, wb, x as for lanczos_update;
+    // x1_lanczos_grid(g) partials of ||u_{k+1}||^2
+    static void x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
+                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials);
+    static int x1_lanczos_grid(const Geometry &g);
+    // standard half-spectrum order <-> n1-tile order of the fused chain's
+    // Krylov vectors (the tile order's padding is left untouched)
+    static void to_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out);
+    static void from_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out);
     // the lagged update of the last step K after the loop; u_K sits in ub
     // for odd K, in ua for even K; w_{K-1} in wd for even K, wc for odd K
     static void minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
-                             cpx<R> *wd, cpx<R> *x, MinresState *state);
+                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long n);
     // Parseval partials of <phi, (G x^)_c>, c = 0..5 (see k_phi_dot); returns
     // the number of blocks (partials[c * nb + block])
     static int phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials);
@@ -162,6 +191,7 @@ template <typename R> struct Launch {
     static int ew_grid(long long n);
     static void table_init(const Geometry &g);
     static int x3_grid(const Geometry &g);
+    static int x3_epart_grid(const Geometry &g);
     static int x1_grid(const Geometry &g);
     static int tma_grids(Geometry &g);
 };
@@ -194,7 +224,8 @@ void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int n
 // end of a captured MINRES body inside a WHILE graph node: count the body and
 // keep looping while the state is not done and the cap is not reached
 void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s);
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np);
+// alpha_k from partials summing to <u_k, A^ u_k> / scale
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale = 1.0);
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np);
 // PCG scalars (MoDBFFT): start from <r0,z0>, ||r0||^2; step length; direction
 void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it);

@@ -113,25 +113,28 @@ __device__ __forceinline__ void gamma_project(cpx<R> *t, cpx<R> x0, cpx<R> x1, c
     t[5] = scale<R>(add<R>(mul<R>(u0, e1), mul<R>(u1, e0)), r2);
 }
 
-// G at frequency (k1,k2,k3) on the 6 Mandel components at p[0..5] (stride 1)
+// The projector of eq. (galop) at one frequency, split into the part that
+// depends on the frequency only (mode and unit vector e = xi / |xi|) and its
+// application, so that a pass projecting two tensors at the same frequency
+// builds xi once.  mode 0: G = 0 (a Nyquist index, or xi = 0 numerically);
+// 1: the projection; 2: xi = 0 (the identity on the stress-controlled
+// components g.mask0, zero on the others).
+template <typename R> struct GammaE {
+    cpx<R> e0, e1, e2;
+    int mode;
+};
+
 template <typename R>
-__device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int k3, cpx<R> *t) {
-    // eq. (galop): at xi = 0 the identity on the stress-controlled components
-    // (g.mask0) and zero on the strain-controlled ones; zero at every
-    // frequency with a Nyquist index
+__device__ __forceinline__ GammaE<R> gamma_e(const Geometry &g, int k1, int k2, int k3) {
+    GammaE<R> q;
+    q.mode = 0;
     if (k1 == 0 && k2 == 0 && k3 == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-            if (!((g.mask0 >> c) & 1)) t[c] = mk<R>(0, 0);
-        return;
+        q.mode = 2;
+        return q;
     }
     const bool nyq = ((g.n1 & 1) == 0 && 2 * k1 == g.n1) || ((g.n2 & 1) == 0 && 2 * k2 == g.n2) ||
                      ((g.n3 & 1) == 0 && 2 * k3 == g.n3);
-    if (nyq) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) t[c] = mk<R>(0, 0);
-        return;
-    }
+    if (nyq) return q;
     const cpx<R> *D0 = reinterpret_cast<const cpx<R> *>(g.D[0]);
     const cpx<R> *D1 = reinterpret_cast<const cpx<R> *>(g.D[1]);
     const cpx<R> *D2 = reinterpret_cast<const cpx<R> *>(g.D[2]);
@@ -144,7 +147,52 @@ __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int 
     const cpx<R> x0 = mul<R>(__ldg(&D0[k1]), mul<R>(m1, m2));
     const cpx<R> x1 = mul<R>(__ldg(&D1[k2]), mul<R>(m0, m2));
     const cpx<R> x2 = mul<R>(__ldg(&D2[k3]), mul<R>(m0, m1));
-    gamma_project<R>(t, x0, x1, x2);
+    const R n2 = x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y + x2.x * x2.x + x2.y * x2.y;
+    if (!(n2 > (R)0)) return q;
+    const R inv = (R)1 / sqrt(n2);
+    q.e0 = scale<R>(x0, inv);
+    q.e1 = scale<R>(x1, inv);
+    q.e2 = scale<R>(x2, inv);
+    q.mode = 1;
+    return q;
+}
+
+// Orthogonal projection of a symmetric tau (Mandel, t[6], overwritten) onto
+// {sym(u (x) e)}, |e| = 1: sym(u (x) e) with u = 2 tau conj(e) - e (conj(e) .
+// tau conj(e)) (Sherman-Morrison inverse of the acoustic tensor 1/2 (I + e e^H)).
+template <typename R>
+__device__ __forceinline__ void gamma_apply(const Geometry &g, const GammaE<R> &q, cpx<R> *t) {
+    if (q.mode != 1) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (q.mode == 0 || !((g.mask0 >> c) & 1)) t[c] = mk<R>(0, 0);
+        return;
+    }
+    const cpx<R> e0 = q.e0, e1 = q.e1, e2 = q.e2;
+    const cpx<R> c0 = conjc<R>(e0), c1 = conjc<R>(e1), c2 = conjc<R>(e2);
+    const R r2 = (R)0.70710678118654752440;   // 1/sqrt(2)
+    const cpx<R> T11 = t[0], T22 = t[1], T33 = t[2];
+    const cpx<R> T23 = scale<R>(t[3], r2), T13 = scale<R>(t[4], r2), T12 = scale<R>(t[5], r2);
+    const cpx<R> v0 = add<R>(add<R>(mul<R>(T11, c0), mul<R>(T12, c1)), mul<R>(T13, c2));
+    const cpx<R> v1 = add<R>(add<R>(mul<R>(T12, c0), mul<R>(T22, c1)), mul<R>(T23, c2));
+    const cpx<R> v2 = add<R>(add<R>(mul<R>(T13, c0), mul<R>(T23, c1)), mul<R>(T33, c2));
+    const cpx<R> sc = add<R>(add<R>(mul<R>(c0, v0), mul<R>(c1, v1)), mul<R>(c2, v2));
+    const cpx<R> u0 = sub<R>(scale<R>(v0, (R)2), mul<R>(e0, sc));
+    const cpx<R> u1 = sub<R>(scale<R>(v1, (R)2), mul<R>(e1, sc));
+    const cpx<R> u2 = sub<R>(scale<R>(v2, (R)2), mul<R>(e2, sc));
+    t[0] = mul<R>(u0, e0);
+    t[1] = mul<R>(u1, e1);
+    t[2] = mul<R>(u2, e2);
+    t[3] = scale<R>(add<R>(mul<R>(u1, e2), mul<R>(u2, e1)), r2);
+    t[4] = scale<R>(add<R>(mul<R>(u0, e2), mul<R>(u2, e0)), r2);
+    t[5] = scale<R>(add<R>(mul<R>(u0, e1), mul<R>(u1, e0)), r2);
+}
+
+// G at frequency (k1,k2,k3) on the 6 Mandel components at p[0..5] (stride 1)
+template <typename R>
+__device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int k3, cpx<R> *t) {
+    const GammaE<R> q = gamma_e<R>(g, k1, k2, k3);
+    gamma_apply<R>(g, q, t);
 }
 
 // Run the transform of the L lines in buf.  Fast engine: in place, returns
@@ -197,7 +245,8 @@ template <> struct Six<double> {
 template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
-                                        const R *__restrict__ phi, const MinresState *state) {
+                                        const R *__restrict__ phi, const MinresState *state,
+                                        double *__restrict__ epart) {
     if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
@@ -257,6 +306,10 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     // ---- scaling and material law on the real-space values
     const R s_in = (in_mode == X3_IN_SPEC) ? (R)(1.0 / (double)g.V) : (R)1;
     const R s_all = s_in * scl;
+    // strain energy sum_x e : C : e of the real-space input (epart): with
+    // e = F^-1 G u this is <u, A^ u> / V, the MINRES alpha numerator, so the
+    // n1 pass needs no dot product with u
+    R en = 0;   // non-negative terms: a short per-thread sum in R is accurate to ~1e-6
     for (int r = 0; r < nr; ++r) {
         const int vbase = (row0 + r) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
@@ -270,7 +323,14 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
             }
             if (mid == X3_MID_MATERIAL || mid == X3_MID_MODB) {
                 const R ph = phi[vbase + e];
-                const R tr = lam * (t[0] + t[1] + t[2]);
+                const R sum = t[0] + t[1] + t[2];
+                const R tr = lam * sum;
+                if (epart) {
+                    R ee = t[0] * t[0];
+#pragma unroll
+                    for (int c = 1; c < 6; ++c) ee += t[c] * t[c];
+                    en += ph * (tr * sum + mu2 * ee);
+                }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : (R)0) + mu2 * t[c]);
                 if constexpr (NC == 10) {
@@ -292,6 +352,10 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
             }
         }
     }
+    if (epart) {
+        const double sum = block_sum((double)en);
+        if (threadIdx.x == 0) epart[blockIdx.x] = sum;
+    }
     if (out_mode == X3_OUT_REAL) return;
     // rows beyond nrows hold zeros already (their inputs were zero)
     __syncthreads();
@@ -311,6 +375,185 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
                                    mk<R>((R)0.5 * (z.y - zm.y), (R)-0.5 * (z.x - zm.x)));
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident n3 pass (FP32, n3 in {64, 128, 256}, 6-component spectra,
+// spectrum in and out): the C2R of a row, the material law with the strain-
+// energy sums, and the R2C, with the row's data in registers.
+//
+// A row is handled by P lanes of one warp; lane j owns the elements j + P m,
+// m < Q, of the three packed lines Z_p = X_2p + i X_2p+1 (N = P Q).  Each
+// transform is two radix stages held in registers -- a length-Q DFT over m,
+// a twiddle, a transpose through a padded per-row shared-memory slab, and
+// length-P DFTs of Q/P columns -- after which lane j again owns the
+// elements j + P m (the inverse maps frequencies j + P m to voxels j + P m,
+// the forward voxels to frequencies).  The other half of the Hermitian
+// spectrum (Z[N-k] from X[k]) and the unpacking of the result come from the
+// partner lane P - j by warp shuffles.  The law needs all six components of
+// a voxel, which lane j holds.  Rows are independent, so only warp-level
+// synchronisation is used.
+// ---------------------------------------------------------------------------
+template <int N> struct X3RPlan;
+template <> struct X3RPlan<64>  { static constexpr int P = 8,  Q = 8,  ROWS = 16; };
+template <> struct X3RPlan<128> { static constexpr int P = 8,  Q = 16, ROWS = 16; };
+template <> struct X3RPlan<256> { static constexpr int P = 16, Q = 16, ROWS = 8; };
+
+
+template <int P>
+__device__ __forceinline__ float2 shfl_partner(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// stage 2 of a transform: lane t takes the Q/P columns t + P i of the slab
+// (line p), a length-P DFT each, and returns element i + (Q/P) n of
+// column i's output n in z[i + (Q/P) n]
+template <int S, int P, int Q>
+__device__ __forceinline__ void x3r_stage2(const float2 *slab, int t, float2 (&z)[Q]) {
+    constexpr int C = Q / P;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        float2 v[P];
+        const float2 *col = slab + (t + P * i) * (P + 1);
+#pragma unroll
+        for (int k = 0; k < P; ++k) v[k] = col[k];
+        dft<float, S, P>(v);
+#pragma unroll
+        for (int n = 0; n < P; ++n) z[i + C * n] = v[n];
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, 3) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                int material, float lam, float mu2, const float *__restrict__ phi,
+                                                const MinresState *state, double *__restrict__ epart) {
+    if (skip(state)) return;
+    using PL = X3RPlan<N>;
+    constexpr int P = PL::P, Q = PL::Q, ROWS = PL::ROWS, H = N / 2 + 1, NC = 6;
+    constexpr int TS = Q * (P + 1);   // one line's transpose slab
+    extern __shared__ __align__(16) float2 xslab[];
+    const int r = threadIdx.x / P, j = threadIdx.x % P;
+    const int nrows = g.n1 * g.n2;
+    const int row = blockIdx.x * ROWS + r;
+    const bool live = row < nrows;
+    float2 *tb = xslab + r * 3 * TS;
+    const float2 *tw = reinterpret_cast<const float2 *>(g.ax[2].tw);   // exp(-2 pi i t / N)
+    const int lane0 = (threadIdx.x & 31) & ~(P - 1);
+    const int partner = lane0 + ((P - j) & (P - 1));
+    float2 z[3][Q];
+    // ---- input: own frequencies k = j + P m <= N/2 (m < Q/2, and m = Q/2 for j = 0)
+    {
+        float2 zc[3][Q / 2 + 1];   // conj X_a[k] + i conj X_b[k] = Z[N - k], for the partner
+        const float2 *rp = in + (size_t)(live ? row : 0) * H * NC;
+#pragma unroll
+        for (int m = 0; m <= Q / 2; ++m) {
+            const int k = j + P * m;
+            const bool own = live && (m < Q / 2 || j == 0);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (own) v = reinterpret_cast<const float4 *>(rp + NC * k)[p];
+                if (k == 0 || 2 * k == N) { v.y = 0.f; v.w = 0.f; }   // self-conjugate bins: real parts
+                // a = (v.x, v.y), b = (v.z, v.w): Z = a + i b, Zc = conj a + i conj b
+                z[p][m < Q ? m : 0] = make_float2(v.x - v.w, v.y + v.z);
+                zc[p][m] = make_float2(v.x + v.w, v.z - v.y);
+            }
+        }
+        // upper half m > Q/2 (and m = Q/2 for j != 0): Z[j + P m] = Zc[N - j - P m],
+        // held by the partner at m' = Q - 1 - m (by lane 0 itself at Q - m)
+#pragma unroll
+        for (int s = 0; s < Q / 2; ++s) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const float2 got = shfl_partner<P>(zc[p][s], partner);
+                const int m = Q - 1 - s;
+                z[p][m] = (j == 0) ? (m > Q / 2 ? zc[p][Q - m] : z[p][m]) : got;
+            }
+        }
+    }
+    // ---- inverse transform (C2R part of eq. linearOp)
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        dft<float, 1, Q>(z[p]);
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+            float2 w = __ldg(&tw[j * n]);
+            w.y = -w.y;
+            tb[p * TS + n * (P + 1) + j] = mul<float>(z[p][n], w);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 3; ++p) x3r_stage2<1, P, Q>(tb + p * TS, j, z[p]);
+    __syncwarp();
+    // ---- material law on voxels j + P m (scaled by 1/V), strain energy
+    const float sV = 1.0f / (float)g.V;
+    float en = 0.f;
+    if (material) {
+        const float *ph_row = phi + (size_t)(live ? row : 0) * N;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const float ph = live ? __ldg(&ph_row[j + P * m]) : 0.f;
+            float t[6];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                t[2 * p] = z[p][m].x * sV;
+                t[2 * p + 1] = z[p][m].y * sV;
+            }
+            const float sum = t[0] + t[1] + t[2];
+            const float tr = lam * sum;
+            float ee = t[0] * t[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c) ee += t[c] * t[c];
+            en += ph * (tr * sum + mu2 * ee);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : 0.f) + mu2 * t[c]);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) z[p][m] = make_float2(t[2 * p], t[2 * p + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int m = 0; m < Q; ++m) z[p][m] = make_float2(z[p][m].x * sV, z[p][m].y * sV);
+    }
+    // ---- forward transform (R2C)
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        dft<float, -1, Q>(z[p]);
+#pragma unroll
+        for (int n = 0; n < Q; ++n) tb[p * TS + n * (P + 1) + j] = mul<float>(z[p][n], __ldg(&tw[j * n]));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 3; ++p) x3r_stage2<-1, P, Q>(tb + p * TS, j, z[p]);
+    // ---- unpack and store own frequencies k = j + P m <= N/2:
+    //   X_a[k] = (W[k] + conj W[N-k]) / 2,  X_b[k] = (W[k] - conj W[N-k]) / (2i),
+    //   W[N-k] from the partner's register Q - 1 - m (lane 0: its own Q - m)
+    float2 *op = out + (size_t)(live ? row : 0) * H * NC;
+#pragma unroll
+    for (int m = 0; m <= Q / 2; ++m) {
+        float2 wm[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float2 got = shfl_partner<P>(z[p][(Q - 1 - m + Q) % Q], partner);
+            wm[p] = (j == 0) ? z[p][(Q - m) % Q] : got;
+        }
+        const int k = j + P * m;
+        if (live && (m < Q / 2 || j == 0)) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const float2 w = z[p][m % Q];
+                const float2 c = make_float2(wm[p].x, -wm[p].y);
+                reinterpret_cast<float4 *>(op + NC * k)[p] =
+                    make_float4(0.5f * (w.x + c.x), 0.5f * (w.y + c.y), 0.5f * (w.y - c.y), -0.5f * (w.x - c.x));
+            }
+        }
+    }
+    if (epart) {
+        const double sum = block_sum((double)en);
+        if (threadIdx.x == 0) epart[blockIdx.x] = sum;
     }
 }
 
@@ -563,6 +806,242 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_
 }
 
 // ---------------------------------------------------------------------------
+// Fused n1 pass of one MINRES step (6-component spectra).  With the work
+// spectrum holding F_3 F_2 of tau = C e_k (the forward n3 and n2 passes of
+// A^ u_k) and alpha_k already known from the n3 pass's strain energy, one
+// pass over each n1 tile
+//   1. finishes p = A^ u_k: forward DFT along n1 and the projector G;
+//   2. takes the Lanczos step on unnormalised vectors,
+//        u_{k+1} = p / beta_k - (alpha_k / beta_k) u_k - (beta_k / beta_{k-1}) u_{k-1},
+//      over the slot of u_{k-1}, with the weighted partial ||u_{k+1}||^2,
+//      and the lagged w / x update of step k-1 (w_{k-1} over w_{k-3});
+//   3. starts A^ u_{k+1}: G on u_{k+1} and the inverse DFT along n1, written
+//      back over the tile of the work spectrum for the next step's n2 pass.
+// p never reaches HBM, and u_k is read once per step instead of three times.
+// ---------------------------------------------------------------------------
+template <typename R> struct LzCoef {
+    R cp, cu, cv;            // 1/beta_k, -alpha_k/beta_k, -beta_k/beta_{k-1}
+    R d, e, ig, tau, ib;     // lagged update of step k-1
+    bool lagged;
+};
+
+template <typename R>
+__device__ __forceinline__ LzCoef<R> lz_coef(const MinresState *st) {
+    LzCoef<R> c;
+    const double bk = st->beta, bkm = st->beta_prev;
+    c.cp = (R)(1.0 / bk);
+    c.cu = (R)(-st->alpha / bk);
+    c.cv = (R)(bkm > 0.0 ? -bk / bkm : 0.0);
+    c.lagged = st->k > 0;
+    c.d = (R)st->u_delta;
+    c.e = (R)st->u_eps;
+    c.ig = (R)st->u_inv_gamma;
+    c.tau = (R)st->u_tau;
+    c.ib = (R)st->u_inv_beta;
+    return c;
+}
+
+// Steps 1-3 on the tile of columns [g0, g0 + T) held in buf (element e of
+// line l at buf[e * L + l], L = 6 T); returns the buffer holding the inverse
+// transform (buf for the register engine).  All threads of the CTA call it.
+// Between the two transforms one loop over the tile's frequencies builds
+// xi once per frequency and applies the projector to p and to u_{k+1}; the
+// Krylov vectors are stored in tile order, so the six components of a
+// frequency are 48 contiguous bytes of each vector and a warp reads and
+// writes a contiguous block.
+template <typename R, int NF>
+__device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *buf, cpx<R> *buf2, int g0,
+                                                   const LzCoef<R> &c, const cpx<R> *__restrict__ uk,
+                                                   cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
+                                                   cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x, Acc<R> &acc) {
+    constexpr int NC = 6;
+    const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
+    const int cols = g.n2 * H;
+    // 1. forward DFT along n1
+    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, L, g.ax[0]);
+    // 2. per frequency: p = G (.), Lanczos step, lagged update, G u_{k+1}
+    const size_t kb = (size_t)(g0 / T) * (size_t)(N * L);
+    for (int f = threadIdx.x; f < N * T; f += blockDim.x) {
+        const int e = f / T, t = f - e * T;
+        const int col = g0 + t;
+        cpx<R> *sp = res + e * L + t * NC;
+        if (col >= cols) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) sp[q] = mk<R>(0, 0);
+            continue;
+        }
+        const int k2 = col / H, k3 = col - k2 * H;
+        const GammaE<R> ge = gamma_e<R>(g, e, k2, k3);
+        cpx<R> v[NC], u[NC], uo[NC];
+        const size_t i = kb + (size_t)f * NC;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            Six<R>::load_pair(sp, p, v[2 * p], v[2 * p + 1]);
+            Six<R>::load_pair(uk + i, p, u[2 * p], u[2 * p + 1]);
+            Six<R>::load_pair(um + i, p, uo[2 * p], uo[2 * p + 1]);
+        }
+        gamma_apply<R>(g, ge, v);
+        const R w = (R)pweight(k3, g.n3);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            v[q] = mk<R>(c.cp * v[q].x + c.cu * u[q].x + c.cv * uo[q].x, c.cp * v[q].y + c.cu * u[q].y + c.cv * uo[q].y);
+            acc.add_prod(w * v[q].x, v[q].x);
+            acc.add_prod(w * v[q].y, v[q].y);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) Six<R>::store_pair(um + i, p, v[2 * p], v[2 * p + 1]);
+        if (c.lagged) {
+            cpx<R> a[NC], b[NC], xx[NC];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                Six<R>::load_pair(wa + i, p, a[2 * p], a[2 * p + 1]);
+                Six<R>::load_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
+                Six<R>::load_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                b[q] = mk<R>((uo[q].x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
+                             (uo[q].y * c.ib - c.d * a[q].y - c.e * b[q].y) * c.ig);
+                xx[q] = mk<R>(xx[q].x + c.tau * b[q].x, xx[q].y + c.tau * b[q].y);
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                Six<R>::store_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
+                Six<R>::store_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
+            }
+        }
+        gamma_apply<R>(g, ge, v);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) Six<R>::store_pair(sp, p, v[2 * p], v[2 * p + 1]);
+    }
+    __syncthreads();
+    // 3. inverse DFT along n1 of G u_{k+1}
+    return run_fft<R, 1, NF>(res, res == buf ? buf2 : buf, L, L, g.ax[0]);
+}
+
+// At most 384 threads per CTA (set_shapes enforces it): the fused pass keeps
+// the Lanczos operands in registers next to the FFT's, so FP32 CTAs may use
+// up to 85 registers and still fit two 384-thread (four 192-thread) CTAs per SM.
+#define HOM_X1L_BOUNDS(R) __launch_bounds__(384, sizeof(R) == 4 ? 2 : 1)
+
+// plain-load form: one tile per CTA
+template <typename R, int NF>
+__global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ spec, const cpx<R> *__restrict__ uk,
+                                                cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
+                                                cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x,
+                                                const MinresState *state, double *__restrict__ partials) {
+    if (skip(state)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int NC = 6;
+    const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
+    cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
+    cpx<R> *buf2 = buf + N * L;
+    const int cols = g.n2 * H;
+    const int g0 = blockIdx.x * T;
+    const size_t sK1 = (size_t)cols * NC;
+    const int lt = threadIdx.x % L, e0 = threadIdx.x / L, es = blockDim.x / L;
+    const bool live = g0 + lt / NC < cols;
+    const LzCoef<R> c = lz_coef<R>(state);
+    {
+        const cpx<R> *src = spec + (size_t)g0 * NC + lt;
+        for (int e = e0; e < N; e += es) buf[e * L + lt] = live ? src[e * sK1] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    Acc<R> acc;
+    cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf2, g0, c, uk, um, wa, wb, x, acc);
+    if (live) {
+        cpx<R> *dst = spec + (size_t)g0 * NC + lt;
+        for (int e = e0; e < N; e += es) dst[e * sK1] = res[e * L + lt];
+    }
+    const double sum = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// L2 prefetch of a contiguous global range (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+                 : "memory");
+}
+
+// persistent TMA-staged form (FP32, register FFT lengths 64..256): the work
+// tile comes and goes by TMA, double-buffered as in k_x1_tma; the contiguous
+// Krylov blocks of the next tile are prefetched into L2 (bulk prefetch)
+// while the current one is computed, and are then read with plain loads.
+template <typename R, int NF>
+__global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec,
+                                                    const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
+                                                    const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
+                                                    cpx<R> *__restrict__ x, const MinresState *state,
+                                                    double *__restrict__ partials) {
+    if (skip(state)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int NC = 6;
+    const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
+    const int cols = g.n2 * H;
+    const int ntiles = (cols + T - 1) / T;
+    const int per = N * L;
+    const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
+    cpx<R> *base = reinterpret_cast<cpx<R> *>(smem_raw);
+    const bool leader = threadIdx.x == 0;
+    const LzCoef<R> c = lz_coef<R>(state);
+    if (leader) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto prefetch = [&](int t) {
+        const size_t o = (size_t)t * per;
+        bulk_prefetch_l2(uk + o, bytes);
+        bulk_prefetch_l2(um + o, bytes);
+        if (c.lagged) {
+            bulk_prefetch_l2(wa + o, bytes);
+            bulk_prefetch_l2(wb + o, bytes);
+            bulk_prefetch_l2(x + o, bytes);
+        }
+    };
+    int tile = blockIdx.x;
+    if (leader && tile < ntiles) {
+        mbar_expect_tx(&bar[0], bytes);
+        tma_load_2d(base, &tspec, NC * T * tile, 0, &bar[0]);
+        prefetch(tile);
+    }
+    Acc<R> acc;
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int s = i & 1;
+        const int next = tile + gridDim.x;
+        if (leader && next < ntiles) {
+            bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
+            mbar_expect_tx(&bar[s ^ 1], bytes);
+            tma_load_2d(base + (s ^ 1) * per, &tspec, NC * T * next, 0, &bar[s ^ 1]);
+            prefetch(next);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
+                atomicExch(g.err, 1);
+                mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
+                bulk_wait_all();
+            }
+            return;
+        }
+        cpx<R> *buf = base + s * per;
+        cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf, tile * T, c, uk, um, wa, wb, x, acc);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (leader) {
+            tma_store_2d(&tspec, NC * T * tile, 0, res);
+            bulk_commit();
+        }
+    }
+    if (leader) bulk_wait_all();
+    const double sum = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// ---------------------------------------------------------------------------
 // Krylov vector kernels on half spectra (n = 6 S complex values).  The
 // Parseval weight of element i depends on k3 = (i / 6) mod h.
 // ---------------------------------------------------------------------------
@@ -598,6 +1077,22 @@ __global__ void __launch_bounds__(kEwThreads) k_lanczos_update(int n, int h, int
     }
     const double s = block_sum(acc.value());
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// standard half-spectrum order <-> n1-tile order (see Geometry::kvec):
+// element (k1, col, c) of the standard order, col = k2 h + k3, sits in the
+// tile order at (col / T) n1 6T + k1 6T + (col % T) 6 + c
+template <typename R>
+__global__ void k_tiles(long long n, int n1, int cols, int T, int to_tiles, const cpx<R> *__restrict__ in,
+                        cpx<R> *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 6);
+        const long long f = i / 6;
+        const int col = (int)(f % cols), k1 = (int)(f / cols);
+        const long long t = (long long)(col / T) * n1 * 6 * T + (long long)k1 * 6 * T + (col % T) * 6 + c;
+        if (to_tiles) out[t] = in[i];
+        else out[i] = in[t];
+    }
 }
 
 // The lagged w / x update of the last step K; skipped when there is none
@@ -718,6 +1213,12 @@ int Launch<R>::ew_grid(long long n) {
 }
 template <typename R>
 int Launch<R>::x3_grid(const Geometry &g) { return (g.n1 * g.n2 + g.rows3 - 1) / g.rows3; }
+// partials written by the n3 pass of the fused chain (spectrum in and out)
+template <typename R>
+int Launch<R>::x3_epart_grid(const Geometry &g) {
+    if (sizeof(R) == 4 && g.x3r) return (g.n1 * g.n2 + x3r_rows(g.n3) - 1) / x3r_rows(g.n3);
+    return x3_grid(g);
+}
 // number of partial sums the dot-product variant of the n1 pass writes
 template <typename R>
 int Launch<R>::x1_grid(const Geometry &g) {
@@ -755,16 +1256,21 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x3<R, NF, 5>))     \
     HOM_SET_ATTR1((k_x2<R, -1, NF>))    \
     HOM_SET_ATTR1((k_x2<R, 1, NF>))     \
-    HOM_SET_ATTR1((k_x1<R, NF>))
+    HOM_SET_ATTR1((k_x1<R, NF>))        \
+    HOM_SET_ATTR1((k_x1_lanczos<R, NF>))
     HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(128)
     HOM_SET_ATTR(256) HOM_SET_ATTR(512)
     if constexpr (sizeof(R) == 4) {
 #define HOM_SET_TMA(NF)                   \
     HOM_SET_ATTR1((k_x2_tma<R, -1, NF>))  \
     HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
-    HOM_SET_ATTR1((k_x1_tma<R, NF>))
+    HOM_SET_ATTR1((k_x1_tma<R, NF>))      \
+    HOM_SET_ATTR1((k_x1_lanczos_tma<R, NF>))
         HOM_SET_TMA(64) HOM_SET_TMA(128) HOM_SET_TMA(256)
 #undef HOM_SET_TMA
+        HOM_SET_ATTR1((k_x3r<64>))
+        HOM_SET_ATTR1((k_x3r<128>))
+        HOM_SET_ATTR1((k_x3r<256>))
     }
 #undef HOM_SET_ATTR
 #undef HOM_SET_ATTR1
@@ -813,7 +1319,26 @@ int Launch<R>::tma_grids(Geometry &g) {
 template <typename R>
 void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro, double scl, int out_mode, void *out, const R *phi,
-                   const MinresState *state) {
+                   const MinresState *state, double *epart) {
+    if constexpr (sizeof(R) == 4) {
+        if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
+            (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
+            const int grid = x3_epart_grid(g);
+            const size_t sm = x3r_smem(g.n3);
+            const int mat = mid == X3_MID_MATERIAL;
+            const float2 *fi = reinterpret_cast<const float2 *>(in);
+            float2 *fo = reinterpret_cast<float2 *>(out);
+            switch (g.n3) {
+                case 64: k_x3r<64><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                                                          (const float *)phi, state, epart); break;
+                case 128: k_x3r<128><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                                                            (const float *)phi, state, epart); break;
+                default: k_x3r<256><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                                                            (const float *)phi, state, epart); break;
+            }
+            return;
+        }
+    }
     Mac6 m{};
     if (macro)
         for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
@@ -821,10 +1346,10 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
         k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state);                \
+                                                            (R)scl, out_mode, out, phi, state, nullptr);       \
     else                                                                                                    \
         k_x3<R, NF, 3><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state)
+                                                            (R)scl, out_mode, out, phi, state, epart)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }
@@ -883,6 +1408,46 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 }
 
 template <typename R>
+int Launch<R>::x1_lanczos_grid(const Geometry &g) {
+    return g.tma ? g.grid1_tma : (g.n2 * g.h + g.tile1 - 1) / g.tile1;
+}
+
+template <typename R>
+void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
+                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials) {
+    if constexpr (sizeof(R) == 4) {
+        if (g.tma) {
+            const CUtensorMap *ts = tma_map(g, spec, TMA_X1, 1);
+#define HOM_X1LT(NF)                                                                                         \
+    k_x1_lanczos_tma<R, NF><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials)
+            switch (g.fast[0]) {
+                case 64: HOM_X1LT(64); break;
+                case 128: HOM_X1LT(128); break;
+                default: HOM_X1LT(256); break;
+            }
+#undef HOM_X1LT
+            return;
+        }
+    }
+    const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1;
+#define HOM_X1L(NF) k_x1_lanczos<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, spec, uk, um, wa, wb, x, state, partials)
+    HOM_FAST_SWITCH(g.fast[0], HOM_X1L)
+#undef HOM_X1L
+}
+
+template <typename R>
+void Launch<R>::to_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out) {
+    const long long n = 6 * g.S;
+    k_tiles<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.n1, g.n2 * g.h, g.tile1, 1, in, out);
+}
+
+template <typename R>
+void Launch<R>::from_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out) {
+    const long long n = 6 * g.S;
+    k_tiles<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, g.n1, g.n2 * g.h, g.tile1, 0, in, out);
+}
+
+template <typename R>
 void Launch<R>::lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> *p, const cpx<R> *uk, cpx<R> *um,
                                const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials) {
     const int n = (int)(6 * g.S);
@@ -891,8 +1456,8 @@ void Launch<R>::lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> 
 
 template <typename R>
 void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
-                             cpx<R> *wd, cpx<R> *x, MinresState *state) {
-    const int n = (int)(6 * g.S);
+                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long nl) {
+    const int n = (int)nl;
     k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, ua, ub, wc, wd, x, state);
 }
 

@@ -28,7 +28,7 @@ HOM_PREC_FP32_FIELDS, HOM_PREC_FP64 = 0, 1
 EXPORTED = [
     "hom_default_options", "hom_create", "hom_solve", "hom_effective_stiffness",
     "hom_fields", "hom_apply", "hom_rhs", "hom_fft_forward", "hom_fft_inverse",
-    "hom_project", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
+    "hom_project", "hom_apply_spectrum", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
     "hom_solve_batch", "hom_autotune", "hom_solve_mixed", "hom_pfs",
     "hom_j2_begin", "hom_j2_increment", "hom_j2_state", "hom_j2_end",
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
     lib.hom_fft_forward.argtypes = [vp, vp, vp]
     lib.hom_fft_inverse.argtypes = [vp, vp, vp]
     lib.hom_project.argtypes = [vp, vp, vp]
+    lib.hom_apply_spectrum.argtypes = [vp, vp, vp]
     lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
     lib.hom_apply_noalloc.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.hom_modb_apply.argtypes = [vp, vp, vp]
@@ -403,8 +404,17 @@ def hom_project(ctx: Context, field, out=None):
     return out
 
 
-KERNEL_NAMES = ["x1_inv_gamma", "x2_inv", "x3_c2r_law_r2c", "x2_fwd", "x1_fwd_gamma_dot", "alpha",
-                "lanczos_update", "givens"]
+def hom_apply_spectrum(ctx: Context, spectrum, out=None):
+    """G F C F^-1 G on a spectrum (n1, n2, n3//2+1, 6) complex, Mandel, units of E."""
+    if out is None:
+        assert not ctx.device_ptrs
+        out = np.empty(spectrum_shape(ctx), dtype=np.complex64 if ctx.dtype == np.float32 else np.complex128)
+    _check(ctx.handle, load_library().hom_apply_spectrum(ctx.handle, _ptr(spectrum), _ptr(out)))
+    return out
+
+
+# hom_time_kernels order: the launches of one elastic MINRES step
+KERNEL_NAMES = ["x2_inv", "x3_c2r_law_energy_r2c", "alpha", "x2_fwd", "x1_fwd_lanczos_inv", "givens"]
 
 
 def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:

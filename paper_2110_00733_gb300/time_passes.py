@@ -35,8 +35,8 @@ from paper_2110_00733_gb300 import hom  # noqa: E402
 
 def bytes_per_voxel(n3: int) -> dict:
     spec = 48.0 * (n3 // 2 + 1) / n3
-    return {"x1_inv_gamma": 2 * spec, "x2_inv": 2 * spec, "x3_c2r_law_r2c": 2 * spec + 4,
-            "x2_fwd": 2 * spec, "x1_fwd_gamma_dot": 3 * spec, "lanczos_update": 9 * spec}
+    return {"x2_inv": 2 * spec, "x3_c2r_law_energy_r2c": 2 * spec + 4, "x2_fwd": 2 * spec,
+            "x1_fwd_lanczos_inv": 10 * spec}
 
 
 def main():
@@ -61,7 +61,7 @@ def main():
 
 
 # kernel launches of one MINRES iteration in hom_time_kernels order
-ORDER = ["x1_inv_gamma", "x2_inv", "x3_c2r_law_r2c", "x2_fwd", "x1_fwd_gamma_dot", "lanczos_update"]
+ORDER = ["x2_inv", "x3_c2r_law_energy_r2c", "x2_fwd", "x1_fwd_lanczos_inv"]
 
 
 def write_traffic(csv_path, shape):

@@ -252,3 +252,25 @@ def test_solve_octet128_matches_stored_oracle(hom, tol):
             err = np.max(np.abs(np.array(inf["sigma_mean"]) - ref)) / np.max(np.abs(ref))
             assert err <= 1e-4, (case["macro_strain"], err)
             assert inf["true_residual"] <= tol
+
+
+# the spectral operator the MINRES iteration applies; n3 in {64, 128, 256}
+# runs the register-resident n3 pass in FP32, the others the shared-memory one
+SPEC_SHAPES = [(16, 8, 64), (8, 12, 128), (64, 64, 256), (12, 10, 9), (32, 32, 32), (6, 4, 256)]
+
+
+@pytest.mark.parametrize("deriv", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", SPEC_SHAPES)
+def test_apply_spectrum(hom, shape, prec, deriv):
+    """G F C F^-1 G on the DFT of a field equals the DFT of the oracle's
+    A(G e), eq. (linearOp) with the projector of eq. (galop) on the input."""
+    phi = ri.random_phi(shape, seed=12)
+    f = ri.random_field(shape, seed=13)
+    spec_in = np.moveaxis(half_spectrum(np.stack([oracle.fft3d(f[c].astype(complex)) for c in range(6)])), 0, -1)
+    ref_real = oracle.apply(phi, 1.0, NU_M, deriv, oracle.project(shape, deriv, f))
+    ref = np.moveaxis(half_spectrum(np.stack([oracle.fft3d(ref_real[c].astype(complex)) for c in range(6)])), 0, -1)
+    with make(hom, phi, prec, deriv) as ctx:
+        cdt = np.complex64 if prec == "fp32" else np.complex128
+        got = hom.hom_apply_spectrum(ctx, np.ascontiguousarray(spec_in.astype(cdt)))
+        assert rel_maxerr(got, ref) <= tol(prec)
