@@ -90,6 +90,7 @@ struct Geometry {
     // spectrum-to-spectrum applications
     int x3r;
     int grid2_tma, grid1_tma, grid1d_tma;
+    int grid1l_tma;         // persistent grid of the fused MINRES n1 pass (0: plain-load form)
     size_t smem2_tma, smem1_tma, smem1d_tma;
     void *tma_cache;
     int *err;

@@ -425,7 +425,7 @@ __device__ __forceinline__ void x3r_stage2(const float2 *slab, int t, float2 (&z
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 3) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
+__global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
                                                 int material, float lam, float mu2, const float *__restrict__ phi,
                                                 const MinresState *state, double *__restrict__ epart) {
     if (skip(state)) return;
@@ -442,34 +442,29 @@ __global__ void __launch_bounds__(128, 3) k_x3r(Geometry g, const float2 *__rest
     const int lane0 = (threadIdx.x & 31) & ~(P - 1);
     const int partner = lane0 + ((P - j) & (P - 1));
     float2 z[3][Q];
-    // ---- input: own frequencies k = j + P m <= N/2 (m < Q/2, and m = Q/2 for j = 0)
-    {
-        float2 zc[3][Q / 2 + 1];   // conj X_a[k] + i conj X_b[k] = Z[N - k], for the partner
-        const float2 *rp = in + (size_t)(live ? row : 0) * H * NC;
+    // ---- input, one line at a time: own frequencies k = j + P m <= N/2
+    // (m < Q/2, and m = Q/2 for j = 0); the upper half m > Q/2 (and m = Q/2
+    // for j != 0) is Z[j + P m] = Zc[N - j - P m], held by the partner at
+    // m' = Q - 1 - m (by lane 0 itself at Q - m)
+    const float2 *rp = in + (size_t)(live ? row : 0) * H * NC;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        float2 zc[Q / 2 + 1];   // conj X_a[k] + i conj X_b[k] = Z[N - k], for the partner
 #pragma unroll
         for (int m = 0; m <= Q / 2; ++m) {
             const int k = j + P * m;
-            const bool own = live && (m < Q / 2 || j == 0);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (own) v = reinterpret_cast<const float4 *>(rp + NC * k)[p];
-                if (k == 0 || 2 * k == N) { v.y = 0.f; v.w = 0.f; }   // self-conjugate bins: real parts
-                // a = (v.x, v.y), b = (v.z, v.w): Z = a + i b, Zc = conj a + i conj b
-                z[p][m < Q ? m : 0] = make_float2(v.x - v.w, v.y + v.z);
-                zc[p][m] = make_float2(v.x + v.w, v.z - v.y);
-            }
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (live && (m < Q / 2 || j == 0)) v = reinterpret_cast<const float4 *>(rp + NC * k)[p];
+            if (k == 0 || 2 * k == N) { v.y = 0.f; v.w = 0.f; }   // self-conjugate bins: real parts
+            // a = (v.x, v.y), b = (v.z, v.w): Z = a + i b, Zc = conj a + i conj b
+            z[p][m] = make_float2(v.x - v.w, v.y + v.z);
+            zc[m] = make_float2(v.x + v.w, v.z - v.y);
         }
-        // upper half m > Q/2 (and m = Q/2 for j != 0): Z[j + P m] = Zc[N - j - P m],
-        // held by the partner at m' = Q - 1 - m (by lane 0 itself at Q - m)
 #pragma unroll
         for (int s = 0; s < Q / 2; ++s) {
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                const float2 got = shfl_partner<P>(zc[p][s], partner);
-                const int m = Q - 1 - s;
-                z[p][m] = (j == 0) ? (m > Q / 2 ? zc[p][Q - m] : z[p][m]) : got;
-            }
+            const float2 got = shfl_partner<P>(zc[s], partner);
+            const int m = Q - 1 - s;
+            z[p][m] = (j == 0) ? (m > Q / 2 ? zc[Q - m] : z[p][m]) : got;
         }
     }
     // ---- inverse transform (C2R part of eq. linearOp)
@@ -871,15 +866,25 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
             continue;
         }
         const int k2 = col / H, k3 = col - k2 * H;
-        const GammaE<R> ge = gamma_e<R>(g, e, k2, k3);
-        cpx<R> v[NC], u[NC], uo[NC];
+        cpx<R> v[NC], u[NC], uo[NC], a[NC], b[NC], xx[NC];
         const size_t i = kb + (size_t)f * NC;
+        // all global loads of the frequency first, then the arithmetic
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            Six<R>::load_pair(sp, p, v[2 * p], v[2 * p + 1]);
             Six<R>::load_pair(uk + i, p, u[2 * p], u[2 * p + 1]);
             Six<R>::load_pair(um + i, p, uo[2 * p], uo[2 * p + 1]);
         }
+        if (c.lagged) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                Six<R>::load_pair(wa + i, p, a[2 * p], a[2 * p + 1]);
+                Six<R>::load_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
+                Six<R>::load_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) Six<R>::load_pair(sp, p, v[2 * p], v[2 * p + 1]);
+        const GammaE<R> ge = gamma_e<R>(g, e, k2, k3);
         gamma_apply<R>(g, ge, v);
         const R w = (R)pweight(k3, g.n3);
 #pragma unroll
@@ -891,13 +896,6 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
 #pragma unroll
         for (int p = 0; p < 3; ++p) Six<R>::store_pair(um + i, p, v[2 * p], v[2 * p + 1]);
         if (c.lagged) {
-            cpx<R> a[NC], b[NC], xx[NC];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                Six<R>::load_pair(wa + i, p, a[2 * p], a[2 * p + 1]);
-                Six<R>::load_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
-                Six<R>::load_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
-            }
 #pragma unroll
             for (int q = 0; q < NC; ++q) {
                 b[q] = mk<R>((uo[q].x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
@@ -957,18 +955,15 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
     if (threadIdx.x == 0) partials[blockIdx.x] = sum;
 }
 
-// L2 prefetch of a contiguous global range (16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void bulk_prefetch_l2(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
-                 : "memory");
-}
 
-// persistent TMA-staged form (FP32, register FFT lengths 64..256): the work
-// tile comes and goes by TMA, double-buffered as in k_x1_tma; the contiguous
-// Krylov blocks of the next tile are prefetched into L2 (bulk prefetch)
-// while the current one is computed, and are then read with plain loads.
+// persistent TMA-staged form (FP32, register FFT lengths 64..256, at most
+// 192 threads per CTA): the work tile comes and goes by TMA, double-buffered
+// as in k_x1_tma; the contiguous Krylov blocks of a tile are read and
+// written with plain coalesced accesses.  (Prefetching the next tile's
+// blocks into L2 was measured to double the DRAM reads: the lines were
+// evicted before use.)
 template <typename R, int NF>
-__global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec,
+__global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec,
                                                     const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
                                                     const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
                                                     cpx<R> *__restrict__ x, const MinresState *state,
@@ -991,21 +986,10 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos_tma(Geometry g, const __grid_cons
         fence_mbar_init();
     }
     __syncthreads();
-    auto prefetch = [&](int t) {
-        const size_t o = (size_t)t * per;
-        bulk_prefetch_l2(uk + o, bytes);
-        bulk_prefetch_l2(um + o, bytes);
-        if (c.lagged) {
-            bulk_prefetch_l2(wa + o, bytes);
-            bulk_prefetch_l2(wb + o, bytes);
-            bulk_prefetch_l2(x + o, bytes);
-        }
-    };
     int tile = blockIdx.x;
     if (leader && tile < ntiles) {
         mbar_expect_tx(&bar[0], bytes);
         tma_load_2d(base, &tspec, NC * T * tile, 0, &bar[0]);
-        prefetch(tile);
     }
     Acc<R> acc;
     for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
@@ -1015,7 +999,6 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos_tma(Geometry g, const __grid_cons
             bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
             mbar_expect_tx(&bar[s ^ 1], bytes);
             tma_load_2d(base + (s ^ 1) * per, &tspec, NC * T * next, 0, &bar[s ^ 1]);
-            prefetch(next);
         }
         const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -1309,6 +1292,16 @@ int Launch<R>::tma_grids(Geometry &g) {
             g.tma = 0;
             return 0;
         }
+        // the fused MINRES n1 pass (launch bounds: 192 threads per CTA)
+        int b1l = 0;
+        if (g.nc == 6 && g.threads1 <= 192) {
+            switch (g.fast[0]) {
+                case 64: b1l = occ(k_x1_lanczos_tma<R, 64>, g.threads1, g.smem1_tma); break;
+                case 128: b1l = occ(k_x1_lanczos_tma<R, 128>, g.threads1, g.smem1_tma); break;
+                default: b1l = occ(k_x1_lanczos_tma<R, 256>, g.threads1, g.smem1_tma); break;
+            }
+        }
+        g.grid1l_tma = b1l * sms;
         g.grid2_tma = b2 * sms;
         g.grid1_tma = b1 * sms;
         g.grid1d_tma = b1d * sms;
@@ -1409,17 +1402,17 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 
 template <typename R>
 int Launch<R>::x1_lanczos_grid(const Geometry &g) {
-    return g.tma ? g.grid1_tma : (g.n2 * g.h + g.tile1 - 1) / g.tile1;
+    return (g.tma && g.grid1l_tma > 0) ? g.grid1l_tma : (g.n2 * g.h + g.tile1 - 1) / g.tile1;
 }
 
 template <typename R>
 void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
                            const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials) {
     if constexpr (sizeof(R) == 4) {
-        if (g.tma) {
+        if (g.tma && g.grid1l_tma > 0) {
             const CUtensorMap *ts = tma_map(g, spec, TMA_X1, 1);
 #define HOM_X1LT(NF)                                                                                         \
-    k_x1_lanczos_tma<R, NF><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials)
+    k_x1_lanczos_tma<R, NF><<<g.grid1l_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials)
             switch (g.fast[0]) {
                 case 64: HOM_X1LT(64); break;
                 case 128: HOM_X1LT(128); break;
