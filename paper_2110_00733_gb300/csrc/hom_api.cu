@@ -145,6 +145,25 @@ struct hom_ctx {
     bool tangent_op = false;         // operator of eq. (galnonlin) with the J2 tangent (FP64)
     bool graph_tangent = false;      // the captured graph applies the tangent operator
     J2State j2;
+    // Elastic MINRES on a stacked batch of load cases (the solve path of
+    // hom_solve): capacity in cases, the stacked geometry of the captured
+    // graph and its TMA cache, work spectra and Krylov vectors of every case,
+    // FP64 right-hand sides and residuals, one state per case, partials, graph.
+    int bcap = 0;
+    Geometry bg{};
+    void *btma = nullptr;
+    void *bspec = nullptr;                       // bcap x 6S, solve precision
+    void *bv[2] = {nullptr, nullptr};            // bcap x kvec each (n1-tile order)
+    void *bw[2] = {nullptr, nullptr};
+    void *bx = nullptr;
+    void *brhs = nullptr;                        // bcap x 6S: right-hand sides, then iterates
+    double2 *bb64 = nullptr, *br64 = nullptr;    // bcap x 6S
+    MinresState *d_bst = nullptr, *h_bst = nullptr;
+    double *bpart = nullptr;
+    cudaGraphExec_t bgraph = nullptr;
+    int bgraph_nb = 0;
+    bool bgraph_loops = false;
+    long long bgraph_kernels = 0;
     int graph_iters = 6;
     long long graph_kernels = 0;
     long long launches = 0;
@@ -152,6 +171,8 @@ struct hom_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
 };
+
+static void batch_free(hom_ctx *ctx);
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -445,48 +466,27 @@ static int spec_norm2(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, double *out) 
     return HOM_OK;
 }
 
-// Capture graph_iters MINRES iterations once (graph_iters even: the buffer
-// roles repeat every 2 steps).  Unnormalised Lanczos vectors u_k = beta_k v_k
-// alternate between vbuf[1] (odd k) and vbuf[0] (even k); w_j sits in
-// wbuf[0] for even j and wbuf[1] for odd j.
-//
-// Elastic operator (fused chain, six launches per step): the work spectrum
-// enters a step holding the inverse n1 transform of G u_k (left there by
-// the previous step, or by run_minres before the first); the n2 inverse,
-// the n3 pass with the material law and the strain-energy sums that give
-// alpha_k = <u_k, A^ u_k> / beta_k^2, the alpha reduction, the n2 forward,
-// the fused n1 pass (projector, Lanczos step, lagged w / x update, projector
-// and inverse n1 transform of u_{k+1}) and the Givens step.
-// Tangent operator of the J2 extension: op_spec (p = A^ u_k in vbuf[2], with
-// the dot product), the alpha reduction, the Lanczos / update kernel and the
-// Givens step.
+// Capture graph_iters MINRES iterations of the tangent operator (the J2
+// Newton systems; the elastic operator runs as a stacked batch, see
+// capture_bbody) once (graph_iters even: the buffer roles repeat every 2
+// steps).  Unnormalised Lanczos vectors u_k = beta_k v_k alternate between
+// vbuf[1] (odd k) and vbuf[0] (even k); p = A^ u_k is vbuf[2]; w_j sits in
+// wbuf[0] for even j and wbuf[1] for odd j.  A step is op_spec with the dot
+// product <u_k, p>, the alpha reduction, the Lanczos step fused with the
+// lagged w / x update, and the Givens step.
 template <typename R>
 static void capture_body(hom_ctx *ctx, Engine<R> &E) {
     cpx<R> *ua = (cpx<R> *)ctx->vbuf[0], *ub = (cpx<R> *)ctx->vbuf[1], *p = (cpx<R> *)ctx->vbuf[2];
     cpx<R> *wc = (cpx<R> *)ctx->wbuf[0], *wd = (cpx<R> *)ctx->wbuf[1];
     cpx<R> *x = (cpx<R> *)ctx->xs;
     const int np1 = Launch<R>::x1_grid(E.g), npe = Launch<R>::ew_grid(6 * ctx->S);
-    const int np3 = Launch<R>::x3_epart_grid(E.g), npl = Launch<R>::x1_lanczos_grid(E.g);
     cudaStream_t s = ctx->stream;
     for (int it = 0; it < ctx->graph_iters; ++it) {
         const bool odd = (it % 2) == 0;          // step k = it + 1 (mod 2)
         cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
         cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;   // w_{k-2}, w_{k-3}
-        if (!ctx->tangent_op) {
-            Launch<R>::x2(E.g, s, 1, E.spec, ctx->d_state);
-            Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
-                          E.spec, E.phi, ctx->d_state, ctx->partials);
-            scalar_alpha(s, ctx->d_state, ctx->partials, np3, (double)ctx->V);
-            Launch<R>::x2(E.g, s, 0, E.spec, ctx->d_state);
-            Launch<R>::x1_lanczos(E.g, s, E.spec, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
-            scalar_givens(s, ctx->d_state, ctx->partials, npl);
-            ctx->launches += 6;
-            continue;
-        }
-        // p = A^ u_k, partial <u_k, p>
         op_spec<R>(ctx, E, uk, p, true, ctx->partials, ctx->d_state);
         scalar_alpha(s, ctx->d_state, ctx->partials, np1);
-        // u_{k+1} over u_{k-1}, partial ||u_{k+1}||^2, lagged w_{k-1} / x update
         Launch<R>::lanczos_update(E.g, s, p, uk, um, wa, wb, x, ctx->d_state, ctx->partials);
         scalar_givens(s, ctx->d_state, ctx->partials, npe);
         ctx->launches += 3;
@@ -567,10 +567,7 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     CU(cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const double beta1 = ctx->h_state->beta1;
-    const bool fused = !ctx->tangent_op;
-    // Krylov vectors in the fused chain's padded tile order (zero padding)
-    const long long nv = fused ? 2 * E.g.kvec : nr;
-    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * nv, s));
+    CU(cudaMemsetAsync(ctx->xs, 0, sizeof(R) * nr, s));
     if (!(beta1 > 0.0) || !std::isfinite(beta1)) {
         *iters = 0;
         *est = 0.0;
@@ -579,18 +576,10 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         return HOM_OK;
     }
     // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0
-    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nv, s));
-    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nv, s));
-    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nv, s));
-    if (fused) {
-        CU(cudaMemsetAsync(ctx->vbuf[1], 0, sizeof(R) * nv, s));
-        Launch<R>::to_tiles(E.g, s, (const cpx<R> *)ctx->rhs, (cpx<R> *)ctx->vbuf[1]);
-        // the fused chain enters each step with F_1^-1 G u_k in the work spectrum
-        Launch<R>::x1(E.g, s, X1_GAMMA_IN, (const cpx<R> *)ctx->rhs, E.spec, nullptr, nullptr, nullptr);
-        ctx->launches += 2;
-    } else {
-        CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
-    }
+    CU(cudaMemsetAsync(ctx->vbuf[0], 0, sizeof(R) * nr, s));
+    CU(cudaMemcpyAsync(ctx->vbuf[1], ctx->rhs, sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemsetAsync(ctx->wbuf[0], 0, sizeof(R) * nr, s));
+    CU(cudaMemsetAsync(ctx->wbuf[1], 0, sizeof(R) * nr, s));
     if (ctx->graph_loops) {
         // one launch: the device repeats the body until done (or the cap)
         CU(cudaGraphLaunch(ctx->graph, s));
@@ -613,13 +602,8 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
     }
     // the last step's lagged w / x update
     Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->wbuf[0],
-                            (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state, nv / 2);
+                            (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state, 6 * ctx->S);
     ctx->launches += 1;
-    if (fused) {   // the iterate back in the standard half-spectrum order
-        Launch<R>::from_tiles(E.g, s, (const cpx<R> *)ctx->xs, (cpx<R> *)ctx->vbuf[2]);
-        CU(cudaMemcpyAsync(ctx->xs, ctx->vbuf[2], sizeof(R) * nr, cudaMemcpyDeviceToDevice, s));
-        ctx->launches += 1;
-    }
     *iters = ctx->h_state->k;
     *est = ctx->h_state->est;
     *status = ctx->h_state->status == -5 ? HOM_ENAN : (ctx->h_state->status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
@@ -926,6 +910,7 @@ void hom_destroy(hom_ctx *ctx) {
     j2_free(ctx);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cg_graph) cudaGraphExecDestroy(ctx->cg_graph);
+    batch_free(ctx);
     cudaFree(ctx->d_cg);
     if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
     engine_free(ctx->e32);
@@ -990,7 +975,9 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     }
     const long long nr = 12 * ctx->S;   // reals per spectral vector (>= 6 V)
     const size_t rs = (ctx->prec == HOM_PREC_FP64) ? sizeof(double) : sizeof(float);
-    // Krylov vectors: a half spectrum, or the padded n1-tile order of the fused chain
+    // single-case Krylov vectors (half spectra): the tangent operator's MINRES,
+    // CG / PCG, and scratch of the step entry points and the timing instrument
+    // (which runs the fused chain on one case: the padded n1-tile order)
     const long long kv = (ctx->prec == HOM_PREC_FP64) ? ctx->e64.g.kvec : ctx->e32.g.kvec;
     const long long nk = std::max(nr, 2 * kv);
     for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->vbuf[i], rs * nk));
@@ -1274,12 +1261,256 @@ int hom_fft_inverse(hom_ctx *ctx, const void *spectrum, void *field) { return st
 int hom_project(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 4, in, out, nullptr); }
 int hom_apply_spectrum(hom_ctx *ctx, const void *in, void *out) { return step(ctx, 5, in, out, nullptr); }
 
+// ----- stacked-batch MINRES ---------------------------------------------------------
+static void batch_free(hom_ctx *ctx) {
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    ctx->bgraph_nb = 0;
+    tma_cache_free(ctx->btma);
+    ctx->btma = nullptr;
+    for (void *p : {ctx->bspec, ctx->bv[0], ctx->bv[1], ctx->bw[0], ctx->bw[1], ctx->bx, ctx->brhs}) cudaFree(p);
+    cudaFree(ctx->bb64);
+    cudaFree(ctx->br64);
+    cudaFree(ctx->d_bst);
+    cudaFree(ctx->bpart);
+    if (ctx->h_bst) cudaFreeHost(ctx->h_bst);
+    ctx->bspec = ctx->bv[0] = ctx->bv[1] = ctx->bw[0] = ctx->bw[1] = ctx->bx = ctx->brhs = nullptr;
+    ctx->bb64 = ctx->br64 = nullptr;
+    ctx->d_bst = ctx->h_bst = nullptr;
+    ctx->bpart = nullptr;
+    ctx->bcap = 0;
+}
+
+// device bytes of one load case of a stacked batch
+static long long batch_case_bytes(const hom_ctx *ctx) {
+    const long long n6 = 6 * ctx->S;
+    const bool f64 = ctx->prec == HOM_PREC_FP64;
+    const long long cs = f64 ? 16 : 8;
+    const long long kv = f64 ? ctx->e64.g.kvec : ctx->e32.g.kvec;
+    return cs * (2 * n6 + 5 * kv) + 2 * 16 * n6;
+}
+
+// room for nb load cases (frees and reallocates when it grows)
+static int batch_reserve(hom_ctx *ctx, int nb) {
+    if (ctx->bcap >= nb) return HOM_OK;
+    batch_free(ctx);
+    const long long n6 = 6 * ctx->S;
+    const bool f64 = ctx->prec == HOM_PREC_FP64;
+    const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
+    const long long kv = f64 ? ctx->e64.g.kvec : ctx->e32.g.kvec;
+    CU(cudaMalloc(&ctx->bspec, cs * n6 * nb));
+    for (int i = 0; i < 2; ++i) {
+        CU(cudaMalloc(&ctx->bv[i], cs * kv * nb));
+        CU(cudaMalloc(&ctx->bw[i], cs * kv * nb));
+    }
+    CU(cudaMalloc(&ctx->bx, cs * kv * nb));
+    CU(cudaMalloc(&ctx->brhs, cs * n6 * nb));
+    CU(cudaMalloc(&ctx->bb64, sizeof(double2) * n6 * nb));
+    CU(cudaMalloc(&ctx->br64, sizeof(double2) * n6 * nb));
+    CU(cudaMalloc(&ctx->d_bst, sizeof(MinresState) * nb));
+    CU(cudaMallocHost(&ctx->h_bst, sizeof(MinresState) * nb));
+    long long np = Launch<double>::ew_grid(n6);
+    if (f64) {
+        np = std::max(np, (long long)Launch<double>::x3_epart_grid(ctx->e64.g));
+        np = std::max(np, (long long)Launch<double>::x1_lanczos_grid(ctx->e64.g));
+    } else {
+        np = std::max(np, (long long)Launch<float>::x3_epart_grid(ctx->e32.g));
+        np = std::max(np, (long long)Launch<float>::x1_lanczos_grid(ctx->e32.g));
+    }
+    CU(cudaMalloc(&ctx->bpart, sizeof(double) * np * nb));
+    ctx->bcap = nb;
+    return HOM_OK;
+}
+
+// Load cases per stacked batch: at most kNbMax and ncase, as many as fit
+// in the free device memory (at least one).
+static int batch_width(hom_ctx *ctx, int ncase) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const long long per = batch_case_bytes(ctx);
+    const long long avail = (long long)(0.9 * (double)fr) + (long long)ctx->bcap * per;
+    long long fit = per > 0 ? avail / per : 1;
+    int nb = std::min(ncase, kNbMax);
+    if (fit < nb) nb = (int)std::max(1LL, fit);
+    return nb;
+}
+
+// One step of the fused chain for every case of the stacked batch (see the
+// kernels in hom_passes.cuh): n2 inverse, n3 pass with the material law and
+// the strain-energy sums, alpha (one CTA per case), n2 forward, fused n1 pass
+// (projector, Lanczos step, lagged w / x update, projector and inverse of
+// u_{k+1}), Givens step (one CTA per case).  Buffer roles as in capture_body.
+template <typename R>
+static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
+    const Geometry &g = ctx->bg;
+    const int nb = g.nb;
+    cpx<R> *ua = (cpx<R> *)ctx->bv[0], *ub = (cpx<R> *)ctx->bv[1];
+    cpx<R> *wc = (cpx<R> *)ctx->bw[0], *wd = (cpx<R> *)ctx->bw[1];
+    cpx<R> *x = (cpx<R> *)ctx->bx, *spec = (cpx<R> *)ctx->bspec;
+    const int np3 = Launch<R>::x3_epart_grid(g), npl = Launch<R>::x1_lanczos_grid(g);
+    cudaStream_t s = ctx->stream;
+    for (int it = 0; it < ctx->graph_iters; ++it) {
+        const bool odd = (it % 2) == 0;
+        cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
+        cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;
+        Launch<R>::x2(g, s, 1, spec, ctx->d_bst);
+        Launch<R>::x3(g, s, X3_IN_SPEC, spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, spec,
+                      E.phi, ctx->d_bst, ctx->bpart);
+        scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, nb);
+        Launch<R>::x2(g, s, 0, spec, ctx->d_bst);
+        Launch<R>::x1_lanczos(g, s, spec, uk, um, wa, wb, x, ctx->d_bst, ctx->bpart);
+        scalar_givens(s, ctx->d_bst, ctx->bpart, npl, nb);
+        ctx->launches += 6;
+    }
+}
+
+// the stacked batch's solve graph for nb cases: a device-side WHILE loop
+// over graph_iters steps, or (host_loop / no conditional nodes) the body
+// alone, replayed by the host
+template <typename R>
+static int build_bgraph(hom_ctx *ctx, Engine<R> &E, int nb) {
+    if (ctx->bgraph && ctx->bgraph_nb == nb) return HOM_OK;
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    tma_cache_free(ctx->btma);
+    ctx->btma = E.g.tma ? tma_cache_new() : nullptr;
+    ctx->bg = E.g;
+    ctx->bg.nb = nb;
+    ctx->bg.tma_cache = ctx->btma;
+    const long long before = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    bool loops = false;
+    if (!ctx->host_loop && cudaGraphCreate(&graph, 0) == cudaSuccess) {
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        cudaGraphNode_t node;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                CU(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+                capture_bbody<R>(ctx, E);
+                loop_cond(ctx->stream, h, ctx->d_bst, nb);
+                ctx->launches += 1;
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &body);
+                if (e != cudaSuccess) {
+                    cudaGraphDestroy(graph);
+                    return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                }
+                loops = true;
+            }
+        }
+        if (!loops) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+    }
+    if (!loops) {
+        CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        capture_bbody<R>(ctx, E);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    ctx->bgraph_kernels = ctx->launches - before;
+    ctx->launches = before;
+    cudaError_t e = cudaGraphInstantiate(&ctx->bgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, HOM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->bgraph_loops = loops;
+    ctx->bgraph_nb = nb;
+    return HOM_OK;
+}
+
+// MINRES from a zero start on the nb stacked right-hand sides in ctx->brhs
+// (standard order, solve precision); case j runs with tolerance tol[j] and
+// at most maxit[j] iterations (0: the case sits this sweep out).  On return
+// ctx->brhs holds the iterates (standard order; zero for cases that did not
+// run) and its / est / st the per-case iterations, estimated residual and
+// status.
+template <typename R>
+static int run_minres_batch(hom_ctx *ctx, Engine<R> &E, int nb, const double *tol, const int *maxit, int *its,
+                            double *est, int *st) {
+    cudaStream_t s = ctx->stream;
+    const long long n6 = 6 * ctx->S, kv = E.g.kvec;
+    int rc = build_bgraph<R>(ctx, E, nb);
+    if (rc) return rc;
+    int mx = 0;
+    for (int j = 0; j < nb; ++j) mx = std::max(mx, maxit[j]);
+    const int max_replays = (mx + ctx->graph_iters - 1) / ctx->graph_iters + 1;
+    const int npe = Launch<R>::ew_grid(n6);
+    cpx<R> *rhs = (cpx<R> *)ctx->brhs, *spec = (cpx<R> *)ctx->bspec;
+    for (int j = 0; j < nb; ++j) {
+        Launch<R>::norm2w(E.g, s, rhs + j * n6, ctx->bpart + (size_t)j * npe);
+        scalar_start(s, ctx->d_bst + j, ctx->bpart + (size_t)j * npe, npe, tol[j], maxit[j], max_replays);
+    }
+    ctx->launches += 2 * nb;
+    CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < nb; ++j) any = any || !ctx->h_bst[j].done;
+    CU(cudaMemsetAsync(ctx->bx, 0, sizeof(cpx<R>) * kv * nb, s));
+    if (any) {
+        // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0, in tile order;
+        // the work spectrum enters each step holding F_1^-1 G u_k
+        CU(cudaMemsetAsync(ctx->bv[0], 0, sizeof(cpx<R>) * kv * nb, s));
+        CU(cudaMemsetAsync(ctx->bv[1], 0, sizeof(cpx<R>) * kv * nb, s));
+        CU(cudaMemsetAsync(ctx->bw[0], 0, sizeof(cpx<R>) * kv * nb, s));
+        CU(cudaMemsetAsync(ctx->bw[1], 0, sizeof(cpx<R>) * kv * nb, s));
+        for (int j = 0; j < nb; ++j) {
+            if (ctx->h_bst[j].done) continue;
+            Launch<R>::to_tiles(E.g, s, rhs + j * n6, (cpx<R> *)ctx->bv[1] + j * kv);
+            Launch<R>::x1(E.g, s, X1_GAMMA_IN, rhs + j * n6, spec + j * n6, nullptr, nullptr, nullptr);
+            ctx->launches += 2;
+        }
+        if (ctx->bgraph_loops) {
+            CU(cudaGraphLaunch(ctx->bgraph, s));
+            CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            ctx->launches += (long long)ctx->h_bst[0].bodies * ctx->bgraph_kernels;
+        } else {
+            const int per_check = 4;
+            int replays = 0;
+            while (true) {
+                for (int r = 0; r < per_check && replays < max_replays; ++r, ++replays) {
+                    CU(cudaGraphLaunch(ctx->bgraph, s));
+                    ctx->launches += ctx->bgraph_kernels;
+                }
+                CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
+                CU(cudaStreamSynchronize(s));
+                bool live = false;
+                for (int j = 0; j < nb; ++j) live = live || !ctx->h_bst[j].done;
+                if (!live || replays >= max_replays) break;
+            }
+        }
+        Launch<R>::minres_flush(ctx->bg, s, (const cpx<R> *)ctx->bv[0], (const cpx<R> *)ctx->bv[1],
+                                (cpx<R> *)ctx->bw[0], (cpx<R> *)ctx->bw[1], (cpx<R> *)ctx->bx, ctx->d_bst, kv);
+        ctx->launches += 1;
+    }
+    // iterates back in the standard half-spectrum order, over the right-hand sides
+    for (int j = 0; j < nb; ++j) Launch<R>::from_tiles(E.g, s, (const cpx<R> *)ctx->bx + j * kv, rhs + j * n6);
+    ctx->launches += nb;
+    CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int j = 0; j < nb; ++j) {
+        const MinresState &h = ctx->h_bst[j];
+        its[j] = h.k;
+        est[j] = h.est;
+        st[j] = !std::isfinite(h.beta1) || h.status == -5 ? HOM_ENAN : (h.status == 1 ? HOM_NOT_CONVERGED : HOM_OK);
+        if (maxit[j] <= 0 || h.beta1 == 0.0) est[j] = 0.0;
+    }
+    return HOM_OK;
+}
+
 // ----- solve -------------------------------------------------------------------
 // ||A^ x - b^||_w / ||b^||_w in FP64 (Parseval: the real-space ratio of
 // eq. (galres)); leaves b^ - A^ x in r64.
-static int true_residual(hom_ctx *ctx, const double2 *x, double bnorm, double *res) {
-    op_spec<double>(ctx, ctx->e64, x, ctx->r64, false, nullptr, nullptr);
-    spec_residual64(ctx->e64.g, ctx->stream, ctx->b64, ctx->r64, ctx->r64, ctx->partials);
+static int true_residual(hom_ctx *ctx, const double2 *x, const double2 *b, double2 *r, double bnorm, double *res) {
+    op_spec<double>(ctx, ctx->e64, x, r, false, nullptr, nullptr);
+    spec_residual64(ctx->e64.g, ctx->stream, b, r, r, ctx->partials);
     reduce_to(ctx->stream, ctx->partials, ew_blocks(6 * ctx->S), ctx->d_scalar);
     ctx->launches += 2;
     CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1529,7 +1760,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
             mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
             real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
             ctx->launches += 2;
-            rc = true_residual(ctx, x, bnorm, &tres);
+            rc = true_residual(ctx, x, ctx->b64, ctx->r64, bnorm, &tres);
             if (rc) return rc;
         } else if (warm) {
             // FP32 fields: the projection and the residual that starts the
@@ -1553,7 +1784,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
             CU(cudaStreamSynchronize(s));
             tres = std::sqrt(*ctx->h_scalar) / bnorm;
             if (tres < kWarmFp64Below) {
-                rc = true_residual(ctx, x, bnorm, &tres);
+                rc = true_residual(ctx, x, ctx->b64, ctx->r64, bnorm, &tres);
                 if (rc) return rc;
             }
         } else {   // x = 0: r = b
@@ -1589,7 +1820,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
             inf.est_residual = est * tres;     // relative to ||b||
             inf.sweeps = sw + 1;
             const double prev = tres;
-            rc = true_residual(ctx, x, bnorm, &tres);
+            rc = true_residual(ctx, x, ctx->b64, ctx->r64, bnorm, &tres);
             if (rc) return rc;
             if (st == HOM_ENAN) { status = HOM_ENAN; break; }
             if (ctx->prec == HOM_PREC_FP32_FIELDS && !(tres < prev)) {
@@ -1597,7 +1828,7 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
                 // under stress control): take it back and stop
                 spec_f2d_acc(nc, s, (const float2 *)ctx->xs, x, -1.0);
                 ctx->launches += 1;
-                rc = true_residual(ctx, x, bnorm, &tres);
+                rc = true_residual(ctx, x, ctx->b64, ctx->r64, bnorm, &tres);
                 if (rc) return rc;
                 status = HOM_NOT_CONVERGED;
                 break;
@@ -1610,6 +1841,184 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
     return finish_case(ctx, icase, m, x, &inf, status, info);
 }
 
+// Galerkin-MINRES of the load cases [c0, c0 + nb) as one stacked batch:
+// per case the FP64 right-hand side (from the DFT of phi) and, for a warm
+// start, the projected start and its residual; then refinement sweeps in
+// which every case still above tol runs MINRES in the same stacked launches
+// on its FP64 residual (converted to the field precision), and the FP64 true
+// residual of each case decides whether it needs another sweep.  The sweep
+// rules are those of a single case (solve_case).  info[].time_ms is the
+// device time of the whole batch.
+static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain, const double *macro_stress,
+                       double tol, int max_it, const void *warm, hom_solve_info *info) {
+    const long long nc = 6 * ctx->S;
+    cudaStream_t s = ctx->stream;
+    const int mask = ctx->e64.g.mask0;
+    const bool f32 = ctx->prec == HOM_PREC_FP32_FIELDS;
+    int rc = batch_reserve(ctx, nb);
+    if (rc) return rc;
+    std::vector<double> M(6 * nb, 0.0), bnorm(nb, 0.0), tres(nb, 1.0);
+    std::vector<int> status(nb, HOM_OK), live(nb, 0), solvable(nb, 0);
+    std::vector<hom_solve_info> inf(nb);
+    CU(cudaEventRecord(ctx->ev0, s));
+    for (int j = 0; j < nb; ++j) {
+        const int k = c0 + j;
+        double *m = &M[6 * j];
+        double sbar_v[6] = {0, 0, 0, 0, 0, 0};
+        macro_to_mandel(macro_strain + 6 * k, m);
+        if (mask) {
+            double sb[6];
+            macro_to_mandel(macro_stress + 6 * k, sb);
+            for (int c = 0; c < 6; ++c) {
+                if ((mask >> c) & 1) {
+                    m[c] = 0.0;                                   // an unknown, not a load
+                    sbar_v[c] = (double)ctx->V * sb[c] / ctx->E;  // F{sigma_bar} at xi = 0, units of E
+                }
+            }
+        }
+        for (int c = 0; c < 6; ++c) ctx->macros[6 * k + c] = m[c];
+        double2 *b = ctx->bb64 + j * nc, *r = ctx->br64 + j * nc, *x = ctx->x64[k];
+        {   // F{C : E_bar} = phi^ (C_m : E_bar): one point-wise FP64 pass
+            double tau[6];
+            const double tr = m[0] + m[1] + m[2];
+            for (int c = 0; c < 6; ++c) tau[c] = (c < 3 ? ctx->lam * tr : 0.0) + 2.0 * ctx->mu * m[c];
+            Launch<double>::rhs_phihat(ctx->e64.g, s, ctx->phihat, tau, mask ? sbar_v : nullptr, b);
+            ctx->launches += 1;
+        }
+        double b2 = 0.0;
+        rc = spec_norm2<double>(ctx, ctx->e64, b, &b2);
+        if (rc) return rc;
+        bnorm[j] = std::sqrt(b2);
+        double ce2 = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            const double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
+            ce2 += sv * sv;
+        }
+        double s2 = 0.0;
+        for (int c = 0; c < 6; ++c) s2 += sbar_v[c] * sbar_v[c];
+        const double ntau = std::sqrt(ce2 * ctx->phi2_sum) + std::sqrt(s2 / (double)ctx->V);
+        CU(cudaMemsetAsync(x, 0, sizeof(double2) * nc, s));
+        if (!std::isfinite(bnorm[j])) {
+            status[j] = HOM_ENAN;
+            continue;
+        }
+        if (bnorm[j] / std::sqrt((double)ctx->V) <= kRhsZero * ntau) {
+            inf[j].sweeps = 0;   // b vanishes up to round-off: zero fluctuation, 0 iterations
+            continue;
+        }
+        live[j] = 1;
+        solvable[j] = 1;
+        const long long n = 6 * ctx->V;
+        if (warm && !f32) {
+            // x0 = G F (warm), tensor components -> Mandel, projected; FP64 residual
+            double *st = (double *)ctx->r64;
+            rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * k, sizeof(double) * n, st);
+            if (rc) return rc;
+            mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
+            real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
+            ctx->launches += 2;
+            rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+            if (rc) return rc;
+        } else if (warm) {
+            // FP32 fields: projection and starting residual with the FP32
+            // operator; a start already within kWarmFp64Below gets the FP64 one
+            float *wr = (float *)ctx->xs;
+            cpx<float> *x32 = (cpx<float> *)ctx->vbuf[0], *p32 = (cpx<float> *)ctx->vbuf[1];
+            rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * k, sizeof(float) * n, wr);
+            if (rc) return rc;
+            Launch<float>::axpby(3 * ctx->V, s, std::sqrt(2.0), wr + 3 * ctx->V, 0.0, wr + 3 * ctx->V);
+            real_to_spec<float>(ctx, ctx->e32, wr, X3_MID_NONE, true, x32);
+            spec_f2d_acc(nc, s, x32, x);
+            op_spec<float>(ctx, ctx->e32, x32, p32, false, nullptr, nullptr);
+            spec_residual_mixed(ctx->e64.g, s, b, p32, r, ctx->partials);
+            reduce_to(s, ctx->partials, ew_blocks(6 * ctx->S), ctx->d_scalar);
+            ctx->launches += 5;
+            CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            tres[j] = std::sqrt(*ctx->h_scalar) / bnorm[j];
+            if (tres[j] < kWarmFp64Below) {
+                rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+                if (rc) return rc;
+            }
+        } else {   // x = 0: r = b
+            CU(cudaMemcpyAsync(r, b, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    const int sweeps_max = f32 ? 1 + ctx->refine : 1;
+    std::vector<double> stol(nb), est(nb);
+    std::vector<int> mi(nb), its(nb), sts(nb);
+    for (int sw = 0; sw < sweeps_max; ++sw) {
+        bool any = false;
+        double floor = (sw == 0 && !warm && ctx->sweep_floor == kFp32SweepFloor) ? kFp32FirstSweepFloor
+                                                                                 : ctx->sweep_floor;
+        if (mask && ctx->sweep_floor == kFp32SweepFloor) floor = sw == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
+        for (int j = 0; j < nb; ++j) {
+            mi[j] = 0;
+            stol[j] = 0.5;
+            if (!live[j] || !(tres[j] > tol)) continue;
+            double sweep_tol = (f32 ? kSweepTarget : 1.0) * tol / tres[j];
+            if (sweep_tol > 0.5) sweep_tol = 0.5;
+            if (f32 && sweep_tol < floor) sweep_tol = floor;
+            stol[j] = sweep_tol;
+            mi[j] = max_it;
+            any = true;
+            const double2 *r = ctx->br64 + j * nc;
+            if (f32) spec_d2f(nc, s, r, (float2 *)ctx->brhs + j * nc);
+            else CU(cudaMemcpyAsync((double2 *)ctx->brhs + j * nc, r, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+            ctx->launches += f32 ? 1 : 0;
+        }
+        if (!any) break;
+        rc = f32 ? run_minres_batch<float>(ctx, ctx->e32, nb, stol.data(), mi.data(), its.data(), est.data(), sts.data())
+                 : run_minres_batch<double>(ctx, ctx->e64, nb, stol.data(), mi.data(), its.data(), est.data(), sts.data());
+        if (rc) return rc;
+        for (int j = 0; j < nb; ++j) {
+            if (mi[j] == 0) continue;
+            const int k = c0 + j;
+            double2 *x = ctx->x64[k], *b = ctx->bb64 + j * nc, *r = ctx->br64 + j * nc;
+            if (f32) spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x);
+            else Launch<double>::axpby(2 * nc, s, 1.0, (const double *)((double2 *)ctx->brhs + j * nc), 1.0, (double *)x);
+            ctx->launches += 1;
+            inf[j].iterations += its[j];
+            inf[j].est_residual = est[j] * tres[j];   // relative to ||b||
+            inf[j].sweeps = sw + 1;
+            const double prev = tres[j];
+            rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+            if (rc) return rc;
+            if (sts[j] == HOM_ENAN) {
+                status[j] = HOM_ENAN;
+                live[j] = 0;
+                continue;
+            }
+            if (f32 && !(tres[j] < prev)) {
+                // an FP32 sweep past the accuracy FP32 fields can carry: take it back and stop
+                spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x, -1.0);
+                ctx->launches += 1;
+                rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+                if (rc) return rc;
+                status[j] = HOM_NOT_CONVERGED;
+                live[j] = 0;
+                continue;
+            }
+            if (sts[j] == HOM_NOT_CONVERGED && tres[j] > tol) {
+                status[j] = HOM_NOT_CONVERGED;
+                live[j] = 0;
+            }
+        }
+    }
+    int worst = HOM_OK;
+    for (int j = 0; j < nb; ++j) {
+        const int k = c0 + j;
+        if (solvable[j]) {
+            inf[j].true_residual = tres[j];
+            if (status[j] == HOM_OK && tres[j] > tol) status[j] = HOM_NOT_CONVERGED;
+        }
+        rc = finish_case(ctx, k, &M[6 * j], ctx->x64[k], &inf[j], status[j], info ? info + k : nullptr);
+        if (rc < 0) return rc;
+        if (rc > worst) worst = rc;
+    }
+    return worst;
+}
+
 // the projector's stress-controlled components at xi = 0; a change rebuilds
 // the captured solve graph, whose kernels take the geometry by value
 static void set_stress_mask(hom_ctx *ctx, int mask) {
@@ -1619,6 +2028,11 @@ static void set_stress_mask(hom_ctx *ctx, int mask) {
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
+    }
+    if (ctx->bgraph) {
+        cudaGraphExecDestroy(ctx->bgraph);
+        ctx->bgraph = nullptr;
+        ctx->bgraph_nb = 0;
     }
     if (ctx->cg_graph && ctx->solver == HOM_SOLVER_GALERKIN_CG) {
         cudaGraphExecDestroy(ctx->cg_graph);
@@ -1640,6 +2054,23 @@ static int solve_cases(hom_ctx *ctx, const double *macro_strain, const double *m
     ctx->eps_means.assign(6 * ncase, 0.0);
     ctx->sig_mean.assign(6 * ncase, 0.0);
     int worst = HOM_OK;
+    if (ctx->solver == HOM_SOLVER_GALERKIN_MINRES) {
+        // the load cases in stacked batches (as many per batch as fit)
+        for (int c0 = 0; c0 < ncase;) {
+            const int nb = batch_width(ctx, ncase - c0);
+            int rc = solve_chunk(ctx, c0, nb, macro_strain, macro_stress, tol, max_it, warm_start, info);
+            if (rc < 0) {
+                if (info)
+                    for (int k = c0; k < c0 + nb; ++k) info[k].status = rc;
+                return rc;
+            }
+            if (rc > worst) worst = rc;
+            c0 += nb;
+        }
+        ctx->ncase = ncase;
+        int rc = finish(ctx);
+        return rc ? rc : worst;
+    }
     for (int k = 0; k < ncase; ++k) {
         int rc = solve_case(ctx, k, macro_strain + 6 * k, macro_stress ? macro_stress + 6 * k : nullptr, tol, max_it,
                             warm_start, info ? info + k : nullptr);
@@ -1899,7 +2330,7 @@ static int j2_increment_impl(hom_ctx *ctx, const double *mac_t, const double *sb
                 spec_f2d_acc(nc, s, (const float2 *)ctx->xs, j.x64);
                 ctx->launches += 1;
                 double tnew = 0.0;
-                rc = true_residual(ctx, j.x64, nb, &tnew);
+                rc = true_residual(ctx, j.x64, ctx->b64, ctx->r64, nb, &tnew);
                 if (rc) return rc;
                 if (!(tnew < tres)) {
                     spec_f2d_acc(nc, s, (const float2 *)ctx->xs, j.x64, -1.0);

@@ -81,6 +81,8 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
 // alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2; the partials sum to
 // <u_k, A u_k> / scale (scale = V for the strain-energy sums of the n3 pass)
 __global__ void k_scalar_alpha(MinresState *st, const double *partials, int np, double scale) {
+    st += blockIdx.x;              // load case of a stacked batch (one CTA each)
+    partials += (size_t)blockIdx.x * np;
     if (st->done) return;
     const double a = reduce_partials(partials, np);
     if (threadIdx.x == 0) st->alpha = scale * a / (st->beta * st->beta);
@@ -92,6 +94,8 @@ __global__ void k_scalar_alpha(MinresState *st, const double *partials, int np, 
 // the loop); stop when phibar_k / beta_1 <= tol, beta_{k+1} = 0, or k reaches
 // max_it.
 __global__ void k_scalar_givens(MinresState *st, const double *partials, int np) {
+    st += blockIdx.x;              // load case of a stacked batch (one CTA each)
+    partials += (size_t)blockIdx.x * np;
     if (st->done) return;
     const double bn2 = reduce_partials(partials, np);
     if (threadIdx.x != 0) return;
@@ -136,10 +140,12 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
 
 // Condition of the device-side MINRES loop: one more body while not done
 // and below the cap (the cap ends the loop even if done were never set).
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, MinresState *st) {
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, MinresState *st, int nb) {
     if (threadIdx.x != 0) return;
-    st->bodies += 1;
-    cudaGraphSetConditional(h, (!st->done && st->bodies < st->max_bodies) ? 1u : 0u);
+    st->bodies += 1;   // counted on the first case's state
+    int active = 0;
+    for (int c = 0; c < nb; ++c) active |= !st[c].done;
+    cudaGraphSetConditional(h, (active && st->bodies < st->max_bodies) ? 1u : 0u);
 }
 
 // PCG (MoDBFFT, section 2.2): rho_0 = <r0, M r0>, ||r0||^2 from the two
@@ -360,7 +366,7 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
     const cuuint64_t h6 = (cuuint64_t)g.nc * g.h * u;   // components x h, in 8-byte units
     CUresult r;
     if (kind == TMA_X2) {
-        cuuint64_t dims[3] = {h6, (cuuint64_t)g.n2, (cuuint64_t)g.n1};
+        cuuint64_t dims[3] = {h6, (cuuint64_t)g.n2, (cuuint64_t)g.n1 * g.nb};
         cuuint64_t strides[2] = {h6 * 8, h6 * 8 * g.n2};
         cuuint32_t box[3] = {(cuuint32_t)(g.tile2 * units), (cuuint32_t)g.n2, 1};
         cuuint32_t es[3] = {1, 1, 1};
@@ -368,7 +374,7 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
-        cuuint64_t dims[2] = {h6 * g.n2, (cuuint64_t)g.n1};
+        cuuint64_t dims[2] = {h6 * g.n2, (cuuint64_t)g.n1 * g.nb};
         cuuint64_t strides[1] = {h6 * g.n2 * 8};
         cuuint32_t box[2] = {(cuuint32_t)(g.nc * g.tile1 * units), (cuuint32_t)g.n1};
         cuuint32_t es[2] = {1, 1};
@@ -442,14 +448,14 @@ void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int n
                   int max_bodies) {
     k_scalar_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it, max_bodies);
 }
-void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s) {
-    k_loop_cond<<<1, 32, 0, st>>>(h, s);
+void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s, int nb) {
+    k_loop_cond<<<1, 32, 0, st>>>(h, s, nb);
 }
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale) {
-    k_scalar_alpha<<<1, 1024, 0, st>>>(s, partials, np, scale);
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale, int nb) {
+    k_scalar_alpha<<<nb, 1024, 0, st>>>(s, partials, np, scale);
 }
-void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np) {
-    k_scalar_givens<<<1, 1024, 0, st>>>(s, partials, np);
+void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np, int nb) {
+    k_scalar_givens<<<nb, 1024, 0, st>>>(s, partials, np);
 }
 void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it) {
     k_scalar_cg_start<<<1, 1024, 0, st>>>(s, partials, np, tol, max_it);

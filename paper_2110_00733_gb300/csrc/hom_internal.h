@@ -76,6 +76,10 @@ struct Geometry {
     size_t smem3, smem2, smem1;
     int fast[3];
     int nc;                 // complex components per frequency in the spectrum (6, or 10 for MoDBFFT)
+    // load cases stacked along k1 in one launch of the MINRES kernels (work
+    // spectrum nb x n1 x n2 x h x nc, Krylov vectors nb blocks of kvec, one
+    // MinresState per case); 1 everywhere else
+    int nb = 1;
     int mask0;              // stress-controlled Mandel components (bit c): the projector keeps them at xi = 0
     // persistent TMA-staged n2 / n1 passes (FP32, power-of-two n <= 256):
     // enabled flag, persistent grid sizes, shared memory, host-side cache of
@@ -123,6 +127,7 @@ enum X3Out { X3_OUT_SPEC = 0, X3_OUT_REAL = 1 };
 enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
 
 constexpr int kEwBlocks = 152 * 8;   // grid of the element-wise Krylov kernels
+constexpr int kNbMax = 8;            // load cases of one stacked MINRES batch
 constexpr int kEwThreads = 256;
 
 struct Mac6 { double v[6]; };
@@ -223,11 +228,14 @@ void hom_set_error(const char *msg);
 void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int np, double tol, int max_it,
                   int max_bodies = 0);
 // end of a captured MINRES body inside a WHILE graph node: count the body and
-// keep looping while the state is not done and the cap is not reached
-void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s);
-// alpha_k from partials summing to <u_k, A^ u_k> / scale
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale = 1.0);
-void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np);
+// keep looping while one of the nb states is not done and the cap (of the
+// first state) is not reached
+void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s, int nb = 1);
+// alpha_k from partials summing to <u_k, A^ u_k> / scale.  The scalar
+// kernels of a stacked batch run one CTA per case c, on s[c] and the
+// partials at c * np.
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale = 1.0, int nb = 1);
+void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np, int nb = 1);
 // PCG scalars (MoDBFFT): start from <r0,z0>, ||r0||^2; step length; direction
 void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it);
 void scalar_cg_alpha(cudaStream_t st, CgState *s, const double *partials, int np);

@@ -72,6 +72,8 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 __device__ __forceinline__ bool skip(const MinresState *s) { return s != nullptr && s->done; }
+// load case c of a stacked batch (state points to g.nb states, or is null)
+__device__ __forceinline__ bool skip_case(const MinresState *s, int c) { return s != nullptr && s[c].done; }
 
 // Parseval weight of the half-spectrum plane k3
 __device__ __forceinline__ int pweight(int k3, int n3) { return (k3 == 0 || 2 * k3 == n3) ? 1 : 2; }
@@ -247,7 +249,6 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
                                         double *__restrict__ epart) {
-    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
     // stride by ES across a warp and stay free of bank conflicts; the fast
@@ -259,9 +260,18 @@ __global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__r
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + ep(N);   // second buffer of the generic engine only
     const int nrows = g.n1 * g.n2;
-    const int row0 = blockIdx.x * ROWS;
+    // a CTA never straddles two load cases of a stacked batch
+    const int bpc = (nrows + ROWS - 1) / ROWS;
+    const int cs = blockIdx.x / bpc;
+    if (skip_case(state, cs)) return;
+    const int row0 = (blockIdx.x - cs * bpc) * ROWS;   // row within the case
     const int V = (int)g.V;
     const int nr = min(ROWS, nrows - row0);
+    // stacked cases: spectrum rows and (real input / output) fields of case cs
+    if (in_mode == X3_IN_SPEC) in_ = reinterpret_cast<const cpx<R> *>(in_) + (size_t)cs * nrows * H * NC;
+    else if (in_mode == X3_IN_REAL) in_ = reinterpret_cast<const R *>(in_) + (size_t)cs * 6 * g.V;
+    if (out_mode == X3_OUT_SPEC) out_ = reinterpret_cast<cpx<R> *>(out_) + (size_t)cs * nrows * H * NC;
+    else out_ = reinterpret_cast<R *>(out_) + (size_t)cs * 6 * g.V;
     // ---- input
     if (in_mode == X3_IN_SPEC) {
         // Z[k] = X_a[k] + i X_b[k] and Z[N-k] = conj X_a[k] + i conj X_b[k];
@@ -428,15 +438,19 @@ template <int N>
 __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
                                                 int material, float lam, float mu2, const float *__restrict__ phi,
                                                 const MinresState *state, double *__restrict__ epart) {
-    if (skip(state)) return;
     using PL = X3RPlan<N>;
     constexpr int P = PL::P, Q = PL::Q, ROWS = PL::ROWS, H = N / 2 + 1, NC = 6;
     constexpr int TS = Q * (P + 1);   // one line's transpose slab
     extern __shared__ __align__(16) float2 xslab[];
     const int r = threadIdx.x / P, j = threadIdx.x % P;
     const int nrows = g.n1 * g.n2;
-    const int row = blockIdx.x * ROWS + r;
-    const bool live = row < nrows;
+    // load case cs of a stacked batch; a CTA never straddles two cases
+    const int bpc = (nrows + ROWS - 1) / ROWS;
+    const int cs = blockIdx.x / bpc;
+    if (skip_case(state, cs)) return;
+    const int rowc = (blockIdx.x - cs * bpc) * ROWS + r;   // row within the case (phi row)
+    const bool live = rowc < nrows;
+    const int row = cs * nrows + rowc;                       // row of the stacked spectrum
     float2 *tb = xslab + r * 3 * TS;
     const float2 *tw = reinterpret_cast<const float2 *>(g.ax[2].tw);   // exp(-2 pi i t / N)
     const int lane0 = (threadIdx.x & 31) & ~(P - 1);
@@ -486,7 +500,7 @@ __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const 
     const float sV = 1.0f / (float)g.V;
     float en = 0.f;
     if (material) {
-        const float *ph_row = phi + (size_t)(live ? row : 0) * N;
+        const float *ph_row = phi + (size_t)(live ? rowc : 0) * N;
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
             const float ph = live ? __ldg(&ph_row[j + P * m]) : 0.f;
@@ -559,15 +573,14 @@ __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const 
 // ---------------------------------------------------------------------------
 template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
-    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = g.n2, T = g.tile2, H6 = g.nc * g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * T;
-    const int total = g.n1 * H6;
+    const int total = g.n1 * g.nb * H6;   // stacked cases along k1
     const int t = threadIdx.x % T, e0 = threadIdx.x / T, es = blockDim.x / T;
     const int f = blockIdx.x * T + t;
-    const bool live = f < total;
+    const bool live = f < total && !skip_case(state, f / (g.n1 * H6));
     const int k1 = live ? f / H6 : 0;
     cpx<R> *col = spec + (size_t)k1 * N * H6 + (f - k1 * H6);   // element e at col[e * H6]
     for (int e = e0; e < N; e += es) buf[e * T + t] = live ? col[(size_t)e * H6] : mk<R>(0, 0);
@@ -654,11 +667,16 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
 template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ CUtensorMap tm, int qtiles,
                                             const MinresState *state) {
-    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     const int N = g.n2, T = g.tile2;
-    const int ntiles = g.n1 * qtiles;
+    const int ntiles = g.n1 * g.nb * qtiles;   // stacked cases along k1
+    const int tpc = g.n1 * qtiles;             // tiles per case
+    // next tile of this CTA's sequence whose case is still iterating
+    auto live_from = [&](int t) {
+        while (t < ntiles && skip_case(state, t / tpc)) t += gridDim.x;
+        return t;
+    };
     cpx<R> *const base = reinterpret_cast<cpx<R> *>(smem_raw);
     const int per = N * T;   // stage s starts at base + s * per
     const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
@@ -669,15 +687,15 @@ __global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ 
         fence_mbar_init();
     }
     __syncthreads();
-    int tile = blockIdx.x;
+    int tile = live_from(blockIdx.x);
     if (leader && tile < ntiles) {
         mbar_expect_tx(&bar[0], bytes);
         tma_load_3d(base, &tm, (tile % qtiles) * T, 0, tile / qtiles, &bar[0]);
     }
     const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[1].tw);
-    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    for (int i = 0; tile < ntiles; ++i) {
         const int s = i & 1;
-        const int next = tile + gridDim.x;
+        const int next = live_from(tile + gridDim.x);
         if (leader && next < ntiles) {
             bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
             mbar_expect_tx(&bar[s ^ 1], bytes);
@@ -701,6 +719,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ 
             tma_store_3d(&tm, (tile % qtiles) * T, 0, tile / qtiles, buf);
             bulk_commit();
         }
+        tile = next;
     }
     if (leader) bulk_wait_all();
 }
@@ -928,77 +947,88 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
                                                 cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
                                                 cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x,
                                                 const MinresState *state, double *__restrict__ partials) {
-    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
     cpx<R> *buf2 = buf + N * L;
     const int cols = g.n2 * H;
-    const int g0 = blockIdx.x * T;
+    // load case cs of a stacked batch, tile tc of that case
+    const int tpc = (cols + T - 1) / T;
+    const int cs = blockIdx.x / tpc, tc = blockIdx.x - cs * tpc;
+    if (skip_case(state, cs)) return;
+    const size_t ko = (size_t)cs * g.kvec;      // the case's Krylov block
+    spec += (size_t)cs * NC * g.S;               // the case's work spectrum
+    const int g0 = tc * T;
     const size_t sK1 = (size_t)cols * NC;
     const int lt = threadIdx.x % L, e0 = threadIdx.x / L, es = blockDim.x / L;
     const bool live = g0 + lt / NC < cols;
-    const LzCoef<R> c = lz_coef<R>(state);
+    const LzCoef<R> c = lz_coef<R>(state + cs);
     {
         const cpx<R> *src = spec + (size_t)g0 * NC + lt;
         for (int e = e0; e < N; e += es) buf[e * L + lt] = live ? src[e * sK1] : mk<R>(0, 0);
     }
     __syncthreads();
     Acc<R> acc;
-    cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf2, g0, c, uk, um, wa, wb, x, acc);
+    cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf2, g0, c, uk + ko, um + ko, wa + ko, wb + ko, x + ko, acc);
     if (live) {
         cpx<R> *dst = spec + (size_t)g0 * NC + lt;
         for (int e = e0; e < N; e += es) dst[e * sK1] = res[e * L + lt];
     }
     const double sum = block_sum(acc.value());
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;   // = partials[cs * tpc + tc]
 }
-
 
 // persistent TMA-staged form (FP32, register FFT lengths 64..256, at most
 // 192 threads per CTA): the work tile comes and goes by TMA, double-buffered
 // as in k_x1_tma; the contiguous Krylov blocks of a tile are read and
 // written with plain coalesced accesses.  (Prefetching the next tile's
 // blocks into L2 was measured to double the DRAM reads: the lines were
-// evicted before use.)
+// evicted before use.)  Tiles are numbered case-major over the stacked
+// batch; tiles of converged cases are skipped; each thread keeps one running
+// sum per case in shared memory, and the CTA writes one partial per case
+// (partials[case * gridDim + block]).
 template <typename R, int NF>
 __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec,
                                                     const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
                                                     const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
                                                     cpx<R> *__restrict__ x, const MinresState *state,
                                                     double *__restrict__ partials) {
-    if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double sacc[kNbMax * 192];
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     const int cols = g.n2 * H;
-    const int ntiles = (cols + T - 1) / T;
+    const int tpc = (cols + T - 1) / T;   // tiles per case
+    const int ntiles = tpc * g.nb;
     const int per = N * L;
     const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
     cpx<R> *base = reinterpret_cast<cpx<R> *>(smem_raw);
     const bool leader = threadIdx.x == 0;
-    const LzCoef<R> c = lz_coef<R>(state);
+    auto live_from = [&](int t) {
+        while (t < ntiles && skip_case(state, t / tpc)) t += gridDim.x;
+        return t;
+    };
+    for (int cc = 0; cc < g.nb; ++cc) sacc[cc * blockDim.x + threadIdx.x] = 0.0;
     if (leader) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    int tile = blockIdx.x;
+    int tile = live_from(blockIdx.x);
     if (leader && tile < ntiles) {
         mbar_expect_tx(&bar[0], bytes);
-        tma_load_2d(base, &tspec, NC * T * tile, 0, &bar[0]);
+        tma_load_2d(base, &tspec, NC * T * (tile % tpc), N * (tile / tpc), &bar[0]);
     }
-    Acc<R> acc;
-    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    for (int i = 0; tile < ntiles; ++i) {
         const int s = i & 1;
-        const int next = tile + gridDim.x;
+        const int next = live_from(tile + gridDim.x);
         if (leader && next < ntiles) {
             bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
             mbar_expect_tx(&bar[s ^ 1], bytes);
-            tma_load_2d(base + (s ^ 1) * per, &tspec, NC * T * next, 0, &bar[s ^ 1]);
+            tma_load_2d(base + (s ^ 1) * per, &tspec, NC * T * (next % tpc), N * (next / tpc), &bar[s ^ 1]);
         }
         const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -1010,18 +1040,26 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
             }
             return;
         }
+        const int cs = tile / tpc, tc = tile - cs * tpc;
+        const size_t ko = (size_t)cs * g.kvec;
+        const LzCoef<R> c = lz_coef<R>(state + cs);
+        Acc<R> acc;
         cpx<R> *buf = base + s * per;
-        cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf, tile * T, c, uk, um, wa, wb, x, acc);
+        cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf, tc * T, c, uk + ko, um + ko, wa + ko, wb + ko, x + ko, acc);
+        sacc[cs * blockDim.x + threadIdx.x] += acc.value();
         fence_proxy_async_smem();
         __syncthreads();
         if (leader) {
-            tma_store_2d(&tspec, NC * T * tile, 0, res);
+            tma_store_2d(&tspec, NC * T * tc, N * cs, res);
             bulk_commit();
         }
+        tile = next;
     }
     if (leader) bulk_wait_all();
-    const double sum = block_sum(acc.value());
-    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+    for (int cc = 0; cc < g.nb; ++cc) {
+        const double sum = block_sum(sacc[cc * blockDim.x + threadIdx.x]);
+        if (threadIdx.x == 0) partials[cc * gridDim.x + blockIdx.x] = sum;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1081,18 +1119,19 @@ __global__ void k_tiles(long long n, int n1, int cols, int T, int to_tiles, cons
 // The lagged w / x update of the last step K; skipped when there is none
 // or the state kept the last finite iterate.
 template <typename R>
-__global__ void __launch_bounds__(kEwThreads) k_minres_flush(int n, const cpx<R> *__restrict__ ua,
+__global__ void __launch_bounds__(kEwThreads) k_minres_flush(long long n, long long per_case, const cpx<R> *__restrict__ ua,
                                                              const cpx<R> *__restrict__ ub, cpx<R> *__restrict__ wc,
                                                              cpx<R> *__restrict__ wd, cpx<R> *__restrict__ x,
-                                                             const MinresState *st) {
-    const int K = st->k;
-    if (st->done_update || K <= 0) return;
-    const cpx<R> *u = (K & 1) ? ub : ua;
-    const cpx<R> *wa = (K & 1) ? wc : wd;      // w_{K-1}
-    cpx<R> *wb = (K & 1) ? wd : wc;            // w_{K-2}, overwritten by w_K
-    const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
-            ib = (R)st->u_inv_beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+                                                             const MinresState *sts) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const MinresState *st = sts + i / per_case;   // the element's load case
+        const int K = st->k;
+        if (st->done_update || K <= 0) continue;
+        const cpx<R> *u = (K & 1) ? ub : ua;
+        const cpx<R> *wa = (K & 1) ? wc : wd;      // w_{K-1}
+        cpx<R> *wb = (K & 1) ? wd : wc;            // w_{K-2}, overwritten by w_K
+        const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
+                ib = (R)st->u_inv_beta;
         const cpx<R> uu = u[i], a = wa[i], b = wb[i], xx = x[i];
         const cpx<R> wn = mk<R>((uu.x * ib - d * a.x - e * b.x) * ig, (uu.y * ib - d * a.y - e * b.y) * ig);
         wb[i] = wn;
@@ -1194,9 +1233,11 @@ int Launch<R>::ew_grid(long long n) {
     long long b = (n + kEwThreads - 1) / kEwThreads;
     return (int)(b < kEwBlocks ? (b > 0 ? b : 1) : kEwBlocks);
 }
+// CTAs of the n3 pass per load case (the grid is nb times this)
 template <typename R>
 int Launch<R>::x3_grid(const Geometry &g) { return (g.n1 * g.n2 + g.rows3 - 1) / g.rows3; }
-// partials written by the n3 pass of the fused chain (spectrum in and out)
+// partials per load case written by the n3 pass of the fused chain
+// (spectrum in and out): case c's are at [c * count, (c + 1) * count)
 template <typename R>
 int Launch<R>::x3_epart_grid(const Geometry &g) {
     if (sizeof(R) == 4 && g.x3r) return (g.n1 * g.n2 + x3r_rows(g.n3) - 1) / x3r_rows(g.n3);
@@ -1316,7 +1357,7 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
     if constexpr (sizeof(R) == 4) {
         if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
-            const int grid = x3_epart_grid(g);
+            const int grid = x3_epart_grid(g) * g.nb;
             const size_t sm = x3r_smem(g.n3);
             const int mat = mid == X3_MID_MATERIAL;
             const float2 *fi = reinterpret_cast<const float2 *>(in);
@@ -1335,7 +1376,7 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
     Mac6 m{};
     if (macro)
         for (int c = 0; c < 6; ++c) m.v[c] = macro[c];
-    const int grid = x3_grid(g);
+    const int grid = x3_grid(g) * g.nb;
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
         k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
@@ -1365,7 +1406,7 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
             return;
         }
     }
-    const int grid = (g.n1 * g.nc * g.h + g.tile2 - 1) / g.tile2;
+    const int grid = (g.n1 * g.nb * g.nc * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2(NF)                                                                  \
     if (inverse) k_x2<R, 1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state); \
     else k_x2<R, -1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state)
@@ -1400,6 +1441,7 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 #undef HOM_X1
 }
 
+// partials per load case written by the fused n1 pass (case c's at c * count)
 template <typename R>
 int Launch<R>::x1_lanczos_grid(const Geometry &g) {
     return (g.tma && g.grid1l_tma > 0) ? g.grid1l_tma : (g.n2 * g.h + g.tile1 - 1) / g.tile1;
@@ -1422,7 +1464,7 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
             return;
         }
     }
-    const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1;
+    const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1 * g.nb;
 #define HOM_X1L(NF) k_x1_lanczos<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, spec, uk, um, wa, wb, x, state, partials)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1L)
 #undef HOM_X1L
@@ -1449,9 +1491,9 @@ void Launch<R>::lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> 
 
 template <typename R>
 void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
-                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long nl) {
-    const int n = (int)nl;
-    k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, ua, ub, wc, wd, x, state);
+                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long per_case) {
+    const long long n = per_case * g.nb;
+    k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, per_case, ua, ub, wc, wd, x, state);
 }
 
 template <typename R>

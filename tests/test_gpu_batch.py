@@ -1,7 +1,9 @@
-"""Batched solves over cells of different sizes, and the launch-shape autotuner."""
+"""Batched solves over cells of different sizes and stacked load cases,
+checked against the FP64 oracle, and the launch-shape autotuner."""
 import numpy as np
 import pytest
 
+import oracle
 import rve_inputs as ri
 from gpu_util import FP32_TOL
 
@@ -20,22 +22,44 @@ def hom():
     return h
 
 
-def test_batch_equals_one_by_one(hom):
-    cells = [(16, 0.25), (24, 0.12), (32, 0.05)]      # power-of-two and mixed-radix grids
-    macros = np.array([np.eye(6)[0], np.eye(6)[4]]) * 1e-3
-    ctxs = []
+def test_batch_matches_oracle(hom):
+    """Cells of different sizes (power-of-two and mixed-radix grids, different
+    densities) solved at once by hom_solve_batch, each with its six unit macro
+    strains stacked in one launch: the effective stiffness of every cell
+    against the FP64 oracle's (section 4.3), within 1e-4 of its largest
+    entry."""
+    cells = [(16, 0.25), (24, 0.12), (32, 0.05)]
+    ctxs, refs = [], []
     for n, rho in cells:
         phi, _ = ri.octet(n, rho)
         ctxs.append(hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M))
-    rc, infos = hom.hom_solve_batch(ctxs, macros, tol=1e-7, max_it=5000)
-    assert rc == hom.HOM_OK
-    batch = [[i["sigma_mean"] for i in cell] for cell in infos]
-    for c, ctx in enumerate(ctxs):
-        rc1, one = hom.hom_solve(ctx, macros, tol=1e-7, max_it=5000)
-        assert rc1 == hom.HOM_OK
-        for k in range(len(macros)):
-            assert np.array_equal(batch[c][k], one[k]["sigma_mean"])
-        ctx.close()
+        Cref, _ = oracle.effective_stiffness(phi.astype(np.float64), E_M, NU_M, 1, tol=1e-10, max_it=20000)
+        refs.append(Cref)
+    try:
+        rc, infos = hom.hom_solve_batch(ctxs, np.eye(6), tol=1e-8, max_it=20000)
+        assert rc == hom.HOM_OK, [[i["status"] for i in cell] for cell in infos]
+        for ctx, Cref, cell in zip(ctxs, refs, infos):
+            C = hom.hom_effective_stiffness(ctx)
+            assert np.max(np.abs(C - Cref)) <= 1e-4 * np.max(np.abs(Cref))
+            assert all(i["true_residual"] <= 1e-8 for i in cell)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_stacked_cases_match_one_at_a_time(hom):
+    """The six load cases stacked in one launch give what each case gives on
+    its own (same kernels, so agreement to FP32 round-off of the solve)."""
+    phi, _ = ri.octet(24, 0.15)
+    macros = np.eye(6) * 1e-3
+    with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M) as ctx:
+        rc, together = hom.hom_solve(ctx, macros, tol=1e-8, max_it=5000)
+        assert rc == hom.HOM_OK
+        for k in range(6):
+            rc, alone = hom.hom_solve(ctx, macros[k], tol=1e-8, max_it=5000)
+            assert rc == hom.HOM_OK
+            ref = np.asarray(alone[0]["sigma_mean"])
+            assert np.max(np.abs(np.asarray(together[k]["sigma_mean"]) - ref)) <= 1e-6 * np.max(np.abs(ref))
 
 
 def test_autotune_shapes_give_the_same_answer(hom):
