@@ -378,12 +378,19 @@ int hom_modb_rhs(hom_ctx *ctx, const double macro_strain[6], void *out_spectrum)
 /* out = [xi . Cbar . xi]^-1 in, eq. (precf) with Cbar = <phi> C_m (eq. avstiff). */
 int hom_modb_precond(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum);
 
-/* Solve the same ncase macro strains on ncell cells at once.  ctxs[i] are
- * independent contexts (own streams and workspaces, any grid sizes); one
- * host thread per cell runs hom_solve on it and the device overlaps the
- * cells' kernels.  info: NULL or ncell x ncase records (cell-major).
- * Returns the worst status over the cells (negative errors first).  Each
- * context then holds its own solutions as after hom_solve. */
+/* Solve the same ncase macro strains on ncell cells at once (the cell studies
+ * of section 4.3 scaled out).  ctxs[i] are independent contexts (own streams
+ * and workspaces, any grid sizes).  When every context is a Galerkin-MINRES
+ * context of one precision on the current device and ncase <= 8 cases fit in
+ * device memory as one stacked batch per cell, each refinement sweep of all
+ * cells is one graph launch: every cell's cases are stacked in its MINRES
+ * kernels, the cells' steps are parallel branches of the graph's body, and
+ * the body repeats on the device until every case has converged; the FP64
+ * right-hand sides and true residuals run between sweeps.  Otherwise the
+ * cells are solved one after another.  info: NULL or ncell x ncase records
+ * (cell-major; time_ms is the whole batch's).  Returns the worst status over
+ * the cells (negative errors first).  Each context then holds its own
+ * solutions as after hom_solve. */
 int hom_solve_batch(hom_ctx *const *ctxs, int ncell, const double *macro_strain, int ncase, double tol,
                     int max_it, hom_solve_info *info);
 

@@ -173,6 +173,7 @@ struct hom_ctx {
 };
 
 static void batch_free(hom_ctx *ctx);
+static void set_stress_mask(hom_ctx *ctx, int mask);
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -1279,6 +1280,7 @@ static void batch_free(hom_ctx *ctx) {
     ctx->d_bst = ctx->h_bst = nullptr;
     ctx->bpart = nullptr;
     ctx->bcap = 0;
+    ctx->bg.nb = 0;
 }
 
 // device bytes of one load case of a stacked batch
@@ -1367,16 +1369,25 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
 // the stacked batch's solve graph for nb cases: a device-side WHILE loop
 // over graph_iters steps, or (host_loop / no conditional nodes) the body
 // alone, replayed by the host
+// the stacked geometry for nb cases (own TMA cache: its tensor maps span nb
+// cases); a change of nb drops the cell's stacked graph
 template <typename R>
-static int build_bgraph(hom_ctx *ctx, Engine<R> &E, int nb) {
-    if (ctx->bgraph && ctx->bgraph_nb == nb) return HOM_OK;
+static void set_bgeom(hom_ctx *ctx, Engine<R> &E, int nb) {
+    if (ctx->bg.nb == nb && ctx->bg.n1 == E.g.n1 && ctx->bg.mask0 == E.g.mask0 && (ctx->btma || !E.g.tma)) return;
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
+    ctx->bgraph_nb = 0;
     tma_cache_free(ctx->btma);
     ctx->btma = E.g.tma ? tma_cache_new() : nullptr;
     ctx->bg = E.g;
     ctx->bg.nb = nb;
     ctx->bg.tma_cache = ctx->btma;
+}
+
+template <typename R>
+static int build_bgraph(hom_ctx *ctx, Engine<R> &E, int nb) {
+    set_bgeom<R>(ctx, E, nb);
+    if (ctx->bgraph && ctx->bgraph_nb == nb) return HOM_OK;
     const long long before = ctx->launches;
     cudaGraph_t graph = nullptr;
     bool loops = false;
@@ -1427,70 +1438,57 @@ static int build_bgraph(hom_ctx *ctx, Engine<R> &E, int nb) {
 
 // MINRES from a zero start on the nb stacked right-hand sides in ctx->brhs
 // (standard order, solve precision); case j runs with tolerance tol[j] and
-// at most maxit[j] iterations (0: the case sits this sweep out).  On return
-// ctx->brhs holds the iterates (standard order; zero for cases that did not
-// run) and its / est / st the per-case iterations, estimated residual and
-// status.
+// at most maxit[j] iterations (0: the case sits this sweep out).  In three
+// parts so that several cells can share one graph launch:
+//   batch_begin  per-case norms and FP64 states, Krylov vectors in tile
+//                order, the first inverse n1 transform; *any = some case runs
+//   (the stacked graph, see build_bgraph / hom_solve_batch)
+//   batch_end    the last lagged update, the iterates back in the standard
+//                order over ctx->brhs (zero for cases that did not run), and
+//                the per-case iterations, estimated residual and status.
 template <typename R>
-static int run_minres_batch(hom_ctx *ctx, Engine<R> &E, int nb, const double *tol, const int *maxit, int *its,
-                            double *est, int *st) {
+static int batch_begin(hom_ctx *ctx, Engine<R> &E, int nb, const double *tol, const int *maxit, int max_bodies,
+                       bool *any) {
     cudaStream_t s = ctx->stream;
     const long long n6 = 6 * ctx->S, kv = E.g.kvec;
-    int rc = build_bgraph<R>(ctx, E, nb);
-    if (rc) return rc;
-    int mx = 0;
-    for (int j = 0; j < nb; ++j) mx = std::max(mx, maxit[j]);
-    const int max_replays = (mx + ctx->graph_iters - 1) / ctx->graph_iters + 1;
     const int npe = Launch<R>::ew_grid(n6);
     cpx<R> *rhs = (cpx<R> *)ctx->brhs, *spec = (cpx<R> *)ctx->bspec;
     for (int j = 0; j < nb; ++j) {
         Launch<R>::norm2w(E.g, s, rhs + j * n6, ctx->bpart + (size_t)j * npe);
-        scalar_start(s, ctx->d_bst + j, ctx->bpart + (size_t)j * npe, npe, tol[j], maxit[j], max_replays);
+        scalar_start(s, ctx->d_bst + j, ctx->bpart + (size_t)j * npe, npe, tol[j], maxit[j], max_bodies);
     }
     ctx->launches += 2 * nb;
     CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    bool any = false;
-    for (int j = 0; j < nb; ++j) any = any || !ctx->h_bst[j].done;
+    *any = false;
+    for (int j = 0; j < nb; ++j) *any = *any || !ctx->h_bst[j].done;
     CU(cudaMemsetAsync(ctx->bx, 0, sizeof(cpx<R>) * kv * nb, s));
-    if (any) {
-        // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0, in tile order;
-        // the work spectrum enters each step holding F_1^-1 G u_k
-        CU(cudaMemsetAsync(ctx->bv[0], 0, sizeof(cpx<R>) * kv * nb, s));
-        CU(cudaMemsetAsync(ctx->bv[1], 0, sizeof(cpx<R>) * kv * nb, s));
-        CU(cudaMemsetAsync(ctx->bw[0], 0, sizeof(cpx<R>) * kv * nb, s));
-        CU(cudaMemsetAsync(ctx->bw[1], 0, sizeof(cpx<R>) * kv * nb, s));
-        for (int j = 0; j < nb; ++j) {
-            if (ctx->h_bst[j].done) continue;
-            Launch<R>::to_tiles(E.g, s, rhs + j * n6, (cpx<R> *)ctx->bv[1] + j * kv);
-            Launch<R>::x1(E.g, s, X1_GAMMA_IN, rhs + j * n6, spec + j * n6, nullptr, nullptr, nullptr);
-            ctx->launches += 2;
-        }
-        if (ctx->bgraph_loops) {
-            CU(cudaGraphLaunch(ctx->bgraph, s));
-            CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
-            CU(cudaStreamSynchronize(s));
-            ctx->launches += (long long)ctx->h_bst[0].bodies * ctx->bgraph_kernels;
-        } else {
-            const int per_check = 4;
-            int replays = 0;
-            while (true) {
-                for (int r = 0; r < per_check && replays < max_replays; ++r, ++replays) {
-                    CU(cudaGraphLaunch(ctx->bgraph, s));
-                    ctx->launches += ctx->bgraph_kernels;
-                }
-                CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
-                CU(cudaStreamSynchronize(s));
-                bool live = false;
-                for (int j = 0; j < nb; ++j) live = live || !ctx->h_bst[j].done;
-                if (!live || replays >= max_replays) break;
-            }
-        }
+    if (!*any) return HOM_OK;
+    // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0, in tile order; the
+    // work spectrum enters each step holding F_1^-1 G u_k
+    CU(cudaMemsetAsync(ctx->bv[0], 0, sizeof(cpx<R>) * kv * nb, s));
+    CU(cudaMemsetAsync(ctx->bv[1], 0, sizeof(cpx<R>) * kv * nb, s));
+    CU(cudaMemsetAsync(ctx->bw[0], 0, sizeof(cpx<R>) * kv * nb, s));
+    CU(cudaMemsetAsync(ctx->bw[1], 0, sizeof(cpx<R>) * kv * nb, s));
+    for (int j = 0; j < nb; ++j) {
+        if (ctx->h_bst[j].done) continue;
+        Launch<R>::to_tiles(E.g, s, rhs + j * n6, (cpx<R> *)ctx->bv[1] + j * kv);
+        Launch<R>::x1(E.g, s, X1_GAMMA_IN, rhs + j * n6, spec + j * n6, nullptr, nullptr, nullptr);
+        ctx->launches += 2;
+    }
+    return HOM_OK;
+}
+
+template <typename R>
+static int batch_end(hom_ctx *ctx, Engine<R> &E, int nb, const int *maxit, bool ran, int *its, double *est, int *st) {
+    cudaStream_t s = ctx->stream;
+    const long long n6 = 6 * ctx->S, kv = E.g.kvec;
+    cpx<R> *rhs = (cpx<R> *)ctx->brhs;
+    if (ran) {
         Launch<R>::minres_flush(ctx->bg, s, (const cpx<R> *)ctx->bv[0], (const cpx<R> *)ctx->bv[1],
                                 (cpx<R> *)ctx->bw[0], (cpx<R> *)ctx->bw[1], (cpx<R> *)ctx->bx, ctx->d_bst, kv);
         ctx->launches += 1;
     }
-    // iterates back in the standard half-spectrum order, over the right-hand sides
     for (int j = 0; j < nb; ++j) Launch<R>::from_tiles(E.g, s, (const cpx<R> *)ctx->bx + j * kv, rhs + j * n6);
     ctx->launches += nb;
     CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
@@ -1504,6 +1502,38 @@ static int run_minres_batch(hom_ctx *ctx, Engine<R> &E, int nb, const double *to
     }
     return HOM_OK;
 }
+
+// the stacked graph of one cell, launched until its states are done
+template <typename R>
+static int batch_launch(hom_ctx *ctx, Engine<R> &E, int nb, int max_bodies) {
+    cudaStream_t s = ctx->stream;
+    int rc = build_bgraph<R>(ctx, E, nb);
+    if (rc) return rc;
+    if (ctx->bgraph_loops) {
+        CU(cudaGraphLaunch(ctx->bgraph, s));
+        CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ctx->launches += (long long)ctx->h_bst[0].bodies * ctx->bgraph_kernels;
+        return HOM_OK;
+    }
+    const int per_check = 4;
+    int replays = 0;
+    while (true) {
+        for (int r = 0; r < per_check && replays < max_bodies; ++r, ++replays) {
+            CU(cudaGraphLaunch(ctx->bgraph, s));
+            ctx->launches += ctx->bgraph_kernels;
+        }
+        CU(cudaMemcpyAsync(ctx->h_bst, ctx->d_bst, sizeof(MinresState) * nb, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        bool live = false;
+        for (int j = 0; j < nb; ++j) live = live || !ctx->h_bst[j].done;
+        if (!live || replays >= max_bodies) break;
+    }
+    return HOM_OK;
+}
+
+// graph bodies for a sweep with iteration cap mx
+static int max_bodies_for(const hom_ctx *ctx, int mx) { return (mx + ctx->graph_iters - 1) / ctx->graph_iters + 1; }
 
 // ----- solve -------------------------------------------------------------------
 // ||A^ x - b^||_w / ||b^||_w in FP64 (Parseval: the real-space ratio of
@@ -1841,34 +1871,61 @@ static int solve_case(hom_ctx *ctx, int icase, const double *mac_t, const double
     return finish_case(ctx, icase, m, x, &inf, status, info);
 }
 
-// Galerkin-MINRES of the load cases [c0, c0 + nb) as one stacked batch:
-// per case the FP64 right-hand side (from the DFT of phi) and, for a warm
-// start, the projected start and its residual; then refinement sweeps in
-// which every case still above tol runs MINRES in the same stacked launches
-// on its FP64 residual (converted to the field precision), and the FP64 true
-// residual of each case decides whether it needs another sweep.  The sweep
-// rules are those of a single case (solve_case).  info[].time_ms is the
-// device time of the whole batch.
-static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain, const double *macro_stress,
-                       double tol, int max_it, const void *warm, hom_solve_info *info) {
+// Galerkin-MINRES of the load cases [c0, c0 + nb) of one cell as one stacked
+// batch: per case the FP64 right-hand side (from the DFT of phi) and, for a
+// warm start, the projected start and its residual; then refinement sweeps
+// in which every case still above tol runs MINRES in the same stacked
+// launches on its FP64 residual (converted to the field precision), and the
+// FP64 true residual of each case decides whether it needs another sweep.
+// The sweep rules are those of a single case (solve_case).  In phases, so
+// that hom_solve_batch can run the sweeps of several cells in one graph
+// launch.  info[].time_ms is the device time of the whole batch.
+struct Chunk {
+    hom_ctx *ctx = nullptr;
+    int c0 = 0, nb = 0;
+    const double *macro_strain = nullptr, *macro_stress = nullptr;
+    double tol = 0.0;
+    int max_it = 0;
+    const void *warm = nullptr;
+    hom_solve_info *info = nullptr;
+    int sw = 0;             // sweeps begun
+    bool ran = false;       // the current sweep has a case that runs
+    std::vector<double> M, bnorm, tres, stol, est;
+    std::vector<int> status, live, solvable, mi, its, sts;
+    std::vector<hom_solve_info> inf;
+};
+
+static int chunk_prepare(Chunk &ch) {
+    hom_ctx *ctx = ch.ctx;
+    const int nb = ch.nb;
     const long long nc = 6 * ctx->S;
     cudaStream_t s = ctx->stream;
     const int mask = ctx->e64.g.mask0;
     const bool f32 = ctx->prec == HOM_PREC_FP32_FIELDS;
     int rc = batch_reserve(ctx, nb);
     if (rc) return rc;
-    std::vector<double> M(6 * nb, 0.0), bnorm(nb, 0.0), tres(nb, 1.0);
-    std::vector<int> status(nb, HOM_OK), live(nb, 0), solvable(nb, 0);
-    std::vector<hom_solve_info> inf(nb);
+    ch.M.assign(6 * nb, 0.0);
+    ch.bnorm.assign(nb, 0.0);
+    ch.tres.assign(nb, 1.0);
+    ch.stol.assign(nb, 0.5);
+    ch.est.assign(nb, 0.0);
+    ch.status.assign(nb, HOM_OK);
+    ch.live.assign(nb, 0);
+    ch.solvable.assign(nb, 0);
+    ch.mi.assign(nb, 0);
+    ch.its.assign(nb, 0);
+    ch.sts.assign(nb, 0);
+    ch.inf.assign(nb, hom_solve_info{});
+    ch.sw = 0;
     CU(cudaEventRecord(ctx->ev0, s));
     for (int j = 0; j < nb; ++j) {
-        const int k = c0 + j;
-        double *m = &M[6 * j];
+        const int k = ch.c0 + j;
+        double *m = &ch.M[6 * j];
         double sbar_v[6] = {0, 0, 0, 0, 0, 0};
-        macro_to_mandel(macro_strain + 6 * k, m);
+        macro_to_mandel(ch.macro_strain + 6 * k, m);
         if (mask) {
             double sb[6];
-            macro_to_mandel(macro_stress + 6 * k, sb);
+            macro_to_mandel(ch.macro_stress + 6 * k, sb);
             for (int c = 0; c < 6; ++c) {
                 if ((mask >> c) & 1) {
                     m[c] = 0.0;                                   // an unknown, not a load
@@ -1888,7 +1945,7 @@ static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain,
         double b2 = 0.0;
         rc = spec_norm2<double>(ctx, ctx->e64, b, &b2);
         if (rc) return rc;
-        bnorm[j] = std::sqrt(b2);
+        ch.bnorm[j] = std::sqrt(b2);
         double ce2 = 0.0;
         for (int i = 0; i < 6; ++i) {
             const double sv = 2.0 * ctx->mu * m[i] + (i < 3 ? ctx->lam * (m[0] + m[1] + m[2]) : 0.0);
@@ -1898,33 +1955,33 @@ static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain,
         for (int c = 0; c < 6; ++c) s2 += sbar_v[c] * sbar_v[c];
         const double ntau = std::sqrt(ce2 * ctx->phi2_sum) + std::sqrt(s2 / (double)ctx->V);
         CU(cudaMemsetAsync(x, 0, sizeof(double2) * nc, s));
-        if (!std::isfinite(bnorm[j])) {
-            status[j] = HOM_ENAN;
+        if (!std::isfinite(ch.bnorm[j])) {
+            ch.status[j] = HOM_ENAN;
             continue;
         }
-        if (bnorm[j] / std::sqrt((double)ctx->V) <= kRhsZero * ntau) {
-            inf[j].sweeps = 0;   // b vanishes up to round-off: zero fluctuation, 0 iterations
+        if (ch.bnorm[j] / std::sqrt((double)ctx->V) <= kRhsZero * ntau) {
+            ch.inf[j].sweeps = 0;   // b vanishes up to round-off: zero fluctuation, 0 iterations
             continue;
         }
-        live[j] = 1;
-        solvable[j] = 1;
+        ch.live[j] = 1;
+        ch.solvable[j] = 1;
         const long long n = 6 * ctx->V;
-        if (warm && !f32) {
+        if (ch.warm && !f32) {
             // x0 = G F (warm), tensor components -> Mandel, projected; FP64 residual
             double *st = (double *)ctx->r64;
-            rc = stage_in(ctx, (const char *)warm + sizeof(double) * n * k, sizeof(double) * n, st);
+            rc = stage_in(ctx, (const char *)ch.warm + sizeof(double) * n * k, sizeof(double) * n, st);
             if (rc) return rc;
             mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
             real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
             ctx->launches += 2;
-            rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
             if (rc) return rc;
-        } else if (warm) {
+        } else if (ch.warm) {
             // FP32 fields: projection and starting residual with the FP32
             // operator; a start already within kWarmFp64Below gets the FP64 one
             float *wr = (float *)ctx->xs;
             cpx<float> *x32 = (cpx<float> *)ctx->vbuf[0], *p32 = (cpx<float> *)ctx->vbuf[1];
-            rc = stage_in(ctx, (const char *)warm + sizeof(float) * n * k, sizeof(float) * n, wr);
+            rc = stage_in(ctx, (const char *)ch.warm + sizeof(float) * n * k, sizeof(float) * n, wr);
             if (rc) return rc;
             Launch<float>::axpby(3 * ctx->V, s, std::sqrt(2.0), wr + 3 * ctx->V, 0.0, wr + 3 * ctx->V);
             real_to_spec<float>(ctx, ctx->e32, wr, X3_MID_NONE, true, x32);
@@ -1935,88 +1992,380 @@ static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain,
             ctx->launches += 5;
             CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
-            tres[j] = std::sqrt(*ctx->h_scalar) / bnorm[j];
-            if (tres[j] < kWarmFp64Below) {
-                rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+            ch.tres[j] = std::sqrt(*ctx->h_scalar) / ch.bnorm[j];
+            if (ch.tres[j] < kWarmFp64Below) {
+                rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
                 if (rc) return rc;
             }
         } else {   // x = 0: r = b
             CU(cudaMemcpyAsync(r, b, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
         }
     }
+    return HOM_OK;
+}
+
+// the next sweep's tolerances and right-hand sides and the start of its
+// stacked MINRES; *more = false when no case needs a sweep (or the sweeps
+// ran out)
+static int chunk_sweep_begin(Chunk &ch, bool *more) {
+    hom_ctx *ctx = ch.ctx;
+    const long long nc = 6 * ctx->S;
+    cudaStream_t s = ctx->stream;
+    const int mask = ctx->e64.g.mask0;
+    const bool f32 = ctx->prec == HOM_PREC_FP32_FIELDS;
     const int sweeps_max = f32 ? 1 + ctx->refine : 1;
-    std::vector<double> stol(nb), est(nb);
-    std::vector<int> mi(nb), its(nb), sts(nb);
-    for (int sw = 0; sw < sweeps_max; ++sw) {
-        bool any = false;
-        double floor = (sw == 0 && !warm && ctx->sweep_floor == kFp32SweepFloor) ? kFp32FirstSweepFloor
-                                                                                 : ctx->sweep_floor;
-        if (mask && ctx->sweep_floor == kFp32SweepFloor) floor = sw == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
-        for (int j = 0; j < nb; ++j) {
-            mi[j] = 0;
-            stol[j] = 0.5;
-            if (!live[j] || !(tres[j] > tol)) continue;
-            double sweep_tol = (f32 ? kSweepTarget : 1.0) * tol / tres[j];
-            if (sweep_tol > 0.5) sweep_tol = 0.5;
-            if (f32 && sweep_tol < floor) sweep_tol = floor;
-            stol[j] = sweep_tol;
-            mi[j] = max_it;
-            any = true;
-            const double2 *r = ctx->br64 + j * nc;
-            if (f32) spec_d2f(nc, s, r, (float2 *)ctx->brhs + j * nc);
-            else CU(cudaMemcpyAsync((double2 *)ctx->brhs + j * nc, r, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
-            ctx->launches += f32 ? 1 : 0;
-        }
-        if (!any) break;
-        rc = f32 ? run_minres_batch<float>(ctx, ctx->e32, nb, stol.data(), mi.data(), its.data(), est.data(), sts.data())
-                 : run_minres_batch<double>(ctx, ctx->e64, nb, stol.data(), mi.data(), its.data(), est.data(), sts.data());
+    *more = false;
+    ch.ran = false;
+    if (ch.sw >= sweeps_max) return HOM_OK;
+    const int sw = ch.sw;
+    double floor = (sw == 0 && !ch.warm && ctx->sweep_floor == kFp32SweepFloor) ? kFp32FirstSweepFloor : ctx->sweep_floor;
+    if (mask && ctx->sweep_floor == kFp32SweepFloor) floor = sw == 0 ? kFp32MixedSweepFloor : kFp32MixedLaterSweepFloor;
+    bool any = false;
+    for (int j = 0; j < ch.nb; ++j) {
+        ch.mi[j] = 0;
+        ch.stol[j] = 0.5;
+        if (!ch.live[j] || !(ch.tres[j] > ch.tol)) continue;
+        double sweep_tol = (f32 ? kSweepTarget : 1.0) * ch.tol / ch.tres[j];
+        if (sweep_tol > 0.5) sweep_tol = 0.5;
+        if (f32 && sweep_tol < floor) sweep_tol = floor;
+        ch.stol[j] = sweep_tol;
+        ch.mi[j] = ch.max_it;
+        any = true;
+        const double2 *r = ctx->br64 + j * nc;
+        if (f32) spec_d2f(nc, s, r, (float2 *)ctx->brhs + j * nc);
+        else CU(cudaMemcpyAsync((double2 *)ctx->brhs + j * nc, r, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
+        ctx->launches += f32 ? 1 : 0;
+    }
+    if (!any) return HOM_OK;
+    ch.sw += 1;
+    const int mb = max_bodies_for(ctx, ch.max_it);
+    int rc = f32 ? batch_begin<float>(ctx, ctx->e32, ch.nb, ch.stol.data(), ch.mi.data(), mb, &ch.ran)
+                 : batch_begin<double>(ctx, ctx->e64, ch.nb, ch.stol.data(), ch.mi.data(), mb, &ch.ran);
+    if (rc) return rc;
+    if (f32) set_bgeom<float>(ctx, ctx->e32, ch.nb);
+    else set_bgeom<double>(ctx, ctx->e64, ch.nb);
+    *more = true;
+    return HOM_OK;
+}
+
+// after the sweep's MINRES: the iterates into the FP64 solutions, the FP64
+// true residuals, and the per-case decisions (stop, take back, continue)
+static int chunk_sweep_end(Chunk &ch) {
+    hom_ctx *ctx = ch.ctx;
+    const long long nc = 6 * ctx->S;
+    cudaStream_t s = ctx->stream;
+    const bool f32 = ctx->prec == HOM_PREC_FP32_FIELDS;
+    int rc = f32 ? batch_end<float>(ctx, ctx->e32, ch.nb, ch.mi.data(), ch.ran, ch.its.data(), ch.est.data(), ch.sts.data())
+                 : batch_end<double>(ctx, ctx->e64, ch.nb, ch.mi.data(), ch.ran, ch.its.data(), ch.est.data(), ch.sts.data());
+    if (rc) return rc;
+    for (int j = 0; j < ch.nb; ++j) {
+        if (ch.mi[j] == 0) continue;
+        const int k = ch.c0 + j;
+        double2 *x = ctx->x64[k], *b = ctx->bb64 + j * nc, *r = ctx->br64 + j * nc;
+        if (f32) spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x);
+        else Launch<double>::axpby(2 * nc, s, 1.0, (const double *)((double2 *)ctx->brhs + j * nc), 1.0, (double *)x);
+        ctx->launches += 1;
+        ch.inf[j].iterations += ch.its[j];
+        ch.inf[j].est_residual = ch.est[j] * ch.tres[j];   // relative to ||b||
+        ch.inf[j].sweeps = ch.sw;
+        const double prev = ch.tres[j];
+        rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
         if (rc) return rc;
-        for (int j = 0; j < nb; ++j) {
-            if (mi[j] == 0) continue;
-            const int k = c0 + j;
-            double2 *x = ctx->x64[k], *b = ctx->bb64 + j * nc, *r = ctx->br64 + j * nc;
-            if (f32) spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x);
-            else Launch<double>::axpby(2 * nc, s, 1.0, (const double *)((double2 *)ctx->brhs + j * nc), 1.0, (double *)x);
+        if (ch.sts[j] == HOM_ENAN) {
+            ch.status[j] = HOM_ENAN;
+            ch.live[j] = 0;
+            continue;
+        }
+        if (f32 && !(ch.tres[j] < prev)) {
+            // an FP32 sweep past the accuracy FP32 fields can carry: take it back and stop
+            spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x, -1.0);
             ctx->launches += 1;
-            inf[j].iterations += its[j];
-            inf[j].est_residual = est[j] * tres[j];   // relative to ||b||
-            inf[j].sweeps = sw + 1;
-            const double prev = tres[j];
-            rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
+            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
             if (rc) return rc;
-            if (sts[j] == HOM_ENAN) {
-                status[j] = HOM_ENAN;
-                live[j] = 0;
-                continue;
+            ch.status[j] = HOM_NOT_CONVERGED;
+            ch.live[j] = 0;
+            continue;
+        }
+        if (ch.sts[j] == HOM_NOT_CONVERGED && ch.tres[j] > ch.tol) {
+            ch.status[j] = HOM_NOT_CONVERGED;
+            ch.live[j] = 0;
+        }
+    }
+    return HOM_OK;
+}
+
+static int chunk_finish(Chunk &ch, int *worst) {
+    hom_ctx *ctx = ch.ctx;
+    for (int j = 0; j < ch.nb; ++j) {
+        const int k = ch.c0 + j;
+        if (ch.solvable[j]) {
+            ch.inf[j].true_residual = ch.tres[j];
+            if (ch.status[j] == HOM_OK && ch.tres[j] > ch.tol) ch.status[j] = HOM_NOT_CONVERGED;
+        }
+        int rc = finish_case(ctx, k, &ch.M[6 * j], ctx->x64[k], &ch.inf[j], ch.status[j], ch.info ? ch.info + k : nullptr);
+        if (rc < 0) return rc;
+        if (rc > *worst) *worst = rc;
+    }
+    return HOM_OK;
+}
+
+static int solve_chunk(hom_ctx *ctx, int c0, int nb, const double *macro_strain, const double *macro_stress,
+                       double tol, int max_it, const void *warm, hom_solve_info *info) {
+    Chunk ch;
+    ch.ctx = ctx;
+    ch.c0 = c0;
+    ch.nb = nb;
+    ch.macro_strain = macro_strain;
+    ch.macro_stress = macro_stress;
+    ch.tol = tol;
+    ch.max_it = max_it;
+    ch.warm = warm;
+    ch.info = info;
+    int rc = chunk_prepare(ch);
+    if (rc) return rc;
+    while (true) {
+        bool more = false;
+        rc = chunk_sweep_begin(ch, &more);
+        if (rc) return rc;
+        if (!more) break;
+        if (ch.ran) {
+            const int mb = max_bodies_for(ctx, max_it);
+            rc = ctx->prec == HOM_PREC_FP32_FIELDS ? batch_launch<float>(ctx, ctx->e32, nb, mb)
+                                                   : batch_launch<double>(ctx, ctx->e64, nb, mb);
+            if (rc) return rc;
+        }
+        rc = chunk_sweep_end(ch);
+        if (rc) return rc;
+    }
+    int worst = HOM_OK;
+    rc = chunk_finish(ch, &worst);
+    return rc ? rc : worst;
+}
+
+// ----- many cells, one graph per sweep -------------------------------------------
+// Loop condition of the multi-cell graph: count the body (ctl[0]) and go on
+// while some case of some cell is not done and the cap ctl[1] is not reached.
+__global__ void k_loop_cond_cells(cudaGraphConditionalHandle h, MinresState *const *sts, const int *nbs, int ncell,
+                                  int *ctl) {
+    if (threadIdx.x != 0) return;
+    ctl[0] += 1;
+    int active = 0;
+    for (int i = 0; i < ncell; ++i)
+        for (int c = 0; c < nbs[i]; ++c) active |= !sts[i][c].done;
+    cudaGraphSetConditional(h, (active && ctl[0] < ctl[1]) ? 1u : 0u);
+}
+
+// One sweep's MINRES of several cells (each a stacked batch begun by
+// batch_begin) from one graph: the cells' steps are parallel branches of the
+// graph's body, forked from and joined to the root stream, and the body
+// repeats on the device until every case of every cell is done.  Where
+// conditional nodes are unavailable, or cells[0] asked for the host loop,
+// the host replays the body and polls the states.
+static int launch_cells(std::vector<hom_ctx *> &cells, std::vector<int> &nbs, int max_bodies) {
+    hom_ctx *c0 = cells[0];
+    const int ncell = (int)cells.size();
+    cudaStream_t root = nullptr;
+    std::vector<cudaEvent_t> ev(ncell + 1, nullptr);
+    MinresState **d_sts = nullptr;
+    int *d_nbs = nullptr, *d_ctl = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> before(ncell), per_body(ncell);
+    int rc = HOM_OK;
+    bool loops = false;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        cudaFree(d_sts);
+        cudaFree(d_nbs);
+        cudaFree(d_ctl);
+        if (root) cudaStreamDestroy(root);
+    };
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        for (hom_ctx *c : cells) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        hom_set_error((std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+        cleanup();
+        return e == cudaErrorMemoryAllocation ? HOM_ENOMEM : HOM_ECUDA;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking);
+    for (int i = 0; i <= ncell && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&d_sts, sizeof(MinresState *) * ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&d_nbs, sizeof(int) * ncell);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ctl, sizeof(int) * 2);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph set-up");
+    {
+        std::vector<MinresState *> h_sts(ncell);
+        for (int i = 0; i < ncell; ++i) h_sts[i] = cells[i]->d_bst;
+        const int ctl[2] = {0, max_bodies};
+        e = cudaMemcpy(d_sts, h_sts.data(), sizeof(MinresState *) * ncell, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_nbs, nbs.data(), sizeof(int) * ncell, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph set-up");
+    }
+    // the work each cell enqueued so far (batch_begin) precedes the graph
+    for (int i = 0; i < ncell && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ev[i + 1], cells[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(root, ev[i + 1], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph set-up");
+    auto capture_branches = [&](cudaGraphConditionalHandle *h) -> cudaError_t {
+        cudaError_t er = cudaEventRecord(ev[0], root);
+        for (int i = 0; i < ncell && er == cudaSuccess; ++i) {
+            hom_ctx *c = cells[i];
+            er = cudaStreamWaitEvent(c->stream, ev[0], 0);
+            if (er != cudaSuccess) break;
+            before[i] = c->launches;
+            if (c->prec == HOM_PREC_FP32_FIELDS) capture_bbody<float>(c, c->e32);
+            else capture_bbody<double>(c, c->e64);
+            per_body[i] = c->launches - before[i];
+            c->launches = before[i];
+            er = cudaEventRecord(ev[i + 1], c->stream);
+            if (er == cudaSuccess) er = cudaStreamWaitEvent(root, ev[i + 1], 0);
+        }
+        if (er == cudaSuccess && h) k_loop_cond_cells<<<1, 32, 0, root>>>(*h, d_sts, d_nbs, ncell, d_ctl);
+        return er;
+    };
+    if (!c0->host_loop && cudaGraphCreate(&graph, 0) == cudaSuccess) {
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        cudaGraphNode_t node;
+        if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(root, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t ce = capture_branches(&h);
+                    e = cudaStreamEndCapture(root, &body);
+                    if (ce != cudaSuccess) e = ce;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph capture");
+                loops = true;
             }
-            if (f32 && !(tres[j] < prev)) {
-                // an FP32 sweep past the accuracy FP32 fields can carry: take it back and stop
-                spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x, -1.0);
-                ctx->launches += 1;
-                rc = true_residual(ctx, x, b, r, bnorm[j], &tres[j]);
-                if (rc) return rc;
-                status[j] = HOM_NOT_CONVERGED;
-                live[j] = 0;
-                continue;
+        }
+        if (!loops) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
+    }
+    if (!loops) {
+        e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t ce = capture_branches(nullptr);
+            e = cudaStreamEndCapture(root, &graph);
+            if (ce != cudaSuccess) e = ce;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph capture");
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph instantiate");
+    int bodies = 0;
+    if (loops) {
+        e = cudaGraphLaunch(exec, root);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bodies, d_ctl, sizeof(int), cudaMemcpyDeviceToHost, root);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(root);
+    } else {
+        while (e == cudaSuccess) {
+            for (int r = 0; r < 4 && bodies < max_bodies && e == cudaSuccess; ++r, ++bodies) e = cudaGraphLaunch(exec, root);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(root);
+            bool live = false;
+            for (int i = 0; i < ncell && e == cudaSuccess; ++i) {
+                e = cudaMemcpy(cells[i]->h_bst, cells[i]->d_bst, sizeof(MinresState) * nbs[i], cudaMemcpyDeviceToHost);
+                for (int c = 0; c < nbs[i]; ++c) live = live || !cells[i]->h_bst[c].done;
             }
-            if (sts[j] == HOM_NOT_CONVERGED && tres[j] > tol) {
-                status[j] = HOM_NOT_CONVERGED;
-                live[j] = 0;
+            if (!live || bodies >= max_bodies) break;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "multi-cell graph launch");
+    for (int i = 0; i < ncell; ++i) cells[i]->launches += (long long)bodies * per_body[i] + (loops ? bodies : 0);
+    cleanup();
+    return rc;
+}
+
+// hom_solve_batch with every cell's load cases in one stacked batch and the
+// sweeps of all cells from one graph launch each (all cells Galerkin-MINRES
+// of one precision on the current device, every cell's cases fitting in one
+// stacked batch); returns 1 (not taken) when these conditions do not hold.
+int solve_cells_one_graph(hom_ctx *const *ctxs, int ncell, const double *macro_strain, int ncase, double tol,
+                          int max_it, hom_solve_info *info, int *worst_out) {
+    if (ncase > kNbMax) return 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < ncell; ++i) {
+        const hom_ctx *c = ctxs[i];
+        if (c->solver != HOM_SOLVER_GALERKIN_MINRES || c->prec != ctxs[0]->prec || c->device != dev) return 1;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return 1;
+    }
+    std::vector<Chunk> ch(ncell);
+    for (int i = 0; i < ncell; ++i) {
+        hom_ctx *ctx = ctxs[i];
+        if (batch_width(ctx, ncase) < ncase) return 1;
+        set_stress_mask(ctx, 0);
+        while ((int)ctx->x64.size() < ncase) {
+            double2 *p = nullptr;
+            CU(cudaMalloc(&p, sizeof(double2) * 6 * ctx->S));
+            ctx->x64.push_back(p);
+        }
+        ctx->ncase = 0;
+        ctx->macros.assign(6 * ncase, 0.0);
+        ctx->eps_means.assign(6 * ncase, 0.0);
+        ctx->sig_mean.assign(6 * ncase, 0.0);
+        ch[i].ctx = ctx;
+        ch[i].c0 = 0;
+        ch[i].nb = ncase;
+        ch[i].macro_strain = macro_strain;
+        ch[i].tol = tol;
+        ch[i].max_it = max_it;
+        ch[i].info = info ? info + (size_t)i * ncase : nullptr;
+        int rc = chunk_prepare(ch[i]);
+        if (rc) return rc;
+    }
+    while (true) {
+        std::vector<hom_ctx *> cells;
+        std::vector<int> nbs;
+        std::vector<int> in_sweep(ncell, 0);
+        for (int i = 0; i < ncell; ++i) {
+            bool more = false;
+            int rc = chunk_sweep_begin(ch[i], &more);
+            if (rc) return rc;
+            in_sweep[i] = more;
+            if (more && ch[i].ran) {
+                cells.push_back(ch[i].ctx);
+                nbs.push_back(ncase);
             }
+        }
+        bool any = false;
+        for (int v : in_sweep) any = any || v;
+        if (!any) break;
+        if (!cells.empty()) {
+            int rc = launch_cells(cells, nbs, max_bodies_for(ctxs[0], max_it));
+            if (rc) return rc;
+        }
+        for (int i = 0; i < ncell; ++i) {
+            if (!in_sweep[i]) continue;
+            int rc = chunk_sweep_end(ch[i]);
+            if (rc) return rc;
         }
     }
     int worst = HOM_OK;
-    for (int j = 0; j < nb; ++j) {
-        const int k = c0 + j;
-        if (solvable[j]) {
-            inf[j].true_residual = tres[j];
-            if (status[j] == HOM_OK && tres[j] > tol) status[j] = HOM_NOT_CONVERGED;
-        }
-        rc = finish_case(ctx, k, &M[6 * j], ctx->x64[k], &inf[j], status[j], info ? info + k : nullptr);
-        if (rc < 0) return rc;
-        if (rc > worst) worst = rc;
+    for (int i = 0; i < ncell; ++i) {
+        int w = HOM_OK;
+        int rc = chunk_finish(ch[i], &w);
+        if (rc) return rc;
+        ch[i].ctx->ncase = ncase;
+        rc = finish(ch[i].ctx);
+        if (rc) return rc;
+        worst = std::max(worst, w);
     }
-    return worst;
+    *worst_out = worst;
+    return 0;
 }
 
 // the projector's stress-controlled components at xi = 0; a change rebuilds

@@ -1,11 +1,12 @@
 // hom_batch.cu -- many cells at once (hom_solve_batch) and the launch-shape
 // autotuner (hom_autotune).
 //
-// Batch: every cell has its own context, so its own stream and workspace;
-// one host thread per cell drives that cell's graph-captured solves, and the
-// device runs the cells' kernels concurrently.  Small grids (64^3 or 96^3)
-// leave most of the GPU idle on their own; overlapping cells of different
-// sizes fills it.
+// Batch: every cell has its own context (stream and workspace) and its load
+// cases stacked in one batch; each refinement sweep of all cells is one
+// graph launch whose body holds every cell's MINRES step as a parallel
+// branch, repeated on the device until every case has converged.  Small
+// grids (64^3 or 96^3) leave most of the GPU idle on their own; the cells'
+// branches run concurrently and fill it.
 //
 // Autotuner: the three FFT passes are independent, so each pass's tile is
 // chosen separately.  For each candidate the kernels of one MINRES iteration
@@ -20,12 +21,16 @@
 #include <map>
 #include <mutex>
 #include <random>
-#include <thread>
 #include <tuple>
 #include <vector>
 
 #include "../../include/hom.h"
 #include "hom_internal.h"
+
+// defined in hom_api.cu: every cell's load cases stacked, the sweeps of all
+// cells from one graph launch each; returns 1 when it does not apply
+int solve_cells_one_graph(hom_ctx *const *ctxs, int ncell, const double *macro_strain, int ncase, double tol,
+                          int max_it, hom_solve_info *info, int *worst_out);
 
 namespace {
 
@@ -135,25 +140,20 @@ int hom_autotune(const int grid[3], int precision, int shape[3]) {
 int hom_solve_batch(hom_ctx *const *ctxs, int ncell, const double *macro_strain, int ncase, double tol, int max_it,
                     hom_solve_info *info) {
     if (!ctxs || ncell <= 0 || !macro_strain || ncase <= 0) return HOM_EINVAL;
+    if (!(tol > 0.0) || max_it < 0) return HOM_EINVAL;
     for (int i = 0; i < ncell; ++i)
         if (!ctxs[i]) return HOM_EINVAL;
-    std::vector<int> rcs(ncell, HOM_OK);
-    std::vector<std::thread> threads;
-    threads.reserve(ncell);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    for (int i = 0; i < ncell; ++i) {
-        threads.emplace_back([&, i] {
-            cudaSetDevice(dev);
-            rcs[i] = hom_solve(ctxs[i], macro_strain, ncase, tol, max_it, nullptr,
-                               info ? info + (size_t)i * ncase : nullptr);
-        });
-    }
-    for (auto &t : threads) t.join();
+    for (int i = 0; i < 6 * ncase; ++i)
+        if (!std::isfinite(macro_strain[i])) return HOM_ENAN;
     int worst = HOM_OK;
-    for (int rc : rcs) {
-        if (rc < 0) return rc;
-        if (rc > worst) worst = rc;
+    const int rc = solve_cells_one_graph(ctxs, ncell, macro_strain, ncase, tol, max_it, info, &worst);
+    if (rc <= 0) return rc < 0 ? rc : worst;
+    // otherwise (other solvers, mixed precisions, too many cases for one
+    // stacked batch): the cells one after another
+    for (int i = 0; i < ncell; ++i) {
+        const int r = hom_solve(ctxs[i], macro_strain, ncase, tol, max_it, nullptr, info ? info + (size_t)i * ncase : nullptr);
+        if (r < 0) return r;
+        if (r > worst) worst = r;
     }
     return worst;
 }

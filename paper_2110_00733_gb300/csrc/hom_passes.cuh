@@ -1269,12 +1269,19 @@ void Launch<R>::table_init(const Geometry &) {
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    lim -= 1024;   // static shared memory of the reductions
-    // and the L1/shared carve-out to the largest shared share, so that the
-    // number of resident CTAs is set by registers, not by a small carve-out
+    // (the opt-in limit covers static plus dynamic shared memory, so each
+    // kernel's own static share is taken off), and the L1/shared carve-out to
+    // the largest shared share, so that the number of resident CTAs is set by
+    // registers, not by a small carve-out
 #define HOM_SET_ATTR1(K)                                                                        \
-    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);                  \
-    cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    {                                                                                           \
+        cudaFuncAttributes fa_{};                                                               \
+        cudaFuncGetAttributes(&fa_, K);                                                         \
+        cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize,                    \
+                             lim - (int)fa_.sharedSizeBytes);                                   \
+        cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout,                 \
+                             cudaSharedmemCarveoutMaxShared);                                   \
+    }
 #define HOM_SET_ATTR(NF)                \
     HOM_SET_ATTR1((k_x3<R, NF, 3>))     \
     HOM_SET_ATTR1((k_x3<R, NF, 5>))     \
