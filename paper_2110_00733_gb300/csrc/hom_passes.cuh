@@ -997,6 +997,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sacc[kNbMax * 192];
+    __shared__ LzCoef<R> scoef[kNbMax];   // each case's coefficients, converted once
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     const int cols = g.n2 * H;
@@ -1011,6 +1012,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
         return t;
     };
     for (int cc = 0; cc < g.nb; ++cc) sacc[cc * blockDim.x + threadIdx.x] = 0.0;
+    if (threadIdx.x < g.nb) scoef[threadIdx.x] = lz_coef<R>(state + threadIdx.x);
     if (leader) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1042,7 +1044,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
         }
         const int cs = tile / tpc, tc = tile - cs * tpc;
         const size_t ko = (size_t)cs * g.kvec;
-        const LzCoef<R> c = lz_coef<R>(state + cs);
+        const LzCoef<R> c = scoef[cs];
         Acc<R> acc;
         cpx<R> *buf = base + s * per;
         cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf, tc * T, c, uk + ko, um + ko, wa + ko, wb + ko, x + ko, acc);

@@ -7,7 +7,7 @@ its algorithmic bytes (the per-kernel figures of the roofline table).  With
 --reps 1 it is a small driver for ncu captures of the pass kernels:
 
     ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
-        --clock-control none -k "regex:k_x|k_lanczos" -c 15 --csv --log-file traffic.csv \
+        --clock-control none -k "regex:k_x" -c 24 --csv --log-file traffic.csv \
         python -m paper_2110_00733_gb300.time_passes --shape 256,128,256 --reps 1
     python -m paper_2110_00733_gb300.time_passes --traffic traffic.csv --shape 256,128,256
 
@@ -78,13 +78,21 @@ def write_traffic(csv_path, shape):
         scale = {"byte": 1e-6, "Kbyte": 1e-3, "Mbyte": 1.0, "Gbyte": 1e3}.get(r[ui], 1.0)
         if r[mi].startswith("dram__bytes"):
             d[r[mi]] = float(r[vi].replace(",", "")) * scale
-    seq = [launches[k] for k in sorted(launches) if "<float" in launches[k]["name"]]
-    # hom_time_kernels launches each kernel twice (warm-up, then --reps 1)
-    firsts = seq[0::2]
+    seq = [launches[k] for k in sorted(launches) if "double" not in launches[k]["name"]]
+    # the first launch of each kernel of the step (hom_time_kernels launches
+    # each twice: warm-up, then --reps 1); FP64 launches of context creation
+    # and the first inverse n1 pass are skipped
+    patterns = {"x2_inv": ("k_x2_tma<float, 1,", "k_x2<float, 1,"), "x3_c2r_law_energy_r2c": ("k_x3r<", "k_x3<float"),
+                "x2_fwd": ("k_x2_tma<float, -1,", "k_x2_tma<float, (int)-1", "k_x2<float, -1,", "k_x2<float, (int)-1"),
+                "x1_fwd_lanczos_inv": ("k_x1_lanczos",)}
+    firsts = []
+    for name in ORDER:
+        d = next((d for d in seq if any(d["name"].startswith(p) or (" " + p) in d["name"] for p in patterns[name])), None)
+        firsts.append(d or {"name": "(not captured)"})
     V = int(np.prod(shape))
     out = {"source_hash": source_hash(), "grid": list(shape),
            "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                      "--clock-control none -k \"regex:k_x|k_lanczos\" -c 15 --csv --log-file traffic.csv "
+                      "--clock-control none -k \"regex:k_x\" -c 24 --csv --log-file traffic.csv "
                       f"python -m paper_2110_00733_gb300.time_passes --shape {','.join(map(str, shape))} --reps 1",
            "note": "bytes per voxel on this grid (work spectrum larger than L2); traffic scales with the voxel "
                    "count at fixed n3, so bench.py multiplies by n^3 for the 256^3 workload",
