@@ -213,7 +213,8 @@ __device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, int ES, const Ax
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident engine for power-of-two lengths known at compile time.
+// Register-resident engine for lengths known at compile time (powers of two,
+// and 96 and 160, the mixed lengths of the batched cell studies).
 // Every thread owns E elements of one line for the whole transform (BPT =
 // E/RAD butterflies per stage), so a stage is: load the thread's butterfly
 // inputs from the single shared buffer into registers, barrier, compute,
@@ -221,20 +222,26 @@ __device__ cpx<R> *fft_lines(cpx<R> *bufA, cpx<R> *bufB, int L, int ES, const Ax
 // arithmetic on compile-time powers of two.  The CTA must have exactly
 // L * N / E threads; thread t works on line t % L.
 // ---------------------------------------------------------------------------
+// Stages in order R0, R1, R2, R3 (NS of them); E is a multiple of every
+// stage's radix.  The mixed lengths 96 = 4 4 2 3 and 160 = 4 4 2 5 put the
+// odd radix last, so that the sub-transform length before every stage is a
+// power of two.
 template <int N> struct FastPlan;
-template <> struct FastPlan<8>   { static constexpr int E = 8,  NS = 1, R0 = 8,  R1 = 1,  R2 = 1; };
-template <> struct FastPlan<16>  { static constexpr int E = 16, NS = 1, R0 = 16, R1 = 1,  R2 = 1; };
-template <> struct FastPlan<32>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 4,  R2 = 1; };
-template <> struct FastPlan<64>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 8,  R2 = 1; };
-template <> struct FastPlan<128> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 8,  R2 = 1; };
-template <> struct FastPlan<256> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 16, R2 = 1; };
-template <> struct FastPlan<512> { static constexpr int E = 16, NS = 3, R0 = 16, R1 = 16, R2 = 2; };
+template <> struct FastPlan<8>   { static constexpr int E = 8,  NS = 1, R0 = 8,  R1 = 1,  R2 = 1, R3 = 1; };
+template <> struct FastPlan<16>  { static constexpr int E = 16, NS = 1, R0 = 16, R1 = 1,  R2 = 1, R3 = 1; };
+template <> struct FastPlan<32>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 4,  R2 = 1, R3 = 1; };
+template <> struct FastPlan<64>  { static constexpr int E = 8,  NS = 2, R0 = 8,  R1 = 8,  R2 = 1, R3 = 1; };
+template <> struct FastPlan<96>  { static constexpr int E = 12, NS = 4, R0 = 4,  R1 = 4,  R2 = 2, R3 = 3; };
+template <> struct FastPlan<128> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 8,  R2 = 1, R3 = 1; };
+template <> struct FastPlan<160> { static constexpr int E = 20, NS = 4, R0 = 4,  R1 = 4,  R2 = 2, R3 = 5; };
+template <> struct FastPlan<256> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 16, R2 = 1, R3 = 1; };
+template <> struct FastPlan<512> { static constexpr int E = 16, NS = 3, R0 = 16, R1 = 16, R2 = 2, R3 = 1; };
 
 __host__ __device__ constexpr bool is_fast_length(int n) {
-    return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512;
+    return n == 8 || n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256 || n == 512;
 }
 __host__ __device__ constexpr int fast_elems(int n) {
-    return (n == 8 || n == 32 || n == 64) ? 8 : 16;
+    return (n == 8 || n == 32 || n == 64) ? 8 : (n == 96 ? 12 : (n == 160 ? 20 : 16));
 }
 
 // Position of element e of a line in a tile with element stride ES; with
@@ -288,6 +295,7 @@ __device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R
     fast_stage<R, S, N, P::R0, 1, PAD>(buf, ES, l, j0, tw);
     if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD>(buf, ES, l, j0, tw);
     if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD>(buf, ES, l, j0, tw);
+    if constexpr (P::NS > 3) fast_stage<R, S, N, P::R3, P::R0 * P::R1 * P::R2, PAD>(buf, ES, l, j0, tw);
 }
 
 }  // namespace hom

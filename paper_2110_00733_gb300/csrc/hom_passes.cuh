@@ -238,6 +238,9 @@ template <> struct Six<double> {
 // (two 512-thread CTAs' worth per SM) so that more CTAs stay resident to hide
 // HBM latency; FP64 kernels keep their data in registers instead.
 #define HOM_PASS_BOUNDS(R) __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+// the same, except for the register FFT lengths with more than 16 elements
+// per thread (160: 20), which keep their elements in registers instead
+#define HOM_PASS_BOUNDS_NF(R, NF) __launch_bounds__(512, (sizeof(R) == 4 && fast_elems(NF) <= 16) ? 2 : 1)
 
 // ---------------------------------------------------------------------------
 // n3 pass.  A CTA owns rows (k1,k2) [row0, row0+rows3); lines are the three
@@ -245,7 +248,7 @@ template <> struct Six<double> {
 // Z = X_2p + i X_2p+1, line index p*rows3 + r.
 // ---------------------------------------------------------------------------
 template <typename R, int NF, int NP>
-__global__ void HOM_PASS_BOUNDS(R) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
                                         double *__restrict__ epart) {
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const 
 // columns per CTA (contiguous runs of tile2 complex values).
 // ---------------------------------------------------------------------------
 template <typename R, int S, int NF>
-__global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = g.n2, T = g.tile2, H6 = g.nc * g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
@@ -596,7 +599,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x2(Geometry g, cpx<R> *__restrict__ spec, c
 // the tile is one contiguous run of 6 tile1 complex values).
 // ---------------------------------------------------------------------------
 template <typename R, int NF>
-__global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1(Geometry g, int flags, const cpx<R> *__restrict__ in,
                                             cpx<R> *__restrict__ out, const cpx<R> *__restrict__ dotv,
                                             double *__restrict__ partials, const MinresState *state) {
     if (skip(state)) return;
@@ -665,7 +668,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x1(Geometry g, int flags, const cpx<R> *__r
 // returns, and the host reports HOM_ETIMEOUT.
 // ---------------------------------------------------------------------------
 template <typename R, int S, int NF>
-__global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ CUtensorMap tm, int qtiles,
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_constant__ CUtensorMap tm, int qtiles,
                                             const MinresState *state) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -725,7 +728,7 @@ __global__ void HOM_PASS_BOUNDS(R) k_x2_tma(Geometry g, const __grid_constant__ 
 }
 
 template <typename R, int NF>
-__global__ void HOM_PASS_BOUNDS(R) k_x1_tma(Geometry g, int flags, const __grid_constant__ CUtensorMap tin,
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const __grid_constant__ CUtensorMap tin,
                                             const __grid_constant__ CUtensorMap tout,
                                             const __grid_constant__ CUtensorMap tdot, double *__restrict__ partials,
                                             const MinresState *state) {
@@ -937,9 +940,9 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
 }
 
 // At most 384 threads per CTA (set_shapes enforces it): the fused pass keeps
-// the Lanczos operands in registers next to the FFT's, so FP32 CTAs may use
-// up to 85 registers and still fit two 384-thread (four 192-thread) CTAs per SM.
-#define HOM_X1L_BOUNDS(R) __launch_bounds__(384, sizeof(R) == 4 ? 2 : 1)
+// the Lanczos operands of a frequency (five Krylov vectors, 60 values) in
+// registers, so it is not held to a register cap that would spill them.
+#define HOM_X1L_BOUNDS(R) __launch_bounds__(384, 1)
 
 // plain-load form: one tile per CTA
 template <typename R, int NF>
@@ -1257,7 +1260,9 @@ int Launch<R>::x1_grid(const Geometry &g) {
         case 16: CALL(16); break;                  \
         case 32: CALL(32); break;                  \
         case 64: CALL(64); break;                  \
+        case 96: CALL(96); break;                  \
         case 128: CALL(128); break;                \
+        case 160: CALL(160); break;                \
         case 256: CALL(256); break;                \
         case 512: CALL(512); break;                \
         default: CALL(0); break;                   \
@@ -1291,15 +1296,15 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x2<R, 1, NF>))     \
     HOM_SET_ATTR1((k_x1<R, NF>))        \
     HOM_SET_ATTR1((k_x1_lanczos<R, NF>))
-    HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(128)
-    HOM_SET_ATTR(256) HOM_SET_ATTR(512)
+    HOM_SET_ATTR(0) HOM_SET_ATTR(8) HOM_SET_ATTR(16) HOM_SET_ATTR(32) HOM_SET_ATTR(64) HOM_SET_ATTR(96)
+    HOM_SET_ATTR(128) HOM_SET_ATTR(160) HOM_SET_ATTR(256) HOM_SET_ATTR(512)
     if constexpr (sizeof(R) == 4) {
 #define HOM_SET_TMA(NF)                   \
     HOM_SET_ATTR1((k_x2_tma<R, -1, NF>))  \
     HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
     HOM_SET_ATTR1((k_x1_tma<R, NF>))      \
     HOM_SET_ATTR1((k_x1_lanczos_tma<R, NF>))
-        HOM_SET_TMA(64) HOM_SET_TMA(128) HOM_SET_TMA(256)
+        HOM_SET_TMA(64) HOM_SET_TMA(96) HOM_SET_TMA(128) HOM_SET_TMA(160) HOM_SET_TMA(256)
 #undef HOM_SET_TMA
         HOM_SET_ATTR1((k_x3r<64>))
         HOM_SET_ATTR1((k_x3r<128>))
@@ -1327,12 +1332,18 @@ int Launch<R>::tma_grids(Geometry &g) {
         };
         switch (g.fast[1]) {
             case 64: b2 = occ(k_x2_tma<R, -1, 64>, g.threads2, g.smem2_tma); break;
+            case 96: b2 = occ(k_x2_tma<R, -1, 96>, g.threads2, g.smem2_tma); break;
+            case 160: b2 = occ(k_x2_tma<R, -1, 160>, g.threads2, g.smem2_tma); break;
             case 128: b2 = occ(k_x2_tma<R, -1, 128>, g.threads2, g.smem2_tma); break;
             default: b2 = occ(k_x2_tma<R, -1, 256>, g.threads2, g.smem2_tma); break;
         }
         switch (g.fast[0]) {
             case 64: b1 = occ(k_x1_tma<R, 64>, g.threads1, g.smem1_tma);
                      b1d = occ(k_x1_tma<R, 64>, g.threads1, g.smem1d_tma); break;
+            case 96: b1 = occ(k_x1_tma<R, 96>, g.threads1, g.smem1_tma);
+                     b1d = occ(k_x1_tma<R, 96>, g.threads1, g.smem1d_tma); break;
+            case 160: b1 = occ(k_x1_tma<R, 160>, g.threads1, g.smem1_tma);
+                      b1d = occ(k_x1_tma<R, 160>, g.threads1, g.smem1d_tma); break;
             case 128: b1 = occ(k_x1_tma<R, 128>, g.threads1, g.smem1_tma);
                       b1d = occ(k_x1_tma<R, 128>, g.threads1, g.smem1d_tma); break;
             default: b1 = occ(k_x1_tma<R, 256>, g.threads1, g.smem1_tma);
@@ -1347,6 +1358,8 @@ int Launch<R>::tma_grids(Geometry &g) {
         if (g.nc == 6 && g.threads1 <= 192) {
             switch (g.fast[0]) {
                 case 64: b1l = occ(k_x1_lanczos_tma<R, 64>, g.threads1, g.smem1_tma); break;
+                case 96: b1l = occ(k_x1_lanczos_tma<R, 96>, g.threads1, g.smem1_tma); break;
+                case 160: b1l = occ(k_x1_lanczos_tma<R, 160>, g.threads1, g.smem1_tma); break;
                 case 128: b1l = occ(k_x1_lanczos_tma<R, 128>, g.threads1, g.smem1_tma); break;
                 default: b1l = occ(k_x1_lanczos_tma<R, 256>, g.threads1, g.smem1_tma); break;
             }
@@ -1408,6 +1421,8 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
     else k_x2_tma<R, -1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state)
             switch (g.fast[1]) {
                 case 64: HOM_X2T(64); break;
+                case 96: HOM_X2T(96); break;
+                case 160: HOM_X2T(160); break;
                 case 128: HOM_X2T(128); break;
                 default: HOM_X2T(256); break;
             }
@@ -1437,6 +1452,8 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 #define HOM_X1T(NF) k_x1_tma<R, NF><<<grid, g.threads1, sm, st>>>(g, flags, *ti, *to, *td, partials, state)
             switch (g.fast[0]) {
                 case 64: HOM_X1T(64); break;
+                case 96: HOM_X1T(96); break;
+                case 160: HOM_X1T(160); break;
                 case 128: HOM_X1T(128); break;
                 default: HOM_X1T(256); break;
             }
@@ -1466,6 +1483,8 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
     k_x1_lanczos_tma<R, NF><<<g.grid1l_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials)
             switch (g.fast[0]) {
                 case 64: HOM_X1LT(64); break;
+                case 96: HOM_X1LT(96); break;
+                case 160: HOM_X1LT(160); break;
                 case 128: HOM_X1LT(128); break;
                 default: HOM_X1LT(256); break;
             }

@@ -274,3 +274,27 @@ def test_apply_spectrum(hom, shape, prec, deriv):
         cdt = np.complex64 if prec == "fp32" else np.complex128
         got = hom.hom_apply_spectrum(ctx, np.ascontiguousarray(spec_in.astype(cdt)))
         assert rel_maxerr(got, ref) <= tol(prec)
+
+
+# the mixed register-FFT plans 96 = 4 4 2 3 and 160 = 4 4 2 5 (the batched
+# cell studies' grids) on every axis: TMA-staged n1 / n2 passes in FP32
+# where both are 96 or 160, plain passes otherwise, and the n3 pass
+MIXED_SHAPES = [(96, 96, 8), (160, 160, 6), (160, 96, 10), (8, 6, 160), (10, 8, 96), (96, 4, 160)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", MIXED_SHAPES)
+def test_mixed_plans_fft(hom, shape, prec):
+    test_fft_forward_inverse(hom, shape, prec)
+
+
+@pytest.mark.parametrize("deriv", [0, 1])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", MIXED_SHAPES)
+def test_mixed_plans_project_apply_rhs(hom, shape, prec, deriv):
+    test_project_apply_rhs(hom, shape, prec, deriv)
+
+
+@pytest.mark.parametrize("shape", [(96, 96, 8), (160, 160, 6), (8, 6, 160)])
+def test_mixed_plans_apply_spectrum(hom, shape):
+    test_apply_spectrum(hom, shape, "fp32", 1)
