@@ -191,6 +191,26 @@ def kernel_traffic(name, n):
     return k["dram_bytes_per_voxel"] * n ** 3
 
 
+def oracle_error(n, rho, sigma_mean):
+    """Error of this result's mean stress against the FP64 oracle's for the
+    same cell and macro strain, solved to a relative residual of 1e-10 and
+    stored in tests/golden/ by tests/golden/make_octet_golden.py (max abs
+    difference over the 6 components / max |oracle|), or None when no stored
+    value exists for this cell."""
+    p = os.path.join(ROOT, "tests", "golden", f"octet{n}_rho{rho:.2f}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        gold = json.load(f)
+    for case in gold["cases"]:
+        if np.allclose(case["macro_strain"], MACRO / np.max(np.abs(MACRO))):
+            ref = np.asarray(case["sigma_mean"]) * np.max(np.abs(MACRO))   # linear in the macro strain
+            err = float(np.max(np.abs(np.asarray(sigma_mean) - ref)) / np.max(np.abs(ref)))
+            return {"rel_err_sigma_mean": err, "oracle_tol": gold["tol"],
+                    "oracle_iterations": case["iterations"], "source": os.path.relpath(p, ROOT)}
+    return None
+
+
 def source_hash():
     """Hash of the solver's kernel sources (the network's files do not change
     the solver kernels' traffic)."""
@@ -383,6 +403,7 @@ def run_ours(args):
                 "time_to_tol_ms": 1e3 * t_max / args.steps,
                 "true_residual": last["true_residual"], "sweeps": last["sweeps"],
                 "sigma11_pa": float(last["sigma_mean"][0]),
+                "vs_fp64_oracle": oracle_error(n, args.rho, last["sigma_mean"]),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)

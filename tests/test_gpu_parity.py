@@ -298,3 +298,20 @@ def test_mixed_plans_project_apply_rhs(hom, shape, prec, deriv):
 @pytest.mark.parametrize("shape", [(96, 96, 8), (160, 160, 6), (8, 6, 160)])
 def test_mixed_plans_apply_spectrum(hom, shape):
     test_apply_spectrum(hom, shape, "fp32", 1)
+
+
+def test_solve_octet256_headline_matches_stored_oracle(hom):
+    """The 256^3 headline cell (octet, density 0.10, E11, tol 1e-6, FP32
+    fields): mean stress against the FP64 oracle's, solved to 1e-10 and stored
+    by tests/golden/make_octet_golden.py, within 1e-4 of its largest entry."""
+    gold = _golden("octet256_rho0.10.json")
+    phi, radius = ri.octet(256, gold["relative_density"])
+    assert abs(radius - gold["radius"]) < 1e-12
+    case = gold["cases"][0]
+    with make(hom, phi.astype(np.float64), "fp32") as ctx:
+        rc, info = hom.hom_solve(ctx, np.array(case["macro_strain"]), tol=1e-6, max_it=5000)
+        assert rc == hom.HOM_OK
+        ref = np.array(case["sigma_mean"])
+        err = np.max(np.abs(np.array(info[0]["sigma_mean"]) - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-4, err
+        assert info[0]["true_residual"] <= 1e-6
