@@ -70,9 +70,13 @@ def parse():
     ap.add_argument("--host-loop", action="store_true",
                     help="replay the MINRES loop body from the host (same kernels; lets ncu list them)")
     ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--warm", action="store_true",
+                    help="asprinted: also solve from the learned warm start (the network is trained first)")
+    ap.add_argument("--train", type=int, default=2000, help="warm start: solver runs in the training set")
+    ap.add_argument("--epochs", type=int, default=24, help="warm start: training epochs")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation",
-                             "smoothing", "j2", "j2curve"],
+                             "smoothing", "j2", "j2curve", "warmstart"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
                          "batch: 16 octet cells x 6 unit strains at once")
     return ap.parse_args()
@@ -580,6 +584,8 @@ def run_j2(args):
                                           "lateral_over_axial": float(np.max(np.abs(info["sigma_mean"][1:])) /
                                                                       abs(info["sigma_mean"][0]))})
             _, _, alpha = hom.hom_j2_state(ctx)
+            # kernel times at the last iterate (CUDA events on the library's stream)
+            run["kernel_ms"] = hom.hom_j2_time_kernels(ctx, reps=20)
             run.update({"voxel_iters_per_s": n ** 3 * lin / (ms / 1e3), "ms_total": ms, "linear_total": lin,
                         "gpu_launches": hom.hom_kernel_launches(ctx) - launches0,
                         "yielded_fraction_of_struts": float((alpha[phi > 0.5] > 0).mean())})
@@ -594,6 +600,20 @@ def run_j2(args):
     best = min(ok, key=lambda k: out[k]["ms_total"]) if ok else "fp64"
     out["value"] = out[best]["voxel_iters_per_s"]
     out["value_from"] = best
+    # roofline of the tangent application (the J2 kernel inside every MINRES
+    # iteration): algorithmic bytes = the 36-entry tangent, the input and the
+    # output strain per voxel, in the operator's precision
+    peak, peak_kind = measured_peaks()
+    kms = out[best]["kernel_ms"]
+    w = 4 if best == "fp32_fields" else 8
+    b_apply = (36 + 12) * w
+    b_return = 8 * (6 + 6 + 1 + 6) + 36 * w + 8     # eps, epsp, alpha, sig (FP64), tangent, phi
+    ach = b_apply * n ** 3 / (kms["j2_tangent_apply"] * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "j2_tangent_apply", "achieved": ach, "peak": peak,
+                       "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                       "bytes_per_voxel": b_apply,
+                       "j2_return": {"bytes_per_voxel": b_return, "ms": kms["j2_return"],
+                                     "achieved_gbs": b_return * n ** 3 / (kms["j2_return"] * 1e-3) / 1e9}}
     out["dtype"] = "f32" if best == "fp32_fields" else "f64"
     print(json.dumps(out), flush=True)
     return 0
@@ -753,7 +773,11 @@ def run_asprinted(args):
     """Synthetic as-printed lattice: 2x2x2 octet cells at 512^3 (134 M voxels),
     12 % density, strut surface moved by a Gaussian random field (correlation
     3 voxels, std 1 voxel), spherical pores (radius 2-8 voxels, 1 % of the
-    solid), Voigt fractions; FP32 fields, six unit strains, tol 1e-6."""
+    solid), Voigt fractions; FP32 fields, six unit strains stacked, tol 1e-6.
+    With --warm the warm-start network is trained on solver runs at 64^3
+    (one unit cell, as in warmstart.py), runs on a 128^3 grid (64 voxels per
+    unit cell, phi averaged over 4^3 blocks) and its prediction starts the
+    same six solves; both lines are printed."""
     import torch
     from paper_2110_00733_gb300 import build, hom
     build.build()
@@ -762,21 +786,90 @@ def run_asprinted(args):
     t0 = time.perf_counter()
     phi, r = ri.as_printed(args.n, cells=2, rho=0.12, seed=0)
     tgen = time.perf_counter() - t0
-    ctx = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rc, info = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=MAX_IT)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    C = hom.hom_effective_stiffness(ctx)
-    its = [i["iterations"] for i in info]
     V = args.n ** 3
-    print(json.dumps({"workload": f"as_printed_2x2x2_octet_{args.n}^3_rho0.12", "rc": rc,
-                      "generation_s": tgen, "phi_mean": float(phi.mean()), "solve_s": dt,
-                      "iterations": its, "voxel_iters_per_s": V * sum(its) / dt,
-                      "true_residual_max": max(i["true_residual"] for i in info),
-                      "C_eff_pa": C.tolist()}), flush=True)
-    ctx.close()
+    phi_d = torch.from_numpy(np.ascontiguousarray(phi, dtype=np.float32)).cuda()
+    wl = f"as_printed_2x2x2_octet_{args.n}^3_rho0.12"
+    with hom.hom_create(phi.shape, phi_d, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M, device_ptrs=True) as ctx:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=MAX_IT)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        C0 = hom.hom_effective_stiffness(ctx)
+        its = [i["iterations"] for i in info]
+        print(json.dumps({"workload": wl, "start": "zero", "rc": rc, "generation_s": tgen,
+                          "phi_mean": float(phi.mean()), "solve_s": dt, "iterations": its,
+                          "voxel_iters_per_s": V * sum(its) / dt,
+                          "true_residual_max": max(i["true_residual"] for i in info),
+                          "C_eff_pa": C0.tolist()}), flush=True)
+        if not args.warm:
+            return 0
+        from paper_2110_00733_gb300 import net as hnet
+        from paper_2110_00733_gb300 import warmstart as ws
+        model = hnet.Net(seed=1)
+        t0 = time.perf_counter()
+        tphi, tmacro, ttarget, _ = ws.make_dataset(64, args.train)
+        tdata = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = ws.train(model, 64, tphi, tmacro, ttarget, epochs=args.epochs)
+        torch.cuda.synchronize()
+        ttrain = time.perf_counter() - t0
+        del tphi, ttarget
+        x0 = torch.zeros((6, 6, V), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model.warm_start((args.n,) * 3, args.n // 128, phi_d.reshape(-1), np.eye(6), x0)
+        torch.cuda.synchronize()
+        tinf = time.perf_counter() - t0
+        rc, infow = hom.hom_solve(ctx, np.eye(6), tol=TOL, max_it=MAX_IT, warm_start=x0)
+        torch.cuda.synchronize()
+        dtw = time.perf_counter() - t0
+        Cw = hom.hom_effective_stiffness(ctx)
+        itw = [i["iterations"] for i in infow]
+        print(json.dumps({"workload": wl, "start": "learned warm start", "rc": rc,
+                          "dataset_s": tdata, "train_s": ttrain, "final_loss": losses[-1],
+                          "inference_s": tinf, "solve_s_with_inference": dtw, "iterations": itw,
+                          "voxel_iters_per_s": V * sum(itw) / dtw,
+                          "true_residual_max": max(i["true_residual"] for i in infow),
+                          "C_eff_rel_diff_vs_zero_start": float(np.max(np.abs(Cw - C0)) / np.max(np.abs(C0))),
+                          "C_eff_pa": Cw.tolist()}), flush=True)
+        model.close()
+    return 0
+
+
+def run_warmstart(args):
+    """Learned warm start against zero start (config 4): the network is
+    trained on --train solver runs at 64^3 (octet, density U[0.03, 0.30],
+    macro strain uniform on the Mandel unit sphere), then on held-out octet
+    cells at --n^3 (seeds 10000+, 8 unless --steps asks for more) each cell
+    is solved from a zero start and from the network's prediction (network on
+    64^3, phi averaged over (n/64)^3 blocks, head interpolated back), FP32
+    fields, tol 1e-6 on the FP64 true residual.  Time to tolerance of the
+    warm start includes inference.  One JSON line with the per-cell rows and
+    the median savings."""
+    import torch
+    from paper_2110_00733_gb300 import build, net as hnet, warmstart as ws
+    build.build()
+    torch.cuda.set_device(0)
+    model = hnet.Net(seed=1)
+    t0 = time.perf_counter()
+    tphi, tmacro, ttarget, its = ws.make_dataset(64, args.train)
+    tdata = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = ws.train(model, 64, tphi, tmacro, ttarget, epochs=args.epochs)
+    torch.cuda.synchronize()
+    ttrain = time.perf_counter() - t0
+    del tphi, ttarget
+    ncell = max(8, args.steps)
+    rows = ws.evaluate(model, 64, args.n, range(10000, 10000 + ncell))
+    model.close()
+    it_save = [1.0 - r["warm_it"] / r["zero_it"] for r in rows]
+    t_save = [1.0 - r["warm_s"] / r["zero_s"] for r in rows]
+    print(json.dumps({"metric": "time_to_tol_saving_learned_warm_start", "unit": "fraction",
+                      "workload": f"warm_start_octet_{args.n}^3_heldout_x{ncell}_trained_64^3_x{args.train}",
+                      "value": statistics.median(t_save), "median_iteration_saving": statistics.median(it_save),
+                      "dataset_s": tdata, "train_s": ttrain, "final_loss": losses[-1],
+                      "mean_train_iterations": float(np.mean(its)), "cells": rows}), flush=True)
     return 0
 
 
@@ -802,6 +895,8 @@ def main():
         return run_j2curve(args)
     if args.workload == "modbfft":
         return run_modbfft(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

@@ -98,7 +98,8 @@ typedef struct {
     int tile2;          /* launch shape: n2-pass columns per CTA (0 = automatic; power of 2, <= 32) */
     int tile1;          /* launch shape: n1-pass columns per CTA (0 = automatic, <= 16) */
     int staging;        /* 0: persistent TMA-staged n1/n2 passes where supported
-                           (FP32, power-of-two n1, n2 in [64, 256]); 1: plain loads */
+                           (FP32, n1 and n2 in {64, 96, 128, 160, 256, 512});
+                           1: plain loads */
     double alpha;       /* MoDBFFT penalty alpha / E (0: 1e-4, section 4.2) */
     int autotune;       /* nonzero (and no explicit rows3/tile2/tile1): launch
                            shapes from hom_autotune for this grid and precision */
@@ -329,6 +330,16 @@ int hom_apply_spectrum(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum
  * the next Lanczos vector), Givens step.  Returns the number of entries
  * written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
+
+/* Average device time in milliseconds of the kernels of the J2 Newton
+ * extension (section 2.1.1) at the context's current iterate, each launched
+ * `reps` times back to back on the context's stream between two CUDA events
+ * (an instrument for roofline measurements; hom_j2_begin first; it changes no
+ * state a later increment reads).  ms[0] radial return with the consistent
+ * tangent at every voxel, ms[1] tangent application C_t : x at every voxel,
+ * ms[2] and ms[3] the tangent operator's n3 passes (C2R to a real field, R2C
+ * from one).  Returns the number of entries written (<= nmax). */
+int hom_j2_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* A(eps) of hom_apply for a small cell, allocating no device memory.  The
  * paper has no counterpart: this is a calling convention for callers that

@@ -160,6 +160,7 @@ struct hom_ctx {
     double2 *bb64 = nullptr, *br64 = nullptr;    // bcap x 6S
     MinresState *d_bst = nullptr, *h_bst = nullptr;
     double *bpart = nullptr;
+    int *bcnt = nullptr;                         // kFoldCounters counters of the folded scalar steps
     cudaGraphExec_t bgraph = nullptr;
     int bgraph_nb = 0;
     bool bgraph_loops = false;
@@ -240,7 +241,7 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
         while (rows > 1 && 2ull * g.n3 * np * rows * cs > 48 * 1024) rows >>= 1;
     }
     if (g.fast[1]) {
-        t2 = g.n2 >= 128 ? 16 : 32;
+        t2 = g.n2 >= 512 ? 8 : (g.n2 >= 128 ? 16 : 32);
     } else {
         t2 = 32;
         while (t2 > 1 && 2ull * g.n2 * t2 * cs > 64 * 1024) t2 >>= 1;
@@ -302,8 +303,8 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     g.tma = 0;
     g.err = ctx->d_err;
     g.tma_cache = nullptr;
-    if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 256 &&
-        g.fast[1] >= 64 && g.fast[1] <= 256 && g.tile2 % 2 == 0) {
+    if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 512 &&
+        g.fast[1] >= 64 && g.fast[1] <= 512 && g.tile2 % 2 == 0) {
         g.tma = 1;
         g.smem2_tma = 2ull * g.n2 * g.tile2 * cs;
         g.smem1_tma = 2ull * nc * g.tile1 * g.n1 * cs;
@@ -1274,6 +1275,8 @@ static void batch_free(hom_ctx *ctx) {
     cudaFree(ctx->br64);
     cudaFree(ctx->d_bst);
     cudaFree(ctx->bpart);
+    cudaFree(ctx->bcnt);
+    ctx->bcnt = nullptr;
     if (ctx->h_bst) cudaFreeHost(ctx->h_bst);
     ctx->bspec = ctx->bv[0] = ctx->bv[1] = ctx->bw[0] = ctx->bw[1] = ctx->bx = ctx->brhs = nullptr;
     ctx->bb64 = ctx->br64 = nullptr;
@@ -1320,6 +1323,8 @@ static int batch_reserve(hom_ctx *ctx, int nb) {
         np = std::max(np, (long long)Launch<float>::x1_lanczos_grid(ctx->e32.g));
     }
     CU(cudaMalloc(&ctx->bpart, sizeof(double) * np * nb));
+    CU(cudaMalloc(&ctx->bcnt, sizeof(int) * kFoldCounters));
+    CU(cudaMemset(ctx->bcnt, 0, sizeof(int) * kFoldCounters));
     ctx->bcap = nb;
     return HOM_OK;
 }
@@ -1338,10 +1343,11 @@ static int batch_width(hom_ctx *ctx, int ncase) {
 }
 
 // One step of the fused chain for every case of the stacked batch (see the
-// kernels in hom_passes.cuh): n2 inverse, n3 pass with the material law and
-// the strain-energy sums, alpha (one CTA per case), n2 forward, fused n1 pass
-// (projector, Lanczos step, lagged w / x update, projector and inverse of
-// u_{k+1}), Givens step (one CTA per case).  Buffer roles as in capture_body.
+// kernels in hom_passes.cuh), five launches: n2 inverse; n3 pass with the
+// material law and the strain-energy sums; alpha (one CTA per case); n2
+// forward; fused n1 pass (projector, Lanczos step, lagged w / x update,
+// projector and inverse of u_{k+1}), whose last CTA takes the Givens step of
+// every case.  Buffer roles as in capture_body.
 template <typename R>
 static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     const Geometry &g = ctx->bg;
@@ -1349,7 +1355,14 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     cpx<R> *ua = (cpx<R> *)ctx->bv[0], *ub = (cpx<R> *)ctx->bv[1];
     cpx<R> *wc = (cpx<R> *)ctx->bw[0], *wd = (cpx<R> *)ctx->bw[1];
     cpx<R> *x = (cpx<R> *)ctx->bx, *spec = (cpx<R> *)ctx->bspec;
-    const int np3 = Launch<R>::x3_epart_grid(g), npl = Launch<R>::x1_lanczos_grid(g);
+    // the Givens step folded into the n1 pass (its last CTA sums one partial
+    // per CTA of a persistent grid); alpha, whose n3-pass partials number one
+    // per eight rows, in its own kernel (1024 threads reduce them faster than
+    // the n3 pass's last CTA: measured 1.556 against 1.538 ms per step at 256^3
+    // with both folded against neither; the fold is kept for the option)
+    const Fold fold{ctx->bcnt, ctx->d_bst, (double)ctx->V};
+    const Fold fold3{nullptr, nullptr, 0.0};
+    const int np3 = Launch<R>::x3_epart_grid(g);
     cudaStream_t s = ctx->stream;
     for (int it = 0; it < ctx->graph_iters; ++it) {
         const bool odd = (it % 2) == 0;
@@ -1357,12 +1370,11 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
         cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;
         Launch<R>::x2(g, s, 1, spec, ctx->d_bst);
         Launch<R>::x3(g, s, X3_IN_SPEC, spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, spec,
-                      E.phi, ctx->d_bst, ctx->bpart);
-        scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, nb);
+                      E.phi, ctx->d_bst, ctx->bpart, fold3);
+        if (!fold3.cnt) scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, g.nb);
         Launch<R>::x2(g, s, 0, spec, ctx->d_bst);
-        Launch<R>::x1_lanczos(g, s, spec, uk, um, wa, wb, x, ctx->d_bst, ctx->bpart);
-        scalar_givens(s, ctx->d_bst, ctx->bpart, npl, nb);
-        ctx->launches += 6;
+        Launch<R>::x1_lanczos(g, s, spec, uk, um, wa, wb, x, ctx->d_bst, ctx->bpart, fold);
+        ctx->launches += fold3.cnt ? 4 : 5;
     }
 }
 
@@ -1464,6 +1476,9 @@ static int batch_begin(hom_ctx *ctx, Engine<R> &E, int nb, const double *tol, co
     for (int j = 0; j < nb; ++j) *any = *any || !ctx->h_bst[j].done;
     CU(cudaMemsetAsync(ctx->bx, 0, sizeof(cpx<R>) * kv * nb, s));
     if (!*any) return HOM_OK;
+    // the folded scalar steps' counters start at zero (each last CTA resets
+    // its own; this also clears any left by a sweep that stopped on an error)
+    CU(cudaMemsetAsync(ctx->bcnt, 0, sizeof(int) * kFoldCounters, s));
     // u_0 = 0, u_1 = rhs (= beta_1 v_1), w_0 = w_{-1} = 0, in tile order; the
     // work spectrum enters each step holding F_1^-1 G u_k
     CU(cudaMemsetAsync(ctx->bv[0], 0, sizeof(cpx<R>) * kv * nb, s));
@@ -2867,6 +2882,70 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
     cudaSetDevice(ctx->device);
     int r = (ctx->prec == HOM_PREC_FP64) ? time_kernels_impl<double>(ctx, ctx->e64, reps, ms, nmax)
                                          : time_kernels_impl<float>(ctx, ctx->e32, reps, ms, nmax);
+    if (r < 0) return r;
+    int rc = finish(ctx);
+    return rc ? rc : r;
+}
+
+// Average device time of the J2 kernels of one Newton iteration and one
+// tangent-operator application, each launched `reps` times back to back on
+// the context's stream between two CUDA events, at the current iterate:
+// ms[0] radial return with the consistent tangent (k_j2_return, tangent in
+// the operator's precision), ms[1] tangent application y = C_t : x
+// (k_j2_tangent_apply, in the operator's precision), ms[2] the tangent
+// operator's n3 C2R pass to a real field, ms[3] its n3 R2C pass from one.
+template <typename R>
+static int j2_time_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
+    J2State &j = ctx->j2;
+    cudaStream_t s = ctx->stream;
+    R *tin, *tout;
+    if constexpr (std::is_same<R, double>::value) {
+        tin = j.sig; tout = j.de;
+    } else {
+        tin = j.sig32; tout = j.de32;
+    }
+    const int nk = 4;
+    for (int k = 0; k < nk && k < nmax; ++k) {
+        for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
+            const int r = pass ? reps : 1;
+            CU(cudaEventRecord(ctx->ev0, s));
+            for (int i = 0; i < r; ++i) {
+                switch (k) {
+                    case 0:
+                        if (j.Ct) j2_return<double>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct, 0, s);
+                        else j2_return<float>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct32, 0, s);
+                        break;
+                    case 1:
+                        if constexpr (std::is_same<R, double>::value) j2_tangent_apply<double, double>(ctx->V, j.Ct, tin, tout, s);
+                        else j2_tangent_apply<float, float>(ctx->V, j.Ct32, tin, tout, s);
+                        break;
+                    case 2:
+                        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL,
+                                      tin, E.phi, nullptr);
+                        break;
+                    default:
+                        Launch<R>::x3(E.g, s, X3_IN_REAL, tout, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
+                                      E.spec, E.phi, nullptr);
+                        break;
+                }
+            }
+            CU(cudaEventRecord(ctx->ev1, s));
+            CU(cudaEventSynchronize(ctx->ev1));
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1));
+            ms[k] = (double)t / r;
+        }
+        ctx->launches += reps + 1;
+    }
+    return nk < nmax ? nk : nmax;
+}
+
+int hom_j2_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
+    if (!ctx || !ms || reps <= 0 || nmax <= 0) return fail(ctx, HOM_EINVAL, "bad argument");
+    if (!ctx->j2.active) return fail(ctx, HOM_EINVAL, "hom_j2_begin first");
+    cudaSetDevice(ctx->device);
+    int r = (ctx->prec == HOM_PREC_FP64) ? j2_time_impl<double>(ctx, ctx->e64, reps, ms, nmax)
+                                         : j2_time_impl<float>(ctx, ctx->e32, reps, ms, nmax);
     if (r < 0) return r;
     int rc = finish(ctx);
     return rc ? rc : r;

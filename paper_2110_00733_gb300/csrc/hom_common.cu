@@ -85,7 +85,7 @@ __global__ void k_scalar_alpha(MinresState *st, const double *partials, int np, 
     partials += (size_t)blockIdx.x * np;
     if (st->done) return;
     const double a = reduce_partials(partials, np);
-    if (threadIdx.x == 0) st->alpha = scale * a / (st->beta * st->beta);
+    if (threadIdx.x == 0) alpha_step(st, a, scale);
 }
 
 // MINRES step k: apply the previous Givens rotation to the new column of the
@@ -98,44 +98,7 @@ __global__ void k_scalar_givens(MinresState *st, const double *partials, int np)
     partials += (size_t)blockIdx.x * np;
     if (st->done) return;
     const double bn2 = reduce_partials(partials, np);
-    if (threadIdx.x != 0) return;
-    const double beta_next = sqrt(bn2 > 0 ? bn2 : 0.0);
-    const double alpha = st->alpha, c = st->c, s = st->s, dbar = st->dbar;
-    const double delta = c * dbar + s * alpha;
-    const double gbar = s * dbar - c * alpha;
-    const double eps_next = s * beta_next;
-    const double dbar_next = -c * beta_next;
-    double gamma = hypot(gbar, beta_next);
-    if (gamma == 0.0) gamma = 1e-300;
-    const double cn = gbar / gamma, sn = beta_next / gamma;
-    const double tau = cn * st->phibar;
-    const double phibar = sn * st->phibar;
-    st->u_delta = delta;
-    st->u_eps = st->eps;            // epsilon_k multiplies w_{k-2}
-    st->u_inv_gamma = 1.0 / gamma;
-    st->u_tau = tau;
-    st->u_inv_beta = 1.0 / st->beta;   // v_k = u_k / beta_k in the lagged update
-    st->c = cn;
-    st->s = sn;
-    st->dbar = dbar_next;
-    st->eps = eps_next;
-    st->phibar = phibar;
-    st->beta_prev = st->beta;
-    st->beta = beta_next;
-    st->k += 1;
-    st->est = phibar / st->beta1;
-    if (!isfinite(alpha) || !isfinite(beta_next) || !isfinite(phibar)) {
-        st->status = -5;
-        st->done = 1;
-        st->done_update = 1;        // keep the last finite iterate
-        return;
-    }
-    if (st->est <= st->tol || beta_next == 0.0) {
-        st->done = 1;               // the flush still applies this step's update
-    } else if (st->k >= st->max_it) {
-        st->status = 1;
-        st->done = 1;
-    }
+    if (threadIdx.x == 0) givens_step(st, bn2);
 }
 
 // Condition of the device-side MINRES loop: one more body while not done
@@ -368,7 +331,9 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
     if (kind == TMA_X2) {
         cuuint64_t dims[3] = {h6, (cuuint64_t)g.n2, (cuuint64_t)g.n1 * g.nb};
         cuuint64_t strides[2] = {h6 * 8, h6 * 8 * g.n2};
-        cuuint32_t box[3] = {(cuuint32_t)(g.tile2 * units), (cuuint32_t)g.n2, 1};
+        // box dimensions hold at most 256 elements: longer columns move in
+        // boxes of 256 rows (the kernels issue one copy per box)
+        cuuint32_t box[3] = {(cuuint32_t)(g.tile2 * units), (cuuint32_t)(g.n2 < 256 ? g.n2 : 256), 1};
         cuuint32_t es[3] = {1, 1, 1};
         r = fn(&e->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -376,7 +341,7 @@ const CUtensorMap *tma_map(const Geometry &g, const void *ptr, int kind, int uni
     } else {
         cuuint64_t dims[2] = {h6 * g.n2, (cuuint64_t)g.n1 * g.nb};
         cuuint64_t strides[1] = {h6 * g.n2 * 8};
-        cuuint32_t box[2] = {(cuuint32_t)(g.nc * g.tile1 * units), (cuuint32_t)g.n1};
+        cuuint32_t box[2] = {(cuuint32_t)(g.nc * g.tile1 * units), (cuuint32_t)(g.n1 < 256 ? g.n1 : 256)};
         cuuint32_t es[2] = {1, 1};
         r = fn(&e->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -14,6 +14,7 @@
 // compatible fields this is the same iteration as MINRES on A(e) in real space.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "hom_fft.cuh"
@@ -49,6 +50,58 @@ struct MinresState {
     int max_bodies;    // hard cap of that loop
 };
 
+// alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2 from sum = <u_k, A u_k> / scale
+__device__ __forceinline__ void alpha_step(MinresState *st, double sum, double scale) {
+    if (st->done) return;
+    st->alpha = scale * sum / (st->beta * st->beta);
+}
+
+// MINRES step k (one thread): apply the previous Givens rotation to the new
+// column of the Lanczos tridiagonal, form the next rotation and the
+// coefficients of the w_k / x_k update (applied by the next step's kernel,
+// or by the flush after the loop); stop when phibar_k / beta_1 <= tol,
+// beta_{k+1} = 0, or k reaches max_it.  bn2 = ||u_{k+1}||^2.
+__device__ __forceinline__ void givens_step(MinresState *st, double bn2) {
+    if (st->done) return;
+    const double beta_next = sqrt(bn2 > 0 ? bn2 : 0.0);
+    const double alpha = st->alpha, c = st->c, s = st->s, dbar = st->dbar;
+    const double delta = c * dbar + s * alpha;
+    const double gbar = s * dbar - c * alpha;
+    const double eps_next = s * beta_next;
+    const double dbar_next = -c * beta_next;
+    double gamma = hypot(gbar, beta_next);
+    if (gamma == 0.0) gamma = 1e-300;
+    const double cn = gbar / gamma, sn = beta_next / gamma;
+    const double tau = cn * st->phibar;
+    const double phibar = sn * st->phibar;
+    st->u_delta = delta;
+    st->u_eps = st->eps;            // epsilon_k multiplies w_{k-2}
+    st->u_inv_gamma = 1.0 / gamma;
+    st->u_tau = tau;
+    st->u_inv_beta = 1.0 / st->beta;   // v_k = u_k / beta_k in the lagged update
+    st->c = cn;
+    st->s = sn;
+    st->dbar = dbar_next;
+    st->eps = eps_next;
+    st->phibar = phibar;
+    st->beta_prev = st->beta;
+    st->beta = beta_next;
+    st->k += 1;
+    st->est = phibar / st->beta1;
+    if (!isfinite(alpha) || !isfinite(beta_next) || !isfinite(phibar)) {
+        st->status = -5;
+        st->done = 1;
+        st->done_update = 1;        // keep the last finite iterate
+        return;
+    }
+    if (st->est <= st->tol || beta_next == 0.0) {
+        st->done = 1;               // the flush still applies this step's update
+    } else if (st->k >= st->max_it) {
+        st->status = 1;
+        st->done = 1;
+    }
+}
+
 // Scalars of one preconditioned CG solve (MoDBFFT, section 2.2); same
 // leading flags as MinresState.
 struct CgState {
@@ -81,7 +134,7 @@ struct Geometry {
     // MinresState per case); 1 everywhere else
     int nb = 1;
     int mask0;              // stress-controlled Mandel components (bit c): the projector keeps them at xi = 0
-    // persistent TMA-staged n2 / n1 passes (FP32, power-of-two n <= 256):
+    // persistent TMA-staged n2 / n1 passes (FP32, register-FFT n in [64, 512]):
     // enabled flag, persistent grid sizes, shared memory, host-side cache of
     // tensor maps (never dereferenced on the device) and the device word a
     // pass sets when a bounded wait gives up
@@ -132,15 +185,30 @@ constexpr int kEwThreads = 256;
 
 struct Mac6 { double v[6]; };
 
+// The MINRES scalar steps folded into the pass that produces their partial
+// sums: every CTA of a group counts itself on a counter after writing its
+// partial, and the last one reduces the group's partials (fixed order) and
+// applies the step to the FP64 state, then resets the counter for the next
+// launch.  cnt == nullptr: no folding (a separate scalar kernel does the step).
+// Counters: cnt[c] the n3 pass's CTAs of case c, cnt[kNbMax + c] the plain
+// n1 pass's CTAs of case c, cnt[2 kNbMax] the persistent n1 pass's CTAs.
+struct Fold {
+    int *cnt;
+    MinresState *st;     // the states (one per case)
+    double scale;        // alpha: the partials sum to <u, A^ u> / scale
+};
+constexpr int kFoldCounters = 2 * kNbMax + 1;
+
 template <typename R> struct Launch {
     // n3 pass: C2R (SPEC in) or real / macro input, optional material law
     // tau = phi C_m e, R2C (SPEC out) or real output; scale applied to the
     // real-space values (1/V for SPEC in is included automatically).
     // epart (6-component spectra only): per-CTA sums of the strain energy
     // e : C : e of the scaled real-space input (x3_grid(g) values).
+    // fold: the alpha step folded into the pass (see Fold in hom_passes.cuh)
     static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart = nullptr);
+                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{});
     // n2 pass, in place on the half spectrum
     static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
     // n1 pass: in -> out (may alias), optional projector before / after, and
@@ -158,8 +226,10 @@ template <typename R> struct Launch {
     // forward n3 / n2 transforms of C e_k on entry and the inverse n1
     // transform of G u_{k+1} on exit; um, wb, x as for lanczos_update;
     // x1_lanczos_grid(g) partials of ||u_{k+1}||^2
+    // (fold: the Givens step folded into the pass)
     static void x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
-                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials);
+                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials,
+                           Fold fold = Fold{});
     static int x1_lanczos_grid(const Geometry &g);
     // standard half-spectrum order <-> n1-tile order of the fused chain's
     // Krylov vectors (the tile order's padding is left untouched)

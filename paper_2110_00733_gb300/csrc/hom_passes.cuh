@@ -75,6 +75,27 @@ __device__ __forceinline__ bool skip(const MinresState *s) { return s != nullptr
 // load case c of a stacked batch (state points to g.nb states, or is null)
 __device__ __forceinline__ bool skip_case(const MinresState *s, int c) { return s != nullptr && s[c].done; }
 
+// true in every thread of the last CTA of a group of `count`; all threads
+// of the CTA call it after thread 0 wrote the CTA's partial
+__device__ __forceinline__ bool last_of(int *cnt, int count) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // the partial is visible before the count
+        s_last = atomicAdd(cnt, 1) == count - 1;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// fixed-order sum of count partials written by other CTAs (read at L2)
+__device__ __forceinline__ double sum_partials(const double *part, int count) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v += __ldcg(part + i);
+    return block_sum(v);
+}
+
 // Parseval weight of the half-spectrum plane k3
 __device__ __forceinline__ int pweight(int k3, int n3) { return (k3 == 0 || 2 * k3 == n3) ? 1 : 2; }
 
@@ -251,7 +272,7 @@ template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
-                                        double *__restrict__ epart) {
+                                        double *__restrict__ epart, Fold fold) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
     // stride by ES across a warp and stay free of bank conflicts; the fast
@@ -368,6 +389,13 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
     if (epart) {
         const double sum = block_sum((double)en);
         if (threadIdx.x == 0) epart[blockIdx.x] = sum;
+        if (fold.cnt && last_of(fold.cnt + cs, bpc)) {   // alpha of case cs
+            const double tot = sum_partials(epart + (size_t)cs * bpc, bpc);
+            if (threadIdx.x == 0) {
+                alpha_step(fold.st + cs, tot, fold.scale);
+                fold.cnt[cs] = 0;
+            }
+        }
     }
     if (out_mode == X3_OUT_REAL) return;
     // rows beyond nrows hold zeros already (their inputs were zero)
@@ -440,7 +468,7 @@ __device__ __forceinline__ void x3r_stage2(const float2 *slab, int t, float2 (&z
 template <int N>
 __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
                                                 int material, float lam, float mu2, const float *__restrict__ phi,
-                                                const MinresState *state, double *__restrict__ epart) {
+                                                const MinresState *state, double *__restrict__ epart, Fold fold) {
     using PL = X3RPlan<N>;
     constexpr int P = PL::P, Q = PL::Q, ROWS = PL::ROWS, H = N / 2 + 1, NC = 6;
     constexpr int TS = Q * (P + 1);   // one line's transpose slab
@@ -566,6 +594,13 @@ __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const 
     if (epart) {
         const double sum = block_sum((double)en);
         if (threadIdx.x == 0) epart[blockIdx.x] = sum;
+        if (fold.cnt && last_of(fold.cnt + cs, bpc)) {   // alpha of case cs
+            const double tot = sum_partials(epart + (size_t)cs * bpc, bpc);
+            if (threadIdx.x == 0) {
+                alpha_step(fold.st + cs, tot, fold.scale);
+                fold.cnt[cs] = 0;
+            }
+        }
     }
 }
 
@@ -658,8 +693,27 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1(Geometry g, int flags, const cpx<
     }
 }
 
+// A TMA box dimension holds at most 256 elements: a tile of n > 256 rows
+// (n = 512) moves as consecutive boxes of 256 rows; rowb is the bytes of one
+// row of the tile in shared memory.
+constexpr int kBoxRows = 256;
+__device__ __forceinline__ void tma_load_rows_3d(void *dst, const CUtensorMap *tm, int x, int n, int z, int rowb,
+                                                 uint64_t *bar) {
+    for (int y0 = 0; y0 < n; y0 += kBoxRows) tma_load_3d((char *)dst + (size_t)y0 * rowb, tm, x, y0, z, bar);
+}
+__device__ __forceinline__ void tma_store_rows_3d(const CUtensorMap *tm, int x, int n, int z, const void *src, int rowb) {
+    for (int y0 = 0; y0 < n; y0 += kBoxRows) tma_store_3d(tm, x, y0, z, (const char *)src + (size_t)y0 * rowb);
+}
+__device__ __forceinline__ void tma_load_rows_2d(void *dst, const CUtensorMap *tm, int x, int y, int n, int rowb,
+                                                 uint64_t *bar) {
+    for (int y0 = 0; y0 < n; y0 += kBoxRows) tma_load_2d((char *)dst + (size_t)y0 * rowb, tm, x, y + y0, bar);
+}
+__device__ __forceinline__ void tma_store_rows_2d(const CUtensorMap *tm, int x, int y, int n, const void *src, int rowb) {
+    for (int y0 = 0; y0 < n; y0 += kBoxRows) tma_store_2d(tm, x, y + y0, (const char *)src + (size_t)y0 * rowb);
+}
+
 // ---------------------------------------------------------------------------
-// Persistent TMA-staged n2 and n1 passes (FP32, n <= 256, fast engine).
+// Persistent TMA-staged n2 and n1 passes (FP32, register-FFT n in [64, 512]).
 // Each CTA loops over tiles with two shared-memory stages: while the FFT runs
 // on stage s, the TMA load of the next tile fills stage s^1; results leave by
 // TMA store.  One thread issues all copies; completion is tracked by one
@@ -693,7 +747,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
     int tile = live_from(blockIdx.x);
     if (leader && tile < ntiles) {
         mbar_expect_tx(&bar[0], bytes);
-        tma_load_3d(base, &tm, (tile % qtiles) * T, 0, tile / qtiles, &bar[0]);
+        tma_load_rows_3d(base, &tm, (tile % qtiles) * T, N, tile / qtiles, T * (int)sizeof(cpx<R>), &bar[0]);
     }
     const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[1].tw);
     for (int i = 0; tile < ntiles; ++i) {
@@ -702,7 +756,8 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
         if (leader && next < ntiles) {
             bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
             mbar_expect_tx(&bar[s ^ 1], bytes);
-            tma_load_3d(base + (s ^ 1) * per, &tm, (next % qtiles) * T, 0, next / qtiles, &bar[s ^ 1]);
+            tma_load_rows_3d(base + (s ^ 1) * per, &tm, (next % qtiles) * T, N, next / qtiles, T * (int)sizeof(cpx<R>),
+                             &bar[s ^ 1]);
         }
         const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -719,7 +774,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
         fence_proxy_async_smem();
         __syncthreads();
         if (leader) {
-            tma_store_3d(&tm, (tile % qtiles) * T, 0, tile / qtiles, buf);
+            tma_store_rows_3d(&tm, (tile % qtiles) * T, N, tile / qtiles, buf, T * (int)sizeof(cpx<R>));
             bulk_commit();
         }
         tile = next;
@@ -753,8 +808,8 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
     __syncthreads();
     auto issue = [&](int t, int s) {
         mbar_expect_tx(&bar[s], bytes);
-        tma_load_2d(base + s * per, &tin, NC * T * t, 0, &bar[s]);
-        if (dot) tma_load_2d(base + s * per + tile_elems, &tdot, NC * T * t, 0, &bar[s]);
+        tma_load_rows_2d(base + s * per, &tin, NC * T * t, 0, N, L * (int)sizeof(cpx<R>), &bar[s]);
+        if (dot) tma_load_rows_2d(base + s * per + tile_elems, &tdot, NC * T * t, 0, N, L * (int)sizeof(cpx<R>), &bar[s]);
     };
     int tile = blockIdx.x;
     if (leader && tile < ntiles) issue(tile, 0);
@@ -811,7 +866,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
         fence_proxy_async_smem();
         __syncthreads();
         if (leader) {
-            tma_store_2d(&tout, NC * T * tile, 0, buf);
+            tma_store_rows_2d(&tout, NC * T * tile, 0, N, buf, L * (int)sizeof(cpx<R>));
             bulk_commit();
         }
     }
@@ -949,7 +1004,7 @@ template <typename R, int NF>
 __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ spec, const cpx<R> *__restrict__ uk,
                                                 cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
                                                 cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x,
-                                                const MinresState *state, double *__restrict__ partials) {
+                                                const MinresState *state, double *__restrict__ partials, Fold fold) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
@@ -980,6 +1035,13 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
     }
     const double sum = block_sum(acc.value());
     if (threadIdx.x == 0) partials[blockIdx.x] = sum;   // = partials[cs * tpc + tc]
+    if (fold.cnt && last_of(fold.cnt + kNbMax + cs, tpc)) {   // Givens step of case cs
+        const double tot = sum_partials(partials + (size_t)cs * tpc, tpc);
+        if (threadIdx.x == 0) {
+            givens_step(fold.st + cs, tot);
+            fold.cnt[kNbMax + cs] = 0;
+        }
+    }
 }
 
 // persistent TMA-staged form (FP32, register FFT lengths 64..256, at most
@@ -996,7 +1058,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
                                                     const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
                                                     const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
                                                     cpx<R> *__restrict__ x, const MinresState *state,
-                                                    double *__restrict__ partials) {
+                                                    double *__restrict__ partials, Fold fold) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sacc[kNbMax * 192];
@@ -1025,7 +1087,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
     int tile = live_from(blockIdx.x);
     if (leader && tile < ntiles) {
         mbar_expect_tx(&bar[0], bytes);
-        tma_load_2d(base, &tspec, NC * T * (tile % tpc), N * (tile / tpc), &bar[0]);
+        tma_load_rows_2d(base, &tspec, NC * T * (tile % tpc), N * (tile / tpc), N, L * (int)sizeof(cpx<R>), &bar[0]);
     }
     for (int i = 0; tile < ntiles; ++i) {
         const int s = i & 1;
@@ -1033,7 +1095,8 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
         if (leader && next < ntiles) {
             bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
             mbar_expect_tx(&bar[s ^ 1], bytes);
-            tma_load_2d(base + (s ^ 1) * per, &tspec, NC * T * (next % tpc), N * (next / tpc), &bar[s ^ 1]);
+            tma_load_rows_2d(base + (s ^ 1) * per, &tspec, NC * T * (next % tpc), N * (next / tpc), N,
+                             L * (int)sizeof(cpx<R>), &bar[s ^ 1]);
         }
         const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -1055,7 +1118,7 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
         fence_proxy_async_smem();
         __syncthreads();
         if (leader) {
-            tma_store_2d(&tspec, NC * T * tc, N * cs, res);
+            tma_store_rows_2d(&tspec, NC * T * tc, N * cs, N, res, L * (int)sizeof(cpx<R>));
             bulk_commit();
         }
         tile = next;
@@ -1064,6 +1127,13 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
     for (int cc = 0; cc < g.nb; ++cc) {
         const double sum = block_sum(sacc[cc * blockDim.x + threadIdx.x]);
         if (threadIdx.x == 0) partials[cc * gridDim.x + blockIdx.x] = sum;
+    }
+    if (fold.cnt && last_of(fold.cnt + 2 * kNbMax, gridDim.x)) {   // Givens step of every case
+        for (int cc = 0; cc < g.nb; ++cc) {
+            const double tot = sum_partials(partials + (size_t)cc * gridDim.x, gridDim.x);
+            if (threadIdx.x == 0) givens_step(fold.st + cc, tot);
+        }
+        if (threadIdx.x == 0) fold.cnt[2 * kNbMax] = 0;
     }
 }
 
@@ -1304,7 +1374,7 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
     HOM_SET_ATTR1((k_x1_tma<R, NF>))      \
     HOM_SET_ATTR1((k_x1_lanczos_tma<R, NF>))
-        HOM_SET_TMA(64) HOM_SET_TMA(96) HOM_SET_TMA(128) HOM_SET_TMA(160) HOM_SET_TMA(256)
+        HOM_SET_TMA(64) HOM_SET_TMA(96) HOM_SET_TMA(128) HOM_SET_TMA(160) HOM_SET_TMA(256) HOM_SET_TMA(512)
 #undef HOM_SET_TMA
         HOM_SET_ATTR1((k_x3r<64>))
         HOM_SET_ATTR1((k_x3r<128>))
@@ -1334,6 +1404,7 @@ int Launch<R>::tma_grids(Geometry &g) {
             case 64: b2 = occ(k_x2_tma<R, -1, 64>, g.threads2, g.smem2_tma); break;
             case 96: b2 = occ(k_x2_tma<R, -1, 96>, g.threads2, g.smem2_tma); break;
             case 160: b2 = occ(k_x2_tma<R, -1, 160>, g.threads2, g.smem2_tma); break;
+            case 512: b2 = occ(k_x2_tma<R, -1, 512>, g.threads2, g.smem2_tma); break;
             case 128: b2 = occ(k_x2_tma<R, -1, 128>, g.threads2, g.smem2_tma); break;
             default: b2 = occ(k_x2_tma<R, -1, 256>, g.threads2, g.smem2_tma); break;
         }
@@ -1344,6 +1415,8 @@ int Launch<R>::tma_grids(Geometry &g) {
                      b1d = occ(k_x1_tma<R, 96>, g.threads1, g.smem1d_tma); break;
             case 160: b1 = occ(k_x1_tma<R, 160>, g.threads1, g.smem1_tma);
                       b1d = occ(k_x1_tma<R, 160>, g.threads1, g.smem1d_tma); break;
+            case 512: b1 = occ(k_x1_tma<R, 512>, g.threads1, g.smem1_tma);
+                      b1d = occ(k_x1_tma<R, 512>, g.threads1, g.smem1d_tma); break;
             case 128: b1 = occ(k_x1_tma<R, 128>, g.threads1, g.smem1_tma);
                       b1d = occ(k_x1_tma<R, 128>, g.threads1, g.smem1d_tma); break;
             default: b1 = occ(k_x1_tma<R, 256>, g.threads1, g.smem1_tma);
@@ -1360,6 +1433,7 @@ int Launch<R>::tma_grids(Geometry &g) {
                 case 64: b1l = occ(k_x1_lanczos_tma<R, 64>, g.threads1, g.smem1_tma); break;
                 case 96: b1l = occ(k_x1_lanczos_tma<R, 96>, g.threads1, g.smem1_tma); break;
                 case 160: b1l = occ(k_x1_lanczos_tma<R, 160>, g.threads1, g.smem1_tma); break;
+                case 512: b1l = occ(k_x1_lanczos_tma<R, 512>, g.threads1, g.smem1_tma); break;
                 case 128: b1l = occ(k_x1_lanczos_tma<R, 128>, g.threads1, g.smem1_tma); break;
                 default: b1l = occ(k_x1_lanczos_tma<R, 256>, g.threads1, g.smem1_tma); break;
             }
@@ -1375,7 +1449,7 @@ int Launch<R>::tma_grids(Geometry &g) {
 template <typename R>
 void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro, double scl, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart) {
+                   const MinresState *state, double *epart, Fold fold) {
     if constexpr (sizeof(R) == 4) {
         if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
@@ -1386,11 +1460,11 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
             float2 *fo = reinterpret_cast<float2 *>(out);
             switch (g.n3) {
                 case 64: k_x3r<64><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
-                                                          (const float *)phi, state, epart); break;
+                                                          (const float *)phi, state, epart, fold); break;
                 case 128: k_x3r<128><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
-                                                            (const float *)phi, state, epart); break;
+                                                            (const float *)phi, state, epart, fold); break;
                 default: k_x3r<256><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
-                                                            (const float *)phi, state, epart); break;
+                                                            (const float *)phi, state, epart, fold); break;
             }
             return;
         }
@@ -1402,10 +1476,10 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
         k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, nullptr);       \
+                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}); \
     else                                                                                                    \
         k_x3<R, NF, 3><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, epart)
+                                                            (R)scl, out_mode, out, phi, state, epart, fold)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }
@@ -1423,6 +1497,7 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
                 case 64: HOM_X2T(64); break;
                 case 96: HOM_X2T(96); break;
                 case 160: HOM_X2T(160); break;
+                case 512: HOM_X2T(512); break;
                 case 128: HOM_X2T(128); break;
                 default: HOM_X2T(256); break;
             }
@@ -1454,6 +1529,7 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
                 case 64: HOM_X1T(64); break;
                 case 96: HOM_X1T(96); break;
                 case 160: HOM_X1T(160); break;
+                case 512: HOM_X1T(512); break;
                 case 128: HOM_X1T(128); break;
                 default: HOM_X1T(256); break;
             }
@@ -1475,16 +1551,19 @@ int Launch<R>::x1_lanczos_grid(const Geometry &g) {
 
 template <typename R>
 void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
-                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials) {
+                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials,
+                           Fold fold) {
     if constexpr (sizeof(R) == 4) {
         if (g.tma && g.grid1l_tma > 0) {
             const CUtensorMap *ts = tma_map(g, spec, TMA_X1, 1);
 #define HOM_X1LT(NF)                                                                                         \
-    k_x1_lanczos_tma<R, NF><<<g.grid1l_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials)
+    k_x1_lanczos_tma<R, NF><<<g.grid1l_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials, \
+                                                                           fold)
             switch (g.fast[0]) {
                 case 64: HOM_X1LT(64); break;
                 case 96: HOM_X1LT(96); break;
                 case 160: HOM_X1LT(160); break;
+                case 512: HOM_X1LT(512); break;
                 case 128: HOM_X1LT(128); break;
                 default: HOM_X1LT(256); break;
             }
@@ -1493,7 +1572,8 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
         }
     }
     const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1 * g.nb;
-#define HOM_X1L(NF) k_x1_lanczos<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, spec, uk, um, wa, wb, x, state, partials)
+#define HOM_X1L(NF) \
+    k_x1_lanczos<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, spec, uk, um, wa, wb, x, state, partials, fold)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1L)
 #undef HOM_X1L
 }

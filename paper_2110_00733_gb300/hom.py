@@ -31,7 +31,7 @@ EXPORTED = [
     "hom_project", "hom_apply_spectrum", "hom_time_kernels", "hom_get_info", "hom_kernel_launches", "hom_destroy",
     "hom_last_error", "hom_apply_noalloc", "hom_modb_apply", "hom_modb_rhs", "hom_modb_precond",
     "hom_solve_batch", "hom_autotune", "hom_solve_mixed", "hom_pfs",
-    "hom_j2_begin", "hom_j2_increment", "hom_j2_state", "hom_j2_end",
+    "hom_j2_begin", "hom_j2_increment", "hom_j2_state", "hom_j2_end", "hom_j2_time_kernels",
 ]
 
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     lib.hom_project.argtypes = [vp, vp, vp]
     lib.hom_apply_spectrum.argtypes = [vp, vp, vp]
     lib.hom_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    lib.hom_j2_time_kernels.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
     lib.hom_apply_noalloc.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp, vp]
     lib.hom_modb_apply.argtypes = [vp, vp, vp]
     lib.hom_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
@@ -422,6 +423,16 @@ def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:
     n = _check(ctx.handle, load_library().hom_time_kernels(
         ctx.handle, int(reps), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 16))
     return {KERNEL_NAMES[i]: float(ms[i]) for i in range(n)}
+
+
+J2_KERNEL_NAMES = ["j2_return", "j2_tangent_apply", "x3_c2r_real", "x3_r2c_real"]
+
+
+def hom_j2_time_kernels(ctx: Context, reps: int = 20) -> dict:
+    ms = np.zeros(8)
+    n = _check(ctx.handle, load_library().hom_j2_time_kernels(
+        ctx.handle, int(reps), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 8))
+    return {J2_KERNEL_NAMES[i]: float(ms[i]) for i in range(n)}
 
 
 def hom_get_info(ctx: Context):

@@ -207,9 +207,10 @@ def test_solve_tma_octet_matches_oracle(hom):
 # Transform lengths of the 256^3 headline and of the 512^3 as-printed run:
 # length 256 on n3 (register engine, the headline's n3 pass) beside TMA-staged
 # n1/n2 passes of length 64; length 256 on the TMA-staged n1 pass; n1 = n2 =
-# 256 (both TMA-staged, as at 256^3); length 512 on n2 and on n1 (the plain-
-# load passes the 512^3 cell takes).
-LONG_SHAPES = [(64, 64, 256), (256, 64, 64), (256, 256, 8), (8, 512, 8), (512, 8, 16)]
+# 256 (both TMA-staged, as at 256^3); length 512 on n2 and on n1 in plain-
+# load passes (the other axis short) and in TMA-staged ones (the other axis
+# 64), as the 512^3 cell takes them.
+LONG_SHAPES = [(64, 64, 256), (256, 64, 64), (256, 256, 8), (8, 512, 8), (512, 8, 16), (512, 64, 8), (64, 512, 8)]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -315,3 +316,18 @@ def test_solve_octet256_headline_matches_stored_oracle(hom):
         err = np.max(np.abs(np.array(info[0]["sigma_mean"]) - ref)) / np.max(np.abs(ref))
         assert err <= 1e-4, err
         assert info[0]["true_residual"] <= 1e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_laminate_512_axis(hom, prec):
+    """Layered cell with n1 = 512 and n2 = 64: the MINRES solve through the
+    TMA-staged n1 pass of length 512 (two 256-row boxes per tile) in FP32,
+    against the exact laminate closed form."""
+    from test_oracle_solver import laminate_closed_form
+    phi = ri.laminate((512, 64, 8), (256, 128, 128), (1.0, 0.2, 0.55), axis=0)
+    with make(hom, phi, prec) as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-9, max_it=500)
+        assert rc == hom.HOM_OK
+        for J in range(6):
+            ref = laminate_closed_form([1.0, 0.2, 0.55], [0.5, 0.25, 0.25], np.eye(6)[J])
+            assert np.allclose(info[J]["sigma_mean"], ref, rtol=1e-5, atol=1e-5 * E_M)
