@@ -396,25 +396,12 @@ static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool
     Launch<R>::x2(E.g, s, 1, E.spec, st);
     if (ctx->tangent_op) {
         // A_i v = G F (C^{i-1}(x) : F^-1 G v), eq. (galnonlin): the point-wise
-        // 6x6 tangent between an inverse and a forward n3 pass
-        R *tin, *tout;
-        if constexpr (std::is_same<R, double>::value) {
-            tin = ctx->j2.sig; tout = ctx->j2.de;
-        } else {
-            tin = ctx->j2.sig32; tout = ctx->j2.de32;
-        }
-        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL, tin,
-                      E.phi, st);
-        // FP64 operator of FP32 fields (their true residual): the FP32 tangent in FP64 arithmetic
-        if constexpr (std::is_same<R, double>::value) {
-            if (ctx->j2.Ct) j2_tangent_apply<double, double>(ctx->V, ctx->j2.Ct, tin, tout, s);
-            else j2_tangent_apply<float, double>(ctx->V, ctx->j2.Ct32, tin, tout, s);
-        } else {
-            j2_tangent_apply<float, float>(ctx->V, ctx->j2.Ct32, tin, tout, s);
-        }
-        Launch<R>::x3(E.g, s, X3_IN_REAL, tout, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
-                      E.phi, st);
-        ctx->launches += 2;
+        // 6x6 tangent applied between the n3 C2R and R2C, in place of the
+        // elastic law (an FP64 operator of FP32 fields, their true residual,
+        // takes the FP32 tangent in FP64 arithmetic)
+        X3Tan tan{ctx->j2.Ct ? (const void *)ctx->j2.Ct : (const void *)ctx->j2.Ct32, ctx->j2.Ct ? 1 : 0};
+        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_TANGENT, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
+                      E.phi, st, nullptr, Fold{}, tan);
     } else {
         Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
                       E.spec, E.phi, st);
@@ -2892,8 +2879,10 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
 // the context's stream between two CUDA events, at the current iterate:
 // ms[0] radial return with the consistent tangent (k_j2_return, tangent in
 // the operator's precision), ms[1] tangent application y = C_t : x
-// (k_j2_tangent_apply, in the operator's precision), ms[2] the tangent
-// operator's n3 C2R pass to a real field, ms[3] its n3 R2C pass from one.
+// (k_j2_tangent_apply, in the operator's precision), ms[2] and ms[3] the n3
+// C2R pass to a real field and the R2C pass from one (the unfused form of
+// the tangent operator's n3 stage), ms[4] the tangent operator's n3 pass
+// with the tangent applied between C2R and R2C, as the solve runs it.
 template <typename R>
 static int j2_time_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
     J2State &j = ctx->j2;
@@ -2904,13 +2893,18 @@ static int j2_time_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nm
     } else {
         tin = j.sig32; tout = j.de32;
     }
-    const int nk = 4;
+    const X3Tan tan{j.Ct ? (const void *)j.Ct : (const void *)j.Ct32, j.Ct ? 1 : 0};
+    const int nk = 5;
     for (int k = 0; k < nk && k < nmax; ++k) {
         for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
             const int r = pass ? reps : 1;
             CU(cudaEventRecord(ctx->ev0, s));
             for (int i = 0; i < r; ++i) {
                 switch (k) {
+                    case 4:
+                        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_TANGENT, ctx->lam, ctx->mu, nullptr, 1.0,
+                                      X3_OUT_SPEC, E.spec, E.phi, nullptr, nullptr, Fold{}, tan);
+                        break;
                     case 0:
                         if (j.Ct) j2_return<double>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct, 0, s);
                         else j2_return<float>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct32, 0, s);

@@ -174,7 +174,14 @@ void tma_cache_free(void *cache);
 // n3 pass (x3): input, middle and output stages
 enum X3In { X3_IN_SPEC = 0, X3_IN_REAL = 1, X3_IN_MACRO = 2 };
 enum X3Mid { X3_MID_NONE = 0, X3_MID_MATERIAL = 1,
-             X3_MID_MODB = 2 };   // 10 components: tau = phi C_m eps (0-5), chi_v g (6-8), 0 (9)
+             X3_MID_MODB = 2,     // 10 components: tau = phi C_m eps (0-5), chi_v g (6-8), 0 (9)
+             X3_MID_TANGENT = 3 };   // tau = C_t(x) : eps, a per-voxel 6x6 tangent (X3Tan)
+// the per-voxel tangent of X3_MID_TANGENT: entry (i, j) of voxel v at
+// ct[(6 i + j) V + v], float or double (f64), Mandel, phi included
+struct X3Tan {
+    const void *ct;
+    int f64;
+};
 enum X3Out { X3_OUT_SPEC = 0, X3_OUT_REAL = 1 };
 // n1 pass (x1) flags
 enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
@@ -208,7 +215,8 @@ template <typename R> struct Launch {
     // fold: the alpha step folded into the pass (see Fold in hom_passes.cuh)
     static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{});
+                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{},
+                   X3Tan tan = X3Tan{});
     // n2 pass, in place on the half spectrum
     static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
     // n1 pass: in -> out (may alias), optional projector before / after, and

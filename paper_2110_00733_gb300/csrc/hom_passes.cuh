@@ -272,7 +272,7 @@ template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
-                                        double *__restrict__ epart, Fold fold) {
+                                        double *__restrict__ epart, Fold fold, X3Tan tan) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
     // stride by ES across a warp and stay free of bank conflicts; the fast
@@ -375,6 +375,26 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
                     t[8] *= chi;
                     t[9] = 0;
                 }
+            }
+            if (mid == X3_MID_TANGENT) {
+                // the consistent tangent of the J2 extension, eq. (galnonlin):
+                // y_i = sum_j C_t,ij(x) e_j, in R arithmetic
+                const size_t v = (size_t)vbase + e;
+                R y[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    R acc = 0;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        const size_t o = (size_t)(6 * i + j) * (size_t)V + v;
+                        const R c = tan.f64 ? (R)__ldg(reinterpret_cast<const double *>(tan.ct) + o)
+                                            : (R)__ldg(reinterpret_cast<const float *>(tan.ct) + o);
+                        acc += c * t[j];
+                    }
+                    y[i] = acc;
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) t[c] = y[c];
             }
             if (out_mode == X3_OUT_REAL) {
                 R *real = reinterpret_cast<R *>(out_);
@@ -1449,7 +1469,7 @@ int Launch<R>::tma_grids(Geometry &g) {
 template <typename R>
 void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro, double scl, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart, Fold fold) {
+                   const MinresState *state, double *epart, Fold fold, X3Tan tan) {
     if constexpr (sizeof(R) == 4) {
         if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
@@ -1476,10 +1496,10 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
         k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}); \
+                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}, tan); \
     else                                                                                                    \
         k_x3<R, NF, 3><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, epart, fold)
+                                                            (R)scl, out_mode, out, phi, state, epart, fold, tan)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }

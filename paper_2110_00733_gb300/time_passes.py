@@ -78,7 +78,7 @@ def write_traffic(csv_path, shape):
         scale = {"byte": 1e-6, "Kbyte": 1e-3, "Mbyte": 1.0, "Gbyte": 1e3}.get(r[ui], 1.0)
         if r[mi].startswith("dram__bytes"):
             d[r[mi]] = float(r[vi].replace(",", "")) * scale
-    seq = [launches[k] for k in sorted(launches) if "double" not in launches[k]["name"]]
+    seq = [launches[k] for k in sorted(launches) if "<double" not in launches[k]["name"]]
     # the first launch of each kernel of the step (hom_time_kernels launches
     # each twice: warm-up, then --reps 1); FP64 launches of context creation
     # and the first inverse n1 pass are skipped
