@@ -600,8 +600,9 @@ def run_j2(args):
     best = min(ok, key=lambda k: out[k]["ms_total"]) if ok else "fp64"
     out["value"] = out[best]["voxel_iters_per_s"]
     out["value_from"] = best
-    # roofline of the tangent operator's n3 pass (the J2 kernel inside every
-    # MINRES iteration: C2R, the tangent, R2C).  At 64^3 the
+    # roofline of the tangent application (the J2 kernel inside every MINRES
+    # iteration): algorithmic bytes = the 36-entry tangent, the input and the
+    # output strain per voxel, in the operator's precision.  At 64^3 the
     # tangent (38 MB in FP32) stays in L2 between back-to-back launches, so
     # the kernels are timed on a 128^3 cell (302 MB of tangent, larger than
     # L2), on its virgin state (an elastic return at every voxel)
@@ -613,14 +614,12 @@ def run_j2(args):
         hom.hom_j2_begin(ctx, sy, H)
         kms = hom.hom_j2_time_kernels(ctx, reps=20)
     w = 4 if best == "fp32_fields" else 8
-    # the tangent operator's n3 pass: the half spectrum in and out plus the
-    # 36-entry tangent per voxel
-    b_x3t = 2 * (2 * w) * 6 * (nt // 2 + 1) / nt + 36 * w
+    b_apply = (36 + 12) * w                          # tangent, input and output strain
     b_return = 8 * (6 + 6 + 1 + 6) + 36 * w + 8     # eps, epsp, alpha, sig (FP64), tangent, phi
-    ach = b_x3t * nt ** 3 / (kms["x3_tangent"] * 1e-3) / 1e9
-    out["roofline"] = {"bound": "hbm", "kernel": "x3_tangent", "grid": [nt] * 3, "achieved": ach, "peak": peak,
+    ach = b_apply * nt ** 3 / (kms["j2_tangent_apply"] * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "j2_tangent_apply", "grid": [nt] * 3, "achieved": ach, "peak": peak,
                        "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                       "bytes_per_voxel": b_x3t, "kernel_ms": kms,
+                       "bytes_per_voxel": b_apply, "kernel_ms": kms,
                        "j2_return": {"bytes_per_voxel": b_return, "ms": kms["j2_return"],
                                      "achieved_gbs": b_return * nt ** 3 / (kms["j2_return"] * 1e-3) / 1e9}}
     out["dtype"] = "f32" if best == "fp32_fields" else "f64"

@@ -49,6 +49,10 @@
  *     negative error, in which case no output buffer has been written;
  *     hom_last_error() then describes the failure.
  *   - A context is not thread-safe: one host thread at a time.
+ *   - The kernels of a MINRES sweep's graph use programmatic dependent
+ *     launch (each starts while its predecessor drains and waits for it
+ *     before touching memory); HOM_PDL=0 in the environment at hom_create
+ *     turns that off.
  */
 #ifndef HOM_H
 #define HOM_H
@@ -337,11 +341,8 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
  * (an instrument for roofline measurements; hom_j2_begin first; it changes no
  * state a later increment reads).  ms[0] radial return with the consistent
  * tangent at every voxel, ms[1] tangent application C_t : x at every voxel,
- * ms[2] and ms[3] an n3 C2R pass to a real field and an R2C pass from one
- * (the unfused form of the tangent operator's n3 stage), ms[4] the tangent
- * operator's n3 pass with the tangent applied between its C2R and R2C, as
- * the Newton systems' MINRES runs it.  Returns the number of entries written
- * (<= nmax). */
+ * ms[2] and ms[3] the tangent operator's n3 passes (C2R to a real field,
+ * R2C from one).  Returns the number of entries written (<= nmax). */
 int hom_j2_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* A(eps) of hom_apply for a small cell, allocating no device memory.  The

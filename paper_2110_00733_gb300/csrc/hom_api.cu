@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -142,6 +143,7 @@ struct hom_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // graph is a device-side WHILE loop over the body
     bool host_loop = false;          // asked for the host-replayed body
+    int pdl = 1;                     // programmatic launches inside the stacked MINRES graph
     bool tangent_op = false;         // operator of eq. (galnonlin) with the J2 tangent (FP64)
     bool graph_tangent = false;      // the captured graph applies the tangent operator
     J2State j2;
@@ -396,12 +398,27 @@ static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool
     Launch<R>::x2(E.g, s, 1, E.spec, st);
     if (ctx->tangent_op) {
         // A_i v = G F (C^{i-1}(x) : F^-1 G v), eq. (galnonlin): the point-wise
-        // 6x6 tangent applied between the n3 C2R and R2C, in place of the
-        // elastic law (an FP64 operator of FP32 fields, their true residual,
-        // takes the FP32 tangent in FP64 arithmetic)
-        X3Tan tan{ctx->j2.Ct ? (const void *)ctx->j2.Ct : (const void *)ctx->j2.Ct32, ctx->j2.Ct ? 1 : 0};
-        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_TANGENT, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
-                      E.phi, st, nullptr, Fold{}, tan);
+        // 6x6 tangent between an inverse and a forward n3 pass (applying it
+        // inside the n3 pass was measured slower: 0.199 against 0.152 ms at
+        // 128^3, the pass's small CTAs do not stream the 36-entry tangent)
+        R *tin, *tout;
+        if constexpr (std::is_same<R, double>::value) {
+            tin = ctx->j2.sig; tout = ctx->j2.de;
+        } else {
+            tin = ctx->j2.sig32; tout = ctx->j2.de32;
+        }
+        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_REAL, tin,
+                      E.phi, st);
+        // FP64 operator of FP32 fields (their true residual): the FP32 tangent in FP64 arithmetic
+        if constexpr (std::is_same<R, double>::value) {
+            if (ctx->j2.Ct) j2_tangent_apply<double, double>(ctx->V, ctx->j2.Ct, tin, tout, s);
+            else j2_tangent_apply<float, double>(ctx->V, ctx->j2.Ct32, tin, tout, s);
+        } else {
+            j2_tangent_apply<float, float>(ctx->V, ctx->j2.Ct32, tin, tout, s);
+        }
+        Launch<R>::x3(E.g, s, X3_IN_REAL, tout, X3_MID_NONE, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec,
+                      E.phi, st);
+        ctx->launches += 2;
     } else {
         Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
                       E.spec, E.phi, st);
@@ -926,6 +943,10 @@ void hom_destroy(hom_ctx *ctx) {
 }
 
 static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int input_kind) {
+    {   // HOM_PDL=0 in the environment: ordinary launches in the MINRES graph
+        const char *e = std::getenv("HOM_PDL");
+        ctx->pdl = (e && e[0] == '0') ? 0 : 1;
+    }
     for (int p = 0; p < 3; ++p) {
         AxisPlan tmp{};
         if (grid[p] < 2 || grid[p] > 512 || !factor_radices(grid[p], tmp))
@@ -1358,7 +1379,7 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
         Launch<R>::x2(g, s, 1, spec, ctx->d_bst);
         Launch<R>::x3(g, s, X3_IN_SPEC, spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, spec,
                       E.phi, ctx->d_bst, ctx->bpart, fold3);
-        if (!fold3.cnt) scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, g.nb);
+        if (!fold3.cnt) scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, g.nb, g.pdl);
         Launch<R>::x2(g, s, 0, spec, ctx->d_bst);
         Launch<R>::x1_lanczos(g, s, spec, uk, um, wa, wb, x, ctx->d_bst, ctx->bpart, fold);
         ctx->launches += fold3.cnt ? 4 : 5;
@@ -1381,6 +1402,7 @@ static void set_bgeom(hom_ctx *ctx, Engine<R> &E, int nb) {
     ctx->bg = E.g;
     ctx->bg.nb = nb;
     ctx->bg.tma_cache = ctx->btma;
+    ctx->bg.pdl = ctx->pdl;
 }
 
 template <typename R>
@@ -2879,10 +2901,8 @@ int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax) {
 // the context's stream between two CUDA events, at the current iterate:
 // ms[0] radial return with the consistent tangent (k_j2_return, tangent in
 // the operator's precision), ms[1] tangent application y = C_t : x
-// (k_j2_tangent_apply, in the operator's precision), ms[2] and ms[3] the n3
-// C2R pass to a real field and the R2C pass from one (the unfused form of
-// the tangent operator's n3 stage), ms[4] the tangent operator's n3 pass
-// with the tangent applied between C2R and R2C, as the solve runs it.
+// (k_j2_tangent_apply, in the operator's precision), ms[2] the tangent
+// operator's n3 C2R pass to a real field, ms[3] its n3 R2C pass from one.
 template <typename R>
 static int j2_time_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nmax) {
     J2State &j = ctx->j2;
@@ -2893,18 +2913,13 @@ static int j2_time_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, int nm
     } else {
         tin = j.sig32; tout = j.de32;
     }
-    const X3Tan tan{j.Ct ? (const void *)j.Ct : (const void *)j.Ct32, j.Ct ? 1 : 0};
-    const int nk = 5;
+    const int nk = 4;
     for (int k = 0; k < nk && k < nmax; ++k) {
         for (int pass = 0; pass < 2; ++pass) {       // pass 0 warms up
             const int r = pass ? reps : 1;
             CU(cudaEventRecord(ctx->ev0, s));
             for (int i = 0; i < r; ++i) {
                 switch (k) {
-                    case 4:
-                        Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_TANGENT, ctx->lam, ctx->mu, nullptr, 1.0,
-                                      X3_OUT_SPEC, E.spec, E.phi, nullptr, nullptr, Fold{}, tan);
-                        break;
                     case 0:
                         if (j.Ct) j2_return<double>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct, 0, s);
                         else j2_return<float>(ctx->V, j.mat, ctx->e64.phi, j.eps, j.epsp, j.alpha, j.sig, j.Ct32, 0, s);

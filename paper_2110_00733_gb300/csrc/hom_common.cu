@@ -81,6 +81,8 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
 // alpha_k = <v_k, A v_k> = <u_k, A u_k> / beta_k^2; the partials sum to
 // <u_k, A u_k> / scale (scale = V for the strain-energy sums of the n3 pass)
 __global__ void k_scalar_alpha(MinresState *st, const double *partials, int np, double scale) {
+    pdl_release();
+    pdl_wait();                    // the n3 pass's partials (programmatic launch in the MINRES graph)
     st += blockIdx.x;              // load case of a stacked batch (one CTA each)
     partials += (size_t)blockIdx.x * np;
     if (st->done) return;
@@ -416,8 +418,8 @@ void scalar_start(cudaStream_t st, MinresState *s, const double *partials, int n
 void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s, int nb) {
     k_loop_cond<<<1, 32, 0, st>>>(h, s, nb);
 }
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale, int nb) {
-    k_scalar_alpha<<<nb, 1024, 0, st>>>(s, partials, np, scale);
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale, int nb, int pdl) {
+    launch_k(pdl, k_scalar_alpha, nb, 1024, 0, st, s, partials, np, scale);
 }
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np, int nb) {
     k_scalar_givens<<<nb, 1024, 0, st>>>(s, partials, np);

@@ -133,6 +133,10 @@ struct Geometry {
     // spectrum nb x n1 x n2 x h x nc, Krylov vectors nb blocks of kvec, one
     // MinresState per case); 1 everywhere else
     int nb = 1;
+    // nonzero: the MINRES passes launch with programmatic stream serialization
+    // (set for the stacked graph's body; the kernels wait on their
+    // predecessor with griddepcontrol before touching memory)
+    int pdl = 0;
     int mask0;              // stress-controlled Mandel components (bit c): the projector keeps them at xi = 0
     // persistent TMA-staged n2 / n1 passes (FP32, register-FFT n in [64, 512]):
     // enabled flag, persistent grid sizes, shared memory, host-side cache of
@@ -162,6 +166,27 @@ __host__ __device__ constexpr size_t x3r_smem(int n) {
     return (size_t)x3r_rows(n) * 3 * (n == 64 ? 8 * 9 : (n == 128 ? 16 * 9 : 16 * 17)) * sizeof(float2);
 }
 
+// A kernel launch, with programmatic stream serialization when pdl != 0.
+template <typename... KArgs, typename... Args>
+inline void launch_k(int pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+    if (!pdl) {
+        k<<<grid, block, smem, st>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // tensor-map kinds of the TMA passes
 enum TmaKind { TMA_X2 = 0, TMA_X1 = 1 };
 // Host: the cached tensor map of `ptr` (a half spectrum of this geometry) for
@@ -174,14 +199,7 @@ void tma_cache_free(void *cache);
 // n3 pass (x3): input, middle and output stages
 enum X3In { X3_IN_SPEC = 0, X3_IN_REAL = 1, X3_IN_MACRO = 2 };
 enum X3Mid { X3_MID_NONE = 0, X3_MID_MATERIAL = 1,
-             X3_MID_MODB = 2,     // 10 components: tau = phi C_m eps (0-5), chi_v g (6-8), 0 (9)
-             X3_MID_TANGENT = 3 };   // tau = C_t(x) : eps, a per-voxel 6x6 tangent (X3Tan)
-// the per-voxel tangent of X3_MID_TANGENT: entry (i, j) of voxel v at
-// ct[(6 i + j) V + v], float or double (f64), Mandel, phi included
-struct X3Tan {
-    const void *ct;
-    int f64;
-};
+             X3_MID_MODB = 2 };   // 10 components: tau = phi C_m eps (0-5), chi_v g (6-8), 0 (9)
 enum X3Out { X3_OUT_SPEC = 0, X3_OUT_REAL = 1 };
 // n1 pass (x1) flags
 enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
@@ -215,8 +233,7 @@ template <typename R> struct Launch {
     // fold: the alpha step folded into the pass (see Fold in hom_passes.cuh)
     static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{},
-                   X3Tan tan = X3Tan{});
+                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{});
     // n2 pass, in place on the half spectrum
     static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
     // n1 pass: in -> out (may alias), optional projector before / after, and
@@ -312,7 +329,8 @@ void loop_cond(cudaStream_t st, cudaGraphConditionalHandle h, MinresState *s, in
 // alpha_k from partials summing to <u_k, A^ u_k> / scale.  The scalar
 // kernels of a stacked batch run one CTA per case c, on s[c] and the
 // partials at c * np.
-void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale = 1.0, int nb = 1);
+void scalar_alpha(cudaStream_t st, MinresState *s, const double *partials, int np, double scale = 1.0, int nb = 1,
+                  int pdl = 0);
 void scalar_givens(cudaStream_t st, MinresState *s, const double *partials, int np, int nb = 1);
 // PCG scalars (MoDBFFT): start from <r0,z0>, ||r0||^2; step length; direction
 void scalar_cg_start(cudaStream_t st, CgState *s, const double *partials, int np, double tol, int max_it);

@@ -272,7 +272,9 @@ template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
-                                        double *__restrict__ epart, Fold fold, X3Tan tan) {
+                                        double *__restrict__ epart, Fold fold) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // element stride ES = L rounded up to odd: the per-element phases below
     // stride by ES across a warp and stay free of bank conflicts; the fast
@@ -376,26 +378,6 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
                     t[9] = 0;
                 }
             }
-            if (mid == X3_MID_TANGENT) {
-                // the consistent tangent of the J2 extension, eq. (galnonlin):
-                // y_i = sum_j C_t,ij(x) e_j, in R arithmetic
-                const size_t v = (size_t)vbase + e;
-                R y[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    R acc = 0;
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) {
-                        const size_t o = (size_t)(6 * i + j) * (size_t)V + v;
-                        const R c = tan.f64 ? (R)__ldg(reinterpret_cast<const double *>(tan.ct) + o)
-                                            : (R)__ldg(reinterpret_cast<const float *>(tan.ct) + o);
-                        acc += c * t[j];
-                    }
-                    y[i] = acc;
-                }
-#pragma unroll
-                for (int c = 0; c < 6; ++c) t[c] = y[c];
-            }
             if (out_mode == X3_OUT_REAL) {
                 R *real = reinterpret_cast<R *>(out_);
 #pragma unroll
@@ -489,6 +471,8 @@ template <int N>
 __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
                                                 int material, float lam, float mu2, const float *__restrict__ phi,
                                                 const MinresState *state, double *__restrict__ epart, Fold fold) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     using PL = X3RPlan<N>;
     constexpr int P = PL::P, Q = PL::Q, ROWS = PL::ROWS, H = N / 2 + 1, NC = 6;
     constexpr int TS = Q * (P + 1);   // one line's transpose slab
@@ -631,6 +615,8 @@ __global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const 
 // ---------------------------------------------------------------------------
 template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2(Geometry g, cpx<R> *__restrict__ spec, const MinresState *state) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = g.n2, T = g.tile2, H6 = g.nc * g.h;
     cpx<R> *buf = reinterpret_cast<cpx<R> *>(smem_raw);
@@ -744,6 +730,8 @@ __device__ __forceinline__ void tma_store_rows_2d(const CUtensorMap *tm, int x, 
 template <typename R, int S, int NF>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_constant__ CUtensorMap tm, int qtiles,
                                             const MinresState *state) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     const int N = g.n2, T = g.tile2;
@@ -1025,6 +1013,8 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
                                                 cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
                                                 cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x,
                                                 const MinresState *state, double *__restrict__ partials, Fold fold) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
@@ -1079,6 +1069,8 @@ __global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __g
                                                     const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
                                                     cpx<R> *__restrict__ x, const MinresState *state,
                                                     double *__restrict__ partials, Fold fold) {
+    pdl_release();
+    pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sacc[kNbMax * 192];
@@ -1469,7 +1461,7 @@ int Launch<R>::tma_grids(Geometry &g) {
 template <typename R>
 void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro, double scl, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart, Fold fold, X3Tan tan) {
+                   const MinresState *state, double *epart, Fold fold) {
     if constexpr (sizeof(R) == 4) {
         if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
@@ -1479,11 +1471,11 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
             const float2 *fi = reinterpret_cast<const float2 *>(in);
             float2 *fo = reinterpret_cast<float2 *>(out);
             switch (g.n3) {
-                case 64: k_x3r<64><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                case 64: launch_k(g.pdl, k_x3r<64>, grid, 128, sm, st, g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
                                                           (const float *)phi, state, epart, fold); break;
-                case 128: k_x3r<128><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                case 128: launch_k(g.pdl, k_x3r<128>, grid, 128, sm, st, g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
                                                             (const float *)phi, state, epart, fold); break;
-                default: k_x3r<256><<<grid, 128, sm, st>>>(g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
+                default: launch_k(g.pdl, k_x3r<256>, grid, 128, sm, st, g, fi, fo, mat, (float)lam, (float)(2.0 * mu),
                                                             (const float *)phi, state, epart, fold); break;
             }
             return;
@@ -1495,11 +1487,11 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
     const int grid = x3_grid(g) * g.nb;
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
-        k_x3<R, NF, 5><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}, tan); \
+        launch_k(g.pdl, k_x3<R, NF, 5>, grid, g.threads3, g.smem3, st, g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, \
+                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}); \
     else                                                                                                    \
-        k_x3<R, NF, 3><<<grid, g.threads3, g.smem3, st>>>(g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m,       \
-                                                            (R)scl, out_mode, out, phi, state, epart, fold, tan)
+        launch_k(g.pdl, k_x3<R, NF, 3>, grid, g.threads3, g.smem3, st, g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, \
+                                                            (R)scl, out_mode, out, phi, state, epart, fold)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }
@@ -1511,8 +1503,8 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
             const CUtensorMap *tm = tma_map(g, spec, TMA_X2, 1);
             const int qtiles = (g.nc * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2T(NF)                                                                                         \
-    if (inverse) k_x2_tma<R, 1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state);    \
-    else k_x2_tma<R, -1, NF><<<g.grid2_tma, g.threads2, g.smem2_tma, st>>>(g, *tm, qtiles, state)
+    if (inverse) launch_k(g.pdl, k_x2_tma<R, 1, NF>, g.grid2_tma, g.threads2, g.smem2_tma, st, g, *tm, qtiles, state); \
+    else launch_k(g.pdl, k_x2_tma<R, -1, NF>, g.grid2_tma, g.threads2, g.smem2_tma, st, g, *tm, qtiles, state)
             switch (g.fast[1]) {
                 case 64: HOM_X2T(64); break;
                 case 96: HOM_X2T(96); break;
@@ -1527,8 +1519,8 @@ void Launch<R>::x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec
     }
     const int grid = (g.n1 * g.nb * g.nc * g.h + g.tile2 - 1) / g.tile2;
 #define HOM_X2(NF)                                                                  \
-    if (inverse) k_x2<R, 1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state); \
-    else k_x2<R, -1, NF><<<grid, g.threads2, g.smem2, st>>>(g, spec, state)
+    if (inverse) launch_k(g.pdl, k_x2<R, 1, NF>, grid, g.threads2, g.smem2, st, g, spec, state); \
+    else launch_k(g.pdl, k_x2<R, -1, NF>, grid, g.threads2, g.smem2, st, g, spec, state)
     HOM_FAST_SWITCH(g.fast[1], HOM_X2)
 #undef HOM_X2
 }
@@ -1577,7 +1569,8 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
         if (g.tma && g.grid1l_tma > 0) {
             const CUtensorMap *ts = tma_map(g, spec, TMA_X1, 1);
 #define HOM_X1LT(NF)                                                                                         \
-    k_x1_lanczos_tma<R, NF><<<g.grid1l_tma, g.threads1, g.smem1_tma, st>>>(g, *ts, uk, um, wa, wb, x, state, partials, \
+    launch_k(g.pdl, k_x1_lanczos_tma<R, NF>, g.grid1l_tma, g.threads1, g.smem1_tma, st, g, *ts, uk, um, wa, wb, x, state, \
+             partials, \
                                                                            fold)
             switch (g.fast[0]) {
                 case 64: HOM_X1LT(64); break;
@@ -1593,7 +1586,7 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
     }
     const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1 * g.nb;
 #define HOM_X1L(NF) \
-    k_x1_lanczos<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, spec, uk, um, wa, wb, x, state, partials, fold)
+    launch_k(g.pdl, k_x1_lanczos<R, NF>, grid, g.threads1, g.smem1, st, g, spec, uk, um, wa, wb, x, state, partials, fold)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1L)
 #undef HOM_X1L
 }

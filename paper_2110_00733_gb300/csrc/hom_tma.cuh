@@ -78,6 +78,15 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, int x, int y
                  : "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor's last CTAs still run;
+// pdl_wait() blocks until the predecessor has completed and its memory is
+// visible (a no-op for an ordinary launch), pdl_release() lets the
+// successor launch early.  A kernel that calls pdl_release() first and
+// pdl_wait() before touching any global memory is safe either way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // the shared-memory sources of all committed bulk stores have been read
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

@@ -425,7 +425,7 @@ def hom_time_kernels(ctx: Context, reps: int = 20) -> dict:
     return {KERNEL_NAMES[i]: float(ms[i]) for i in range(n)}
 
 
-J2_KERNEL_NAMES = ["j2_return", "j2_tangent_apply", "x3_c2r_real", "x3_r2c_real", "x3_tangent"]
+J2_KERNEL_NAMES = ["j2_return", "j2_tangent_apply", "x3_c2r_real", "x3_r2c_real"]
 
 
 def hom_j2_time_kernels(ctx: Context, reps: int = 20) -> dict:
