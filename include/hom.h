@@ -49,10 +49,10 @@
  *     negative error, in which case no output buffer has been written;
  *     hom_last_error() then describes the failure.
  *   - A context is not thread-safe: one host thread at a time.
- *   - The kernels of a MINRES sweep's graph use programmatic dependent
- *     launch (each starts while its predecessor drains and waits for it
- *     before touching memory); HOM_PDL=0 in the environment at hom_create
- *     turns that off.
+ *   - HOM_PDL=1 in the environment at hom_create makes the kernels of a
+ *     MINRES sweep's graph use programmatic dependent launch (each starts
+ *     while its predecessor drains and waits for it before touching
+ *     memory); off by default, where it measured slower.
  */
 #ifndef HOM_H
 #define HOM_H
