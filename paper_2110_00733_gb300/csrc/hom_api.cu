@@ -155,7 +155,7 @@ struct hom_ctx {
     Geometry bg{};
     void *btma = nullptr;
     void *bspec = nullptr;                       // bcap x 6S, solve precision
-    void *bv[2] = {nullptr, nullptr};            // bcap x kvec each (n1-tile order)
+    void *bv[3] = {nullptr, nullptr, nullptr};   // bcap x kvec each (n1-tile order): u_k in bv[k mod 3]
     void *bw[2] = {nullptr, nullptr};
     void *bx = nullptr;
     void *brhs = nullptr;                        // bcap x 6S: right-hand sides, then iterates
@@ -607,7 +607,7 @@ static int run_minres(hom_ctx *ctx, Engine<R> &E, double tol, int max_it, int *i
         }
     }
     // the last step's lagged w / x update
-    Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], (cpx<R> *)ctx->wbuf[0],
+    Launch<R>::minres_flush(E.g, s, (const cpx<R> *)ctx->vbuf[0], (const cpx<R> *)ctx->vbuf[1], nullptr, (cpx<R> *)ctx->wbuf[0],
                             (cpx<R> *)ctx->wbuf[1], (cpx<R> *)ctx->xs, ctx->d_state, 6 * ctx->S);
     ctx->launches += 1;
     *iters = ctx->h_state->k;
@@ -1280,7 +1280,7 @@ static void batch_free(hom_ctx *ctx) {
     ctx->bgraph_nb = 0;
     tma_cache_free(ctx->btma);
     ctx->btma = nullptr;
-    for (void *p : {ctx->bspec, ctx->bv[0], ctx->bv[1], ctx->bw[0], ctx->bw[1], ctx->bx, ctx->brhs}) cudaFree(p);
+    for (void *p : {ctx->bspec, ctx->bv[0], ctx->bv[1], ctx->bv[2], ctx->bw[0], ctx->bw[1], ctx->bx, ctx->brhs}) cudaFree(p);
     cudaFree(ctx->bb64);
     cudaFree(ctx->br64);
     cudaFree(ctx->d_bst);
@@ -1288,7 +1288,7 @@ static void batch_free(hom_ctx *ctx) {
     cudaFree(ctx->bcnt);
     ctx->bcnt = nullptr;
     if (ctx->h_bst) cudaFreeHost(ctx->h_bst);
-    ctx->bspec = ctx->bv[0] = ctx->bv[1] = ctx->bw[0] = ctx->bw[1] = ctx->bx = ctx->brhs = nullptr;
+    ctx->bspec = ctx->bv[0] = ctx->bv[1] = ctx->bv[2] = ctx->bw[0] = ctx->bw[1] = ctx->bx = ctx->brhs = nullptr;
     ctx->bb64 = ctx->br64 = nullptr;
     ctx->d_bst = ctx->h_bst = nullptr;
     ctx->bpart = nullptr;
@@ -1302,7 +1302,7 @@ static long long batch_case_bytes(const hom_ctx *ctx) {
     const bool f64 = ctx->prec == HOM_PREC_FP64;
     const long long cs = f64 ? 16 : 8;
     const long long kv = f64 ? ctx->e64.g.kvec : ctx->e32.g.kvec;
-    return cs * (2 * n6 + 5 * kv) + 2 * 16 * n6;
+    return cs * (2 * n6 + 6 * kv) + 2 * 16 * n6;
 }
 
 // room for nb load cases (frees and reallocates when it grows)
@@ -1314,10 +1314,8 @@ static int batch_reserve(hom_ctx *ctx, int nb) {
     const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
     const long long kv = f64 ? ctx->e64.g.kvec : ctx->e32.g.kvec;
     CU(cudaMalloc(&ctx->bspec, cs * n6 * nb));
-    for (int i = 0; i < 2; ++i) {
-        CU(cudaMalloc(&ctx->bv[i], cs * kv * nb));
-        CU(cudaMalloc(&ctx->bw[i], cs * kv * nb));
-    }
+    for (int i = 0; i < 3; ++i) CU(cudaMalloc(&ctx->bv[i], cs * kv * nb));
+    for (int i = 0; i < 2; ++i) CU(cudaMalloc(&ctx->bw[i], cs * kv * nb));
     CU(cudaMalloc(&ctx->bx, cs * kv * nb));
     CU(cudaMalloc(&ctx->brhs, cs * n6 * nb));
     CU(cudaMalloc(&ctx->bb64, sizeof(double2) * n6 * nb));
@@ -1362,7 +1360,7 @@ template <typename R>
 static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     const Geometry &g = ctx->bg;
     const int nb = g.nb;
-    cpx<R> *ua = (cpx<R> *)ctx->bv[0], *ub = (cpx<R> *)ctx->bv[1];
+    cpx<R> *u3[3] = {(cpx<R> *)ctx->bv[0], (cpx<R> *)ctx->bv[1], (cpx<R> *)ctx->bv[2]};
     cpx<R> *wc = (cpx<R> *)ctx->bw[0], *wd = (cpx<R> *)ctx->bw[1];
     cpx<R> *x = (cpx<R> *)ctx->bx, *spec = (cpx<R> *)ctx->bspec;
     // the Givens step folded into the n1 pass (its last CTA sums one partial
@@ -1374,16 +1372,19 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     const Fold fold3{nullptr, nullptr, 0.0};
     const int np3 = Launch<R>::x3_epart_grid(g);
     cudaStream_t s = ctx->stream;
+    // step it of the body is step k = 1 + it (mod graph_iters, a multiple of
+    // 6) of the sweep: u_k in bv[k mod 3] (u_{k+1} into the third buffer, so
+    // that u_{k-1} stays readable for the lagged update), w by parity
     for (int it = 0; it < ctx->graph_iters; ++it) {
         const bool odd = (it % 2) == 0;
-        cpx<R> *uk = odd ? ub : ua, *um = odd ? ua : ub;
+        cpx<R> *uk = u3[(it + 1) % 3], *um = u3[it % 3], *un = u3[(it + 2) % 3];
         cpx<R> *wa = odd ? wd : wc, *wb = odd ? wc : wd;
         Launch<R>::x2(g, s, 1, spec, ctx->d_bst);
         Launch<R>::x3(g, s, X3_IN_SPEC, spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, spec,
                       E.phi, ctx->d_bst, ctx->bpart, fold3);
         if (!fold3.cnt) scalar_alpha(s, ctx->d_bst, ctx->bpart, np3, (double)ctx->V, g.nb, g.pdl);
         Launch<R>::x2(g, s, 0, spec, ctx->d_bst);
-        Launch<R>::x1_lanczos(g, s, spec, uk, um, wa, wb, x, ctx->d_bst, ctx->bpart, fold);
+        Launch<R>::x1_lanczos(g, s, spec, uk, um, un, wa, wb, x, ctx->d_bst, ctx->bpart, fold);
         ctx->launches += fold3.cnt ? 4 : 5;
     }
 }
@@ -1494,6 +1495,7 @@ static int batch_begin(hom_ctx *ctx, Engine<R> &E, int nb, const double *tol, co
     // work spectrum enters each step holding F_1^-1 G u_k
     CU(cudaMemsetAsync(ctx->bv[0], 0, sizeof(cpx<R>) * kv * nb, s));
     CU(cudaMemsetAsync(ctx->bv[1], 0, sizeof(cpx<R>) * kv * nb, s));
+    CU(cudaMemsetAsync(ctx->bv[2], 0, sizeof(cpx<R>) * kv * nb, s));
     CU(cudaMemsetAsync(ctx->bw[0], 0, sizeof(cpx<R>) * kv * nb, s));
     CU(cudaMemsetAsync(ctx->bw[1], 0, sizeof(cpx<R>) * kv * nb, s));
     for (int j = 0; j < nb; ++j) {
@@ -1512,7 +1514,7 @@ static int batch_end(hom_ctx *ctx, Engine<R> &E, int nb, const int *maxit, bool 
     cpx<R> *rhs = (cpx<R> *)ctx->brhs;
     if (ran) {
         Launch<R>::minres_flush(ctx->bg, s, (const cpx<R> *)ctx->bv[0], (const cpx<R> *)ctx->bv[1],
-                                (cpx<R> *)ctx->bw[0], (cpx<R> *)ctx->bw[1], (cpx<R> *)ctx->bx, ctx->d_bst, kv);
+                                (const cpx<R> *)ctx->bv[2], (cpx<R> *)ctx->bw[0], (cpx<R> *)ctx->bw[1], (cpx<R> *)ctx->bx, ctx->d_bst, kv);
         ctx->launches += 1;
     }
     for (int j = 0; j < nb; ++j) Launch<R>::from_tiles(E.g, s, (const cpx<R> *)ctx->bx + j * kv, rhs + j * n6);
@@ -2871,7 +2873,8 @@ static int time_kernels_impl(hom_ctx *ctx, Engine<R> &E, int reps, double *ms, i
                     case 2: scalar_alpha(s, d, ctx->partials, np3, (double)ctx->V);
                             CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
                     case 3: Launch<R>::x2(E.g, s, 0, E.spec, d); break;
-                    case 4: Launch<R>::x1_lanczos(E.g, s, E.spec, v1, v0, w1, w2, x, d, ctx->partials); break;
+                    case 4: Launch<R>::x1_lanczos(E.g, s, E.spec, v1, v0, (cpx<R> *)ctx->vbuf[2], w1, w2, x, d,
+                                                  ctx->partials); break;
                     default: scalar_givens(s, d, ctx->partials, npl);
                              CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s)); break;
                 }

@@ -249,8 +249,16 @@ __host__ __device__ constexpr int fast_elems(int n) {
 // a radix-16 stage spread over the shared-memory banks.
 template <int PAD> __device__ __forceinline__ int epos(int e, int ES) { return e * ES + (PAD ? (e >> 4) : 0); }
 
+// Barrier of the threads that run a transform: the whole CTA (n = 0), or
+// the first n threads on named barrier 1 (n a multiple of 32).
+__device__ __forceinline__ void group_sync(int n) {
+    if (n == 0) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
 template <typename R, int S, int N, int RAD, int NS_BEFORE, int PAD>
-__device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, const cpx<R> *__restrict__ tw) {
+__device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, const cpx<R> *__restrict__ tw,
+                                           int nsync) {
     constexpr int E = FastPlan<N>::E;
     constexpr int BPT = E / RAD;
     constexpr int nb = N / RAD;
@@ -263,7 +271,7 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, c
 #pragma unroll
         for (int r = 0; r < RAD; ++r) v[i][r] = buf[epos<PAD>(j + r * nb, ES) + l];
     }
-    __syncthreads();
+    group_sync(nsync);
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int j = j0 + i * jstep;
@@ -281,21 +289,23 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, c
 #pragma unroll
         for (int r = 0; r < RAD; ++r) buf[epos<PAD>(o + r * NS_BEFORE, ES) + l] = v[i][r];
     }
-    __syncthreads();
+    group_sync(nsync);
 }
 
 // Transform of L interleaved lines in buf (in place), element e of line l
-// at buf[epos<PAD>(e, ES) + l] (ES >= L).  The CTA must have exactly
-// L * N / E threads (every thread takes part in every barrier).
+// at buf[epos<PAD>(e, ES) + l] (ES >= L).  With nsync = 0 the CTA must have
+// exactly L * N / E threads (every thread takes part in every barrier);
+// otherwise threads 0 .. nsync-1 (= L * N / E) run it and synchronise on
+// named barrier 1, and the CTA's other warps are free for other work.
 template <typename R, int S, int N, int PAD = 0>
-__device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R> *__restrict__ tw) {
+__device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R> *__restrict__ tw, int nsync = 0) {
     using P = FastPlan<N>;
     const int l = (int)threadIdx.x % L;
     const int j0 = (int)threadIdx.x / L;
-    fast_stage<R, S, N, P::R0, 1, PAD>(buf, ES, l, j0, tw);
-    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD>(buf, ES, l, j0, tw);
-    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD>(buf, ES, l, j0, tw);
-    if constexpr (P::NS > 3) fast_stage<R, S, N, P::R3, P::R0 * P::R1 * P::R2, PAD>(buf, ES, l, j0, tw);
+    fast_stage<R, S, N, P::R0, 1, PAD>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 3) fast_stage<R, S, N, P::R3, P::R0 * P::R1 * P::R2, PAD>(buf, ES, l, j0, tw, nsync);
 }
 
 }  // namespace hom

@@ -153,6 +153,8 @@ struct Geometry {
     int grid2_tma, grid1_tma, grid1d_tma;
     int grid1l_tma;         // persistent grid of the fused MINRES n1 pass (0: plain-load form)
     size_t smem2_tma, smem1_tma, smem1d_tma;
+    size_t smem1l_tma = 0;  // fused MINRES n1 pass: work-tile stages + lagged-update ring
+    int x1_lag_stages = 0;  // stages of that ring (kX1LagChunk bytes of each of 4 operands)
     void *tma_cache;
     int *err;
 };
@@ -206,6 +208,12 @@ enum X1Flags { X1_FWD = 1, X1_GAMMA_IN = 2, X1_GAMMA_OUT = 4, X1_DOT = 8 };
 
 constexpr int kEwBlocks = 152 * 8;   // grid of the element-wise Krylov kernels
 constexpr int kNbMax = 8;            // load cases of one stacked MINRES batch
+// threads of the persistent fused n1 pass: the transform group (the fast
+// lengths' n1 tiles take 192 threads) and the lagged-update warps
+constexpr int kX1Group = 192;
+constexpr int kX1LagThreads = 64;
+constexpr int kX1LagChunk = 4096;      // bytes of one operand per ring stage
+constexpr int kX1LagMaxStages = 3;
 constexpr int kEwThreads = 256;
 
 struct Mac6 { double v[6]; };
@@ -249,21 +257,23 @@ template <typename R> struct Launch {
                                const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials);
     // fused n1 pass of a MINRES step (see k_x1_lanczos): spec holds the
     // forward n3 / n2 transforms of C e_k on entry and the inverse n1
-    // transform of G u_{k+1} on exit; um, wb, x as for lanczos_update;
+    // transform of G u_{k+1} on exit; u_{k+1} is written to un (a third
+    // buffer, neither uk nor um); wb, x as for lanczos_update;
     // x1_lanczos_grid(g) partials of ||u_{k+1}||^2
     // (fold: the Givens step folded into the pass)
-    static void x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
-                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials,
-                           Fold fold = Fold{});
+    static void x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, const cpx<R> *um,
+                           cpx<R> *un, const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state,
+                           double *partials, Fold fold = Fold{});
     static int x1_lanczos_grid(const Geometry &g);
     // standard half-spectrum order <-> n1-tile order of the fused chain's
     // Krylov vectors (the tile order's padding is left untouched)
     static void to_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out);
     static void from_tiles(const Geometry &g, cudaStream_t st, const cpx<R> *in, cpx<R> *out);
-    // the lagged update of the last step K after the loop; u_K sits in ub
-    // for odd K, in ua for even K; w_{K-1} in wd for even K, wc for odd K
-    static void minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
-                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long n);
+    // the lagged update of the last step K after the loop; u_K sits in
+    // buffer K mod 3 of (ua, ub, uc), or without uc (two Lanczos buffers) in
+    // ub for odd K, in ua for even K; w_{K-1} in wd for even K, wc for odd K
+    static void minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub,
+                             const cpx<R> *uc, cpx<R> *wc, cpx<R> *wd, cpx<R> *x, MinresState *state, long long n);
     // Parseval partials of <phi, (G x^)_c>, c = 0..5 (see k_phi_dot); returns
     // the number of blocks (partials[c * nb + block])
     static int phi_dot(const Geometry &g, cudaStream_t st, const cpx<R> *x, const cpx<R> *phihat, double *partials);

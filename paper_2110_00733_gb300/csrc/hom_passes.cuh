@@ -17,6 +17,8 @@
 #pragma once
 #include <math.h>
 
+#include <type_traits>
+
 #include "hom_internal.h"
 
 namespace hom {
@@ -221,10 +223,12 @@ __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int 
 // Run the transform of the L lines in buf.  Fast engine: in place, returns
 // buf.  Generic engine: ping-pong with buf2, returns the buffer holding the
 // result.
+// nsync != 0 (fast engine only): the first nsync threads run it on named
+// barrier 1.
 template <typename R, int S, int NF, int PAD = 0>
-__device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, int ES, const AxisPlan &p) {
+__device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, int ES, const AxisPlan &p, int nsync = 0) {
     if constexpr (NF > 0) {
-        fast_fft<R, S, NF, PAD>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw));
+        fast_fft<R, S, NF, PAD>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw), nsync);
         return buf;
     } else {
         return fft_lines<R, S>(buf, buf2, L, ES, p);
@@ -923,25 +927,30 @@ __device__ __forceinline__ LzCoef<R> lz_coef(const MinresState *st) {
 
 // Steps 1-3 on the tile of columns [g0, g0 + T) held in buf (element e of
 // line l at buf[e * L + l], L = 6 T); returns the buffer holding the inverse
-// transform (buf for the register engine).  All threads of the CTA call it.
-// Between the two transforms one loop over the tile's frequencies builds
-// xi once per frequency and applies the projector to p and to u_{k+1}; the
-// Krylov vectors are stored in tile order, so the six components of a
-// frequency are 48 contiguous bytes of each vector and a warp reads and
-// writes a contiguous block.
-template <typename R, int NF>
+// transform (buf for the register engine).  The CTA's threads (nsync = 0) or
+// its first nsync threads (named barrier 1) call it.  Between the two
+// transforms one loop over the tile's frequencies builds xi once per
+// frequency and applies the projector to p and to u_{k+1}; the Krylov
+// vectors are stored in tile order, so the six components of a frequency
+// are 48 contiguous bytes of each vector and a warp reads and writes a
+// contiguous block.  u_{k+1} goes to un, a third buffer (u_{k-1} stays
+// readable for the lagged update); with LAG the lagged w / x update of step
+// k-1 is done here too, else by other warps (x1_lagged_block).
+template <typename R, int NF, bool LAG>
 __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *buf, cpx<R> *buf2, int g0,
                                                    const LzCoef<R> &c, const cpx<R> *__restrict__ uk,
-                                                   cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
-                                                   cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x, Acc<R> &acc) {
+                                                   const cpx<R> *__restrict__ um, cpx<R> *__restrict__ un,
+                                                   const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
+                                                   cpx<R> *__restrict__ x, Acc<R> &acc, int nsync) {
     constexpr int NC = 6;
     const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
     const int cols = g.n2 * H;
+    const int nthr = nsync ? nsync : (int)blockDim.x;
     // 1. forward DFT along n1
-    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, L, g.ax[0]);
+    cpx<R> *res = run_fft<R, -1, NF>(buf, buf2, L, L, g.ax[0], nsync);
     // 2. per frequency: p = G (.), Lanczos step, lagged update, G u_{k+1}
     const size_t kb = (size_t)(g0 / T) * (size_t)(N * L);
-    for (int f = threadIdx.x; f < N * T; f += blockDim.x) {
+    for (int f = threadIdx.x; f < N * T; f += nthr) {
         const int e = f / T, t = f - e * T;
         const int col = g0 + t;
         cpx<R> *sp = res + e * L + t * NC;
@@ -951,24 +960,14 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
             continue;
         }
         const int k2 = col / H, k3 = col - k2 * H;
-        cpx<R> v[NC], u[NC], uo[NC], a[NC], b[NC], xx[NC];
         const size_t i = kb + (size_t)f * NC;
-        // all global loads of the frequency first, then the arithmetic
+        cpx<R> v[NC], u[NC], uo[NC];
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
+            Six<R>::load_pair(sp, p, v[2 * p], v[2 * p + 1]);
             Six<R>::load_pair(uk + i, p, u[2 * p], u[2 * p + 1]);
             Six<R>::load_pair(um + i, p, uo[2 * p], uo[2 * p + 1]);
         }
-        if (c.lagged) {
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                Six<R>::load_pair(wa + i, p, a[2 * p], a[2 * p + 1]);
-                Six<R>::load_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
-                Six<R>::load_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < 3; ++p) Six<R>::load_pair(sp, p, v[2 * p], v[2 * p + 1]);
         const GammaE<R> ge = gamma_e<R>(g, e, k2, k3);
         gamma_apply<R>(g, ge, v);
         const R w = (R)pweight(k3, g.n3);
@@ -979,27 +978,32 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
             acc.add_prod(w * v[q].y, v[q].y);
         }
 #pragma unroll
-        for (int p = 0; p < 3; ++p) Six<R>::store_pair(um + i, p, v[2 * p], v[2 * p + 1]);
-        if (c.lagged) {
-#pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                b[q] = mk<R>((uo[q].x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
-                             (uo[q].y * c.ib - c.d * a[q].y - c.e * b[q].y) * c.ig);
-                xx[q] = mk<R>(xx[q].x + c.tau * b[q].x, xx[q].y + c.tau * b[q].y);
-            }
+        for (int p = 0; p < 3; ++p) Six<R>::store_pair(un + i, p, v[2 * p], v[2 * p + 1]);
+        if (LAG && c.lagged) {
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                Six<R>::store_pair(wb + i, p, b[2 * p], b[2 * p + 1]);
-                Six<R>::store_pair(x + i, p, xx[2 * p], xx[2 * p + 1]);
+                cpx<R> a[2], b[2], xx[2];
+                Six<R>::load_pair(wa + i, p, a[0], a[1]);
+                Six<R>::load_pair(wb + i, p, b[0], b[1]);
+                Six<R>::load_pair(x + i, p, xx[0], xx[1]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const cpx<R> &o = uo[2 * p + q];
+                    b[q] = mk<R>((o.x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
+                                 (o.y * c.ib - c.d * a[q].y - c.e * b[q].y) * c.ig);
+                    xx[q] = mk<R>(xx[q].x + c.tau * b[q].x, xx[q].y + c.tau * b[q].y);
+                }
+                Six<R>::store_pair(wb + i, p, b[0], b[1]);
+                Six<R>::store_pair(x + i, p, xx[0], xx[1]);
             }
         }
         gamma_apply<R>(g, ge, v);
 #pragma unroll
         for (int p = 0; p < 3; ++p) Six<R>::store_pair(sp, p, v[2 * p], v[2 * p + 1]);
     }
-    __syncthreads();
+    group_sync(nsync);
     // 3. inverse DFT along n1 of G u_{k+1}
-    return run_fft<R, 1, NF>(res, res == buf ? buf2 : buf, L, L, g.ax[0]);
+    return run_fft<R, 1, NF>(res, res == buf ? buf2 : buf, L, L, g.ax[0], nsync);
 }
 
 // At most 384 threads per CTA (set_shapes enforces it): the fused pass keeps
@@ -1007,12 +1011,13 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
 // registers, so it is not held to a register cap that would spill them.
 #define HOM_X1L_BOUNDS(R) __launch_bounds__(384, 1)
 
-// plain-load form: one tile per CTA
+// plain-load form: one tile per CTA, the lagged update inline
 template <typename R, int NF>
 __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ spec, const cpx<R> *__restrict__ uk,
-                                                cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
-                                                cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x,
-                                                const MinresState *state, double *__restrict__ partials, Fold fold) {
+                                                const cpx<R> *__restrict__ um, cpx<R> *__restrict__ un,
+                                                const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
+                                                cpx<R> *__restrict__ x, const MinresState *state,
+                                                double *__restrict__ partials, Fold fold) {
     pdl_release();
     pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1038,7 +1043,8 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
     }
     __syncthreads();
     Acc<R> acc;
-    cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf2, g0, c, uk + ko, um + ko, wa + ko, wb + ko, x + ko, acc);
+    cpx<R> *res = x1_lanczos_tile<R, NF, true>(g, buf, buf2, g0, c, uk + ko, um + ko, un + ko, wa + ko, wb + ko,
+                                               x + ko, acc, 0);
     if (live) {
         cpx<R> *dst = spec + (size_t)g0 * NC + lt;
         for (int e = e0; e < N; e += es) dst[e * sK1] = res[e * L + lt];
@@ -1054,90 +1060,214 @@ __global__ void HOM_X1L_BOUNDS(R) k_x1_lanczos(Geometry g, cpx<R> *__restrict__ 
     }
 }
 
-// persistent TMA-staged form (FP32, register FFT lengths 64..256, at most
-// 192 threads per CTA): the work tile comes and goes by TMA, double-buffered
-// as in k_x1_tma; the contiguous Krylov blocks of a tile are read and
-// written with plain coalesced accesses.  (Prefetching the next tile's
-// blocks into L2 was measured to double the DRAM reads: the lines were
-// evicted before use.)  Tiles are numbered case-major over the stacked
-// batch; tiles of converged cases are skipped; each thread keeps one running
-// sum per case in shared memory, and the CTA writes one partial per case
-// (partials[case * gridDim + block]).
+// OR of a predicate over the n threads that use named barrier ID
+template <int ID>
+__device__ __forceinline__ bool group_or(bool v, int n) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(ID), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// The lagged update of step k-1 by the lagged-update warps (named barrier
+// 2) of the fused n1 pass, over the Krylov blocks of the CTA's tiles whose
+// case has one:
+//   w_{k-1} = (u_{k-1} / beta_{k-1} - delta w_{k-2} - eps w_{k-3}) / gamma
+// over the slot of w_{k-3}, and x += tau w_{k-1}.  The blocks are cut into
+// items of kX1LagChunk bytes; one thread brings an item's four operands
+// (u_{k-1}, w_{k-2}, w_{k-3}, x) into a ring of S stages with untiled bulk
+// copies, S items ahead, and the warps update it from shared memory and
+// store w_{k-1} and x to HBM.  The update is the same on every real number,
+// so it runs on 16-byte vectors.  Returns false after a bounded wait ran
+// out (the copies in flight have been waited for, bounded).
+template <typename R, typename LiveFrom>
+__device__ __forceinline__ bool x1_lagged(const Geometry &g, const LzCoef<R> *scoef, LiveFrom live_from, int ntiles,
+                                          int tpc, int per, unsigned char *ring, uint64_t *lbar,
+                                          const cpx<R> *__restrict__ um, const cpx<R> *__restrict__ wa,
+                                          cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x) {
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int NR = 16 / sizeof(R);
+    const int S = g.x1_lag_stages;
+    const int lt = threadIdx.x - kX1Group;
+    const long long pbytes = (long long)per * sizeof(cpx<R>);
+    auto next_tile = [&](int t) {
+        t = live_from(t);
+        while (t < ntiles && !scoef[t / tpc].lagged) t = live_from(t + gridDim.x);
+        return t;
+    };
+    auto base_of = [&](int t) {   // byte offset of tile t's block in each Krylov vector
+        return ((long long)(t / tpc) * g.kvec + (long long)(t % tpc) * per) * (long long)sizeof(cpx<R>);
+    };
+    int pt = next_tile(blockIdx.x), ct = pt;   // producer / consumer cursors (tile, byte offset)
+    long long po = 0, co = 0;
+    int issued = 0;                            // items issued (thread lt = 0)
+    auto issue = [&]() {
+        const int s = issued % S;
+        const uint32_t nb = (uint32_t)(pbytes - po < kX1LagChunk ? pbytes - po : kX1LagChunk);
+        const long long o = base_of(pt) + po;
+        unsigned char *st = ring + (size_t)s * 4 * kX1LagChunk;
+        mbar_expect_tx(&lbar[s], 4 * nb);
+        bulk_load(st, reinterpret_cast<const char *>(um) + o, nb, &lbar[s]);
+        bulk_load(st + kX1LagChunk, reinterpret_cast<const char *>(wa) + o, nb, &lbar[s]);
+        bulk_load(st + 2 * kX1LagChunk, reinterpret_cast<const char *>(wb) + o, nb, &lbar[s]);
+        bulk_load(st + 3 * kX1LagChunk, reinterpret_cast<const char *>(x) + o, nb, &lbar[s]);
+        ++issued;
+        po += kX1LagChunk;
+        if (po >= pbytes) {
+            po = 0;
+            pt = next_tile(pt + gridDim.x);
+        }
+    };
+    if (lt == 0)
+        for (int s = 0; s < S && pt < ntiles; ++s) issue();
+    int n = 0;
+    for (; ct < ntiles; ++n) {
+        const int s = n % S;
+        const bool got = mbar_wait_bounded(&lbar[s], (uint32_t)(n / S) & 1u);
+        if (group_or<2>(!got, kX1LagThreads)) {
+            if (lt == 0) {   // record, then wait (bounded) for the items in flight
+                atomicExch(g.err, 1);
+                for (int m = n; m < issued; ++m) mbar_wait_bounded(&lbar[m % S], (uint32_t)(m / S) & 1u);
+            }
+            return false;
+        }
+        const LzCoef<R> c = scoef[ct / tpc];
+        const int nv = (int)((pbytes - co < kX1LagChunk ? pbytes - co : kX1LagChunk) / 16);
+        const long long o = base_of(ct) + co;
+        const V *su = reinterpret_cast<const V *>(ring + (size_t)s * 4 * kX1LagChunk);
+        const V *sa = su + kX1LagChunk / 16, *sb = su + 2 * (kX1LagChunk / 16), *sx = su + 3 * (kX1LagChunk / 16);
+        V *gb = reinterpret_cast<V *>(reinterpret_cast<char *>(wb) + o);
+        V *gx = reinterpret_cast<V *>(reinterpret_cast<char *>(x) + o);
+        for (int j = lt; j < nv; j += kX1LagThreads) {
+            V vu = su[j], va = sa[j], vb = sb[j], vx = sx[j];
+            const R *u = reinterpret_cast<const R *>(&vu);
+            const R *a = reinterpret_cast<const R *>(&va);
+            R *b = reinterpret_cast<R *>(&vb);
+            R *xx = reinterpret_cast<R *>(&vx);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                b[r] = (u[r] * c.ib - c.d * a[r] - c.e * b[r]) * c.ig;
+                xx[r] += c.tau * b[r];
+            }
+            gb[j] = vb;
+            gx[j] = vx;
+        }
+        co += kX1LagChunk;
+        if (co >= pbytes) {
+            co = 0;
+            ct = next_tile(ct + gridDim.x);
+        }
+        asm volatile("bar.sync 2, %0;" ::"n"(kX1LagThreads) : "memory");   // stage s is read
+        if (lt == 0 && pt < ntiles) issue();
+    }
+    return true;
+}
+
+// persistent TMA-staged form (FP32, register FFT lengths 64..512), warp-
+// specialised.  The first g.threads1 threads (the transform group, named
+// barrier 1) take the work tiles: each comes and goes by TMA, double-
+// buffered as in k_x1_tma, and the Lanczos step reads u_k and u_{k-1} and
+// writes u_{k+1} with plain coalesced accesses.  The last kX1LagThreads
+// threads (two warps) run the lagged w / x update on the same tiles' Krylov
+// blocks, streaming u_{k-1}, w_{k-2}, w_{k-3} and x while the transform
+// group works in shared memory; the two groups share no written data (u_{k+1}
+// has its own buffer), so they never wait on each other.  (Prefetching the
+// next tile's blocks into L2 was measured to double the DRAM reads: the lines
+// were evicted before use.)  Tiles are numbered case-major over the stacked
+// batch; tiles of converged cases are skipped; each transform thread keeps
+// one running sum per case in shared memory, and the CTA writes one partial
+// per case (partials[case * gridDim + block]).
 template <typename R, int NF>
-__global__ void __launch_bounds__(192, 2) k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec,
-                                                    const cpx<R> *__restrict__ uk, cpx<R> *__restrict__ um,
-                                                    const cpx<R> *__restrict__ wa, cpx<R> *__restrict__ wb,
-                                                    cpx<R> *__restrict__ x, const MinresState *state,
-                                                    double *__restrict__ partials, Fold fold) {
+__global__ void __launch_bounds__(kX1Group + kX1LagThreads, 2)
+    k_x1_lanczos_tma(Geometry g, const __grid_constant__ CUtensorMap tspec, const cpx<R> *__restrict__ uk,
+                     const cpx<R> *__restrict__ um, cpx<R> *__restrict__ un, const cpx<R> *__restrict__ wa,
+                     cpx<R> *__restrict__ wb, cpx<R> *__restrict__ x, const MinresState *state,
+                     double *__restrict__ partials, Fold fold) {
     pdl_release();
     pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ double sacc[kNbMax * 192];
+    __shared__ __align__(8) uint64_t lbar[kX1LagMaxStages];
+    __shared__ double sacc[kNbMax * kX1Group];
     __shared__ LzCoef<R> scoef[kNbMax];   // each case's coefficients, converted once
     constexpr int NC = 6;
-    const int N = g.n1, T = g.tile1, H = g.h, L = NC * T;
-    const int cols = g.n2 * H;
+    const int N = g.n1, T = g.tile1, L = NC * T;
+    const int cols = g.n2 * g.h;
     const int tpc = (cols + T - 1) / T;   // tiles per case
     const int ntiles = tpc * g.nb;
     const int per = N * L;
     const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
     cpx<R> *base = reinterpret_cast<cpx<R> *>(smem_raw);
     const bool leader = threadIdx.x == 0;
+    const bool xform = threadIdx.x < kX1Group;
     auto live_from = [&](int t) {
         while (t < ntiles && skip_case(state, t / tpc)) t += gridDim.x;
         return t;
     };
-    for (int cc = 0; cc < g.nb; ++cc) sacc[cc * blockDim.x + threadIdx.x] = 0.0;
+    if (xform)
+        for (int cc = 0; cc < g.nb; ++cc) sacc[cc * kX1Group + threadIdx.x] = 0.0;
     if (threadIdx.x < g.nb) scoef[threadIdx.x] = lz_coef<R>(state + threadIdx.x);
     if (leader) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        for (int q = 0; q < kX1LagMaxStages; ++q) mbar_init(&lbar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    int tile = live_from(blockIdx.x);
-    if (leader && tile < ntiles) {
-        mbar_expect_tx(&bar[0], bytes);
-        tma_load_rows_2d(base, &tspec, NC * T * (tile % tpc), N * (tile / tpc), N, L * (int)sizeof(cpx<R>), &bar[0]);
-    }
-    for (int i = 0; tile < ntiles; ++i) {
-        const int s = i & 1;
-        const int next = live_from(tile + gridDim.x);
-        if (leader && next < ntiles) {
-            bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
-            mbar_expect_tx(&bar[s ^ 1], bytes);
-            tma_load_rows_2d(base + (s ^ 1) * per, &tspec, NC * T * (next % tpc), N * (next / tpc), N,
-                             L * (int)sizeof(cpx<R>), &bar[s ^ 1]);
+    if (!xform) {
+        x1_lagged<R>(g, scoef, live_from, ntiles, tpc, per, smem_raw + g.smem1_tma, lbar, um, wa, wb, x);
+    } else {
+        int tile = live_from(blockIdx.x);
+        if (leader && tile < ntiles) {
+            mbar_expect_tx(&bar[0], bytes);
+            tma_load_rows_2d(base, &tspec, NC * T * (tile % tpc), N * (tile / tpc), N, L * (int)sizeof(cpx<R>),
+                             &bar[0]);
         }
-        const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
-                atomicExch(g.err, 1);
-                mbar_wait_bounded(&bar[s], (i >> 1) & 1);
-                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
-                bulk_wait_all();
+        for (int i = 0; tile < ntiles; ++i) {
+            const int s = i & 1;
+            const int next = live_from(tile + gridDim.x);
+            if (leader && next < ntiles) {
+                bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
+                mbar_expect_tx(&bar[s ^ 1], bytes);
+                tma_load_rows_2d(base + (s ^ 1) * per, &tspec, NC * T * (next % tpc), N * (next / tpc), N,
+                                 L * (int)sizeof(cpx<R>), &bar[s ^ 1]);
             }
-            return;
+            const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+            if (group_or<1>(!ok, kX1Group)) {
+                if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
+                    atomicExch(g.err, 1);
+                    mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+                    if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
+                }
+                break;
+            }
+            const int cs = tile / tpc, tc = tile - cs * tpc;
+            const size_t ko = (size_t)cs * g.kvec;
+            const LzCoef<R> c = scoef[cs];
+            Acc<R> acc;
+            cpx<R> *buf = base + s * per;
+            cpx<R> *res = x1_lanczos_tile<R, NF, false>(g, buf, buf, tc * T, c, uk + ko, um + ko, un + ko, wa + ko,
+                                                        wb + ko, x + ko, acc, kX1Group);
+            sacc[cs * kX1Group + threadIdx.x] += acc.value();
+            fence_proxy_async_smem();
+            group_sync(kX1Group);
+            if (leader) {
+                tma_store_rows_2d(&tspec, NC * T * tc, N * cs, N, res, L * (int)sizeof(cpx<R>));
+                bulk_commit();
+            }
+            tile = next;
         }
-        const int cs = tile / tpc, tc = tile - cs * tpc;
-        const size_t ko = (size_t)cs * g.kvec;
-        const LzCoef<R> c = scoef[cs];
-        Acc<R> acc;
-        cpx<R> *buf = base + s * per;
-        cpx<R> *res = x1_lanczos_tile<R, NF>(g, buf, buf, tc * T, c, uk + ko, um + ko, wa + ko, wb + ko, x + ko, acc);
-        sacc[cs * blockDim.x + threadIdx.x] += acc.value();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (leader) {
-            tma_store_rows_2d(&tspec, NC * T * tc, N * cs, N, res, L * (int)sizeof(cpx<R>));
-            bulk_commit();
-        }
-        tile = next;
+        if (leader) bulk_wait_all();
     }
-    if (leader) bulk_wait_all();
+    __syncthreads();   // both groups done
     for (int cc = 0; cc < g.nb; ++cc) {
-        const double sum = block_sum(sacc[cc * blockDim.x + threadIdx.x]);
+        const double sum = block_sum(xform ? sacc[cc * kX1Group + threadIdx.x] : 0.0);
         if (threadIdx.x == 0) partials[cc * gridDim.x + blockIdx.x] = sum;
     }
     if (fold.cnt && last_of(fold.cnt + 2 * kNbMax, gridDim.x)) {   // Givens step of every case
@@ -1207,14 +1337,15 @@ __global__ void k_tiles(long long n, int n1, int cols, int T, int to_tiles, cons
 // or the state kept the last finite iterate.
 template <typename R>
 __global__ void __launch_bounds__(kEwThreads) k_minres_flush(long long n, long long per_case, const cpx<R> *__restrict__ ua,
-                                                             const cpx<R> *__restrict__ ub, cpx<R> *__restrict__ wc,
-                                                             cpx<R> *__restrict__ wd, cpx<R> *__restrict__ x,
-                                                             const MinresState *sts) {
+                                                             const cpx<R> *__restrict__ ub, const cpx<R> *__restrict__ uc,
+                                                             cpx<R> *__restrict__ wc, cpx<R> *__restrict__ wd,
+                                                             cpx<R> *__restrict__ x, const MinresState *sts) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const MinresState *st = sts + i / per_case;   // the element's load case
         const int K = st->k;
         if (st->done_update || K <= 0) continue;
-        const cpx<R> *u = (K & 1) ? ub : ua;
+        // u_K: buffer K mod 3 of (ua, ub, uc), or K mod 2 of (ua, ub) without uc
+        const cpx<R> *u = uc ? (K % 3 == 0 ? ua : (K % 3 == 1 ? ub : uc)) : ((K & 1) ? ub : ua);
         const cpx<R> *wa = (K & 1) ? wc : wd;      // w_{K-1}
         cpx<R> *wb = (K & 1) ? wd : wc;            // w_{K-2}, overwritten by w_K
         const R d = (R)st->u_delta, e = (R)st->u_eps, ig = (R)st->u_inv_gamma, tau = (R)st->u_tau,
@@ -1438,16 +1569,26 @@ int Launch<R>::tma_grids(Geometry &g) {
             g.tma = 0;
             return 0;
         }
-        // the fused MINRES n1 pass (launch bounds: 192 threads per CTA)
+        // the fused MINRES n1 pass: a transform group of exactly kX1Group
+        // threads plus the lagged-update warps, whose ring takes as many
+        // stages (up to kX1LagMaxStages) as leave room for two CTAs per SM
         int b1l = 0;
-        if (g.nc == 6 && g.threads1 <= 192) {
+        if (g.nc == 6 && g.threads1 == kX1Group) {
+            const int t = kX1Group + kX1LagThreads;
+            int smem_sm = 0;
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            const size_t ring = 4 * (size_t)kX1LagChunk, fixed = 15 * 1024;   // static + reserved per CTA
+            int st = kX1LagMaxStages;
+            while (st > 1 && 2 * (g.smem1_tma + st * ring + fixed) > (size_t)smem_sm) --st;
+            g.x1_lag_stages = st;
+            g.smem1l_tma = g.smem1_tma + st * ring;
             switch (g.fast[0]) {
-                case 64: b1l = occ(k_x1_lanczos_tma<R, 64>, g.threads1, g.smem1_tma); break;
-                case 96: b1l = occ(k_x1_lanczos_tma<R, 96>, g.threads1, g.smem1_tma); break;
-                case 160: b1l = occ(k_x1_lanczos_tma<R, 160>, g.threads1, g.smem1_tma); break;
-                case 512: b1l = occ(k_x1_lanczos_tma<R, 512>, g.threads1, g.smem1_tma); break;
-                case 128: b1l = occ(k_x1_lanczos_tma<R, 128>, g.threads1, g.smem1_tma); break;
-                default: b1l = occ(k_x1_lanczos_tma<R, 256>, g.threads1, g.smem1_tma); break;
+                case 64: b1l = occ(k_x1_lanczos_tma<R, 64>, t, g.smem1l_tma); break;
+                case 96: b1l = occ(k_x1_lanczos_tma<R, 96>, t, g.smem1l_tma); break;
+                case 160: b1l = occ(k_x1_lanczos_tma<R, 160>, t, g.smem1l_tma); break;
+                case 512: b1l = occ(k_x1_lanczos_tma<R, 512>, t, g.smem1l_tma); break;
+                case 128: b1l = occ(k_x1_lanczos_tma<R, 128>, t, g.smem1l_tma); break;
+                default: b1l = occ(k_x1_lanczos_tma<R, 256>, t, g.smem1l_tma); break;
             }
         }
         g.grid1l_tma = b1l * sms;
@@ -1562,16 +1703,15 @@ int Launch<R>::x1_lanczos_grid(const Geometry &g) {
 }
 
 template <typename R>
-void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, cpx<R> *um,
-                           const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state, double *partials,
-                           Fold fold) {
+void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, const cpx<R> *uk, const cpx<R> *um,
+                           cpx<R> *un, const cpx<R> *wa, cpx<R> *wb, cpx<R> *x, const MinresState *state,
+                           double *partials, Fold fold) {
     if constexpr (sizeof(R) == 4) {
         if (g.tma && g.grid1l_tma > 0) {
             const CUtensorMap *ts = tma_map(g, spec, TMA_X1, 1);
 #define HOM_X1LT(NF)                                                                                         \
-    launch_k(g.pdl, k_x1_lanczos_tma<R, NF>, g.grid1l_tma, g.threads1, g.smem1_tma, st, g, *ts, uk, um, wa, wb, x, state, \
-             partials, \
-                                                                           fold)
+    launch_k(g.pdl, k_x1_lanczos_tma<R, NF>, g.grid1l_tma, kX1Group + kX1LagThreads, g.smem1l_tma, st, g, *ts, uk, um, \
+             un, wa, wb, x, state, partials, fold)
             switch (g.fast[0]) {
                 case 64: HOM_X1LT(64); break;
                 case 96: HOM_X1LT(96); break;
@@ -1586,7 +1726,8 @@ void Launch<R>::x1_lanczos(const Geometry &g, cudaStream_t st, cpx<R> *spec, con
     }
     const int grid = (g.n2 * g.h + g.tile1 - 1) / g.tile1 * g.nb;
 #define HOM_X1L(NF) \
-    launch_k(g.pdl, k_x1_lanczos<R, NF>, grid, g.threads1, g.smem1, st, g, spec, uk, um, wa, wb, x, state, partials, fold)
+    launch_k(g.pdl, k_x1_lanczos<R, NF>, grid, g.threads1, g.smem1, st, g, spec, uk, um, un, wa, wb, x, state, partials, \
+             fold)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1L)
 #undef HOM_X1L
 }
@@ -1611,10 +1752,10 @@ void Launch<R>::lanczos_update(const Geometry &g, cudaStream_t st, const cpx<R> 
 }
 
 template <typename R>
-void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, cpx<R> *wc,
-                             cpx<R> *wd, cpx<R> *x, MinresState *state, long long per_case) {
+void Launch<R>::minres_flush(const Geometry &g, cudaStream_t st, const cpx<R> *ua, const cpx<R> *ub, const cpx<R> *uc,
+                             cpx<R> *wc, cpx<R> *wd, cpx<R> *x, MinresState *state, long long per_case) {
     const long long n = per_case * g.nb;
-    k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, per_case, ua, ub, wc, wd, x, state);
+    k_minres_flush<R><<<ew_grid(n), kEwThreads, 0, st>>>(n, per_case, ua, ub, uc, wc, wd, x, state);
 }
 
 template <typename R>
