@@ -344,11 +344,12 @@ def run_ours(args):
     t_max, units = reduce_over_ranks(dist, t_local, V * iters, "cuda")
     value = units / t_max
 
-    # Roofline of the MINRES step as a whole: its algorithmic bytes (the
-    # survey's 196 B per voxel-iteration: read v_k, phi, v_{k-1}, w_{k-1},
-    # w_{k-2}, x, write v_{k+1}, w_k, x) over the live time per iteration of
-    # the timed solves; the per-kernel figures come from CUDA events on the
-    # library's stream (hom_time_kernels) and explain it.
+    # Roofline of the MINRES step as a whole: its algorithmic bytes (196 B
+    # per voxel-iteration, the least an iteration can move with FP32 fields:
+    # read v_k, phi, v_{k-1}, w_{k-1}, w_{k-2}, x, write v_{k+1}, w_k, x)
+    # over the live time per iteration of the timed solves; the per-kernel
+    # figures come from CUDA events on the library's stream
+    # (hom_time_kernels) and explain it.
     ktimes = hom.hom_time_kernels(ctx, reps=20)
     kb = kernel_bytes_per_voxel(n)
     peak, peak_kind = measured_peaks()

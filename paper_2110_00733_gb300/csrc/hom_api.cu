@@ -300,7 +300,9 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
         return fail(ctx, HOM_EINVAL, "launch shape needs more than 384 threads per CTA in the fused n1 pass");
     g.kvec = (long long)((g.n2 * g.h + t1 - 1) / t1) * g.n1 * nc * t1;
     g.x3r = (sizeof(R) == 4 && nc == 6 && x3r_length(g.n3) && ctx->shape[0] == 0 &&
-             x3r_smem(g.n3) + 1024 <= (size_t)dev_smem) ? 1 : 0;
+             x3r_smem(g.n3) + 1024 <= (size_t)dev_smem && (g.n1 * g.n2) % x3r_rows_per_warp(g.n3) == 0) ? 1 : 0;
+    g.grid3r = g.x3r ? Launch<R>::x3r_grid(g) : 0;
+    if (g.grid3r <= 0) g.x3r = 0;
     // persistent TMA-staged n2 / n1 passes: FP32, register-FFT lengths <= 256
     g.tma = 0;
     g.err = ctx->d_err;

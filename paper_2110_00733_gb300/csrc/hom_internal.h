@@ -153,6 +153,7 @@ struct Geometry {
     int grid2_tma, grid1_tma, grid1d_tma;
     int grid1l_tma;         // persistent grid of the fused MINRES n1 pass (0: plain-load form)
     size_t smem2_tma, smem1_tma, smem1d_tma;
+    int grid3r = 0;         // persistent grid of the register n3 pass
     size_t smem1l_tma = 0;  // fused MINRES n1 pass: work-tile stages + lagged-update ring
     int x1_lag_stages = 0;  // stages of that ring (kX1LagChunk bytes of each of 4 operands)
     void *tma_cache;
@@ -163,10 +164,23 @@ struct Geometry {
 // CTA, and its shared memory (per row, the transpose slab of 3 lines x Q x
 // (P + 1) complex values, N = P Q)
 __host__ __device__ constexpr bool x3r_length(int n) { return n == 64 || n == 128 || n == 256; }
-__host__ __device__ constexpr int x3r_rows(int n) { return n == 256 ? 8 : 16; }
-__host__ __device__ constexpr size_t x3r_smem(int n) {
-    return (size_t)x3r_rows(n) * 3 * (n == 64 ? 8 * 9 : (n == 128 ? 16 * 9 : 16 * 17)) * sizeof(float2);
+// register n3 pass: rows per warp (32 / lanes per row), and per warp the
+// prefetch buffer of a row group (its rows' half spectra, then phi) and one
+// transpose slab per row; four warps per CTA
+__host__ __device__ constexpr int x3r_row_lanes(int n) { return n == 256 ? 16 : 8; }
+__host__ __device__ constexpr int x3r_rows_per_warp(int n) { return 32 / x3r_row_lanes(n); }
+__host__ __device__ constexpr size_t x3r_in_bytes(int n) {
+    return (size_t)x3r_rows_per_warp(n) * (n / 2 + 1) * 6 * sizeof(float2);
 }
+__host__ __device__ constexpr size_t x3r_phi_bytes(int n) { return (size_t)x3r_rows_per_warp(n) * n * sizeof(float); }
+__host__ __device__ constexpr size_t x3r_slab_elems(int n) {
+    return (size_t)(n / x3r_row_lanes(n)) * (x3r_row_lanes(n) + 1);
+}
+__host__ __device__ constexpr size_t x3r_warp_bytes(int n) {
+    return x3r_in_bytes(n) + x3r_phi_bytes(n) + (size_t)x3r_rows_per_warp(n) * x3r_slab_elems(n) * sizeof(float2);
+}
+constexpr int kX3rWarps = 4;
+__host__ __device__ constexpr size_t x3r_smem(int n) { return kX3rWarps * x3r_warp_bytes(n); }
 
 // A kernel launch, with programmatic stream serialization when pdl != 0.
 template <typename... KArgs, typename... Args>
@@ -303,6 +317,8 @@ template <typename R> struct Launch {
     static void table_init(const Geometry &g);
     static int x3_grid(const Geometry &g);
     static int x3_epart_grid(const Geometry &g);
+    // resident CTAs x SMs of the persistent register n3 pass (0: it cannot run)
+    static int x3r_grid(const Geometry &g);
     static int x1_grid(const Geometry &g);
     static int tma_grids(Geometry &g);
 };

@@ -439,8 +439,14 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
 // the forward voxels to frequencies).  The other half of the Hermitian
 // spectrum (Z[N-k] from X[k]) and the unpacking of the result come from the
 // partner lane P - j by warp shuffles.  The law needs all six components of
-// a voxel, which lane j holds.  Rows are independent, so only warp-level
-// synchronisation is used.
+// a voxel, which lane j holds.
+//
+// Persistent and warp-independent: each warp takes groups of 32 / P
+// consecutive rows (one contiguous block of the stacked spectrum) in turn.
+// The group's rows and phi come from a per-warp shared-memory buffer, filled
+// by cp.async while the warp computes the previous group's R2C and stores
+// it, so the HBM latency is off the warp's critical path.  Only warp-level
+// synchronisation is used until the final energy reduction.
 // ---------------------------------------------------------------------------
 template <int N> struct X3RPlan;
 template <> struct X3RPlan<64>  { static constexpr int P = 8,  Q = 8,  ROWS = 16; };
@@ -471,143 +477,194 @@ __device__ __forceinline__ void x3r_stage2(const float2 *slab, int t, float2 (&z
     }
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int N>
-__global__ void __launch_bounds__(128, N == 64 ? 5 : 4) k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                int material, float lam, float mu2, const float *__restrict__ phi,
-                                                const MinresState *state, double *__restrict__ epart, Fold fold) {
+__global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
+    k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out, int material, float lam, float mu2,
+          const float *__restrict__ phi, const MinresState *state, double *__restrict__ epart, Fold fold) {
     pdl_release();
     pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     using PL = X3RPlan<N>;
-    constexpr int P = PL::P, Q = PL::Q, ROWS = PL::ROWS, H = N / 2 + 1, NC = 6;
-    constexpr int TS = Q * (P + 1);   // one line's transpose slab
-    extern __shared__ __align__(16) float2 xslab[];
-    const int r = threadIdx.x / P, j = threadIdx.x % P;
+    constexpr int P = PL::P, Q = PL::Q, H = N / 2 + 1, NC = 6;
+    constexpr int RW = 32 / P;                  // rows per warp group
+    constexpr int TS = Q * (P + 1);             // one line's transpose slab
+    static_assert(P == x3r_row_lanes(N) && TS == (int)x3r_slab_elems(N), "x3r layout");
+    extern __shared__ __align__(16) unsigned char x3r_smem_raw[];
+    __shared__ double sacc[kNbMax * kX3rWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rw = lane / P, j = lane % P;
+    unsigned char *wbase = x3r_smem_raw + (size_t)warp * x3r_warp_bytes(N);
+    float2 *inb = reinterpret_cast<float2 *>(wbase);                               // RW rows x H x 6
+    float *phb = reinterpret_cast<float *>(wbase + x3r_in_bytes(N));                // RW rows x N
+    float2 *tb = reinterpret_cast<float2 *>(wbase + x3r_in_bytes(N) + x3r_phi_bytes(N)) + rw * TS;
     const int nrows = g.n1 * g.n2;
-    // load case cs of a stacked batch; a CTA never straddles two cases
-    const int bpc = (nrows + ROWS - 1) / ROWS;
-    const int cs = blockIdx.x / bpc;
-    if (skip_case(state, cs)) return;
-    const int rowc = (blockIdx.x - cs * bpc) * ROWS + r;   // row within the case (phi row)
-    const bool live = rowc < nrows;
-    const int row = cs * nrows + rowc;                       // row of the stacked spectrum
-    float2 *tb = xslab + r * 3 * TS;
+    const int gpc = nrows / RW;                  // row groups per case (nrows is a multiple of RW)
+    const int ngroups = gpc * g.nb;
+    const int gstride = gridDim.x * kX3rWarps;
+    if (threadIdx.x < kNbMax * kX3rWarps) sacc[threadIdx.x] = 0.0;
+    __syncthreads();
+    auto live_from = [&](int q) {
+        while (q < ngroups && skip_case(state, q / gpc)) q += gstride;
+        return q;
+    };
+    // the group's rows (contiguous) and, with the law, its phi rows
+    auto prefetch = [&](int q) {
+        const int cs = q / gpc, rowc = (q - cs * gpc) * RW;
+        const char *src = reinterpret_cast<const char *>(in + ((size_t)cs * nrows + rowc) * H * NC);
+        constexpr int nin = (int)(x3r_in_bytes(N) / 16);
+        for (int i = lane; i < nin; i += 32) cp_async16(reinterpret_cast<char *>(inb) + 16 * i, src + 16 * i);
+        if (material) {
+            const char *ps = reinterpret_cast<const char *>(phi + (size_t)rowc * N);
+            constexpr int nph = (int)(x3r_phi_bytes(N) / 16);
+            for (int i = lane; i < nph; i += 32) cp_async16(reinterpret_cast<char *>(phb) + 16 * i, ps + 16 * i);
+        }
+        cp_async_commit();
+    };
     const float2 *tw = reinterpret_cast<const float2 *>(g.ax[2].tw);   // exp(-2 pi i t / N)
-    const int lane0 = (threadIdx.x & 31) & ~(P - 1);
+    const int lane0 = lane & ~(P - 1);
     const int partner = lane0 + ((P - j) & (P - 1));
-    float2 z[3][Q];
-    // ---- input, one line at a time: own frequencies k = j + P m <= N/2
-    // (m < Q/2, and m = Q/2 for j = 0); the upper half m > Q/2 (and m = Q/2
-    // for j != 0) is Z[j + P m] = Zc[N - j - P m], held by the partner at
-    // m' = Q - 1 - m (by lane 0 itself at Q - m)
-    const float2 *rp = in + (size_t)(live ? row : 0) * H * NC;
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        float2 zc[Q / 2 + 1];   // conj X_a[k] + i conj X_b[k] = Z[N - k], for the partner
-#pragma unroll
-        for (int m = 0; m <= Q / 2; ++m) {
-            const int k = j + P * m;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (live && (m < Q / 2 || j == 0)) v = reinterpret_cast<const float4 *>(rp + NC * k)[p];
-            if (k == 0 || 2 * k == N) { v.y = 0.f; v.w = 0.f; }   // self-conjugate bins: real parts
-            // a = (v.x, v.y), b = (v.z, v.w): Z = a + i b, Zc = conj a + i conj b
-            z[p][m] = make_float2(v.x - v.w, v.y + v.z);
-            zc[m] = make_float2(v.x + v.w, v.z - v.y);
-        }
-#pragma unroll
-        for (int s = 0; s < Q / 2; ++s) {
-            const float2 got = shfl_partner<P>(zc[s], partner);
-            const int m = Q - 1 - s;
-            z[p][m] = (j == 0) ? (m > Q / 2 ? zc[Q - m] : z[p][m]) : got;
-        }
-    }
-    // ---- inverse transform (C2R part of eq. linearOp)
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        dft<float, 1, Q>(z[p]);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) {
-            float2 w = __ldg(&tw[j * n]);
-            w.y = -w.y;
-            tb[p * TS + n * (P + 1) + j] = mul<float>(z[p][n], w);
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int p = 0; p < 3; ++p) x3r_stage2<1, P, Q>(tb + p * TS, j, z[p]);
-    __syncwarp();
-    // ---- material law on voxels j + P m (scaled by 1/V), strain energy
     const float sV = 1.0f / (float)g.V;
-    float en = 0.f;
-    if (material) {
-        const float *ph_row = phi + (size_t)(live ? rowc : 0) * N;
-#pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            const float ph = live ? __ldg(&ph_row[j + P * m]) : 0.f;
-            float t[6];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                t[2 * p] = z[p][m].x * sV;
-                t[2 * p + 1] = z[p][m].y * sV;
-            }
-            const float sum = t[0] + t[1] + t[2];
-            const float tr = lam * sum;
-            float ee = t[0] * t[0];
-#pragma unroll
-            for (int c = 1; c < 6; ++c) ee += t[c] * t[c];
-            en += ph * (tr * sum + mu2 * ee);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : 0.f) + mu2 * t[c]);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) z[p][m] = make_float2(t[2 * p], t[2 * p + 1]);
-        }
-    } else {
-#pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-            for (int m = 0; m < Q; ++m) z[p][m] = make_float2(z[p][m].x * sV, z[p][m].y * sV);
-    }
-    // ---- forward transform (R2C)
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        dft<float, -1, Q>(z[p]);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) tb[p * TS + n * (P + 1) + j] = mul<float>(z[p][n], __ldg(&tw[j * n]));
-    }
-    __syncwarp();
-#pragma unroll
-    for (int p = 0; p < 3; ++p) x3r_stage2<-1, P, Q>(tb + p * TS, j, z[p]);
-    // ---- unpack and store own frequencies k = j + P m <= N/2:
-    //   X_a[k] = (W[k] + conj W[N-k]) / 2,  X_b[k] = (W[k] - conj W[N-k]) / (2i),
-    //   W[N-k] from the partner's register Q - 1 - m (lane 0: its own Q - m)
-    float2 *op = out + (size_t)(live ? row : 0) * H * NC;
-#pragma unroll
-    for (int m = 0; m <= Q / 2; ++m) {
-        float2 wm[3];
+    int q = live_from(blockIdx.x * kX3rWarps + warp);
+    if (q < ngroups) prefetch(q);
+    while (q < ngroups) {
+        const int qn = live_from(q + gstride);
+        const int cs = q / gpc;
+        const size_t row = (size_t)cs * nrows + (size_t)(q - cs * gpc) * RW + rw;   // row of the stacked spectrum
+        cp_async_wait_all();
+        __syncwarp();
+        float2 z[3][Q];
+        // ---- input, one line at a time: own frequencies k = j + P m <= N/2
+        // (m < Q/2, and m = Q/2 for j = 0); the upper half m > Q/2 (and m = Q/2
+        // for j != 0) is Z[j + P m] = Zc[N - j - P m], held by the partner at
+        // m' = Q - 1 - m (by lane 0 itself at Q - m)
+        const float2 *rp = inb + (size_t)rw * H * NC;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float2 got = shfl_partner<P>(z[p][(Q - 1 - m + Q) % Q], partner);
-            wm[p] = (j == 0) ? z[p][(Q - m) % Q] : got;
+            float2 zc[Q / 2 + 1];   // conj X_a[k] + i conj X_b[k] = Z[N - k], for the partner
+#pragma unroll
+            for (int m = 0; m <= Q / 2; ++m) {
+                const int k = j + P * m;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (m < Q / 2 || j == 0) v = reinterpret_cast<const float4 *>(rp + NC * k)[p];
+                if (k == 0 || 2 * k == N) { v.y = 0.f; v.w = 0.f; }   // self-conjugate bins: real parts
+                // a = (v.x, v.y), b = (v.z, v.w): Z = a + i b, Zc = conj a + i conj b
+                z[p][m] = make_float2(v.x - v.w, v.y + v.z);
+                zc[m] = make_float2(v.x + v.w, v.z - v.y);
+            }
+#pragma unroll
+            for (int s = 0; s < Q / 2; ++s) {
+                const float2 got = shfl_partner<P>(zc[s], partner);
+                const int m = Q - 1 - s;
+                z[p][m] = (j == 0) ? (m > Q / 2 ? zc[Q - m] : z[p][m]) : got;
+            }
         }
-        const int k = j + P * m;
-        if (live && (m < Q / 2 || j == 0)) {
+        // ---- inverse transform (C2R part of eq. linearOp), one line's
+        // transpose at a time through the row's slab
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            dft<float, 1, Q>(z[p]);
+#pragma unroll
+            for (int n = 0; n < Q; ++n) {
+                float2 w = __ldg(&tw[j * n]);
+                w.y = -w.y;
+                tb[n * (P + 1) + j] = mul<float>(z[p][n], w);
+            }
+            __syncwarp();
+            x3r_stage2<1, P, Q>(tb, j, z[p]);
+            __syncwarp();
+        }
+        // ---- material law on voxels j + P m (scaled by 1/V), strain energy
+        float en = 0.f;
+        if (material) {
+            const float *ph_row = phb + rw * N;
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                const float ph = ph_row[j + P * m];
+                float t[6];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    t[2 * p] = z[p][m].x * sV;
+                    t[2 * p + 1] = z[p][m].y * sV;
+                }
+                const float sum = t[0] + t[1] + t[2];
+                const float tr = lam * sum;
+                float ee = t[0] * t[0];
+#pragma unroll
+                for (int c = 1; c < 6; ++c) ee += t[c] * t[c];
+                en += ph * (tr * sum + mu2 * ee);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : 0.f) + mu2 * t[c]);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) z[p][m] = make_float2(t[2 * p], t[2 * p + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int m = 0; m < Q; ++m) z[p][m] = make_float2(z[p][m].x * sV, z[p][m].y * sV);
+        }
+        // the buffer is read: bring in the next group while this one finishes
+        __syncwarp();
+        if (qn < ngroups) prefetch(qn);
+        // ---- forward transform (R2C)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            dft<float, -1, Q>(z[p]);
+#pragma unroll
+            for (int n = 0; n < Q; ++n) tb[n * (P + 1) + j] = mul<float>(z[p][n], __ldg(&tw[j * n]));
+            __syncwarp();
+            x3r_stage2<-1, P, Q>(tb, j, z[p]);
+            __syncwarp();
+        }
+        // ---- unpack and store own frequencies k = j + P m <= N/2:
+        //   X_a[k] = (W[k] + conj W[N-k]) / 2,  X_b[k] = (W[k] - conj W[N-k]) / (2i),
+        //   W[N-k] from the partner's register Q - 1 - m (lane 0: its own Q - m)
+        float2 *op = out + row * H * NC;
+#pragma unroll
+        for (int m = 0; m <= Q / 2; ++m) {
+            float2 wm[3];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                const float2 w = z[p][m % Q];
-                const float2 c = make_float2(wm[p].x, -wm[p].y);
-                reinterpret_cast<float4 *>(op + NC * k)[p] =
-                    make_float4(0.5f * (w.x + c.x), 0.5f * (w.y + c.y), 0.5f * (w.y - c.y), -0.5f * (w.x - c.x));
+                const float2 got = shfl_partner<P>(z[p][(Q - 1 - m + Q) % Q], partner);
+                wm[p] = (j == 0) ? z[p][(Q - m) % Q] : got;
+            }
+            const int k = j + P * m;
+            if (m < Q / 2 || j == 0) {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    const float2 w = z[p][m % Q];
+                    const float2 c = make_float2(wm[p].x, -wm[p].y);
+                    reinterpret_cast<float4 *>(op + NC * k)[p] =
+                        make_float4(0.5f * (w.x + c.x), 0.5f * (w.y + c.y), 0.5f * (w.y - c.y), -0.5f * (w.x - c.x));
+                }
             }
         }
+        if (epart) {
+            const double ws = warp_sum((double)en);
+            if (lane == 0) sacc[cs * kX3rWarps + warp] += ws;
+        }
+        q = qn;
     }
+    cp_async_wait_all();
     if (epart) {
-        const double sum = block_sum((double)en);
-        if (threadIdx.x == 0) epart[blockIdx.x] = sum;
-        if (fold.cnt && last_of(fold.cnt + cs, bpc)) {   // alpha of case cs
-            const double tot = sum_partials(epart + (size_t)cs * bpc, bpc);
-            if (threadIdx.x == 0) {
-                alpha_step(fold.st + cs, tot, fold.scale);
-                fold.cnt[cs] = 0;
+        __syncthreads();
+        if (threadIdx.x < g.nb) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < kX3rWarps; ++w) t += sacc[threadIdx.x * kX3rWarps + w];
+            epart[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;   // = epart[case * grid + block]
+        }
+        if (fold.cnt && last_of(fold.cnt, gridDim.x)) {   // alpha of every case
+            for (int cc = 0; cc < g.nb; ++cc) {
+                const double tot = sum_partials(epart + (size_t)cc * gridDim.x, gridDim.x);
+                if (threadIdx.x == 0) alpha_step(fold.st + cc, tot, fold.scale);
             }
+            if (threadIdx.x == 0) fold.cnt[0] = 0;
         }
     }
 }
@@ -1458,8 +1515,26 @@ int Launch<R>::x3_grid(const Geometry &g) { return (g.n1 * g.n2 + g.rows3 - 1) /
 // (spectrum in and out): case c's are at [c * count, (c + 1) * count)
 template <typename R>
 int Launch<R>::x3_epart_grid(const Geometry &g) {
-    if (sizeof(R) == 4 && g.x3r) return (g.n1 * g.n2 + x3r_rows(g.n3) - 1) / x3r_rows(g.n3);
+    if (sizeof(R) == 4 && g.x3r) return g.grid3r;
     return x3_grid(g);
+}
+template <typename R>
+int Launch<R>::x3r_grid(const Geometry &g) {
+    if constexpr (sizeof(R) != 4) {
+        return 0;
+    } else {
+        int dev = 0, sms = 0, nb = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t sm = x3r_smem(g.n3);
+        switch (g.n3) {
+            case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_x3r<64>, kX3rWarps * 32, sm); break;
+            case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_x3r<128>, kX3rWarps * 32, sm); break;
+            case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_x3r<256>, kX3rWarps * 32, sm); break;
+            default: return 0;
+        }
+        return nb * sms;
+    }
 }
 // number of partial sums the dot-product variant of the n1 pass writes
 template <typename R>
@@ -1606,7 +1681,7 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
     if constexpr (sizeof(R) == 4) {
         if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
-            const int grid = x3_epart_grid(g) * g.nb;
+            const int grid = g.grid3r;   // persistent: every case's row groups
             const size_t sm = x3r_smem(g.n3);
             const int mat = mid == X3_MID_MATERIAL;
             const float2 *fi = reinterpret_cast<const float2 *>(in);
