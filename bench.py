@@ -50,12 +50,15 @@ def kernel_bytes_per_voxel(n3: int) -> dict:
         "x2_inv": 2 * spec,                   # work spectrum in place
         "x3_c2r_law_energy_r2c": 2 * spec + 4,   # + phi
         "x2_fwd": 2 * spec,
-        # read work, u_k, u_{k-1}, w_{k-2}, w_{k-3}, x; write u_{k+1}, w_{k-1}, x, work
-        "x1_fwd_lanczos_inv": 10 * spec,
+        # read work, u_k, u_{k-1}, w_{k-2}, w_{k-3}; write u_{k+1}, w_{k-1},
+        # work; x read and written on one step in three
+        "x1_fwd_lanczos_inv": (8 + 2 / 3) * spec,
     }
 
 
-ITER_BYTES_PER_VOXEL = 196.0   # algorithmic minimum of one MINRES iteration (FP32 fields)
+# algorithmic minimum of one MINRES iteration (FP32 fields) with x read and
+# written on every step; the fused step touches x on one step in three
+ITER_BYTES_PER_VOXEL = 196.0
 
 
 def parse():

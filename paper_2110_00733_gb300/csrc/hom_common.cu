@@ -65,7 +65,7 @@ __global__ void k_scalar_start(MinresState *st, const double *partials, int np, 
     st->eps = 0.0;
     st->phibar = beta1;
     st->tol = tol;
-    st->u_delta = st->u_eps = st->u_tau = 0.0;
+    st->u_delta = st->u_eps = st->u_tau = st->u_tau1 = st->u_tau2 = 0.0;
     st->u_inv_gamma = st->u_inv_beta = 0.0;
     st->est = 1.0;
     st->k = 0;

@@ -45,6 +45,10 @@ struct MinresState {
     // applied one iteration later: w_k = (u_k u_inv_beta - u_delta w_{k-1}
     // - u_eps w_{k-2}) u_inv_gamma, x += u_tau w_k
     double u_delta, u_eps, u_inv_gamma, u_tau, u_inv_beta;
+    // tau_{k-1}, tau_{k-2}: the fused MINRES step adds tau_j w_j to x for
+    // three j at once, every third iteration (x is read and written a third
+    // as often)
+    double u_tau1, u_tau2;
     double est;        // phibar_k / beta_1
     int bodies;        // captured bodies run by the device-side loop
     int max_bodies;    // hard cap of that loop
@@ -77,6 +81,8 @@ __device__ __forceinline__ void givens_step(MinresState *st, double bn2) {
     st->u_delta = delta;
     st->u_eps = st->eps;            // epsilon_k multiplies w_{k-2}
     st->u_inv_gamma = 1.0 / gamma;
+    st->u_tau2 = st->u_tau1;
+    st->u_tau1 = st->u_tau;
     st->u_tau = tau;
     st->u_inv_beta = 1.0 / st->beta;   // v_k = u_k / beta_k in the lagged update
     st->c = cn;
@@ -172,7 +178,13 @@ __host__ __device__ constexpr int x3r_rows_per_warp(int n) { return 32 / x3r_row
 __host__ __device__ constexpr size_t x3r_in_bytes(int n) {
     return (size_t)x3r_rows_per_warp(n) * (n / 2 + 1) * 6 * sizeof(float2);
 }
-__host__ __device__ constexpr size_t x3r_phi_bytes(int n) { return (size_t)x3r_rows_per_warp(n) * n * sizeof(float); }
+// phi is prefetched with the rows except at n = 128, where its 2 KB per
+// warp would leave room for two CTAs per SM instead of three (it is read
+// from L2 there)
+__host__ __device__ constexpr bool x3r_phi_prefetch(int n) { return n != 128; }
+__host__ __device__ constexpr size_t x3r_phi_bytes(int n) {
+    return x3r_phi_prefetch(n) ? (size_t)x3r_rows_per_warp(n) * n * sizeof(float) : 0;
+}
 __host__ __device__ constexpr size_t x3r_slab_elems(int n) {
     return (size_t)(n / x3r_row_lanes(n)) * (x3r_row_lanes(n) + 1);
 }

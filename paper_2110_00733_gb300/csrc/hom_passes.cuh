@@ -483,6 +483,14 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// a twiddle factor, loaded where it is used (volatile: not hoisted out of
+// the persistent loop, where the 2 Q of them would stay live in registers)
+__device__ __forceinline__ float2 tw_load(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 template <int N>
 __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
     k_x3r(Geometry g, const float2 *__restrict__ in, float2 *__restrict__ out, int material, float lam, float mu2,
@@ -517,10 +525,12 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
         const int cs = q / gpc, rowc = (q - cs * gpc) * RW;
         const char *src = reinterpret_cast<const char *>(in + ((size_t)cs * nrows + rowc) * H * NC);
         constexpr int nin = (int)(x3r_in_bytes(N) / 16);
+#pragma unroll 1
         for (int i = lane; i < nin; i += 32) cp_async16(reinterpret_cast<char *>(inb) + 16 * i, src + 16 * i);
-        if (material) {
+        if (material && x3r_phi_prefetch(N)) {
             const char *ps = reinterpret_cast<const char *>(phi + (size_t)rowc * N);
             constexpr int nph = (int)(x3r_phi_bytes(N) / 16);
+#pragma unroll 1
             for (int i = lane; i < nph; i += 32) cp_async16(reinterpret_cast<char *>(phb) + 16 * i, ps + 16 * i);
         }
         cp_async_commit();
@@ -537,6 +547,10 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
         const size_t row = (size_t)cs * nrows + (size_t)(q - cs * gpc) * RW + rw;   // row of the stacked spectrum
         cp_async_wait_all();
         __syncwarp();
+        // this group's twiddle row j (opaque to the compiler, so that the Q
+        // twiddle addresses are formed here, not kept live across the loop)
+        const float2 *twj;
+        asm volatile("mov.b64 %0, %1;" : "=l"(twj) : "l"(tw + j));
         float2 z[3][Q];
         // ---- input, one line at a time: own frequencies k = j + P m <= N/2
         // (m < Q/2, and m = Q/2 for j = 0); the upper half m > Q/2 (and m = Q/2
@@ -570,7 +584,7 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
             dft<float, 1, Q>(z[p]);
 #pragma unroll
             for (int n = 0; n < Q; ++n) {
-                float2 w = __ldg(&tw[j * n]);
+                float2 w = tw_load(twj + (j * n - j));
                 w.y = -w.y;
                 tb[n * (P + 1) + j] = mul<float>(z[p][n], w);
             }
@@ -581,10 +595,11 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
         // ---- material law on voxels j + P m (scaled by 1/V), strain energy
         float en = 0.f;
         if (material) {
-            const float *ph_row = phb + rw * N;
+            const float *ph_row = x3r_phi_prefetch(N) ? phb + rw * N
+                                                      : phi + ((size_t)(q - cs * gpc) * RW + rw) * N;
 #pragma unroll
             for (int m = 0; m < Q; ++m) {
-                const float ph = ph_row[j + P * m];
+                const float ph = x3r_phi_prefetch(N) ? ph_row[j + P * m] : __ldg(&ph_row[j + P * m]);
                 float t[6];
 #pragma unroll
                 for (int p = 0; p < 3; ++p) {
@@ -616,7 +631,7 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
         for (int p = 0; p < 3; ++p) {
             dft<float, -1, Q>(z[p]);
 #pragma unroll
-            for (int n = 0; n < Q; ++n) tb[n * (P + 1) + j] = mul<float>(z[p][n], __ldg(&tw[j * n]));
+            for (int n = 0; n < Q; ++n) tb[n * (P + 1) + j] = mul<float>(z[p][n], tw_load(twj + (j * n - j)));
             __syncwarp();
             x3r_stage2<-1, P, Q>(tb, j, z[p]);
             __syncwarp();
@@ -954,17 +969,27 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
 //   1. finishes p = A^ u_k: forward DFT along n1 and the projector G;
 //   2. takes the Lanczos step on unnormalised vectors,
 //        u_{k+1} = p / beta_k - (alpha_k / beta_k) u_k - (beta_k / beta_{k-1}) u_{k-1},
-//      over the slot of u_{k-1}, with the weighted partial ||u_{k+1}||^2,
-//      and the lagged w / x update of step k-1 (w_{k-1} over w_{k-3});
+//      into a third buffer, with the weighted partial ||u_{k+1}||^2, and the
+//      lagged w update of step k-1 (w_{k-1} over w_{k-3});
 //   3. starts A^ u_{k+1}: G on u_{k+1} and the inverse DFT along n1, written
 //      back over the tile of the work spectrum for the next step's n2 pass.
 // p never reaches HBM, and u_k is read once per step instead of three times.
+// x is updated every third step only, with the three newest w at once,
+//   x += tau_{k-3} w_{k-3} + tau_{k-2} w_{k-2} + tau_{k-1} w_{k-1},
+// which the two w buffers still hold at that step (w_{k-3} is read before
+// w_{k-1} replaces it); the flush after the loop adds what is pending.  The
+// sum is the same as one update per step, rounded in another order.
 // ---------------------------------------------------------------------------
 template <typename R> struct LzCoef {
     R cp, cu, cv;            // 1/beta_k, -alpha_k/beta_k, -beta_k/beta_{k-1}
     R d, e, ig, tau, ib;     // lagged update of step k-1
+    R t1, t2;                // tau of the two steps before
     bool lagged;
+    bool xstep;              // this step updates x
 };
+
+// x is updated when the iterations done (the state's k) are a multiple of 3
+__host__ __device__ constexpr bool minres_xstep(int k) { return k > 0 && k % 3 == 0; }
 
 template <typename R>
 __device__ __forceinline__ LzCoef<R> lz_coef(const MinresState *st) {
@@ -979,6 +1004,9 @@ __device__ __forceinline__ LzCoef<R> lz_coef(const MinresState *st) {
     c.ig = (R)st->u_inv_gamma;
     c.tau = (R)st->u_tau;
     c.ib = (R)st->u_inv_beta;
+    c.t1 = (R)st->u_tau1;
+    c.t2 = (R)st->u_tau2;
+    c.xstep = minres_xstep(st->k);
     return c;
 }
 
@@ -1039,19 +1067,25 @@ __device__ __forceinline__ cpx<R> *x1_lanczos_tile(const Geometry &g, cpx<R> *bu
         if (LAG && c.lagged) {
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                cpx<R> a[2], b[2], xx[2];
+                cpx<R> a[2], b[2], wn[2];
                 Six<R>::load_pair(wa + i, p, a[0], a[1]);
                 Six<R>::load_pair(wb + i, p, b[0], b[1]);
-                Six<R>::load_pair(x + i, p, xx[0], xx[1]);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const cpx<R> &o = uo[2 * p + q];
-                    b[q] = mk<R>((o.x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
-                                 (o.y * c.ib - c.d * a[q].y - c.e * b[q].y) * c.ig);
-                    xx[q] = mk<R>(xx[q].x + c.tau * b[q].x, xx[q].y + c.tau * b[q].y);
+                    wn[q] = mk<R>((o.x * c.ib - c.d * a[q].x - c.e * b[q].x) * c.ig,
+                                  (o.y * c.ib - c.d * a[q].y - c.e * b[q].y) * c.ig);
                 }
-                Six<R>::store_pair(wb + i, p, b[0], b[1]);
-                Six<R>::store_pair(x + i, p, xx[0], xx[1]);
+                Six<R>::store_pair(wb + i, p, wn[0], wn[1]);
+                if (c.xstep) {
+                    cpx<R> xx[2];
+                    Six<R>::load_pair(x + i, p, xx[0], xx[1]);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        xx[q] = mk<R>(xx[q].x + c.t2 * b[q].x + c.t1 * a[q].x + c.tau * wn[q].x,
+                                      xx[q].y + c.t2 * b[q].y + c.t1 * a[q].y + c.tau * wn[q].y);
+                    Six<R>::store_pair(x + i, p, xx[0], xx[1]);
+                }
             }
         }
         gamma_apply<R>(g, ge, v);
@@ -1136,11 +1170,11 @@ __device__ __forceinline__ bool group_or(bool v, int n) {
 // 2) of the fused n1 pass, over the Krylov blocks of the CTA's tiles whose
 // case has one:
 //   w_{k-1} = (u_{k-1} / beta_{k-1} - delta w_{k-2} - eps w_{k-3}) / gamma
-// over the slot of w_{k-3}, and x += tau w_{k-1}.  The blocks are cut into
-// items of kX1LagChunk bytes; one thread brings an item's four operands
-// (u_{k-1}, w_{k-2}, w_{k-3}, x) into a ring of S stages with untiled bulk
-// copies, S items ahead, and the warps update it from shared memory and
-// store w_{k-1} and x to HBM.  The update is the same on every real number,
+// over the slot of w_{k-3}, and on every third step the deferred x update.
+// The blocks are cut into items of kX1LagChunk bytes; one thread brings an
+// item's operands (u_{k-1}, w_{k-2}, w_{k-3}, and x on an x step) into a
+// ring of S stages with untiled bulk copies, S items ahead, and the warps
+// update it from shared memory and store w_{k-1} (and x) to HBM.  The update is the same on every real number,
 // so it runs on 16-byte vectors.  Returns false after a bounded wait ran
 // out (the copies in flight have been waited for, bounded).
 template <typename R, typename LiveFrom>
@@ -1169,11 +1203,12 @@ __device__ __forceinline__ bool x1_lagged(const Geometry &g, const LzCoef<R> *sc
         const uint32_t nb = (uint32_t)(pbytes - po < kX1LagChunk ? pbytes - po : kX1LagChunk);
         const long long o = base_of(pt) + po;
         unsigned char *st = ring + (size_t)s * 4 * kX1LagChunk;
-        mbar_expect_tx(&lbar[s], 4 * nb);
+        const bool xs = scoef[pt / tpc].xstep;
+        mbar_expect_tx(&lbar[s], (xs ? 4 : 3) * nb);
         bulk_load(st, reinterpret_cast<const char *>(um) + o, nb, &lbar[s]);
         bulk_load(st + kX1LagChunk, reinterpret_cast<const char *>(wa) + o, nb, &lbar[s]);
         bulk_load(st + 2 * kX1LagChunk, reinterpret_cast<const char *>(wb) + o, nb, &lbar[s]);
-        bulk_load(st + 3 * kX1LagChunk, reinterpret_cast<const char *>(x) + o, nb, &lbar[s]);
+        if (xs) bulk_load(st + 3 * kX1LagChunk, reinterpret_cast<const char *>(x) + o, nb, &lbar[s]);
         ++issued;
         po += kX1LagChunk;
         if (po >= pbytes) {
@@ -1201,19 +1236,32 @@ __device__ __forceinline__ bool x1_lagged(const Geometry &g, const LzCoef<R> *sc
         const V *sa = su + kX1LagChunk / 16, *sb = su + 2 * (kX1LagChunk / 16), *sx = su + 3 * (kX1LagChunk / 16);
         V *gb = reinterpret_cast<V *>(reinterpret_cast<char *>(wb) + o);
         V *gx = reinterpret_cast<V *>(reinterpret_cast<char *>(x) + o);
-        for (int j = lt; j < nv; j += kX1LagThreads) {
-            V vu = su[j], va = sa[j], vb = sb[j], vx = sx[j];
-            const R *u = reinterpret_cast<const R *>(&vu);
-            const R *a = reinterpret_cast<const R *>(&va);
-            R *b = reinterpret_cast<R *>(&vb);
-            R *xx = reinterpret_cast<R *>(&vx);
+        if (c.xstep) {
+            for (int j = lt; j < nv; j += kX1LagThreads) {
+                V vu = su[j], va = sa[j], vb = sb[j], vx = sx[j], vn;
+                const R *u = reinterpret_cast<const R *>(&vu);
+                const R *a = reinterpret_cast<const R *>(&va);
+                const R *b = reinterpret_cast<const R *>(&vb);
+                R *wn = reinterpret_cast<R *>(&vn);
+                R *xx = reinterpret_cast<R *>(&vx);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                b[r] = (u[r] * c.ib - c.d * a[r] - c.e * b[r]) * c.ig;
-                xx[r] += c.tau * b[r];
+                for (int r = 0; r < NR; ++r) {
+                    wn[r] = (u[r] * c.ib - c.d * a[r] - c.e * b[r]) * c.ig;
+                    xx[r] += c.t2 * b[r] + c.t1 * a[r] + c.tau * wn[r];
+                }
+                gb[j] = vn;
+                gx[j] = vx;
             }
-            gb[j] = vb;
-            gx[j] = vx;
+        } else {
+            for (int j = lt; j < nv; j += kX1LagThreads) {
+                V vu = su[j], va = sa[j], vb = sb[j];
+                const R *u = reinterpret_cast<const R *>(&vu);
+                const R *a = reinterpret_cast<const R *>(&va);
+                R *b = reinterpret_cast<R *>(&vb);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) b[r] = (u[r] * c.ib - c.d * a[r] - c.e * b[r]) * c.ig;
+                gb[j] = vb;
+            }
         }
         co += kX1LagChunk;
         if (co >= pbytes) {
@@ -1392,6 +1440,9 @@ __global__ void k_tiles(long long n, int n1, int cols, int T, int to_tiles, cons
 
 // The lagged w / x update of the last step K; skipped when there is none
 // or the state kept the last finite iterate.
+// With three Lanczos buffers (the fused step) x has been updated every
+// third step, and the flush also adds the pending tau_j w_j of the steps
+// since the last x update (in the two w buffers).
 template <typename R>
 __global__ void __launch_bounds__(kEwThreads) k_minres_flush(long long n, long long per_case, const cpx<R> *__restrict__ ua,
                                                              const cpx<R> *__restrict__ ub, const cpx<R> *__restrict__ uc,
@@ -1410,7 +1461,10 @@ __global__ void __launch_bounds__(kEwThreads) k_minres_flush(long long n, long l
         const cpx<R> uu = u[i], a = wa[i], b = wb[i], xx = x[i];
         const cpx<R> wn = mk<R>((uu.x * ib - d * a.x - e * b.x) * ig, (uu.y * ib - d * a.y - e * b.y) * ig);
         wb[i] = wn;
-        x[i] = mk<R>(xx.x + tau * wn.x, xx.y + tau * wn.y);
+        // pending with the deferred update: w_{K-1} (r >= 1) and w_{K-2} (r = 2)
+        const int r = uc ? (K - 1) % 3 : 0;
+        const R t1 = r >= 1 ? (R)st->u_tau1 : (R)0, t2 = r == 2 ? (R)st->u_tau2 : (R)0;
+        x[i] = mk<R>(xx.x + t2 * b.x + t1 * a.x + tau * wn.x, xx.y + t2 * b.y + t1 * a.y + tau * wn.y);
     }
 }
 

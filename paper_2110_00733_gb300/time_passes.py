@@ -36,7 +36,7 @@ from paper_2110_00733_gb300 import hom  # noqa: E402
 def bytes_per_voxel(n3: int) -> dict:
     spec = 48.0 * (n3 // 2 + 1) / n3
     return {"x2_inv": 2 * spec, "x3_c2r_law_energy_r2c": 2 * spec + 4, "x2_fwd": 2 * spec,
-            "x1_fwd_lanczos_inv": 10 * spec}
+            "x1_fwd_lanczos_inv": (8 + 2 / 3) * spec}   # x read and written on one step in three
 
 
 def main():
