@@ -79,9 +79,10 @@ def parse():
     ap.add_argument("--epochs", type=int, default=24, help="warm start: training epochs")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "modbfft", "batch", "config2", "asprinted", "uniaxial", "ablation",
-                             "smoothing", "j2", "j2curve", "warmstart"],
+                             "smoothing", "j2", "j2curve", "warmstart", "stacked"],
                     help="headline: the default line; modbfft: the same cell with the MoDBFFT solver; "
-                         "batch: 16 octet cells x 6 unit strains at once")
+                         "batch: 16 octet cells x 6 unit strains at once; stacked: one against six "
+                         "stacked load cases per grid size")
     return ap.parse_args()
 
 
@@ -454,6 +455,35 @@ def run_batch(args):
                       "iterations": [[i["iterations"] for i in cell] for cell in infos]}), flush=True)
     for c in ctxs:
         c.close()
+    return 0
+
+
+def run_stacked(args):
+    """One load case (E11) against the six unit strains stacked in one
+    hom_solve, octet cells at rho = 0.15 on grids 64, 96, 128, 160, 256;
+    FP32 fields, tol 1e-6, one warm-up solve, then one timed (wall clock).
+    One line per grid and case count."""
+    import torch
+    from paper_2110_00733_gb300 import build, hom
+    build.build()
+    import rve_inputs as ri
+    torch.cuda.set_device(0)
+    for n in (64, 96, 128, 160, 256):
+        phi, _ = ri.octet(n, 0.15)
+        for ncase in (1, 6):
+            ctx = hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M)
+            macros = np.eye(6)[:ncase]
+            hom.hom_solve(ctx, macros, tol=TOL, max_it=MAX_IT)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = hom.hom_solve(ctx, macros, tol=TOL, max_it=MAX_IT)
+            dt = time.perf_counter() - t0
+            it = sum(i["iterations"] for i in info)
+            print(json.dumps({"metric": "minres_voxel_iters_per_s", "value": n ** 3 * it / dt,
+                              "unit": "voxel-iter/s", "workload": f"stacked_octet_{n}^3_rho0.15_x{ncase}",
+                              "rc": rc, "iterations": it, "s": dt,
+                              "worst_true_residual": max(i["true_residual"] for i in info)}), flush=True)
+            ctx.close()
     return 0
 
 
@@ -909,6 +939,8 @@ def main():
         return run_modbfft(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "stacked":
+        return run_stacked(args)
     return run_ours(args)
 
 
