@@ -310,7 +310,23 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 512 &&
         g.fast[1] >= 64 && g.fast[1] <= 512 && g.tile2 % 2 == 0) {
         g.tma = 1;
-        g.smem2_tma = 2ull * g.n2 * g.tile2 * cs;
+        // n2 ring stages: 3 at n2 = 256 (0.143 against 0.148 ms per pass at
+        // 256^3), 2 otherwise (at 128^3 three were slower: 0.0185 against
+        // 0.0165 ms); HOM_X2_STAGES (2..4) overrides
+        {
+            const char *e = getenv("HOM_X2_STAGES");
+            const int v = e ? atoi(e) : (g.n2 == 256 ? 3 : 2);
+            g.x2_stages = v < 2 ? 2 : (v > kX2MaxStages ? kX2MaxStages : v);
+        }
+        g.smem2_tma = (size_t)g.x2_stages * g.n2 * g.tile2 * cs;
+        // fused n1 pass: bulk L2 prefetch of each tile's u_k and u_{k-1}
+        // blocks at the tile's start (0.625 against 0.647 ms at 256^3; the
+        // two warp groups' reads of u_{k-1} then both hit L2); HOM_X1_L2PF=0
+        // turns it off
+        {
+            const char *e = getenv("HOM_X1_L2PF");
+            g.x1_l2pf = e ? atoi(e) : 1;
+        }
         g.smem1_tma = 2ull * nc * g.tile1 * g.n1 * cs;
         g.smem1d_tma = 2 * g.smem1_tma;
         if (g.smem1d_tma + 1024 > (size_t)dev_smem || g.smem2_tma + 1024 > (size_t)dev_smem) g.tma = 0;

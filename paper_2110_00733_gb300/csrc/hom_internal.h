@@ -160,6 +160,8 @@ struct Geometry {
     int grid1l_tma;         // persistent grid of the fused MINRES n1 pass (0: plain-load form)
     size_t smem2_tma, smem1_tma, smem1d_tma;
     int grid3r = 0;         // persistent grid of the register n3 pass
+    int x2_stages = 2;      // TMA ring stages of the persistent n2 pass
+    int x1_l2pf = 1;        // fused n1 pass: L2 prefetch of each tile's u_k, u_{k-1} blocks
     size_t smem1l_tma = 0;  // fused MINRES n1 pass: work-tile stages + lagged-update ring
     int x1_lag_stages = 0;  // stages of that ring (kX1LagChunk bytes of each of 4 operands)
     void *tma_cache;
@@ -240,6 +242,7 @@ constexpr int kX1Group = 192;
 constexpr int kX1LagThreads = 64;
 constexpr int kX1LagChunk = 4096;      // bytes of one operand per ring stage
 constexpr int kX1LagMaxStages = 3;
+constexpr int kX2MaxStages = 4;        // TMA ring of the persistent n2 pass
 constexpr int kEwThreads = 256;
 
 struct Mac6 { double v[6]; };

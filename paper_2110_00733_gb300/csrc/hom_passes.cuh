@@ -809,8 +809,8 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
     pdl_release();
     pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
-    const int N = g.n2, T = g.tile2;
+    __shared__ __align__(8) uint64_t bar[kX2MaxStages];
+    const int N = g.n2, T = g.tile2, NS = g.x2_stages;
     const int ntiles = g.n1 * g.nb * qtiles;   // stacked cases along k1
     const int tpc = g.n1 * qtiles;             // tiles per case
     // next tile of this CTA's sequence whose case is still iterating
@@ -823,37 +823,41 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
     const uint32_t bytes = (uint32_t)(per * sizeof(cpx<R>));
     const bool leader = threadIdx.x == 0;
     if (leader) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    // NS-stage ring: the leader keeps NS - 1 tiles in flight ahead of the one
+    // being transformed (tile j of the sequence in stage j mod NS)
     int tile = live_from(blockIdx.x);
-    if (leader && tile < ntiles) {
-        mbar_expect_tx(&bar[0], bytes);
-        tma_load_rows_3d(base, &tm, (tile % qtiles) * T, N, tile / qtiles, T * (int)sizeof(cpx<R>), &bar[0]);
-    }
+    int ahead = tile, issued = 0;   // next tile to load, tiles loaded (leader)
+    auto issue = [&]() {
+        const int q = issued % NS;
+        mbar_expect_tx(&bar[q], bytes);
+        tma_load_rows_3d(base + q * per, &tm, (ahead % qtiles) * T, N, ahead / qtiles, T * (int)sizeof(cpx<R>),
+                         &bar[q]);
+        ++issued;
+        ahead = live_from(ahead + gridDim.x);
+    };
+    if (leader)
+        for (int q = 0; q < NS - 1 && ahead < ntiles; ++q) issue();
     const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[1].tw);
     for (int i = 0; tile < ntiles; ++i) {
-        const int s = i & 1;
-        const int next = live_from(tile + gridDim.x);
-        if (leader && next < ntiles) {
-            bulk_wait_read_all();   // the store of the tile that used stage s^1 has read it
-            mbar_expect_tx(&bar[s ^ 1], bytes);
-            tma_load_rows_3d(base + (s ^ 1) * per, &tm, (next % qtiles) * T, N, next / qtiles, T * (int)sizeof(cpx<R>),
-                             &bar[s ^ 1]);
+        const int q = i % NS;
+        if (leader && ahead < ntiles) {
+            bulk_wait_read_all();   // the store of the tile that used this stage has read it
+            issue();
         }
-        const bool ok = mbar_wait_bounded(&bar[s], (i >> 1) & 1);
+        const bool ok = mbar_wait_bounded(&bar[q], (uint32_t)(i / NS) & 1u);
         if (__syncthreads_or(!ok)) {
             if (leader) {   // record, then wait (bounded) for this CTA's loads in flight
                 atomicExch(g.err, 1);
-                mbar_wait_bounded(&bar[s], (i >> 1) & 1);
-                if (next < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((i + 1) >> 1) & 1);
+                for (int m = i; m < issued; ++m) mbar_wait_bounded(&bar[m % NS], (uint32_t)(m / NS) & 1u);
                 bulk_wait_all();
             }
             return;
         }
-        cpx<R> *buf = base + s * per;
+        cpx<R> *buf = base + q * per;
         fast_fft<R, S, NF>(buf, T, T, tw);
         fence_proxy_async_smem();
         __syncthreads();
@@ -861,7 +865,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
             tma_store_rows_3d(&tm, (tile % qtiles) * T, N, tile / qtiles, buf, T * (int)sizeof(cpx<R>));
             bulk_commit();
         }
-        tile = next;
+        tile = live_from(tile + gridDim.x);
     }
     if (leader) bulk_wait_all();
 }
@@ -1277,14 +1281,16 @@ __device__ __forceinline__ bool x1_lagged(const Geometry &g, const LzCoef<R> *sc
 // persistent TMA-staged form (FP32, register FFT lengths 64..512), warp-
 // specialised.  The first g.threads1 threads (the transform group, named
 // barrier 1) take the work tiles: each comes and goes by TMA, double-
-// buffered as in k_x1_tma, and the Lanczos step reads u_k and u_{k-1} and
-// writes u_{k+1} with plain coalesced accesses.  The last kX1LagThreads
-// threads (two warps) run the lagged w / x update on the same tiles' Krylov
-// blocks, streaming u_{k-1}, w_{k-2}, w_{k-3} and x while the transform
-// group works in shared memory; the two groups share no written data (u_{k+1}
-// has its own buffer), so they never wait on each other.  (Prefetching the
-// next tile's blocks into L2 was measured to double the DRAM reads: the lines
-// were evicted before use.)  Tiles are numbered case-major over the stacked
+// buffered as in k_x1_tma, and the Lanczos step reads u_k and u_{k-1}
+// (bulk-prefetched into L2 at the tile's start) and writes u_{k+1} with
+// plain coalesced accesses.  The last kX1LagThreads threads (two warps) run
+// the lagged w update (and on one step in three the deferred x update) on
+// the same tiles' Krylov blocks, streaming u_{k-1}, w_{k-2}, w_{k-3} (and x)
+// while the transform group works in shared memory; the two groups share no
+// written data (u_{k+1} has its own buffer), so they never wait on each
+// other.  (Prefetching the next tile's blocks into L2 was measured to double
+// the DRAM reads: the lines were evicted before use; the current tile's are
+// used within microseconds.)  Tiles are numbered case-major over the stacked
 // batch; tiles of converged cases are skipped; each transform thread keeps
 // one running sum per case in shared memory, and the CTA writes one partial
 // per case (partials[case * gridDim + block]).
@@ -1354,6 +1360,10 @@ __global__ void __launch_bounds__(kX1Group + kX1LagThreads, 2)
             }
             const int cs = tile / tpc, tc = tile - cs * tpc;
             const size_t ko = (size_t)cs * g.kvec;
+            if (leader && g.x1_l2pf) {   // this tile's u_k and u_{k-1} blocks into L2 for the Lanczos step
+                bulk_prefetch_l2(uk + ko + (size_t)tc * per, bytes);
+                bulk_prefetch_l2(um + ko + (size_t)tc * per, bytes);
+            }
             const LzCoef<R> c = scoef[cs];
             Acc<R> acc;
             cpx<R> *buf = base + s * per;

@@ -331,3 +331,24 @@ def test_laminate_512_axis(hom, prec):
         for J in range(6):
             ref = laminate_closed_form([1.0, 0.2, 0.55], [0.5, 0.25, 0.25], np.eye(6)[J])
             assert np.allclose(info[J]["sigma_mean"], ref, rtol=1e-5, atol=1e-5 * E_M)
+
+
+@pytest.mark.parametrize("shape,thick", [((96, 64, 8), (48, 24, 24)), ((160, 64, 8), (80, 40, 40)),
+                                         ((64, 96, 8), (32, 16, 16))])
+def test_laminate_mixed_n1_fused_step(hom, shape, thick):
+    """Layered cells whose n1 is 96 or 160 (mixed register plans) with a
+    register-length n2: FP32 solves through the warp-specialised fused n1
+    pass, whose lagged-update items do not divide its Krylov blocks evenly
+    (18 and 30 KB per tile against 4 KB items), against the exact laminate
+    closed form (layers normal to e1, section 4's periodic setting)."""
+    from test_oracle_solver import laminate_closed_form
+    n1 = shape[0]
+    fr = [t / n1 for t in thick]
+    phi = ri.laminate(shape, thick, (1.0, 0.2, 0.55), axis=0)
+    with make(hom, phi, "fp32") as ctx:
+        rc, info = hom.hom_solve(ctx, np.eye(6), tol=1e-9, max_it=800)
+        assert rc == hom.HOM_OK
+        for J in range(6):
+            ref = laminate_closed_form([1.0, 0.2, 0.55], fr, np.eye(6)[J])
+            assert np.allclose(info[J]["sigma_mean"], ref, rtol=1e-5, atol=1e-5 * E_M)
+            assert info[J]["true_residual"] <= 1e-9
