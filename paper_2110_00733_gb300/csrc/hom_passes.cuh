@@ -507,9 +507,15 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rw = lane / P, j = lane % P;
     unsigned char *wbase = x3r_smem_raw + (size_t)warp * x3r_warp_bytes(N);
+    // per warp: [rows of the group | one slab per row | phi]; the inverse
+    // transform, which runs between reading the rows and prefetching the next
+    // group, transposes its three lines at once through 3 RW slabs laid over
+    // the first two regions
     float2 *inb = reinterpret_cast<float2 *>(wbase);                               // RW rows x H x 6
-    float *phb = reinterpret_cast<float *>(wbase + x3r_in_bytes(N));                // RW rows x N
-    float2 *tb = reinterpret_cast<float2 *>(wbase + x3r_in_bytes(N) + x3r_phi_bytes(N)) + rw * TS;
+    float2 *tb = reinterpret_cast<float2 *>(wbase + x3r_in_bytes(N)) + rw * TS;    // the forward's slab
+    float *phb = reinterpret_cast<float *>(wbase + x3r_in_bytes(N) + (size_t)RW * TS * sizeof(float2));
+    float2 *tb3 = reinterpret_cast<float2 *>(wbase) + rw * TS;                     // line p at tb3 + p RW TS
+    static_assert(2 * RW * TS * sizeof(float2) <= x3r_in_bytes(N), "three inverse slabs over rows + slab");
     const int nrows = g.n1 * g.n2;
     const int gpc = nrows / RW;                  // row groups per case (nrows is a multiple of RW)
     const int ngroups = gpc * g.nb;
@@ -577,8 +583,9 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
                 z[p][m] = (j == 0) ? (m > Q / 2 ? zc[Q - m] : z[p][m]) : got;
             }
         }
-        // ---- inverse transform (C2R part of eq. linearOp), one line's
-        // transpose at a time through the row's slab
+        // ---- inverse transform (C2R part of eq. linearOp): the three
+        // lines' transposes at once, over the rows just read
+        __syncwarp();
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             dft<float, 1, Q>(z[p]);
@@ -586,12 +593,13 @@ __global__ void __launch_bounds__(kX3rWarps * 32, N == 64 ? 5 : 3)
             for (int n = 0; n < Q; ++n) {
                 float2 w = tw_load(twj + (j * n - j));
                 w.y = -w.y;
-                tb[n * (P + 1) + j] = mul<float>(z[p][n], w);
+                tb3[p * RW * TS + n * (P + 1) + j] = mul<float>(z[p][n], w);
             }
-            __syncwarp();
-            x3r_stage2<1, P, Q>(tb, j, z[p]);
-            __syncwarp();
         }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 3; ++p) x3r_stage2<1, P, Q>(tb3 + p * RW * TS, j, z[p]);
+        __syncwarp();
         // ---- material law on voxels j + P m (scaled by 1/V), strain energy
         float en = 0.f;
         if (material) {
