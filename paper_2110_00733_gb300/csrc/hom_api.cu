@@ -1382,12 +1382,13 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     cpx<R> *wc = (cpx<R> *)ctx->bw[0], *wd = (cpx<R> *)ctx->bw[1];
     cpx<R> *x = (cpx<R> *)ctx->bx, *spec = (cpx<R> *)ctx->bspec;
     // the Givens step folded into the n1 pass (its last CTA sums one partial
-    // per CTA of a persistent grid); alpha, whose n3-pass partials number one
-    // per eight rows, in its own kernel (1024 threads reduce them faster than
-    // the n3 pass's last CTA: measured 1.556 against 1.538 ms per step at 256^3
-    // with both folded against neither; the fold is kept for the option)
+    // per CTA of a persistent grid); alpha folded into the persistent
+    // register n3 pass when HOM_FOLD_ALPHA=1 (one partial per CTA), else in
+    // its own kernel
     const Fold fold{ctx->bcnt, ctx->d_bst, (double)ctx->V};
-    const Fold fold3{nullptr, nullptr, 0.0};
+    const char *fa = std::getenv("HOM_FOLD_ALPHA");
+    const bool fold_alpha = g.x3r && fa && std::atoi(fa) == 1;
+    const Fold fold3 = fold_alpha ? Fold{ctx->bcnt, ctx->d_bst, (double)ctx->V} : Fold{nullptr, nullptr, 0.0};
     const int np3 = Launch<R>::x3_epart_grid(g);
     cudaStream_t s = ctx->stream;
     // step it of the body is step k = 1 + it (mod graph_iters, a multiple of
