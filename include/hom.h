@@ -57,6 +57,9 @@
  *     the TMA ring of the FP32 n2 pass (default 3 at n2 = 256, else 2).
  *   - HOM_X1_L2PF=0 in the environment at hom_create turns off the L2
  *     prefetch of each tile's Lanczos blocks in the fused FP32 n1 pass.
+ *   - HOM_FOLD_ALPHA=1 in the environment at the first solve folds the
+ *     MINRES alpha reduction into the register n3 pass (one launch fewer
+ *     per step; off by default).
  */
 #ifndef HOM_H
 #define HOM_H

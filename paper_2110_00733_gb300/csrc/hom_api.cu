@@ -139,6 +139,7 @@ struct hom_ctx {
     MinresState *h_state = nullptr;  // pinned
     double *d_scalar = nullptr;
     double *h_scalar = nullptr;      // pinned
+    double *tsum_part = nullptr;     // per-CTA stress sums of the FP64 n3 pass (6 x x3_grid)
     int *d_flag = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // graph is a device-side WHILE loop over the body
@@ -410,7 +411,7 @@ static void engine_free(Engine<R> &E) {
 // p = A^ v = G F C F^-1 G v (spectral vectors); optional <v, p> partials.
 template <typename R>
 static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool dot, double *partials,
-                    const MinresState *st) {
+                    const MinresState *st, double *tsum = nullptr) {
     cudaStream_t s = ctx->stream;
     Launch<R>::x1(E.g, s, X1_GAMMA_IN, v, E.spec, nullptr, nullptr, st);
     Launch<R>::x2(E.g, s, 1, E.spec, st);
@@ -439,7 +440,7 @@ static void op_spec(hom_ctx *ctx, Engine<R> &E, const cpx<R> *v, cpx<R> *p, bool
         ctx->launches += 2;
     } else {
         Launch<R>::x3(E.g, s, X3_IN_SPEC, E.spec, X3_MID_MATERIAL, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC,
-                      E.spec, E.phi, st);
+                      E.spec, E.phi, st, nullptr, Fold{}, tsum);
     }
     Launch<R>::x2(E.g, s, 0, E.spec, st);
     Launch<R>::x1(E.g, s, X1_FWD | X1_GAMMA_OUT | (dot ? X1_DOT : 0), E.spec, p, dot ? v : nullptr, partials, st);
@@ -950,6 +951,7 @@ void hom_destroy(hom_ctx *ctx) {
     cudaFree(ctx->partials);
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_scalar);
+    cudaFree(ctx->tsum_part);
     cudaFree(ctx->d_flag);
     cudaFree(ctx->d_err);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -1032,6 +1034,7 @@ static int create_impl(hom_ctx *ctx, const int grid[3], const void *phase, int i
     CU(cudaMalloc(&ctx->partials, sizeof(double) * ctx->npartials));
     CU(cudaMalloc(&ctx->d_state, sizeof(MinresState)));
     CU(cudaMalloc(&ctx->d_scalar, sizeof(double) * 8));
+    CU(cudaMalloc(&ctx->tsum_part, sizeof(double) * 6 * Launch<double>::x3_grid(ctx->e64.g)));
     CU(cudaMalloc(&ctx->d_flag, sizeof(int)));
     CU(cudaMallocHost(&ctx->h_state, sizeof(MinresState)));
     CU(cudaMallocHost(&ctx->h_scalar, sizeof(double) * 8));
@@ -1384,7 +1387,8 @@ static void capture_bbody(hom_ctx *ctx, Engine<R> &E) {
     // the Givens step folded into the n1 pass (its last CTA sums one partial
     // per CTA of a persistent grid); alpha folded into the persistent
     // register n3 pass when HOM_FOLD_ALPHA=1 (one partial per CTA), else in
-    // its own kernel
+    // its own kernel (the fold measured within noise of it: 13.18 G
+    // voxel-iterations/s either way at 256^3)
     const Fold fold{ctx->bcnt, ctx->d_bst, (double)ctx->V};
     const char *fa = std::getenv("HOM_FOLD_ALPHA");
     const bool fold_alpha = g.x3r && fa && std::atoi(fa) == 1;
@@ -1585,14 +1589,29 @@ static int max_bodies_for(const hom_ctx *ctx, int mx) { return (mx + ctx->graph_
 // ----- solve -------------------------------------------------------------------
 // ||A^ x - b^||_w / ||b^||_w in FP64 (Parseval: the real-space ratio of
 // eq. (galres)); leaves b^ - A^ x in r64.
-static int true_residual(hom_ctx *ctx, const double2 *x, const double2 *b, double2 *r, double bnorm, double *res) {
-    op_spec<double>(ctx, ctx->e64, x, r, false, nullptr, nullptr);
+// r = b - A^ x in FP64 and |r| / |b|.  With tau (elastic Galerkin operator
+// only), also the mean over the voxels of the stress phi C_m : eps~ formed by
+// its n3 pass, eps~ = F^-1 G x: with the constant part this is the mean stress
+// of the solution x (tau[c], Mandel, units of E), taken here instead of in a
+// separate pass over the spectrum.
+static int true_residual(hom_ctx *ctx, const double2 *x, const double2 *b, double2 *r, double bnorm, double *res,
+                         double *tau = nullptr) {
+    const bool ts = tau && !ctx->tangent_op;
+    op_spec<double>(ctx, ctx->e64, x, r, false, nullptr, nullptr, ts ? ctx->tsum_part : nullptr);
     spec_residual64(ctx->e64.g, ctx->stream, b, r, r, ctx->partials);
     reduce_to(ctx->stream, ctx->partials, ew_blocks(6 * ctx->S), ctx->d_scalar);
     ctx->launches += 2;
-    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ts) {
+        const int n3 = Launch<double>::x3_grid(ctx->e64.g);
+        for (int c = 0; c < 6; ++c) reduce_to(ctx->stream, ctx->tsum_part + (size_t)c * n3, n3, ctx->d_scalar + 1 + c);
+        ctx->launches += 6;
+    }
+    CU(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, (ts ? 7 : 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     *res = (bnorm > 0) ? std::sqrt(*ctx->h_scalar) / bnorm : 0.0;
+    if (ts)
+        for (int c = 0; c < 6; ++c) tau[c] = ctx->h_scalar[1 + c] / (double)ctx->V;
     return HOM_OK;
 }
 
@@ -1704,11 +1723,19 @@ static int solve_case_modb(hom_ctx *ctx, int icase, const double *m, double tol,
 
 // mean stress <phi C_m : (E_bar + e~)> in FP64, timing, info record
 static int finish_case(hom_ctx *ctx, int icase, const double *m, double2 *x, hom_solve_info *inf, int status,
-                       hom_solve_info *info) {
+                       hom_solve_info *info, const double *tau = nullptr) {
     cudaStream_t s = ctx->stream;
     const double r2 = std::sqrt(2.0);
     double sig[6];
-    if (ctx->solver != HOM_SOLVER_MODBFFT_CG) {
+    if (ctx->solver != HOM_SOLVER_MODBFFT_CG && tau) {
+        // <sigma> = phibar C_m : E_bar + <phi C_m : eps~>, the second term from
+        // the n3 pass of the last true residual (taken on this x)
+        const double trE = m[0] + m[1] + m[2];
+        for (int c = 0; c < 6; ++c)
+            sig[c] = ctx->phibar * ((c < 3 ? ctx->lam * trE : 0.0) + 2.0 * ctx->mu * m[c]) + tau[c];
+        CU(cudaEventRecord(ctx->ev1, s));
+        CU(cudaEventSynchronize(ctx->ev1));
+    } else if (ctx->solver != HOM_SOLVER_MODBFFT_CG) {
         // <sigma> = phibar C_m : E_bar + C_m : <phi eps~>, with <phi eps~> by
         // Parseval from phi^ and the projected spectrum: one point-wise pass
         const int nb = Launch<double>::phi_dot(ctx->e64.g, s, x, ctx->phihat, ctx->partials);
@@ -1940,6 +1967,10 @@ struct Chunk {
     std::vector<double> M, bnorm, tres, stol, est;
     std::vector<int> status, live, solvable, mi, its, sts;
     std::vector<hom_solve_info> inf;
+    // per case: the mean of phi C_m : eps~ at the last true residual (tau_ok:
+    // taken on the current x)
+    std::vector<double> tau;
+    std::vector<int> tau_ok;
 };
 
 static int chunk_prepare(Chunk &ch) {
@@ -1963,6 +1994,8 @@ static int chunk_prepare(Chunk &ch) {
     ch.its.assign(nb, 0);
     ch.sts.assign(nb, 0);
     ch.inf.assign(nb, hom_solve_info{});
+    ch.tau.assign(6 * nb, 0.0);
+    ch.tau_ok.assign(nb, 0);
     ch.sw = 0;
     CU(cudaEventRecord(ctx->ev0, s));
     for (int j = 0; j < nb; ++j) {
@@ -2008,6 +2041,7 @@ static int chunk_prepare(Chunk &ch) {
         }
         if (ch.bnorm[j] / std::sqrt((double)ctx->V) <= kRhsZero * ntau) {
             ch.inf[j].sweeps = 0;   // b vanishes up to round-off: zero fluctuation, 0 iterations
+            ch.tau_ok[j] = 1;       // x = 0: no fluctuation stress
             continue;
         }
         ch.live[j] = 1;
@@ -2021,8 +2055,9 @@ static int chunk_prepare(Chunk &ch) {
             mandel_scale64(ctx->V, s, st, std::sqrt(2.0));
             real_to_spec<double>(ctx, ctx->e64, st, X3_MID_NONE, true, x);
             ctx->launches += 2;
-            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
+            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j], &ch.tau[6 * j]);
             if (rc) return rc;
+            ch.tau_ok[j] = 1;
         } else if (ch.warm) {
             // FP32 fields: projection and starting residual with the FP32
             // operator; a start already within kWarmFp64Below gets the FP64 one
@@ -2041,8 +2076,9 @@ static int chunk_prepare(Chunk &ch) {
             CU(cudaStreamSynchronize(s));
             ch.tres[j] = std::sqrt(*ctx->h_scalar) / ch.bnorm[j];
             if (ch.tres[j] < kWarmFp64Below) {
-                rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
+                rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j], &ch.tau[6 * j]);
                 if (rc) return rc;
+                ch.tau_ok[j] = 1;
             }
         } else {   // x = 0: r = b
             CU(cudaMemcpyAsync(r, b, sizeof(double2) * nc, cudaMemcpyDeviceToDevice, s));
@@ -2116,8 +2152,9 @@ static int chunk_sweep_end(Chunk &ch) {
         ch.inf[j].est_residual = ch.est[j] * ch.tres[j];   // relative to ||b||
         ch.inf[j].sweeps = ch.sw;
         const double prev = ch.tres[j];
-        rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
+        rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j], &ch.tau[6 * j]);
         if (rc) return rc;
+        ch.tau_ok[j] = 1;
         if (ch.sts[j] == HOM_ENAN) {
             ch.status[j] = HOM_ENAN;
             ch.live[j] = 0;
@@ -2127,7 +2164,7 @@ static int chunk_sweep_end(Chunk &ch) {
             // an FP32 sweep past the accuracy FP32 fields can carry: take it back and stop
             spec_f2d_acc(nc, s, (const float2 *)ctx->brhs + j * nc, x, -1.0);
             ctx->launches += 1;
-            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j]);
+            rc = true_residual(ctx, x, b, r, ch.bnorm[j], &ch.tres[j], &ch.tau[6 * j]);
             if (rc) return rc;
             ch.status[j] = HOM_NOT_CONVERGED;
             ch.live[j] = 0;
@@ -2149,7 +2186,8 @@ static int chunk_finish(Chunk &ch, int *worst) {
             ch.inf[j].true_residual = ch.tres[j];
             if (ch.status[j] == HOM_OK && ch.tres[j] > ch.tol) ch.status[j] = HOM_NOT_CONVERGED;
         }
-        int rc = finish_case(ctx, k, &ch.M[6 * j], ctx->x64[k], &ch.inf[j], ch.status[j], ch.info ? ch.info + k : nullptr);
+        int rc = finish_case(ctx, k, &ch.M[6 * j], ctx->x64[k], &ch.inf[j], ch.status[j], ch.info ? ch.info + k : nullptr,
+                             ch.tau_ok[j] ? &ch.tau[6 * j] : nullptr);
         if (rc < 0) return rc;
         if (rc > *worst) *worst = rc;
     }

@@ -268,9 +268,12 @@ template <typename R> struct Launch {
     // epart (6-component spectra only): per-CTA sums of the strain energy
     // e : C : e of the scaled real-space input (x3_grid(g) values).
     // fold: the alpha step folded into the pass (see Fold in hom_passes.cuh)
+    // tsum (shared-memory pass with the material law only): per-CTA partial
+    // sums over the voxels of the six stress components it forms,
+    // tsum[c * x3_grid(g) + block]
     static void x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro_mandel, double scale, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{});
+                   const MinresState *state, double *epart = nullptr, Fold fold = Fold{}, double *tsum = nullptr);
     // n2 pass, in place on the half spectrum
     static void x2(const Geometry &g, cudaStream_t st, int inverse, cpx<R> *spec, const MinresState *state);
     // n1 pass: in -> out (may alias), optional projector before / after, and

@@ -276,7 +276,7 @@ template <typename R, int NF, int NP>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
-                                        double *__restrict__ epart, Fold fold) {
+                                        double *__restrict__ epart, Fold fold, double *__restrict__ tsum) {
     pdl_release();
     pdl_wait();   // predecessor complete (programmatic launch in the MINRES graph)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -350,6 +350,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
     // e = F^-1 G u this is <u, A^ u> / V, the MINRES alpha numerator, so the
     // n1 pass needs no dot product with u
     R en = 0;   // non-negative terms: a short per-thread sum in R is accurate to ~1e-6
+    double ts[6] = {0, 0, 0, 0, 0, 0};   // stress sums (tsum)
     for (int r = 0; r < nr; ++r) {
         const int vbase = (row0 + r) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) {
@@ -373,6 +374,10 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) t[c] = ph * ((c < 3 ? tr : (R)0) + mu2 * t[c]);
+                if (tsum) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) ts[c] += (double)t[c];
+                }
                 if constexpr (NC == 10) {
                     // MoDBFFT penalty vector on the empty phase: chi_v g, eq. (modbfftfop)
                     const R chi = (ph == (R)0) ? (R)1 : (R)0;
@@ -390,6 +395,13 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
 #pragma unroll
                 for (int p = 0; p < NP; ++p) q[p * ROWS] = mk<R>(t[2 * p], t[2 * p + 1]);
             }
+        }
+    }
+    if (tsum) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double sum = block_sum(ts[c]);
+            if (threadIdx.x == 0) tsum[(size_t)c * gridDim.x + blockIdx.x] = sum;
         }
     }
     if (epart) {
@@ -1749,9 +1761,9 @@ int Launch<R>::tma_grids(Geometry &g) {
 template <typename R>
 void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *in, int mid, double lam, double mu,
                    const double *macro, double scl, int out_mode, void *out, const R *phi,
-                   const MinresState *state, double *epart, Fold fold) {
+                   const MinresState *state, double *epart, Fold fold, double *tsum) {
     if constexpr (sizeof(R) == 4) {
-        if (g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
+        if (!tsum && g.x3r && g.nc == 6 && in_mode == X3_IN_SPEC && out_mode == X3_OUT_SPEC && scl == 1.0 &&
             (mid == X3_MID_MATERIAL || mid == X3_MID_NONE)) {
             const int grid = g.grid3r;   // persistent: every case's row groups
             const size_t sm = x3r_smem(g.n3);
@@ -1776,10 +1788,10 @@ void Launch<R>::x3(const Geometry &g, cudaStream_t st, int in_mode, const void *
 #define HOM_X3(NF)                                                                                          \
     if (g.nc == 10)                                                                                         \
         launch_k(g.pdl, k_x3<R, NF, 5>, grid, g.threads3, g.smem3, st, g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, \
-                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}); \
+                                                            (R)scl, out_mode, out, phi, state, nullptr, Fold{}, nullptr); \
     else                                                                                                    \
         launch_k(g.pdl, k_x3<R, NF, 3>, grid, g.threads3, g.smem3, st, g, in_mode, in, mid, (R)lam, (R)(2.0 * mu), m, \
-                                                            (R)scl, out_mode, out, phi, state, epart, fold)
+                                                            (R)scl, out_mode, out, phi, state, epart, fold, tsum)
     HOM_FAST_SWITCH(g.fast[2], HOM_X3)
 #undef HOM_X3
 }
