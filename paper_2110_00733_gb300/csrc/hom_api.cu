@@ -237,7 +237,7 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     g.nc = nc;
     int rows, t2, t1;
     if (g.fast[2]) {
-        rows = 48 / (np * (g.n3 / fast_elems(g.n3)));
+        rows = 48 / (np * (g.n3 / fast_elems_n3r<R>(g.n3)));
         rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
     } else {
         rows = 16;
@@ -268,7 +268,7 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     auto clampt = [](int v) { return v < 128 ? 128 : (v > 512 ? 512 : v); };
     const int es3 = (np * rows) | 1;   // element stride of the n3 tile (odd)
     if (g.fast[2]) {
-        g.threads3 = np * rows * (g.n3 / fast_elems(g.n3));
+        g.threads3 = np * rows * (g.n3 / fast_elems_n3r<R>(g.n3));
         g.smem3 = ((size_t)es3 * g.n3 + g.n3 / 16 + 1) * cs;   // + one pad slot per 16 elements
     } else {
         g.threads3 = clampt(round32(np * rows * g.n3 / 16));

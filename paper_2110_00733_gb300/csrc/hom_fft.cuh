@@ -9,6 +9,7 @@
 // butterflies (R in {2,3,4,5,8,16}) held in registers; twiddles come from a
 // per-axis table w[t] = exp(-2 pi i t / N) computed on the host in double.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -146,13 +147,63 @@ template <typename R, int S> __device__ __forceinline__ void dft16(cpx<R> *v) {
     }
 }
 
+// exp(S 2 pi i e / N) for N = 12 or 20 (e known at compile time after
+// unrolling): cosines of multiples of 30 and 18 degrees
+template <typename R, int N> __device__ __forceinline__ R cos_n(int e) {
+    e %= N;
+    if constexpr (N == 12) {
+        const R c30 = (R)0.86602540378443864676;   // cos(pi/6)
+        const R t[12] = {1, c30, (R)0.5, 0, (R)-0.5, -c30, -1, -c30, (R)-0.5, 0, (R)0.5, c30};
+        return t[e];
+    } else {
+        const R a = (R)0.95105651629515357212, b = (R)0.80901699437494742410;   // cos(pi/10), cos(pi/5)
+        const R c = (R)0.58778525229247312917, d = (R)0.30901699437494742410;   // cos(3pi/10), cos(2pi/5)
+        const R t[20] = {1, a, b, c, d, 0, -d, -c, -b, -a, -1, -a, -b, -c, -d, 0, d, c, b, a};
+        return t[e];
+    }
+}
+template <typename R, int S, int N> __device__ __forceinline__ cpx<R> w_n(int e) {
+    // sin(2 pi e / N) = cos(2 pi (e - N/4) / N)
+    return mk<R>(cos_n<R, N>(e), (R)S * cos_n<R, N>(e + 3 * N / 4));
+}
+
+// Composite DFT of length N1 N2 in registers (Cooley-Tukey): DFT-N1 over n1
+// for each n2 on x[N2 n1 + n2], the twiddle w_N^(n2 k1), DFT-N2 over n2 for
+// each k1, output X[k1 + N1 k2].
+template <typename R, int S, int N1, int N2> __device__ __forceinline__ void dft_ct(cpx<R> *v);
+
 template <typename R, int S, int RAD> __device__ __forceinline__ void dft(cpx<R> *v) {
     if constexpr (RAD == 2) dft2<R, S>(v[0], v[1]);
     else if constexpr (RAD == 3) dft3<R, S>(v);
     else if constexpr (RAD == 4) dft4<R, S>(v);
     else if constexpr (RAD == 5) dft5<R, S>(v);
     else if constexpr (RAD == 8) dft8<R, S>(v);
+    else if constexpr (RAD == 12) dft_ct<R, S, 4, 3>(v);
+    else if constexpr (RAD == 20) dft_ct<R, S, 4, 5>(v);
     else dft16<R, S>(v);
+}
+
+template <typename R, int S, int N1, int N2> __device__ __forceinline__ void dft_ct(cpx<R> *v) {
+    constexpr int N = N1 * N2;
+    cpx<R> y[N];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+        cpx<R> a[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) a[n1] = v[N2 * n1 + n2];
+        dft<R, S, N1>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) y[N2 * k1 + n2] = (n2 * k1 == 0) ? a[k1] : mul<R>(a[k1], w_n<R, S, N>(n2 * k1));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        cpx<R> b[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) b[n2] = y[N2 * k1 + n2];
+        dft<R, S, N2>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k1 + N1 * k2] = b[k2];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -237,11 +288,26 @@ template <> struct FastPlan<160> { static constexpr int E = 20, NS = 4, R0 = 4, 
 template <> struct FastPlan<256> { static constexpr int E = 16, NS = 2, R0 = 16, R1 = 16, R2 = 1, R3 = 1; };
 template <> struct FastPlan<512> { static constexpr int E = 16, NS = 3, R0 = 16, R1 = 16, R2 = 2, R3 = 1; };
 
+// The n3 pass (shared-memory form) takes 96 and 160 in two stages instead
+// of four, with radix-12 and radix-20 butterflies in registers (24 and 40
+// elements per thread): 96 = 8 12, 160 = 8 20.  Other lengths as FastPlan.
+template <int N> struct FastPlanN3 : FastPlan<N> {};
+template <> struct FastPlanN3<96>  { static constexpr int E = 24, NS = 2, R0 = 8, R1 = 12, R2 = 1, R3 = 1; };
+template <> struct FastPlanN3<160> { static constexpr int E = 40, NS = 2, R0 = 8, R1 = 20, R2 = 1, R3 = 1; };
+
 __host__ __device__ constexpr bool is_fast_length(int n) {
     return n == 8 || n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256 || n == 512;
 }
 __host__ __device__ constexpr int fast_elems(int n) {
     return (n == 8 || n == 32 || n == 64) ? 8 : (n == 96 ? 12 : (n == 160 ? 20 : 16));
+}
+__host__ __device__ constexpr int fast_elems_n3(int n) { return n == 96 ? 24 : (n == 160 ? 40 : fast_elems(n)); }
+// the n3 pass's plan by precision: the two-stage plans in FP32 only (FP64
+// elements would not fit in registers)
+template <typename R, int N>
+using PlanN3 = typename std::conditional<sizeof(R) == 4, FastPlanN3<N>, FastPlan<N>>::type;
+template <typename R> __host__ __device__ constexpr int fast_elems_n3r(int n) {
+    return sizeof(R) == 4 ? fast_elems_n3(n) : fast_elems(n);
 }
 
 // Position of element e of a line in a tile with element stride ES; with
@@ -256,10 +322,10 @@ __device__ __forceinline__ void group_sync(int n) {
     else asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
 }
 
-template <typename R, int S, int N, int RAD, int NS_BEFORE, int PAD>
+template <typename R, int S, int N, int RAD, int NS_BEFORE, int PAD, typename Plan = FastPlan<N>>
 __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, const cpx<R> *__restrict__ tw,
                                            int nsync) {
-    constexpr int E = FastPlan<N>::E;
+    constexpr int E = Plan::E;
     constexpr int BPT = E / RAD;
     constexpr int nb = N / RAD;
     constexpr int jstep = N / E;
@@ -297,15 +363,14 @@ __device__ __forceinline__ void fast_stage(cpx<R> *buf, int ES, int l, int j0, c
 // exactly L * N / E threads (every thread takes part in every barrier);
 // otherwise threads 0 .. nsync-1 (= L * N / E) run it and synchronise on
 // named barrier 1, and the CTA's other warps are free for other work.
-template <typename R, int S, int N, int PAD = 0>
+template <typename R, int S, int N, int PAD = 0, typename P = FastPlan<N>>
 __device__ __forceinline__ void fast_fft(cpx<R> *buf, int L, int ES, const cpx<R> *__restrict__ tw, int nsync = 0) {
-    using P = FastPlan<N>;
     const int l = (int)threadIdx.x % L;
     const int j0 = (int)threadIdx.x / L;
-    fast_stage<R, S, N, P::R0, 1, PAD>(buf, ES, l, j0, tw, nsync);
-    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD>(buf, ES, l, j0, tw, nsync);
-    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD>(buf, ES, l, j0, tw, nsync);
-    if constexpr (P::NS > 3) fast_stage<R, S, N, P::R3, P::R0 * P::R1 * P::R2, PAD>(buf, ES, l, j0, tw, nsync);
+    fast_stage<R, S, N, P::R0, 1, PAD, P>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 1) fast_stage<R, S, N, P::R1, P::R0, PAD, P>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 2) fast_stage<R, S, N, P::R2, P::R0 * P::R1, PAD, P>(buf, ES, l, j0, tw, nsync);
+    if constexpr (P::NS > 3) fast_stage<R, S, N, P::R3, P::R0 * P::R1 * P::R2, PAD, P>(buf, ES, l, j0, tw, nsync);
 }
 
 }  // namespace hom

@@ -198,7 +198,7 @@ int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, 
     auto clampt = [](int v) { return v < 128 ? 128 : (v > 512 ? 512 : v); };
     int rows, t2, t1;
     if (g.fast[2]) {
-        rows = 48 / (3 * (g.n3 / fast_elems(g.n3)));
+        rows = 48 / (3 * (g.n3 / fast_elems_n3(g.n3)));
         rows = rows < 1 ? 1 : (rows > 64 ? 64 : rows);
     } else {
         rows = 16;
@@ -221,7 +221,7 @@ int hom_apply_noalloc(const int grid[3], const float *phi, double E, double nu, 
     g.tile1 = t1;
     const int es3 = (3 * rows) | 1;
     if (g.fast[2]) {
-        g.threads3 = 3 * rows * (g.n3 / fast_elems(g.n3));
+        g.threads3 = 3 * rows * (g.n3 / fast_elems_n3(g.n3));
         g.smem3 = ((size_t)es3 * g.n3 + g.n3 / 16 + 1) * cs;
     } else {
         g.threads3 = clampt(round32(3 * rows * g.n3 / 16));

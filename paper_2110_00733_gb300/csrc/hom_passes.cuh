@@ -225,10 +225,10 @@ __device__ __forceinline__ void gamma_at(const Geometry &g, int k1, int k2, int 
 // result.
 // nsync != 0 (fast engine only): the first nsync threads run it on named
 // barrier 1.
-template <typename R, int S, int NF, int PAD = 0>
+template <typename R, int S, int NF, int PAD = 0, typename Plan = FastPlan<NF>>
 __device__ __forceinline__ cpx<R> *run_fft(cpx<R> *buf, cpx<R> *buf2, int L, int ES, const AxisPlan &p, int nsync = 0) {
     if constexpr (NF > 0) {
-        fast_fft<R, S, NF, PAD>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw), nsync);
+        fast_fft<R, S, NF, PAD, Plan>(buf, L, ES, reinterpret_cast<const cpx<R> *>(p.tw), nsync);
         return buf;
     } else {
         return fft_lines<R, S>(buf, buf2, L, ES, p);
@@ -266,6 +266,8 @@ template <> struct Six<double> {
 // the same, except for the register FFT lengths with more than 16 elements
 // per thread (160: 20), which keep their elements in registers instead
 #define HOM_PASS_BOUNDS_NF(R, NF) __launch_bounds__(512, (sizeof(R) == 4 && fast_elems(NF) <= 16) ? 2 : 1)
+// the n3 pass, by its own plan's elements per thread
+#define HOM_PASS_BOUNDS_N3(R, NF) __launch_bounds__(512, (sizeof(R) == 4 && fast_elems_n3(NF) <= 16) ? 2 : 1)
 
 // ---------------------------------------------------------------------------
 // n3 pass.  A CTA owns rows (k1,k2) [row0, row0+rows3); lines are the three
@@ -273,7 +275,7 @@ template <> struct Six<double> {
 // Z = X_2p + i X_2p+1, line index p*rows3 + r.
 // ---------------------------------------------------------------------------
 template <typename R, int NF, int NP>
-__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
+__global__ void HOM_PASS_BOUNDS_N3(R, NF) k_x3(Geometry g, int in_mode, const void *__restrict__ in_, int mid, R lam,
                                         R mu2, Mac6 mac, R scl, int out_mode, void *__restrict__ out_,
                                         const R *__restrict__ phi, const MinresState *state,
                                         double *__restrict__ epart, Fold fold, double *__restrict__ tsum) {
@@ -322,7 +324,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
             }
         }
         __syncthreads();
-        cpx<R> *res = run_fft<R, 1, NF, PAD>(buf, buf2, L, ES, g.ax[2]);
+        cpx<R> *res = run_fft<R, 1, NF, PAD, PlanN3<R, NF>>(buf, buf2, L, ES, g.ax[2]);
         if (res != buf) {   // generic engine ended in the second buffer
             for (int i = threadIdx.x; i < N * ES; i += blockDim.x) buf[i] = res[i];
             __syncthreads();
@@ -418,7 +420,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x3(Geometry g, int in_mode, const vo
     if (out_mode == X3_OUT_REAL) return;
     // rows beyond nrows hold zeros already (their inputs were zero)
     __syncthreads();
-    cpx<R> *res = run_fft<R, -1, NF, PAD>(buf, buf2, L, ES, g.ax[2]);
+    cpx<R> *res = run_fft<R, -1, NF, PAD, PlanN3<R, NF>>(buf, buf2, L, ES, g.ax[2]);
     // unpack the two real transforms of each packed line:
     //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i)
     cpx<R> *spec = reinterpret_cast<cpx<R> *>(out_);
