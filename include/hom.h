@@ -338,8 +338,10 @@ int hom_apply_spectrum(hom_ctx *ctx, const void *in_spectrum, void *out_spectrum
  * order: n2 inverse, n3 pass (C2R + material law with the strain-energy sums
  * of alpha + R2C), alpha reduction, n2 forward, fused n1 pass (forward +
  * projector, Lanczos step + norm, lagged w/x update, projector + inverse of
- * the next Lanczos vector), Givens step.  Returns the number of entries
- * written (<= nmax). */
+ * the next Lanczos vector), Givens step.  The fused n1 pass is launched a
+ * multiple of 3 times (reps rounded up), cycling through the three steps of
+ * its deferred x update (x is read and written on one of them), and ms[4]
+ * is their mean.  Returns the number of entries written (<= nmax). */
 int hom_time_kernels(hom_ctx *ctx, int reps, double *ms, int nmax);
 
 /* Average device time in milliseconds of the kernels of the J2 Newton
