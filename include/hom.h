@@ -54,7 +54,7 @@
  *     while its predecessor drains and waits for it before touching
  *     memory); off by default, where it measured slower.
  *   - HOM_X2_STAGES=2..4 in the environment at hom_create sets the depth of
- *     the TMA ring of the FP32 n2 pass (default 3 at n2 = 256, else 2).
+ *     the TMA ring of the FP32 n2 pass (default 3 at n2 >= 256, else 2).
  *   - HOM_X1_L2PF=0 in the environment at hom_create turns off the L2
  *     prefetch of each tile's Lanczos blocks in the fused FP32 n1 pass.
  *   - HOM_FOLD_ALPHA=1 in the environment at the first solve folds the

@@ -311,12 +311,13 @@ static int set_shapes(hom_ctx *ctx, Geometry &g, int nc) {
     if (sizeof(R) == 4 && ctx->staging == 0 && tma_available() && g.fast[0] >= 64 && g.fast[0] <= 512 &&
         g.fast[1] >= 64 && g.fast[1] <= 512 && g.tile2 % 2 == 0) {
         g.tma = 1;
-        // n2 ring stages: 3 at n2 = 256 (0.143 against 0.148 ms per pass at
-        // 256^3), 2 otherwise (at 128^3 three were slower: 0.0185 against
-        // 0.0165 ms); HOM_X2_STAGES (2..4) overrides
+        // n2 ring stages: 3 at n2 >= 256 (0.143 against 0.148 ms per pass at
+        // 256^3; 0.280 against 0.36 ms on 256 x 512 x 256), 2 below (at 128^3
+        // three were slower: 0.0185 against 0.0165 ms); HOM_X2_STAGES (2..4)
+        // overrides
         {
             const char *e = getenv("HOM_X2_STAGES");
-            const int v = e ? atoi(e) : (g.n2 == 256 ? 3 : 2);
+            const int v = e ? atoi(e) : (g.n2 >= 256 ? 3 : 2);
             g.x2_stages = v < 2 ? 2 : (v > kX2MaxStages ? kX2MaxStages : v);
         }
         g.smem2_tma = (size_t)g.x2_stages * g.n2 * g.tile2 * cs;
