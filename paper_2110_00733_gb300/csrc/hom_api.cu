@@ -656,8 +656,9 @@ static int engine_init_modb(hom_ctx *ctx, Engine<R> &E) {
 
 // out3 = A^alpha(u3), eq. (modbfftfop); optional <dotv, out3> partials
 template <typename R>
-static void op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, const cpx<R> *dotv, double *partials,
-                    const MinresState *st) {
+static int op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, const cpx<R> *dotv, double *partials,
+                   const MinresState *st) {
+    // returns the number of dot partials written (with dotv)
     cudaStream_t s = ctx->stream;
     const Geometry &g = E.gm;
     Launch<R>::modb_expand(g, s, ctx->alpha, 1, u, E.spec10, 10, st);
@@ -666,9 +667,16 @@ static void op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, co
     Launch<R>::x3(g, s, X3_IN_SPEC, E.spec10, X3_MID_MODB, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec10,
                   E.phi, st);
     Launch<R>::x2(g, s, 0, E.spec10, st);
+    // the forward n1 pass with the contraction fused where it is TMA-staged
+    int np = Launch<R>::x1_modb_contract(g, s, E.spec10, out, dotv, partials, ctx->npartials, st);
+    if (np > 0) {
+        ctx->launches += 6;
+        return np;
+    }
     Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, st);
     Launch<R>::modb_contract(g, s, E.spec10, out, dotv, partials, st);
     ctx->launches += 7;
+    return Launch<R>::ew_grid(g.S);
 }
 
 // b3 = -F{C : E_bar} . xi, eq. (modbfftfrhs) with sigma_bar = 0
@@ -715,8 +723,8 @@ static int build_cg_graph(hom_ctx *ctx, Engine<R> &E) {
     CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     const long long before = ctx->launches;
     for (int it = 0; it < 4; ++it) {
-        op_modb<R>(ctx, E, p, q, p, ctx->partials, flags);
-        scalar_cg_alpha(ctx->stream, ctx->d_cg, ctx->partials, np);
+        const int npq = op_modb<R>(ctx, E, p, q, p, ctx->partials, flags);
+        scalar_cg_alpha(ctx->stream, ctx->d_cg, ctx->partials, npq);
         Launch<R>::cg_xr(E.g, ctx->stream, lam_b, mu_b, x, r, p, q, z, ctx->d_cg, ctx->partials);
         scalar_cg_beta(ctx->stream, ctx->d_cg, ctx->partials, np);
         Launch<R>::cg_p(E.g, ctx->stream, p, z, ctx->d_cg);

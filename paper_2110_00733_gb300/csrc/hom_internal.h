@@ -280,6 +280,13 @@ template <typename R> struct Launch {
     // the weighted partial sum <dotv, out> per CTA
     static void x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *in, cpx<R> *out,
                    const cpx<R> *dotv, double *partials, const MinresState *state);
+    // MoDBFFT: forward n1 pass of the 10-component spectrum in10 with the
+    // contraction to 3 components fused (out3 = tau xi + g, eq. modbfftfop;
+    // with dot3, the weighted <dot3, out3> partials).  Returns the number of
+    // partials written, or 0 without launching where the fused form does not
+    // apply (not the TMA-staged FP32 pass, or more partials than max_partials).
+    static int x1_modb_contract(const Geometry &g, cudaStream_t st, const cpx<R> *in10, cpx<R> *out3,
+                                const cpx<R> *dot3, double *partials, int max_partials, const MinresState *state);
     // MINRES step k on unnormalised Lanczos vectors u_j = beta_j v_j, p = A u_k:
     //   um <- (p - alpha u_k - beta_k^2/beta_{k-1} um) / beta_k   (= u_{k+1}),
     //   weighted partial ||u_{k+1}||^2, and the lagged update of step k-1

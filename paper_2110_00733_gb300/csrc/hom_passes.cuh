@@ -892,11 +892,46 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x2_tma(Geometry g, const __grid_cons
     if (leader) bulk_wait_all();
 }
 
+// MoDBFFT contraction at frequency (k1, k2, k3) of the 10-component
+// forward transform t (the stress tau and the penalty vector g), eq.
+// (modbfftfop): r = tau xi + g with xi = i 2 pi q, q the integer frequency (0
+// on a Nyquist index); r = 0 at xi = 0.  The same arithmetic as the
+// contraction kernel of the MoDBFFT operator.
+template <typename R>
+__device__ __forceinline__ void modb_contract_at(const Geometry &g, int k1, int k2, int k3, const cpx<R> *t,
+                                                 cpx<R> r[3]) {
+    const int ks[3] = {k1, k2, k3}, ns[3] = {g.n1, g.n2, g.n3};
+    double q[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int n = ns[p], k = ks[p];
+        q[p] = ((n & 1) == 0 && 2 * k == n) ? 0.0 : (double)((2 * k < n) ? k : k - n);
+    }
+    r[0] = r[1] = r[2] = mk<R>(0, 0);
+    if (q[0] == 0.0 && q[1] == 0.0 && q[2] == 0.0) return;
+    const R tp = (R)6.28318530717958647692;
+    const R r2 = (R)0.70710678118654752440;
+    const R sv[3] = {tp * (R)q[0], tp * (R)q[1], tp * (R)q[2]};
+    const cpx<R> T[3][3] = {{t[0], scale<R>(t[5], r2), scale<R>(t[4], r2)},
+                            {scale<R>(t[5], r2), t[1], scale<R>(t[3], r2)},
+                            {scale<R>(t[4], r2), scale<R>(t[3], r2), t[2]}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const cpx<R> a = add<R>(add<R>(scale<R>(T[i][0], sv[0]), scale<R>(T[i][1], sv[1])), scale<R>(T[i][2], sv[2]));
+        r[i] = add<R>(mk<R>(-a.y, a.x), t[6 + i]);
+    }
+}
+
 template <typename R, int NF>
+// With out3 (MoDBFFT, 10 components, forward): instead of storing the
+// transformed tile, contract each frequency to the 3-component result
+// (modb_contract_at) and write it to out3, with the weighted dot product
+// against dot3 (if given) in the partials.
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const __grid_constant__ CUtensorMap tin,
                                             const __grid_constant__ CUtensorMap tout,
                                             const __grid_constant__ CUtensorMap tdot, double *__restrict__ partials,
-                                            const MinresState *state) {
+                                            const MinresState *state, cpx<R> *__restrict__ out3,
+                                            const cpx<R> *__restrict__ dot3) {
     if (skip(state)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -960,6 +995,27 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
                 for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC);
             __syncthreads();
         }
+        if (out3) {   // MoDBFFT contraction in place of the store
+            if (colg < cols) {
+                const R w = (R)pweight(k3g, g.n3);
+                for (int e = eg0; e < N; e += egs) {
+                    cpx<R> r[3];
+                    modb_contract_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC, r);
+                    const size_t f = ((size_t)e * g.n2 + k2g) * H + k3g;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        out3[3 * f + c] = r[c];
+                        if (dot3) {
+                            const cpx<R> d = dot3[3 * f + c];
+                            acc.add_prod(w * r[c].x, d.x);
+                            acc.add_prod(w * r[c].y, d.y);
+                        }
+                    }
+                }
+            }
+            __syncthreads();   // the stage is read before the next load into it
+            continue;
+        }
         if (dot) {
             const int colt = g0 + lt / NC;
             if (colt < cols) {
@@ -981,7 +1037,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
         }
     }
     if (leader) bulk_wait_all();
-    if (dot) {
+    if (dot || (out3 && dot3)) {
         const double sum = block_sum(acc.value());
         if (threadIdx.x == 0) partials[blockIdx.x] = sum;
     }
@@ -1838,7 +1894,7 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
             const CUtensorMap *td = dot ? tma_map(g, dotv, TMA_X1, 1) : ti;
             const int grid = dot ? g.grid1d_tma : g.grid1_tma;
             const size_t sm = dot ? g.smem1d_tma : g.smem1_tma;
-#define HOM_X1T(NF) k_x1_tma<R, NF><<<grid, g.threads1, sm, st>>>(g, flags, *ti, *to, *td, partials, state)
+#define HOM_X1T(NF) k_x1_tma<R, NF><<<grid, g.threads1, sm, st>>>(g, flags, *ti, *to, *td, partials, state, nullptr, nullptr)
             switch (g.fast[0]) {
                 case 64: HOM_X1T(64); break;
                 case 96: HOM_X1T(96); break;
@@ -1855,6 +1911,30 @@ void Launch<R>::x1(const Geometry &g, cudaStream_t st, int flags, const cpx<R> *
 #define HOM_X1(NF) k_x1<R, NF><<<grid, g.threads1, g.smem1, st>>>(g, flags, in, out, dotv, partials, state)
     HOM_FAST_SWITCH(g.fast[0], HOM_X1)
 #undef HOM_X1
+}
+
+template <typename R>
+int Launch<R>::x1_modb_contract(const Geometry &g, cudaStream_t st, const cpx<R> *in10, cpx<R> *out3,
+                                const cpx<R> *dot3, double *partials, int max_partials, const MinresState *state) {
+    if constexpr (sizeof(R) == 4) {
+        if (g.tma && g.nc == 10 && g.grid1_tma > 0 && (!dot3 || g.grid1_tma <= max_partials)) {
+            const CUtensorMap *ti = tma_map(g, in10, TMA_X1, 1);
+#define HOM_X1C(NF)                                                                                              \
+    k_x1_tma<R, NF><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, X1_FWD, *ti, *ti, *ti, partials, state, out3, \
+                                                                dot3)
+            switch (g.fast[0]) {
+                case 64: HOM_X1C(64); break;
+                case 96: HOM_X1C(96); break;
+                case 160: HOM_X1C(160); break;
+                case 512: HOM_X1C(512); break;
+                case 128: HOM_X1C(128); break;
+                default: HOM_X1C(256); break;
+            }
+#undef HOM_X1C
+            return g.grid1_tma;
+        }
+    }
+    return 0;
 }
 
 // partials per load case written by the fused n1 pass (case c's at c * count)
