@@ -922,11 +922,11 @@ __device__ __forceinline__ void modb_contract_at(const Geometry &g, int k1, int 
     }
 }
 
-template <typename R, int NF>
-// With out3 (MoDBFFT, 10 components, forward): instead of storing the
+// With MC (MoDBFFT, 10 components, forward): instead of storing the
 // transformed tile, contract each frequency to the 3-component result
 // (modb_contract_at) and write it to out3, with the weighted dot product
 // against dot3 (if given) in the partials.
+template <typename R, int NF, bool MC = false>
 __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const __grid_constant__ CUtensorMap tin,
                                             const __grid_constant__ CUtensorMap tout,
                                             const __grid_constant__ CUtensorMap tdot, double *__restrict__ partials,
@@ -995,7 +995,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
                 for (int e = eg0; e < N; e += egs) gamma_at<R>(g, e, k2g, k3g, buf + e * L + tg * NC);
             __syncthreads();
         }
-        if (out3) {   // MoDBFFT contraction in place of the store
+        if constexpr (MC) {   // MoDBFFT contraction in place of the store
             if (colg < cols) {
                 const R w = (R)pweight(k3g, g.n3);
                 for (int e = eg0; e < N; e += egs) {
@@ -1037,7 +1037,7 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
         }
     }
     if (leader) bulk_wait_all();
-    if (dot || (out3 && dot3)) {
+    if (dot || (MC && dot3)) {
         const double sum = block_sum(acc.value());
         if (threadIdx.x == 0) partials[blockIdx.x] = sum;
     }
@@ -1733,6 +1733,7 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x2_tma<R, -1, NF>))  \
     HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
     HOM_SET_ATTR1((k_x1_tma<R, NF>))      \
+    HOM_SET_ATTR1((k_x1_tma<R, NF, true>)) \
     HOM_SET_ATTR1((k_x1_lanczos_tma<R, NF>))
         HOM_SET_TMA(64) HOM_SET_TMA(96) HOM_SET_TMA(128) HOM_SET_TMA(160) HOM_SET_TMA(256) HOM_SET_TMA(512)
 #undef HOM_SET_TMA
@@ -1920,8 +1921,8 @@ int Launch<R>::x1_modb_contract(const Geometry &g, cudaStream_t st, const cpx<R>
         if (g.tma && g.nc == 10 && g.grid1_tma > 0 && (!dot3 || g.grid1_tma <= max_partials)) {
             const CUtensorMap *ti = tma_map(g, in10, TMA_X1, 1);
 #define HOM_X1C(NF)                                                                                              \
-    k_x1_tma<R, NF><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, X1_FWD, *ti, *ti, *ti, partials, state, out3, \
-                                                                dot3)
+    k_x1_tma<R, NF, true><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, X1_FWD, *ti, *ti, *ti, partials, state, \
+                                                                      out3, dot3)
             switch (g.fast[0]) {
                 case 64: HOM_X1C(64); break;
                 case 96: HOM_X1C(96); break;
