@@ -74,3 +74,49 @@ def test_autotune_shapes_give_the_same_answer(hom):
         a0 = hom.hom_apply(c0, f)
         a1 = hom.hom_apply(c1, f)
         assert np.max(np.abs(a0 - a1)) <= FP32_TOL * np.max(np.abs(a0))
+
+
+def test_batch_of_laminates_on_the_fused_kernels(hom):
+    """Two layered cells at sizes that take the fused MINRES step (TMA-staged
+    n1 / n2 passes, the warp-specialised n1 pass with its lagged-update ring
+    and deferred x update, the persistent register n3 pass at n3 = 64 and the
+    two-stage shared-memory n3 pass at n3 = 96), solved together by
+    hom_solve_batch with the six unit strains stacked: every mean stress
+    against the exact laminate closed form (layers normal to e1)."""
+    from test_oracle_solver import laminate_closed_form
+    vals = (1.0, 0.2, 0.55)
+    cells = [((64, 64, 64), (32, 16, 16)), ((96, 64, 96), (48, 24, 24))]
+    ctxs = []
+    for shape, thick in cells:
+        phi = ri.laminate(shape, thick, vals, axis=0)
+        ctxs.append(hom.hom_create(phi.shape, phi.astype(np.float32), hom.HOM_INPUT_FRACTION_F32, E_M, NU_M))
+    try:
+        rc, infos = hom.hom_solve_batch(ctxs, np.eye(6), tol=1e-9, max_it=2000)
+        assert rc == hom.HOM_OK, [[i["status"] for i in cell] for cell in infos]
+        for (shape, thick), cell in zip(cells, infos):
+            fr = [t / shape[0] for t in thick]
+            for J in range(6):
+                ref = laminate_closed_form(list(vals), fr, np.eye(6)[J])
+                assert np.allclose(cell[J]["sigma_mean"], ref, rtol=1e-5, atol=1e-5 * E_M), (shape, J)
+                assert cell[J]["true_residual"] <= 1e-9
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_stacked_cases_match_one_at_a_time_64(hom):
+    """The same at 64^3, where the persistent register n3 pass and the
+    warp-specialised n1 pass run (cases that converge at different steps are
+    skipped by those kernels while the others go on)."""
+    phi, _ = ri.octet(64, 0.15)
+    macros = np.eye(6) * 1e-3
+    with hom.hom_create(phi.shape, phi, hom.HOM_INPUT_FRACTION_F32, E_M, NU_M) as ctx:
+        rc, together = hom.hom_solve(ctx, macros, tol=1e-8, max_it=5000)
+        assert rc == hom.HOM_OK
+        its = {i["iterations"] for i in together}
+        for k in range(6):
+            rc, alone = hom.hom_solve(ctx, macros[k], tol=1e-8, max_it=5000)
+            assert rc == hom.HOM_OK
+            ref = np.asarray(alone[0]["sigma_mean"])
+            assert np.max(np.abs(np.asarray(together[k]["sigma_mean"]) - ref)) <= 1e-6 * np.max(np.abs(ref))
+        assert len(its) > 1   # the cases did converge at different steps
