@@ -7,8 +7,9 @@ Checked through the C ABI against the existing hom_apply entry point, within
 the FP32 parity tolerance, on two calls in a row (the scratch arrays are
 shared by every call and keep the previous call's contents), and against the
 FP64 oracle's A(eps) of eq. (linearOp) for both derivative schemes, on the
-legacy default stream and on a side stream.  The call only enqueues its
-kernels, so each check synchronises before reading the output.  This file is
+legacy default stream, on a side stream and recorded in a CUDA graph.  The
+call only enqueues its kernels, so each check synchronises before reading the
+output.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test."""
 import numpy as np
@@ -87,3 +88,33 @@ def test_noalloc_rejects_grids_beyond_the_limit(hom):
         hom.hom_apply_noalloc(shape, phi, eps, torch.empty_like(eps))
     assert e.value.code == hom.HOM_EUNSUPPORTED_GRID
     assert "32768" in hom.hom_last_error(None)
+
+
+@pytest.mark.parametrize("deriv", [0, 1])
+def test_noalloc_recorded_in_a_cuda_graph(hom, deriv):
+    """The call records into a CUDA graph (it enqueues kernels only and does
+    not wait on the stream): one eager call first makes the per-device set-up,
+    then the call is captured on torch's capture stream and replayed on new
+    contents of the same input buffer; each replay is compared with the oracle."""
+    import torch
+    shape = (64, 16, 32)
+    phi = ri.random_phi(shape, seed=41).astype(np.float32)
+    phi_d = torch.tensor(phi, device="cuda")
+    eps = torch.zeros((6,) + shape, dtype=torch.float32, device="cuda")
+    out = torch.full_like(eps, float("nan"))
+    hom.hom_apply_noalloc(shape, phi_d, eps, out, E=E_M, nu=NU_M, derivative=deriv)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        hom.hom_apply_noalloc(shape, phi_d, eps, out, E=E_M, nu=NU_M, derivative=deriv,
+                              stream=torch.cuda.current_stream().cuda_stream)
+    for seed in (42, 43):
+        f = ri.random_field(shape, seed=seed)
+        eps.copy_(torch.tensor(f, dtype=torch.float32))
+        out.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        ref = oracle.apply(phi.astype(np.float64), 1.0, NU_M, deriv, f)
+        assert np.all(np.isfinite(got))
+        assert rel_maxerr(got, ref) <= FP32_TOL
