@@ -661,8 +661,13 @@ static int op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, con
     // returns the number of dot partials written (with dotv)
     cudaStream_t s = ctx->stream;
     const Geometry &g = E.gm;
-    Launch<R>::modb_expand(g, s, ctx->alpha, 1, u, E.spec10, 10, st);
-    Launch<R>::x1(g, s, 0, E.spec10, E.spec10, nullptr, nullptr, st);
+    // the expansion fused into the inverse n1 pass where it is TMA-staged
+    int nl = 4;   // launches before the forward n1 pass
+    if (!Launch<R>::x1_modb_expand(g, s, ctx->alpha, u, E.spec10, st)) {
+        Launch<R>::modb_expand(g, s, ctx->alpha, 1, u, E.spec10, 10, st);
+        Launch<R>::x1(g, s, 0, E.spec10, E.spec10, nullptr, nullptr, st);
+        nl += 1;
+    }
     Launch<R>::x2(g, s, 1, E.spec10, st);
     Launch<R>::x3(g, s, X3_IN_SPEC, E.spec10, X3_MID_MODB, ctx->lam, ctx->mu, nullptr, 1.0, X3_OUT_SPEC, E.spec10,
                   E.phi, st);
@@ -670,12 +675,12 @@ static int op_modb(hom_ctx *ctx, Engine<R> &E, const cpx<R> *u, cpx<R> *out, con
     // the forward n1 pass with the contraction fused where it is TMA-staged
     int np = Launch<R>::x1_modb_contract(g, s, E.spec10, out, dotv, partials, ctx->npartials, st);
     if (np > 0) {
-        ctx->launches += 6;
+        ctx->launches += nl + 1;
         return np;
     }
     Launch<R>::x1(g, s, X1_FWD, E.spec10, E.spec10, nullptr, nullptr, st);
     Launch<R>::modb_contract(g, s, E.spec10, out, dotv, partials, st);
-    ctx->launches += 7;
+    ctx->launches += nl + 2;
     return Launch<R>::ew_grid(g.S);
 }
 

@@ -287,6 +287,12 @@ template <typename R> struct Launch {
     // apply (not the TMA-staged FP32 pass, or more partials than max_partials).
     static int x1_modb_contract(const Geometry &g, cudaStream_t st, const cpx<R> *in10, cpx<R> *out3,
                                 const cpx<R> *dot3, double *partials, int max_partials, const MinresState *state);
+    // MoDBFFT: the expansion of u3 to 10 components with the penalty alpha
+    // (modb_expand) and the inverse n1 pass as one TMA-staged FP32 pass into
+    // out10.  Returns false without launching where the fused form does not
+    // apply (not the TMA-staged FP32 pass).
+    static bool x1_modb_expand(const Geometry &g, cudaStream_t st, double alpha, const cpx<R> *u3, cpx<R> *out10,
+                               const MinresState *state);
     // MINRES step k on unnormalised Lanczos vectors u_j = beta_j v_j, p = A u_k:
     //   um <- (p - alpha u_k - beta_k^2/beta_{k-1} um) / beta_k   (= u_{k+1}),
     //   weighted partial ||u_{k+1}||^2, and the lagged update of step k-1

@@ -28,51 +28,17 @@ __device__ __forceinline__ void modb_freq(const Geometry &g, int f, double q[3],
     }
 }
 
-// out10 = (sym(u (x) xi) Mandel, alpha sym(u (x) xi) . xi, 0)
+// out10 = (sym(u (x) xi) Mandel, alpha sym(u (x) xi) . xi, 0), or the first
+// six with nc_out = 6 (modb_expand_at)
 template <typename R>
 __global__ void k_modb_expand(Geometry g, R alpha, int with_penalty, const cpx<R> *__restrict__ u,
                               cpx<R> *__restrict__ out, int nc_out, const MinresState *state) {
     if (state && state->done) return;
-    const R tp = (R)6.28318530717958647692;   // 2 pi
-    const R r2 = (R)1.41421356237309504880;
+    const int hh = g.h;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < (int)g.S; f += gridDim.x * blockDim.x) {
-        double qd[3];
-        int k3;
-        modb_freq(g, f, qd, k3);
-        cpx<R> *o = out + (size_t)f * nc_out;
-        if (qd[0] == 0.0 && qd[1] == 0.0 && qd[2] == 0.0) {
-            for (int c = 0; c < nc_out; ++c) o[c] = mk<R>(0, 0);
-            continue;
-        }
-        // xi = i s, s = 2 pi q (real): sym(u (x) xi)_ij = i/2 (u_i s_j + u_j s_i)
-        const R s0 = tp * (R)qd[0], s1 = tp * (R)qd[1], s2 = tp * (R)qd[2];
-        const cpx<R> u0 = u[3 * f], u1 = u[3 * f + 1], u2 = u[3 * f + 2];
-        auto isym = [](cpx<R> a, R sa, cpx<R> b, R sb) {   // i/2 (a sb + b sa)
-            const R re = (R)0.5 * (a.x * sb + b.x * sa), im = (R)0.5 * (a.y * sb + b.y * sa);
-            return mk<R>(-im, re);
-        };
-        const cpx<R> e00 = isym(u0, s0, u0, s0), e11 = isym(u1, s1, u1, s1), e22 = isym(u2, s2, u2, s2);
-        const cpx<R> e12 = isym(u1, s1, u2, s2), e02 = isym(u0, s0, u2, s2), e01 = isym(u0, s0, u1, s1);
-        o[0] = e00;
-        o[1] = e11;
-        o[2] = e22;
-        o[3] = scale<R>(e12, r2);
-        o[4] = scale<R>(e02, r2);
-        o[5] = scale<R>(e01, r2);
-        if (nc_out == 10) {
-            // g_i = alpha sum_j e_ij xi_j = alpha i sum_j e_ij s_j
-            cpx<R> gv[3];
-            const cpx<R> E[3][3] = {{e00, e01, e02}, {e01, e11, e12}, {e02, e12, e22}};
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const cpx<R> t = add<R>(add<R>(scale<R>(E[i][0], s0), scale<R>(E[i][1], s1)), scale<R>(E[i][2], s2));
-                gv[i] = with_penalty ? mk<R>(-alpha * t.y, alpha * t.x) : mk<R>(0, 0);
-            }
-            o[6] = gv[0];
-            o[7] = gv[1];
-            o[8] = gv[2];
-            o[9] = mk<R>(0, 0);
-        }
+        const int k3 = f % hh, rest = f / hh;
+        const int k2 = rest % g.n2, k1 = rest / g.n2;
+        modb_expand_at<R>(g, k1, k2, k3, u + 3 * (size_t)f, alpha, with_penalty, nc_out, out + (size_t)f * nc_out);
     }
 }
 

@@ -922,6 +922,55 @@ __device__ __forceinline__ void modb_contract_at(const Geometry &g, int k1, int 
     }
 }
 
+// MoDBFFT expansion at frequency (k1, k2, k3) of the displacement u (3
+// components), eq. (modbfftfop): o = sym(u (x) xi) in Mandel order and, with
+// nc_out = 10, the penalty vector alpha sym(u (x) xi) . xi (0 without the
+// penalty) and a zero pad; xi = i 2 pi q, q the integer frequency (0 on a
+// Nyquist index); o = 0 at xi = 0.  The point-wise expansion kernel and the
+// inverse n1 pass with the expansion fused both take it from here.
+template <typename R>
+__device__ __forceinline__ void modb_expand_at(const Geometry &g, int k1, int k2, int k3, const cpx<R> *u, R alpha,
+                                               int with_penalty, int nc_out, cpx<R> *o) {
+    const int ks[3] = {k1, k2, k3}, ns[3] = {g.n1, g.n2, g.n3};
+    double qd[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int n = ns[p], k = ks[p];
+        qd[p] = ((n & 1) == 0 && 2 * k == n) ? 0.0 : (double)((2 * k < n) ? k : k - n);
+    }
+    if (qd[0] == 0.0 && qd[1] == 0.0 && qd[2] == 0.0) {
+        for (int c = 0; c < nc_out; ++c) o[c] = mk<R>(0, 0);
+        return;
+    }
+    const R tp = (R)6.28318530717958647692;   // 2 pi
+    const R r2 = (R)1.41421356237309504880;
+    // xi = i s, s = 2 pi q (real): sym(u (x) xi)_ij = i/2 (u_i s_j + u_j s_i)
+    const R s0 = tp * (R)qd[0], s1 = tp * (R)qd[1], s2 = tp * (R)qd[2];
+    const cpx<R> u0 = u[0], u1 = u[1], u2 = u[2];
+    auto isym = [](cpx<R> a, R sa, cpx<R> b, R sb) {   // i/2 (a sb + b sa)
+        const R re = (R)0.5 * (a.x * sb + b.x * sa), im = (R)0.5 * (a.y * sb + b.y * sa);
+        return mk<R>(-im, re);
+    };
+    const cpx<R> e00 = isym(u0, s0, u0, s0), e11 = isym(u1, s1, u1, s1), e22 = isym(u2, s2, u2, s2);
+    const cpx<R> e12 = isym(u1, s1, u2, s2), e02 = isym(u0, s0, u2, s2), e01 = isym(u0, s0, u1, s1);
+    o[0] = e00;
+    o[1] = e11;
+    o[2] = e22;
+    o[3] = scale<R>(e12, r2);
+    o[4] = scale<R>(e02, r2);
+    o[5] = scale<R>(e01, r2);
+    if (nc_out == 10) {
+        // g_i = alpha sum_j e_ij xi_j = alpha i sum_j e_ij s_j
+        const cpx<R> E[3][3] = {{e00, e01, e02}, {e01, e11, e12}, {e02, e12, e22}};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const cpx<R> t = add<R>(add<R>(scale<R>(E[i][0], s0), scale<R>(E[i][1], s1)), scale<R>(E[i][2], s2));
+            o[6 + i] = with_penalty ? mk<R>(-alpha * t.y, alpha * t.x) : mk<R>(0, 0);
+        }
+        o[9] = mk<R>(0, 0);
+    }
+}
+
 // With MC (MoDBFFT, 10 components, forward): instead of storing the
 // transformed tile, contract each frequency to the 3-component result
 // (modb_contract_at) and write it to out3, with the weighted dot product
@@ -1041,6 +1090,53 @@ __global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma(Geometry g, int flags, const 
         const double sum = block_sum(acc.value());
         if (threadIdx.x == 0) partials[blockIdx.x] = sum;
     }
+}
+
+// MoDBFFT inverse n1 pass with the expansion fused (TMA-staged, FP32, 10
+// components): each tile is formed in shared memory from u (3 components,
+// plain loads) by modb_expand_at with the penalty, transformed (inverse DFT
+// along n1) and stored by TMA, so that the 10-component spectrum is written
+// once instead of being written by the expansion kernel and read back by the
+// pass.  Two stage buffers: a tile is expanded into one while the store of
+// the previous tile still reads the other.
+template <typename R, int NF>
+__global__ void HOM_PASS_BOUNDS_NF(R, NF) k_x1_tma_expand(Geometry g, const __grid_constant__ CUtensorMap tout,
+                                                   const cpx<R> *__restrict__ u3, R alpha,
+                                                   const MinresState *state) {
+    if (skip(state)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int NC = g.nc, N = g.n1, T = g.tile1, H = g.h, L = NC * T;
+    const int cols = g.n2 * H;
+    const int ntiles = (cols + T - 1) / T;
+    const int tile_elems = N * L;
+    cpx<R> *base = reinterpret_cast<cpx<R> *>(smem_raw);
+    const bool leader = threadIdx.x == 0;
+    const cpx<R> *tw = reinterpret_cast<const cpx<R> *>(g.ax[0].tw);
+    const int tg = threadIdx.x % T, eg0 = threadIdx.x / T, egs = blockDim.x / T;
+    for (int i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += gridDim.x) {
+        cpx<R> *buf = base + (i & 1) * tile_elems;
+        // the store issued from this stage two tiles ago has read its source
+        if (leader) bulk_wait_read_1();
+        __syncthreads();
+        const int colg = tile * T + tg;
+        const int k2g = colg / H, k3g = colg - k2g * H;
+        for (int e = eg0; e < N; e += egs) {
+            cpx<R> *o = buf + e * L + tg * NC;
+            if (colg < cols)
+                modb_expand_at<R>(g, e, k2g, k3g, u3 + 3 * (((size_t)e * g.n2 + k2g) * H + k3g), alpha, 1, NC, o);
+            else
+                for (int c = 0; c < NC; ++c) o[c] = mk<R>(0, 0);
+        }
+        __syncthreads();
+        fast_fft<R, 1, NF>(buf, L, L, tw);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (leader) {
+            tma_store_rows_2d(&tout, NC * T * tile, 0, N, buf, L * (int)sizeof(cpx<R>));
+            bulk_commit();
+        }
+    }
+    if (leader) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -1734,6 +1830,7 @@ void Launch<R>::table_init(const Geometry &) {
     HOM_SET_ATTR1((k_x2_tma<R, 1, NF>))   \
     HOM_SET_ATTR1((k_x1_tma<R, NF>))      \
     HOM_SET_ATTR1((k_x1_tma<R, NF, true>)) \
+    HOM_SET_ATTR1((k_x1_tma_expand<R, NF>)) \
     HOM_SET_ATTR1((k_x1_lanczos_tma<R, NF>))
         HOM_SET_TMA(64) HOM_SET_TMA(96) HOM_SET_TMA(128) HOM_SET_TMA(160) HOM_SET_TMA(256) HOM_SET_TMA(512)
 #undef HOM_SET_TMA
@@ -1936,6 +2033,30 @@ int Launch<R>::x1_modb_contract(const Geometry &g, cudaStream_t st, const cpx<R>
         }
     }
     return 0;
+}
+
+template <typename R>
+bool Launch<R>::x1_modb_expand(const Geometry &g, cudaStream_t st, double alpha, const cpx<R> *u3, cpx<R> *out10,
+                               const MinresState *state) {
+    if constexpr (sizeof(R) == 4) {
+        if (g.tma && g.nc == 10 && g.grid1_tma > 0) {
+            const CUtensorMap *to = tma_map(g, out10, TMA_X1, 1);
+            if (!to) return false;
+#define HOM_X1E(NF) \
+    k_x1_tma_expand<R, NF><<<g.grid1_tma, g.threads1, g.smem1_tma, st>>>(g, *to, u3, (R)alpha, state)
+            switch (g.fast[0]) {
+                case 64: HOM_X1E(64); break;
+                case 96: HOM_X1E(96); break;
+                case 160: HOM_X1E(160); break;
+                case 512: HOM_X1E(512); break;
+                case 128: HOM_X1E(128); break;
+                default: HOM_X1E(256); break;
+            }
+#undef HOM_X1E
+            return true;
+        }
+    }
+    return false;
 }
 
 // partials per load case written by the fused n1 pass (case c's at c * count)
