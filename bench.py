@@ -174,6 +174,18 @@ def reduce_over_ranks(dist, t_local, units_local, device):
     return float(t.item()), float(u.item())
 
 
+def step_stats(step_ms, step_units):
+    """Best and median over the timed solves: per-solve milliseconds (CUDA
+    events on the library's stream between consecutive solves) and the
+    voxel-iterations/s each solve gives.  None without a timed solve."""
+    if not step_ms:
+        return None
+    rates = [u / (ms * 1e-3) for ms, u in zip(step_ms, step_units) if ms > 0]
+    return {"n": len(step_ms), "best_ms": min(step_ms), "median_ms": statistics.median(step_ms),
+            "best_voxel_iters_per_s": max(rates) if rates else None,
+            "median_voxel_iters_per_s": statistics.median(rates) if rates else None}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -332,15 +344,19 @@ def run_ours(args):
     l0 = hom.hom_kernel_launches(ctx)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]   # after each solve
     barrier()
     ev0.record(stream)
-    iters, infos = 0, []
-    for _ in range(args.steps):
+    iters, infos, step_units = 0, [], []
+    for i in range(args.steps):
         rc, inf = step()
+        marks[i].record(stream)
         iters += inf["iterations"]
+        step_units.append(V * inf["iterations"])
         infos.append(inf)
     ev1.record(stream)
     barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip([ev0] + marks[:-1], marks)]
     launches = hom.hom_kernel_launches(ctx) - l0
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
@@ -410,6 +426,7 @@ def run_ours(args):
                                **({"loop": "host-replayed body"} if args.host_loop else {})),
                 "iterations_per_step": iters / args.steps,
                 "time_to_tol_ms": 1e3 * t_max / args.steps,
+                "step_ms": step_stats(step_ms, step_units),
                 "true_residual": last["true_residual"], "sweeps": last["sweeps"],
                 "sigma11_pa": float(last["sigma_mean"][0]),
                 "vs_fp64_oracle": oracle_error(n, args.rho, last["sigma_mean"]),

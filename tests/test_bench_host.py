@@ -89,3 +89,13 @@ def test_j2_cpu_sample_counts_the_oracle_minres_iterations():
     phi, _ = ri.octet(12, 0.2)
     lin, dt, cores = bench.j2_cpu_sample(phi.astype(np.float64), 110e9, 0.3, 70e6, 1.1e9, -2.5e-3, 7)
     assert lin == 7 and dt > 0 and cores >= 1
+
+
+def test_step_stats_best_and_median():
+    """best and median of the timed solves, and the rate of each"""
+    import bench
+    st = bench.step_stats([350.0, 340.0, 360.0, 345.0, 355.0], [4.0e9] * 5)
+    assert st["n"] == 5 and st["best_ms"] == 340.0 and st["median_ms"] == 350.0
+    assert abs(st["best_voxel_iters_per_s"] - 4.0e9 / 0.340) < 1.0
+    assert abs(st["median_voxel_iters_per_s"] - 4.0e9 / 0.350) < 1.0
+    assert bench.step_stats([], []) is None
