@@ -99,3 +99,24 @@ def test_step_stats_best_and_median():
     assert abs(st["best_voxel_iters_per_s"] - 4.0e9 / 0.340) < 1.0
     assert abs(st["median_voxel_iters_per_s"] - 4.0e9 / 0.350) < 1.0
     assert bench.step_stats([], []) is None
+
+
+def test_roofline_bytes_per_voxel():
+    """the bench's algorithmic bytes: one MINRES iteration with FP32 fields
+    reads five 6-component real fields (v_k, v_{k-1}, w_{k-1}, w_{k-2}, x,
+    24 B each) and phi (4 B) and writes three (v_{k+1}, w_k, x): 196 B per
+    voxel; a half spectrum of 6 complex64 per frequency holds (n/2+1)/n
+    frequencies per voxel; the n2 passes read and write it once, the n3 pass
+    also reads phi, the fused n1 pass reads 5 and writes 3 spectra plus x
+    (read and written) on one step in three"""
+    import bench
+    assert bench.ITER_BYTES_PER_VOXEL == 5 * 24 + 4 + 3 * 24
+    n = 256
+    spec = 6 * 8 * (n // 2 + 1) / n
+    kb = bench.kernel_bytes_per_voxel(n)
+    assert abs(kb["x2_inv"] - 2 * spec) < 1e-9 and abs(kb["x2_fwd"] - 2 * spec) < 1e-9
+    assert abs(kb["x3_c2r_law_energy_r2c"] - (2 * spec + 4)) < 1e-9
+    assert abs(kb["x1_fwd_lanczos_inv"] - (5 + 3 + 2 / 3) * spec) < 1e-9
+    # the figures quoted for 256^3: 48.4, 52.4, 209.6 and about 359 in all
+    assert [round(kb[k], 1) for k in ("x2_inv", "x3_c2r_law_energy_r2c", "x1_fwd_lanczos_inv")] == [48.4, 52.4, 209.6]
+    assert round(sum(kb.values())) == 359
