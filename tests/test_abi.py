@@ -78,3 +78,46 @@ def test_missing_library_fails_loudly(tmp_path):
             hom.load_library(str(tmp_path / "nope.so"))
     finally:
         hom._lib = saved
+
+
+@pytest.mark.parametrize("kw, msg", [
+    (dict(E=0.0), "E > 0"),
+    (dict(nu=0.5), "nu < 0.5"),
+    (dict(input_kind=7), "input_kind"),
+    (dict(smoothing=3), "smoothing"),
+    (dict(derivative=5), "derivative"),
+    (dict(solver=9), "solver"),
+    (dict(precision=4), "precision"),
+    (dict(shape=(65, 0, 0)), "launch-shape"),
+    (dict(sweep_floor=1.0), "sweep_floor"),
+])
+def test_create_rejects_bad_arguments_before_device_work(lib, kw, msg):
+    """hom_create checks its arguments before it touches a device: each bad
+    one returns HOM_EINVAL with its message (this runs without a GPU)"""
+    import numpy as np
+    from paper_2110_00733_gb300 import hom
+    phi = np.zeros((8, 8, 8), np.float32)
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create((8, 8, 8), phi, **kw)
+    assert e.value.code == hom.HOM_EINVAL
+    assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("grid, kw, code", [
+    ((65, 8, 8), {}, "HOM_EUNSUPPORTED_GRID"),
+    ((7, 8, 8), {}, "HOM_EUNSUPPORTED_GRID"),
+    ((64, 32, 20), {}, "HOM_EUNSUPPORTED_GRID"),
+    ((8, 8, 8), dict(E=-1.0), "HOM_EINVAL"),
+    ((8, 8, 8), dict(derivative=3), "HOM_EINVAL"),
+])
+def test_noalloc_rejects_bad_arguments_before_device_work(lib, grid, kw, code):
+    """the allocation-free A(eps) checks grid sizes (each in [2, 64] of the
+    form 2^a 3^b 5^c, at most 32768 voxels), E, nu and the derivative before
+    it touches a device"""
+    import numpy as np
+    from paper_2110_00733_gb300 import hom
+    phi = np.zeros(grid, np.float32)
+    eps = np.zeros((6,) + grid, np.float32)
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_apply_noalloc(grid, phi, eps, np.zeros_like(eps), **kw)
+    assert e.value.code == getattr(hom, code)
